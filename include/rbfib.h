@@ -1,0 +1,185 @@
+/* rbfib.h - C ABI of the GB300 RB-FIB mobility-solve library (librbfib.so).
+ *
+ * The library solves the constrained saddle-point system of the Rigid-Body
+ * Fluctuating Immersed Boundary method (Sprinkle, Donev, Bhalla, Patankar,
+ * "Brownian dynamics of fully confined suspensions of rigid particles without
+ * Green's functions", Sec. III.C, Eqs. LangevinD1-D4) and advances rigid
+ * bodies with the Split-Euler-Maruyama scheme (Sec. IV.B, Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ *  - Units: h, eta, kT and dt are inputs; all lengths are in the same units.
+ *  - Pointers marked "device" are CUDA device memory owned by the caller; they
+ *    are read/written only during the call, in stream order on the grid's
+ *    stream.  Pointers marked "host" are host memory.  The library owns its own
+ *    workspaces (allocated in rbfib_create_grid / rbfib_set_bodies).
+ *  - Every call is asynchronous on the grid's stream unless it says otherwise;
+ *    calls that return solver information synchronise the stream.
+ *  - Return value: RBFIB_OK (0) or a negative RBFIB_E* status; no call exits,
+ *    traps or throws.  rbfib_last_error() gives a one-line message.
+ *  - Grid layout: velocity component a lives on a-faces.  Along its own axis a
+ *    the unknown faces are physical faces p = 1..n_a-1 (wall axis; the two
+ *    boundary faces carry zero normal velocity) or p = 0..n_a-1 (periodic),
+ *    compact index p-1 or p; along the other axes faces sit at cell centres.
+ *    Arrays are x-fastest over each component's extents.  Cells (i,j,k) are
+ *    x-fastest.  Blob arrays are (N_bl, 3) row-major, body arrays (N_b, 6) =
+ *    (u_x, u_y, u_z, w_x, w_y, w_z) or (f, tau).
+ *  - Saddle vector x = [v_x | v_y | v_z | pi | lambda (N_bl x 3) | U (N_b x 6)]
+ *    (offsets from rbfib_saddle_layout).
+ */
+#ifndef RBFIB_H
+#define RBFIB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  RBFIB_OK = 0,
+  RBFIB_EINVAL = -1,     /* bad argument or unsupported configuration        */
+  RBFIB_ENOCONV = -2,    /* Krylov solve hit max_iter above the tolerance    */
+  RBFIB_ENAN = -3,       /* non-finite residual                              */
+  RBFIB_EREJECT = -4,    /* SEM step produced an unphysical configuration    */
+  RBFIB_ETIMEOUT = -5,   /* a bounded device-side wait gave up               */
+  RBFIB_ECUDA = -6,      /* a CUDA runtime call failed                       */
+  RBFIB_EINTERNAL = -7   /* internal inconsistency (device error word set)   */
+};
+
+enum { RBFIB_FP64 = 0, RBFIB_FP32_REFINED = 1 };   /* rbfib_grid_desc.precision */
+enum { RBFIB_DTYPE_F64 = 0, RBFIB_DTYPE_F32 = 1 };  /* element type of a vector  */
+
+typedef struct rbfib_grid rbfib_grid;   /* opaque; owns all device workspaces */
+
+/* Grid and solver description (Sec. III.A).  A domain with every axis periodic
+ * is rejected (EINVAL). */
+typedef struct {
+  int32_t n[3];              /* cells per axis                                  */
+  double  h;                 /* grid spacing; cell volume dV = h^3              */
+  double  eta;               /* viscosity                                       */
+  int32_t periodic[3];       /* 1: periodic axis, 0: no-slip walls on both ends */
+  double  wall_vel[6][3];    /* walls -x,+x,-y,+y,-z,+z; tangential components  */
+                             /* only (a normal component gives EINVAL)          */
+  int32_t kernel;            /* 3 = three-point Peskin kernel (only value)      */
+  int32_t precision;         /* RBFIB_FP64 or RBFIB_FP32_REFINED                */
+  int32_t restart;           /* FGMRES restart length m (1..64)                 */
+  int32_t max_iter;          /* total Krylov iterations allowed per solve       */
+  double  rtol;              /* relative residual ||b - A x||_W / ||b||_W       */
+} rbfib_grid_desc;
+
+typedef struct {
+  int32_t iterations;        /* Krylov iterations (all restarts, inner solves)  */
+  int32_t refinements;       /* outer FP64 refinement sweeps (FP32 mode)        */
+  double  rel_residual;      /* true relative residual of the returned x        */
+} rbfib_solve_info;
+
+/* Parameters of one Split-Euler-Maruyama step (Algorithm 1) and of the
+ * potentials of Sec. V (a zero strength switches a potential off).  The force
+ * law of each potential: Usoft Eq. (Usoft), Yukawa Eq. (YukawaPot),
+ * substrate Sec. V.B.1. */
+typedef struct {
+  double dt, kT;
+  double delta;              /* RFD step; <= 0 selects eps^(1/3), eps = 2^-52    */
+  double gravity;            /* force -gravity * z on every body                */
+  double pair_phi0, pair_b, pair_d;      /* Usoft between body centres          */
+  double wall_phi0, wall_b, wall_d;      /* Usoft between centres and walls     */
+  double blob_wall_phi0, blob_wall_b, blob_wall_d;   /* Usoft blob-wall         */
+  double yukawa_u0, yukawa_dh, yukawa_lambda;        /* Yukawa pair             */
+  double substrate_u0, substrate_s;                  /* substrate potential     */
+  const double* force_ext;   /* device (N_b, 6) extra force/torque or NULL      */
+  const double* slip;        /* device (N_bl, 3) active slip or NULL            */
+} rbfib_sem_params;
+
+typedef struct {
+  rbfib_solve_info solve_rfd;       /* Algorithm 1 step 2                        */
+  rbfib_solve_info solve_stokes;    /* Algorithm 1 step 4                        */
+  rbfib_solve_info solve_main;      /* Algorithm 1 step 6                        */
+  int32_t rejected;                 /* 1 if the new configuration was rejected   */
+} rbfib_step_info;
+
+/* Create a grid object bound to a CUDA stream (cudaStream_t, NULL = default).
+ * Allocates the fluid workspaces and the multigrid hierarchy. */
+int rbfib_create_grid(const rbfib_grid_desc* desc, void* cuda_stream, rbfib_grid** out);
+void rbfib_destroy(rbfib_grid* g);
+const char* rbfib_last_error(const rbfib_grid* g);   /* g may be NULL */
+
+/* Bodies as rigid agglomerates of blobs (Sec. III.B).  blob_offsets (host,
+ * n_bodies+1) delimit each body's blobs; ref_blobs (device, N_bl x 3) are the
+ * blob offsets in the body frame; q (device, N_b x 3) tracking points; quat
+ * (device, N_b x 4) unit quaternions (w,x,y,z).  Blob positions are
+ * r_i = q_p + R(quat_p) ref_i.  Builds the blob-to-cell binning and the
+ * body-block preconditioner.  Synchronises the stream. */
+int rbfib_set_bodies(rbfib_grid* g, int32_t n_bodies, const int32_t* blob_offsets,
+                     const double* ref_blobs, const double* q, const double* quat);
+
+/* offsets[7] = start of v_x, v_y, v_z, pi, lambda, U and the total length. */
+int rbfib_saddle_layout(const rbfib_grid* g, int64_t offsets[7]);
+
+/* y = A x for the homogeneous saddle operator (Sec. III.C; sign convention:
+ *   [-eta LL  G  -S  0; -D 0 0 0; -J 0 0 K; 0 0 K^T 0],
+ * self-adjoint in the inner product weighted by dV on v and pi).  x and y are
+ * device vectors of the saddle layout with element type dtype.  K^T sums are
+ * accumulated in FP64 for either dtype. */
+int rbfib_apply_saddle(rbfib_grid* g, const void* x, void* y, int32_t dtype);
+
+/* Solve the constrained system (Eqs. LangevinD1-D4) with forces/torques FT
+ * (device N_b x 6), optional active slip (device N_bl x 3), optional fluid
+ * forcing (device, N_f face values added to the momentum right-hand side) and
+ * the moving-wall terms of the grid.  Writes U (device N_b x 6) and, if
+ * x_full != NULL, the whole solution (device, saddle layout, FP64, mean(pi)=0).
+ * Uses right-preconditioned FGMRES to desc.rtol.  Synchronises. */
+int rbfib_mobility_solve(rbfib_grid* g, const double* FT, const double* slip,
+                         const double* fluid_rhs, double* U, double* x_full,
+                         rbfib_solve_info* info);
+
+/* Unconstrained Stokes solve (Algorithm 1 step 4): -eta LL v + G pi = f,
+ * -D v = 0 with homogeneous boundary conditions; f and v are device face
+ * arrays (N_f, FP64); pi (device N_c, FP64, mean zero) may be NULL. */
+int rbfib_stokes_solve(rbfib_grid* g, const double* f, double* v, double* pi,
+                       rbfib_solve_info* info);
+
+/* One Split-Euler-Maruyama step (Algorithm 1, steps 1-7) from the
+ * configuration (q, quat) (device, in/out).  Random numbers come from
+ * Philox4x64-10 with key (seed, 0) and counter (block, step,
+ * (attempt << 32) | purpose, 0).  On an unphysical new configuration (a blob
+ * outside the domain along a wall axis) q and quat are left unchanged and the
+ * call returns RBFIB_EREJECT; retry with attempt + 1 (Sec. V). */
+int rbfib_sem_step(rbfib_grid* g, const rbfib_sem_params* p, uint64_t seed, uint64_t step,
+                   uint32_t attempt, double* q, double* quat, rbfib_step_info* info);
+
+/* ---- building blocks of the hot path, exposed for parity checks ---------- */
+
+/* Blob-to-cell counting sort of the current bodies: perm (device int32 N_bl)
+ * and cell_offsets (device int32 N_c + 1); the blobs of cell c are
+ * perm[cell_offsets[c] .. cell_offsets[c+1]) in increasing blob id.  Cell
+ * index: floor(x/h) per axis, clamped on wall axes, wrapped on periodic ones. */
+int rbfib_binning(rbfib_grid* g, int32_t* perm, int32_t* cell_offsets);
+
+/* Current blob positions r (device, N_bl x 3, FP64). */
+int rbfib_blob_positions(rbfib_grid* g, double* r);
+
+/* count standard normals of the Philox stream (seed, step, attempt, purpose)
+ * into out (device FP64): normal g is lane g%4 of block g/4 (Box-Muller on the
+ * block's uniforms u = (2 (word >> 12) + 1) 2^-53, lanes (0,1) and (2,3)). */
+int rbfib_philox_normals(rbfib_grid* g, uint64_t seed, uint64_t step, uint32_t attempt,
+                         uint32_t purpose, int64_t count, double* out);
+
+/* Fluid forcing sqrt(2 eta kT / (dV dt)) DD W of Eq. LangevinD1 for the
+ * stress drawn from purpose 1 of the Philox stream (device out, N_f FP64). */
+int rbfib_stochastic_forcing(rbfib_grid* g, double kT, double dt, uint64_t seed,
+                             uint64_t step, uint32_t attempt, double* out);
+
+/* Spreading f = S lambda (device lambda N_bl x 3 -> device f N_f, FP64) and
+ * interpolation u = J v (device v N_f -> device u N_bl x 3, FP64; with_walls
+ * adds the ghost values of moving walls) at the current blob positions. */
+int rbfib_spread(rbfib_grid* g, const double* lambda, double* f);
+int rbfib_interpolate(rbfib_grid* g, const double* v, double* u, int32_t with_walls);
+
+/* Body forces and torques of the potentials in p at the current configuration
+ * (device out N_b x 6). */
+int rbfib_body_forces(rbfib_grid* g, const rbfib_sem_params* p, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBFIB_H */

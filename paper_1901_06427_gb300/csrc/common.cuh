@@ -1,0 +1,158 @@
+// Shared device-side definitions: grid dimensions, index decoding, the
+// three-point kernel and its wall folding.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+typedef long long i64;
+
+// Dimensions of one (multigrid) level of the MAC grid.  Spacing may differ per
+// axis on semi-coarsened levels.
+struct Dims {
+  int n[3];          // cells per axis
+  int per[3];        // 1 = periodic axis
+  double h[3];       // spacing per axis
+  int fe[3][3];      // fe[a][ax]: extent of component a's unknown faces along ax
+  i64 fo[4];         // offsets of the three face blocks; fo[3] = N_f
+  i64 nc;            // N_c
+};
+
+inline Dims make_dims(const int n[3], const int per[3], const double h[3]) {
+  Dims d;
+  for (int a = 0; a < 3; ++a) { d.n[a] = n[a]; d.per[a] = per[a]; d.h[a] = h[a]; }
+  i64 off = 0;
+  for (int a = 0; a < 3; ++a) {
+    for (int ax = 0; ax < 3; ++ax) d.fe[a][ax] = n[ax];
+    if (!per[a]) d.fe[a][a] = n[a] - 1;
+    d.fo[a] = off;
+    off += (i64)d.fe[a][0] * d.fe[a][1] * d.fe[a][2];
+  }
+  d.fo[3] = off;
+  d.nc = (i64)n[0] * n[1] * n[2];
+  return d;
+}
+
+__host__ __device__ inline i64 flat3(const int e[3], int i, int j, int k) {
+  return (i64)i + (i64)e[0] * ((i64)j + (i64)e[1] * k);
+}
+
+// Decode a global face index into (component, i, j, k).
+__device__ inline void decode_face(const Dims& d, i64 f, int& a, int c[3]) {
+  a = (f >= d.fo[1]) + (f >= d.fo[2]);
+  i64 l = f - d.fo[a];
+  const int e0 = d.fe[a][0], e1 = d.fe[a][1];
+  c[0] = (int)(l % e0);
+  i64 t = l / e0;
+  c[1] = (int)(t % e1);
+  c[2] = (int)(t / e1);
+}
+
+__device__ inline void decode_cell(const Dims& d, i64 l, int c[3]) {
+  c[0] = (int)(l % d.n[0]);
+  i64 t = l / d.n[0];
+  c[1] = (int)(t % d.n[1]);
+  c[2] = (int)(t / d.n[1]);
+}
+
+// Three-point Peskin kernel: the unique phi on |r| < 3/2 with partition of
+// unity, zero first moment and sum of squares 1/2.
+__device__ inline double phi3(double r) {
+  r = fabs(r);
+  if (r <= 0.5) return (1.0 + sqrt(1.0 - 3.0 * r * r)) / 3.0;
+  if (r < 1.5) {
+    double t = 1.0 - r;
+    return (5.0 - 3.0 * r - sqrt(1.0 - 3.0 * t * t)) / 6.0;
+  }
+  return 0.0;
+}
+
+// phi'(r), odd in r.
+__device__ inline double dphi3(double r) {
+  double a = fabs(r), s = r < 0 ? -1.0 : 1.0;
+  if (a <= 0.5) return s * (-a / sqrt(1.0 - 3.0 * a * a));
+  if (a < 1.5) {
+    double t = 1.0 - a;
+    return s * ((-3.0 - 3.0 * t / sqrt(1.0 - 3.0 * t * t)) / 6.0);
+  }
+  return 0.0;
+}
+
+// The three kernel points of a blob coordinate x along axis ax for velocity
+// component a, folded at walls:
+//   - a point on a wall-normal boundary face is dropped (zero normal velocity);
+//   - a point beyond a wall mirrors onto the reflected interior point with
+//     sign -1; a tangential ghost also records which wall it came from (its
+//     affine ghost value is 2 u_w);
+//   - a point whose mirror is not an unknown is dropped.
+struct AxisStencil {
+  int idx[3];      // compact index along the axis
+  double w[3];     // kernel weight phi(s - p)
+  double dw[3];    // dphi/dx (derivative with respect to the blob coordinate)
+  signed char sgn[3];
+  signed char wall[3];   // tangential ghost wall id (2 ax or 2 ax + 1) or -1
+  bool keep[3];
+};
+
+__device__ inline void axis_stencil(const Dims& d, int a, int ax, double x, AxisStencil& S) {
+  const double o = (ax == a) ? 0.0 : 0.5;
+  const double s = x / d.h[ax] - o;
+  const int i0 = (int)floor(s + 0.5);
+  const int n = d.n[ax];
+  for (int t = 0; t < 3; ++t) {
+    const int p = i0 - 1 + t;
+    S.w[t] = phi3(s - (double)p);
+    S.dw[t] = dphi3(s - (double)p) / d.h[ax];
+    S.sgn[t] = 1;
+    S.wall[t] = -1;
+    if (d.per[ax]) {
+      int m = p % n; if (m < 0) m += n;
+      S.idx[t] = m; S.keep[t] = true;
+    } else if (ax == a) {          // normal component: physical faces 0..n
+      if (p >= 1 && p <= n - 1) { S.idx[t] = p - 1; S.keep[t] = true; }
+      else if (p < 0) { int m = -p; S.idx[t] = m - 1; S.sgn[t] = -1; S.keep[t] = (m >= 1 && m <= n - 1); }
+      else if (p > n) { int m = 2 * n - p; S.idx[t] = m - 1; S.sgn[t] = -1; S.keep[t] = (m >= 1 && m <= n - 1); }
+      else { S.idx[t] = 0; S.keep[t] = false; }
+    } else {                       // tangential: cell centres 0..n-1
+      if (p < 0) { int m = -1 - p; S.idx[t] = m; S.sgn[t] = -1; S.wall[t] = 2 * ax; S.keep[t] = (m <= n - 1); }
+      else if (p > n - 1) { int m = 2 * n - 1 - p; S.idx[t] = m; S.sgn[t] = -1; S.wall[t] = 2 * ax + 1; S.keep[t] = (m >= 0); }
+      else { S.idx[t] = p; S.keep[t] = true; }
+    }
+  }
+}
+
+// Philox4x64-10 (Salmon et al., SC11): multipliers, Weyl constants.
+__device__ inline void philox4x64_10(unsigned long long c[4], unsigned long long k0, unsigned long long k1) {
+  const unsigned long long M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const unsigned long long W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    unsigned long long hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+    unsigned long long hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+    unsigned long long n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+}
+
+__device__ inline double philox_uniform(unsigned long long w) {
+  return (double)((w >> 12) * 2ULL + 1ULL) * 0x1.0p-53;
+}
+
+// Four standard normals of Philox block b of stream (seed, step, attempt, purpose).
+__device__ inline void philox_normals4(unsigned long long seed, unsigned long long step,
+                                       unsigned attempt, unsigned purpose,
+                                       unsigned long long b, double out[4]) {
+  unsigned long long c[4] = {b, step, ((unsigned long long)attempt << 32) | purpose, 0ULL};
+  philox4x64_10(c, seed, 0ULL);
+#pragma unroll
+  for (int pr = 0; pr < 2; ++pr) {
+    const double u0 = philox_uniform(c[2 * pr]), u1 = philox_uniform(c[2 * pr + 1]);
+    const double rad = sqrt(-2.0 * log(u0));
+    double sn, cs;
+    sincospi(2.0 * u1, &sn, &cs);
+    out[2 * pr] = rad * cs;
+    out[2 * pr + 1] = rad * sn;
+  }
+}
+
+#define RBFIB_DEVFN __device__ __forceinline__

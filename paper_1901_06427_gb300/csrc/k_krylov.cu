@@ -1,0 +1,230 @@
+// Krylov building blocks for FGMRES (Sec. III.C; the paper solves the
+// saddle system with a preconditioned flexible GMRES): multi-column inner
+// products with FP64 accumulation (warp shuffles -> block -> fixed-order
+// final sum, deterministic), fused multi-axpy with the norm of the result,
+// Givens rotations and the small triangular solve on the device.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rbfib {
+
+static inline unsigned nblk(i64 n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+RBFIB_DEVFN double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum (blockDim.x multiple of 32, <= 1024); result valid in thread 0
+RBFIB_DEVFN double block_sum(double v) {
+  __shared__ double sh[32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (wid == 0) v = warp_sum(v);
+  return v;
+}
+
+// part[col * gridDim.x + blockIdx.x] = sum over this block's chunk of W w V_col
+template <typename T>
+__global__ void k_dot_part(const T* __restrict__ w, const T* __restrict__ V, i64 ldv, i64 n, i64 nfl, double wf,
+                           double* __restrict__ part) {
+  const int col = blockIdx.y;
+  const T* v = V + (i64)col * ldv;
+  double acc = 0.0;
+  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+    const double prod = (double)w[i] * (double)v[i];
+    acc += (i < nfl) ? wf * prod : prod;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[(i64)col * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void k_dot_finish(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+  const int col = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[(i64)col * nparts + i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) out[col] = acc;
+}
+
+template <typename T>
+void multi_dot(const T* w, const T* V, i64 ldv, int ncols, i64 n, i64 nfl, double wf, double* part, int nparts,
+               double* out, cudaStream_t s) {
+  dim3 grid(nparts, ncols);
+  k_dot_part<T><<<grid, 256, 0, s>>>(w, V, ldv, n, nfl, wf, part);
+  k_dot_finish<<<ncols, 256, 0, s>>>(part, nparts, out);
+}
+
+// w += sign * sum_c coef[c] V_c ; part[blockIdx.x] = partial ||w||_W^2
+template <typename T>
+__global__ void k_multi_axpy(T* __restrict__ w, const T* __restrict__ V, i64 ldv, int ncols,
+                             const double* __restrict__ coef, double sign, i64 n, i64 nfl, double wf,
+                             double* __restrict__ part) {
+  __shared__ double c[128];
+  for (int i = threadIdx.x; i < ncols; i += blockDim.x) c[i] = sign * coef[i];
+  __syncthreads();
+  double acc = 0.0;
+  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+    double x = (double)w[i];
+    for (int k = 0; k < ncols; ++k) x += c[k] * (double)V[(i64)k * ldv + i];
+    const T xt = (T)x;
+    w[i] = xt;
+    const double xx = (double)xt * (double)xt;
+    acc += (i < nfl) ? wf * xx : xx;
+  }
+  if (part) {
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  }
+}
+
+template <typename T>
+void multi_axpy(T* w, const T* V, i64 ldv, int ncols, const double* coef, double sign, i64 n, i64 nfl, double wf,
+                double* part, int nparts, double* nrm2, cudaStream_t s) {
+  k_multi_axpy<T><<<nparts, 256, 0, s>>>(w, V, ldv, ncols, coef, sign, n, nfl, wf, nrm2 ? part : nullptr);
+  if (nrm2) k_dot_finish<<<1, 256, 0, s>>>(part, nparts, nrm2);
+}
+
+// mode 0: out = in * d[0]; mode 1: out = in / d[0]; mode 2: out = in / sqrt(d[0])
+// (a zero divisor gives zeros)
+template <typename T>
+__global__ void k_scale(T* __restrict__ out, const T* __restrict__ in, const double* __restrict__ denom, int invert,
+                        i64 n) {
+  const double dv = invert == 2 ? sqrt(fmax(denom[0], 0.0)) : denom[0];
+  const double f = invert ? (dv != 0.0 ? 1.0 / dv : 0.0) : dv;
+  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    out[i] = (T)((double)in[i] * f);
+}
+
+template <typename T>
+void scale_by(T* out, const T* in, const double* denom, int invert, i64 n, cudaStream_t s) {
+  const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);
+  k_scale<T><<<nb, 256, 0, s>>>(out, in, denom, invert, n);
+}
+
+// Hessenberg column j: H[0..j] = hcol (CGS2 sum), H[j+1] = sqrt(hnext2); apply
+// the previous rotations, form rotation j, update g; res_out = |g[j+1]|.
+__global__ void k_givens(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
+                         const double* hcol2, const double* hnext2, double* res_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double* h = H + (i64)j * ldh;
+  for (int i = 0; i <= j; ++i) h[i] = hcol[i] + (hcol2 ? hcol2[i] : 0.0);
+  h[j + 1] = sqrt(fmax(hnext2[0], 0.0));
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+    h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+    h[i] = t;
+  }
+  const double a = h[j], b = h[j + 1];
+  const double r = hypot(a, b);
+  const double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
+  cs[j] = c; sn[j] = s;
+  h[j] = r; h[j + 1] = 0.0;
+  g[j + 1] = -s * g[j];
+  g[j] = c * g[j];
+  res_out[0] = fabs(g[j + 1]);
+}
+
+void givens_step(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
+                 const double* hcol2, const double* hnext2, double* res_out, cudaStream_t s) {
+  k_givens<<<1, 32, 0, s>>>(H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, res_out);
+}
+
+// y = H[0:k,0:k]^{-1} g (upper triangular, column-major with leading dim ldh)
+__global__ void k_tri(const double* H, int ldh, const double* g, int k, double* y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double acc = g[i];
+    for (int c = i + 1; c < k; ++c) acc -= H[(i64)c * ldh + i] * y[c];
+    y[i] = acc / H[(i64)i * ldh + i];
+  }
+}
+
+void tri_solve(const double* H, int ldh, const double* g, int k, double* y, cudaStream_t s) {
+  k_tri<<<1, 32, 0, s>>>(H, ldh, g, k, y);
+}
+
+template <typename A, typename B>
+__global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, i64 n) {
+  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    out[i] = (B)in[i];
+}
+template <typename A, typename B>
+void convert(const A* in, B* out, i64 n, cudaStream_t s) {
+  const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);
+  if (n > 0) k_convert<A, B><<<nb, 256, 0, s>>>(in, out, n);
+}
+
+// y = a x + b y
+template <typename T>
+__global__ void k_axpby(T* __restrict__ y, const T* __restrict__ x, double a, double b, i64 n) {
+  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+    double v = a * (double)x[i];
+    if (b != 0.0) v += b * (double)y[i];
+    y[i] = (T)v;
+  }
+}
+template <typename T>
+void axpby(T* y, const T* x, double a, double b, i64 n, cudaStream_t s) {
+  const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);
+  if (n > 0) k_axpby<T><<<nb, 256, 0, s>>>(y, x, a, b, n);
+}
+
+// x -= mean(x)  (two passes, deterministic)
+__global__ void k_sub(double* x, i64 n, const double* mean_sum) {
+  const double m = mean_sum[0] / (double)n;
+  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) x[i] -= m;
+}
+__global__ void k_sum_part(const double* __restrict__ x, i64 n, double* part) {
+  double acc = 0.0;
+  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) acc += x[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+void project_mean(double* x, i64 n, double* part, int nparts, cudaStream_t s) {
+  if (n == 0) return;
+  k_sum_part<<<nparts, 256, 0, s>>>(x, n, part);
+  k_dot_finish<<<1, 256, 0, s>>>(part, nparts, part + nparts);
+  k_sub<<<nparts, 256, 0, s>>>(x, n, part + nparts);
+}
+
+// bv += eta * 2 u_w / h^2 on faces adjacent (along a tangential axis) to a moving wall
+template <typename T>
+__global__ void k_wall_rhs(Dims d, Walls wl, double eta, T* __restrict__ bv) {
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.fo[3]) return;
+  int a, c[3];
+  decode_face(d, t, a, c);
+  double add = 0.0;
+  for (int b = 0; b < 3; ++b) {
+    if (b == a || d.per[b]) continue;
+    const double ih2 = 1.0 / (d.h[b] * d.h[b]);
+    if (c[b] == 0) add += eta * 2.0 * wl.v[2 * b][a] * ih2;
+    if (c[b] == d.n[b] - 1) add += eta * 2.0 * wl.v[2 * b + 1][a] * ih2;
+  }
+  if (add != 0.0) bv[t] = (T)((double)bv[t] + add);
+}
+template <typename T>
+void wall_rhs(const Dims& d, const Walls& wl, double eta, T* bv, cudaStream_t s) {
+  k_wall_rhs<T><<<nblk(d.fo[3], 256), 256, 0, s>>>(d, wl, eta, bv);
+}
+
+#define INST(T)                                                                                              \
+  template void multi_dot<T>(const T*, const T*, i64, int, i64, i64, double, double*, int, double*, cudaStream_t); \
+  template void multi_axpy<T>(T*, const T*, i64, int, const double*, double, i64, i64, double, double*, int,    \
+                              double*, cudaStream_t);                                                            \
+  template void scale_by<T>(T*, const T*, const double*, int, i64, cudaStream_t);                               \
+  template void axpby<T>(T*, const T*, double, double, i64, cudaStream_t);                                      \
+  template void wall_rhs<T>(const Dims&, const Walls&, double, T*, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+template void convert<double, float>(const double*, float*, i64, cudaStream_t);
+template void convert<float, double>(const float*, double*, i64, cudaStream_t);
+
+}  // namespace rbfib

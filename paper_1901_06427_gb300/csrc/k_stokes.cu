@@ -1,0 +1,458 @@
+// MAC-grid Stokes kernels (Sec. III.A): the homogeneous Stokes operator and
+// the geometric multigrid used by the projection preconditioner of the
+// velocity-pressure block.  Templated on the storage/arithmetic type T
+// (double for the FP64 path, float inside FP64 iterative refinement).
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rbfib {
+
+// ---------------------------------------------------------------- helpers
+template <typename T>
+RBFIB_DEVFN T face_at(const Dims& d, const T* __restrict__ v, int a, const int c[3]) {
+  return v[d.fo[a] + flat3(d.fe[a], c[0], c[1], c[2])];
+}
+
+// Laplacian of component a at compact face c with the ghost-reflection
+// boundary conditions: Dirichlet zero at wall-normal boundary faces along a,
+// ghost = -self across walls along tangential axes, wrap on periodic axes.
+// Returns sum_nb u_nb / h^2 (neighbours) and the diagonal coefficient.
+template <typename T>
+RBFIB_DEVFN void lap_parts(const Dims& d, const T* __restrict__ v, int a, const int c[3], T& nbsum, T& diag) {
+  nbsum = T(0);
+  diag = T(0);
+  const i64 base = d.fo[a];
+  const int* e = d.fe[a];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const T ih2 = T(1.0 / (d.h[ax] * d.h[ax]));
+    diag += T(2) * ih2;
+    int lo[3] = {c[0], c[1], c[2]}, hi[3] = {c[0], c[1], c[2]};
+    lo[ax] -= 1; hi[ax] += 1;
+    if (d.per[ax]) {
+      if (lo[ax] < 0) lo[ax] += e[ax];
+      if (hi[ax] >= e[ax]) hi[ax] -= e[ax];
+      nbsum += (v[base + flat3(e, lo[0], lo[1], lo[2])] + v[base + flat3(e, hi[0], hi[1], hi[2])]) * ih2;
+    } else {
+      if (lo[ax] >= 0) nbsum += v[base + flat3(e, lo[0], lo[1], lo[2])] * ih2;
+      else if (ax != a) diag += ih2;
+      if (hi[ax] < e[ax]) nbsum += v[base + flat3(e, hi[0], hi[1], hi[2])] * ih2;
+      else if (ax != a) diag += ih2;
+    }
+  }
+}
+
+// ------------------------------------------------------- Stokes operator
+template <typename T>
+__global__ void k_stokes_apply(Dims d, T eta, const T* __restrict__ v, const T* __restrict__ p,
+                               T* __restrict__ yv, T* __restrict__ yp) {
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  const i64 nf = d.fo[3];
+  if (t < nf) {
+    int a, c[3];
+    decode_face(d, t, a, c);
+    T nb, dg;
+    lap_parts(d, v, a, c, nb, dg);
+    const T u = v[t];
+    // pressure gradient across the face
+    int cl[3] = {c[0], c[1], c[2]}, cr[3] = {c[0], c[1], c[2]};
+    if (d.per[a]) { cl[a] = c[a] - 1; if (cl[a] < 0) cl[a] += d.n[a]; }
+    else { cr[a] = c[a] + 1; }
+    const T gp = (p[flat3(d.n, cr[0], cr[1], cr[2])] - p[flat3(d.n, cl[0], cl[1], cl[2])]) * T(1.0 / d.h[a]);
+    yv[t] = eta * (dg * u - nb) + gp;
+  } else if (t < nf + d.nc) {
+    const i64 l = t - nf;
+    int c[3];
+    decode_cell(d, l, c);
+    T div = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T vr = T(0), vl = T(0);
+      int f[3] = {c[0], c[1], c[2]};
+      if (d.per[a]) {
+        vl = face_at(d, v, a, f);
+        f[a] = c[a] + 1; if (f[a] >= d.n[a]) f[a] = 0;
+        vr = face_at(d, v, a, f);
+      } else {
+        if (c[a] <= d.n[a] - 2) vr = face_at(d, v, a, f);
+        if (c[a] >= 1) { f[a] = c[a] - 1; vl = face_at(d, v, a, f); }
+      }
+      div += (vr - vl) * T(1.0 / d.h[a]);
+    }
+    yp[l] = -div;
+  }
+}
+
+// ------------------------------------------ velocity multigrid (A = -eta LL)
+template <typename T>
+__global__ void k_vel_rbgs(Dims d, T eta, int color, T* __restrict__ u, const T* __restrict__ rhs) {
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.fo[3]) return;
+  int a, c[3];
+  decode_face(d, t, a, c);
+  if (((c[0] + c[1] + c[2]) & 1) != color) return;
+  T nb, dg;
+  lap_parts(d, u, a, c, nb, dg);
+  u[t] = (rhs[t] / eta + nb) / dg;
+}
+
+template <typename T>
+__global__ void k_vel_residual(Dims d, T eta, const T* __restrict__ u, const T* __restrict__ rhs, T* __restrict__ res) {
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.fo[3]) return;
+  int a, c[3];
+  decode_face(d, t, a, c);
+  T nb, dg;
+  lap_parts(d, u, a, c, nb, dg);
+  res[t] = rhs[t] - eta * (dg * u[t] - nb);
+}
+
+// One-dimensional transfer stencils.  kind: 0 = not coarsened,
+// 1 = face-centred on a periodic axis, 2 = face-centred on a wall axis,
+// 3 = cell-centred.  ghost_sign: value of a cell-centred ghost beyond a wall
+// in units of the adjacent interior value (-1 Dirichlet, +1 Neumann).
+struct T1 { int cnt; int idx[3]; double w[3]; };
+
+__device__ inline void restrict_1d(int kind, int ic, int nfext, T1& s) {
+  if (kind == 0) { s.cnt = 1; s.idx[0] = ic; s.w[0] = 1.0; return; }
+  if (kind == 3) { s.cnt = 2; s.idx[0] = 2 * ic; s.idx[1] = 2 * ic + 1; s.w[0] = s.w[1] = 0.5; return; }
+  if (kind == 1) {   // periodic faces, compact == physical; fine extent nfext
+    int P = 2 * ic;
+    s.cnt = 3;
+    s.idx[0] = (P - 1 + nfext) % nfext; s.w[0] = 0.25;
+    s.idx[1] = P; s.w[1] = 0.5;
+    s.idx[2] = (P + 1) % nfext; s.w[2] = 0.25;
+    return;
+  }
+  // wall faces: coarse compact ic <-> physical Q = ic + 1 <-> fine physical 2Q
+  int P = 2 * (ic + 1);
+  s.cnt = 3;
+  s.idx[0] = P - 2; s.w[0] = 0.25;     // fine compact of physical P-1
+  s.idx[1] = P - 1; s.w[1] = 0.5;
+  s.idx[2] = P;     s.w[2] = 0.25;     // physical P+1
+}
+
+__device__ inline void prolong_1d(int kind, int jf, int ncext, double ghost_sign, T1& s) {
+  if (kind == 0) { s.cnt = 1; s.idx[0] = jf; s.w[0] = 1.0; return; }
+  if (kind == 1) {
+    if ((jf & 1) == 0) { s.cnt = 1; s.idx[0] = jf / 2; s.w[0] = 1.0; return; }
+    s.cnt = 2; s.idx[0] = (jf - 1) / 2; s.idx[1] = ((jf + 1) / 2) % ncext; s.w[0] = s.w[1] = 0.5; return;
+  }
+  if (kind == 2) {   // fine physical P = jf + 1; coarse physical Q; boundary Q carry zero
+    int P = jf + 1;
+    if ((P & 1) == 0) { s.cnt = 1; s.idx[0] = P / 2 - 1; s.w[0] = 1.0; return; }
+    s.cnt = 0;
+    int q1 = (P - 1) / 2, q2 = (P + 1) / 2;
+    int nq = ncext + 1;   // coarse physical faces 0..nq
+    if (q1 >= 1 && q1 <= nq - 1) { s.idx[s.cnt] = q1 - 1; s.w[s.cnt] = 0.5; ++s.cnt; }
+    if (q2 >= 1 && q2 <= nq - 1) { s.idx[s.cnt] = q2 - 1; s.w[s.cnt] = 0.5; ++s.cnt; }
+    return;
+  }
+  // cell-centred linear interpolation
+  int jc = jf >> 1;
+  int nb = (jf & 1) ? jc + 1 : jc - 1;
+  s.cnt = 2;
+  s.idx[0] = jc; s.w[0] = 0.75;
+  if (nb < 0 || nb >= ncext) {
+    if (ghost_sign == 2.0) { nb = (nb + ncext) % ncext; s.idx[1] = nb; s.w[1] = 0.25; }   // periodic
+    else { s.cnt = 1; s.w[0] = 0.75 + 0.25 * ghost_sign; }
+  } else { s.idx[1] = nb; s.w[1] = 0.25; }
+}
+
+// Restriction of face residuals to the coarse level: full weighting along a
+// face-centred axis, averaging of the two children along cell-centred axes.
+template <typename T>
+__global__ void k_vel_restrict(Dims df, Dims dc, int3 cz, const T* __restrict__ rf, T* __restrict__ rc) {
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= dc.fo[3]) return;
+  int a, c[3];
+  decode_face(dc, t, a, c);
+  const int cf[3] = {cz.x, cz.y, cz.z};
+  T1 s[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    int kind = !cf[ax] ? 0 : (ax == a ? (df.per[ax] ? 1 : 2) : 3);
+    restrict_1d(kind, c[ax], df.fe[a][ax], s[ax]);
+  }
+  double acc = 0.0;
+  for (int x = 0; x < s[0].cnt; ++x)
+    for (int y = 0; y < s[1].cnt; ++y)
+      for (int z = 0; z < s[2].cnt; ++z)
+        acc += s[0].w[x] * s[1].w[y] * s[2].w[z] *
+               (double)rf[df.fo[a] + flat3(df.fe[a], s[0].idx[x], s[1].idx[y], s[2].idx[z])];
+  rc[t] = (T)acc;
+}
+
+template <typename T>
+__global__ void k_vel_prolong(Dims df, Dims dc, int3 cz, const T* __restrict__ uc, T* __restrict__ uf) {
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= df.fo[3]) return;
+  int a, c[3];
+  decode_face(df, t, a, c);
+  const int cf[3] = {cz.x, cz.y, cz.z};
+  T1 s[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    int kind = !cf[ax] ? 0 : (ax == a ? (df.per[ax] ? 1 : 2) : 3);
+    double gs = df.per[ax] ? 2.0 : -1.0;
+    prolong_1d(kind, c[ax], dc.fe[a][ax], gs, s[ax]);
+  }
+  double acc = 0.0;
+  for (int x = 0; x < s[0].cnt; ++x)
+    for (int y = 0; y < s[1].cnt; ++y)
+      for (int z = 0; z < s[2].cnt; ++z)
+        acc += s[0].w[x] * s[1].w[y] * s[2].w[z] *
+               (double)uc[dc.fo[a] + flat3(dc.fe[a], s[0].idx[x], s[1].idx[y], s[2].idx[z])];
+  uf[t] += (T)acc;
+}
+
+// ---------------------------------- pressure multigrid (-L_p = -D G, Neumann)
+template <typename T>
+RBFIB_DEVFN void plap_parts(const Dims& d, const T* __restrict__ p, const int c[3], T& nbsum, T& diag) {
+  nbsum = T(0); diag = T(0);
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const T ih2 = T(1.0 / (d.h[ax] * d.h[ax]));
+    int lo[3] = {c[0], c[1], c[2]}, hi[3] = {c[0], c[1], c[2]};
+    lo[ax] -= 1; hi[ax] += 1;
+    if (d.per[ax]) {
+      if (lo[ax] < 0) lo[ax] += d.n[ax];
+      if (hi[ax] >= d.n[ax]) hi[ax] -= d.n[ax];
+      nbsum += (p[flat3(d.n, lo[0], lo[1], lo[2])] + p[flat3(d.n, hi[0], hi[1], hi[2])]) * ih2;
+      diag += T(2) * ih2;
+    } else {
+      if (lo[ax] >= 0) { nbsum += p[flat3(d.n, lo[0], lo[1], lo[2])] * ih2; diag += ih2; }
+      if (hi[ax] < d.n[ax]) { nbsum += p[flat3(d.n, hi[0], hi[1], hi[2])] * ih2; diag += ih2; }
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_p_rbgs(Dims d, int color, T* __restrict__ u, const T* __restrict__ rhs) {
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.nc) return;
+  int c[3];
+  decode_cell(d, t, c);
+  if (((c[0] + c[1] + c[2]) & 1) != color) return;
+  T nb, dg;
+  plap_parts(d, u, c, nb, dg);
+  u[t] = (rhs[t] + nb) / dg;
+}
+
+template <typename T>
+__global__ void k_p_residual(Dims d, const T* __restrict__ u, const T* __restrict__ rhs, T* __restrict__ res) {
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.nc) return;
+  int c[3];
+  decode_cell(d, t, c);
+  T nb, dg;
+  plap_parts(d, u, c, nb, dg);
+  res[t] = rhs[t] - (dg * u[t] - nb);
+}
+
+template <typename T>
+__global__ void k_p_restrict(Dims df, Dims dc, int3 cz, const T* __restrict__ rf, T* __restrict__ rc) {
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= dc.nc) return;
+  int c[3];
+  decode_cell(dc, t, c);
+  const int cf[3] = {cz.x, cz.y, cz.z};
+  T1 s[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) restrict_1d(cf[ax] ? 3 : 0, c[ax], df.n[ax], s[ax]);
+  double acc = 0.0;
+  for (int x = 0; x < s[0].cnt; ++x)
+    for (int y = 0; y < s[1].cnt; ++y)
+      for (int z = 0; z < s[2].cnt; ++z)
+        acc += s[0].w[x] * s[1].w[y] * s[2].w[z] * (double)rf[flat3(df.n, s[0].idx[x], s[1].idx[y], s[2].idx[z])];
+  rc[t] = (T)acc;
+}
+
+template <typename T>
+__global__ void k_p_prolong(Dims df, Dims dc, int3 cz, const T* __restrict__ uc, T* __restrict__ uf) {
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= df.nc) return;
+  int c[3];
+  decode_cell(df, t, c);
+  const int cf[3] = {cz.x, cz.y, cz.z};
+  T1 s[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) prolong_1d(cf[ax] ? 3 : 0, c[ax], dc.n[ax], df.per[ax] ? 2.0 : 1.0, s[ax]);
+  double acc = 0.0;
+  for (int x = 0; x < s[0].cnt; ++x)
+    for (int y = 0; y < s[1].cnt; ++y)
+      for (int z = 0; z < s[2].cnt; ++z)
+        acc += s[0].w[x] * s[1].w[y] * s[2].w[z] * (double)uc[flat3(dc.n, s[0].idx[x], s[1].idx[y], s[2].idx[z])];
+  uf[t] += (T)acc;
+}
+
+// Coarsest-level solves: one block, red-black sweeps with block barriers.
+template <typename T>
+__global__ void k_vel_coarse(Dims d, T eta, T* __restrict__ u, const T* __restrict__ rhs, int sweeps) {
+  const i64 n = d.fo[3];
+  for (i64 t = threadIdx.x; t < n; t += blockDim.x) u[t] = T(0);
+  __syncthreads();
+  for (int s = 0; s < sweeps; ++s) {
+    for (int color = 0; color < 2; ++color) {
+      for (i64 t = threadIdx.x; t < n; t += blockDim.x) {
+        int a, c[3];
+        decode_face(d, t, a, c);
+        if (((c[0] + c[1] + c[2]) & 1) != color) continue;
+        T nb, dg;
+        lap_parts(d, u, a, c, nb, dg);
+        u[t] = (rhs[t] / eta + nb) / dg;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_p_coarse(Dims d, T* __restrict__ u, T* __restrict__ rhs, int sweeps) {
+  __shared__ double red[1024];
+  const i64 n = d.nc;
+  double s = 0.0;
+  for (i64 t = threadIdx.x; t < n; t += blockDim.x) s += (double)rhs[t];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const T mean = (T)(red[0] / (double)n);
+  __syncthreads();
+  for (i64 t = threadIdx.x; t < n; t += blockDim.x) { rhs[t] -= mean; u[t] = T(0); }
+  __syncthreads();
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int color = 0; color < 2; ++color) {
+      for (i64 t = threadIdx.x; t < n; t += blockDim.x) {
+        int c[3];
+        decode_cell(d, t, c);
+        if (((c[0] + c[1] + c[2]) & 1) != color) continue;
+        T nb, dg;
+        plap_parts(d, u, c, nb, dg);
+        u[t] = (rhs[t] + nb) / dg;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------ projection preconditioner
+// q = r_pi + D v~ ; pi = -eta q
+template <typename T>
+__global__ void k_div_q(Dims d, T eta, const T* __restrict__ vt, const T* __restrict__ rpi,
+                        T* __restrict__ q, T* __restrict__ pi) {
+  const i64 l = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= d.nc) return;
+  int c[3];
+  decode_cell(d, l, c);
+  T div = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    T vr = T(0), vl = T(0);
+    int f[3] = {c[0], c[1], c[2]};
+    if (d.per[a]) {
+      vl = face_at(d, vt, a, f);
+      f[a] = c[a] + 1; if (f[a] >= d.n[a]) f[a] = 0;
+      vr = face_at(d, vt, a, f);
+    } else {
+      if (c[a] <= d.n[a] - 2) vr = face_at(d, vt, a, f);
+      if (c[a] >= 1) { f[a] = c[a] - 1; vl = face_at(d, vt, a, f); }
+    }
+    div += (vr - vl) * T(1.0 / d.h[a]);
+  }
+  const T qq = rpi[l] + div;
+  q[l] = qq;
+  pi[l] = -eta * qq;
+}
+
+// v += G phi
+template <typename T>
+__global__ void k_add_grad(Dims d, const T* __restrict__ phi, T* __restrict__ v) {
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.fo[3]) return;
+  int a, c[3];
+  decode_face(d, t, a, c);
+  int cl[3] = {c[0], c[1], c[2]}, cr[3] = {c[0], c[1], c[2]};
+  if (d.per[a]) { cl[a] = c[a] - 1; if (cl[a] < 0) cl[a] += d.n[a]; }
+  else { cr[a] = c[a] + 1; }
+  v[t] += (phi[flat3(d.n, cr[0], cr[1], cr[2])] - phi[flat3(d.n, cl[0], cl[1], cl[2])]) * T(1.0 / d.h[a]);
+}
+
+// ---------------------------------------------------------------- launchers
+static inline unsigned nblk(i64 n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+template <typename T>
+void stokes_apply(const Dims& d, T eta, const T* v, const T* p, T* yv, T* yp, cudaStream_t s) {
+  const i64 n = d.fo[3] + d.nc;
+  k_stokes_apply<T><<<nblk(n, 256), 256, 0, s>>>(d, eta, v, p, yv, yp);
+}
+template <typename T>
+void vel_rbgs(const Dims& d, T eta, int color, T* u, const T* rhs, cudaStream_t s) {
+  k_vel_rbgs<T><<<nblk(d.fo[3], 256), 256, 0, s>>>(d, eta, color, u, rhs);
+}
+template <typename T>
+void vel_residual(const Dims& d, T eta, const T* u, const T* rhs, T* res, cudaStream_t s) {
+  k_vel_residual<T><<<nblk(d.fo[3], 256), 256, 0, s>>>(d, eta, u, rhs, res);
+}
+template <typename T>
+void vel_restrict(const Dims& df, const Dims& dc, int3 cz, const T* rf, T* rc, cudaStream_t s) {
+  k_vel_restrict<T><<<nblk(dc.fo[3], 256), 256, 0, s>>>(df, dc, cz, rf, rc);
+}
+template <typename T>
+void vel_prolong(const Dims& df, const Dims& dc, int3 cz, const T* uc, T* uf, cudaStream_t s) {
+  k_vel_prolong<T><<<nblk(df.fo[3], 256), 256, 0, s>>>(df, dc, cz, uc, uf);
+}
+template <typename T>
+void vel_coarse(const Dims& d, T eta, T* u, const T* rhs, int sweeps, cudaStream_t s) {
+  k_vel_coarse<T><<<1, 1024, 0, s>>>(d, eta, u, rhs, sweeps);
+}
+template <typename T>
+void p_rbgs(const Dims& d, int color, T* u, const T* rhs, cudaStream_t s) {
+  k_p_rbgs<T><<<nblk(d.nc, 256), 256, 0, s>>>(d, color, u, rhs);
+}
+template <typename T>
+void p_residual(const Dims& d, const T* u, const T* rhs, T* res, cudaStream_t s) {
+  k_p_residual<T><<<nblk(d.nc, 256), 256, 0, s>>>(d, u, rhs, res);
+}
+template <typename T>
+void p_restrict(const Dims& df, const Dims& dc, int3 cz, const T* rf, T* rc, cudaStream_t s) {
+  k_p_restrict<T><<<nblk(dc.nc, 256), 256, 0, s>>>(df, dc, cz, rf, rc);
+}
+template <typename T>
+void p_prolong(const Dims& df, const Dims& dc, int3 cz, const T* uc, T* uf, cudaStream_t s) {
+  k_p_prolong<T><<<nblk(df.nc, 256), 256, 0, s>>>(df, dc, cz, uc, uf);
+}
+template <typename T>
+void p_coarse(const Dims& d, T* u, T* rhs, int sweeps, cudaStream_t s) {
+  k_p_coarse<T><<<1, 1024, 0, s>>>(d, u, rhs, sweeps);
+}
+template <typename T>
+void div_q(const Dims& d, T eta, const T* vt, const T* rpi, T* q, T* pi, cudaStream_t s) {
+  k_div_q<T><<<nblk(d.nc, 256), 256, 0, s>>>(d, eta, vt, rpi, q, pi);
+}
+template <typename T>
+void add_grad(const Dims& d, const T* phi, T* v, cudaStream_t s) {
+  k_add_grad<T><<<nblk(d.fo[3], 256), 256, 0, s>>>(d, phi, v);
+}
+
+#define INST(T)                                                                                  \
+  template void stokes_apply<T>(const Dims&, T, const T*, const T*, T*, T*, cudaStream_t);       \
+  template void vel_rbgs<T>(const Dims&, T, int, T*, const T*, cudaStream_t);                    \
+  template void vel_residual<T>(const Dims&, T, const T*, const T*, T*, cudaStream_t);           \
+  template void vel_restrict<T>(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);     \
+  template void vel_prolong<T>(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);      \
+  template void vel_coarse<T>(const Dims&, T, T*, const T*, int, cudaStream_t);                  \
+  template void p_rbgs<T>(const Dims&, int, T*, const T*, cudaStream_t);                         \
+  template void p_residual<T>(const Dims&, const T*, const T*, T*, cudaStream_t);                \
+  template void p_restrict<T>(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);       \
+  template void p_prolong<T>(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);        \
+  template void p_coarse<T>(const Dims&, T*, T*, int, cudaStream_t);                             \
+  template void div_q<T>(const Dims&, T, const T*, const T*, T*, T*, cudaStream_t);              \
+  template void add_grad<T>(const Dims&, const T*, T*, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace rbfib

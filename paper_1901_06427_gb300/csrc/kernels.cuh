@@ -1,0 +1,111 @@
+// Launchers of the device kernels, grouped by file.  All launches are
+// asynchronous on the given stream.
+#pragma once
+#include "common.cuh"
+
+namespace rbfib {
+
+struct Walls { double v[6][3]; };   // wall velocities, walls -x,+x,-y,+y,-z,+z
+
+// Device views of the bodies of one configuration.
+struct BodyView {
+  int nb = 0, nbl = 0;
+  const int* boff = nullptr;     // nb + 1
+  const int* bob = nullptr;      // body of blob, nbl
+  const int* perm = nullptr;     // blob order sorted by cell (may be null)
+  const double* ref = nullptr;   // nbl x 3 (body frame)
+  const double* q = nullptr;     // nb x 3
+  const double* quat = nullptr;  // nb x 4
+  const double* r = nullptr;     // nbl x 3 blob positions
+  const double* arm = nullptr;   // nbl x 3 r - q
+};
+
+struct PrecondView {
+  int max_blobs = 0;
+  const int* shape_of = nullptr;
+  const i64* minv_off = nullptr;
+  const double* minv = nullptr;
+  const double* nmat = nullptr;
+  const int* shape_ref_blob = nullptr;
+};
+
+struct Potentials {
+  double gravity;
+  double pair_phi0, pair_b, pair_d;
+  double wall_phi0, wall_b, wall_d;
+  double bw_phi0, bw_b, bw_d;
+  double yuk_u0, yuk_dh, yuk_lambda;
+  double sub_u0, sub_s;
+};
+
+// Offsets and extents of the nine stress blocks (global order: for a = x,y,z:
+// W_aa then W_ab for the other two axes b in increasing order).
+struct StressLayout {
+  i64 off[3][3];
+  int ext[3][3][3];
+  i64 total;
+};
+
+// k_stokes.cu
+template <typename T> void stokes_apply(const Dims&, T eta, const T* v, const T* p, T* yv, T* yp, cudaStream_t);
+template <typename T> void vel_rbgs(const Dims&, T eta, int color, T* u, const T* rhs, cudaStream_t);
+template <typename T> void vel_residual(const Dims&, T eta, const T* u, const T* rhs, T* res, cudaStream_t);
+template <typename T> void vel_restrict(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);
+template <typename T> void vel_prolong(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);
+template <typename T> void vel_coarse(const Dims&, T eta, T* u, const T* rhs, int sweeps, cudaStream_t);
+template <typename T> void p_rbgs(const Dims&, int color, T* u, const T* rhs, cudaStream_t);
+template <typename T> void p_residual(const Dims&, const T* u, const T* rhs, T* res, cudaStream_t);
+template <typename T> void p_restrict(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);
+template <typename T> void p_prolong(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);
+template <typename T> void p_coarse(const Dims&, T* u, T* rhs, int sweeps, cudaStream_t);
+template <typename T> void div_q(const Dims&, T eta, const T* vt, const T* rpi, T* q, T* pi, cudaStream_t);
+template <typename T> void add_grad(const Dims&, const T* phi, T* v, cudaStream_t);
+
+// k_ib.cu
+void geometry(int nbl, const int* bob, const double* ref, const double* q, const double* quat,
+              double* r, double* arm, cudaStream_t);
+void binning(const Dims&, int nbl, const double* r, int* perm, int* off, int* key, int* count, int* fill,
+             int* bsum, cudaStream_t);
+template <typename T> void saddle_bodies(const Dims&, const BodyView&, const T* v, const T* lam, const T* U,
+                                         T* yv, T* ylam, T* yU, cudaStream_t);
+template <typename T> void spread(const Dims&, int nbl, const int* perm, const double* r, const T* lam,
+                                  double scale, T* f, cudaStream_t);
+template <typename T> void interp(const Dims&, const Walls&, int nbl, const double* r, const T* v, double alpha,
+                                  double beta, double gamma, T* out, cudaStream_t);
+template <typename T> void interp_res(const Dims&, int nbl, const double* r, const T* v, const T* rl,
+                                      double* out, cudaStream_t);
+template <typename T> void body_precond(const BodyView&, const PrecondView&, const double* sres, const T* rU,
+                                        T* zlam, T* zU, cudaStream_t);
+void kt_apply(int nb, const int* boff, const double* arm, const double* lam, double alpha, double beta,
+              double* out, cudaStream_t);
+void k_apply(int nbl, const int* bob, const double* arm, const double* U, double alpha, double beta,
+             double* out, cudaStream_t);
+void body_forces(const Dims&, const Potentials&, const BodyView&, const double* fext, double* out, cudaStream_t);
+void wft(int nb, const double* wn, const double* Lp, double kT, double* out, cudaStream_t);
+void move_bodies(int nb, const double* q, const double* quat, const double* vec6, const double* Lp, double a,
+                 double* qo, double* quato, cudaStream_t);
+void outside_check(const Dims&, int nbl, const double* r, int* flag, cudaStream_t);
+
+// k_krylov.cu
+// Weighted inner products <x, y>_W with weight wf on the first nfl entries
+// and 1 on the rest.
+template <typename T> void multi_dot(const T* w, const T* V, i64 ldv, int ncols, i64 n, i64 nfl, double wf,
+                                     double* part, int nparts, double* out, cudaStream_t);
+template <typename T> void multi_axpy(T* w, const T* V, i64 ldv, int ncols, const double* coef, double sign,
+                                      i64 n, i64 nfl, double wf, double* part, int nparts, double* nrm2,
+                                      cudaStream_t);
+template <typename T> void scale_by(T* out, const T* in, const double* denom, int invert, i64 n, cudaStream_t);
+void givens_step(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
+                 const double* hcol2, const double* hnext2, double* res_out, cudaStream_t);
+void tri_solve(const double* H, int ldh, const double* g, int k, double* y, cudaStream_t);
+template <typename A, typename B> void convert(const A* in, B* out, i64 n, cudaStream_t);
+template <typename T> void axpby(T* y, const T* x, double a, double b, i64 n, cudaStream_t);
+template <typename T> void wall_rhs(const Dims&, const Walls&, double eta, T* bv, cudaStream_t);
+void project_mean(double* x, i64 n, double* part, int nparts, cudaStream_t);
+
+// k_noise.cu
+void philox_normals(unsigned long long seed, unsigned long long step, unsigned attempt, unsigned purpose,
+                    i64 count, double* out, cudaStream_t);
+void stress_divergence(const Dims&, const StressLayout&, const double* W, double c, double* out, cudaStream_t);
+
+}  // namespace rbfib

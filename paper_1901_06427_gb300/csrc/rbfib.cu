@@ -1,0 +1,1052 @@
+// Host side of librbfib: the grid object, the multigrid hierarchy, the
+// preconditioned FGMRES solver of the constrained saddle system (Sec. III.C),
+// the Split-Euler-Maruyama step (Sec. IV.B, Algorithm 1) and the C ABI.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rbfib.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace rbfib;
+
+namespace {
+
+const double kDeltaDefault = 6.0554544523933395e-06;   // eps^(1/3), eps = 2^-52
+const double kBlobRadius = 0.91;                         // hydrodynamic radius of a 3-point blob, units of h
+
+struct CudaError {
+  cudaError_t e;
+};
+
+inline void ck(cudaError_t e) {
+  if (e != cudaSuccess) throw CudaError{e};
+}
+
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  void alloc(size_t k) {
+    release();
+    if (k) ck(cudaMalloc((void**)&p, k * sizeof(T)));
+    n = k;
+  }
+  void ensure(size_t k) {
+    if (k > n) alloc(k);
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  ~DBuf() { release(); }
+  operator T*() const { return p; }
+};
+
+struct Level {
+  Dims d;
+  int3 cz;   // axes coarsened towards the next level
+};
+
+// Multigrid storage of one precision.
+template <typename T>
+struct MGStore {
+  std::vector<DBuf<T>*> vu, vrhs, vres, pu, prhs, pres;
+  void build(const std::vector<Level>& L) {
+    release();
+    for (size_t l = 0; l < L.size(); ++l) {
+      const i64 nf = L[l].d.fo[3], nc = L[l].d.nc;
+      auto mk = [](i64 n) { auto* b = new DBuf<T>(); b->alloc(n); return b; };
+      vu.push_back(mk(nf)); vrhs.push_back(mk(nf)); vres.push_back(mk(nf));
+      pu.push_back(mk(nc)); prhs.push_back(mk(nc)); pres.push_back(mk(nc));
+    }
+  }
+  void release() {
+    for (auto* v : {&vu, &vrhs, &vres, &pu, &prhs, &pres}) {
+      for (auto* b : *v) delete b;
+      v->clear();
+    }
+  }
+  ~MGStore() { release(); }
+};
+
+// Krylov storage of one precision (basis V, flexible basis Z).
+template <typename T>
+struct KrylovStore {
+  int m = 0;
+  i64 n = 0;
+  DBuf<T> V, Z, w;
+  void build(int m_, i64 n_) {
+    m = m_; n = n_;
+    V.alloc((size_t)(m + 1) * n);
+    Z.alloc((size_t)m * n);
+    w.alloc(n);
+  }
+};
+
+struct Config {   // one body configuration (positions derived from q, quat)
+  DBuf<double> q, quat, r, arm;
+  DBuf<int> perm;
+};
+
+}  // namespace
+
+struct rbfib_grid {
+  rbfib_grid_desc desc{};
+  cudaStream_t s = nullptr;
+  std::string err;
+  std::vector<Level> levels;
+  Dims d{};
+  Walls walls{};
+  i64 nf = 0, nc = 0, nfl = 0;
+  double dV = 1.0;
+  StressLayout stress{};
+  // bodies
+  int nb = 0, nbl = 0;
+  std::vector<int> h_boff;
+  DBuf<int> boff, bob, celloff, bkey, bcount, bfill, bbsum;
+  DBuf<double> ref, Lp;
+  Config cur, plus, minus, next;
+  // body-block preconditioner
+  int max_blobs = 0;
+  DBuf<int> shape_of, shape_ref_blob;
+  DBuf<i64> minv_off;
+  DBuf<double> minv, nmat;
+  // work vectors (FP64)
+  DBuf<double> part, scal, bvec, xvec, xrfd, rres, sres, fsharp, vsharp, fnoise, Wst;
+  DBuf<double> bodyA, bodyB, bodyF, bodyW, bodyWn, blobA, blobB, blobC, blobD, blobS;
+  double* h_pinned = nullptr;
+  int nparts = 0;
+  // precision-specific stores
+  MGStore<double> mg64;
+  MGStore<float> mg32;
+  KrylovStore<double> kr64;
+  KrylovStore<float> kr32;
+  DBuf<float> f32a, f32b;
+  DBuf<double> small;     // Hessenberg, rotations, g, y, dots
+  int total_iters = 0;
+
+  i64 n_total() const { return nfl + 3 * (i64)nbl + 6 * (i64)nb; }
+};
+
+namespace {
+
+int fail(rbfib_grid* g, int code, const std::string& msg) {
+  if (g) g->err = msg;
+  return code;
+}
+
+BodyView view_of(rbfib_grid* g, Config& c) {
+  BodyView b;
+  b.nb = g->nb; b.nbl = g->nbl;
+  b.boff = g->boff; b.bob = g->bob; b.perm = c.perm.p;
+  b.ref = g->ref; b.q = c.q; b.quat = c.quat; b.r = c.r; b.arm = c.arm;
+  return b;
+}
+
+PrecondView pview(rbfib_grid* g) {
+  PrecondView p;
+  p.max_blobs = g->max_blobs;
+  p.shape_of = g->shape_of; p.minv_off = g->minv_off; p.minv = g->minv; p.nmat = g->nmat;
+  p.shape_ref_blob = g->shape_ref_blob;
+  return p;
+}
+
+// --------------------------------------------------------------- multigrid
+// Small-array layout inside g->small: [H (m+1)*m | cs m | sn m | g m+1 | y m |
+// hcol 128 | hcol2 128 | nrm2 2 | res 2 | bnorm 2]
+struct SmallPtrs {
+  double *H, *cs, *sn, *gv, *y, *hcol, *hcol2, *nrm2, *res, *bn;
+};
+SmallPtrs small_ptrs(rbfib_grid* g, int m) {
+  SmallPtrs p;
+  double* b = g->small;
+  p.H = b; b += (size_t)(m + 1) * m;
+  p.cs = b; b += m;
+  p.sn = b; b += m;
+  p.gv = b; b += m + 1;
+  p.y = b; b += m;
+  p.hcol = b; b += 128;
+  p.hcol2 = b; b += 128;
+  p.nrm2 = b; b += 2;
+  p.res = b; b += 2;
+  p.bn = b; b += 2;
+  return p;
+}
+
+template <typename T>
+MGStore<T>& mg_of(rbfib_grid* g);
+template <>
+MGStore<double>& mg_of<double>(rbfib_grid* g) { return g->mg64; }
+template <>
+MGStore<float>& mg_of<float>(rbfib_grid* g) { return g->mg32; }
+template <typename T>
+KrylovStore<T>& kr_of(rbfib_grid* g);
+template <>
+KrylovStore<double>& kr_of<double>(rbfib_grid* g) { return g->kr64; }
+template <>
+KrylovStore<float>& kr_of<float>(rbfib_grid* g) { return g->kr32; }
+
+const int kNu = 2;   // pre- and post-smoothing sweeps
+
+int coarse_sweeps(const Dims& d) { return 4 * std::max(d.n[0], std::max(d.n[1], d.n[2])) + 8; }
+
+// u0 <- V-cycle approximation of (-eta LL)^{-1} rhs0 (zero initial guess)
+template <typename T>
+void vcycle_vel(rbfib_grid* g, T* u0, const T* rhs0) {
+  MGStore<T>& M = mg_of<T>(g);
+  const int L = (int)g->levels.size();
+  const T eta = (T)g->desc.eta;
+  std::vector<T*> u(L), rhs(L);
+  for (int l = 0; l < L; ++l) { u[l] = *M.vu[l]; rhs[l] = *M.vrhs[l]; }
+  u[0] = u0;
+  rhs[0] = const_cast<T*>(rhs0);
+  for (int l = 0; l < L - 1; ++l) {
+    const Dims& d = g->levels[l].d;
+    ck(cudaMemsetAsync(u[l], 0, sizeof(T) * d.fo[3], g->s));
+    for (int s = 0; s < kNu; ++s) { vel_rbgs<T>(d, eta, 0, u[l], rhs[l], g->s); vel_rbgs<T>(d, eta, 1, u[l], rhs[l], g->s); }
+    vel_residual<T>(d, eta, u[l], rhs[l], *M.vres[l], g->s);
+    vel_restrict<T>(d, g->levels[l + 1].d, g->levels[l].cz, *M.vres[l], rhs[l + 1], g->s);
+  }
+  vel_coarse<T>(g->levels[L - 1].d, eta, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
+  for (int l = L - 2; l >= 0; --l) {
+    const Dims& d = g->levels[l].d;
+    vel_prolong<T>(d, g->levels[l + 1].d, g->levels[l].cz, u[l + 1], u[l], g->s);
+    for (int s = 0; s < kNu; ++s) { vel_rbgs<T>(d, eta, 1, u[l], rhs[l], g->s); vel_rbgs<T>(d, eta, 0, u[l], rhs[l], g->s); }
+  }
+}
+
+// u0 <- V-cycle approximation of (-D G)^{-1} rhs0 (Neumann; rhs0 is scratch)
+template <typename T>
+void vcycle_p(rbfib_grid* g, T* u0, T* rhs0) {
+  MGStore<T>& M = mg_of<T>(g);
+  const int L = (int)g->levels.size();
+  std::vector<T*> u(L), rhs(L);
+  for (int l = 0; l < L; ++l) { u[l] = *M.pu[l]; rhs[l] = *M.prhs[l]; }
+  u[0] = u0;
+  rhs[0] = rhs0;
+  for (int l = 0; l < L - 1; ++l) {
+    const Dims& d = g->levels[l].d;
+    ck(cudaMemsetAsync(u[l], 0, sizeof(T) * d.nc, g->s));
+    for (int s = 0; s < kNu; ++s) { p_rbgs<T>(d, 0, u[l], rhs[l], g->s); p_rbgs<T>(d, 1, u[l], rhs[l], g->s); }
+    p_residual<T>(d, u[l], rhs[l], *M.pres[l], g->s);
+    p_restrict<T>(d, g->levels[l + 1].d, g->levels[l].cz, *M.pres[l], rhs[l + 1], g->s);
+  }
+  p_coarse<T>(g->levels[L - 1].d, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
+  for (int l = L - 2; l >= 0; --l) {
+    const Dims& d = g->levels[l].d;
+    p_prolong<T>(d, g->levels[l + 1].d, g->levels[l].cz, u[l + 1], u[l], g->s);
+    for (int s = 0; s < kNu; ++s) { p_rbgs<T>(d, 1, u[l], rhs[l], g->s); p_rbgs<T>(d, 0, u[l], rhs[l], g->s); }
+  }
+}
+
+// ---------------------------------------------------------- preconditioner
+// Block lower-triangular preconditioner of the saddle operator.
+// Fluid block (projection method): v~ = (-eta LL)^{-1} r_v (V-cycle),
+// q = r_pi + D v~, phi = (-D G)^{-1} q (V-cycle), v = v~ + G phi, pi = -eta q.
+// Body block: Schur complement [-M K; K^T 0] with M replaced per body by the
+// free-space RPY blob mobility of its shape, right-hand side
+// (r_lam + J v, r_U).
+template <typename T>
+void precond(rbfib_grid* g, const T* r, T* z, bool with_bodies) {
+  const Dims& d = g->d;
+  T* zv = z;
+  T* zp = z + g->nf;
+  MGStore<T>& M = mg_of<T>(g);
+  vcycle_vel<T>(g, zv, r);
+  T* q = *M.prhs[0];
+  T* phi = *M.pu[0];
+  div_q<T>(d, (T)g->desc.eta, zv, r + g->nf, q, zp, g->s);
+  vcycle_p<T>(g, phi, q);
+  add_grad<T>(d, phi, zv, g->s);
+  if (with_bodies && g->nb > 0) {
+    const T* rl = r + g->nfl;
+    const T* rU = rl + 3 * (i64)g->nbl;
+    T* zl = z + g->nfl;
+    T* zU = zl + 3 * (i64)g->nbl;
+    interp_res<T>(d, g->nbl, g->cur.r, zv, rl, g->sres, g->s);
+    body_precond<T>(view_of(g, g->cur), pview(g), g->sres, rU, zl, zU, g->s);
+  }
+}
+
+// y = A x (saddle operator; fluid-only when with_bodies is false)
+template <typename T>
+void apply_A(rbfib_grid* g, const T* x, T* y, bool with_bodies) {
+  stokes_apply<T>(g->d, (T)g->desc.eta, x, x + g->nf, y, y + g->nf, g->s);
+  if (with_bodies && g->nb > 0) {
+    const T* xl = x + g->nfl;
+    const T* xU = xl + 3 * (i64)g->nbl;
+    saddle_bodies<T>(g->d, view_of(g, g->cur), x, xl, xU, y, y + g->nfl, y + g->nfl + 3 * (i64)g->nbl, g->s);
+  }
+}
+
+double read_scalar(rbfib_grid* g, const double* dev) {
+  ck(cudaMemcpyAsync(g->h_pinned, dev, sizeof(double), cudaMemcpyDeviceToHost, g->s));
+  ck(cudaStreamSynchronize(g->s));
+  return g->h_pinned[0];
+}
+
+// Right-preconditioned flexible GMRES(m) with classical Gram-Schmidt and one
+// re-orthogonalisation, inner products weighted by dV on the fluid unknowns.
+// Solves A x = b from x = 0 to ||b - A x||_W <= rtol ||b||_W.
+// Returns 0, RBFIB_ENOCONV or RBFIB_ENAN; iters and relres report progress.
+template <typename T>
+int fgmres(rbfib_grid* g, const T* b, T* x, bool with_bodies, double rtol, int maxit, int& iters, double& relres) {
+  KrylovStore<T>& K = kr_of<T>(g);
+  const int m = K.m;
+  const i64 n = with_bodies ? g->n_total() : g->nfl;
+  const i64 ld = K.n;
+  const i64 nfl = g->nfl;
+  const double wf = g->dV;
+  SmallPtrs sp = small_ptrs(g, m);
+  T* V = K.V;
+  T* Z = K.Z;
+  T* w = K.w;
+  iters = 0;
+  relres = 0.0;
+  multi_dot<T>(b, b, ld, 1, n, nfl, wf, g->part, g->nparts, sp.bn, g->s);
+  const double bnorm = std::sqrt(std::max(read_scalar(g, sp.bn), 0.0));
+  ck(cudaMemsetAsync(x, 0, sizeof(T) * n, g->s));
+  if (!(bnorm > 0.0)) {
+    if (std::isnan(bnorm)) return RBFIB_ENAN;
+    return 0;
+  }
+  // r = b (x = 0)
+  ck(cudaMemcpyAsync(w, b, sizeof(T) * n, cudaMemcpyDeviceToDevice, g->s));
+  double beta = bnorm;
+  for (;;) {
+    // V_0 = r / beta ; g = (beta, 0, ...)
+    ck(cudaMemsetAsync(sp.gv, 0, sizeof(double) * (m + 1), g->s));
+    g->h_pinned[1] = beta;
+    ck(cudaMemcpyAsync(sp.gv, g->h_pinned + 1, sizeof(double), cudaMemcpyHostToDevice, g->s));
+    scale_by<T>(V, w, sp.gv, 1, n, g->s);
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      T* vj = V + (i64)j * ld;
+      T* zj = Z + (i64)j * ld;
+      precond<T>(g, vj, zj, with_bodies);
+      apply_A<T>(g, zj, w, with_bodies);
+      multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol, g->s);
+      multi_axpy<T>(w, V, ld, j + 1, sp.hcol, -1.0, n, nfl, wf, g->part, g->nparts, nullptr, g->s);
+      multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol2, g->s);
+      multi_axpy<T>(w, V, ld, j + 1, sp.hcol2, -1.0, n, nfl, wf, g->part, g->nparts, sp.nrm2, g->s);
+      givens_step(sp.H, m + 1, sp.cs, sp.sn, sp.gv, j, sp.hcol, sp.hcol2, sp.nrm2, sp.res, g->s);
+      scale_by<T>(V + (i64)(j + 1) * ld, w, sp.nrm2, 2, n, g->s);
+      ++iters;
+      k = j + 1;
+      const double res = read_scalar(g, sp.res);
+      if (std::isnan(res)) return RBFIB_ENAN;
+      if (res <= rtol * bnorm || iters >= maxit) break;
+    }
+    tri_solve(sp.H, m + 1, sp.gv, k, sp.y, g->s);
+    multi_axpy<T>(x, Z, ld, k, sp.y, 1.0, n, nfl, wf, g->part, g->nparts, nullptr, g->s);
+    // true residual
+    apply_A<T>(g, x, w, with_bodies);
+    axpby<T>(w, b, 1.0, -1.0, n, g->s);   // w = b - A x
+    multi_dot<T>(w, w, ld, 1, n, nfl, wf, g->part, g->nparts, sp.bn, g->s);
+    beta = std::sqrt(std::max(read_scalar(g, sp.bn), 0.0));
+    relres = beta / bnorm;
+    if (std::isnan(relres)) return RBFIB_ENAN;
+    if (relres <= rtol) return 0;
+    if (iters >= maxit) return RBFIB_ENOCONV;
+  }
+}
+
+// --------------------------------------------------------------- set-up
+void build_levels(rbfib_grid* g) {
+  g->levels.clear();
+  Level L0;
+  double h3[3] = {g->desc.h, g->desc.h, g->desc.h};
+  L0.d = make_dims(g->desc.n, g->desc.periodic, h3);
+  g->levels.push_back(L0);
+  for (;;) {
+    Level& cur = g->levels.back();
+    int cz[3];
+    int any = 0;
+    for (int a = 0; a < 3; ++a) {
+      cz[a] = (cur.d.n[a] % 2 == 0 && cur.d.n[a] >= 4) ? 1 : 0;
+      any |= cz[a];
+    }
+    if (!any || cur.d.nc <= 256) { cur.cz = make_int3(0, 0, 0); break; }
+    cur.cz = make_int3(cz[0], cz[1], cz[2]);
+    int n2[3], per[3];
+    double h2[3];
+    for (int a = 0; a < 3; ++a) {
+      n2[a] = cz[a] ? cur.d.n[a] / 2 : cur.d.n[a];
+      h2[a] = cz[a] ? 2.0 * cur.d.h[a] : cur.d.h[a];
+      per[a] = cur.d.per[a];
+    }
+    Level nx;
+    nx.d = make_dims(n2, per, h2);
+    g->levels.push_back(nx);
+  }
+}
+
+void build_stress_layout(rbfib_grid* g) {
+  i64 off = 0;
+  for (int a = 0; a < 3; ++a) {
+    for (int bb = 0; bb < 3; ++bb) {
+      int b = (bb == 0) ? a : (bb == 1 ? (a == 0 ? 1 : 0) : (a == 2 ? 1 : 2));
+      int* e = g->stress.ext[a][b];
+      for (int ax = 0; ax < 3; ++ax) e[ax] = g->d.n[ax];
+      if (b != a) {
+        e[a] = g->d.fe[a][a];
+        e[b] = g->d.per[b] ? g->d.n[b] : g->d.n[b] + 1;
+      }
+      g->stress.off[a][b] = off;
+      off += (i64)e[0] * e[1] * e[2];
+    }
+  }
+  g->stress.total = off;
+}
+
+// dense symmetric positive definite inverse (Cholesky), n small
+bool spd_inverse(std::vector<double>& A, int n) {
+  std::vector<double> L(A);
+  for (int j = 0; j < n; ++j) {
+    double s = L[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+    if (!(s > 0.0)) return false;
+    const double d = std::sqrt(s);
+    L[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double t = L[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      L[(size_t)i * n + j] = t / d;
+    }
+  }
+  // inverse column by column
+  std::vector<double> inv((size_t)n * n), y(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) {
+      double t = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) t -= L[(size_t)i * n + k] * y[k];
+      y[i] = t / L[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double t = y[i];
+      for (int k = i + 1; k < n; ++k) t -= L[(size_t)k * n + i] * inv[(size_t)k * n + c];
+      inv[(size_t)i * n + c] = t / L[(size_t)i * n + i];
+    }
+  }
+  A.swap(inv);
+  return true;
+}
+
+// free-space Rotne-Prager-Yamakawa blob mobility of blobs x (n x 3), radius a
+void rpy_matrix(const double* x, int nbp, double a, double eta, std::vector<double>& M) {
+  const int n3 = 3 * nbp;
+  M.assign((size_t)n3 * n3, 0.0);
+  const double c0 = 1.0 / (6.0 * M_PI * eta * a);
+  for (int i = 0; i < nbp; ++i)
+    for (int j = 0; j < nbp; ++j) {
+      double dvec[3] = {x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1], x[3 * i + 2] - x[3 * j + 2]};
+      const double r = std::sqrt(dvec[0] * dvec[0] + dvec[1] * dvec[1] + dvec[2] * dvec[2]);
+      double fI, fR;
+      if (i == j) { fI = c0; fR = 0.0; }
+      else if (r >= 2.0 * a) {
+        const double c = 1.0 / (8.0 * M_PI * eta * r);
+        fI = c * (1.0 + 2.0 * a * a / (3.0 * r * r));
+        fR = c * (1.0 - 2.0 * a * a / (r * r));
+      } else {
+        fI = c0 * (1.0 - 9.0 * r / (32.0 * a));
+        fR = c0 * (3.0 * r / (32.0 * a));
+      }
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) {
+          double v = (p == q ? fI : 0.0);
+          if (i != j) v += fR * dvec[p] * dvec[q] / (r * r);
+          M[(size_t)(3 * i + p) * n3 + 3 * j + q] = v;
+        }
+    }
+}
+
+bool inverse6(double A[36]) {
+  double aug[6][12];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 12; ++j) aug[i][j] = j < 6 ? A[6 * i + j] : (j - 6 == i ? 1.0 : 0.0);
+  for (int c = 0; c < 6; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 6; ++r)
+      if (std::fabs(aug[r][c]) > std::fabs(aug[piv][c])) piv = r;
+    if (aug[piv][c] == 0.0) return false;
+    for (int j = 0; j < 12; ++j) std::swap(aug[c][j], aug[piv][j]);
+    const double d = aug[c][c];
+    for (int j = 0; j < 12; ++j) aug[c][j] /= d;
+    for (int r = 0; r < 6; ++r) {
+      if (r == c) continue;
+      const double f = aug[r][c];
+      for (int j = 0; j < 12; ++j) aug[r][j] -= f * aug[c][j];
+    }
+  }
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) A[6 * i + j] = aug[i][j + 6];
+  return true;
+}
+
+void refresh_config(rbfib_grid* g, Config& c, bool bin) {
+  geometry(g->nbl, g->bob, g->ref, c.q, c.quat, c.r, c.arm, g->s);
+  if (bin) binning(g->d, g->nbl, c.r, c.perm, g->celloff, g->bkey, g->bcount, g->bfill, g->bbsum, g->s);
+}
+
+void alloc_config(rbfib_grid* g, Config& c) {
+  c.q.alloc(3 * (size_t)g->nb);
+  c.quat.alloc(4 * (size_t)g->nb);
+  c.r.alloc(3 * (size_t)g->nbl);
+  c.arm.alloc(3 * (size_t)g->nbl);
+  c.perm.alloc((size_t)g->nbl);
+}
+
+void alloc_solver(rbfib_grid* g) {
+  const i64 n = g->n_total();
+  const int m = g->desc.restart;
+  if (g->desc.precision == RBFIB_FP64) {
+    if (g->kr64.n < n || g->kr64.m != m) g->kr64.build(m, n);
+  } else {
+    if (g->kr32.n < n || g->kr32.m != m) g->kr32.build(m, n);
+    g->f32a.ensure(n);
+    g->f32b.ensure(n);
+    g->rres.ensure(n);
+  }
+  g->bvec.ensure(n); g->xvec.ensure(n); g->xrfd.ensure(n);
+  // the FP32 refinement keeps an FP64 residual and correction
+  g->blobA.ensure(std::max<i64>(3 * (i64)g->nbl, 1));
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+const char* rbfib_last_error(const rbfib_grid* g) { return g ? g->err.c_str() : "null grid"; }
+
+int rbfib_create_grid(const rbfib_grid_desc* desc, void* stream, rbfib_grid** out) {
+  if (!desc || !out) return RBFIB_EINVAL;
+  *out = nullptr;
+  const rbfib_grid_desc& D = *desc;
+  for (int a = 0; a < 3; ++a)
+    if (D.n[a] < 2 || (D.periodic[a] != 0 && D.periodic[a] != 1)) return RBFIB_EINVAL;
+  if (D.periodic[0] && D.periodic[1] && D.periodic[2]) return RBFIB_EINVAL;
+  if (!(D.h > 0) || !(D.eta > 0) || D.kernel != 3 || D.restart < 1 || D.restart > 64 || D.max_iter < 1 ||
+      !(D.rtol > 0) || (D.precision != RBFIB_FP64 && D.precision != RBFIB_FP32_REFINED))
+    return RBFIB_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (D.wall_vel[2 * a][a] != 0.0 || D.wall_vel[2 * a + 1][a] != 0.0) return RBFIB_EINVAL;
+  rbfib_grid* g = new rbfib_grid();
+  try {
+    g->desc = D;
+    g->s = (cudaStream_t)stream;
+    build_levels(g);
+    g->d = g->levels[0].d;
+    for (int w = 0; w < 6; ++w)
+      for (int c = 0; c < 3; ++c) g->walls.v[w][c] = D.wall_vel[w][c];
+    g->nf = g->d.fo[3];
+    g->nc = g->d.nc;
+    g->nfl = g->nf + g->nc;
+    g->dV = D.h * D.h * D.h;
+    build_stress_layout(g);
+    g->nparts = 152 * 4;
+    g->part.alloc((size_t)g->nparts * 130 + 8);
+    g->small.alloc((size_t)(D.restart + 1) * D.restart + 4 * D.restart + 512);
+    ck(cudaMallocHost((void**)&g->h_pinned, 64 * sizeof(double)));
+    if (D.precision == RBFIB_FP64) g->mg64.build(g->levels);
+    else { g->mg32.build(g->levels); g->mg64.build(g->levels); }
+    g->bcount.alloc(g->nc + 1);
+    g->bfill.alloc(g->nc);
+    g->celloff.alloc(g->nc + 1);
+    g->bbsum.alloc((g->nc + 1) / 1024 + 2);
+    g->boff.alloc(1);
+    ck(cudaMemsetAsync(g->boff, 0, sizeof(int), g->s));
+    g->h_boff.assign(1, 0);
+    g->fsharp.alloc(g->nf); g->vsharp.alloc(g->nf); g->fnoise.alloc(g->nf);
+    g->Wst.alloc(g->stress.total);
+    alloc_solver(g);
+    ck(cudaStreamSynchronize(g->s));
+  } catch (CudaError& e) {
+    std::string msg = std::string("create_grid: ") + cudaGetErrorString(e.e);
+    delete g;
+    (void)msg;
+    return RBFIB_ECUDA;
+  }
+  *out = g;
+  return RBFIB_OK;
+}
+
+void rbfib_destroy(rbfib_grid* g) {
+  if (!g) return;
+  if (g->s) cudaStreamSynchronize(g->s);
+  if (g->h_pinned) cudaFreeHost(g->h_pinned);
+  delete g;
+}
+
+int rbfib_saddle_layout(const rbfib_grid* g, int64_t off[7]) {
+  if (!g || !off) return RBFIB_EINVAL;
+  off[0] = 0;
+  off[1] = g->d.fo[1];
+  off[2] = g->d.fo[2];
+  off[3] = g->nf;
+  off[4] = g->nfl;
+  off[5] = g->nfl + 3 * (i64)g->nbl;
+  off[6] = off[5] + 6 * (i64)g->nb;
+  return RBFIB_OK;
+}
+
+int rbfib_set_bodies(rbfib_grid* g, int32_t n_bodies, const int32_t* blob_offsets, const double* ref_blobs,
+                     const double* q, const double* quat) {
+  if (!g || n_bodies < 0 || (n_bodies > 0 && (!blob_offsets || !ref_blobs || !q || !quat)))
+    return fail(g, RBFIB_EINVAL, "set_bodies: bad arguments");
+  std::vector<int> off(n_bodies + 1, 0);
+  if (n_bodies > 0) {
+    std::memcpy(off.data(), blob_offsets, sizeof(int) * (n_bodies + 1));
+    if (off[0] != 0) return fail(g, RBFIB_EINVAL, "set_bodies: blob_offsets[0] must be 0");
+    for (int p = 0; p < n_bodies; ++p)
+      if (off[p + 1] <= off[p]) return fail(g, RBFIB_EINVAL, "set_bodies: every body needs at least one blob");
+  }
+  try {
+    ck(cudaStreamSynchronize(g->s));
+    g->nb = n_bodies;
+    g->nbl = off[n_bodies];
+    g->h_boff = off;
+    const int nb = g->nb, nbl = g->nbl;
+    g->boff.alloc(nb + 1);
+    ck(cudaMemcpyAsync(g->boff, off.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, g->s));
+    std::vector<int> bob(nbl);
+    for (int p = 0; p < nb; ++p)
+      for (int i = off[p]; i < off[p + 1]; ++i) bob[i] = p;
+    g->bob.alloc(std::max(nbl, 1));
+    if (nbl) ck(cudaMemcpyAsync(g->bob, bob.data(), sizeof(int) * nbl, cudaMemcpyHostToDevice, g->s));
+    g->ref.alloc(3 * (size_t)std::max(nbl, 1));
+    if (nbl) ck(cudaMemcpyAsync(g->ref, ref_blobs, sizeof(double) * 3 * nbl, cudaMemcpyDeviceToDevice, g->s));
+    for (Config* c : {&g->cur, &g->plus, &g->minus, &g->next}) alloc_config(g, *c);
+    if (nb) {
+      ck(cudaMemcpyAsync(g->cur.q, q, sizeof(double) * 3 * nb, cudaMemcpyDeviceToDevice, g->s));
+      ck(cudaMemcpyAsync(g->cur.quat, quat, sizeof(double) * 4 * nb, cudaMemcpyDeviceToDevice, g->s));
+    }
+    g->bkey.alloc(std::max(nbl, 1));
+    refresh_config(g, g->cur, true);
+    // host copy of the reference blobs: body lengths and shape table
+    std::vector<double> href(3 * (size_t)nbl);
+    if (nbl) ck(cudaMemcpyAsync(href.data(), ref_blobs, sizeof(double) * 3 * nbl, cudaMemcpyDeviceToHost, g->s));
+    ck(cudaStreamSynchronize(g->s));
+    std::vector<double> Lp(std::max(nb, 1), 0.0);
+    std::vector<int> shape_of(std::max(nb, 1), 0), shape_rep;
+    g->max_blobs = 0;
+    for (int p = 0; p < nb; ++p) {
+      const int n = off[p + 1] - off[p];
+      g->max_blobs = std::max(g->max_blobs, n);
+      const double* x = href.data() + 3 * (size_t)off[p];
+      double mx = 0.0;
+      for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+          double dd = 0.0;
+          for (int a = 0; a < 3; ++a) dd += (x[3 * i + a] - x[3 * j + a]) * (x[3 * i + a] - x[3 * j + a]);
+          mx = std::max(mx, std::sqrt(dd));
+        }
+      Lp[p] = mx;
+      int found = -1;
+      for (size_t s = 0; s < shape_rep.size(); ++s) {
+        const int q0 = shape_rep[s];
+        if (off[q0 + 1] - off[q0] == n &&
+            std::memcmp(href.data() + 3 * (size_t)off[q0], x, sizeof(double) * 3 * n) == 0) { found = (int)s; break; }
+      }
+      if (found < 0) { found = (int)shape_rep.size(); shape_rep.push_back(p); }
+      shape_of[p] = found;
+    }
+    g->Lp.alloc(std::max(nb, 1));
+    ck(cudaMemcpyAsync(g->Lp, Lp.data(), sizeof(double) * std::max(nb, 1), cudaMemcpyHostToDevice, g->s));
+    // per-shape RPY inverse and body mobility
+    const int ns = (int)shape_rep.size();
+    std::vector<i64> moff(std::max(ns, 1), 0);
+    std::vector<double> minv_all, nmat(36 * (size_t)std::max(ns, 1), 0.0);
+    std::vector<int> srep(std::max(ns, 1), 0);
+    for (int s = 0; s < ns; ++s) {
+      const int p = shape_rep[s];
+      const int n = off[p + 1] - off[p];
+      const double* x = href.data() + 3 * (size_t)off[p];
+      std::vector<double> M;
+      rpy_matrix(x, n, kBlobRadius * g->desc.h, g->desc.eta, M);
+      if (!spd_inverse(M, 3 * n)) return fail(g, RBFIB_EINVAL, "set_bodies: blob mobility of a shape is singular");
+      moff[s] = (i64)minv_all.size();
+      srep[s] = off[p];
+      // K^T M^-1 K in the body frame
+      double A[36] = {0};
+      std::vector<double> Kc(3 * (size_t)n * 6, 0.0);   // K (3n x 6)
+      for (int i = 0; i < n; ++i) {
+        const double* r = x + 3 * i;
+        for (int a = 0; a < 3; ++a) Kc[(size_t)(3 * i + a) * 6 + a] = 1.0;
+        // w x r = -[r]_x w
+        Kc[(size_t)(3 * i + 0) * 6 + 4] = r[2];  Kc[(size_t)(3 * i + 0) * 6 + 5] = -r[1];
+        Kc[(size_t)(3 * i + 1) * 6 + 3] = -r[2]; Kc[(size_t)(3 * i + 1) * 6 + 5] = r[0];
+        Kc[(size_t)(3 * i + 2) * 6 + 3] = r[1];  Kc[(size_t)(3 * i + 2) * 6 + 4] = -r[0];
+      }
+      const int n3 = 3 * n;
+      std::vector<double> MK((size_t)n3 * 6, 0.0);
+      for (int r = 0; r < n3; ++r)
+        for (int c = 0; c < 6; ++c) {
+          double acc = 0.0;
+          for (int k = 0; k < n3; ++k) acc += M[(size_t)r * n3 + k] * Kc[(size_t)k * 6 + c];
+          MK[(size_t)r * 6 + c] = acc;
+        }
+      for (int r = 0; r < 6; ++r)
+        for (int c = 0; c < 6; ++c) {
+          double acc = 0.0;
+          for (int k = 0; k < n3; ++k) acc += Kc[(size_t)k * 6 + r] * MK[(size_t)k * 6 + c];
+          A[6 * r + c] = acc;
+        }
+      if (!inverse6(A)) return fail(g, RBFIB_EINVAL, "set_bodies: body resistance is singular");
+      std::memcpy(nmat.data() + 36 * (size_t)s, A, sizeof(A));
+      minv_all.insert(minv_all.end(), M.begin(), M.end());
+    }
+    g->shape_of.alloc(std::max(nb, 1));
+    ck(cudaMemcpyAsync(g->shape_of, shape_of.data(), sizeof(int) * std::max(nb, 1), cudaMemcpyHostToDevice, g->s));
+    g->shape_ref_blob.alloc(std::max(ns, 1));
+    ck(cudaMemcpyAsync(g->shape_ref_blob, srep.data(), sizeof(int) * std::max(ns, 1), cudaMemcpyHostToDevice, g->s));
+    g->minv_off.alloc(std::max(ns, 1));
+    ck(cudaMemcpyAsync(g->minv_off, moff.data(), sizeof(i64) * std::max(ns, 1), cudaMemcpyHostToDevice, g->s));
+    g->minv.alloc(std::max<size_t>(minv_all.size(), 1));
+    if (!minv_all.empty())
+      ck(cudaMemcpyAsync(g->minv, minv_all.data(), sizeof(double) * minv_all.size(), cudaMemcpyHostToDevice, g->s));
+    g->nmat.alloc(nmat.size());
+    ck(cudaMemcpyAsync(g->nmat, nmat.data(), sizeof(double) * nmat.size(), cudaMemcpyHostToDevice, g->s));
+    // body-sized work arrays
+    const size_t b6 = 6 * (size_t)std::max(nb, 1), l3 = 3 * (size_t)std::max(nbl, 1);
+    for (DBuf<double>* b : {&g->bodyA, &g->bodyB, &g->bodyF, &g->bodyW, &g->bodyWn}) b->alloc(b6);
+    for (DBuf<double>* b : {&g->blobA, &g->blobB, &g->blobC, &g->blobD, &g->blobS, &g->sres}) b->alloc(l3);
+    alloc_solver(g);
+    ck(cudaStreamSynchronize(g->s));
+    ck(cudaGetLastError());
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, std::string("set_bodies: ") + cudaGetErrorString(e.e));
+  }
+  return RBFIB_OK;
+}
+
+int rbfib_apply_saddle(rbfib_grid* g, const void* x, void* y, int32_t dtype) {
+  if (!g || !x || !y) return fail(g, RBFIB_EINVAL, "apply_saddle: null argument");
+  try {
+    if (dtype == RBFIB_DTYPE_F64) apply_A<double>(g, (const double*)x, (double*)y, true);
+    else if (dtype == RBFIB_DTYPE_F32) apply_A<float>(g, (const float*)x, (float*)y, true);
+    else return fail(g, RBFIB_EINVAL, "apply_saddle: dtype");
+    ck(cudaGetLastError());
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, std::string("apply_saddle: ") + cudaGetErrorString(e.e));
+  }
+  return RBFIB_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Right-hand side of the constrained system: fluid forcing + wall terms,
+// -slip + J wall part, forces.  b is FP64 in the saddle layout.
+void build_rhs(rbfib_grid* g, const double* FT, const double* slip, const double* fluid, bool walls, double* b) {
+  const i64 n = g->n_total();
+  ck(cudaMemsetAsync(b, 0, sizeof(double) * n, g->s));
+  if (fluid) ck(cudaMemcpyAsync(b, fluid, sizeof(double) * g->nf, cudaMemcpyDeviceToDevice, g->s));
+  if (walls) wall_rhs<double>(g->d, g->walls, g->desc.eta, b, g->s);
+  if (g->nbl > 0) {
+    double* bl = b + g->nfl;
+    if (walls) interp<double>(g->d, g->walls, g->nbl, g->cur.r, (const double*)nullptr, 0.0, 0.0, 1.0, bl, g->s);
+    if (slip) axpby<double>(bl, slip, -1.0, 1.0, 3 * (i64)g->nbl, g->s);
+  }
+  if (g->nb > 0 && FT)
+    ck(cudaMemcpyAsync(b + g->nfl + 3 * (i64)g->nbl, FT, sizeof(double) * 6 * g->nb, cudaMemcpyDeviceToDevice, g->s));
+}
+
+// Solve A x = b (FP64 in and out).  FP64 mode: FGMRES in FP64.  FP32 mode:
+// iterative refinement, r = b - A x in FP64, inner FGMRES in FP32.
+int solve_system(rbfib_grid* g, const double* b, double* x, bool with_bodies, rbfib_solve_info* info) {
+  const i64 n = with_bodies ? g->n_total() : g->nfl;
+  const double rtol = g->desc.rtol;
+  int iters = 0, st = 0;
+  double rel = 0.0;
+  if (g->desc.precision == RBFIB_FP64) {
+    st = fgmres<double>(g, b, x, with_bodies, rtol, g->desc.max_iter, iters, rel);
+    if (info) { info->iterations = iters; info->refinements = 0; info->rel_residual = rel; }
+  } else {
+    // outer refinement in FP64
+    SmallPtrs sp = small_ptrs(g, g->desc.restart);
+    double* r = g->rres;      // FP64 residual of the refinement
+    multi_dot<double>(b, b, n, 1, n, g->nfl, g->dV, g->part, g->nparts, sp.bn, g->s);
+    const double bn = std::sqrt(std::max(read_scalar(g, sp.bn), 0.0));
+    ck(cudaMemsetAsync(x, 0, sizeof(double) * n, g->s));
+    if (!(bn > 0.0)) { if (info) { info->iterations = 0; info->refinements = 0; info->rel_residual = 0; } return 0; }
+    ck(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->s));
+    int sweeps = 0, total = 0;
+    rel = 1.0;
+    const double inner_tol = 1e-4;
+    while (rel > rtol && total < g->desc.max_iter && sweeps < 50) {
+      convert<double, float>(r, g->f32a, n, g->s);
+      int it = 0;
+      double irel = 0.0;
+      int ist = fgmres<float>(g, g->f32a, g->f32b, with_bodies, inner_tol, g->desc.max_iter - total, it, irel);
+      total += it;
+      ++sweeps;
+      if (ist == RBFIB_ENAN) { st = ist; break; }
+      // x += d (FP64), r = b - A x (FP64)
+      convert<float, double>(g->f32b, r, n, g->s);
+      axpby<double>(x, r, 1.0, 1.0, n, g->s);
+      apply_A<double>(g, x, r, with_bodies);
+      axpby<double>(r, b, 1.0, -1.0, n, g->s);
+      multi_dot<double>(r, r, n, 1, n, g->nfl, g->dV, g->part, g->nparts, sp.bn, g->s);
+      rel = std::sqrt(std::max(read_scalar(g, sp.bn), 0.0)) / bn;
+      if (std::isnan(rel)) { st = RBFIB_ENAN; break; }
+    }
+    if (st == 0 && rel > rtol) st = RBFIB_ENOCONV;
+    if (info) { info->iterations = total; info->refinements = sweeps; info->rel_residual = rel; }
+  }
+  // pressure gauge: mean(pi) = 0
+  project_mean(x + g->nf, g->nc, g->part, g->nparts, g->s);
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rbfib_mobility_solve(rbfib_grid* g, const double* FT, const double* slip, const double* fluid_rhs, double* U,
+                         double* x_full, rbfib_solve_info* info) {
+  if (!g || (g->nb > 0 && !FT)) return fail(g, RBFIB_EINVAL, "mobility_solve: null argument");
+  try {
+    build_rhs(g, FT, slip, fluid_rhs, true, g->bvec);
+    int st = solve_system(g, g->bvec, g->xvec, true, info);
+    if (U && g->nb > 0)
+      ck(cudaMemcpyAsync(U, g->xvec.p + g->nfl + 3 * (i64)g->nbl, sizeof(double) * 6 * g->nb,
+                         cudaMemcpyDeviceToDevice, g->s));
+    if (x_full) ck(cudaMemcpyAsync(x_full, g->xvec, sizeof(double) * g->n_total(), cudaMemcpyDeviceToDevice, g->s));
+    ck(cudaStreamSynchronize(g->s));
+    ck(cudaGetLastError());
+    if (st) return fail(g, st, st == RBFIB_ENOCONV ? "mobility_solve: no convergence" : "mobility_solve: NaN");
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, std::string("mobility_solve: ") + cudaGetErrorString(e.e));
+  }
+  return RBFIB_OK;
+}
+
+int rbfib_stokes_solve(rbfib_grid* g, const double* f, double* v, double* pi, rbfib_solve_info* info) {
+  if (!g || !f || !v) return fail(g, RBFIB_EINVAL, "stokes_solve: null argument");
+  try {
+    ck(cudaMemsetAsync(g->bvec, 0, sizeof(double) * g->nfl, g->s));
+    ck(cudaMemcpyAsync(g->bvec, f, sizeof(double) * g->nf, cudaMemcpyDeviceToDevice, g->s));
+    int st = solve_system(g, g->bvec, g->xvec, false, info);
+    ck(cudaMemcpyAsync(v, g->xvec, sizeof(double) * g->nf, cudaMemcpyDeviceToDevice, g->s));
+    if (pi) ck(cudaMemcpyAsync(pi, g->xvec.p + g->nf, sizeof(double) * g->nc, cudaMemcpyDeviceToDevice, g->s));
+    ck(cudaStreamSynchronize(g->s));
+    ck(cudaGetLastError());
+    if (st) return fail(g, st, "stokes_solve: no convergence");
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, std::string("stokes_solve: ") + cudaGetErrorString(e.e));
+  }
+  return RBFIB_OK;
+}
+
+int rbfib_binning(rbfib_grid* g, int32_t* perm, int32_t* cell_offsets) {
+  if (!g) return RBFIB_EINVAL;
+  try {
+    if (perm && g->nbl) ck(cudaMemcpyAsync(perm, g->cur.perm, sizeof(int) * g->nbl, cudaMemcpyDeviceToDevice, g->s));
+    if (cell_offsets)
+      ck(cudaMemcpyAsync(cell_offsets, g->celloff, sizeof(int) * (g->nc + 1), cudaMemcpyDeviceToDevice, g->s));
+    ck(cudaGetLastError());
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, std::string("binning: ") + cudaGetErrorString(e.e));
+  }
+  return RBFIB_OK;
+}
+
+int rbfib_blob_positions(rbfib_grid* g, double* r) {
+  if (!g || !r) return RBFIB_EINVAL;
+  try {
+    if (g->nbl) ck(cudaMemcpyAsync(r, g->cur.r, sizeof(double) * 3 * g->nbl, cudaMemcpyDeviceToDevice, g->s));
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+  }
+  return RBFIB_OK;
+}
+
+int rbfib_philox_normals(rbfib_grid* g, uint64_t seed, uint64_t step, uint32_t attempt, uint32_t purpose,
+                         int64_t count, double* out) {
+  if (!g || count < 0 || (count > 0 && !out)) return fail(g, RBFIB_EINVAL, "philox_normals: bad argument");
+  try {
+    philox_normals(seed, step, attempt, purpose, count, out, g->s);
+    ck(cudaGetLastError());
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+  }
+  return RBFIB_OK;
+}
+
+int rbfib_stochastic_forcing(rbfib_grid* g, double kT, double dt, uint64_t seed, uint64_t step, uint32_t attempt,
+                             double* out) {
+  if (!g || !out || !(dt > 0) || !(kT >= 0)) return fail(g, RBFIB_EINVAL, "stochastic_forcing: bad argument");
+  try {
+    philox_normals(seed, step, attempt, 1u, g->stress.total, g->Wst, g->s);
+    const double c = std::sqrt(2.0 * g->desc.eta * kT / (g->dV * dt));
+    stress_divergence(g->d, g->stress, g->Wst, c, out, g->s);
+    ck(cudaGetLastError());
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+  }
+  return RBFIB_OK;
+}
+
+int rbfib_spread(rbfib_grid* g, const double* lambda, double* f) {
+  if (!g || !f || (g->nbl && !lambda)) return fail(g, RBFIB_EINVAL, "spread: null argument");
+  try {
+    ck(cudaMemsetAsync(f, 0, sizeof(double) * g->nf, g->s));
+    spread<double>(g->d, g->nbl, g->cur.perm, g->cur.r, lambda, 1.0 / g->dV, f, g->s);
+    ck(cudaGetLastError());
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+  }
+  return RBFIB_OK;
+}
+
+int rbfib_interpolate(rbfib_grid* g, const double* v, double* u, int32_t with_walls) {
+  if (!g || !v || (g->nbl && !u)) return fail(g, RBFIB_EINVAL, "interpolate: null argument");
+  try {
+    interp<double>(g->d, g->walls, g->nbl, g->cur.r, v, 1.0, 0.0, with_walls ? 1.0 : 0.0, u, g->s);
+    ck(cudaGetLastError());
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+  }
+  return RBFIB_OK;
+}
+
+}  // extern "C"
+
+namespace {
+Potentials potentials_of(const rbfib_sem_params* p) {
+  Potentials P;
+  P.gravity = p->gravity;
+  P.pair_phi0 = p->pair_phi0; P.pair_b = p->pair_b; P.pair_d = p->pair_d;
+  P.wall_phi0 = p->wall_phi0; P.wall_b = p->wall_b; P.wall_d = p->wall_d;
+  P.bw_phi0 = p->blob_wall_phi0; P.bw_b = p->blob_wall_b; P.bw_d = p->blob_wall_d;
+  P.yuk_u0 = p->yukawa_u0; P.yuk_dh = p->yukawa_dh; P.yuk_lambda = p->yukawa_lambda;
+  P.sub_u0 = p->substrate_u0; P.sub_s = p->substrate_s;
+  return P;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rbfib_body_forces(rbfib_grid* g, const rbfib_sem_params* p, double* out) {
+  if (!g || !p || (g->nb && !out)) return fail(g, RBFIB_EINVAL, "body_forces: null argument");
+  try {
+    body_forces(g->d, potentials_of(p), view_of(g, g->cur), p->force_ext, out, g->s);
+    ck(cudaGetLastError());
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+  }
+  return RBFIB_OK;
+}
+
+// Algorithm 1 (Split-Euler-Maruyama), steps 1-7.
+int rbfib_sem_step(rbfib_grid* g, const rbfib_sem_params* p, uint64_t seed, uint64_t step, uint32_t attempt,
+                   double* q, double* quat, rbfib_step_info* info) {
+  if (!g || !p || (g->nb > 0 && (!q || !quat)) || !(p->dt > 0) || !(p->kT >= 0))
+    return fail(g, RBFIB_EINVAL, "sem_step: bad argument");
+  const int nb = g->nb, nbl = g->nbl;
+  const double delta = p->delta > 0 ? p->delta : kDeltaDefault;
+  rbfib_step_info loc{};
+  int st = 0;
+  try {
+    const i64 n = g->n_total();
+    const cudaStream_t s = g->s;
+    // current configuration
+    if (nb) {
+      ck(cudaMemcpyAsync(g->cur.q, q, sizeof(double) * 3 * nb, cudaMemcpyDeviceToDevice, s));
+      ck(cudaMemcpyAsync(g->cur.quat, quat, sizeof(double) * 4 * nb, cudaMemcpyDeviceToDevice, s));
+    }
+    refresh_config(g, g->cur, true);
+    // forces F^n
+    body_forces(g->d, potentials_of(p), view_of(g, g->cur), p->force_ext, g->bodyF, s);
+    // step 1: random forces and torques W^FT = kT [W^f / L_p ; W^tau]
+    philox_normals(seed, step, attempt, 2u, 6 * (i64)nb, g->bodyWn, s);
+    wft(nb, g->bodyWn, g->Lp, p->kT, g->bodyW, s);
+    // step 2: constrained solve with W^FT (homogeneous)
+    build_rhs(g, g->bodyW, nullptr, nullptr, false, g->bvec);
+    int st1 = solve_system(g, g->bvec, g->xvec, true, &loc.solve_rfd);
+    if (st1) st = st1;
+    ck(cudaMemcpyAsync(g->xrfd, g->xvec, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    const double* v_rfd = g->xrfd;
+    const double* lam_rfd = g->xrfd.p + g->nfl;
+    const double* U_rfd = lam_rfd + 3 * (i64)nbl;
+    // step 3: displaced configurations Q+- (lab-frame rotations by +-(delta/2) W^tau)
+    move_bodies(nb, g->cur.q, g->cur.quat, g->bodyWn, g->Lp, 0.5 * delta, g->plus.q, g->plus.quat, s);
+    move_bodies(nb, g->cur.q, g->cur.quat, g->bodyWn, g->Lp, -0.5 * delta, g->minus.q, g->minus.quat, s);
+    refresh_config(g, g->plus, false);
+    refresh_config(g, g->minus, false);
+    // step 4: unconstrained Stokes solve with (S(Q+) - S(Q-)) lambda / delta
+    ck(cudaMemsetAsync(g->fsharp, 0, sizeof(double) * g->nf, s));
+    spread<double>(g->d, nbl, nullptr, g->plus.r, lam_rfd, 1.0 / (delta * g->dV), g->fsharp, s);
+    spread<double>(g->d, nbl, nullptr, g->minus.r, lam_rfd, -1.0 / (delta * g->dV), g->fsharp, s);
+    ck(cudaMemsetAsync(g->bvec, 0, sizeof(double) * g->nfl, s));
+    ck(cudaMemcpyAsync(g->bvec, g->fsharp, sizeof(double) * g->nf, cudaMemcpyDeviceToDevice, s));
+    int st2 = solve_system(g, g->bvec, g->xvec, false, &loc.solve_stokes);
+    if (st2 && !st) st = st2;
+    ck(cudaMemcpyAsync(g->vsharp, g->xvec, sizeof(double) * g->nf, cudaMemcpyDeviceToDevice, s));
+    // step 5: random finite differences
+    Walls w0 = {};
+    kt_apply(nb, g->boff, g->plus.arm, lam_rfd, 1.0, 0.0, g->bodyA, s);
+    kt_apply(nb, g->boff, g->minus.arm, lam_rfd, 1.0, 0.0, g->bodyB, s);
+    axpby<double>(g->bodyA, g->bodyB, -1.0, 1.0, 6 * (i64)nb, s);          // A = KT+ - KT-
+    axpby<double>(g->bodyA, g->bodyA, 0.0, 1.0 / delta, 6 * (i64)nb, s);   // D^{K^T}
+    k_apply(nbl, g->bob, g->plus.arm, U_rfd, 1.0, 0.0, g->blobA, s);
+    k_apply(nbl, g->bob, g->minus.arm, U_rfd, 1.0, 0.0, g->blobB, s);
+    axpby<double>(g->blobA, g->blobB, -1.0, 1.0, 3 * (i64)nbl, s);
+    axpby<double>(g->blobA, g->blobA, 0.0, 1.0 / delta, 3 * (i64)nbl, s);  // D^K
+    interp<double>(g->d, w0, nbl, g->plus.r, v_rfd, 1.0, 0.0, 0.0, g->blobC, s);
+    interp<double>(g->d, w0, nbl, g->minus.r, v_rfd, 1.0, 0.0, 0.0, g->blobD, s);
+    axpby<double>(g->blobC, g->blobD, -1.0, 1.0, 3 * (i64)nbl, s);
+    axpby<double>(g->blobC, g->blobC, 0.0, 1.0 / delta, 3 * (i64)nbl, s);  // D^J
+    interp<double>(g->d, w0, nbl, g->cur.r, (const double*)g->vsharp, 1.0, 0.0, 0.0, g->blobD, s);  // D^S
+    // slip_tot = slip + D^K - D^J - D^S ; F_tot = F - D^{K^T}
+    if (p->slip) ck(cudaMemcpyAsync(g->blobS, p->slip, sizeof(double) * 3 * nbl, cudaMemcpyDeviceToDevice, s));
+    else ck(cudaMemsetAsync(g->blobS, 0, sizeof(double) * 3 * std::max(nbl, 1), s));
+    axpby<double>(g->blobS, g->blobA, 1.0, 1.0, 3 * (i64)nbl, s);
+    axpby<double>(g->blobS, g->blobC, -1.0, 1.0, 3 * (i64)nbl, s);
+    axpby<double>(g->blobS, g->blobD, -1.0, 1.0, 3 * (i64)nbl, s);
+    axpby<double>(g->bodyF, g->bodyA, -1.0, 1.0, 6 * (i64)nb, s);
+    // step 6: fluctuating constrained solve
+    philox_normals(seed, step, attempt, 1u, g->stress.total, g->Wst, s);
+    stress_divergence(g->d, g->stress, g->Wst, std::sqrt(2.0 * g->desc.eta * p->kT / (g->dV * p->dt)), g->fnoise, s);
+    build_rhs(g, g->bodyF, g->blobS, g->fnoise, true, g->bvec);
+    int st3 = solve_system(g, g->bvec, g->xvec, true, &loc.solve_main);
+    if (st3 && !st) st = st3;
+    // step 7: update and rejection test
+    const double* Un = g->xvec.p + g->nfl + 3 * (i64)nbl;
+    move_bodies(nb, g->cur.q, g->cur.quat, Un, nullptr, p->dt, g->next.q, g->next.quat, s);
+    refresh_config(g, g->next, false);
+    int* flag = (int*)g->part.p;   // scratch word
+    ck(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    outside_check(g->d, nbl, g->next.r, flag, s);
+    int hflag = 0;
+    ck(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ck(cudaStreamSynchronize(s));
+    loc.rejected = hflag ? 1 : 0;
+    if (!hflag && !st && nb) {
+      ck(cudaMemcpyAsync(q, g->next.q, sizeof(double) * 3 * nb, cudaMemcpyDeviceToDevice, s));
+      ck(cudaMemcpyAsync(quat, g->next.quat, sizeof(double) * 4 * nb, cudaMemcpyDeviceToDevice, s));
+    }
+    ck(cudaStreamSynchronize(s));
+    ck(cudaGetLastError());
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, std::string("sem_step: ") + cudaGetErrorString(e.e));
+  }
+  if (info) *info = loc;
+  if (st) return fail(g, st, "sem_step: a solve did not converge");
+  if (loc.rejected) return fail(g, RBFIB_EREJECT, "sem_step: unphysical configuration rejected");
+  return RBFIB_OK;
+}
+
+}  // extern "C"
