@@ -1,0 +1,298 @@
+#!/usr/bin/env python3
+"""Benchmark of the RB-FIB hot path on one GB300.
+
+Workload: the fluctuating two-sphere cavity (two 42-blob spheres, R = 2.5h,
+48x48x32 cells, no-slip walls, kT = 1, dt = 0.05, FP64, GMRES relative
+residual 1e-8).  A step is one Split-Euler-Maruyama step (Algorithm 1): three
+Krylov solves (RFD solve, unconstrained Stokes solve, fluctuating solve) plus
+noise, RFD differences, forces and the update.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank advances its own
+independent replica (different seed); value = all ranks' steps / max time.
+The reference arm times the FP64 CPU oracle on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SEM steps/s at GMRES rel.res 1e-8; Stokes-IB matvec HBM GB/s; refined vs FP64"
+L2_FLUSH_BYTES = 512 << 20
+TIMER_NAMES = {"matvec": 1, "smooth": 2, "dot": 3, "axpy": 4}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--roofline-kernel", default="dot", choices=list(TIMER_NAMES))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-rhs", type=int, default=16)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload_config(w):
+    return {"workload": w.name, "grid": list(w.n), "bodies": w.n_bodies, "blobs_per_body": 42,
+            "kernel": "3-point Peskin", "dt": w.dt, "kT": w.kT, "rtol": 1e-8, "precision": "fp64",
+            "l2": "flushed (512 MiB write) between timed steps", "data": "synthetic, seeded"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        out.update({"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                    "reasons": reasons, "samples": len(rows)})
+        return out
+
+
+# -------------------------------------------------------------- CPU oracle
+def oracle_sample(w, n_rhs):
+    """Time the oracle's unit of work for this workload on the host cores.
+
+    The oracle's SEM step performs 3 N_bl + 5 Stokes solves (the dense blob
+    mobility, two constrained solves with two Stokes solves each and the
+    unconstrained solve).  The sample is one batch of n_rhs of them (spread
+    unit blob forces, as in its mobility assembly); the step rate is scaled
+    from the per-solve time."""
+    import numpy as np
+    import oracle
+    from oracle import saddle, solve, ib
+    g = oracle.Grid(w.n, periodic=w.periodic, wall_vel=w.wall_vel)
+    b = saddle.Bodies(w.ref_blobs, w.blob_offsets, w.q, w.quat)
+    op = solve.StokesOperator(g, w.eta)
+    r = b.positions()
+    F = np.zeros((n_rhs, g.N_f))
+    for t in range(n_rhs):
+        e = np.zeros(3 * b.n_blobs); e[t % (3 * b.n_blobs)] = 1.0
+        F[t] = ib.spread(g, r, e)
+    t0 = time.perf_counter()
+    op.solve(F)
+    dt = time.perf_counter() - t0
+    solves_per_step = 3 * b.n_blobs + 5
+    sec_per_step = dt / n_rhs * solves_per_step
+    return {"value": 1.0 / sec_per_step, "unit": "SEM steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n_rhs} of the {solves_per_step} Stokes solves of one oracle SEM step on the "
+                      f"{w.n[0]}x{w.n[1]}x{w.n[2]} two-sphere workload ({dt:.1f} s), scaled to one step; "
+                      "numpy/scipy FP64, scipy.fft single-threaded",
+            "sample_seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads
+    w = workloads.two_sphere_cavity(steps=1)
+    n_rhs = max(2, args.cpu_sample_rhs // 2)
+    for _ in range(args.warmup):
+        oracle_sample(w, n_rhs)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_sample(w, n_rhs))
+    wall = time.perf_counter() - t0
+    sec = sum(1.0 / v["value"] for v in vals)
+    value = args.steps / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "SEM steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w),
+            "cpu_baseline": {"value": value, "unit": "SEM steps/s", "cores": 1, "kind": "oracle",
+                             "sample": vals[0]["sample"] + f"; {args.steps} samples in {wall:.1f} s"},
+            "e2e": {"value": value, "unit": "SEM steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_1901_06427_gb300.binding as B
+    import workloads
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = workloads.two_sphere_cavity(steps=args.steps)
+    g = B.grid_for(w, rtol=1e-8)
+    p = B.sem_params(w.potentials, dt=w.dt, kT=w.kT)
+    q = torch.tensor(w.q.ravel(), device="cuda")
+    quat = torch.tensor(w.quat.ravel(), device="cuda")
+    seed = w.seed + 7919 * rank
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    state = {"step": 0, "rejects": 0, "iters": []}
+
+    def one_step(qq, qt):
+        attempt = 0
+        while True:
+            st, info = g.sem_step(p, seed, state["step"], attempt, qq, qt)
+            if st == 0:
+                break
+            attempt += 1
+            state["rejects"] += 1
+            if attempt > 20:
+                raise RuntimeError("too many rejected steps")
+        state["step"] += 1
+        state["iters"].append((info["solve_rfd"]["iterations"], info["solve_stokes"]["iterations"],
+                               info["solve_main"]["iterations"]))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        one_step(q, quat)
+    torch.cuda.synchronize()
+    # ------------------------------------------------ device-resident timing
+    g.kernel_timer(TIMER_NAMES[args.roofline_kernel])
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    l0 = B.launch_count()
+    state["iters"].clear()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        one_step(q, quat)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    launches = B.launch_count() - l0
+    clk = clocks.stop()
+    kms, klaunch, kbytes = g.kernel_timer_read()
+    g.kernel_timer(0)
+    step_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    ms_per_step = step_ms / args.steps
+    value = world * args.steps / (step_ms / 1000.0)
+    # ----------------------------------------------------- end-to-end (host)
+    qh = torch.tensor(w.q.ravel(), dtype=torch.float64).pin_memory()
+    quath = torch.tensor(w.quat.ravel(), dtype=torch.float64).pin_memory()
+    qd = torch.empty_like(q)
+    quatd = torch.empty_like(quat)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        qd.copy_(qh, non_blocking=True)
+        quatd.copy_(quath, non_blocking=True)
+        one_step(qd, quatd)
+        qh.copy_(qd, non_blocking=True)
+        quath.copy_(quatd, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    nbytes = (qh.numel() + quath.numel()) * 8
+    e2e = {"value": world * args.steps / (e2e_ms / 1000.0), "unit": "SEM steps/s",
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    # ----------------------------------------------------------- roofline
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    achieved = (kbytes / max(klaunch, 1)) / ((kms / max(klaunch, 1)) * 1e-3) / 1e9 if klaunch else None
+    roofline = {"kernel": args.roofline_kernel, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
+                "launches": klaunch, "avg_launch_us": (1000.0 * kms / klaunch) if klaunch else None,
+                "alg_bytes_per_launch": (kbytes / klaunch) if klaunch else None}
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": "SEM steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(w),
+            "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+            "krylov_iterations_per_step": [list(map(int, np.mean(np.array(state["iters"]), axis=0)))] if state["iters"] else None,
+            "rejected_steps": state["rejects"], "wall_s": t_wall}
+    if world == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample(w, args.cpu_sample_rhs)
+        cb.pop("sample_seconds", None)
+        line["cpu_baseline"] = cb
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

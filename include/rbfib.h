@@ -179,6 +179,23 @@ int rbfib_interpolate(rbfib_grid* g, const double* v, double* u, int32_t with_wa
  * (device out N_b x 6). */
 int rbfib_body_forces(rbfib_grid* g, const rbfib_sem_params* p, double* out);
 
+/* ---- instrumentation --------------------------------------------------- */
+
+/* Number of kernel launches the library has issued so far (all grids). */
+uint64_t rbfib_launch_count(void);
+
+/* Kernel timer for roofline reports.  which: 0 off, 1 saddle matvec (Stokes
+ * stencil + body rows), 2 finest-level velocity smoothing sweep, 3 Krylov
+ * multi-column inner product, 4 Krylov multi-axpy.  While a class is
+ * selected, CUDA events are recorded on the grid's stream around each of its
+ * launches and the algorithmic bytes of each launch are added up (matvec:
+ * 2 n s + 24 N_bl + 56 N_b; smoothing sweep: 2 N_f s; inner product over k
+ * columns: (k + 1) n s; multi-axpy over k columns: (k + 2) n s; s = element
+ * size).  Selecting resets the counters.  _read synchronises the stream and
+ * returns the summed event time (ms), the launch count and the bytes. */
+int rbfib_kernel_timer(rbfib_grid* g, int32_t which);
+int rbfib_kernel_timer_read(rbfib_grid* g, double* total_ms, int64_t* launches, double* alg_bytes);
+
 #ifdef __cplusplus
 }
 #endif

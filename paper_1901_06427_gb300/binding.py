@@ -81,6 +81,9 @@ def lib():
             "rbfib_spread": ([P, P, P], I32),
             "rbfib_interpolate": ([P, P, P, I32], I32),
             "rbfib_body_forces": ([P, ctypes.POINTER(SemParams), P], I32),
+            "rbfib_launch_count": ([], U64),
+            "rbfib_kernel_timer": ([P, I32], I32),
+            "rbfib_kernel_timer_read": ([P, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D)], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -88,6 +91,13 @@ def lib():
             f.restype = res
         _lib = L
     return _lib
+
+
+TIMER_OFF, TIMER_MATVEC, TIMER_SMOOTH, TIMER_DOT, TIMER_AXPY = 0, 1, 2, 3, 4
+
+
+def launch_count():
+    return int(lib().rbfib_launch_count())
 
 
 def exported_symbols():
@@ -273,6 +283,14 @@ class Grid:
         self._check(lib().rbfib_interpolate(self._h, _ptr(v, numel=self.layout()[3], name="v"), _ptr(out),
                                             int(bool(with_walls))))
         return out[:3 * self.n_blobs]
+
+    def kernel_timer(self, which):
+        self._check(lib().rbfib_kernel_timer(self._h, int(which)))
+
+    def kernel_timer_read(self):
+        ms, n, b = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        self._check(lib().rbfib_kernel_timer_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
+        return ms.value, n.value, b.value
 
     def body_forces(self, params):
         out = torch.empty(6 * max(self.n_bodies, 1), dtype=torch.float64, device="cuda")

@@ -156,3 +156,9 @@ __device__ inline void philox_normals4(unsigned long long seed, unsigned long lo
 }
 
 #define RBFIB_DEVFN __device__ __forceinline__
+
+namespace rbfib {
+// Count of kernel launches issued by the library (host side, all grids).
+extern unsigned long long g_launches;
+inline void note_launch() { ++g_launches; }
+}  // namespace rbfib

@@ -35,7 +35,7 @@ __global__ void k_geometry(int nbl, const int* __restrict__ bob, const double* _
 
 void geometry(int nbl, const int* bob, const double* ref, const double* q, const double* quat,
               double* r, double* arm, cudaStream_t s) {
-  if (nbl > 0) k_geometry<<<nblk(nbl, 128), 128, 0, s>>>(nbl, bob, ref, q, quat, r, arm);
+  if (nbl > 0) { k_geometry<<<nblk(nbl, 128), 128, 0, s>>>(nbl, bob, ref, q, quat, r, arm); note_launch(); }
 }
 
 // -------------------------------------------------------------- binning
@@ -108,14 +108,19 @@ void binning(const Dims& d, int nbl, const double* r, int* perm, int* off, int* 
   const i64 n1 = d.nc + 1;
   cudaMemsetAsync(count, 0, sizeof(int) * n1, s);
   cudaMemsetAsync(fill, 0, sizeof(int) * d.nc, s);
-  if (nbl > 0) k_bin_keys<<<nblk(nbl, 128), 128, 0, s>>>(d, nbl, r, key, count);
+  if (nbl > 0) { k_bin_keys<<<nblk(nbl, 128), 128, 0, s>>>(d, nbl, r, key, count); note_launch(); }
   const int nb = (int)((n1 + 1023) / 1024);
   k_scan_blocks<<<nb, 1024, 0, s>>>(count, (int)n1, off, bsum);
+  note_launch();
   k_scan_sums<<<1, 32, 0, s>>>(bsum, nb);
+  note_launch();
   k_scan_add<<<nb, 1024, 0, s>>>(off, (int)n1, bsum);
+  note_launch();
   if (nbl > 0) {
     k_bin_scatter<<<nblk(nbl, 128), 128, 0, s>>>(nbl, key, off, fill, perm);
+    note_launch();
     k_bin_sort<<<nblk(d.nc, 256), 256, 0, s>>>(d.nc, off, perm);
+    note_launch();
   }
 }
 
@@ -219,7 +224,7 @@ __global__ void k_interp_res(Dims d, int nbl, const double* __restrict__ r, cons
 
 template <typename T>
 void interp_res(const Dims& d, int nbl, const double* r, const T* v, const T* rl, double* out, cudaStream_t s) {
-  if (nbl > 0) k_interp_res<T><<<nblk(3 * (i64)nbl, 128), 128, 0, s>>>(d, nbl, r, v, rl, out);
+  if (nbl > 0) { k_interp_res<T><<<nblk(3 * (i64)nbl, 128), 128, 0, s>>>(d, nbl, r, v, rl, out); note_launch(); }
 }
 
 // --------------------------------------------------- saddle body rows (fused)
@@ -302,18 +307,19 @@ void saddle_bodies(const Dims& d, const BodyView& b, const T* v, const T* lam, c
   const double inv_dV = 1.0 / (d.h[0] * d.h[1] * d.h[2]);
   k_saddle_bodies<T><<<nbA + nbB + nbC, bs, 0, s>>>(d, b.nbl, b.nb, b.perm, b.r, b.arm, b.bob, b.boff,
                                                    v, lam, U, yv, ylam, yU, nbA, nbB, inv_dV);
+                                                   note_launch();
 }
 
 template <typename T>
 void spread(const Dims& d, int nbl, const int* perm, const double* r, const T* lam, double scale, T* f,
             cudaStream_t s) {
-  if (nbl > 0) k_spread<T><<<nblk(3 * (i64)nbl, 128), 128, 0, s>>>(d, nbl, perm, r, lam, scale, f);
+  if (nbl > 0) { k_spread<T><<<nblk(3 * (i64)nbl, 128), 128, 0, s>>>(d, nbl, perm, r, lam, scale, f); note_launch(); }
 }
 
 template <typename T>
 void interp(const Dims& d, const Walls& wl, int nbl, const double* r, const T* v, double alpha,
             double beta, double gamma, T* out, cudaStream_t s) {
-  if (nbl > 0) k_interp<T><<<nblk(3 * (i64)nbl, 128), 128, 0, s>>>(d, wl, nbl, r, v, alpha, beta, gamma, out);
+  if (nbl > 0) { k_interp<T><<<nblk(3 * (i64)nbl, 128), 128, 0, s>>>(d, wl, nbl, r, v, alpha, beta, gamma, out); note_launch(); }
 }
 
 // K^T lam per body (FP64): out = alpha * K^T lam + beta * out
@@ -343,7 +349,7 @@ __global__ void k_kt(int nb, const int* __restrict__ boff, const double* __restr
 
 void kt_apply(int nb, const int* boff, const double* arm, const double* lam, double alpha, double beta,
               double* out, cudaStream_t s) {
-  if (nb > 0) k_kt<double><<<nblk(32 * (i64)nb, 128), 128, 0, s>>>(nb, boff, arm, lam, alpha, beta, out);
+  if (nb > 0) { k_kt<double><<<nblk(32 * (i64)nb, 128), 128, 0, s>>>(nb, boff, arm, lam, alpha, beta, out); note_launch(); }
 }
 
 // K U per blob: out = alpha * (u + w x arm) + beta * out
@@ -366,7 +372,7 @@ __global__ void k_k(int nbl, const int* __restrict__ bob, const double* __restri
 
 void k_apply(int nbl, const int* bob, const double* arm, const double* U, double alpha, double beta,
              double* out, cudaStream_t s) {
-  if (nbl > 0) k_k<<<nblk(3 * (i64)nbl, 128), 128, 0, s>>>(nbl, bob, arm, U, alpha, beta, out);
+  if (nbl > 0) { k_k<<<nblk(3 * (i64)nbl, 128), 128, 0, s>>>(nbl, bob, arm, U, alpha, beta, out); note_launch(); }
 }
 
 // ------------------------------------------------ body-block preconditioner
@@ -465,6 +471,7 @@ void body_precond(const BodyView& b, const PrecondView& pv, const double* sres, 
   const size_t shm = sizeof(double) * (2 * 3 * (size_t)pv.max_blobs + 12);
   k_body_precond<T><<<b.nb, 128, shm, s>>>(b.nb, b.boff, pv.shape_of, pv.minv_off, pv.minv, pv.nmat,
                                           pv.shape_ref_blob, b.ref, b.quat, sres, rU, zlam, zU);
+                                          note_launch();
 }
 
 // ------------------------------------------------------------------ forces
@@ -540,7 +547,7 @@ __global__ void k_forces(Dims d, Potentials P, int nb, const int* __restrict__ b
 
 void body_forces(const Dims& d, const Potentials& P, const BodyView& b, const double* fext, double* out,
                  cudaStream_t s) {
-  if (b.nb > 0) k_forces<<<nblk(b.nb, 64), 64, 0, s>>>(d, P, b.nb, b.boff, b.q, b.r, b.arm, fext, out);
+  if (b.nb > 0) { k_forces<<<nblk(b.nb, 64), 64, 0, s>>>(d, P, b.nb, b.boff, b.q, b.r, b.arm, fext, out); note_launch(); }
 }
 
 // ----------------------------------------------------------- SEM helpers
@@ -573,7 +580,7 @@ __global__ void k_wft(int nb, const double* __restrict__ wn, const double* __res
 }
 
 void wft(int nb, const double* wn, const double* Lp, double kT, double* out, cudaStream_t s) {
-  if (nb > 0) k_wft<<<nblk(6 * (i64)nb, 128), 128, 0, s>>>(nb, wn, Lp, kT, out);
+  if (nb > 0) { k_wft<<<nblk(6 * (i64)nb, 128), 128, 0, s>>>(nb, wn, Lp, kT, out); note_launch(); }
 }
 
 // q' = q + a * (scale_t L_p W^f)  or  q' = q + a * U_trans;  quat' = Rotate(quat, a * W^tau | a * w)
@@ -590,7 +597,7 @@ __global__ void k_move(int nb, const double* __restrict__ q, const double* __res
 
 void move_bodies(int nb, const double* q, const double* quat, const double* vec6, const double* Lp, double a,
                  double* qo, double* quato, cudaStream_t s) {
-  if (nb > 0) k_move<<<nblk(nb, 64), 64, 0, s>>>(nb, q, quat, vec6, Lp, a, qo, quato);
+  if (nb > 0) { k_move<<<nblk(nb, 64), 64, 0, s>>>(nb, q, quat, vec6, Lp, a, qo, quato); note_launch(); }
 }
 
 __global__ void k_outside(Dims d, int nbl, const double* __restrict__ r, int* __restrict__ flag) {
@@ -604,7 +611,7 @@ __global__ void k_outside(Dims d, int nbl, const double* __restrict__ r, int* __
 }
 
 void outside_check(const Dims& d, int nbl, const double* r, int* flag, cudaStream_t s) {
-  if (nbl > 0) k_outside<<<nblk(nbl, 128), 128, 0, s>>>(d, nbl, r, flag);
+  if (nbl > 0) { k_outside<<<nblk(nbl, 128), 128, 0, s>>>(d, nbl, r, flag); note_launch(); }
 }
 
 #define INST(T)                                                                                          \

@@ -57,7 +57,9 @@ void multi_dot(const T* w, const T* V, i64 ldv, int ncols, i64 n, i64 nfl, doubl
                double* out, cudaStream_t s) {
   dim3 grid(nparts, ncols);
   k_dot_part<T><<<grid, 256, 0, s>>>(w, V, ldv, n, nfl, wf, part);
+  note_launch();
   k_dot_finish<<<ncols, 256, 0, s>>>(part, nparts, out);
+  note_launch();
 }
 
 // w += sign * sum_c coef[c] V_c ; part[blockIdx.x] = partial ||w||_W^2
@@ -87,7 +89,8 @@ template <typename T>
 void multi_axpy(T* w, const T* V, i64 ldv, int ncols, const double* coef, double sign, i64 n, i64 nfl, double wf,
                 double* part, int nparts, double* nrm2, cudaStream_t s) {
   k_multi_axpy<T><<<nparts, 256, 0, s>>>(w, V, ldv, ncols, coef, sign, n, nfl, wf, nrm2 ? part : nullptr);
-  if (nrm2) k_dot_finish<<<1, 256, 0, s>>>(part, nparts, nrm2);
+  note_launch();
+  if (nrm2) { k_dot_finish<<<1, 256, 0, s>>>(part, nparts, nrm2); note_launch(); }
 }
 
 // mode 0: out = in * d[0]; mode 1: out = in / d[0]; mode 2: out = in / sqrt(d[0])
@@ -105,6 +108,7 @@ template <typename T>
 void scale_by(T* out, const T* in, const double* denom, int invert, i64 n, cudaStream_t s) {
   const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);
   k_scale<T><<<nb, 256, 0, s>>>(out, in, denom, invert, n);
+  note_launch();
 }
 
 // Hessenberg column j: H[0..j] = hcol (CGS2 sum), H[j+1] = sqrt(hnext2); apply
@@ -133,6 +137,7 @@ __global__ void k_givens(double* H, int ldh, double* cs, double* sn, double* g, 
 void givens_step(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                  const double* hcol2, const double* hnext2, double* res_out, cudaStream_t s) {
   k_givens<<<1, 32, 0, s>>>(H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, res_out);
+  note_launch();
 }
 
 // y = H[0:k,0:k]^{-1} g (upper triangular, column-major with leading dim ldh)
@@ -147,6 +152,7 @@ __global__ void k_tri(const double* H, int ldh, const double* g, int k, double* 
 
 void tri_solve(const double* H, int ldh, const double* g, int k, double* y, cudaStream_t s) {
   k_tri<<<1, 32, 0, s>>>(H, ldh, g, k, y);
+  note_launch();
 }
 
 template <typename A, typename B>
@@ -157,7 +163,7 @@ __global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, i64 n) 
 template <typename A, typename B>
 void convert(const A* in, B* out, i64 n, cudaStream_t s) {
   const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);
-  if (n > 0) k_convert<A, B><<<nb, 256, 0, s>>>(in, out, n);
+  if (n > 0) { k_convert<A, B><<<nb, 256, 0, s>>>(in, out, n); note_launch(); }
 }
 
 // y = a x + b y
@@ -172,7 +178,7 @@ __global__ void k_axpby(T* __restrict__ y, const T* __restrict__ x, double a, do
 template <typename T>
 void axpby(T* y, const T* x, double a, double b, i64 n, cudaStream_t s) {
   const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);
-  if (n > 0) k_axpby<T><<<nb, 256, 0, s>>>(y, x, a, b, n);
+  if (n > 0) { k_axpby<T><<<nb, 256, 0, s>>>(y, x, a, b, n); note_launch(); }
 }
 
 // x -= mean(x)  (two passes, deterministic)
@@ -189,8 +195,11 @@ __global__ void k_sum_part(const double* __restrict__ x, i64 n, double* part) {
 void project_mean(double* x, i64 n, double* part, int nparts, cudaStream_t s) {
   if (n == 0) return;
   k_sum_part<<<nparts, 256, 0, s>>>(x, n, part);
+  note_launch();
   k_dot_finish<<<1, 256, 0, s>>>(part, nparts, part + nparts);
+  note_launch();
   k_sub<<<nparts, 256, 0, s>>>(x, n, part + nparts);
+  note_launch();
 }
 
 // bv += eta * 2 u_w / h^2 on faces adjacent (along a tangential axis) to a moving wall
@@ -212,6 +221,7 @@ __global__ void k_wall_rhs(Dims d, Walls wl, double eta, T* __restrict__ bv) {
 template <typename T>
 void wall_rhs(const Dims& d, const Walls& wl, double eta, T* bv, cudaStream_t s) {
   k_wall_rhs<T><<<nblk(d.fo[3], 256), 256, 0, s>>>(d, wl, eta, bv);
+  note_launch();
 }
 
 #define INST(T)                                                                                              \

@@ -21,7 +21,7 @@ __global__ void k_philox_normals(unsigned long long seed, unsigned long long ste
 void philox_normals(unsigned long long seed, unsigned long long step, unsigned attempt, unsigned purpose,
                     i64 count, double* out, cudaStream_t s) {
   const i64 nb = (count + 3) / 4;
-  if (nb > 0) k_philox_normals<<<nblk(nb, 128), 128, 0, s>>>(seed, step, attempt, purpose, count, out);
+  if (nb > 0) { k_philox_normals<<<nblk(nb, 128), 128, 0, s>>>(seed, step, attempt, purpose, count, out); note_launch(); }
 }
 
 // out(face of component a) = c * [ (W_aa(right) - W_aa(left)) / h_a
@@ -56,6 +56,7 @@ __global__ void k_stress_div(Dims d, StressLayout L, const double* __restrict__ 
 
 void stress_divergence(const Dims& d, const StressLayout& L, const double* W, double c, double* out, cudaStream_t s) {
   k_stress_div<<<nblk(d.fo[3], 256), 256, 0, s>>>(d, L, W, c, out);
+  note_launch();
 }
 
 }  // namespace rbfib

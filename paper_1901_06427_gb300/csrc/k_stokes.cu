@@ -387,54 +387,67 @@ template <typename T>
 void stokes_apply(const Dims& d, T eta, const T* v, const T* p, T* yv, T* yp, cudaStream_t s) {
   const i64 n = d.fo[3] + d.nc;
   k_stokes_apply<T><<<nblk(n, 256), 256, 0, s>>>(d, eta, v, p, yv, yp);
+  note_launch();
 }
 template <typename T>
 void vel_rbgs(const Dims& d, T eta, int color, T* u, const T* rhs, cudaStream_t s) {
   k_vel_rbgs<T><<<nblk(d.fo[3], 256), 256, 0, s>>>(d, eta, color, u, rhs);
+  note_launch();
 }
 template <typename T>
 void vel_residual(const Dims& d, T eta, const T* u, const T* rhs, T* res, cudaStream_t s) {
   k_vel_residual<T><<<nblk(d.fo[3], 256), 256, 0, s>>>(d, eta, u, rhs, res);
+  note_launch();
 }
 template <typename T>
 void vel_restrict(const Dims& df, const Dims& dc, int3 cz, const T* rf, T* rc, cudaStream_t s) {
   k_vel_restrict<T><<<nblk(dc.fo[3], 256), 256, 0, s>>>(df, dc, cz, rf, rc);
+  note_launch();
 }
 template <typename T>
 void vel_prolong(const Dims& df, const Dims& dc, int3 cz, const T* uc, T* uf, cudaStream_t s) {
   k_vel_prolong<T><<<nblk(df.fo[3], 256), 256, 0, s>>>(df, dc, cz, uc, uf);
+  note_launch();
 }
 template <typename T>
 void vel_coarse(const Dims& d, T eta, T* u, const T* rhs, int sweeps, cudaStream_t s) {
   k_vel_coarse<T><<<1, 1024, 0, s>>>(d, eta, u, rhs, sweeps);
+  note_launch();
 }
 template <typename T>
 void p_rbgs(const Dims& d, int color, T* u, const T* rhs, cudaStream_t s) {
   k_p_rbgs<T><<<nblk(d.nc, 256), 256, 0, s>>>(d, color, u, rhs);
+  note_launch();
 }
 template <typename T>
 void p_residual(const Dims& d, const T* u, const T* rhs, T* res, cudaStream_t s) {
   k_p_residual<T><<<nblk(d.nc, 256), 256, 0, s>>>(d, u, rhs, res);
+  note_launch();
 }
 template <typename T>
 void p_restrict(const Dims& df, const Dims& dc, int3 cz, const T* rf, T* rc, cudaStream_t s) {
   k_p_restrict<T><<<nblk(dc.nc, 256), 256, 0, s>>>(df, dc, cz, rf, rc);
+  note_launch();
 }
 template <typename T>
 void p_prolong(const Dims& df, const Dims& dc, int3 cz, const T* uc, T* uf, cudaStream_t s) {
   k_p_prolong<T><<<nblk(df.nc, 256), 256, 0, s>>>(df, dc, cz, uc, uf);
+  note_launch();
 }
 template <typename T>
 void p_coarse(const Dims& d, T* u, T* rhs, int sweeps, cudaStream_t s) {
   k_p_coarse<T><<<1, 1024, 0, s>>>(d, u, rhs, sweeps);
+  note_launch();
 }
 template <typename T>
 void div_q(const Dims& d, T eta, const T* vt, const T* rpi, T* q, T* pi, cudaStream_t s) {
   k_div_q<T><<<nblk(d.nc, 256), 256, 0, s>>>(d, eta, vt, rpi, q, pi);
+  note_launch();
 }
 template <typename T>
 void add_grad(const Dims& d, const T* phi, T* v, cudaStream_t s) {
   k_add_grad<T><<<nblk(d.fo[3], 256), 256, 0, s>>>(d, phi, v);
+  note_launch();
 }
 
 #define INST(T)                                                                                  \

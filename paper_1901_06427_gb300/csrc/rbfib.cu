@@ -14,6 +14,8 @@
 
 using namespace rbfib;
 
+unsigned long long rbfib::g_launches = 0;
+
 namespace {
 
 const double kDeltaDefault = 6.0554544523933395e-06;   // eps^(1/3), eps = 2^-52
@@ -133,11 +135,45 @@ struct rbfib_grid {
   DBuf<float> f32a, f32b;
   DBuf<double> small;     // Hessenberg, rotations, g, y, dots
   int total_iters = 0;
+  // kernel timer (roofline reports): events around launches of one class
+  int timer_kind = 0;
+  std::vector<cudaEvent_t> tev;
+  size_t tev_used = 0;
+  double timer_bytes = 0.0;
+  int64_t timer_launches = 0;
 
   i64 n_total() const { return nfl + 3 * (i64)nbl + 6 * (i64)nb; }
 };
 
 namespace {
+
+// Records events around launches of the selected kernel class.
+struct TimerScope {
+  rbfib_grid* g;
+  bool on;
+  TimerScope(rbfib_grid* g_, int kind, double bytes) : g(g_), on(g_->timer_kind == kind) {
+    if (!on) return;
+    if (g->tev_used + 2 > g->tev.size()) {
+      if (g->tev.size() >= 400000) { on = false; return; }
+      for (int i = 0; i < 256; ++i) {
+        cudaEvent_t e;
+        ck(cudaEventCreate(&e));
+        g->tev.push_back(e);
+      }
+    }
+    ck(cudaEventRecord(g->tev[g->tev_used], g->s));
+    g->timer_bytes += bytes;
+    g->timer_launches += 1;
+  }
+  ~TimerScope() {
+    if (on) {
+      cudaEventRecord(g->tev[g->tev_used + 1], g->s);
+      g->tev_used += 2;
+    }
+  }
+};
+
+enum { TK_MATVEC = 1, TK_SMOOTH = 2, TK_DOT = 3, TK_AXPY = 4 };
 
 int fail(rbfib_grid* g, int code, const std::string& msg) {
   if (g) g->err = msg;
@@ -197,7 +233,7 @@ KrylovStore<float>& kr_of<float>(rbfib_grid* g) { return g->kr32; }
 
 const int kNu = 2;   // pre- and post-smoothing sweeps
 
-int coarse_sweeps(const Dims& d) { return 4 * std::max(d.n[0], std::max(d.n[1], d.n[2])) + 8; }
+int coarse_sweeps(const Dims& d) { return 2 * std::max(d.n[0], std::max(d.n[1], d.n[2])) + 4; }
 
 // u0 <- V-cycle approximation of (-eta LL)^{-1} rhs0 (zero initial guess)
 template <typename T>
@@ -209,10 +245,15 @@ void vcycle_vel(rbfib_grid* g, T* u0, const T* rhs0) {
   for (int l = 0; l < L; ++l) { u[l] = *M.vu[l]; rhs[l] = *M.vrhs[l]; }
   u[0] = u0;
   rhs[0] = const_cast<T*>(rhs0);
+  auto smooth = [&](int l, int color) {
+    const Dims& d = g->levels[l].d;
+    TimerScope ts(g, l == 0 ? TK_SMOOTH : -1, 2.0 * (double)d.fo[3] * sizeof(T));
+    vel_rbgs<T>(d, eta, color, u[l], rhs[l], g->s);
+  };
   for (int l = 0; l < L - 1; ++l) {
     const Dims& d = g->levels[l].d;
     ck(cudaMemsetAsync(u[l], 0, sizeof(T) * d.fo[3], g->s));
-    for (int s = 0; s < kNu; ++s) { vel_rbgs<T>(d, eta, 0, u[l], rhs[l], g->s); vel_rbgs<T>(d, eta, 1, u[l], rhs[l], g->s); }
+    for (int s = 0; s < kNu; ++s) { smooth(l, 0); smooth(l, 1); }
     vel_residual<T>(d, eta, u[l], rhs[l], *M.vres[l], g->s);
     vel_restrict<T>(d, g->levels[l + 1].d, g->levels[l].cz, *M.vres[l], rhs[l + 1], g->s);
   }
@@ -220,7 +261,7 @@ void vcycle_vel(rbfib_grid* g, T* u0, const T* rhs0) {
   for (int l = L - 2; l >= 0; --l) {
     const Dims& d = g->levels[l].d;
     vel_prolong<T>(d, g->levels[l + 1].d, g->levels[l].cz, u[l + 1], u[l], g->s);
-    for (int s = 0; s < kNu; ++s) { vel_rbgs<T>(d, eta, 1, u[l], rhs[l], g->s); vel_rbgs<T>(d, eta, 0, u[l], rhs[l], g->s); }
+    for (int s = 0; s < kNu; ++s) { smooth(l, 1); smooth(l, 0); }
   }
 }
 
@@ -277,9 +318,24 @@ void precond(rbfib_grid* g, const T* r, T* z, bool with_bodies) {
   }
 }
 
+// The preconditioner always runs in FP32: it only has to approximate A^{-1}
+// (FGMRES is flexible), and FP32 halves the bytes of every multigrid sweep and
+// avoids GB300's narrow FP64 pipe.  FP64 vectors are converted on the way in
+// and out.
+void precond_any(rbfib_grid* g, const double* r, double* z, bool with_bodies) {
+  const i64 n = with_bodies ? g->n_total() : g->nfl;
+  convert<double, float>(r, g->f32a, n, g->s);
+  precond<float>(g, g->f32a, g->f32b, with_bodies);
+  convert<float, double>(g->f32b, z, n, g->s);
+}
+void precond_any(rbfib_grid* g, const float* r, float* z, bool with_bodies) { precond<float>(g, r, z, with_bodies); }
+
 // y = A x (saddle operator; fluid-only when with_bodies is false)
 template <typename T>
 void apply_A(rbfib_grid* g, const T* x, T* y, bool with_bodies) {
+  const double nbytes = 2.0 * (double)(with_bodies ? g->n_total() : g->nfl) * sizeof(T) +
+                        (with_bodies ? 24.0 * g->nbl + 56.0 * g->nb : 0.0);
+  TimerScope ts(g, TK_MATVEC, nbytes);
   stokes_apply<T>(g->d, (T)g->desc.eta, x, x + g->nf, y, y + g->nf, g->s);
   if (with_bodies && g->nb > 0) {
     const T* xl = x + g->nfl;
@@ -332,12 +388,13 @@ int fgmres(rbfib_grid* g, const T* b, T* x, bool with_bodies, double rtol, int m
     for (int j = 0; j < m; ++j) {
       T* vj = V + (i64)j * ld;
       T* zj = Z + (i64)j * ld;
-      precond<T>(g, vj, zj, with_bodies);
+      precond_any(g, vj, zj, with_bodies);
       apply_A<T>(g, zj, w, with_bodies);
-      multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol, g->s);
-      multi_axpy<T>(w, V, ld, j + 1, sp.hcol, -1.0, n, nfl, wf, g->part, g->nparts, nullptr, g->s);
-      multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol2, g->s);
-      multi_axpy<T>(w, V, ld, j + 1, sp.hcol2, -1.0, n, nfl, wf, g->part, g->nparts, sp.nrm2, g->s);
+      const double bd = (double)(j + 2) * n * sizeof(T), ba = (double)(j + 3) * n * sizeof(T);
+      { TimerScope ts(g, TK_DOT, bd); multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol, g->s); }
+      { TimerScope ts(g, TK_AXPY, ba); multi_axpy<T>(w, V, ld, j + 1, sp.hcol, -1.0, n, nfl, wf, g->part, g->nparts, nullptr, g->s); }
+      { TimerScope ts(g, TK_DOT, bd); multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol2, g->s); }
+      { TimerScope ts(g, TK_AXPY, ba); multi_axpy<T>(w, V, ld, j + 1, sp.hcol2, -1.0, n, nfl, wf, g->part, g->nparts, sp.nrm2, g->s); }
       givens_step(sp.H, m + 1, sp.cs, sp.sn, sp.gv, j, sp.hcol, sp.hcol2, sp.nrm2, sp.res, g->s);
       scale_by<T>(V + (i64)(j + 1) * ld, w, sp.nrm2, 2, n, g->s);
       ++iters;
@@ -375,7 +432,7 @@ void build_levels(rbfib_grid* g) {
       cz[a] = (cur.d.n[a] % 2 == 0 && cur.d.n[a] >= 4) ? 1 : 0;
       any |= cz[a];
     }
-    if (!any || cur.d.nc <= 256) { cur.cz = make_int3(0, 0, 0); break; }
+    if (!any || cur.d.nc <= 64) { cur.cz = make_int3(0, 0, 0); break; }
     cur.cz = make_int3(cz[0], cz[1], cz[2]);
     int n2[3], per[3];
     double h2[3];
@@ -512,10 +569,10 @@ void alloc_solver(rbfib_grid* g) {
     if (g->kr64.n < n || g->kr64.m != m) g->kr64.build(m, n);
   } else {
     if (g->kr32.n < n || g->kr32.m != m) g->kr32.build(m, n);
-    g->f32a.ensure(n);
-    g->f32b.ensure(n);
     g->rres.ensure(n);
   }
+  g->f32a.ensure(n);
+  g->f32b.ensure(n);
   g->bvec.ensure(n); g->xvec.ensure(n); g->xrfd.ensure(n);
   // the FP32 refinement keeps an FP64 residual and correction
   g->blobA.ensure(std::max<i64>(3 * (i64)g->nbl, 1));
@@ -527,6 +584,41 @@ void alloc_solver(rbfib_grid* g) {
 extern "C" {
 
 const char* rbfib_last_error(const rbfib_grid* g) { return g ? g->err.c_str() : "null grid"; }
+
+uint64_t rbfib_launch_count(void) { return rbfib::g_launches; }
+
+int rbfib_kernel_timer(rbfib_grid* g, int32_t which) {
+  if (!g || which < 0 || which > 4) return RBFIB_EINVAL;
+  try {
+    ck(cudaStreamSynchronize(g->s));
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+  }
+  g->timer_kind = which;
+  g->tev_used = 0;
+  g->timer_bytes = 0.0;
+  g->timer_launches = 0;
+  return RBFIB_OK;
+}
+
+int rbfib_kernel_timer_read(rbfib_grid* g, double* total_ms, int64_t* launches, double* alg_bytes) {
+  if (!g) return RBFIB_EINVAL;
+  double tot = 0.0;
+  try {
+    ck(cudaStreamSynchronize(g->s));
+    for (size_t i = 0; i + 1 < g->tev_used; i += 2) {
+      float ms = 0.f;
+      ck(cudaEventElapsedTime(&ms, g->tev[i], g->tev[i + 1]));
+      tot += ms;
+    }
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+  }
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = g->timer_launches;
+  if (alg_bytes) *alg_bytes = g->timer_bytes;
+  return RBFIB_OK;
+}
 
 int rbfib_create_grid(const rbfib_grid_desc* desc, void* stream, rbfib_grid** out) {
   if (!desc || !out) return RBFIB_EINVAL;
@@ -557,8 +649,7 @@ int rbfib_create_grid(const rbfib_grid_desc* desc, void* stream, rbfib_grid** ou
     g->part.alloc((size_t)g->nparts * 130 + 8);
     g->small.alloc((size_t)(D.restart + 1) * D.restart + 4 * D.restart + 512);
     ck(cudaMallocHost((void**)&g->h_pinned, 64 * sizeof(double)));
-    if (D.precision == RBFIB_FP64) g->mg64.build(g->levels);
-    else { g->mg32.build(g->levels); g->mg64.build(g->levels); }
+    g->mg32.build(g->levels);
     g->bcount.alloc(g->nc + 1);
     g->bfill.alloc(g->nc);
     g->celloff.alloc(g->nc + 1);
@@ -583,6 +674,7 @@ int rbfib_create_grid(const rbfib_grid_desc* desc, void* stream, rbfib_grid** ou
 void rbfib_destroy(rbfib_grid* g) {
   if (!g) return;
   if (g->s) cudaStreamSynchronize(g->s);
+  for (cudaEvent_t e : g->tev) cudaEventDestroy(e);
   if (g->h_pinned) cudaFreeHost(g->h_pinned);
   delete g;
 }
