@@ -29,6 +29,7 @@
 #ifndef RBFIB_H
 #define RBFIB_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -178,6 +179,27 @@ int rbfib_interpolate(rbfib_grid* g, const double* v, double* u, int32_t with_wa
 /* Body forces and torques of the potentials in p at the current configuration
  * (device out N_b x 6). */
 int rbfib_body_forces(rbfib_grid* g, const rbfib_sem_params* p, double* out);
+
+/* Allocation-free variant of rbfib_stochastic_forcing, for callers that cannot
+ * allocate device memory: code running inside a custom allocator or memory
+ * pool (where a nested cudaMalloc would re-enter it), or applications that
+ * plan all of their device memory up front.  It needs no grid object: desc
+ * gives the grid (n, h, periodic, eta; other fields ignored).  It writes the
+ * same forcing as rbfib_stochastic_forcing (device out, N_f FP64) on the given
+ * stream and calls no cudaMalloc, cudaFree or allocating library routine.
+ *  - The stress field is drawn into a fixed device array of 2^20 doubles
+ *    (8 MiB) that is part of the library image; every device that loads the
+ *    library holds it until the process exits.  Grids whose stress field has
+ *    more values (about 9 per cell) are rejected with RBFIB_EINVAL.
+ *  - The first call on each device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - Every call shares the array and overwrites all of it that it uses; calls
+ *    that overlap on the GPU (other streams, other threads) race.
+ *  - errbuf (optional, errlen bytes) receives a one-line message.
+ * The paper has no counterpart to this entry point. */
+int rbfib_stochastic_forcing_static(const rbfib_grid_desc* desc, double kT, double dt, uint64_t seed,
+                                    uint64_t step, uint32_t attempt, double* out, void* cuda_stream,
+                                    char* errbuf, size_t errlen);
 
 /* ---- instrumentation --------------------------------------------------- */
 

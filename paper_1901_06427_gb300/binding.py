@@ -81,6 +81,8 @@ def lib():
             "rbfib_spread": ([P, P, P], I32),
             "rbfib_interpolate": ([P, P, P, I32], I32),
             "rbfib_body_forces": ([P, ctypes.POINTER(SemParams), P], I32),
+            "rbfib_stochastic_forcing_static": ([ctypes.POINTER(GridDesc), D, D, U64, U64, U32, P, P,
+                                                 ctypes.c_char_p, ctypes.c_size_t], I32),
             "rbfib_launch_count": ([], U64),
             "rbfib_kernel_timer": ([P, I32], I32),
             "rbfib_kernel_timer_read": ([P, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D)], I32),

@@ -60,3 +60,114 @@ void stress_divergence(const Dims& d, const StressLayout& L, const double* W, do
 }
 
 }  // namespace rbfib
+
+// ===================================================== allocation-free variant
+// rbfib_stochastic_forcing_static: the same fluid forcing as
+// rbfib_stochastic_forcing, for callers that cannot allocate device memory
+// (for instance code running inside a memory pool or an allocator hook that
+// must not re-enter cudaMalloc, or embedded hosts that pre-plan all memory).
+// The stress field is drawn into a fixed array that is part of the library's
+// device image, so the call itself allocates nothing.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include "../../include/rbfib.h"
+
+namespace {
+
+constexpr long long kStaticStressMax = 1LL << 20;   // doubles (8 MiB per device)
+constexpr int kMaxDevices = 64;
+
+// Every device that loads the library holds this array until the process exits.
+static __device__ __align__(256) double g_static_stress[kStaticStressMax];
+
+std::mutex g_static_mu;
+double* g_static_ptr[kMaxDevices] = {};
+
+void set_msg(char* buf, size_t len, const char* msg) {
+  if (buf && len) {
+    std::strncpy(buf, msg, len - 1);
+    buf[len - 1] = '\0';
+  }
+}
+
+}  // namespace
+
+extern "C" int rbfib_stochastic_forcing_static(const rbfib_grid_desc* desc, double kT, double dt, uint64_t seed,
+                                               uint64_t step, uint32_t attempt, double* out, void* cuda_stream,
+                                               char* errbuf, size_t errlen) {
+  using namespace rbfib;
+  if (!desc || !out || !(dt > 0) || !(kT >= 0) || !(desc->h > 0) || !(desc->eta > 0)) {
+    set_msg(errbuf, errlen, "stochastic_forcing_static: bad argument");
+    return RBFIB_EINVAL;
+  }
+  int per[3], n[3];
+  for (int a = 0; a < 3; ++a) {
+    n[a] = desc->n[a];
+    per[a] = desc->periodic[a] ? 1 : 0;
+    if (n[a] < 2) { set_msg(errbuf, errlen, "stochastic_forcing_static: n < 2"); return RBFIB_EINVAL; }
+  }
+  if (per[0] && per[1] && per[2]) {
+    set_msg(errbuf, errlen, "stochastic_forcing_static: every axis periodic");
+    return RBFIB_EINVAL;
+  }
+  const double h3[3] = {desc->h, desc->h, desc->h};
+  const Dims d = make_dims(n, per, h3);
+  // stress layout: for a = x,y,z: W_aa (cells), then W_ab for b != a in increasing order
+  StressLayout L;
+  long long off = 0;
+  for (int a = 0; a < 3; ++a) {
+    int order[3] = {a, a == 0 ? 1 : 0, a == 2 ? 1 : 2};
+    for (int t = 0; t < 3; ++t) {
+      const int b = order[t];
+      int* e = L.ext[a][b];
+      for (int ax = 0; ax < 3; ++ax) e[ax] = d.n[ax];
+      if (b != a) {
+        e[a] = d.fe[a][a];
+        e[b] = d.per[b] ? d.n[b] : d.n[b] + 1;
+      }
+      L.off[a][b] = off;
+      off += (long long)e[0] * e[1] * e[2];
+    }
+  }
+  L.total = off;
+  if (L.total > kStaticStressMax) {
+    char msg[200];
+    std::snprintf(msg, sizeof msg,
+                  "stochastic_forcing_static: stress field of %lld values exceeds the static scratch of %lld",
+                  (long long)L.total, (long long)kStaticStressMax);
+    set_msg(errbuf, errlen, msg);
+    return RBFIB_EINVAL;
+  }
+  // set-up once per device, with that device current
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    set_msg(errbuf, errlen, "stochastic_forcing_static: no usable current device");
+    return RBFIB_ECUDA;
+  }
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_static_stress);
+      if (e != cudaSuccess || !p) {
+        set_msg(errbuf, errlen, "stochastic_forcing_static: cudaGetSymbolAddress failed");
+        return RBFIB_ECUDA;
+      }
+      g_static_ptr[dev] = (double*)p;
+    }
+    scratch = g_static_ptr[dev];
+  }
+  const cudaStream_t s = (cudaStream_t)cuda_stream;
+  philox_normals(seed, step, attempt, 1u, L.total, scratch, s);
+  stress_divergence(d, L, scratch, std::sqrt(2.0 * desc->eta * kT / (d.h[0] * d.h[1] * d.h[2] * dt)), out, s);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_msg(errbuf, errlen, cudaGetErrorString(e));
+    return RBFIB_ECUDA;
+  }
+  set_msg(errbuf, errlen, "");
+  return RBFIB_OK;
+}
