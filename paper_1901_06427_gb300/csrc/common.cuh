@@ -15,7 +15,16 @@ struct Dims {
   int fe[3][3];      // fe[a][ax]: extent of component a's unknown faces along ax
   i64 fo[4];         // offsets of the three face blocks; fo[3] = N_f
   i64 nc;            // N_c
+  double ih[3], ih2[3];   // 1/h, 1/h^2 per axis (precomputed: no divisions in kernels)
+  float ihf[3], ih2f[3];
 };
+
+template <typename T> __host__ __device__ inline T inv_h(const Dims& d, int ax);
+template <> __host__ __device__ inline double inv_h<double>(const Dims& d, int ax) { return d.ih[ax]; }
+template <> __host__ __device__ inline float inv_h<float>(const Dims& d, int ax) { return d.ihf[ax]; }
+template <typename T> __host__ __device__ inline T inv_h2(const Dims& d, int ax);
+template <> __host__ __device__ inline double inv_h2<double>(const Dims& d, int ax) { return d.ih2[ax]; }
+template <> __host__ __device__ inline float inv_h2<float>(const Dims& d, int ax) { return d.ih2f[ax]; }
 
 inline Dims make_dims(const int n[3], const int per[3], const double h[3]) {
   Dims d;
@@ -29,6 +38,12 @@ inline Dims make_dims(const int n[3], const int per[3], const double h[3]) {
   }
   d.fo[3] = off;
   d.nc = (i64)n[0] * n[1] * n[2];
+  for (int a = 0; a < 3; ++a) {
+    d.ih[a] = 1.0 / h[a];
+    d.ih2[a] = 1.0 / (h[a] * h[a]);
+    d.ihf[a] = (float)d.ih[a];
+    d.ih2f[a] = (float)d.ih2[a];
+  }
   return d;
 }
 
@@ -36,23 +51,80 @@ __host__ __device__ inline i64 flat3(const int e[3], int i, int j, int k) {
   return (i64)i + (i64)e[0] * ((i64)j + (i64)e[1] * k);
 }
 
-// Decode a global face index into (component, i, j, k).
+// Decode a global face index into (component, i, j, k).  Grids are limited
+// to fewer than 2^31 unknowns, so the index arithmetic is 32-bit.
 __device__ inline void decode_face(const Dims& d, i64 f, int& a, int c[3]) {
   a = (f >= d.fo[1]) + (f >= d.fo[2]);
-  i64 l = f - d.fo[a];
-  const int e0 = d.fe[a][0], e1 = d.fe[a][1];
-  c[0] = (int)(l % e0);
-  i64 t = l / e0;
-  c[1] = (int)(t % e1);
+  const unsigned l = (unsigned)(f - d.fo[a]);
+  const unsigned e0 = d.fe[a][0], e1 = d.fe[a][1];
+  const unsigned t = l / e0;
+  c[0] = (int)(l - t * e0);
   c[2] = (int)(t / e1);
+  c[1] = (int)(t - (unsigned)c[2] * e1);
 }
 
-__device__ inline void decode_cell(const Dims& d, i64 l, int c[3]) {
-  c[0] = (int)(l % d.n[0]);
-  i64 t = l / d.n[0];
-  c[1] = (int)(t % d.n[1]);
-  c[2] = (int)(t / d.n[1]);
+__device__ inline void decode_cell(const Dims& d, i64 l64, int c[3]) {
+  const unsigned l = (unsigned)l64;
+  const unsigned e0 = d.n[0], e1 = d.n[1];
+  const unsigned t = l / e0;
+  c[0] = (int)(l - t * e0);
+  c[2] = (int)(t / e1);
+  c[1] = (int)(t - (unsigned)c[2] * e1);
 }
+
+// Points of one red-black colour ((i + j + k) % 2 == color) of the three face
+// grids: thread t -> component, row (j, k) and i.  Returns false for the
+// padding thread of an odd-length row.
+struct ColorMap { unsigned cnt[3]; unsigned hx[3]; };
+
+inline ColorMap make_color_map_faces(const Dims& d) {
+  ColorMap m;
+  for (int a = 0; a < 3; ++a) {
+    m.hx[a] = (unsigned)(d.fe[a][0] + 1) / 2;
+    m.cnt[a] = m.hx[a] * (unsigned)d.fe[a][1] * (unsigned)d.fe[a][2];
+  }
+  return m;
+}
+inline ColorMap make_color_map_cells(const Dims& d) {
+  ColorMap m;
+  m.hx[0] = (unsigned)(d.n[0] + 1) / 2;
+  m.cnt[0] = m.hx[0] * (unsigned)d.n[1] * (unsigned)d.n[2];
+  m.cnt[1] = m.cnt[2] = 0; m.hx[1] = m.hx[2] = 1;
+  return m;
+}
+
+__device__ inline bool color_face(const Dims& d, const ColorMap& m, unsigned t, int color, int& a, int c[3]) {
+  a = 0;
+  if (t >= m.cnt[0]) { t -= m.cnt[0]; a = 1; if (t >= m.cnt[1]) { t -= m.cnt[1]; a = 2; } }
+  if (t >= m.cnt[a]) return false;
+  const unsigned hx = m.hx[a], e1 = d.fe[a][1];
+  const unsigned row = t / hx;
+  const unsigned mm = t - row * hx;
+  c[2] = (int)(row / e1);
+  c[1] = (int)(row - (unsigned)c[2] * e1);
+  c[0] = (int)(2 * mm + ((c[1] + c[2] + color) & 1));
+  return c[0] < d.fe[a][0];
+}
+
+__device__ inline bool color_cell(const Dims& d, const ColorMap& m, unsigned t, int color, int c[3]) {
+  if (t >= m.cnt[0]) return false;
+  const unsigned hx = m.hx[0], e1 = d.n[1];
+  const unsigned row = t / hx;
+  const unsigned mm = t - row * hx;
+  c[2] = (int)(row / e1);
+  c[1] = (int)(row - (unsigned)c[2] * e1);
+  c[0] = (int)(2 * mm + ((c[1] + c[2] + color) & 1));
+  return c[0] < d.n[0];
+}
+
+// Per-configuration kernel stencil of one blob and velocity component:
+// indices along x, y, z (3 each) and the folded weights (sign included, zero
+// for dropped points).
+template <typename W>
+struct BlobStencil {
+  int idx[9];
+  W w[9];
+};
 
 // Three-point Peskin kernel: the unique phi on |r| < 3/2 with partition of
 // unity, zero first moment and sum of squares 1/2.

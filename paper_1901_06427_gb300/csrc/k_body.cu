@@ -1,0 +1,216 @@
+// Coupled body block of the preconditioner for suspensions with few blobs:
+// the Schur complement [-M K; K^T 0] of the saddle operator with the blob
+// mobility M replaced by the free-space Rotne-Prager-Yamakawa mobility of all
+// blobs of all bodies (inter-body coupling included).  Built once per
+// configuration: dense RPY matrix, in-place Gauss-Jordan inverse (FP32, no
+// pivoting: the RPY matrix is symmetric positive definite), P = M^-1 K,
+// N = (K^T M^-1 K)^-1 (FP64).  Applied by one CTA.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rbfib {
+
+static inline unsigned nblk(i64 n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+__global__ void k_rpy_full(int nbl, const double* __restrict__ r, double a, double eta, float* __restrict__ M) {
+  const i64 n3 = 3 * (i64)nbl;
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n3 * n3) return;
+  const int row = (int)(t / n3), col = (int)(t - (i64)row * n3);
+  const int i = row / 3, p = row % 3, j = col / 3, q = col % 3;
+  const double c0 = 1.0 / (6.0 * M_PI * eta * a);
+  double v;
+  if (i == j) {
+    v = (p == q) ? c0 : 0.0;
+  } else {
+    const double d[3] = {r[3 * i] - r[3 * j], r[3 * i + 1] - r[3 * j + 1], r[3 * i + 2] - r[3 * j + 2]};
+    const double rr2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double rr = sqrt(rr2);
+    double fI, fR;
+    if (rr >= 2.0 * a) {
+      const double c = 1.0 / (8.0 * M_PI * eta * rr);
+      fI = c * (1.0 + 2.0 * a * a / (3.0 * rr2));
+      fR = c * (1.0 - 2.0 * a * a / rr2);
+    } else {
+      fI = c0 * (1.0 - 9.0 * rr / (32.0 * a));
+      fR = c0 * (3.0 * rr / (32.0 * a));
+    }
+    v = (p == q ? fI : 0.0) + fR * d[p] * d[q] / rr2;
+  }
+  M[t] = (float)v;
+}
+
+// In-place Gauss-Jordan inverse of an n x n matrix by one block.  status is
+// set to 1 on a zero pivot.
+template <typename R>
+__global__ void k_gj_inverse(R* __restrict__ A, int n, int* __restrict__ status) {
+  extern __shared__ unsigned char shraw[];
+  R* col = (R*)shraw;
+  for (int k = 0; k < n; ++k) {
+    __syncthreads();
+    const R p = A[(i64)k * n + k];
+    if (!(p > R(0) || p < R(0))) {
+      if (threadIdx.x == 0) *status = 1;
+      return;
+    }
+    const R ip = R(1) / p;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = A[(i64)i * n + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) A[(i64)k * n + j] = (j == k) ? ip : A[(i64)k * n + j] * ip;
+    __syncthreads();
+    const i64 nn = (i64)n * n;
+    for (i64 t = threadIdx.x; t < nn; t += blockDim.x) {
+      const int i = (int)(t / n), j = (int)(t - (i64)i * n);
+      if (i == k) continue;
+      const R f = col[i];
+      if (j == k) A[t] = -f * ip;
+      else A[t] -= f * A[(i64)k * n + j];
+    }
+  }
+}
+
+// P = M^-1 K (n3 x 6 nb): column (p, c) of K is nonzero on the blobs of body p
+// only: identity for c < 3, w x arm for c >= 3.
+__global__ void k_mk(int nbl, int nb, const int* __restrict__ boff, const double* __restrict__ arm,
+                     const float* __restrict__ Mi, float* __restrict__ P) {
+  const i64 n3 = 3 * (i64)nbl, m = 6 * (i64)nb;
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n3 * m) return;
+  const int row = (int)(t / m), col = (int)(t - (i64)row * m);
+  const int p = col / 6, c = col % 6;
+  double acc = 0.0;
+  for (int i = boff[p]; i < boff[p + 1]; ++i) {
+    const float* Mr = Mi + (i64)row * n3 + 3 * i;
+    if (c < 3) {
+      acc += Mr[c];
+    } else {
+      // (w x arm) for w = e_{c-3}: e_x x d = (0, -dz, dy), e_y x d = (dz, 0, -dx), e_z x d = (-dy, dx, 0)
+      const double* d = arm + 3 * i;
+      double k0, k1, k2;
+      if (c == 3) { k0 = 0; k1 = -d[2]; k2 = d[1]; }
+      else if (c == 4) { k0 = d[2]; k1 = 0; k2 = -d[0]; }
+      else { k0 = -d[1]; k1 = d[0]; k2 = 0; }
+      acc += Mr[0] * k0 + Mr[1] * k1 + Mr[2] * k2;
+    }
+  }
+  P[t] = (float)acc;
+}
+
+// A = K^T P (6 nb x 6 nb, FP64)
+__global__ void k_ktp(int nbl, int nb, const int* __restrict__ boff, const double* __restrict__ arm,
+                      const float* __restrict__ P, double* __restrict__ A) {
+  const int m = 6 * nb;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * m) return;
+  const int row = t / m, col = t - row * m;
+  const int p = row / 6, c = row % 6;
+  double acc = 0.0;
+  for (int i = boff[p]; i < boff[p + 1]; ++i) {
+    const double x = P[(i64)(3 * i) * m + col], y = P[(i64)(3 * i + 1) * m + col], z = P[(i64)(3 * i + 2) * m + col];
+    const double* d = arm + 3 * i;
+    if (c == 0) acc += x;
+    else if (c == 1) acc += y;
+    else if (c == 2) acc += z;
+    else if (c == 3) acc += d[1] * z - d[2] * y;
+    else if (c == 4) acc += d[2] * x - d[0] * z;
+    else acc += d[0] * y - d[1] * x;
+  }
+  A[t] = acc;
+}
+
+// Build: M (float n3^2) -> M^-1, P, N (double (6nb)^2).  scratch: P (n3 x 6nb
+// floats), status word.
+void dense_body_build(int nbl, int nb, const int* boff, const double* r, const double* arm, double a, double eta,
+                      float* Minv, float* P, double* N, int* status, cudaStream_t s) {
+  const i64 n3 = 3 * (i64)nbl, m = 6 * (i64)nb;
+  cudaMemsetAsync(status, 0, sizeof(int), s);
+  k_rpy_full<<<nblk(n3 * n3, 256), 256, 0, s>>>(nbl, r, a, eta, Minv);
+  note_launch();
+  k_gj_inverse<float><<<1, 1024, sizeof(float) * n3, s>>>(Minv, (int)n3, status);
+  note_launch();
+  k_mk<<<nblk(n3 * m, 256), 256, 0, s>>>(nbl, nb, boff, arm, Minv, P);
+  note_launch();
+  k_ktp<<<nblk(m * m, 256), 256, 0, s>>>(nbl, nb, boff, arm, P, N);
+  note_launch();
+  k_gj_inverse<double><<<1, 1024, sizeof(double) * m, s>>>(N, (int)m, status);
+  note_launch();
+}
+
+// Apply (one block): t = M^-1 s; f = r_U + K^T t; U = N f; y = K U - s;
+// lam = M^-1 y.  s, r_U in, lam, U out (type T; internal FP32 / FP64).
+template <typename T>
+__global__ void k_dense_body_apply(int nbl, int nb, const int* __restrict__ boff, const int* __restrict__ bob,
+                                   const double* __restrict__ arm, const float* __restrict__ Mi,
+                                   const double* __restrict__ N, const T* __restrict__ sres, const T* __restrict__ rU,
+                                   T* __restrict__ zlam, T* __restrict__ zU) {
+  extern __shared__ unsigned char shraw[];
+  const int n3 = 3 * nbl, m = 6 * nb;
+  double* f = (double*)shraw;          // m
+  double* U = f + m;                   // m
+  float* tv = (float*)(U + m);         // n3
+  float* sv = tv + n3;                 // n3
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < n3; i += blockDim.x) sv[i] = (float)sres[i];
+  __syncthreads();
+  for (int row = wid; row < n3; row += nw) {
+    float acc = 0.f;
+    for (int c = lane; c < n3; c += 32) acc += Mi[(i64)row * n3 + c] * sv[c];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) tv[row] = acc;
+  }
+  __syncthreads();
+  for (int p = wid; p < nb; p += nw) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = boff[p] + lane; i < boff[p + 1]; i += 32) {
+      const double x = tv[3 * i], y = tv[3 * i + 1], z = tv[3 * i + 2];
+      const double* d = arm + 3 * i;
+      acc[0] += x; acc[1] += y; acc[2] += z;
+      acc[3] += d[1] * z - d[2] * y;
+      acc[4] += d[2] * x - d[0] * z;
+      acc[5] += d[0] * y - d[1] * x;
+    }
+    for (int c = 0; c < 6; ++c)
+      for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    if (lane < 6) f[6 * p + lane] = acc[lane] + (double)rU[6 * p + lane];
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    double acc = 0.0;
+    for (int c = 0; c < m; ++c) acc += N[(i64)r * m + c] * f[c];
+    U[r] = acc;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+    const int i = t / 3, a = t - 3 * i, p = bob[i];
+    const double* d = arm + 3 * i;
+    const double* Up = U + 6 * p;
+    double cr;
+    if (a == 0) cr = Up[4] * d[2] - Up[5] * d[1];
+    else if (a == 1) cr = Up[5] * d[0] - Up[3] * d[2];
+    else cr = Up[3] * d[1] - Up[4] * d[0];
+    tv[t] = (float)(Up[a] + cr) - sv[t];
+  }
+  __syncthreads();
+  for (int row = wid; row < n3; row += nw) {
+    float acc = 0.f;
+    for (int c = lane; c < n3; c += 32) acc += Mi[(i64)row * n3 + c] * tv[c];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) zlam[row] = (T)acc;
+  }
+  for (int r = threadIdx.x; r < m; r += blockDim.x) zU[r] = (T)U[r];
+}
+
+template <typename T>
+void dense_body_apply(int nbl, int nb, const int* boff, const int* bob, const double* arm, const float* Minv,
+                      const double* N, const T* sres, const T* rU, T* zlam, T* zU, cudaStream_t s) {
+  const size_t shm = sizeof(double) * 12 * (size_t)nb + sizeof(float) * 6 * (size_t)nbl;
+  k_dense_body_apply<T><<<1, 1024, shm, s>>>(nbl, nb, boff, bob, arm, Minv, N, sres, rU, zlam, zU);
+  note_launch();
+}
+
+template void dense_body_apply<float>(int, int, const int*, const int*, const double*, const float*, const double*,
+                                      const float*, const float*, float*, float*, cudaStream_t);
+template void dense_body_apply<double>(int, int, const int*, const int*, const double*, const float*, const double*,
+                                       const double*, const double*, double*, double*, cudaStream_t);
+
+}  // namespace rbfib

@@ -209,90 +209,171 @@ __global__ void k_interp(Dims d, Walls wl, int nbl, const double* __restrict__ r
   out[t] = (T)o;
 }
 
-// out = r_lam + J v   (FP64 output, used by the body-block preconditioner)
-template <typename T>
-__global__ void k_interp_res(Dims d, int nbl, const double* __restrict__ r, const T* __restrict__ v,
-                             const T* __restrict__ rl, double* __restrict__ out) {
+// -------------------------------------------- per-configuration stencil table
+// Folded kernel weights of every blob and component, computed once per
+// configuration (FP64 for the FP64 operators, FP32 for the preconditioner and
+// the FP32 operators) so that every J / S application is a plain gather or
+// scatter.
+__global__ void k_stencil_build(Dims d, int nbl, const double* __restrict__ r, BlobStencil<double>* __restrict__ s64,
+                                BlobStencil<float>* __restrict__ s32) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * nbl) return;
   const int i = t / 3, a = t - 3 * i;
-  double jv, aff;
-  Walls w0 = {};
-  interp_one(d, w0, a, r + 3 * i, v, jv, aff);
-  out[t] = (double)rl[t] + jv;
+  BlobStencil<double> S;
+  BlobStencil<float> F;
+  for (int ax = 0; ax < 3; ++ax) {
+    AxisStencil A;
+    axis_stencil(d, a, ax, r[3 * i + ax], A);
+    for (int k = 0; k < 3; ++k) {
+      const double w = A.keep[k] ? A.w[k] * (double)A.sgn[k] : 0.0;
+      S.idx[3 * ax + k] = A.keep[k] ? A.idx[k] : 0;
+      S.w[3 * ax + k] = w;
+      F.idx[3 * ax + k] = S.idx[3 * ax + k];
+      F.w[3 * ax + k] = (float)w;
+    }
+  }
+  s64[t] = S;
+  s32[t] = F;
+}
+
+void stencil_build(const Dims& d, int nbl, const double* r, BlobStencil<double>* s64, BlobStencil<float>* s32,
+                   cudaStream_t s) {
+  if (nbl > 0) { k_stencil_build<<<nblk(3 * (i64)nbl, 128), 128, 0, s>>>(d, nbl, r, s64, s32); note_launch(); }
+}
+
+template <typename T> RBFIB_DEVFN const BlobStencil<T>* table_of(const BodyView& b);
+template <> RBFIB_DEVFN const BlobStencil<double>* table_of<double>(const BodyView& b) { return b.st64; }
+template <> RBFIB_DEVFN const BlobStencil<float>* table_of<float>(const BodyView& b) { return b.st32; }
+
+// (J v)_ia by one warp: lane l < 27 takes kernel point (l % 3, l / 3 % 3, l / 9).
+template <typename T>
+RBFIB_DEVFN T warp_interp(const Dims& d, int a, const BlobStencil<T>* __restrict__ S, const T* __restrict__ v,
+                          int lane) {
+  T val = T(0);
+  if (lane < 27) {
+    const int x = lane % 3, y = (lane / 3) % 3, z = lane / 9;
+    const T w = S->w[x] * S->w[3 + y] * S->w[6 + z];
+    if (w != T(0)) val = w * v[d.fo[a] + flat3(d.fe[a], S->idx[x], S->idx[3 + y], S->idx[6 + z])];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+  return val;
+}
+
+// f_a += val * w at the 27 kernel points, one atomic per lane.
+template <typename T>
+RBFIB_DEVFN void warp_spread(const Dims& d, int a, const BlobStencil<T>* __restrict__ S, T val, T* __restrict__ f,
+                             int lane) {
+  if (lane < 27 && val != T(0)) {
+    const int x = lane % 3, y = (lane / 3) % 3, z = lane / 9;
+    const T w = S->w[x] * S->w[3 + y] * S->w[6 + z];
+    if (w != T(0)) atomicAdd(f + d.fo[a] + flat3(d.fe[a], S->idx[x], S->idx[3 + y], S->idx[6 + z]), w * val);
+  }
+}
+
+// out = r_lam + J v  (body-block preconditioner input), warp per blob component
+template <typename T>
+__global__ void k_interp_res(Dims d, int nbl, const BlobStencil<T>* __restrict__ tab, const T* __restrict__ v,
+                             const T* __restrict__ rl, T* __restrict__ out) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (gw >= 3 * nbl) return;
+  const T jv = warp_interp<T>(d, gw % 3, tab + gw, v, lane);
+  if (lane == 0) out[gw] = rl[gw] + jv;
 }
 
 template <typename T>
-void interp_res(const Dims& d, int nbl, const double* r, const T* v, const T* rl, double* out, cudaStream_t s) {
-  if (nbl > 0) { k_interp_res<T><<<nblk(3 * (i64)nbl, 128), 128, 0, s>>>(d, nbl, r, v, rl, out); note_launch(); }
+void interp_res(const Dims& d, const BodyView& b, const T* v, const T* rl, T* out, cudaStream_t s) {
+  if (b.nbl > 0) {
+    const BlobStencil<T>* tab = nullptr;
+    if constexpr (sizeof(T) == 8) tab = (const BlobStencil<T>*)b.st64; else tab = (const BlobStencil<T>*)b.st32;
+    k_interp_res<T><<<nblk(32 * 3 * (i64)b.nbl, 128), 128, 0, s>>>(d, b.nbl, tab, v, rl, out);
+    note_launch();
+  }
+}
+
+// out = alpha * J v + beta * out with the configuration's table
+template <typename T>
+__global__ void k_interp_tab(Dims d, int nbl, const BlobStencil<T>* __restrict__ tab, const T* __restrict__ v,
+                             double alpha, double beta, T* __restrict__ out) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (gw >= 3 * nbl) return;
+  const T jv = warp_interp<T>(d, gw % 3, tab + gw, v, lane);
+  if (lane == 0) {
+    double o = alpha * (double)jv;
+    if (beta != 0.0) o += beta * (double)out[gw];
+    out[gw] = (T)o;
+  }
+}
+
+void interp_tab(const Dims& d, const BodyView& b, const double* v, double alpha, double beta, double* out,
+                cudaStream_t s) {
+  if (b.nbl > 0) {
+    k_interp_tab<double><<<nblk(32 * 3 * (i64)b.nbl, 128), 128, 0, s>>>(d, b.nbl, b.st64, v, alpha, beta, out);
+    note_launch();
+  }
+}
+
+// f += scale * S-like scatter of lam with the configuration's table (no 1/dV)
+__global__ void k_spread_tab(Dims d, int nbl, const int* __restrict__ perm, const BlobStencil<double>* __restrict__ tab,
+                             const double* __restrict__ lam, double scale, double* __restrict__ f) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (gw >= 3 * nbl) return;
+  const int s = gw / 3, a = gw - 3 * s;
+  const int i = perm ? perm[s] : s;
+  warp_spread<double>(d, a, tab + 3 * i + a, lam[3 * i + a] * scale, f, lane);
+}
+
+void spread_tab(const Dims& d, const BodyView& b, const double* lam, double scale, double* f, cudaStream_t s) {
+  if (b.nbl > 0) {
+    k_spread_tab<<<nblk(32 * 3 * (i64)b.nbl, 128), 128, 0, s>>>(d, b.nbl, b.perm, b.st64, lam, scale, f);
+    note_launch();
+  }
 }
 
 // --------------------------------------------------- saddle body rows (fused)
-// blocks [0, nbA): y_lam = -J v + K U          (thread per blob component)
-// blocks [nbA, nbA + nbB): y_U = K^T lam         (warp per body, FP64 sums)
-// blocks [nbA + nbB, ...): y_v -= S lam / dV     (thread per blob component)
+// warps [0, 3 N_bl): y_lam = -J v + K U            (warp per blob component)
+// warps [3 N_bl, 3 N_bl + N_b): y_U = K^T lam       (warp per body, FP64 sums)
+// warps beyond: y_v -= S lam / dV                  (warp per blob component, bin order)
 template <typename T>
-__global__ void k_saddle_bodies(Dims d, int nbl, int nb, const int* __restrict__ perm,
-                                const double* __restrict__ r, const double* __restrict__ arm,
-                                const int* __restrict__ bob, const int* __restrict__ boff,
-                                const T* __restrict__ v, const T* __restrict__ lam, const T* __restrict__ U,
-                                T* __restrict__ yv, T* __restrict__ ylam, T* __restrict__ yU,
-                                int nbA, int nbB, double inv_dV) {
-  const int blk = blockIdx.x;
-  if (blk < nbA) {
-    const int t = blk * blockDim.x + threadIdx.x;
-    if (t >= 3 * nbl) return;
-    const int i = t / 3, a = t - 3 * i;
-    double jv, aff;
-    Walls wl0 = {};
-    interp_one(d, wl0, a, r + 3 * i, v, jv, aff);
-    const int p = bob[i];
-    const double* ar = arm + 3 * i;
-    const double w0 = (double)U[6 * p + 3], w1 = (double)U[6 * p + 4], w2 = (double)U[6 * p + 5];
-    double cr;
-    if (a == 0) cr = w1 * ar[2] - w2 * ar[1];
-    else if (a == 1) cr = w2 * ar[0] - w0 * ar[2];
-    else cr = w0 * ar[1] - w1 * ar[0];
-    ylam[t] = (T)(-jv + ((double)U[6 * p + a] + cr));
-  } else if (blk < nbA + nbB) {
-    const int warp = ((blk - nbA) * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= nb) return;
+__global__ void k_saddle_bodies(Dims d, BodyView b, const T* __restrict__ v, const T* __restrict__ lam,
+                                const T* __restrict__ U, T* __restrict__ yv, T* __restrict__ ylam, T* __restrict__ yU,
+                                double inv_dV) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nA = 3 * b.nbl, nB = b.nb;
+  const BlobStencil<T>* tab = table_of<T>(b);
+  if (gw < nA) {
+    const int i = gw / 3, a = gw - 3 * i;
+    const T jv = warp_interp<T>(d, a, tab + gw, v, lane);
+    if (lane == 0) {
+      const int p = b.bob[i];
+      const double* ar = b.arm + 3 * i;
+      const double w0 = (double)U[6 * p + 3], w1 = (double)U[6 * p + 4], w2 = (double)U[6 * p + 5];
+      double cr;
+      if (a == 0) cr = w1 * ar[2] - w2 * ar[1];
+      else if (a == 1) cr = w2 * ar[0] - w0 * ar[2];
+      else cr = w0 * ar[1] - w1 * ar[0];
+      ylam[gw] = (T)(-(double)jv + ((double)U[6 * p + a] + cr));
+    }
+  } else if (gw < nA + nB) {
+    const int p = gw - nA;
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int i = boff[warp] + lane; i < boff[warp + 1]; i += 32) {
+    for (int i = b.boff[p] + lane; i < b.boff[p + 1]; i += 32) {
       const double lx = (double)lam[3 * i], ly = (double)lam[3 * i + 1], lz = (double)lam[3 * i + 2];
-      const double* ar = arm + 3 * i;
+      const double* ar = b.arm + 3 * i;
       acc[0] += lx; acc[1] += ly; acc[2] += lz;
       acc[3] += ar[1] * lz - ar[2] * ly;
       acc[4] += ar[2] * lx - ar[0] * lz;
       acc[5] += ar[0] * ly - ar[1] * lx;
     }
+#pragma unroll
     for (int c = 0; c < 6; ++c)
       for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-    if (lane < 6) yU[6 * warp + lane] = (T)acc[lane];
-  } else {
-    const int t = (blk - nbA - nbB) * blockDim.x + threadIdx.x;
-    if (t >= 3 * nbl) return;
-    const int s = t / 3, a = t - 3 * s;
-    const int i = perm ? perm[s] : s;
-    const double val = -(double)lam[3 * i + a] * inv_dV;
-    if (val == 0.0) return;
-    Stencil27 S;
-    load_stencil(d, a, r + 3 * i, S);
-    T* fa = yv + d.fo[a];
-    for (int z = 0; z < 3; ++z) {
-      if (!S.ax[2].keep[z]) continue;
-      const double wz = S.ax[2].w[z] * S.ax[2].sgn[z];
-      for (int y = 0; y < 3; ++y) {
-        if (!S.ax[1].keep[y]) continue;
-        const double wyz = wz * S.ax[1].w[y] * S.ax[1].sgn[y];
-        for (int x = 0; x < 3; ++x) {
-          if (!S.ax[0].keep[x]) continue;
-          const double w = wyz * S.ax[0].w[x] * S.ax[0].sgn[x];
-          atomicAdd(fa + flat3(d.fe[a], S.ax[0].idx[x], S.ax[1].idx[y], S.ax[2].idx[z]), (T)(w * val));
-        }
-      }
-    }
+    if (lane < 6) yU[6 * p + lane] = (T)acc[lane];
+  } else if (gw < 2 * nA + nB) {
+    const int s = gw - nA - nB;
+    const int sb = s / 3, a = s - 3 * sb;
+    const int i = b.perm ? b.perm[sb] : sb;
+    warp_spread<T>(d, a, tab + 3 * i + a, (T)(-(double)lam[3 * i + a] * inv_dV), yv, lane);
   }
 }
 
@@ -300,14 +381,10 @@ template <typename T>
 void saddle_bodies(const Dims& d, const BodyView& b, const T* v, const T* lam, const T* U,
                    T* yv, T* ylam, T* yU, cudaStream_t s) {
   if (b.nbl == 0) return;
-  const int bs = 128;
-  const int nbA = (int)nblk(3 * (i64)b.nbl, bs);
-  const int nbB = (int)nblk(32 * (i64)b.nb, bs);
-  const int nbC = nbA;
+  const i64 warps = 2 * 3 * (i64)b.nbl + b.nb;
   const double inv_dV = 1.0 / (d.h[0] * d.h[1] * d.h[2]);
-  k_saddle_bodies<T><<<nbA + nbB + nbC, bs, 0, s>>>(d, b.nbl, b.nb, b.perm, b.r, b.arm, b.bob, b.boff,
-                                                   v, lam, U, yv, ylam, yU, nbA, nbB, inv_dV);
-                                                   note_launch();
+  k_saddle_bodies<T><<<nblk(32 * warps, 128), 128, 0, s>>>(d, b, v, lam, U, yv, ylam, yU, inv_dV);
+  note_launch();
 }
 
 template <typename T>
@@ -385,45 +462,50 @@ void k_apply(int nbl, const int* bob, const double* arm, const double* U, double
 // (K_s^T M_s^-1 K_s)^-1; both precomputed on the host.
 template <typename T>
 __global__ void k_body_precond(int nb, const int* __restrict__ boff, const int* __restrict__ shape_of,
-                               const i64* __restrict__ shape_minv_off, const double* __restrict__ minv,
+                               const i64* __restrict__ shape_minv_off, const T* __restrict__ minv,
                                const double* __restrict__ nmat, const int* __restrict__ shape_ref_blob,
                                const double* __restrict__ ref, const double* __restrict__ quat,
-                               const double* __restrict__ sres, const T* __restrict__ rU,
+                               const T* __restrict__ sres, const T* __restrict__ rU,
                                T* __restrict__ zlam, T* __restrict__ zU) {
-  extern __shared__ double sh[];
+  extern __shared__ unsigned char shraw[];
+  T* sh = (T*)shraw;
   const int p = blockIdx.x;
   if (p >= nb) return;
   const int b0 = boff[p], nbp = boff[p + 1] - b0;
   const int n3 = 3 * nbp;
   const int s = shape_of[p];
-  const double* Mi = minv + shape_minv_off[s];
+  const T* Mi = minv + shape_minv_off[s];
   const double* Ns = nmat + 36 * s;
   const double* rf = ref + 3 * shape_ref_blob[s];
-  double* sp = sh;            // n3: s'
-  double* tp = sh + n3;       // n3: M^-1 s', later K U' - s'
-  double* w6 = sh + 2 * n3;   // 6 (+6 scratch)
+  T* sp = sh;            // n3: s'
+  T* tp = sh + n3;       // n3: M^-1 s', later K U' - s'
+  __shared__ double w6[6];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double R[9];
   quat_rot(quat + 4 * p, R);
   for (int i = threadIdx.x; i < nbp; i += blockDim.x) {
-    const double* x = sres + 3 * (b0 + i);
-    for (int a = 0; a < 3; ++a) sp[3 * i + a] = R[a] * x[0] + R[3 + a] * x[1] + R[6 + a] * x[2];
+    const T* x = sres + 3 * (b0 + i);
+    for (int a = 0; a < 3; ++a)
+      sp[3 * i + a] = (T)(R[a] * (double)x[0] + R[3 + a] * (double)x[1] + R[6 + a] * (double)x[2]);
   }
   __syncthreads();
-  for (int row = threadIdx.x; row < n3; row += blockDim.x) {
-    double acc = 0.0;
-    for (int c = 0; c < n3; ++c) acc += Mi[(i64)row * n3 + c] * sp[c];
-    tp[row] = acc;
+  // tp = M^-1 sp, one warp per row, lanes over columns (coalesced)
+  for (int row = wid; row < n3; row += nw) {
+    T acc = T(0);
+    for (int c = lane; c < n3; c += 32) acc += Mi[(i64)row * n3 + c] * sp[c];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) tp[row] = acc;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double f[6] = {0, 0, 0, 0, 0, 0};
     for (int i = 0; i < nbp; ++i) {
-      const double* t = tp + 3 * i;
+      const double t0 = tp[3 * i], t1 = tp[3 * i + 1], t2 = tp[3 * i + 2];
       const double* a = rf + 3 * i;
-      f[0] += t[0]; f[1] += t[1]; f[2] += t[2];
-      f[3] += a[1] * t[2] - a[2] * t[1];
-      f[4] += a[2] * t[0] - a[0] * t[2];
-      f[5] += a[0] * t[1] - a[1] * t[0];
+      f[0] += t0; f[1] += t1; f[2] += t2;
+      f[3] += a[1] * t2 - a[2] * t1;
+      f[4] += a[2] * t0 - a[0] * t2;
+      f[5] += a[0] * t1 - a[1] * t0;
     }
     double ru[6];
     for (int c = 0; c < 6; ++c) ru[c] = (double)rU[6 * p + c];
@@ -442,21 +524,22 @@ __global__ void k_body_precond(int nb, const int* __restrict__ boff, const int* 
     const double kx = w6[0] + (w6[4] * a[2] - w6[5] * a[1]);
     const double ky = w6[1] + (w6[5] * a[0] - w6[3] * a[2]);
     const double kz = w6[2] + (w6[3] * a[1] - w6[4] * a[0]);
-    tp[3 * i] = kx - sp[3 * i];
-    tp[3 * i + 1] = ky - sp[3 * i + 1];
-    tp[3 * i + 2] = kz - sp[3 * i + 2];
+    tp[3 * i] = (T)kx - sp[3 * i];
+    tp[3 * i + 1] = (T)ky - sp[3 * i + 1];
+    tp[3 * i + 2] = (T)kz - sp[3 * i + 2];
   }
   __syncthreads();
-  for (int row = threadIdx.x; row < n3; row += blockDim.x) {
-    double acc = 0.0;
-    for (int c = 0; c < n3; ++c) acc += Mi[(i64)row * n3 + c] * tp[c];
-    sp[row] = acc;      // lam' (s' no longer needed)
+  for (int row = wid; row < n3; row += nw) {
+    T acc = T(0);
+    for (int c = lane; c < n3; c += 32) acc += Mi[(i64)row * n3 + c] * tp[c];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) sp[row] = acc;   // lam' (s' no longer needed)
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nbp; i += blockDim.x) {
-    const double* l = sp + 3 * i;
+    const T* l = sp + 3 * i;
     for (int a = 0; a < 3; ++a)
-      zlam[3 * (b0 + i) + a] = (T)(R[3 * a] * l[0] + R[3 * a + 1] * l[1] + R[3 * a + 2] * l[2]);
+      zlam[3 * (b0 + i) + a] = (T)(R[3 * a] * (double)l[0] + R[3 * a + 1] * (double)l[1] + R[3 * a + 2] * (double)l[2]);
   }
   if (threadIdx.x < 6) {
     const int h = threadIdx.x / 3, a = threadIdx.x % 3;
@@ -465,13 +548,15 @@ __global__ void k_body_precond(int nb, const int* __restrict__ boff, const int* 
 }
 
 template <typename T>
-void body_precond(const BodyView& b, const PrecondView& pv, const double* sres, const T* rU, T* zlam, T* zU,
+void body_precond(const BodyView& b, const PrecondView& pv, const T* sres, const T* rU, T* zlam, T* zU,
                   cudaStream_t s) {
   if (b.nb == 0) return;
-  const size_t shm = sizeof(double) * (2 * 3 * (size_t)pv.max_blobs + 12);
-  k_body_precond<T><<<b.nb, 128, shm, s>>>(b.nb, b.boff, pv.shape_of, pv.minv_off, pv.minv, pv.nmat,
+  const size_t shm = sizeof(T) * (2 * 3 * (size_t)pv.max_blobs + 8);
+  const T* mi = nullptr;
+  if constexpr (sizeof(T) == 8) mi = (const T*)pv.minv; else mi = (const T*)pv.minv32;
+  k_body_precond<T><<<b.nb, 256, shm, s>>>(b.nb, b.boff, pv.shape_of, pv.minv_off, mi, pv.nmat,
                                           pv.shape_ref_blob, b.ref, b.quat, sres, rU, zlam, zU);
-                                          note_launch();
+  note_launch();
 }
 
 // ------------------------------------------------------------------ forces
@@ -620,9 +705,9 @@ void outside_check(const Dims& d, int nbl, const double* r, int* flag, cudaStrea
   template void spread<T>(const Dims&, int, const int*, const double*, const T*, double, T*, cudaStream_t); \
   template void interp<T>(const Dims&, const Walls&, int, const double*, const T*, double, double, double, \
                           T*, cudaStream_t);                                                             \
-  template void body_precond<T>(const BodyView&, const PrecondView&, const double*, const T*, T*, T*,   \
+  template void body_precond<T>(const BodyView&, const PrecondView&, const T*, const T*, T*, T*,        \
                                 cudaStream_t);                                                          \
-  template void interp_res<T>(const Dims&, int, const double*, const T*, const T*, double*, cudaStream_t);
+  template void interp_res<T>(const Dims&, const BodyView&, const T*, const T*, T*, cudaStream_t);
 INST(double)
 INST(float)
 #undef INST

@@ -35,12 +35,12 @@ __global__ void k_dot_part(const T* __restrict__ w, const T* __restrict__ V, i64
                            double* __restrict__ part) {
   const int col = blockIdx.y;
   const T* v = V + (i64)col * ldv;
-  double acc = 0.0;
+  double af = 0.0, ab = 0.0;   // fluid and body parts; the weight is applied once
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-    const double prod = (double)w[i] * (double)v[i];
-    acc += (i < nfl) ? wf * prod : prod;
+    if (i < nfl) af = fma((double)w[i], (double)v[i], af);
+    else ab = fma((double)w[i], (double)v[i], ab);
   }
-  acc = block_sum(acc);
+  double acc = block_sum(wf * af + ab);
   if (threadIdx.x == 0) part[(i64)col * gridDim.x + blockIdx.x] = acc;
 }
 
@@ -52,13 +52,21 @@ __global__ void k_dot_finish(const double* __restrict__ part, int nparts, double
   if (threadIdx.x == 0) out[col] = acc;
 }
 
+// About 16 elements per thread: enough work per block to amortise its
+// reduction, while the columns still give several blocks per SM.
+inline int dot_blocks(i64 n, int nparts) {
+  const i64 b = (n + 256 * 16 - 1) / (256 * 16);
+  return (int)std::max<i64>(1, std::min<i64>(b, nparts));
+}
+
 template <typename T>
 void multi_dot(const T* w, const T* V, i64 ldv, int ncols, i64 n, i64 nfl, double wf, double* part, int nparts,
                double* out, cudaStream_t s) {
-  dim3 grid(nparts, ncols);
+  const int nb = dot_blocks(n, nparts);
+  dim3 grid(nb, ncols);
   k_dot_part<T><<<grid, 256, 0, s>>>(w, V, ldv, n, nfl, wf, part);
   note_launch();
-  k_dot_finish<<<ncols, 256, 0, s>>>(part, nparts, out);
+  k_dot_finish<<<ncols, 256, 0, s>>>(part, nb, out);
   note_launch();
 }
 
@@ -70,17 +78,17 @@ __global__ void k_multi_axpy(T* __restrict__ w, const T* __restrict__ V, i64 ldv
   __shared__ double c[128];
   for (int i = threadIdx.x; i < ncols; i += blockDim.x) c[i] = sign * coef[i];
   __syncthreads();
-  double acc = 0.0;
+  double af = 0.0, ab = 0.0;
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
     double x = (double)w[i];
-    for (int k = 0; k < ncols; ++k) x += c[k] * (double)V[(i64)k * ldv + i];
+    for (int k = 0; k < ncols; ++k) x = fma(c[k], (double)V[(i64)k * ldv + i], x);
     const T xt = (T)x;
     w[i] = xt;
-    const double xx = (double)xt * (double)xt;
-    acc += (i < nfl) ? wf * xx : xx;
+    if (i < nfl) af = fma((double)xt, (double)xt, af);
+    else ab = fma((double)xt, (double)xt, ab);
   }
   if (part) {
-    acc = block_sum(acc);
+    double acc = block_sum(wf * af + ab);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
   }
 }

@@ -25,7 +25,7 @@ RBFIB_DEVFN void lap_parts(const Dims& d, const T* __restrict__ v, int a, const 
   const int* e = d.fe[a];
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
-    const T ih2 = T(1.0 / (d.h[ax] * d.h[ax]));
+    const T ih2 = inv_h2<T>(d, ax);
     diag += T(2) * ih2;
     int lo[3] = {c[0], c[1], c[2]}, hi[3] = {c[0], c[1], c[2]};
     lo[ax] -= 1; hi[ax] += 1;
@@ -43,6 +43,29 @@ RBFIB_DEVFN void lap_parts(const Dims& d, const T* __restrict__ v, int a, const 
 }
 
 // ------------------------------------------------------- Stokes operator
+// Laplacian parts on a level with one spacing h on every axis: neighbour sum
+// and diagonal in units of 1/h^2 (fewer multiplies in the FP64 operator).
+template <typename T>
+RBFIB_DEVFN void lap_parts_uniform(const Dims& d, const T* __restrict__ v, int a, const int c[3], T& nbsum, int& diag) {
+  nbsum = T(0);
+  diag = 6;
+  const i64 base = d.fo[a];
+  const int* e = d.fe[a];
+  const i64 id = base + flat3(e, c[0], c[1], c[2]);
+  const i64 str[3] = {1, (i64)e[0], (i64)e[0] * e[1]};
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int lo = c[ax] - 1, hi = c[ax] + 1;
+    if (d.per[ax]) {
+      nbsum += v[lo < 0 ? id + (e[ax] - 1) * str[ax] : id - str[ax]];
+      nbsum += v[hi >= e[ax] ? id - (e[ax] - 1) * str[ax] : id + str[ax]];
+    } else {
+      if (lo >= 0) nbsum += v[id - str[ax]]; else if (ax != a) ++diag;
+      if (hi < e[ax]) nbsum += v[id + str[ax]]; else if (ax != a) ++diag;
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_stokes_apply(Dims d, T eta, const T* __restrict__ v, const T* __restrict__ p,
                                T* __restrict__ yv, T* __restrict__ yp) {
@@ -51,15 +74,24 @@ __global__ void k_stokes_apply(Dims d, T eta, const T* __restrict__ v, const T* 
   if (t < nf) {
     int a, c[3];
     decode_face(d, t, a, c);
-    T nb, dg;
-    lap_parts(d, v, a, c, nb, dg);
     const T u = v[t];
+    T visc;
+    if (d.h[0] == d.h[1] && d.h[1] == d.h[2]) {
+      T nb;
+      int di;
+      lap_parts_uniform(d, v, a, c, nb, di);
+      visc = (eta * inv_h2<T>(d, 0)) * ((T)di * u - nb);
+    } else {
+      T nb, dg;
+      lap_parts(d, v, a, c, nb, dg);
+      visc = eta * (dg * u - nb);
+    }
     // pressure gradient across the face
     int cl[3] = {c[0], c[1], c[2]}, cr[3] = {c[0], c[1], c[2]};
     if (d.per[a]) { cl[a] = c[a] - 1; if (cl[a] < 0) cl[a] += d.n[a]; }
     else { cr[a] = c[a] + 1; }
-    const T gp = (p[flat3(d.n, cr[0], cr[1], cr[2])] - p[flat3(d.n, cl[0], cl[1], cl[2])]) * T(1.0 / d.h[a]);
-    yv[t] = eta * (dg * u - nb) + gp;
+    const T gp = (p[flat3(d.n, cr[0], cr[1], cr[2])] - p[flat3(d.n, cl[0], cl[1], cl[2])]) * inv_h<T>(d, a);
+    yv[t] = visc + gp;
   } else if (t < nf + d.nc) {
     const i64 l = t - nf;
     int c[3];
@@ -77,23 +109,50 @@ __global__ void k_stokes_apply(Dims d, T eta, const T* __restrict__ v, const T* 
         if (c[a] <= d.n[a] - 2) vr = face_at(d, v, a, f);
         if (c[a] >= 1) { f[a] = c[a] - 1; vl = face_at(d, v, a, f); }
       }
-      div += (vr - vl) * T(1.0 / d.h[a]);
+      div += (vr - vl) * inv_h<T>(d, a);
     }
     yp[l] = -div;
   }
 }
 
 // ------------------------------------------ velocity multigrid (A = -eta LL)
+// Diagonal of -LL at a face (ghost faces across tangential walls add 1/h^2).
 template <typename T>
-__global__ void k_vel_rbgs(Dims d, T eta, int color, T* __restrict__ u, const T* __restrict__ rhs) {
+RBFIB_DEVFN T lap_diag(const Dims& d, int a, const int c[3]) {
+  T dg = T(0);
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const T ih2 = inv_h2<T>(d, ax);
+    dg += T(2) * ih2;
+    if (!d.per[ax] && ax != a) {
+      if (c[ax] == 0) dg += ih2;
+      if (c[ax] == d.fe[a][ax] - 1) dg += ih2;
+    }
+  }
+  return dg;
+}
+
+// One red-black Gauss-Seidel half sweep: threads map to the points of one colour.
+template <typename T>
+__global__ void k_vel_rbgs(Dims d, ColorMap m, T eta, int color, T* __restrict__ u, const T* __restrict__ rhs) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  int a, c[3];
+  if (!color_face(d, m, t, color, a, c)) return;
+  T nb, dg;
+  lap_parts(d, u, a, c, nb, dg);
+  const i64 id = d.fo[a] + flat3(d.fe[a], c[0], c[1], c[2]);
+  u[id] = (rhs[id] / eta + nb) / dg;
+}
+
+// First half sweep from a zero initial guess: colour 0 gets rhs / (eta diag),
+// colour 1 is zeroed.
+template <typename T>
+__global__ void k_vel_first(Dims d, T eta, T* __restrict__ u, const T* __restrict__ rhs) {
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.fo[3]) return;
   int a, c[3];
   decode_face(d, t, a, c);
-  if (((c[0] + c[1] + c[2]) & 1) != color) return;
-  T nb, dg;
-  lap_parts(d, u, a, c, nb, dg);
-  u[t] = (rhs[t] / eta + nb) / dg;
+  u[t] = (((c[0] + c[1] + c[2]) & 1) == 0) ? rhs[t] / (eta * lap_diag<T>(d, a, c)) : T(0);
 }
 
 template <typename T>
@@ -183,6 +242,35 @@ __global__ void k_vel_restrict(Dims df, Dims dc, int3 cz, const T* __restrict__ 
   rc[t] = (T)acc;
 }
 
+// Restriction of the residual rhs - A u, computed on the fly at the fine points.
+template <typename T>
+__global__ void k_vel_restrict_res(Dims df, Dims dc, int3 cz, T eta, const T* __restrict__ uf,
+                                   const T* __restrict__ rhsf, T* __restrict__ rc) {
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= dc.fo[3]) return;
+  int a, c[3];
+  decode_face(dc, t, a, c);
+  const int cf[3] = {cz.x, cz.y, cz.z};
+  T1 s[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    int kind = !cf[ax] ? 0 : (ax == a ? (df.per[ax] ? 1 : 2) : 3);
+    restrict_1d(kind, c[ax], df.fe[a][ax], s[ax]);
+  }
+  float acc = 0.f;
+  for (int x = 0; x < s[0].cnt; ++x)
+    for (int y = 0; y < s[1].cnt; ++y)
+      for (int z = 0; z < s[2].cnt; ++z) {
+        const int fc[3] = {s[0].idx[x], s[1].idx[y], s[2].idx[z]};
+        T nb, dg;
+        lap_parts(df, uf, a, fc, nb, dg);
+        const i64 id = df.fo[a] + flat3(df.fe[a], fc[0], fc[1], fc[2]);
+        const T r = rhsf[id] - eta * (dg * uf[id] - nb);
+        acc += (float)(s[0].w[x] * s[1].w[y] * s[2].w[z]) * (float)r;
+      }
+  rc[t] = (T)acc;
+}
+
 template <typename T>
 __global__ void k_vel_prolong(Dims df, Dims dc, int3 cz, const T* __restrict__ uc, T* __restrict__ uf) {
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
@@ -212,7 +300,7 @@ RBFIB_DEVFN void plap_parts(const Dims& d, const T* __restrict__ p, const int c[
   nbsum = T(0); diag = T(0);
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
-    const T ih2 = T(1.0 / (d.h[ax] * d.h[ax]));
+    const T ih2 = inv_h2<T>(d, ax);
     int lo[3] = {c[0], c[1], c[2]}, hi[3] = {c[0], c[1], c[2]};
     lo[ax] -= 1; hi[ax] += 1;
     if (d.per[ax]) {
@@ -228,15 +316,35 @@ RBFIB_DEVFN void plap_parts(const Dims& d, const T* __restrict__ p, const int c[
 }
 
 template <typename T>
-__global__ void k_p_rbgs(Dims d, int color, T* __restrict__ u, const T* __restrict__ rhs) {
+__global__ void k_p_rbgs(Dims d, ColorMap m, int color, T* __restrict__ u, const T* __restrict__ rhs) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  int c[3];
+  if (!color_cell(d, m, t, color, c)) return;
+  T nb, dg;
+  plap_parts(d, u, c, nb, dg);
+  const i64 id = flat3(d.n, c[0], c[1], c[2]);
+  u[id] = (rhs[id] + nb) / dg;
+}
+
+template <typename T>
+RBFIB_DEVFN T plap_diag(const Dims& d, const int c[3]) {
+  T dg = T(0);
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const T ih2 = inv_h2<T>(d, ax);
+    if (d.per[ax]) dg += T(2) * ih2;
+    else dg += ih2 * (T)((c[ax] > 0) + (c[ax] < d.n[ax] - 1));
+  }
+  return dg;
+}
+
+template <typename T>
+__global__ void k_p_first(Dims d, T* __restrict__ u, const T* __restrict__ rhs) {
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.nc) return;
   int c[3];
   decode_cell(d, t, c);
-  if (((c[0] + c[1] + c[2]) & 1) != color) return;
-  T nb, dg;
-  plap_parts(d, u, c, nb, dg);
-  u[t] = (rhs[t] + nb) / dg;
+  u[t] = (((c[0] + c[1] + c[2]) & 1) == 0) ? rhs[t] / plap_diag<T>(d, c) : T(0);
 }
 
 template <typename T>
@@ -265,6 +373,30 @@ __global__ void k_p_restrict(Dims df, Dims dc, int3 cz, const T* __restrict__ rf
     for (int y = 0; y < s[1].cnt; ++y)
       for (int z = 0; z < s[2].cnt; ++z)
         acc += s[0].w[x] * s[1].w[y] * s[2].w[z] * (double)rf[flat3(df.n, s[0].idx[x], s[1].idx[y], s[2].idx[z])];
+  rc[t] = (T)acc;
+}
+
+template <typename T>
+__global__ void k_p_restrict_res(Dims df, Dims dc, int3 cz, const T* __restrict__ uf, const T* __restrict__ rhsf,
+                                 T* __restrict__ rc) {
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= dc.nc) return;
+  int c[3];
+  decode_cell(dc, t, c);
+  const int cf[3] = {cz.x, cz.y, cz.z};
+  T1 s[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) restrict_1d(cf[ax] ? 3 : 0, c[ax], df.n[ax], s[ax]);
+  float acc = 0.f;
+  for (int x = 0; x < s[0].cnt; ++x)
+    for (int y = 0; y < s[1].cnt; ++y)
+      for (int z = 0; z < s[2].cnt; ++z) {
+        const int fc[3] = {s[0].idx[x], s[1].idx[y], s[2].idx[z]};
+        T nb, dg;
+        plap_parts(df, uf, fc, nb, dg);
+        const i64 id = flat3(df.n, fc[0], fc[1], fc[2]);
+        acc += (float)(s[0].w[x] * s[1].w[y] * s[2].w[z]) * (float)(rhsf[id] - (dg * uf[id] - nb));
+      }
   rc[t] = (T)acc;
 }
 
@@ -360,7 +492,7 @@ __global__ void k_div_q(Dims d, T eta, const T* __restrict__ vt, const T* __rest
       if (c[a] <= d.n[a] - 2) vr = face_at(d, vt, a, f);
       if (c[a] >= 1) { f[a] = c[a] - 1; vl = face_at(d, vt, a, f); }
     }
-    div += (vr - vl) * T(1.0 / d.h[a]);
+    div += (vr - vl) * inv_h<T>(d, a);
   }
   const T qq = rpi[l] + div;
   q[l] = qq;
@@ -377,7 +509,7 @@ __global__ void k_add_grad(Dims d, const T* __restrict__ phi, T* __restrict__ v)
   int cl[3] = {c[0], c[1], c[2]}, cr[3] = {c[0], c[1], c[2]};
   if (d.per[a]) { cl[a] = c[a] - 1; if (cl[a] < 0) cl[a] += d.n[a]; }
   else { cr[a] = c[a] + 1; }
-  v[t] += (phi[flat3(d.n, cr[0], cr[1], cr[2])] - phi[flat3(d.n, cl[0], cl[1], cl[2])]) * T(1.0 / d.h[a]);
+  v[t] += (phi[flat3(d.n, cr[0], cr[1], cr[2])] - phi[flat3(d.n, cl[0], cl[1], cl[2])]) * inv_h<T>(d, a);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -391,7 +523,19 @@ void stokes_apply(const Dims& d, T eta, const T* v, const T* p, T* yv, T* yp, cu
 }
 template <typename T>
 void vel_rbgs(const Dims& d, T eta, int color, T* u, const T* rhs, cudaStream_t s) {
-  k_vel_rbgs<T><<<nblk(d.fo[3], 256), 256, 0, s>>>(d, eta, color, u, rhs);
+  const ColorMap m = make_color_map_faces(d);
+  k_vel_rbgs<T><<<nblk((i64)m.cnt[0] + m.cnt[1] + m.cnt[2], 256), 256, 0, s>>>(d, m, eta, color, u, rhs);
+  note_launch();
+}
+template <typename T>
+void vel_first(const Dims& d, T eta, T* u, const T* rhs, cudaStream_t s) {
+  k_vel_first<T><<<nblk(d.fo[3], 256), 256, 0, s>>>(d, eta, u, rhs);
+  note_launch();
+}
+template <typename T>
+void vel_restrict_res(const Dims& df, const Dims& dc, int3 cz, T eta, const T* uf, const T* rhsf, T* rc,
+                      cudaStream_t s) {
+  k_vel_restrict_res<T><<<nblk(dc.fo[3], 256), 256, 0, s>>>(df, dc, cz, eta, uf, rhsf, rc);
   note_launch();
 }
 template <typename T>
@@ -416,7 +560,18 @@ void vel_coarse(const Dims& d, T eta, T* u, const T* rhs, int sweeps, cudaStream
 }
 template <typename T>
 void p_rbgs(const Dims& d, int color, T* u, const T* rhs, cudaStream_t s) {
-  k_p_rbgs<T><<<nblk(d.nc, 256), 256, 0, s>>>(d, color, u, rhs);
+  const ColorMap m = make_color_map_cells(d);
+  k_p_rbgs<T><<<nblk(m.cnt[0], 256), 256, 0, s>>>(d, m, color, u, rhs);
+  note_launch();
+}
+template <typename T>
+void p_first(const Dims& d, T* u, const T* rhs, cudaStream_t s) {
+  k_p_first<T><<<nblk(d.nc, 256), 256, 0, s>>>(d, u, rhs);
+  note_launch();
+}
+template <typename T>
+void p_restrict_res(const Dims& df, const Dims& dc, int3 cz, const T* uf, const T* rhsf, T* rc, cudaStream_t s) {
+  k_p_restrict_res<T><<<nblk(dc.nc, 256), 256, 0, s>>>(df, dc, cz, uf, rhsf, rc);
   note_launch();
 }
 template <typename T>
@@ -453,6 +608,10 @@ void add_grad(const Dims& d, const T* phi, T* v, cudaStream_t s) {
 #define INST(T)                                                                                  \
   template void stokes_apply<T>(const Dims&, T, const T*, const T*, T*, T*, cudaStream_t);       \
   template void vel_rbgs<T>(const Dims&, T, int, T*, const T*, cudaStream_t);                    \
+  template void vel_first<T>(const Dims&, T, T*, const T*, cudaStream_t);                         \
+  template void vel_restrict_res<T>(const Dims&, const Dims&, int3, T, const T*, const T*, T*, cudaStream_t); \
+  template void p_first<T>(const Dims&, T*, const T*, cudaStream_t);                              \
+  template void p_restrict_res<T>(const Dims&, const Dims&, int3, const T*, const T*, T*, cudaStream_t); \
   template void vel_residual<T>(const Dims&, T, const T*, const T*, T*, cudaStream_t);           \
   template void vel_restrict<T>(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);     \
   template void vel_prolong<T>(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);      \

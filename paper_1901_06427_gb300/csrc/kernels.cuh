@@ -18,6 +18,8 @@ struct BodyView {
   const double* quat = nullptr;  // nb x 4
   const double* r = nullptr;     // nbl x 3 blob positions
   const double* arm = nullptr;   // nbl x 3 r - q
+  const BlobStencil<double>* st64 = nullptr;   // 3 nbl folded kernel stencils
+  const BlobStencil<float>* st32 = nullptr;
 };
 
 struct PrecondView {
@@ -25,6 +27,7 @@ struct PrecondView {
   const int* shape_of = nullptr;
   const i64* minv_off = nullptr;
   const double* minv = nullptr;
+  const float* minv32 = nullptr;
   const double* nmat = nullptr;
   const int* shape_ref_blob = nullptr;
 };
@@ -49,6 +52,12 @@ struct StressLayout {
 // k_stokes.cu
 template <typename T> void stokes_apply(const Dims&, T eta, const T* v, const T* p, T* yv, T* yp, cudaStream_t);
 template <typename T> void vel_rbgs(const Dims&, T eta, int color, T* u, const T* rhs, cudaStream_t);
+template <typename T> void vel_first(const Dims&, T eta, T* u, const T* rhs, cudaStream_t);
+template <typename T> void vel_restrict_res(const Dims&, const Dims&, int3, T eta, const T* uf, const T* rhsf,
+                                            T* rc, cudaStream_t);
+template <typename T> void p_first(const Dims&, T* u, const T* rhs, cudaStream_t);
+template <typename T> void p_restrict_res(const Dims&, const Dims&, int3, const T* uf, const T* rhsf, T* rc,
+                                          cudaStream_t);
 template <typename T> void vel_residual(const Dims&, T eta, const T* u, const T* rhs, T* res, cudaStream_t);
 template <typename T> void vel_restrict(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);
 template <typename T> void vel_prolong(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);
@@ -72,10 +81,13 @@ template <typename T> void spread(const Dims&, int nbl, const int* perm, const d
                                   double scale, T* f, cudaStream_t);
 template <typename T> void interp(const Dims&, const Walls&, int nbl, const double* r, const T* v, double alpha,
                                   double beta, double gamma, T* out, cudaStream_t);
-template <typename T> void interp_res(const Dims&, int nbl, const double* r, const T* v, const T* rl,
-                                      double* out, cudaStream_t);
-template <typename T> void body_precond(const BodyView&, const PrecondView&, const double* sres, const T* rU,
+template <typename T> void interp_res(const Dims&, const BodyView&, const T* v, const T* rl, T* out, cudaStream_t);
+template <typename T> void body_precond(const BodyView&, const PrecondView&, const T* sres, const T* rU,
                                         T* zlam, T* zU, cudaStream_t);
+void stencil_build(const Dims&, int nbl, const double* r, BlobStencil<double>* s64, BlobStencil<float>* s32,
+                   cudaStream_t);
+void interp_tab(const Dims&, const BodyView&, const double* v, double alpha, double beta, double* out, cudaStream_t);
+void spread_tab(const Dims&, const BodyView&, const double* lam, double scale, double* f, cudaStream_t);
 void kt_apply(int nb, const int* boff, const double* arm, const double* lam, double alpha, double beta,
               double* out, cudaStream_t);
 void k_apply(int nbl, const int* bob, const double* arm, const double* U, double alpha, double beta,
@@ -85,6 +97,13 @@ void wft(int nb, const double* wn, const double* Lp, double kT, double* out, cud
 void move_bodies(int nb, const double* q, const double* quat, const double* vec6, const double* Lp, double a,
                  double* qo, double* quato, cudaStream_t);
 void outside_check(const Dims&, int nbl, const double* r, int* flag, cudaStream_t);
+
+// k_body.cu
+void dense_body_build(int nbl, int nb, const int* boff, const double* r, const double* arm, double a, double eta,
+                      float* Minv, float* P, double* N, int* status, cudaStream_t);
+template <typename T> void dense_body_apply(int nbl, int nb, const int* boff, const int* bob, const double* arm,
+                                            const float* Minv, const double* N, const T* sres, const T* rU,
+                                            T* zlam, T* zU, cudaStream_t);
 
 // k_krylov.cu
 // Weighted inner products <x, y>_W with weight wf on the first nfl entries

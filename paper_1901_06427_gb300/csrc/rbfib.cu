@@ -20,6 +20,8 @@ namespace {
 
 const double kDeltaDefault = 6.0554544523933395e-06;   // eps^(1/3), eps = 2^-52
 const double kBlobRadius = 0.91;                         // hydrodynamic radius of a 3-point blob, units of h
+const int kDenseBodyMaxRows = 1536;                      // 3 N_bl limit of the coupled body block
+const int kDenseBodyMaxBodyRows = 384;                   // 6 N_b limit of the coupled body block
 
 struct CudaError {
   cudaError_t e;
@@ -97,6 +99,8 @@ struct KrylovStore {
 struct Config {   // one body configuration (positions derived from q, quat)
   DBuf<double> q, quat, r, arm;
   DBuf<int> perm;
+  DBuf<BlobStencil<double>> st64;   // kernel stencils (current configuration only)
+  DBuf<BlobStencil<float>> st32;
 };
 
 }  // namespace
@@ -122,6 +126,12 @@ struct rbfib_grid {
   DBuf<int> shape_of, shape_ref_blob;
   DBuf<i64> minv_off;
   DBuf<double> minv, nmat;
+  DBuf<float> minv32, sres32;
+  // coupled (all-blob) body block for small suspensions
+  bool dense_body = false;
+  DBuf<float> dM, dP;
+  DBuf<double> dN;
+  DBuf<int> dstatus;
   // work vectors (FP64)
   DBuf<double> part, scal, bvec, xvec, xrfd, rres, sres, fsharp, vsharp, fnoise, Wst;
   DBuf<double> bodyA, bodyB, bodyF, bodyW, bodyWn, blobA, blobB, blobC, blobD, blobS;
@@ -185,6 +195,7 @@ BodyView view_of(rbfib_grid* g, Config& c) {
   b.nb = g->nb; b.nbl = g->nbl;
   b.boff = g->boff; b.bob = g->bob; b.perm = c.perm.p;
   b.ref = g->ref; b.q = c.q; b.quat = c.quat; b.r = c.r; b.arm = c.arm;
+  b.st64 = c.st64.p; b.st32 = c.st32.p;
   return b;
 }
 
@@ -192,6 +203,7 @@ PrecondView pview(rbfib_grid* g) {
   PrecondView p;
   p.max_blobs = g->max_blobs;
   p.shape_of = g->shape_of; p.minv_off = g->minv_off; p.minv = g->minv; p.nmat = g->nmat;
+  p.minv32 = g->minv32;
   p.shape_ref_blob = g->shape_ref_blob;
   return p;
 }
@@ -252,10 +264,10 @@ void vcycle_vel(rbfib_grid* g, T* u0, const T* rhs0) {
   };
   for (int l = 0; l < L - 1; ++l) {
     const Dims& d = g->levels[l].d;
-    ck(cudaMemsetAsync(u[l], 0, sizeof(T) * d.fo[3], g->s));
-    for (int s = 0; s < kNu; ++s) { smooth(l, 0); smooth(l, 1); }
-    vel_residual<T>(d, eta, u[l], rhs[l], *M.vres[l], g->s);
-    vel_restrict<T>(d, g->levels[l + 1].d, g->levels[l].cz, *M.vres[l], rhs[l + 1], g->s);
+    vel_first<T>(d, eta, u[l], rhs[l], g->s);          // zero guess + first colour-0 update
+    smooth(l, 1);
+    for (int s = 1; s < kNu; ++s) { smooth(l, 0); smooth(l, 1); }
+    vel_restrict_res<T>(d, g->levels[l + 1].d, g->levels[l].cz, eta, u[l], rhs[l], rhs[l + 1], g->s);
   }
   vel_coarse<T>(g->levels[L - 1].d, eta, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
   for (int l = L - 2; l >= 0; --l) {
@@ -276,10 +288,10 @@ void vcycle_p(rbfib_grid* g, T* u0, T* rhs0) {
   rhs[0] = rhs0;
   for (int l = 0; l < L - 1; ++l) {
     const Dims& d = g->levels[l].d;
-    ck(cudaMemsetAsync(u[l], 0, sizeof(T) * d.nc, g->s));
-    for (int s = 0; s < kNu; ++s) { p_rbgs<T>(d, 0, u[l], rhs[l], g->s); p_rbgs<T>(d, 1, u[l], rhs[l], g->s); }
-    p_residual<T>(d, u[l], rhs[l], *M.pres[l], g->s);
-    p_restrict<T>(d, g->levels[l + 1].d, g->levels[l].cz, *M.pres[l], rhs[l + 1], g->s);
+    p_first<T>(d, u[l], rhs[l], g->s);
+    p_rbgs<T>(d, 1, u[l], rhs[l], g->s);
+    for (int s = 1; s < kNu; ++s) { p_rbgs<T>(d, 0, u[l], rhs[l], g->s); p_rbgs<T>(d, 1, u[l], rhs[l], g->s); }
+    p_restrict_res<T>(d, g->levels[l + 1].d, g->levels[l].cz, u[l], rhs[l], rhs[l + 1], g->s);
   }
   p_coarse<T>(g->levels[L - 1].d, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
   for (int l = L - 2; l >= 0; --l) {
@@ -288,6 +300,10 @@ void vcycle_p(rbfib_grid* g, T* u0, T* rhs0) {
     for (int s = 0; s < kNu; ++s) { p_rbgs<T>(d, 1, u[l], rhs[l], g->s); p_rbgs<T>(d, 0, u[l], rhs[l], g->s); }
   }
 }
+
+template <typename T> T* sres_of(rbfib_grid* g);
+template <> double* sres_of<double>(rbfib_grid* g) { return g->sres; }
+template <> float* sres_of<float>(rbfib_grid* g) { return g->sres32; }
 
 // ---------------------------------------------------------- preconditioner
 // Block lower-triangular preconditioner of the saddle operator.
@@ -313,8 +329,12 @@ void precond(rbfib_grid* g, const T* r, T* z, bool with_bodies) {
     const T* rU = rl + 3 * (i64)g->nbl;
     T* zl = z + g->nfl;
     T* zU = zl + 3 * (i64)g->nbl;
-    interp_res<T>(d, g->nbl, g->cur.r, zv, rl, g->sres, g->s);
-    body_precond<T>(view_of(g, g->cur), pview(g), g->sres, rU, zl, zU, g->s);
+    T* sres = sres_of<T>(g);
+    interp_res<T>(d, view_of(g, g->cur), zv, rl, sres, g->s);
+    if (g->dense_body)
+      dense_body_apply<T>(g->nbl, g->nb, g->boff, g->bob, g->cur.arm, g->dM, g->dN, sres, rU, zl, zU, g->s);
+    else
+      body_precond<T>(view_of(g, g->cur), pview(g), sres, rU, zl, zU, g->s);
   }
 }
 
@@ -551,7 +571,13 @@ bool inverse6(double A[36]) {
 
 void refresh_config(rbfib_grid* g, Config& c, bool bin) {
   geometry(g->nbl, g->bob, g->ref, c.q, c.quat, c.r, c.arm, g->s);
-  if (bin) binning(g->d, g->nbl, c.r, c.perm, g->celloff, g->bkey, g->bcount, g->bfill, g->bbsum, g->s);
+  if (bin) {
+    binning(g->d, g->nbl, c.r, c.perm, g->celloff, g->bkey, g->bcount, g->bfill, g->bbsum, g->s);
+    stencil_build(g->d, g->nbl, c.r, c.st64, c.st32, g->s);
+    if (g->dense_body)
+      dense_body_build(g->nbl, g->nb, g->boff, c.r, c.arm, kBlobRadius * g->desc.h, g->desc.eta, g->dM, g->dP,
+                       g->dN, g->dstatus, g->s);
+  }
 }
 
 void alloc_config(rbfib_grid* g, Config& c) {
@@ -560,6 +586,8 @@ void alloc_config(rbfib_grid* g, Config& c) {
   c.r.alloc(3 * (size_t)g->nbl);
   c.arm.alloc(3 * (size_t)g->nbl);
   c.perm.alloc((size_t)g->nbl);
+  c.st64.alloc(3 * (size_t)g->nbl);
+  c.st32.alloc(3 * (size_t)g->nbl);
 }
 
 void alloc_solver(rbfib_grid* g) {
@@ -723,6 +751,14 @@ int rbfib_set_bodies(rbfib_grid* g, int32_t n_bodies, const int32_t* blob_offset
       ck(cudaMemcpyAsync(g->cur.quat, quat, sizeof(double) * 4 * nb, cudaMemcpyDeviceToDevice, g->s));
     }
     g->bkey.alloc(std::max(nbl, 1));
+    // coupled body block when every blob pair fits a small dense matrix
+    g->dense_body = nb >= 2 && 3 * nbl <= kDenseBodyMaxRows && 6 * nb <= kDenseBodyMaxBodyRows;
+    if (g->dense_body) {
+      g->dM.alloc((size_t)9 * nbl * nbl);
+      g->dP.alloc((size_t)18 * nbl * nb);
+      g->dN.alloc((size_t)36 * nb * nb);
+      g->dstatus.alloc(1);
+    }
     refresh_config(g, g->cur, true);
     // host copy of the reference blobs: body lengths and shape table
     std::vector<double> href(3 * (size_t)nbl);
@@ -806,12 +842,20 @@ int rbfib_set_bodies(rbfib_grid* g, int32_t n_bodies, const int32_t* blob_offset
     g->minv.alloc(std::max<size_t>(minv_all.size(), 1));
     if (!minv_all.empty())
       ck(cudaMemcpyAsync(g->minv, minv_all.data(), sizeof(double) * minv_all.size(), cudaMemcpyHostToDevice, g->s));
+    {
+      std::vector<float> m32(minv_all.begin(), minv_all.end());
+      g->minv32.alloc(std::max<size_t>(m32.size(), 1));
+      if (!m32.empty())
+        ck(cudaMemcpyAsync(g->minv32, m32.data(), sizeof(float) * m32.size(), cudaMemcpyHostToDevice, g->s));
+      ck(cudaStreamSynchronize(g->s));
+    }
     g->nmat.alloc(nmat.size());
     ck(cudaMemcpyAsync(g->nmat, nmat.data(), sizeof(double) * nmat.size(), cudaMemcpyHostToDevice, g->s));
     // body-sized work arrays
     const size_t b6 = 6 * (size_t)std::max(nb, 1), l3 = 3 * (size_t)std::max(nbl, 1);
     for (DBuf<double>* b : {&g->bodyA, &g->bodyB, &g->bodyF, &g->bodyW, &g->bodyWn}) b->alloc(b6);
     for (DBuf<double>* b : {&g->blobA, &g->blobB, &g->blobC, &g->blobD, &g->blobS, &g->sres}) b->alloc(l3);
+    g->sres32.alloc(l3);
     alloc_solver(g);
     ck(cudaStreamSynchronize(g->s));
     ck(cudaGetLastError());
@@ -994,7 +1038,7 @@ int rbfib_spread(rbfib_grid* g, const double* lambda, double* f) {
   if (!g || !f || (g->nbl && !lambda)) return fail(g, RBFIB_EINVAL, "spread: null argument");
   try {
     ck(cudaMemsetAsync(f, 0, sizeof(double) * g->nf, g->s));
-    spread<double>(g->d, g->nbl, g->cur.perm, g->cur.r, lambda, 1.0 / g->dV, f, g->s);
+    spread_tab(g->d, view_of(g, g->cur), lambda, 1.0 / g->dV, f, g->s);
     ck(cudaGetLastError());
   } catch (CudaError& e) {
     return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
@@ -1005,7 +1049,9 @@ int rbfib_spread(rbfib_grid* g, const double* lambda, double* f) {
 int rbfib_interpolate(rbfib_grid* g, const double* v, double* u, int32_t with_walls) {
   if (!g || !v || (g->nbl && !u)) return fail(g, RBFIB_EINVAL, "interpolate: null argument");
   try {
-    interp<double>(g->d, g->walls, g->nbl, g->cur.r, v, 1.0, 0.0, with_walls ? 1.0 : 0.0, u, g->s);
+    interp_tab(g->d, view_of(g, g->cur), v, 1.0, 0.0, u, g->s);
+    if (with_walls)
+      interp<double>(g->d, g->walls, g->nbl, g->cur.r, (const double*)nullptr, 0.0, 1.0, 1.0, u, g->s);
     ck(cudaGetLastError());
   } catch (CudaError& e) {
     return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
@@ -1101,7 +1147,7 @@ int rbfib_sem_step(rbfib_grid* g, const rbfib_sem_params* p, uint64_t seed, uint
     interp<double>(g->d, w0, nbl, g->minus.r, v_rfd, 1.0, 0.0, 0.0, g->blobD, s);
     axpby<double>(g->blobC, g->blobD, -1.0, 1.0, 3 * (i64)nbl, s);
     axpby<double>(g->blobC, g->blobC, 0.0, 1.0 / delta, 3 * (i64)nbl, s);  // D^J
-    interp<double>(g->d, w0, nbl, g->cur.r, (const double*)g->vsharp, 1.0, 0.0, 0.0, g->blobD, s);  // D^S
+    interp_tab(g->d, view_of(g, g->cur), g->vsharp, 1.0, 0.0, g->blobD, s);                          // D^S
     // slip_tot = slip + D^K - D^J - D^S ; F_tot = F - D^{K^T}
     if (p->slip) ck(cudaMemcpyAsync(g->blobS, p->slip, sizeof(double) * 3 * nbl, cudaMemcpyDeviceToDevice, s));
     else ck(cudaMemsetAsync(g->blobS, 0, sizeof(double) * 3 * std::max(nbl, 1), s));

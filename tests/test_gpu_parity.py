@@ -196,3 +196,37 @@ def test_errors_are_status_codes(B):
     with pytest.raises(B.RbfibError) as e:
         g.mobility_solve(dev(w.force_torque))
     assert e.value.code == B.ENOCONV
+
+
+# ----------------------------------------------- FP32 inside FP64 refinement
+@pytest.mark.parametrize("name", ["walls", "xper_moving", "ragged42"])
+def test_refined_mobility_solve(B, name):
+    """FP32 stencils, spreading, multigrid and Krylov basis inside an FP64
+    iterative-refinement loop reach the FP64 tolerance; the error against the
+    FP64 oracle is reported per output block."""
+    w, og, ob = case(name)
+    g = B.grid_for(w, precision=B.FP32_REFINED, rtol=1e-10)
+    U, info, x = g.mobility_solve(dev(w.force_torque), slip=dev(w.slip), return_x=True)
+    f = saddle.rhs(og, ob, w.eta, F=w.force_torque, slip=w.slip)
+    x0 = solve.constrained(og, ob, w.eta, f)
+    assert info["rel_residual"] <= 1e-10 and info["refinements"] >= 1
+    xg = x.cpu().numpy()
+    lay = g.layout()
+    errs = {blk: rel(xg[lay[i]:lay[i + 1]], x0[lay[i]:lay[i + 1]])
+            for i, blk in enumerate(["vx", "vy", "vz", "pi", "lambda", "U"])}
+    print("refined errors vs oracle:", {k: f"{v:.2e}" for k, v in errs.items()})
+    assert errs["U"] < 1e-8
+    assert max(errs.values()) < 1e-7
+
+
+def test_refined_sem_step(B):
+    w, og, ob = case("walls")
+    g = B.grid_for(w, precision=B.FP32_REFINED, rtol=1e-11)
+    q, quat = dev(w.q), dev(w.quat)
+    st, info = g.sem_step(B.sem_params(w.potentials, dt=0.05, kT=1.0), 11, 2, 1, q, quat)
+    ref = sem.sem_step(og, ob, w.eta, 1.0, 0.05, w.potentials, seed=11, step=2, attempt=1)
+    assert st == 0
+    for k in ("solve_rfd", "solve_stokes", "solve_main"):
+        assert info[k]["rel_residual"] <= 1e-11
+    dq = q.cpu().numpy().reshape(-1, 3) - w.q
+    assert rel(dq, ref["q"] - w.q) < 1e-7
