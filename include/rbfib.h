@@ -123,6 +123,14 @@ int rbfib_saddle_layout(const rbfib_grid* g, int64_t offsets[7]);
  * accumulated in FP64 for either dtype. */
 int rbfib_apply_saddle(rbfib_grid* g, const void* x, void* y, int32_t dtype);
 
+/* z = P^{-1} r: the block preconditioner used inside the Krylov solves (the
+ * paper defers its preconditioner to the cited rigid-multiblob work; this one
+ * is ours): a projection-method multigrid V-cycle pair for the Stokes block
+ * and, for the bodies, the Schur complement with the blob mobility replaced
+ * by free-space Rotne-Prager-Yamakawa blocks.  r, z: device FP64 saddle
+ * vectors; computed in FP32 internally. */
+int rbfib_apply_preconditioner(rbfib_grid* g, const double* r, double* z);
+
 /* Solve the constrained system (Eqs. LangevinD1-D4) with forces/torques FT
  * (device N_b x 6), optional active slip (device N_bl x 3), optional fluid
  * forcing (device, N_f face values added to the momentum right-hand side) and

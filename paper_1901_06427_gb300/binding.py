@@ -71,6 +71,7 @@ def lib():
             "rbfib_set_bodies": ([P, I32, ctypes.POINTER(ctypes.c_int32), P, P, P], I32),
             "rbfib_saddle_layout": ([P, ctypes.POINTER(ctypes.c_int64)], I32),
             "rbfib_apply_saddle": ([P, P, P, I32], I32),
+            "rbfib_apply_preconditioner": ([P, P, P], I32),
             "rbfib_mobility_solve": ([P, P, P, P, P, P, ctypes.POINTER(SolveInfo)], I32),
             "rbfib_stokes_solve": ([P, P, P, P, ctypes.POINTER(SolveInfo)], I32),
             "rbfib_sem_step": ([P, ctypes.POINTER(SemParams), U64, U64, U32, P, P, ctypes.POINTER(StepInfo)], I32),
@@ -221,6 +222,13 @@ class Grid:
             y = torch.empty_like(x)
         self._check(lib().rbfib_apply_saddle(self._h, _ptr(x, x.dtype, n, "x"), _ptr(y, x.dtype, n, "y"), dtype))
         return y
+
+    def apply_preconditioner(self, r, z=None):
+        n = self.n_total
+        if z is None:
+            z = torch.empty_like(r)
+        self._check(lib().rbfib_apply_preconditioner(self._h, _ptr(r, numel=n, name="r"), _ptr(z, numel=n, name="z")))
+        return z
 
     def mobility_solve(self, FT, slip=None, fluid_rhs=None, return_x=False):
         U = torch.empty(6 * self.n_bodies, dtype=torch.float64, device="cuda")

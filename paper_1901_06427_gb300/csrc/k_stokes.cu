@@ -170,52 +170,52 @@ __global__ void k_vel_residual(Dims d, T eta, const T* __restrict__ u, const T* 
 // 1 = face-centred on a periodic axis, 2 = face-centred on a wall axis,
 // 3 = cell-centred.  ghost_sign: value of a cell-centred ghost beyond a wall
 // in units of the adjacent interior value (-1 Dirichlet, +1 Neumann).
-struct T1 { int cnt; int idx[3]; double w[3]; };
+struct T1 { int cnt; int idx[3]; float w[3]; };   // weights exact in FP32
 
 __device__ inline void restrict_1d(int kind, int ic, int nfext, T1& s) {
-  if (kind == 0) { s.cnt = 1; s.idx[0] = ic; s.w[0] = 1.0; return; }
-  if (kind == 3) { s.cnt = 2; s.idx[0] = 2 * ic; s.idx[1] = 2 * ic + 1; s.w[0] = s.w[1] = 0.5; return; }
+  if (kind == 0) { s.cnt = 1; s.idx[0] = ic; s.w[0] = 1.0f; return; }
+  if (kind == 3) { s.cnt = 2; s.idx[0] = 2 * ic; s.idx[1] = 2 * ic + 1; s.w[0] = s.w[1] = 0.5f; return; }
   if (kind == 1) {   // periodic faces, compact == physical; fine extent nfext
     int P = 2 * ic;
     s.cnt = 3;
-    s.idx[0] = (P - 1 + nfext) % nfext; s.w[0] = 0.25;
-    s.idx[1] = P; s.w[1] = 0.5;
-    s.idx[2] = (P + 1) % nfext; s.w[2] = 0.25;
+    s.idx[0] = (P - 1 + nfext) % nfext; s.w[0] = 0.25f;
+    s.idx[1] = P; s.w[1] = 0.5f;
+    s.idx[2] = (P + 1) % nfext; s.w[2] = 0.25f;
     return;
   }
   // wall faces: coarse compact ic <-> physical Q = ic + 1 <-> fine physical 2Q
   int P = 2 * (ic + 1);
   s.cnt = 3;
-  s.idx[0] = P - 2; s.w[0] = 0.25;     // fine compact of physical P-1
-  s.idx[1] = P - 1; s.w[1] = 0.5;
-  s.idx[2] = P;     s.w[2] = 0.25;     // physical P+1
+  s.idx[0] = P - 2; s.w[0] = 0.25f;    // fine compact of physical P-1
+  s.idx[1] = P - 1; s.w[1] = 0.5f;
+  s.idx[2] = P;     s.w[2] = 0.25f;    // physical P+1
 }
 
-__device__ inline void prolong_1d(int kind, int jf, int ncext, double ghost_sign, T1& s) {
-  if (kind == 0) { s.cnt = 1; s.idx[0] = jf; s.w[0] = 1.0; return; }
+__device__ inline void prolong_1d(int kind, int jf, int ncext, float ghost_sign, T1& s) {
+  if (kind == 0) { s.cnt = 1; s.idx[0] = jf; s.w[0] = 1.0f; return; }
   if (kind == 1) {
-    if ((jf & 1) == 0) { s.cnt = 1; s.idx[0] = jf / 2; s.w[0] = 1.0; return; }
-    s.cnt = 2; s.idx[0] = (jf - 1) / 2; s.idx[1] = ((jf + 1) / 2) % ncext; s.w[0] = s.w[1] = 0.5; return;
+    if ((jf & 1) == 0) { s.cnt = 1; s.idx[0] = jf / 2; s.w[0] = 1.0f; return; }
+    s.cnt = 2; s.idx[0] = (jf - 1) / 2; s.idx[1] = ((jf + 1) / 2) % ncext; s.w[0] = s.w[1] = 0.5f; return;
   }
   if (kind == 2) {   // fine physical P = jf + 1; coarse physical Q; boundary Q carry zero
     int P = jf + 1;
-    if ((P & 1) == 0) { s.cnt = 1; s.idx[0] = P / 2 - 1; s.w[0] = 1.0; return; }
+    if ((P & 1) == 0) { s.cnt = 1; s.idx[0] = P / 2 - 1; s.w[0] = 1.0f; return; }
     s.cnt = 0;
     int q1 = (P - 1) / 2, q2 = (P + 1) / 2;
     int nq = ncext + 1;   // coarse physical faces 0..nq
-    if (q1 >= 1 && q1 <= nq - 1) { s.idx[s.cnt] = q1 - 1; s.w[s.cnt] = 0.5; ++s.cnt; }
-    if (q2 >= 1 && q2 <= nq - 1) { s.idx[s.cnt] = q2 - 1; s.w[s.cnt] = 0.5; ++s.cnt; }
+    if (q1 >= 1 && q1 <= nq - 1) { s.idx[s.cnt] = q1 - 1; s.w[s.cnt] = 0.5f; ++s.cnt; }
+    if (q2 >= 1 && q2 <= nq - 1) { s.idx[s.cnt] = q2 - 1; s.w[s.cnt] = 0.5f; ++s.cnt; }
     return;
   }
   // cell-centred linear interpolation
   int jc = jf >> 1;
   int nb = (jf & 1) ? jc + 1 : jc - 1;
   s.cnt = 2;
-  s.idx[0] = jc; s.w[0] = 0.75;
+  s.idx[0] = jc; s.w[0] = 0.75f;
   if (nb < 0 || nb >= ncext) {
-    if (ghost_sign == 2.0) { nb = (nb + ncext) % ncext; s.idx[1] = nb; s.w[1] = 0.25; }   // periodic
-    else { s.cnt = 1; s.w[0] = 0.75 + 0.25 * ghost_sign; }
-  } else { s.idx[1] = nb; s.w[1] = 0.25; }
+    if (ghost_sign == 2.0f) { nb = (nb + ncext) % ncext; s.idx[1] = nb; s.w[1] = 0.25f; }   // periodic
+    else { s.cnt = 1; s.w[0] = 0.75f + 0.25f * ghost_sign; }
+  } else { s.idx[1] = nb; s.w[1] = 0.25f; }
 }
 
 // Restriction of face residuals to the coarse level: full weighting along a
@@ -233,12 +233,12 @@ __global__ void k_vel_restrict(Dims df, Dims dc, int3 cz, const T* __restrict__ 
     int kind = !cf[ax] ? 0 : (ax == a ? (df.per[ax] ? 1 : 2) : 3);
     restrict_1d(kind, c[ax], df.fe[a][ax], s[ax]);
   }
-  double acc = 0.0;
+  T acc = T(0);
   for (int x = 0; x < s[0].cnt; ++x)
     for (int y = 0; y < s[1].cnt; ++y)
       for (int z = 0; z < s[2].cnt; ++z)
-        acc += s[0].w[x] * s[1].w[y] * s[2].w[z] *
-               (double)rf[df.fo[a] + flat3(df.fe[a], s[0].idx[x], s[1].idx[y], s[2].idx[z])];
+        acc += (T)(s[0].w[x] * s[1].w[y] * s[2].w[z]) *
+               rf[df.fo[a] + flat3(df.fe[a], s[0].idx[x], s[1].idx[y], s[2].idx[z])];
   rc[t] = (T)acc;
 }
 
@@ -266,7 +266,7 @@ __global__ void k_vel_restrict_res(Dims df, Dims dc, int3 cz, T eta, const T* __
         lap_parts(df, uf, a, fc, nb, dg);
         const i64 id = df.fo[a] + flat3(df.fe[a], fc[0], fc[1], fc[2]);
         const T r = rhsf[id] - eta * (dg * uf[id] - nb);
-        acc += (float)(s[0].w[x] * s[1].w[y] * s[2].w[z]) * (float)r;
+        acc += (s[0].w[x] * s[1].w[y] * s[2].w[z]) * (float)r;
       }
   rc[t] = (T)acc;
 }
@@ -282,15 +282,15 @@ __global__ void k_vel_prolong(Dims df, Dims dc, int3 cz, const T* __restrict__ u
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
     int kind = !cf[ax] ? 0 : (ax == a ? (df.per[ax] ? 1 : 2) : 3);
-    double gs = df.per[ax] ? 2.0 : -1.0;
+    float gs = df.per[ax] ? 2.0f : -1.0f;
     prolong_1d(kind, c[ax], dc.fe[a][ax], gs, s[ax]);
   }
-  double acc = 0.0;
+  T acc = T(0);
   for (int x = 0; x < s[0].cnt; ++x)
     for (int y = 0; y < s[1].cnt; ++y)
       for (int z = 0; z < s[2].cnt; ++z)
-        acc += s[0].w[x] * s[1].w[y] * s[2].w[z] *
-               (double)uc[dc.fo[a] + flat3(dc.fe[a], s[0].idx[x], s[1].idx[y], s[2].idx[z])];
+        acc += (T)(s[0].w[x] * s[1].w[y] * s[2].w[z]) *
+               uc[dc.fo[a] + flat3(dc.fe[a], s[0].idx[x], s[1].idx[y], s[2].idx[z])];
   uf[t] += (T)acc;
 }
 
@@ -368,11 +368,11 @@ __global__ void k_p_restrict(Dims df, Dims dc, int3 cz, const T* __restrict__ rf
   T1 s[3];
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) restrict_1d(cf[ax] ? 3 : 0, c[ax], df.n[ax], s[ax]);
-  double acc = 0.0;
+  T acc = T(0);
   for (int x = 0; x < s[0].cnt; ++x)
     for (int y = 0; y < s[1].cnt; ++y)
       for (int z = 0; z < s[2].cnt; ++z)
-        acc += s[0].w[x] * s[1].w[y] * s[2].w[z] * (double)rf[flat3(df.n, s[0].idx[x], s[1].idx[y], s[2].idx[z])];
+        acc += (T)(s[0].w[x] * s[1].w[y] * s[2].w[z]) * rf[flat3(df.n, s[0].idx[x], s[1].idx[y], s[2].idx[z])];
   rc[t] = (T)acc;
 }
 
@@ -395,7 +395,7 @@ __global__ void k_p_restrict_res(Dims df, Dims dc, int3 cz, const T* __restrict_
         T nb, dg;
         plap_parts(df, uf, fc, nb, dg);
         const i64 id = flat3(df.n, fc[0], fc[1], fc[2]);
-        acc += (float)(s[0].w[x] * s[1].w[y] * s[2].w[z]) * (float)(rhsf[id] - (dg * uf[id] - nb));
+        acc += (s[0].w[x] * s[1].w[y] * s[2].w[z]) * (float)(rhsf[id] - (dg * uf[id] - nb));
       }
   rc[t] = (T)acc;
 }
@@ -409,12 +409,12 @@ __global__ void k_p_prolong(Dims df, Dims dc, int3 cz, const T* __restrict__ uc,
   const int cf[3] = {cz.x, cz.y, cz.z};
   T1 s[3];
 #pragma unroll
-  for (int ax = 0; ax < 3; ++ax) prolong_1d(cf[ax] ? 3 : 0, c[ax], dc.n[ax], df.per[ax] ? 2.0 : 1.0, s[ax]);
-  double acc = 0.0;
+  for (int ax = 0; ax < 3; ++ax) prolong_1d(cf[ax] ? 3 : 0, c[ax], dc.n[ax], df.per[ax] ? 2.0f : 1.0f, s[ax]);
+  T acc = T(0);
   for (int x = 0; x < s[0].cnt; ++x)
     for (int y = 0; y < s[1].cnt; ++y)
       for (int z = 0; z < s[2].cnt; ++z)
-        acc += s[0].w[x] * s[1].w[y] * s[2].w[z] * (double)uc[flat3(dc.n, s[0].idx[x], s[1].idx[y], s[2].idx[z])];
+        acc += (T)(s[0].w[x] * s[1].w[y] * s[2].w[z]) * uc[flat3(dc.n, s[0].idx[x], s[1].idx[y], s[2].idx[z])];
   uf[t] += (T)acc;
 }
 
@@ -626,5 +626,349 @@ void add_grad(const Dims& d, const T* phi, T* v, cudaStream_t s) {
 INST(double)
 INST(float)
 #undef INST
+
+}  // namespace rbfib
+
+// ===================================================================
+// Lower part of a V-cycle in one thread-block cluster.
+// Every level from l0 down to the coarsest is small enough for one cluster
+// of 8 CTAs; the phases of the V-cycle (half sweeps, restriction, coarse
+// solve, prolongation) are separated by hardware cluster barriers instead of
+// kernel launches.  Loads go through L2 (ld.global.cg) so that values written
+// by other CTAs of the cluster before a barrier are seen after it.
+#include <cooperative_groups.h>
+
+namespace rbfib {
+namespace cgx = cooperative_groups;
+
+// Loads of the tail: from L2 (cluster variant, data written by other CTAs)
+// or plain (shared-memory variant).
+template <bool SH, typename T>
+RBFIB_DEVFN T ldt(const T* p) {
+  if constexpr (SH) return *p; else return __ldcg(p);
+}
+template <typename T>
+RBFIB_DEVFN T ldg2(const T* p) { return __ldcg(p); }
+
+template <bool SH, typename T>
+RBFIB_DEVFN void lap_parts_c(const Dims& d, const T* v, int a, const int c[3], T& nbsum, T& diag) {
+  nbsum = T(0);
+  diag = T(0);
+  const i64 base = d.fo[a];
+  const int* e = d.fe[a];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const T ih2 = inv_h2<T>(d, ax);
+    diag += T(2) * ih2;
+    int lo[3] = {c[0], c[1], c[2]}, hi[3] = {c[0], c[1], c[2]};
+    lo[ax] -= 1; hi[ax] += 1;
+    if (d.per[ax]) {
+      if (lo[ax] < 0) lo[ax] += e[ax];
+      if (hi[ax] >= e[ax]) hi[ax] -= e[ax];
+      nbsum += (ldt<SH>(v + base + flat3(e, lo[0], lo[1], lo[2])) + ldt<SH>(v + base + flat3(e, hi[0], hi[1], hi[2]))) * ih2;
+    } else {
+      if (lo[ax] >= 0) nbsum += ldt<SH>(v + base + flat3(e, lo[0], lo[1], lo[2])) * ih2;
+      else if (ax != a) diag += ih2;
+      if (hi[ax] < e[ax]) nbsum += ldt<SH>(v + base + flat3(e, hi[0], hi[1], hi[2])) * ih2;
+      else if (ax != a) diag += ih2;
+    }
+  }
+}
+
+template <bool SH, typename T>
+RBFIB_DEVFN void plap_parts_c(const Dims& d, const T* p, const int c[3], T& nbsum, T& diag) {
+  nbsum = T(0); diag = T(0);
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const T ih2 = inv_h2<T>(d, ax);
+    int lo[3] = {c[0], c[1], c[2]}, hi[3] = {c[0], c[1], c[2]};
+    lo[ax] -= 1; hi[ax] += 1;
+    if (d.per[ax]) {
+      if (lo[ax] < 0) lo[ax] += d.n[ax];
+      if (hi[ax] >= d.n[ax]) hi[ax] -= d.n[ax];
+      nbsum += (ldt<SH>(p + flat3(d.n, lo[0], lo[1], lo[2])) + ldt<SH>(p + flat3(d.n, hi[0], hi[1], hi[2]))) * ih2;
+      diag += T(2) * ih2;
+    } else {
+      if (lo[ax] >= 0) { nbsum += ldt<SH>(p + flat3(d.n, lo[0], lo[1], lo[2])) * ih2; diag += ih2; }
+      if (hi[ax] < d.n[ax]) { nbsum += ldt<SH>(p + flat3(d.n, hi[0], hi[1], hi[2])) * ih2; diag += ih2; }
+    }
+  }
+}
+
+constexpr int kTailCtas = 8;
+constexpr int kTailThreads = 1024;
+
+// Body of the lower V-cycle for the face grids.  u[l], rhs[l]: level arrays
+// (global or shared), barrier: cluster or block synchronisation.
+template <bool SH, typename T, typename Sync>
+RBFIB_DEVFN void vel_tail_body(const TailParams& P, T* const* u, T* const* rhs, T eta, unsigned tid, unsigned nthr,
+                               Sync sync) {
+  auto half = [&](int l, int color) {
+    const TailLevel& L = P.lev[l];
+    const unsigned cnt = L.cm.cnt[0] + L.cm.cnt[1] + L.cm.cnt[2];
+    for (unsigned t = tid; t < cnt; t += nthr) {
+      int a, c[3];
+      if (!color_face(L.d, L.cm, t, color, a, c)) continue;
+      T nb, dg;
+      lap_parts_c<SH>(L.d, u[l], a, c, nb, dg);
+      const i64 id = L.d.fo[a] + flat3(L.d.fe[a], c[0], c[1], c[2]);
+      u[l][id] = (ldt<SH>(rhs[l] + id) / eta + nb) / dg;
+    }
+    sync();
+  };
+  for (int l = P.l0; l < P.L - 1; ++l) {
+    const TailLevel& L = P.lev[l];
+    for (unsigned t = tid; t < (unsigned)L.d.fo[3]; t += nthr) {
+      int a, c[3];
+      decode_face(L.d, t, a, c);
+      u[l][t] = (((c[0] + c[1] + c[2]) & 1) == 0) ? ldt<SH>(rhs[l] + t) / (eta * lap_diag<T>(L.d, a, c)) : T(0);
+    }
+    sync();
+    half(l, 1);
+    for (int s = 1; s < P.nu; ++s) { half(l, 0); half(l, 1); }
+    const TailLevel& C = P.lev[l + 1];
+    for (unsigned t = tid; t < (unsigned)C.d.fo[3]; t += nthr) {
+      int a, c[3];
+      decode_face(C.d, t, a, c);
+      const int cf[3] = {L.cz.x, L.cz.y, L.cz.z};
+      T1 s[3];
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        int kind = !cf[ax] ? 0 : (ax == a ? (L.d.per[ax] ? 1 : 2) : 3);
+        restrict_1d(kind, c[ax], L.d.fe[a][ax], s[ax]);
+      }
+      float acc = 0.f;
+      for (int x = 0; x < s[0].cnt; ++x)
+        for (int y = 0; y < s[1].cnt; ++y)
+          for (int z = 0; z < s[2].cnt; ++z) {
+            const int fc[3] = {s[0].idx[x], s[1].idx[y], s[2].idx[z]};
+            T nb, dg;
+            lap_parts_c<SH>(L.d, (const T*)u[l], a, fc, nb, dg);
+            const i64 id = L.d.fo[a] + flat3(L.d.fe[a], fc[0], fc[1], fc[2]);
+            const T r = ldt<SH>(rhs[l] + id) - eta * (dg * ldt<SH>(u[l] + id) - nb);
+            acc += (s[0].w[x] * s[1].w[y] * s[2].w[z]) * (float)r;
+          }
+      rhs[l + 1][t] = (T)acc;
+    }
+    sync();
+  }
+  {
+    const int l = P.L - 1;
+    for (unsigned t = tid; t < (unsigned)P.lev[l].d.fo[3]; t += nthr) u[l][t] = T(0);
+    sync();
+    for (int s = 0; s < P.sweeps; ++s) { half(l, 0); half(l, 1); }
+  }
+  for (int l = P.L - 2; l >= P.l0; --l) {
+    const TailLevel& L = P.lev[l];
+    const TailLevel& C = P.lev[l + 1];
+    for (unsigned t = tid; t < (unsigned)L.d.fo[3]; t += nthr) {
+      int a, c[3];
+      decode_face(L.d, t, a, c);
+      const int cf[3] = {L.cz.x, L.cz.y, L.cz.z};
+      T1 s[3];
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        int kind = !cf[ax] ? 0 : (ax == a ? (L.d.per[ax] ? 1 : 2) : 3);
+        prolong_1d(kind, c[ax], C.d.fe[a][ax], L.d.per[ax] ? 2.0f : -1.0f, s[ax]);
+      }
+      float acc = 0.f;
+      for (int x = 0; x < s[0].cnt; ++x)
+        for (int y = 0; y < s[1].cnt; ++y)
+          for (int z = 0; z < s[2].cnt; ++z)
+            acc += (s[0].w[x] * s[1].w[y] * s[2].w[z]) *
+                   (float)ldt<SH>(u[l + 1] + C.d.fo[a] + flat3(C.d.fe[a], s[0].idx[x], s[1].idx[y], s[2].idx[z]));
+      u[l][t] = ldt<SH>(u[l] + t) + (T)acc;
+    }
+    sync();
+    for (int s = 0; s < P.nu; ++s) { half(l, 1); half(l, 0); }
+  }
+}
+
+template <bool SH, typename T, typename Sync>
+RBFIB_DEVFN void p_tail_body(const TailParams& P, T* const* u, T* const* rhs, unsigned tid, unsigned nthr, Sync sync) {
+  auto half = [&](int l, int color) {
+    const TailLevel& L = P.lev[l];
+    for (unsigned t = tid; t < L.cm.cnt[0]; t += nthr) {
+      int c[3];
+      if (!color_cell(L.d, L.cm, t, color, c)) continue;
+      T nb, dg;
+      plap_parts_c<SH>(L.d, u[l], c, nb, dg);
+      const i64 id = flat3(L.d.n, c[0], c[1], c[2]);
+      u[l][id] = (ldt<SH>(rhs[l] + id) + nb) / dg;
+    }
+    sync();
+  };
+  for (int l = P.l0; l < P.L - 1; ++l) {
+    const TailLevel& L = P.lev[l];
+    for (unsigned t = tid; t < (unsigned)L.d.nc; t += nthr) {
+      int c[3];
+      decode_cell(L.d, t, c);
+      u[l][t] = (((c[0] + c[1] + c[2]) & 1) == 0) ? ldt<SH>(rhs[l] + t) / plap_diag<T>(L.d, c) : T(0);
+    }
+    sync();
+    half(l, 1);
+    for (int s = 1; s < P.nu; ++s) { half(l, 0); half(l, 1); }
+    const TailLevel& C = P.lev[l + 1];
+    for (unsigned t = tid; t < (unsigned)C.d.nc; t += nthr) {
+      int c[3];
+      decode_cell(C.d, t, c);
+      const int cf[3] = {L.cz.x, L.cz.y, L.cz.z};
+      T1 s[3];
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) restrict_1d(cf[ax] ? 3 : 0, c[ax], L.d.n[ax], s[ax]);
+      float acc = 0.f;
+      for (int x = 0; x < s[0].cnt; ++x)
+        for (int y = 0; y < s[1].cnt; ++y)
+          for (int z = 0; z < s[2].cnt; ++z) {
+            const int fc[3] = {s[0].idx[x], s[1].idx[y], s[2].idx[z]};
+            T nb, dg;
+            plap_parts_c<SH>(L.d, (const T*)u[l], fc, nb, dg);
+            const i64 id = flat3(L.d.n, fc[0], fc[1], fc[2]);
+            acc += (s[0].w[x] * s[1].w[y] * s[2].w[z]) * (float)(ldt<SH>(rhs[l] + id) - (dg * ldt<SH>(u[l] + id) - nb));
+          }
+      rhs[l + 1][t] = (T)acc;
+    }
+    sync();
+  }
+  {
+    const int l = P.L - 1;
+    const unsigned n = (unsigned)P.lev[l].d.nc;
+    if (tid == 0) {
+      double sm = 0.0;
+      for (unsigned t = 0; t < n; ++t) sm += (double)ldt<SH>(rhs[l] + t);
+      const T mean = (T)(sm / (double)n);
+      for (unsigned t = 0; t < n; ++t) rhs[l][t] = ldt<SH>(rhs[l] + t) - mean;
+    }
+    for (unsigned t = tid; t < n; t += nthr) u[l][t] = T(0);
+    sync();
+    for (int s = 0; s < P.sweeps; ++s) { half(l, 0); half(l, 1); }
+  }
+  for (int l = P.L - 2; l >= P.l0; --l) {
+    const TailLevel& L = P.lev[l];
+    const TailLevel& C = P.lev[l + 1];
+    for (unsigned t = tid; t < (unsigned)L.d.nc; t += nthr) {
+      int c[3];
+      decode_cell(L.d, t, c);
+      const int cf[3] = {L.cz.x, L.cz.y, L.cz.z};
+      T1 s[3];
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) prolong_1d(cf[ax] ? 3 : 0, c[ax], C.d.n[ax], L.d.per[ax] ? 2.0f : 1.0f, s[ax]);
+      float acc = 0.f;
+      for (int x = 0; x < s[0].cnt; ++x)
+        for (int y = 0; y < s[1].cnt; ++y)
+          for (int z = 0; z < s[2].cnt; ++z)
+            acc += (s[0].w[x] * s[1].w[y] * s[2].w[z]) *
+                   (float)ldt<SH>(u[l + 1] + flat3(C.d.n, s[0].idx[x], s[1].idx[y], s[2].idx[z]));
+      u[l][t] = ldt<SH>(u[l] + t) + (T)acc;
+    }
+    sync();
+    for (int s = 0; s < P.nu; ++s) { half(l, 1); half(l, 0); }
+  }
+}
+
+// Cluster variant: level arrays in global memory, cluster barriers.
+template <typename T>
+__global__ void __cluster_dims__(kTailCtas, 1, 1) __launch_bounds__(kTailThreads)
+k_vel_tail(TailParams P, T eta) {
+  cgx::cluster_group cl = cgx::this_cluster();
+  T* u[kMaxTail];
+  T* r[kMaxTail];
+  for (int l = 0; l < kMaxTail; ++l) { u[l] = (T*)P.lev[l].u; r[l] = (T*)P.lev[l].rhs; }
+  vel_tail_body<false, T>(P, u, r, eta, blockIdx.x * kTailThreads + threadIdx.x, kTailCtas * kTailThreads,
+                          [&]() { cl.sync(); });
+}
+
+template <typename T>
+__global__ void __cluster_dims__(kTailCtas, 1, 1) __launch_bounds__(kTailThreads)
+k_p_tail(TailParams P) {
+  cgx::cluster_group cl = cgx::this_cluster();
+  T* u[kMaxTail];
+  T* r[kMaxTail];
+  for (int l = 0; l < kMaxTail; ++l) { u[l] = (T*)P.lev[l].u; r[l] = (T*)P.lev[l].rhs; }
+  p_tail_body<false, T>(P, u, r, blockIdx.x * kTailThreads + threadIdx.x, kTailCtas * kTailThreads,
+                        [&]() { cl.sync(); });
+}
+
+// Shared-memory variant (one CTA): every tail level lives in shared memory;
+// the top level's right-hand side is loaded from global memory and its
+// solution written back.
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads) k_vel_tail_smem(TailParams P, T eta) {
+  extern __shared__ unsigned char shraw[];
+  T* u[kMaxTail];
+  T* r[kMaxTail];
+  T* p = (T*)shraw;
+  for (int l = P.l0; l < P.L; ++l) {
+    const i64 n = P.lev[l].d.fo[3];
+    u[l] = p; p += n;
+    r[l] = p; p += n;
+  }
+  const i64 n0 = P.lev[P.l0].d.fo[3];
+  const T* g_rhs = (const T*)P.lev[P.l0].rhs;
+  for (i64 t = threadIdx.x; t < n0; t += blockDim.x) r[P.l0][t] = g_rhs[t];
+  __syncthreads();
+  vel_tail_body<true, T>(P, u, r, eta, threadIdx.x, blockDim.x, []() { __syncthreads(); });
+  T* g_u = (T*)P.lev[P.l0].u;
+  for (i64 t = threadIdx.x; t < n0; t += blockDim.x) g_u[t] = u[P.l0][t];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads) k_p_tail_smem(TailParams P) {
+  extern __shared__ unsigned char shraw[];
+  T* u[kMaxTail];
+  T* r[kMaxTail];
+  T* p = (T*)shraw;
+  for (int l = P.l0; l < P.L; ++l) {
+    const i64 n = P.lev[l].d.nc;
+    u[l] = p; p += n;
+    r[l] = p; p += n;
+  }
+  const i64 n0 = P.lev[P.l0].d.nc;
+  const T* g_rhs = (const T*)P.lev[P.l0].rhs;
+  for (i64 t = threadIdx.x; t < n0; t += blockDim.x) r[P.l0][t] = g_rhs[t];
+  __syncthreads();
+  p_tail_body<true, T>(P, u, r, threadIdx.x, blockDim.x, []() { __syncthreads(); });
+  T* g_u = (T*)P.lev[P.l0].u;
+  for (i64 t = threadIdx.x; t < n0; t += blockDim.x) g_u[t] = u[P.l0][t];
+}
+
+size_t tail_smem_bytes(const TailParams& P, bool faces, size_t elem) {
+  size_t n = 0;
+  for (int l = P.l0; l < P.L; ++l) n += 2 * (size_t)(faces ? P.lev[l].d.fo[3] : P.lev[l].d.nc);
+  return n * elem;
+}
+
+template <typename T>
+void vel_tail(const TailParams& P, T eta, cudaStream_t s) {
+  const size_t shm = tail_smem_bytes(P, true, sizeof(T));
+  if (shm <= kTailSmemBytes) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_vel_tail_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemBytes);
+      attr = true;
+    }
+    k_vel_tail_smem<T><<<1, kTailThreads, shm, s>>>(P, eta);
+  } else {
+    k_vel_tail<T><<<kTailCtas, kTailThreads, 0, s>>>(P, eta);
+  }
+  note_launch();
+}
+template <typename T>
+void p_tail(const TailParams& P, cudaStream_t s) {
+  const size_t shm = tail_smem_bytes(P, false, sizeof(T));
+  if (shm <= kTailSmemBytes) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_p_tail_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemBytes);
+      attr = true;
+    }
+    k_p_tail_smem<T><<<1, kTailThreads, shm, s>>>(P);
+  } else {
+    k_p_tail<T><<<kTailCtas, kTailThreads, 0, s>>>(P);
+  }
+  note_launch();
+}
+template void vel_tail<float>(const TailParams&, float, cudaStream_t);
+template void p_tail<float>(const TailParams&, cudaStream_t);
 
 }  // namespace rbfib

@@ -70,6 +70,25 @@ template <typename T> void p_coarse(const Dims&, T* u, T* rhs, int sweeps, cudaS
 template <typename T> void div_q(const Dims&, T eta, const T* vt, const T* rpi, T* q, T* pi, cudaStream_t);
 template <typename T> void add_grad(const Dims&, const T* phi, T* v, cudaStream_t);
 
+// Lower part of a V-cycle in one 8-CTA cluster (k_stokes.cu)
+struct TailLevel {
+  Dims d;
+  int3 cz;
+  ColorMap cm;
+  void* u;
+  void* rhs;
+};
+constexpr int kMaxTail = 10;
+struct TailParams {
+  int l0, L, nu, sweeps;
+  TailLevel lev[kMaxTail];
+};
+constexpr long long kTailMaxUnknowns = 8LL * 1024 * 4;   // per level, faces or cells (cluster variant)
+constexpr size_t kTailSmemBytes = 200 * 1024;             // shared-memory variant limit
+size_t tail_smem_bytes(const TailParams& P, bool faces, size_t elem);
+template <typename T> void vel_tail(const TailParams&, T eta, cudaStream_t);
+template <typename T> void p_tail(const TailParams&, cudaStream_t);
+
 // k_ib.cu
 void geometry(int nbl, const int* bob, const double* ref, const double* q, const double* quat,
               double* r, double* arm, cudaStream_t);

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/rbfib.h"
@@ -247,7 +248,41 @@ const int kNu = 2;   // pre- and post-smoothing sweeps
 
 int coarse_sweeps(const Dims& d) { return 2 * std::max(d.n[0], std::max(d.n[1], d.n[2])) + 4; }
 
-// u0 <- V-cycle approximation of (-eta LL)^{-1} rhs0 (zero initial guess)
+// First level handled by the cluster tail: the first level whose unknowns
+// fit one 8-CTA cluster (every coarser level then fits too).
+// Prefer the shared-memory tail (levels l.. fit one CTA's shared memory); the
+// cluster tail only when some level still exceeds it.
+int tail_start(const std::vector<Level>& L, bool faces) {
+  const int n = (int)L.size();
+  for (int l = 0; l < n; ++l) {
+    if (n - l > kMaxTail) continue;
+    size_t bytes = 0;
+    for (int k = l; k < n; ++k) bytes += 2 * sizeof(float) * (size_t)(faces ? L[k].d.fo[3] : L[k].d.nc);
+    if (bytes <= kTailSmemBytes) return l;
+  }
+  return n - 1;
+}
+
+TailParams tail_params(rbfib_grid* g, int l0, const std::vector<void*>& u, const std::vector<void*>& rhs,
+                       bool faces) {
+  TailParams P{};
+  P.l0 = l0;
+  P.L = (int)g->levels.size();
+  P.nu = kNu;
+  P.sweeps = coarse_sweeps(g->levels[P.L - 1].d);
+  for (int l = l0; l < P.L; ++l) {
+    TailLevel& T = P.lev[l];
+    T.d = g->levels[l].d;
+    T.cz = g->levels[l].cz;
+    T.cm = faces ? make_color_map_faces(T.d) : make_color_map_cells(T.d);
+    T.u = u[l];
+    T.rhs = rhs[l];
+  }
+  return P;
+}
+
+// u0 <- V-cycle approximation of (-eta LL)^{-1} rhs0 (zero initial guess).
+// Levels above the tail run as separate kernels; the rest in one cluster.
 template <typename T>
 void vcycle_vel(rbfib_grid* g, T* u0, const T* rhs0) {
   MGStore<T>& M = mg_of<T>(g);
@@ -262,15 +297,25 @@ void vcycle_vel(rbfib_grid* g, T* u0, const T* rhs0) {
     TimerScope ts(g, l == 0 ? TK_SMOOTH : -1, 2.0 * (double)d.fo[3] * sizeof(T));
     vel_rbgs<T>(d, eta, color, u[l], rhs[l], g->s);
   };
-  for (int l = 0; l < L - 1; ++l) {
+  const int lt = std::is_same<T, float>::value && L <= kMaxTail ? tail_start(g->levels, true) : L - 1;
+  for (int l = 0; l < lt; ++l) {
     const Dims& d = g->levels[l].d;
     vel_first<T>(d, eta, u[l], rhs[l], g->s);          // zero guess + first colour-0 update
     smooth(l, 1);
     for (int s = 1; s < kNu; ++s) { smooth(l, 0); smooth(l, 1); }
     vel_restrict_res<T>(d, g->levels[l + 1].d, g->levels[l].cz, eta, u[l], rhs[l], rhs[l + 1], g->s);
   }
-  vel_coarse<T>(g->levels[L - 1].d, eta, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
-  for (int l = L - 2; l >= 0; --l) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (L <= kMaxTail) {
+      std::vector<void*> uu(u.begin(), u.end()), rr(rhs.begin(), rhs.end());
+      vel_tail<float>(tail_params(g, lt, uu, rr, true), eta, g->s);
+    } else {
+      vel_coarse<T>(g->levels[L - 1].d, eta, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
+    }
+  } else {
+    vel_coarse<T>(g->levels[L - 1].d, eta, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
+  }
+  for (int l = lt - 1; l >= 0; --l) {
     const Dims& d = g->levels[l].d;
     vel_prolong<T>(d, g->levels[l + 1].d, g->levels[l].cz, u[l + 1], u[l], g->s);
     for (int s = 0; s < kNu; ++s) { smooth(l, 1); smooth(l, 0); }
@@ -286,15 +331,25 @@ void vcycle_p(rbfib_grid* g, T* u0, T* rhs0) {
   for (int l = 0; l < L; ++l) { u[l] = *M.pu[l]; rhs[l] = *M.prhs[l]; }
   u[0] = u0;
   rhs[0] = rhs0;
-  for (int l = 0; l < L - 1; ++l) {
+  const int lt = std::is_same<T, float>::value && L <= kMaxTail ? tail_start(g->levels, false) : L - 1;
+  for (int l = 0; l < lt; ++l) {
     const Dims& d = g->levels[l].d;
     p_first<T>(d, u[l], rhs[l], g->s);
     p_rbgs<T>(d, 1, u[l], rhs[l], g->s);
     for (int s = 1; s < kNu; ++s) { p_rbgs<T>(d, 0, u[l], rhs[l], g->s); p_rbgs<T>(d, 1, u[l], rhs[l], g->s); }
     p_restrict_res<T>(d, g->levels[l + 1].d, g->levels[l].cz, u[l], rhs[l], rhs[l + 1], g->s);
   }
-  p_coarse<T>(g->levels[L - 1].d, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
-  for (int l = L - 2; l >= 0; --l) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (L <= kMaxTail) {
+      std::vector<void*> uu(u.begin(), u.end()), rr(rhs.begin(), rhs.end());
+      p_tail<float>(tail_params(g, lt, uu, rr, false), g->s);
+    } else {
+      p_coarse<T>(g->levels[L - 1].d, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
+    }
+  } else {
+    p_coarse<T>(g->levels[L - 1].d, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
+  }
+  for (int l = lt - 1; l >= 0; --l) {
     const Dims& d = g->levels[l].d;
     p_prolong<T>(d, g->levels[l + 1].d, g->levels[l].cz, u[l + 1], u[l], g->s);
     for (int s = 0; s < kNu; ++s) { p_rbgs<T>(d, 1, u[l], rhs[l], g->s); p_rbgs<T>(d, 0, u[l], rhs[l], g->s); }
@@ -861,6 +916,17 @@ int rbfib_set_bodies(rbfib_grid* g, int32_t n_bodies, const int32_t* blob_offset
     ck(cudaGetLastError());
   } catch (CudaError& e) {
     return fail(g, RBFIB_ECUDA, std::string("set_bodies: ") + cudaGetErrorString(e.e));
+  }
+  return RBFIB_OK;
+}
+
+int rbfib_apply_preconditioner(rbfib_grid* g, const double* r, double* z) {
+  if (!g || !r || !z) return fail(g, RBFIB_EINVAL, "apply_preconditioner: null argument");
+  try {
+    precond_any(g, r, z, true);
+    ck(cudaGetLastError());
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, std::string("apply_preconditioner: ") + cudaGetErrorString(e.e));
   }
   return RBFIB_OK;
 }
