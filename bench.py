@@ -39,6 +39,10 @@ def parse():
     ap.add_argument("--roofline-kernel", default="dot", choices=list(TIMER_NAMES))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rhs", type=int, default=16)
+    ap.add_argument("--ensemble", type=int, default=0,
+                    help="also time a batched ensemble of this many systems (0: skip)")
+    ap.add_argument("--ensemble-steps", type=int, default=2)
+    ap.add_argument("--workers", type=int, default=16)
     return ap.parse_args()
 
 
@@ -155,6 +159,43 @@ def run_reference(args):
                              "sample": vals[0]["sample"] + f"; {args.steps} samples in {wall:.1f} s"},
             "e2e": {"value": value, "unit": "SEM steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- ensemble
+def run_ensemble(args, B, torch):
+    """Batched ensemble: independent cuboids n ~ U{16, 20, ..., 48} with 1-16
+    12-blob spheres, one SEM step of every system per batch step; FP32-refined
+    and plain FP64 at the same relative residual 1e-8."""
+    import workloads
+    out = {}
+    ws = workloads.batched_ensemble(args.ensemble)
+    for label, prec in (("fp32_refined", B.FP32_REFINED), ("fp64", B.FP64)):
+        t0 = time.perf_counter()
+        batch = B.Batch(ws, precision=prec, workers=args.workers)
+        setup = time.perf_counter() - t0
+        q = [torch.tensor(w.q.ravel(), device="cuda") for w in ws]
+        quat = [torch.tensor(w.quat.ravel(), device="cuda") for w in ws]
+        params = [B.sem_params(w.potentials, dt=w.dt, kT=w.kT) for w in ws]
+        seeds = [w.seed + 31 * i for i, w in enumerate(ws)]
+        batch.sem_step(params, seeds, 0, q, quat)            # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        iters = 0
+        for k in range(args.ensemble_steps):
+            status, infos = batch.sem_step(params, seeds, k + 1, q, quat)
+            iters += sum(i[key]["iterations"] for i in infos for key in ("solve_rfd", "solve_stokes", "solve_main"))
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[label] = {"value": args.ensemble * args.ensemble_steps / dt, "unit": "systems*steps/s",
+                      "ms_per_batch_step": 1000.0 * dt / args.ensemble_steps, "setup_s": setup,
+                      "krylov_iterations_per_system_step": iters / (args.ensemble * args.ensemble_steps)}
+        batch.close()
+        del q, quat
+        torch.cuda.empty_cache()
+    out["systems"] = args.ensemble
+    out["workers"] = args.workers
+    out["mean_cells"] = float(sum(w.n[0] * w.n[1] * w.n[2] for w in ws) / len(ws))
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -279,6 +320,23 @@ def run_ours(args):
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
             "krylov_iterations_per_step": [list(map(int, np.mean(np.array(state["iters"]), axis=0)))] if state["iters"] else None,
             "rejected_steps": state["rejects"], "wall_s": t_wall}
+    # same workload with FP32 kernels inside FP64 refinement (same 1e-8)
+    gr = B.grid_for(w, precision=B.FP32_REFINED, rtol=1e-8)
+    qr, quatr = torch.tensor(w.q.ravel(), device="cuda"), torch.tensor(w.quat.ravel(), device="cuda")
+    for k in range(2):
+        gr.sem_step(p, seed, 10_000 + k, 0, qr, quatr)
+    torch.cuda.synchronize()
+    er0, er1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    er0.record(stream)
+    for k in range(args.steps):
+        gr.sem_step(p, seed, 20_000 + k, 0, qr, quatr)
+    er1.record(stream)
+    torch.cuda.synchronize()
+    line["refined_vs_fp64"] = {"fp32_refined_steps_per_s": args.steps / (er0.elapsed_time(er1) / 1000.0),
+                               "fp64_steps_per_s": value / world, "rtol": 1e-8}
+    line["autotuned_blocks"] = dict(zip(["stokes_fp64", "stokes_fp32", "vel_sweep", "p_sweep"], g.tuned_blocks()))
+    if args.ensemble:
+        line["ensemble"] = run_ensemble(args, B, torch)
     if world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample(w, args.cpu_sample_rhs)
         cb.pop("sample_seconds", None)

@@ -156,6 +156,34 @@ int rbfib_stokes_solve(rbfib_grid* g, const double* f, double* v, double* pi,
 int rbfib_sem_step(rbfib_grid* g, const rbfib_sem_params* p, uint64_t seed, uint64_t step,
                    uint32_t attempt, double* q, double* quat, rbfib_step_info* info);
 
+/* ---- ensembles of independent systems ------------------------------------ */
+
+/* An ensemble of independent suspensions (the many independent trajectories
+ * of Sec. V), e.g. cuboids of different sizes.  System i gets a grid created
+ * from descs[i] (host array of n_sys descriptors) and bound to worker stream
+ * i % n_workers; the batch owns the streams and the grids.  Set each
+ * system's bodies with rbfib_set_bodies(rbfib_batch_grid(b, i), ...). */
+typedef struct rbfib_batch rbfib_batch;
+int rbfib_create_batch(int32_t n_sys, const rbfib_grid_desc* descs, int32_t n_workers, rbfib_batch** out);
+void rbfib_destroy_batch(rbfib_batch* b);
+rbfib_grid* rbfib_batch_grid(rbfib_batch* b, int32_t sys);   /* NULL if out of range */
+
+/* One Split-Euler-Maruyama step of every system (Algorithm 1): system i uses
+ * params[i], seeds[i], attempts[i] (NULL = 0) and its device configuration
+ * q[i], quat[i] (host arrays of device pointers).  Workers run concurrently
+ * on their own host threads and streams.  status[i] receives each system's
+ * rbfib_sem_step status (RBFIB_EREJECT leaves that system unchanged); infos
+ * may be NULL.  Returns the first status other than OK / EREJECT, else OK.
+ * Synchronises every worker stream. */
+int rbfib_batch_sem_step(rbfib_batch* b, const rbfib_sem_params* params, const uint64_t* seeds, uint64_t step,
+                         const uint32_t* attempts, double* const* q, double* const* quat, rbfib_step_info* infos,
+                         int32_t* status);
+
+/* Threads per block the autotuner picked for this grid's finest-level
+ * kernels: out[0] FP64 Stokes operator, out[1] FP32 Stokes operator, out[2]
+ * velocity smoothing sweep, out[3] pressure smoothing sweep. */
+int rbfib_tuned_blocks(const rbfib_grid* g, int32_t out[4]);
+
 /* ---- building blocks of the hot path, exposed for parity checks ---------- */
 
 /* Blob-to-cell counting sort of the current bodies: perm (device int32 N_bl)

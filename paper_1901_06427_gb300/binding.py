@@ -85,6 +85,13 @@ def lib():
             "rbfib_stochastic_forcing_static": ([ctypes.POINTER(GridDesc), D, D, U64, U64, U32, P, P,
                                                  ctypes.c_char_p, ctypes.c_size_t], I32),
             "rbfib_launch_count": ([], U64),
+            "rbfib_tuned_blocks": ([P, ctypes.POINTER(ctypes.c_int32)], I32),
+            "rbfib_create_batch": ([I32, ctypes.POINTER(GridDesc), I32, ctypes.POINTER(P)], I32),
+            "rbfib_destroy_batch": ([P], None),
+            "rbfib_batch_grid": ([P, I32], P),
+            "rbfib_batch_sem_step": ([P, ctypes.POINTER(SemParams), ctypes.POINTER(U64), U64, ctypes.POINTER(U32),
+                                      ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(StepInfo),
+                                      ctypes.POINTER(ctypes.c_int32)], I32),
             "rbfib_kernel_timer": ([P, I32], I32),
             "rbfib_kernel_timer_read": ([P, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D)], I32),
         }
@@ -198,6 +205,7 @@ class Grid:
         ref = torch.as_tensor(np.asarray(ref_blobs), dtype=torch.float64, device=dev).contiguous()
         q = torch.as_tensor(np.asarray(q) if not isinstance(q, torch.Tensor) else q, dtype=torch.float64, device=dev).contiguous()
         quat = torch.as_tensor(np.asarray(quat) if not isinstance(quat, torch.Tensor) else quat, dtype=torch.float64, device=dev).contiguous()
+        torch.cuda.current_stream().synchronize()   # the library may copy on another stream
         self._check(lib().rbfib_set_bodies(
             self._h, nb, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
             _ptr(ref, numel=3 * nbl, name="ref_blobs") if nbl else None,
@@ -302,10 +310,95 @@ class Grid:
         self._check(lib().rbfib_kernel_timer_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
         return ms.value, n.value, b.value
 
+    def tuned_blocks(self):
+        out = (ctypes.c_int32 * 4)()
+        self._check(lib().rbfib_tuned_blocks(self._h, out))
+        return list(out)
+
     def body_forces(self, params):
         out = torch.empty(6 * max(self.n_bodies, 1), dtype=torch.float64, device="cuda")
         self._check(lib().rbfib_body_forces(self._h, ctypes.byref(params), _ptr(out)))
         return out[:6 * self.n_bodies]
+
+
+class _BatchMember(Grid):
+    """A grid owned by a Batch (not created or destroyed here)."""
+
+    def __init__(self, handle, desc, n):
+        self._h = handle
+        self.desc = desc
+        self.n = tuple(n)
+        self.n_bodies = 0
+        self.n_blobs = 0
+
+    def close(self):
+        self._h = None
+
+
+def _desc(n, h=1.0, eta=1.0, periodic=(False, False, False), wall_vel=None, precision=FP64, restart=30,
+          max_iter=2000, rtol=1e-8):
+    d = GridDesc()
+    for a in range(3):
+        d.n[a] = int(n[a])
+        d.periodic[a] = int(bool(periodic[a]))
+    d.h, d.eta = float(h), float(eta)
+    wv = np.zeros((6, 3)) if wall_vel is None else np.asarray(wall_vel, dtype=np.float64).reshape(6, 3)
+    for w in range(6):
+        for c in range(3):
+            d.wall_vel[w][c] = float(wv[w, c])
+    d.kernel, d.precision, d.restart, d.max_iter, d.rtol = 3, int(precision), int(restart), int(max_iter), float(rtol)
+    return d
+
+
+class Batch:
+    """An ensemble of independent systems advanced together (C ABI
+    rbfib_create_batch / rbfib_batch_sem_step)."""
+
+    def __init__(self, workloads_, precision=None, workers=8, restart=30, max_iter=4000):
+        n = len(workloads_)
+        descs = (GridDesc * n)()
+        for i, w in enumerate(workloads_):
+            prec = precision if precision is not None else (FP32_REFINED if w.precision == "f32-refined" else FP64)
+            descs[i] = _desc(w.n, w.h, w.eta, w.periodic, w.wall_vel, prec, restart, max_iter, w.rtol)
+        h = ctypes.c_void_p()
+        st = lib().rbfib_create_batch(n, descs, int(workers), ctypes.byref(h))
+        if st != OK:
+            raise RbfibError(st, "create_batch failed")
+        self._h = h
+        self.systems = []
+        for i, w in enumerate(workloads_):
+            m = _BatchMember(lib().rbfib_batch_grid(self._h, i), descs[i], w.n)
+            m.set_bodies(w.blob_offsets, w.ref_blobs, w.q, w.quat)
+            self.systems.append(m)
+        self.n = n
+
+    def sem_step(self, params, seeds, step, q, quat, attempts=None):
+        n = self.n
+        P = (SemParams * n)(*params)
+        S = (ctypes.c_uint64 * n)(*[int(s) for s in seeds])
+        A = (ctypes.c_uint32 * n)(*([0] * n if attempts is None else [int(a) for a in attempts]))
+        Q = (ctypes.c_void_p * n)(*[_ptr(t, numel=3 * m.n_bodies, name="q") for t, m in zip(q, self.systems)])
+        QT = (ctypes.c_void_p * n)(*[_ptr(t, numel=4 * m.n_bodies, name="quat") for t, m in zip(quat, self.systems)])
+        infos = (StepInfo * n)()
+        status = (ctypes.c_int32 * n)()
+        torch.cuda.current_stream().synchronize()   # inputs are read on the worker streams
+        st = lib().rbfib_batch_sem_step(self._h, P, S, int(step), A, Q, QT, infos, status)
+        if st != OK:
+            raise RbfibError(st, "batch_sem_step failed")
+        return list(status), [i.as_dict() for i in infos]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for m in self.systems:
+                m._h = None
+            lib().rbfib_destroy_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def grid_for(workload, precision=None, restart=30, max_iter=4000, rtol=None):

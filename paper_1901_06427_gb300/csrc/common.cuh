@@ -229,8 +229,10 @@ __device__ inline void philox_normals4(unsigned long long seed, unsigned long lo
 
 #define RBFIB_DEVFN __device__ __forceinline__
 
+#include <atomic>
 namespace rbfib {
-// Count of kernel launches issued by the library (host side, all grids).
-extern unsigned long long g_launches;
-inline void note_launch() { ++g_launches; }
+// Count of kernel launches issued by the library (host side, all grids and
+// threads).
+extern std::atomic<unsigned long long> g_launches;
+inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 }  // namespace rbfib

@@ -516,15 +516,15 @@ __global__ void k_add_grad(Dims d, const T* __restrict__ phi, T* __restrict__ v)
 static inline unsigned nblk(i64 n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 template <typename T>
-void stokes_apply(const Dims& d, T eta, const T* v, const T* p, T* yv, T* yp, cudaStream_t s) {
+void stokes_apply(const Dims& d, T eta, const T* v, const T* p, T* yv, T* yp, cudaStream_t s, int bs) {
   const i64 n = d.fo[3] + d.nc;
-  k_stokes_apply<T><<<nblk(n, 256), 256, 0, s>>>(d, eta, v, p, yv, yp);
+  k_stokes_apply<T><<<nblk(n, bs), bs, 0, s>>>(d, eta, v, p, yv, yp);
   note_launch();
 }
 template <typename T>
-void vel_rbgs(const Dims& d, T eta, int color, T* u, const T* rhs, cudaStream_t s) {
+void vel_rbgs(const Dims& d, T eta, int color, T* u, const T* rhs, cudaStream_t s, int bs) {
   const ColorMap m = make_color_map_faces(d);
-  k_vel_rbgs<T><<<nblk((i64)m.cnt[0] + m.cnt[1] + m.cnt[2], 256), 256, 0, s>>>(d, m, eta, color, u, rhs);
+  k_vel_rbgs<T><<<nblk((i64)m.cnt[0] + m.cnt[1] + m.cnt[2], bs), bs, 0, s>>>(d, m, eta, color, u, rhs);
   note_launch();
 }
 template <typename T>
@@ -559,9 +559,9 @@ void vel_coarse(const Dims& d, T eta, T* u, const T* rhs, int sweeps, cudaStream
   note_launch();
 }
 template <typename T>
-void p_rbgs(const Dims& d, int color, T* u, const T* rhs, cudaStream_t s) {
+void p_rbgs(const Dims& d, int color, T* u, const T* rhs, cudaStream_t s, int bs) {
   const ColorMap m = make_color_map_cells(d);
-  k_p_rbgs<T><<<nblk(m.cnt[0], 256), 256, 0, s>>>(d, m, color, u, rhs);
+  k_p_rbgs<T><<<nblk(m.cnt[0], bs), bs, 0, s>>>(d, m, color, u, rhs);
   note_launch();
 }
 template <typename T>
@@ -606,8 +606,8 @@ void add_grad(const Dims& d, const T* phi, T* v, cudaStream_t s) {
 }
 
 #define INST(T)                                                                                  \
-  template void stokes_apply<T>(const Dims&, T, const T*, const T*, T*, T*, cudaStream_t);       \
-  template void vel_rbgs<T>(const Dims&, T, int, T*, const T*, cudaStream_t);                    \
+  template void stokes_apply<T>(const Dims&, T, const T*, const T*, T*, T*, cudaStream_t, int);  \
+  template void vel_rbgs<T>(const Dims&, T, int, T*, const T*, cudaStream_t, int);               \
   template void vel_first<T>(const Dims&, T, T*, const T*, cudaStream_t);                         \
   template void vel_restrict_res<T>(const Dims&, const Dims&, int3, T, const T*, const T*, T*, cudaStream_t); \
   template void p_first<T>(const Dims&, T*, const T*, cudaStream_t);                              \
@@ -616,7 +616,7 @@ void add_grad(const Dims& d, const T* phi, T* v, cudaStream_t s) {
   template void vel_restrict<T>(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);     \
   template void vel_prolong<T>(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);      \
   template void vel_coarse<T>(const Dims&, T, T*, const T*, int, cudaStream_t);                  \
-  template void p_rbgs<T>(const Dims&, int, T*, const T*, cudaStream_t);                         \
+  template void p_rbgs<T>(const Dims&, int, T*, const T*, cudaStream_t, int);                    \
   template void p_residual<T>(const Dims&, const T*, const T*, T*, cudaStream_t);                \
   template void p_restrict<T>(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);       \
   template void p_prolong<T>(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);        \
@@ -637,6 +637,7 @@ INST(float)
 // kernel launches.  Loads go through L2 (ld.global.cg) so that values written
 // by other CTAs of the cluster before a barrier are seen after it.
 #include <cooperative_groups.h>
+#include <mutex>
 
 namespace rbfib {
 namespace cgx = cooperative_groups;
@@ -942,11 +943,10 @@ template <typename T>
 void vel_tail(const TailParams& P, T eta, cudaStream_t s) {
   const size_t shm = tail_smem_bytes(P, true, sizeof(T));
   if (shm <= kTailSmemBytes) {
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag once;
+    std::call_once(once, [] {
       cudaFuncSetAttribute(k_vel_tail_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemBytes);
-      attr = true;
-    }
+    });
     k_vel_tail_smem<T><<<1, kTailThreads, shm, s>>>(P, eta);
   } else {
     k_vel_tail<T><<<kTailCtas, kTailThreads, 0, s>>>(P, eta);
@@ -957,11 +957,10 @@ template <typename T>
 void p_tail(const TailParams& P, cudaStream_t s) {
   const size_t shm = tail_smem_bytes(P, false, sizeof(T));
   if (shm <= kTailSmemBytes) {
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag once;
+    std::call_once(once, [] {
       cudaFuncSetAttribute(k_p_tail_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemBytes);
-      attr = true;
-    }
+    });
     k_p_tail_smem<T><<<1, kTailThreads, shm, s>>>(P);
   } else {
     k_p_tail<T><<<kTailCtas, kTailThreads, 0, s>>>(P);

@@ -50,8 +50,9 @@ struct StressLayout {
 };
 
 // k_stokes.cu
-template <typename T> void stokes_apply(const Dims&, T eta, const T* v, const T* p, T* yv, T* yp, cudaStream_t);
-template <typename T> void vel_rbgs(const Dims&, T eta, int color, T* u, const T* rhs, cudaStream_t);
+template <typename T> void stokes_apply(const Dims&, T eta, const T* v, const T* p, T* yv, T* yp, cudaStream_t,
+                                        int block = 256);
+template <typename T> void vel_rbgs(const Dims&, T eta, int color, T* u, const T* rhs, cudaStream_t, int block = 256);
 template <typename T> void vel_first(const Dims&, T eta, T* u, const T* rhs, cudaStream_t);
 template <typename T> void vel_restrict_res(const Dims&, const Dims&, int3, T eta, const T* uf, const T* rhsf,
                                             T* rc, cudaStream_t);
@@ -62,7 +63,7 @@ template <typename T> void vel_residual(const Dims&, T eta, const T* u, const T*
 template <typename T> void vel_restrict(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);
 template <typename T> void vel_prolong(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);
 template <typename T> void vel_coarse(const Dims&, T eta, T* u, const T* rhs, int sweeps, cudaStream_t);
-template <typename T> void p_rbgs(const Dims&, int color, T* u, const T* rhs, cudaStream_t);
+template <typename T> void p_rbgs(const Dims&, int color, T* u, const T* rhs, cudaStream_t, int block = 256);
 template <typename T> void p_residual(const Dims&, const T* u, const T* rhs, T* res, cudaStream_t);
 template <typename T> void p_restrict(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);
 template <typename T> void p_prolong(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);

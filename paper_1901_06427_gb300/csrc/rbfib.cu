@@ -5,6 +5,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -15,7 +17,7 @@
 
 using namespace rbfib;
 
-unsigned long long rbfib::g_launches = 0;
+std::atomic<unsigned long long> rbfib::g_launches{0};
 
 namespace {
 
@@ -106,7 +108,14 @@ struct Config {   // one body configuration (positions derived from q, quat)
 
 }  // namespace
 
+// Threads per block of the finest-level stencil and smoothing kernels, picked
+// by timing candidates once per grid shape (see autotune).
+struct Tuning {
+  int stokes64 = 256, stokes32 = 256, vrbgs = 256, prbgs = 256;
+};
+
 struct rbfib_grid {
+  Tuning tune;
   rbfib_grid_desc desc{};
   cudaStream_t s = nullptr;
   std::string err;
@@ -295,7 +304,7 @@ void vcycle_vel(rbfib_grid* g, T* u0, const T* rhs0) {
   auto smooth = [&](int l, int color) {
     const Dims& d = g->levels[l].d;
     TimerScope ts(g, l == 0 ? TK_SMOOTH : -1, 2.0 * (double)d.fo[3] * sizeof(T));
-    vel_rbgs<T>(d, eta, color, u[l], rhs[l], g->s);
+    vel_rbgs<T>(d, eta, color, u[l], rhs[l], g->s, l == 0 ? g->tune.vrbgs : 256);
   };
   const int lt = std::is_same<T, float>::value && L <= kMaxTail ? tail_start(g->levels, true) : L - 1;
   for (int l = 0; l < lt; ++l) {
@@ -334,9 +343,10 @@ void vcycle_p(rbfib_grid* g, T* u0, T* rhs0) {
   const int lt = std::is_same<T, float>::value && L <= kMaxTail ? tail_start(g->levels, false) : L - 1;
   for (int l = 0; l < lt; ++l) {
     const Dims& d = g->levels[l].d;
+    const int bs = l == 0 ? g->tune.prbgs : 256;
     p_first<T>(d, u[l], rhs[l], g->s);
-    p_rbgs<T>(d, 1, u[l], rhs[l], g->s);
-    for (int s = 1; s < kNu; ++s) { p_rbgs<T>(d, 0, u[l], rhs[l], g->s); p_rbgs<T>(d, 1, u[l], rhs[l], g->s); }
+    p_rbgs<T>(d, 1, u[l], rhs[l], g->s, bs);
+    for (int s = 1; s < kNu; ++s) { p_rbgs<T>(d, 0, u[l], rhs[l], g->s, bs); p_rbgs<T>(d, 1, u[l], rhs[l], g->s, bs); }
     p_restrict_res<T>(d, g->levels[l + 1].d, g->levels[l].cz, u[l], rhs[l], rhs[l + 1], g->s);
   }
   if constexpr (std::is_same<T, float>::value) {
@@ -352,7 +362,8 @@ void vcycle_p(rbfib_grid* g, T* u0, T* rhs0) {
   for (int l = lt - 1; l >= 0; --l) {
     const Dims& d = g->levels[l].d;
     p_prolong<T>(d, g->levels[l + 1].d, g->levels[l].cz, u[l + 1], u[l], g->s);
-    for (int s = 0; s < kNu; ++s) { p_rbgs<T>(d, 1, u[l], rhs[l], g->s); p_rbgs<T>(d, 0, u[l], rhs[l], g->s); }
+    const int bs = l == 0 ? g->tune.prbgs : 256;
+    for (int s = 0; s < kNu; ++s) { p_rbgs<T>(d, 1, u[l], rhs[l], g->s, bs); p_rbgs<T>(d, 0, u[l], rhs[l], g->s, bs); }
   }
 }
 
@@ -411,7 +422,8 @@ void apply_A(rbfib_grid* g, const T* x, T* y, bool with_bodies) {
   const double nbytes = 2.0 * (double)(with_bodies ? g->n_total() : g->nfl) * sizeof(T) +
                         (with_bodies ? 24.0 * g->nbl + 56.0 * g->nb : 0.0);
   TimerScope ts(g, TK_MATVEC, nbytes);
-  stokes_apply<T>(g->d, (T)g->desc.eta, x, x + g->nf, y, y + g->nf, g->s);
+  stokes_apply<T>(g->d, (T)g->desc.eta, x, x + g->nf, y, y + g->nf, g->s,
+                  sizeof(T) == 8 ? g->tune.stokes64 : g->tune.stokes32);
   if (with_bodies && g->nb > 0) {
     const T* xl = x + g->nfl;
     const T* xU = xl + 3 * (i64)g->nbl;
@@ -661,6 +673,68 @@ void alloc_solver(rbfib_grid* g) {
   g->blobA.ensure(std::max<i64>(3 * (i64)g->nbl, 1));
 }
 
+// ---------------------------------------------------------------- autotuner
+// For each tunable kernel and grid shape, time every candidate block size
+// (CUDA events on the grid's stream, best of a few launches) and keep the
+// fastest.  Results are cached process-wide by shape, so a batch of many grids
+// of a few sizes tunes each size once.
+std::mutex g_tune_mu;
+std::map<std::string, Tuning> g_tune_cache;
+
+template <typename F>
+int pick_block(cudaStream_t s, F launch) {
+  const int cand[4] = {64, 128, 256, 512};
+  cudaEvent_t e0, e1;
+  ck(cudaEventCreate(&e0));
+  ck(cudaEventCreate(&e1));
+  int best = 256;
+  float best_ms = 1e30f;
+  for (int bs : cand) {
+    launch(bs);   // warm-up
+    float mn = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+      ck(cudaEventRecord(e0, s));
+      for (int k = 0; k < 4; ++k) launch(bs);
+      ck(cudaEventRecord(e1, s));
+      ck(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      ck(cudaEventElapsedTime(&ms, e0, e1));
+      mn = std::min(mn, ms);
+    }
+    if (mn < best_ms) { best_ms = mn; best = bs; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+void autotune(rbfib_grid* g) {
+  const Dims& d = g->d;
+  char key[160];
+  std::snprintf(key, sizeof key, "%d,%d,%d,%d%d%d", d.n[0], d.n[1], d.n[2], d.per[0], d.per[1], d.per[2]);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) { g->tune = it->second; return; }
+  }
+  Tuning t;
+  double* x64 = g->xvec;
+  double* y64 = g->bvec;
+  float* x32 = g->f32a;
+  float* y32 = g->f32b;
+  ck(cudaMemsetAsync(x64, 0, sizeof(double) * g->nfl, g->s));
+  ck(cudaMemsetAsync(x32, 0, sizeof(float) * g->nfl, g->s));
+  ck(cudaMemsetAsync(y32, 0, sizeof(float) * g->nfl, g->s));
+  const double eta = g->desc.eta;
+  t.stokes64 = pick_block(g->s, [&](int bs) { stokes_apply<double>(d, eta, x64, x64 + g->nf, y64, y64 + g->nf, g->s, bs); });
+  t.stokes32 = pick_block(g->s, [&](int bs) { stokes_apply<float>(d, (float)eta, x32, x32 + g->nf, y32, y32 + g->nf, g->s, bs); });
+  t.vrbgs = pick_block(g->s, [&](int bs) { vel_rbgs<float>(d, (float)eta, 0, x32, y32, g->s, bs); });
+  t.prbgs = pick_block(g->s, [&](int bs) { p_rbgs<float>(d, 0, x32 + g->nf, y32 + g->nf, g->s, bs); });
+  g->tune = t;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = t;
+}
+
 }  // namespace
 
 // ======================================================================= ABI
@@ -668,7 +742,13 @@ extern "C" {
 
 const char* rbfib_last_error(const rbfib_grid* g) { return g ? g->err.c_str() : "null grid"; }
 
-uint64_t rbfib_launch_count(void) { return rbfib::g_launches; }
+uint64_t rbfib_launch_count(void) { return rbfib::g_launches.load(); }
+
+int rbfib_tuned_blocks(const rbfib_grid* g, int32_t out[4]) {
+  if (!g || !out) return RBFIB_EINVAL;
+  out[0] = g->tune.stokes64; out[1] = g->tune.stokes32; out[2] = g->tune.vrbgs; out[3] = g->tune.prbgs;
+  return RBFIB_OK;
+}
 
 int rbfib_kernel_timer(rbfib_grid* g, int32_t which) {
   if (!g || which < 0 || which > 4) return RBFIB_EINVAL;
@@ -743,6 +823,7 @@ int rbfib_create_grid(const rbfib_grid_desc* desc, void* stream, rbfib_grid** ou
     g->fsharp.alloc(g->nf); g->vsharp.alloc(g->nf); g->fnoise.alloc(g->nf);
     g->Wst.alloc(g->stress.total);
     alloc_solver(g);
+    autotune(g);
     ck(cudaStreamSynchronize(g->s));
   } catch (CudaError& e) {
     std::string msg = std::string("create_grid: ") + cudaGetErrorString(e.e);
