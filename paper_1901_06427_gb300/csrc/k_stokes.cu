@@ -115,6 +115,115 @@ __global__ void k_stokes_apply(Dims d, T eta, const T* __restrict__ v, const T* 
   }
 }
 
+// Column-chunked Stokes operator for uniform spacing: each thread owns one
+// (x, y) point of one grid (three face grids, then the cell grid) and marches
+// kKChunk consecutive z-planes, keeping the z-neighbours in registers.
+// blockIdx.z enumerates (grid, z-chunk) pairs, blockIdx.y the rows; no index
+// divisions, 32-bit offsets.
+constexpr int kKChunk = 8;
+struct ColMap {
+  unsigned zend[4];     // cumulative z-chunk counts: faces x, y, z, then cells
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_stokes_cols(Dims d, ColMap cm, T eta, const T* __restrict__ v,
+                                                     const T* __restrict__ p, T* __restrict__ yv, T* __restrict__ yp) {
+  const unsigned zc = blockIdx.z;
+  const int a = (zc >= cm.zend[0]) + (zc >= cm.zend[1]) + (zc >= cm.zend[2]);
+  const int k0 = kKChunk * (int)(zc - (a ? cm.zend[a - 1] : 0u));
+  const int j = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const T ih = inv_h<T>(d, 0), ih2 = inv_h2<T>(d, 0);
+  const int nx = d.n[0], ny = d.n[1];
+  if (a < 3) {
+    const int e0 = d.fe[a][0], e1 = d.fe[a][1], e2 = d.fe[a][2];
+    if (i >= e0 || j >= e1) return;
+    const int k1 = min(k0 + kKChunk, e2);
+    const unsigned base = (unsigned)d.fo[a];
+    const unsigned sy = (unsigned)e0, sz = (unsigned)e0 * (unsigned)e1;
+    const T* va = v + base;
+    const bool perz = d.per[2];
+    // fixed x/y boundary handling for this column
+    int dxy = 4;
+    unsigned xm, xp, ym, yp_;
+    bool hxm = true, hxp = true, hym = true, hyp = true;
+    {
+      if (d.per[0]) { xm = i > 0 ? (unsigned)(i - 1) : (unsigned)(e0 - 1); xp = i < e0 - 1 ? (unsigned)(i + 1) : 0u; }
+      else {
+        xm = (unsigned)(i - 1); xp = (unsigned)(i + 1);
+        if (i == 0) { hxm = false; if (a != 0) ++dxy; }
+        if (i == e0 - 1) { hxp = false; if (a != 0) ++dxy; }
+      }
+      if (d.per[1]) { ym = j > 0 ? (unsigned)(j - 1) : (unsigned)(e1 - 1); yp_ = j < e1 - 1 ? (unsigned)(j + 1) : 0u; }
+      else {
+        ym = (unsigned)(j - 1); yp_ = (unsigned)(j + 1);
+        if (j == 0) { hym = false; if (a != 1) ++dxy; }
+        if (j == e1 - 1) { hyp = false; if (a != 1) ++dxy; }
+      }
+    }
+    // pressure cells either side along a (x/y part fixed for the column)
+    int cxl = i, cxr = i, cyl = j, cyr = j;
+    if (a == 0) { if (d.per[0]) cxl = i > 0 ? i - 1 : nx - 1; else cxr = i + 1; }
+    if (a == 1) { if (d.per[1]) cyl = j > 0 ? j - 1 : ny - 1; else cyr = j + 1; }
+    const unsigned row = (unsigned)i + sy * (unsigned)j;
+    auto at = [&](int kk) -> T { return va[row + sz * (unsigned)kk]; };
+    T um = T(0), u0 = at(k0);
+    bool hzm = true;
+    if (k0 > 0) um = at(k0 - 1);
+    else if (perz) um = at(e2 - 1);
+    else hzm = false;
+    for (int k = k0; k < k1; ++k) {
+      T up = T(0);
+      bool hzp = true;
+      if (k < e2 - 1) up = at(k + 1);
+      else if (perz) up = at(0);
+      else hzp = false;
+      const unsigned id = row + sz * (unsigned)k;
+      T nb = um + up;
+      int diag = dxy + 2;
+      if (!perz) {
+        if (!hzm && a != 2) ++diag;
+        if (!hzp && a != 2) ++diag;
+      }
+      if (hxm) nb += va[xm + sy * (unsigned)j + sz * (unsigned)k];
+      if (hxp) nb += va[xp + sy * (unsigned)j + sz * (unsigned)k];
+      if (hym) nb += va[(unsigned)i + sy * ym + sz * (unsigned)k];
+      if (hyp) nb += va[(unsigned)i + sy * yp_ + sz * (unsigned)k];
+      int czl = k, czr = k;
+      if (a == 2) { if (perz) czl = k > 0 ? k - 1 : d.n[2] - 1; else czr = k + 1; }
+      const unsigned pl = (unsigned)cxl + (unsigned)nx * ((unsigned)cyl + (unsigned)ny * (unsigned)czl);
+      const unsigned pr = (unsigned)cxr + (unsigned)nx * ((unsigned)cyr + (unsigned)ny * (unsigned)czr);
+      yv[base + id] = (eta * ih2) * ((T)diag * u0 - nb) + (p[pr] - p[pl]) * ih;
+      um = u0; u0 = up; hzm = true;
+    }
+  } else {
+    if (i >= nx || j >= ny) return;
+    const int k1 = min(k0 + kKChunk, d.n[2]);
+    for (int k = k0; k < k1; ++k) {
+      const unsigned id = (unsigned)i + (unsigned)nx * ((unsigned)j + (unsigned)ny * (unsigned)k);
+      const int c[3] = {i, j, k};
+      T div = T(0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const int* e = d.fe[b];
+        const T* vb = v + (unsigned)d.fo[b];
+        int f[3] = {i, j, k};
+        T vr = T(0), vl = T(0);
+        if (d.per[b]) {
+          vl = vb[(unsigned)f[0] + (unsigned)e[0] * ((unsigned)f[1] + (unsigned)e[1] * (unsigned)f[2])];
+          f[b] = c[b] + 1; if (f[b] >= d.n[b]) f[b] = 0;
+          vr = vb[(unsigned)f[0] + (unsigned)e[0] * ((unsigned)f[1] + (unsigned)e[1] * (unsigned)f[2])];
+        } else {
+          if (c[b] <= d.n[b] - 2) vr = vb[(unsigned)f[0] + (unsigned)e[0] * ((unsigned)f[1] + (unsigned)e[1] * (unsigned)f[2])];
+          if (c[b] >= 1) { f[b] = c[b] - 1; vl = vb[(unsigned)f[0] + (unsigned)e[0] * ((unsigned)f[1] + (unsigned)e[1] * (unsigned)f[2])]; }
+        }
+        div += vr - vl;
+      }
+      yp[id] = -div * ih;
+    }
+  }
+}
+
 // ------------------------------------------ velocity multigrid (A = -eta LL)
 // Diagonal of -LL at a face (ghost faces across tangential walls add 1/h^2).
 template <typename T>
@@ -517,8 +626,20 @@ static inline unsigned nblk(i64 n, int bs) { return (unsigned)((n + bs - 1) / bs
 
 template <typename T>
 void stokes_apply(const Dims& d, T eta, const T* v, const T* p, T* yv, T* yp, cudaStream_t s, int bs) {
-  const i64 n = d.fo[3] + d.nc;
-  k_stokes_apply<T><<<nblk(n, bs), bs, 0, s>>>(d, eta, v, p, yv, yp);
+  const bool uniform = d.h[0] == d.h[1] && d.h[1] == d.h[2];
+  if (uniform && d.fo[3] + d.nc < ((i64)1 << 31)) {
+    ColMap cm;
+    auto chunks = [](int e) { return (unsigned)((e + kKChunk - 1) / kKChunk); };
+    cm.zend[0] = chunks(d.fe[0][2]);
+    cm.zend[1] = cm.zend[0] + chunks(d.fe[1][2]);
+    cm.zend[2] = cm.zend[1] + chunks(d.fe[2][2]);
+    cm.zend[3] = cm.zend[2] + chunks(d.n[2]);
+    dim3 grid((d.n[0] + 127) / 128, d.n[1], cm.zend[3]);
+    k_stokes_cols<T><<<grid, 128, 0, s>>>(d, cm, eta, v, p, yv, yp);
+  } else {
+    const i64 n = d.fo[3] + d.nc;
+    k_stokes_apply<T><<<nblk(n, bs), bs, 0, s>>>(d, eta, v, p, yv, yp);
+  }
   note_launch();
 }
 template <typename T>
@@ -894,16 +1015,23 @@ k_p_tail(TailParams P) {
 // the top level's right-hand side is loaded from global memory and its
 // solution written back.
 template <typename T>
-__global__ void __launch_bounds__(kTailThreads) k_vel_tail_smem(TailParams P, T eta) {
+__global__ void __launch_bounds__(kTailThreads) k_vel_tail_smem(TailParams Pg, T eta) {
   extern __shared__ unsigned char shraw[];
-  T* u[kMaxTail];
-  T* r[kMaxTail];
-  T* p = (T*)shraw;
-  for (int l = P.l0; l < P.L; ++l) {
-    const i64 n = P.lev[l].d.fo[3];
-    u[l] = p; p += n;
-    r[l] = p; p += n;
+  __shared__ TailParams P;   // level descriptors in shared memory (indexed by level at run time)
+  for (int i = threadIdx.x; i < (int)(sizeof(TailParams) / 4); i += blockDim.x)
+    ((int*)&P)[i] = ((const int*)&Pg)[i];
+  __syncthreads();
+  __shared__ T* u[kMaxTail];
+  __shared__ T* r[kMaxTail];
+  if (threadIdx.x == 0) {
+    T* p = (T*)shraw;
+    for (int l = P.l0; l < P.L; ++l) {
+      const i64 n = P.lev[l].d.fo[3];
+      u[l] = p; p += n;
+      r[l] = p; p += n;
+    }
   }
+  __syncthreads();
   const i64 n0 = P.lev[P.l0].d.fo[3];
   const T* g_rhs = (const T*)P.lev[P.l0].rhs;
   for (i64 t = threadIdx.x; t < n0; t += blockDim.x) r[P.l0][t] = g_rhs[t];
@@ -914,16 +1042,23 @@ __global__ void __launch_bounds__(kTailThreads) k_vel_tail_smem(TailParams P, T 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTailThreads) k_p_tail_smem(TailParams P) {
+__global__ void __launch_bounds__(kTailThreads) k_p_tail_smem(TailParams Pg) {
   extern __shared__ unsigned char shraw[];
-  T* u[kMaxTail];
-  T* r[kMaxTail];
-  T* p = (T*)shraw;
-  for (int l = P.l0; l < P.L; ++l) {
-    const i64 n = P.lev[l].d.nc;
-    u[l] = p; p += n;
-    r[l] = p; p += n;
+  __shared__ TailParams P;
+  for (int i = threadIdx.x; i < (int)(sizeof(TailParams) / 4); i += blockDim.x)
+    ((int*)&P)[i] = ((const int*)&Pg)[i];
+  __syncthreads();
+  __shared__ T* u[kMaxTail];
+  __shared__ T* r[kMaxTail];
+  if (threadIdx.x == 0) {
+    T* p = (T*)shraw;
+    for (int l = P.l0; l < P.L; ++l) {
+      const i64 n = P.lev[l].d.nc;
+      u[l] = p; p += n;
+      r[l] = p; p += n;
+    }
   }
+  __syncthreads();
   const i64 n0 = P.lev[P.l0].d.nc;
   const T* g_rhs = (const T*)P.lev[P.l0].rhs;
   for (i64 t = threadIdx.x; t < n0; t += blockDim.x) r[P.l0][t] = g_rhs[t];

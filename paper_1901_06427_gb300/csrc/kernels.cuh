@@ -85,7 +85,7 @@ struct TailParams {
   TailLevel lev[kMaxTail];
 };
 constexpr long long kTailMaxUnknowns = 8LL * 1024 * 4;   // per level, faces or cells (cluster variant)
-constexpr size_t kTailSmemBytes = 200 * 1024;             // shared-memory variant limit
+constexpr size_t kTailSmemBytes = 190 * 1024;             // shared-memory variant limit (dynamic part)
 size_t tail_smem_bytes(const TailParams& P, bool faces, size_t elem);
 template <typename T> void vel_tail(const TailParams&, T eta, cudaStream_t);
 template <typename T> void p_tail(const TailParams&, cudaStream_t);

@@ -193,7 +193,7 @@ struct TimerScope {
   }
 };
 
-enum { TK_MATVEC = 1, TK_SMOOTH = 2, TK_DOT = 3, TK_AXPY = 4 };
+enum { TK_MATVEC = 1, TK_SMOOTH = 2, TK_DOT = 3, TK_AXPY = 4, TK_TAIL = 5 };
 
 int fail(rbfib_grid* g, int code, const std::string& msg) {
   if (g) g->err = msg;
@@ -253,9 +253,11 @@ KrylovStore<double>& kr_of<double>(rbfib_grid* g) { return g->kr64; }
 template <>
 KrylovStore<float>& kr_of<float>(rbfib_grid* g) { return g->kr32; }
 
-const int kNu = 2;   // pre- and post-smoothing sweeps
+const int kNu = 2;       // pre- and post-smoothing sweeps on the GPU-wide levels
+const int kNuTail = 1;   // on the small levels run inside one CTA
+const long long kTailStartUnknowns = 4096;
 
-int coarse_sweeps(const Dims& d) { return 2 * std::max(d.n[0], std::max(d.n[1], d.n[2])) + 4; }
+int coarse_sweeps(const Dims& d) { return std::max(d.n[0], std::max(d.n[1], d.n[2])) + 2; }
 
 // First level handled by the cluster tail: the first level whose unknowns
 // fit one 8-CTA cluster (every coarser level then fits too).
@@ -265,6 +267,7 @@ int tail_start(const std::vector<Level>& L, bool faces) {
   const int n = (int)L.size();
   for (int l = 0; l < n; ++l) {
     if (n - l > kMaxTail) continue;
+    if ((faces ? L[l].d.fo[3] : L[l].d.nc) > kTailStartUnknowns) continue;   // keep big levels GPU-wide
     size_t bytes = 0;
     for (int k = l; k < n; ++k) bytes += 2 * sizeof(float) * (size_t)(faces ? L[k].d.fo[3] : L[k].d.nc);
     if (bytes <= kTailSmemBytes) return l;
@@ -277,7 +280,7 @@ TailParams tail_params(rbfib_grid* g, int l0, const std::vector<void*>& u, const
   TailParams P{};
   P.l0 = l0;
   P.L = (int)g->levels.size();
-  P.nu = kNu;
+  P.nu = kNuTail;
   P.sweeps = coarse_sweeps(g->levels[P.L - 1].d);
   for (int l = l0; l < P.L; ++l) {
     TailLevel& T = P.lev[l];
@@ -317,7 +320,9 @@ void vcycle_vel(rbfib_grid* g, T* u0, const T* rhs0) {
   if constexpr (std::is_same<T, float>::value) {
     if (L <= kMaxTail) {
       std::vector<void*> uu(u.begin(), u.end()), rr(rhs.begin(), rhs.end());
-      vel_tail<float>(tail_params(g, lt, uu, rr, true), eta, g->s);
+      const TailParams P = tail_params(g, lt, uu, rr, true);
+      TimerScope ts(g, TK_TAIL, (double)tail_smem_bytes(P, true, sizeof(float)));
+      vel_tail<float>(P, eta, g->s);
     } else {
       vel_coarse<T>(g->levels[L - 1].d, eta, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
     }
@@ -352,7 +357,9 @@ void vcycle_p(rbfib_grid* g, T* u0, T* rhs0) {
   if constexpr (std::is_same<T, float>::value) {
     if (L <= kMaxTail) {
       std::vector<void*> uu(u.begin(), u.end()), rr(rhs.begin(), rhs.end());
-      p_tail<float>(tail_params(g, lt, uu, rr, false), g->s);
+      const TailParams P = tail_params(g, lt, uu, rr, false);
+      TimerScope ts(g, TK_TAIL, (double)tail_smem_bytes(P, false, sizeof(float)));
+      p_tail<float>(P, g->s);
     } else {
       p_coarse<T>(g->levels[L - 1].d, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
     }
@@ -718,6 +725,12 @@ void autotune(rbfib_grid* g) {
     if (it != g_tune_cache.end()) { g->tune = it->second; return; }
   }
   Tuning t;
+  if (g->nfl > (i64)8 * 1024 * 1024) {   // large grids are bandwidth-bound: keep 256
+    g->tune = t;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = t;
+    return;
+  }
   double* x64 = g->xvec;
   double* y64 = g->bvec;
   float* x32 = g->f32a;
@@ -751,7 +764,7 @@ int rbfib_tuned_blocks(const rbfib_grid* g, int32_t out[4]) {
 }
 
 int rbfib_kernel_timer(rbfib_grid* g, int32_t which) {
-  if (!g || which < 0 || which > 4) return RBFIB_EINVAL;
+  if (!g || which < 0 || which > 5) return RBFIB_EINVAL;
   try {
     ck(cudaStreamSynchronize(g->s));
   } catch (CudaError& e) {

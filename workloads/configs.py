@@ -235,3 +235,16 @@ def small_case(n=(12, 10, 8), periodic=(False, False, False), n_bodies=2, blobs=
                     "pair_soft": {"phi0": 4.0, "b": 0.1 * radius, "d": 2.0 * radius},
                     "wall_soft": {"phi0": 4.0, "b": 0.1 * radius, "d": radius}}
     return w
+
+
+def matvec_box(n=256, n_bodies=64):
+    """A large no-slip box (n^3 cells, vectors well beyond the 129 MB L2) with
+    42-blob spheres (R = 2.5h) at seeded non-overlapping positions: the
+    saddle matvec at HBM-bound size."""
+    rng = _rng(5)
+    shell = icosahedral_shell(42, 2.5)
+    centres = _place_spheres(rng, (n, n, n), n_bodies, 2.5, 7.0, 4.0)
+    quats = random_unit_quaternions(rng, centres.shape[0])
+    w = Workload(name=f"matvec-box-{n}c", n=(n, n, n), rtol=1e-8, seed=WORKLOAD_SEED_BASE + 5)
+    w.bodies = [Body(shell, centres[i], quats[i]) for i in range(centres.shape[0])]
+    return w
