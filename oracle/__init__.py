@@ -13,7 +13,7 @@ brute force (see tests/test_oracle_*.py).
 """
 from .grid import Grid
 
-from . import operators, kernel, ib, rigid, saddle, solve, philox, noise, forces, sem, binning
+from . import operators, kernel, ib, rigid, saddle, solve, philox, noise, forces, sem, binning, adjoint
 
 __all__ = ["Grid", "operators", "kernel", "ib", "rigid", "saddle", "solve",
-           "philox", "noise", "forces", "sem", "binning"]
+           "philox", "noise", "forces", "sem", "binning", "adjoint"]

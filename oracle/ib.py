@@ -164,3 +164,58 @@ def S_matrix(g: Grid, r):
         e = np.zeros(3 * r.shape[0]); e[c] = 1.0
         cols.append(sp.csr_matrix(spread(g, r, e)).T)
     return sp.hstack(cols).tocsr() if cols else sp.csr_matrix((g.N_f, 0))
+
+
+def stencil_grad(g: Grid, r, a):
+    """Derivatives of the folded weights of component a with respect to the
+    blob position: (idx (N,27), coef (N,27), dcoef (N,27,3)) where
+    dcoef[..., b] = d coef / d r_b = phi'(s_b - p_b)/h * prod_{c != b} phi * sign."""
+    from .kernel import dphi
+    r = np.asarray(r, dtype=np.float64).reshape(-1, 3)
+    N = r.shape[0]
+    ext = g.face_ext(a)
+    per_axis = []
+    for ax in range(3):
+        o = 0.0 if ax == a else 0.5
+        s = r[:, ax] / g.h - o
+        i0 = np.floor(s + 0.5).astype(np.int64)
+        p = i0[:, None] + np.array([-1, 0, 1])[None, :]
+        w = phi(s[:, None] - p)
+        dw = dphi(s[:, None] - p) / g.h
+        comp, sign, wall, keep = _fold(g, a, ax, p)
+        per_axis.append((comp, sign, keep, w, dw))
+    idx = np.zeros((N, 27), dtype=np.int64)
+    coef = np.zeros((N, 27))
+    dcoef = np.zeros((N, 27, 3))
+    t = 0
+    for dz in range(3):
+        for dy in range(3):
+            for dx in range(3):
+                d = (dx, dy, dz)
+                comps = [per_axis[ax][0][:, d[ax]] for ax in range(3)]
+                keep = np.ones(N, dtype=bool)
+                sgn = np.ones(N)
+                ws = [per_axis[ax][3][:, d[ax]] for ax in range(3)]
+                dws = [per_axis[ax][4][:, d[ax]] for ax in range(3)]
+                for ax in range(3):
+                    keep &= per_axis[ax][2][:, d[ax]]
+                    sgn = sgn * per_axis[ax][1][:, d[ax]]
+                idx[:, t] = np.where(keep, g.flat(ext, *comps), 0)
+                coef[:, t] = np.where(keep, ws[0] * ws[1] * ws[2] * sgn, 0.0)
+                for b in range(3):
+                    prod = dws[b] * ws[(b + 1) % 3] * ws[(b + 2) % 3]
+                    dcoef[:, t, b] = np.where(keep, prod * sgn, 0.0)
+                t += 1
+    return idx, coef, dcoef
+
+
+def interpolate_derivative(g: Grid, r, f):
+    """D(f)[i, a, b] = sum over the kernel points of d w_a / d r_{i,b} * f_a:
+    the derivative of (J f)_{ia} with respect to blob position r_i."""
+    r = np.asarray(r).reshape(-1, 3)
+    out = np.zeros((r.shape[0], 3, 3))
+    for a in range(3):
+        idx, _, dcoef = stencil_grad(g, r, a)
+        fa = f[g.face_offset(a):g.face_offset(a) + g.n_face(a)]
+        out[:, a, :] = np.einsum("ntb,nt->nb", dcoef, fa[idx])
+    return out

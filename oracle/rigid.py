@@ -78,7 +78,10 @@ def body_length(ref, offsets):
 
 def K_matrix(ref, offsets, quat):
     """K as a dense (3 N_bl, 6 N_b) array: (K U)_i = u_p + w_p x (r_i - q_p)."""
-    d = arms(ref, offsets, quat)
+    return K_matrix_arms(arms(ref, offsets, quat), offsets)
+
+
+def K_matrix_arms(d, offsets):
     bb = body_of_blob(offsets)
     nbl, nb = d.shape[0], len(offsets) - 1
     K = np.zeros((3 * nbl, 6 * nb))
@@ -92,7 +95,10 @@ def K_matrix(ref, offsets, quat):
 
 
 def K_apply(ref, offsets, quat, U):
-    d = arms(ref, offsets, quat)
+    return K_apply_arms(arms(ref, offsets, quat), offsets, U)
+
+
+def K_apply_arms(d, offsets, U):
     bb = body_of_blob(offsets)
     U = np.asarray(U).reshape(-1, 6)
     return (U[bb, :3] + np.cross(U[bb, 3:], d)).ravel()
@@ -100,7 +106,10 @@ def K_apply(ref, offsets, quat, U):
 
 def KT_apply(ref, offsets, quat, lam):
     """K^T lambda = [sum_i lambda_i ; sum_i (r_i - q) x lambda_i] per body."""
-    d = arms(ref, offsets, quat)
+    return KT_apply_arms(arms(ref, offsets, quat), offsets, lam)
+
+
+def KT_apply_arms(d, offsets, lam):
     bb = body_of_blob(offsets)
     lam = np.asarray(lam).reshape(-1, 3)
     nb = len(offsets) - 1

@@ -19,13 +19,16 @@ from . import operators, ib, rigid
 
 
 class Bodies:
-    """Blob shells, body placements and orientations."""
+    """Blob shells, body placements and orientations.  With ``r`` given, the
+    blob positions are taken as independent inputs (arms r_i - q_p), as the
+    adjoint's gradient with respect to blob positions requires."""
 
-    def __init__(self, ref, offsets, q, quat):
+    def __init__(self, ref, offsets, q, quat, r=None):
         self.ref = np.asarray(ref, dtype=np.float64).reshape(-1, 3)
         self.offsets = np.asarray(offsets, dtype=np.int64)
         self.q = np.asarray(q, dtype=np.float64).reshape(-1, 3)
         self.quat = np.asarray(quat, dtype=np.float64).reshape(-1, 4)
+        self.r = None if r is None else np.asarray(r, dtype=np.float64).reshape(-1, 3)
 
     @property
     def n_blobs(self):
@@ -36,10 +39,29 @@ class Bodies:
         return self.q.shape[0]
 
     def positions(self):
+        if self.r is not None:
+            return self.r
         return rigid.blob_positions(self.ref, self.offsets, self.q, self.quat)
+
+    def arms(self):
+        if self.r is not None:
+            return self.r - self.q[rigid.body_of_blob(self.offsets)]
+        return rigid.arms(self.ref, self.offsets, self.quat)
+
+    def K_matrix(self):
+        return rigid.K_matrix_arms(self.arms(), self.offsets)
+
+    def K_apply(self, U):
+        return rigid.K_apply_arms(self.arms(), self.offsets, U)
+
+    def KT_apply(self, lam):
+        return rigid.KT_apply_arms(self.arms(), self.offsets, lam)
 
     def moved(self, q, quat):
         return Bodies(self.ref, self.offsets, q, quat)
+
+    def with_positions(self, r):
+        return Bodies(self.ref, self.offsets, self.q, self.quat, r=r)
 
 
 def layout(g: Grid, b: Bodies):
@@ -58,7 +80,7 @@ def assemble(g: Grid, b: Bodies, eta):
     r = b.positions()
     J = ib.J_matrix(g, r)
     S = (J.T / g.dV).tocsr()
-    K = sp.csr_matrix(rigid.K_matrix(b.ref, b.offsets, b.quat))
+    K = sp.csr_matrix(b.K_matrix())
     nl, nU = 3 * b.n_blobs, 6 * b.n_bodies
     blocks = [[-eta * L, G, -S, None],
               [-D, None, None, None],
@@ -85,8 +107,8 @@ def apply(g: Grid, b: Bodies, eta, x, L=None, D=None, G=None):
     y = np.zeros_like(x)
     y[o[0]:o[3]] = -eta * (L @ v) + G @ pi - ib.spread(g, r, lam)
     y[o[3]:o[4]] = -(D @ v)
-    y[o[4]:o[5]] = -ib.interpolate(g, r, v) + rigid.K_apply(b.ref, b.offsets, b.quat, U)
-    y[o[5]:o[6]] = rigid.KT_apply(b.ref, b.offsets, b.quat, lam)
+    y[o[4]:o[5]] = -ib.interpolate(g, r, v) + b.K_apply(U)
+    y[o[5]:o[6]] = b.KT_apply(lam)
     return y
 
 

@@ -182,7 +182,7 @@ def constrained(g: Grid, b, eta, f, M=None, op=None):
         return np.concatenate([v0, p0])
     if M is None:
         M = blob_mobility(g, b, eta, op=op)
-    K = rigid.K_matrix(b.ref, b.offsets, b.quat)
+    K = b.K_matrix()
     cf = sla.cho_factor(M)
     N = np.linalg.inv(K.T @ sla.cho_solve(cf, K))
     s = fl + ib.interpolate(g, r, v0)
