@@ -141,6 +141,28 @@ int rbfib_mobility_solve(rbfib_grid* g, const double* FT, const double* slip,
                          const double* fluid_rhs, double* U, double* x_full,
                          rbfib_solve_info* info);
 
+/* Replace the current blob positions (device, N_bl x 3) by independent values:
+ * arms become r_i - q_p; binning, kernel stencils and the body-block
+ * preconditioner are rebuilt.  For mobility problems and their adjoint
+ * (blob positions as inputs); rbfib_sem_step recomputes positions from q, quat. */
+int rbfib_set_blob_positions(rbfib_grid* g, const double* r);
+
+/* Adjoint of rbfib_mobility_solve (an extension; the paper defines the forward
+ * map, Eqs. LangevinD1-D4): for a loss L(U) with gradient dL_dU (device N_b x 6)
+ * at the forward solution x_fwd (device, saddle layout FP64, as returned in
+ * x_full; this is the checkpointed forward state), writes dL/dr (device N_bl x 3,
+ * blob positions as independent inputs) and dL/dslip (device N_bl x 3); either
+ * may be NULL.  Because W A is symmetric (W = diag(dV, dV, 1, 1)), the adjoint
+ * system A^T y = dL/dx is the forward system A z = [0, 0, 0, dL/dU], y = W z;
+ * then dL/dslip = -z_lambda and
+ *   dL/dr_i = sum_a lam_ia D(z_v)_ia + sum_a z_lam,ia D(v)_ia
+ *             - z_lam,i x w_p - lam_i x tau_p,
+ * with D(f)_ia = d(J f)_ia / d r_i from the kernel derivative phi' and tau_p
+ * the rotational part of z_U.  Grids with moving walls give EINVAL.
+ * Synchronises. */
+int rbfib_mobility_solve_adjoint(rbfib_grid* g, const double* dL_dU, const double* x_fwd, double* dL_dr,
+                                 double* dL_dslip, rbfib_solve_info* info);
+
 /* Unconstrained Stokes solve (Algorithm 1 step 4): -eta LL v + G pi = f,
  * -D v = 0 with homogeneous boundary conditions; f and v are device face
  * arrays (N_f, FP64); pi (device N_c, FP64, mean zero) may be NULL. */

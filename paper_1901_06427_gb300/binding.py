@@ -74,6 +74,8 @@ def lib():
             "rbfib_apply_preconditioner": ([P, P, P], I32),
             "rbfib_mobility_solve": ([P, P, P, P, P, P, ctypes.POINTER(SolveInfo)], I32),
             "rbfib_stokes_solve": ([P, P, P, P, ctypes.POINTER(SolveInfo)], I32),
+            "rbfib_set_blob_positions": ([P, P], I32),
+            "rbfib_mobility_solve_adjoint": ([P, P, P, P, P, ctypes.POINTER(SolveInfo)], I32),
             "rbfib_sem_step": ([P, ctypes.POINTER(SemParams), U64, U64, U32, P, P, ctypes.POINTER(StepInfo)], I32),
             "rbfib_binning": ([P, P, P], I32),
             "rbfib_blob_positions": ([P, P], I32),
@@ -247,6 +249,18 @@ class Grid:
             self._h, _ptr(FT, numel=6 * self.n_bodies, name="FT"), _ptr(slip, numel=3 * self.n_blobs, name="slip"),
             _ptr(fluid_rhs, numel=lay[3], name="fluid_rhs"), _ptr(U), _ptr(x), ctypes.byref(info)))
         return (U, info.as_dict(), x) if return_x else (U, info.as_dict())
+
+    def set_blob_positions(self, r):
+        self._check(lib().rbfib_set_blob_positions(self._h, _ptr(r, numel=3 * self.n_blobs, name="r")))
+
+    def mobility_solve_adjoint(self, dL_dU, x_fwd):
+        dr = torch.empty(3 * max(self.n_blobs, 1), dtype=torch.float64, device="cuda")
+        ds = torch.empty(3 * max(self.n_blobs, 1), dtype=torch.float64, device="cuda")
+        info = SolveInfo()
+        self._check(lib().rbfib_mobility_solve_adjoint(
+            self._h, _ptr(dL_dU, numel=6 * self.n_bodies, name="dL_dU"), _ptr(x_fwd, numel=self.n_total, name="x_fwd"),
+            _ptr(dr), _ptr(ds), ctypes.byref(info)))
+        return dr[:3 * self.n_blobs], ds[:3 * self.n_blobs], info.as_dict()
 
     def stokes_solve(self, f):
         lay = self.layout()

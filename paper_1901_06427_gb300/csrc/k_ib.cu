@@ -713,3 +713,82 @@ INST(float)
 #undef INST
 
 }  // namespace rbfib
+
+namespace rbfib {
+
+// ------------------------------------------------------------------ adjoint
+// arm_i = r_i - q_p for blob positions given as independent inputs
+__global__ void k_arms_from_positions(int nbl, const int* __restrict__ bob, const double* __restrict__ r,
+                                      const double* __restrict__ q, double* __restrict__ arm) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * nbl) return;
+  arm[t] = r[t] - q[3 * bob[t / 3] + t % 3];
+}
+
+void arms_from_positions(int nbl, const int* bob, const double* r, const double* q, double* arm, cudaStream_t s) {
+  if (nbl > 0) { k_arms_from_positions<<<nblk(3 * (i64)nbl, 128), 128, 0, s>>>(nbl, bob, r, q, arm); note_launch(); }
+}
+
+// dL/dr_i = sum_a lam_ia D(zv)_ia + sum_a zl_ia D(v)_ia - zl_i x w_p - lam_i x tau_p,
+// D(f)_ia,b = sum over the 27 folded kernel points of d w_a / d r_b * f_a.
+// One warp per blob; lanes over kernel points; FP64; deterministic.
+__global__ void k_adjoint_positions(Dims d, int nbl, const int* __restrict__ bob, const double* __restrict__ r,
+                                    const double* __restrict__ v, const double* __restrict__ lam,
+                                    const double* __restrict__ U, const double* __restrict__ zv,
+                                    const double* __restrict__ zl, const double* __restrict__ zU,
+                                    double* __restrict__ dr) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= nbl) return;
+  double g[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < 3; ++a) {
+    AxisStencil S[3];
+    axis_stencil(d, a, 0, r[3 * i], S[0]);
+    axis_stencil(d, a, 1, r[3 * i + 1], S[1]);
+    axis_stencil(d, a, 2, r[3 * i + 2], S[2]);
+    double A[3] = {0.0, 0.0, 0.0}, Bv[3] = {0.0, 0.0, 0.0};
+    if (lane < 27) {
+      const int pt[3] = {lane % 3, (lane / 3) % 3, lane / 9};
+      bool keep = true;
+      double sg = 1.0;
+      for (int ax = 0; ax < 3; ++ax) { keep = keep && S[ax].keep[pt[ax]]; sg *= (double)S[ax].sgn[pt[ax]]; }
+      if (keep) {
+        const i64 id = d.fo[a] + flat3(d.fe[a], S[0].idx[pt[0]], S[1].idx[pt[1]], S[2].idx[pt[2]]);
+        const double fz = zv[id], fv = v[id];
+        for (int b = 0; b < 3; ++b) {
+          const int c1 = (b + 1) % 3, c2 = (b + 2) % 3;
+          const double dw = S[b].dw[pt[b]] * S[c1].w[pt[c1]] * S[c2].w[pt[c2]] * sg;
+          A[b] = dw * fz;
+          Bv[b] = dw * fv;
+        }
+      }
+    }
+    for (int b = 0; b < 3; ++b)
+      for (int o = 16; o > 0; o >>= 1) {
+        A[b] += __shfl_xor_sync(0xffffffffu, A[b], o);
+        Bv[b] += __shfl_xor_sync(0xffffffffu, Bv[b], o);
+      }
+    const double la = lam[3 * i + a], za = zl[3 * i + a];
+    for (int b = 0; b < 3; ++b) g[b] += la * A[b] + za * Bv[b];
+  }
+  if (lane == 0) {
+    const int p = bob[i];
+    const double* w = U + 6 * p + 3;
+    const double* tau = zU + 6 * p + 3;
+    const double* z = zl + 3 * i;
+    const double* l = lam + 3 * i;
+    dr[3 * i + 0] = g[0] - (z[1] * w[2] - z[2] * w[1]) - (l[1] * tau[2] - l[2] * tau[1]);
+    dr[3 * i + 1] = g[1] - (z[2] * w[0] - z[0] * w[2]) - (l[2] * tau[0] - l[0] * tau[2]);
+    dr[3 * i + 2] = g[2] - (z[0] * w[1] - z[1] * w[0]) - (l[0] * tau[1] - l[1] * tau[0]);
+  }
+}
+
+void adjoint_positions(const Dims& d, int nbl, const int* bob, const double* r, const double* v, const double* lam,
+                       const double* U, const double* zv, const double* zl, const double* zU, double* dr,
+                       cudaStream_t s) {
+  if (nbl > 0) {
+    k_adjoint_positions<<<nblk(32 * (i64)nbl, 128), 128, 0, s>>>(d, nbl, bob, r, v, lam, U, zv, zl, zU, dr);
+    note_launch();
+  }
+}
+
+}  // namespace rbfib

@@ -117,6 +117,10 @@ void wft(int nb, const double* wn, const double* Lp, double kT, double* out, cud
 void move_bodies(int nb, const double* q, const double* quat, const double* vec6, const double* Lp, double a,
                  double* qo, double* quato, cudaStream_t);
 void outside_check(const Dims&, int nbl, const double* r, int* flag, cudaStream_t);
+void arms_from_positions(int nbl, const int* bob, const double* r, const double* q, double* arm, cudaStream_t);
+void adjoint_positions(const Dims&, int nbl, const int* bob, const double* r, const double* v, const double* lam,
+                       const double* U, const double* zv, const double* zl, const double* zU, double* dr,
+                       cudaStream_t);
 
 // k_body.cu
 void dense_body_build(int nbl, int nb, const int* boff, const double* r, const double* arm, double a, double eta,

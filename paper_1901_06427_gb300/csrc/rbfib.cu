@@ -1248,6 +1248,51 @@ int rbfib_body_forces(rbfib_grid* g, const rbfib_sem_params* p, double* out) {
   return RBFIB_OK;
 }
 
+int rbfib_set_blob_positions(rbfib_grid* g, const double* r) {
+  if (!g || (g->nbl > 0 && !r)) return fail(g, RBFIB_EINVAL, "set_blob_positions: null argument");
+  try {
+    if (g->nbl) ck(cudaMemcpyAsync(g->cur.r, r, sizeof(double) * 3 * g->nbl, cudaMemcpyDeviceToDevice, g->s));
+    arms_from_positions(g->nbl, g->bob, g->cur.r, g->cur.q, g->cur.arm, g->s);
+    binning(g->d, g->nbl, g->cur.r, g->cur.perm, g->celloff, g->bkey, g->bcount, g->bfill, g->bbsum, g->s);
+    stencil_build(g->d, g->nbl, g->cur.r, g->cur.st64, g->cur.st32, g->s);
+    if (g->dense_body)
+      dense_body_build(g->nbl, g->nb, g->boff, g->cur.r, g->cur.arm, kBlobRadius * g->desc.h, g->desc.eta, g->dM,
+                       g->dP, g->dN, g->dstatus, g->s);
+    ck(cudaGetLastError());
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+  }
+  return RBFIB_OK;
+}
+
+int rbfib_mobility_solve_adjoint(rbfib_grid* g, const double* dL_dU, const double* x_fwd, double* dL_dr,
+                                 double* dL_dslip, rbfib_solve_info* info) {
+  if (!g || !dL_dU || !x_fwd) return fail(g, RBFIB_EINVAL, "mobility_solve_adjoint: null argument");
+  for (int w = 0; w < 6; ++w)
+    for (int c = 0; c < 3; ++c)
+      if (g->walls.v[w][c] != 0.0) return fail(g, RBFIB_EINVAL, "mobility_solve_adjoint: moving walls");
+  try {
+    const i64 n = g->n_total();
+    // A z = [0, 0, 0, dL/dU]  (A^T y = dL/dx with y = W z)
+    build_rhs(g, dL_dU, nullptr, nullptr, false, g->bvec);
+    int st = solve_system(g, g->bvec, g->xvec, true, info);
+    const double* z = g->xvec;
+    const double* zl = z + g->nfl;
+    const double* zU = zl + 3 * (i64)g->nbl;
+    const double* lam = x_fwd + g->nfl;
+    const double* U = lam + 3 * (i64)g->nbl;
+    if (dL_dslip && g->nbl) axpby<double>(dL_dslip, zl, -1.0, 0.0, 3 * (i64)g->nbl, g->s);
+    if (dL_dr) adjoint_positions(g->d, g->nbl, g->bob, g->cur.r, x_fwd, lam, U, z, zl, zU, dL_dr, g->s);
+    (void)n;
+    ck(cudaStreamSynchronize(g->s));
+    ck(cudaGetLastError());
+    if (st) return fail(g, st, "mobility_solve_adjoint: adjoint solve did not converge");
+  } catch (CudaError& e) {
+    return fail(g, RBFIB_ECUDA, std::string("mobility_solve_adjoint: ") + cudaGetErrorString(e.e));
+  }
+  return RBFIB_OK;
+}
+
 // Algorithm 1 (Split-Euler-Maruyama), steps 1-7.
 int rbfib_sem_step(rbfib_grid* g, const rbfib_sem_params* p, uint64_t seed, uint64_t step, uint32_t attempt,
                    double* q, double* quat, rbfib_step_info* info) {
