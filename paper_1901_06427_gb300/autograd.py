@@ -12,6 +12,8 @@ import torch
 
 
 class MobilitySolve(torch.autograd.Function):
+    last_info = {}
+
     @staticmethod
     def forward(ctx, r, slip, grid, FT):
         grid.set_blob_positions(r.detach().contiguous())
@@ -19,6 +21,7 @@ class MobilitySolve(torch.autograd.Function):
         ctx.grid = grid
         ctx.save_for_backward(x)
         ctx.info = info
+        MobilitySolve.last_info = info
         return U
 
     @staticmethod

@@ -36,9 +36,20 @@ __global__ void k_dot_part(const T* __restrict__ w, const T* __restrict__ V, i64
   const int col = blockIdx.y;
   const T* v = V + (i64)col * ldv;
   double af = 0.0, ab = 0.0;   // fluid and body parts; the weight is applied once
-  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-    if (i < nfl) af = fma((double)w[i], (double)v[i], af);
-    else ab = fma((double)w[i], (double)v[i], ab);
+  if constexpr (sizeof(T) == 4) {
+    // FP32 products and per-thread FP32 sums (about 16 terms), FP64 across
+    // threads and blocks: enough for the FP32 inner solve of the refinement
+    float sf = 0.f, sb = 0.f;
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+      if (i < nfl) sf = fmaf((float)w[i], (float)v[i], sf);
+      else sb = fmaf((float)w[i], (float)v[i], sb);
+    }
+    af = sf; ab = sb;
+  } else {
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+      if (i < nfl) af = fma((double)w[i], (double)v[i], af);
+      else ab = fma((double)w[i], (double)v[i], ab);
+    }
   }
   double acc = block_sum(wf * af + ab);
   if (threadIdx.x == 0) part[(i64)col * gridDim.x + blockIdx.x] = acc;
@@ -79,13 +90,28 @@ __global__ void k_multi_axpy(T* __restrict__ w, const T* __restrict__ V, i64 ldv
   for (int i = threadIdx.x; i < ncols; i += blockDim.x) c[i] = sign * coef[i];
   __syncthreads();
   double af = 0.0, ab = 0.0;
-  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-    double x = (double)w[i];
-    for (int k = 0; k < ncols; ++k) x = fma(c[k], (double)V[(i64)k * ldv + i], x);
-    const T xt = (T)x;
-    w[i] = xt;
-    if (i < nfl) af = fma((double)xt, (double)xt, af);
-    else ab = fma((double)xt, (double)xt, ab);
+  if constexpr (sizeof(T) == 4) {
+    __shared__ float c32[128];
+    for (int i = threadIdx.x; i < ncols; i += blockDim.x) c32[i] = (float)c[i];
+    __syncthreads();
+    float sf = 0.f, sb = 0.f;
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+      float x = (float)w[i];
+      for (int k = 0; k < ncols; ++k) x = fmaf(c32[k], (float)V[(i64)k * ldv + i], x);
+      w[i] = (T)x;
+      if (i < nfl) sf = fmaf(x, x, sf);
+      else sb = fmaf(x, x, sb);
+    }
+    af = sf; ab = sb;
+  } else {
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+      double x = (double)w[i];
+      for (int k = 0; k < ncols; ++k) x = fma(c[k], (double)V[(i64)k * ldv + i], x);
+      const T xt = (T)x;
+      w[i] = xt;
+      if (i < nfl) af = fma((double)xt, (double)xt, af);
+      else ab = fma((double)xt, (double)xt, ab);
+    }
   }
   if (part) {
     double acc = block_sum(wf * af + ab);
@@ -244,5 +270,135 @@ INST(float)
 #undef INST
 template void convert<double, float>(const double*, float*, i64, cudaStream_t);
 template void convert<float, double>(const float*, double*, i64, cudaStream_t);
+
+}  // namespace rbfib
+
+// =================================================================
+// Device-side state of one restart cycle of FGMRES run as a CUDA graph.
+// ist: [0] columns done in this cycle k, [1] total iterations, [2] continue
+// flag; dpar: [0] absolute tolerance, [1] max iterations, [2] ||w||^2 of the
+// current residual w (written by the cycle's last reduction).
+namespace rbfib {
+
+template <typename T>
+__global__ void k_fg_start(T* __restrict__ V0, const T* __restrict__ w, i64 n, double* __restrict__ gvec, int m,
+                           int* __restrict__ ist, const double* __restrict__ dpar) {
+  const double beta = sqrt(fmax(dpar[2], 0.0));
+  const double f = beta > 0.0 ? 1.0 / beta : 0.0;
+  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    V0[i] = (T)((double)w[i] * f);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    gvec[0] = beta;
+    for (int i = 1; i <= m; ++i) gvec[i] = 0.0;
+    ist[0] = 0;
+    ist[2] = 1;
+  }
+}
+
+template <typename T>
+void fg_start(T* V0, const T* w, i64 n, double* gvec, int m, int* ist, const double* dpar, cudaStream_t s) {
+  const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);
+  k_fg_start<T><<<nb, 256, 0, s>>>(V0, w, n, gvec, m, ist, dpar);
+  note_launch();
+}
+
+__global__ void k_setcond(cudaGraphConditionalHandle h, const int* __restrict__ ist) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, ist[2] ? 1u : 0u);
+}
+
+void set_condition(cudaGraphConditionalHandle h, const int* ist, cudaStream_t s) {
+  k_setcond<<<1, 32, 0, s>>>(h, ist);
+  note_launch();
+}
+
+// Givens update of column j (as k_givens) plus the continue decision.
+__global__ void k_givens_flag(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
+                              const double* hcol2, const double* hnext2, double* res_out, int* ist,
+                              const double* dpar) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double* h = H + (i64)j * ldh;
+  for (int i = 0; i <= j; ++i) h[i] = hcol[i] + (hcol2 ? hcol2[i] : 0.0);
+  h[j + 1] = sqrt(fmax(hnext2[0], 0.0));
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+    h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+    h[i] = t;
+  }
+  const double a = h[j], b = h[j + 1];
+  const double r = hypot(a, b);
+  const double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
+  cs[j] = c; sn[j] = s;
+  h[j] = r; h[j + 1] = 0.0;
+  g[j + 1] = -s * g[j];
+  g[j] = c * g[j];
+  const double res = fabs(g[j + 1]);
+  res_out[0] = res;
+  ist[0] = j + 1;
+  ist[1] += 1;
+  const bool cont = (res > dpar[0]) && ((double)ist[1] < dpar[1]) && isfinite(res) && (r > 0.0);
+  ist[2] = cont ? 1 : 0;
+}
+
+void givens_flag(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
+                 const double* hcol2, const double* hnext2, double* res_out, int* ist, const double* dpar,
+                 cudaStream_t s) {
+  k_givens_flag<<<1, 32, 0, s>>>(H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, res_out, ist, dpar);
+  note_launch();
+}
+
+__global__ void k_tri_dev(const double* H, int ldh, const double* g, const int* ist, double* y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = ist[0];
+  for (int i = k - 1; i >= 0; --i) {
+    double acc = g[i];
+    for (int c = i + 1; c < k; ++c) acc -= H[(i64)c * ldh + i] * y[c];
+    y[i] = acc / H[(i64)i * ldh + i];
+  }
+}
+
+void tri_solve_dev(const double* H, int ldh, const double* g, const int* ist, double* y, cudaStream_t s) {
+  k_tri_dev<<<1, 32, 0, s>>>(H, ldh, g, ist, y);
+  note_launch();
+}
+
+// w += sign * sum_{c < ist[0]} coef[c] V_c  (column count read on the device)
+template <typename T>
+__global__ void k_multi_axpy_dev(T* __restrict__ w, const T* __restrict__ V, i64 ldv, const int* __restrict__ ist,
+                                 const double* __restrict__ coef, double sign, i64 n) {
+  __shared__ double c[128];
+  const int ncols = ist[0];
+  for (int i = threadIdx.x; i < ncols; i += blockDim.x) c[i] = sign * coef[i];
+  __syncthreads();
+  if constexpr (sizeof(T) == 4) {
+    __shared__ float c32[128];
+    for (int i = threadIdx.x; i < ncols; i += blockDim.x) c32[i] = (float)c[i];
+    __syncthreads();
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+      float x = (float)w[i];
+      for (int k = 0; k < ncols; ++k) x = fmaf(c32[k], (float)V[(i64)k * ldv + i], x);
+      w[i] = (T)x;
+    }
+  } else {
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+      double x = (double)w[i];
+      for (int k = 0; k < ncols; ++k) x = fma(c[k], (double)V[(i64)k * ldv + i], x);
+      w[i] = (T)x;
+    }
+  }
+}
+
+template <typename T>
+void multi_axpy_dev(T* w, const T* V, i64 ldv, const int* ist, const double* coef, double sign, i64 n, int nparts,
+                    cudaStream_t s) {
+  k_multi_axpy_dev<T><<<nparts, 256, 0, s>>>(w, V, ldv, ist, coef, sign, n);
+  note_launch();
+}
+
+template void fg_start<double>(double*, const double*, i64, double*, int, int*, const double*, cudaStream_t);
+template void fg_start<float>(float*, const float*, i64, double*, int, int*, const double*, cudaStream_t);
+template void multi_axpy_dev<double>(double*, const double*, i64, const int*, const double*, double, i64, int,
+                                     cudaStream_t);
+template void multi_axpy_dev<float>(float*, const float*, i64, const int*, const double*, double, i64, int,
+                                    cudaStream_t);
 
 }  // namespace rbfib

@@ -146,6 +146,17 @@ template <typename T> void axpby(T* y, const T* x, double a, double b, i64 n, cu
 template <typename T> void wall_rhs(const Dims&, const Walls&, double eta, T* bv, cudaStream_t);
 void project_mean(double* x, i64 n, double* part, int nparts, cudaStream_t);
 
+// FGMRES restart cycle as a graph (k_krylov.cu)
+template <typename T> void fg_start(T* V0, const T* w, i64 n, double* gvec, int m, int* ist, const double* dpar,
+                                    cudaStream_t);
+void set_condition(cudaGraphConditionalHandle h, const int* ist, cudaStream_t);
+void givens_flag(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
+                 const double* hcol2, const double* hnext2, double* res_out, int* ist, const double* dpar,
+                 cudaStream_t);
+void tri_solve_dev(const double* H, int ldh, const double* g, const int* ist, double* y, cudaStream_t);
+template <typename T> void multi_axpy_dev(T* w, const T* V, i64 ldv, const int* ist, const double* coef,
+                                          double sign, i64 n, int nparts, cudaStream_t);
+
 // k_noise.cu
 void philox_normals(unsigned long long seed, unsigned long long step, unsigned attempt, unsigned purpose,
                     i64 count, double* out, cudaStream_t);

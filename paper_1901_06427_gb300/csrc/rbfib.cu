@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -155,6 +156,17 @@ struct rbfib_grid {
   DBuf<float> f32a, f32b;
   DBuf<double> small;     // Hessenberg, rotations, g, y, dots
   int total_iters = 0;
+  // FGMRES restart cycles captured as CUDA graphs: [precision 0 = FP64, 1 = FP32][with bodies]
+  struct CycleGraph {
+    cudaGraphExec_t exec = nullptr;
+    const void* b = nullptr;
+    const void* x = nullptr;
+    i64 n = 0;
+    long long per_iter = 0, fixed = 0;
+  } cgraph[2][2];
+  bool use_graphs = true;
+  DBuf<int> gst;
+  DBuf<double> dpar;
   // kernel timer (roofline reports): events around launches of one class
   int timer_kind = 0;
   std::vector<cudaEvent_t> tev;
@@ -194,6 +206,14 @@ struct TimerScope {
 };
 
 enum { TK_MATVEC = 1, TK_SMOOTH = 2, TK_DOT = 3, TK_AXPY = 4, TK_TAIL = 5 };
+
+void drop_graphs(rbfib_grid* g) {
+  for (auto& row : g->cgraph)
+    for (auto& c : row) {
+      if (c.exec) cudaGraphExecDestroy(c.exec);
+      c = rbfib_grid::CycleGraph();
+    }
+}
 
 int fail(rbfib_grid* g, int code, const std::string& msg) {
   if (g) g->err = msg;
@@ -293,6 +313,22 @@ TailParams tail_params(rbfib_grid* g, int l0, const std::vector<void*>& u, const
   return P;
 }
 
+// Algorithmic FP32 operations of one tail launch: every point update of a
+// red-black sweep is a 7-point stencil (13 operations); the fused
+// restriction evaluates up to 12 fine residuals per coarse point; the
+// prolongation adds up to 8 weighted coarse values per fine point.
+double tail_flops(const TailParams& P, bool faces) {
+  double f = 0.0;
+  auto npts = [&](int l) { return (double)(faces ? P.lev[l].d.fo[3] : P.lev[l].d.nc); };
+  for (int l = P.l0; l < P.L - 1; ++l) {
+    f += 2.0 * P.nu * npts(l) * 13.0 * 2.0;     // pre + post sweeps, both colours
+    f += npts(l + 1) * 12.0 * 15.0;            // fused residual-restriction
+    f += npts(l) * 8.0 * 2.0;                  // prolongation
+  }
+  f += 2.0 * P.sweeps * npts(P.L - 1) * 13.0;  // coarsest sweeps
+  return f;
+}
+
 // u0 <- V-cycle approximation of (-eta LL)^{-1} rhs0 (zero initial guess).
 // Levels above the tail run as separate kernels; the rest in one cluster.
 template <typename T>
@@ -321,7 +357,7 @@ void vcycle_vel(rbfib_grid* g, T* u0, const T* rhs0) {
     if (L <= kMaxTail) {
       std::vector<void*> uu(u.begin(), u.end()), rr(rhs.begin(), rhs.end());
       const TailParams P = tail_params(g, lt, uu, rr, true);
-      TimerScope ts(g, TK_TAIL, (double)tail_smem_bytes(P, true, sizeof(float)));
+      TimerScope ts(g, TK_TAIL, tail_flops(P, true));
       vel_tail<float>(P, eta, g->s);
     } else {
       vel_coarse<T>(g->levels[L - 1].d, eta, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
@@ -358,7 +394,7 @@ void vcycle_p(rbfib_grid* g, T* u0, T* rhs0) {
     if (L <= kMaxTail) {
       std::vector<void*> uu(u.begin(), u.end()), rr(rhs.begin(), rhs.end());
       const TailParams P = tail_params(g, lt, uu, rr, false);
-      TimerScope ts(g, TK_TAIL, (double)tail_smem_bytes(P, false, sizeof(float)));
+      TimerScope ts(g, TK_TAIL, tail_flops(P, false));
       p_tail<float>(P, g->s);
     } else {
       p_coarse<T>(g->levels[L - 1].d, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
@@ -508,6 +544,151 @@ int fgmres(rbfib_grid* g, const T* b, T* x, bool with_bodies, double rtol, int m
     if (std::isnan(relres)) return RBFIB_ENAN;
     if (relres <= rtol) return 0;
     if (iters >= maxit) return RBFIB_ENOCONV;
+  }
+}
+
+// One restart cycle of FGMRES(m) as a CUDA graph: the cycle start, then m
+// Arnoldi iterations, iteration j inside an IF node whose condition a small
+// kernel sets from the device continue-flag written by iteration j-1's
+// Givens update (so at most m iterations run per launch, whatever the
+// flags), then the solution update and the true residual w = b - A x with its
+// norm.  The host launches one graph per restart and reads three numbers.
+template <typename T>
+void capture_iteration(rbfib_grid* g, int j, const T* /*b*/, bool wb) {
+  KrylovStore<T>& K = kr_of<T>(g);
+  const int m = K.m;
+  const i64 n = wb ? g->n_total() : g->nfl, ld = K.n, nfl = g->nfl;
+  const double wf = g->dV;
+  SmallPtrs sp = small_ptrs(g, m);
+  T* V = K.V;
+  T* Z = K.Z;
+  T* w = K.w;
+  precond_any(g, V + (i64)j * ld, Z + (i64)j * ld, wb);
+  apply_A<T>(g, Z + (i64)j * ld, w, wb);
+  multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol, g->s);
+  multi_axpy<T>(w, V, ld, j + 1, sp.hcol, -1.0, n, nfl, wf, g->part, g->nparts, nullptr, g->s);
+  multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol2, g->s);
+  multi_axpy<T>(w, V, ld, j + 1, sp.hcol2, -1.0, n, nfl, wf, g->part, g->nparts, sp.nrm2, g->s);
+  scale_by<T>(V + (i64)(j + 1) * ld, w, sp.nrm2, 2, n, g->s);
+  givens_flag(sp.H, m + 1, sp.cs, sp.sn, sp.gv, j, sp.hcol, sp.hcol2, sp.nrm2, sp.res, g->gst, g->dpar, g->s);
+}
+
+template <typename T>
+bool build_cycle_graph(rbfib_grid* g, const T* b, T* x, bool wb, rbfib_grid::CycleGraph& G) {
+  KrylovStore<T>& K = kr_of<T>(g);
+  const int m = K.m;
+  const i64 n = wb ? g->n_total() : g->nfl, ld = K.n, nfl = g->nfl;
+  const double wf = g->dV;
+  SmallPtrs sp = small_ptrs(g, m);
+  cudaStream_t s0 = g->s, sc = nullptr, sb = nullptr;
+  const int saved_timer = g->timer_kind;
+  bool ok = true;
+  const long long l0 = rbfib::g_launches.load();
+  long long per_iter = 0;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamCreateWithFlags(&sc, cudaStreamNonBlocking) != cudaSuccess) return false;
+  if (cudaStreamCreateWithFlags(&sb, cudaStreamNonBlocking) != cudaSuccess) { cudaStreamDestroy(sc); return false; }
+  g->timer_kind = 0;
+  g->s = sc;
+  try {
+    ck(cudaStreamBeginCapture(sc, cudaStreamCaptureModeRelaxed));
+    fg_start<T>(K.V, K.w, n, sp.gv, m, g->gst, g->dpar, sc);
+    for (int j = 0; j < m; ++j) {
+      cudaStreamCaptureStatus cst;
+      cudaGraph_t capg = nullptr;
+      ck(cudaStreamGetCaptureInfo(sc, &cst, nullptr, &capg, nullptr, nullptr, nullptr));
+      cudaGraphConditionalHandle h;
+      ck(cudaGraphConditionalHandleCreate(&h, capg, j == 0 ? 1u : 0u, cudaGraphCondAssignDefault));
+      if (j > 0) set_condition(h, g->gst, sc);
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      ck(cudaStreamGetCaptureInfo(sc, &cst, nullptr, &capg, &deps, nullptr, &nd));
+      cudaGraphNodeParams p = {};
+      p.type = cudaGraphNodeTypeConditional;
+      p.conditional.handle = h;
+      p.conditional.type = cudaGraphCondTypeIf;
+      p.conditional.size = 1;
+      cudaGraphNode_t node;
+      ck(cudaGraphAddNode(&node, capg, deps, nullptr, nd, &p));
+      ck(cudaStreamUpdateCaptureDependencies(sc, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+      cudaGraph_t body = p.conditional.phGraph_out[0];
+      g->s = sb;
+      ck(cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      const long long a0 = rbfib::g_launches.load();
+      capture_iteration<T>(g, j, b, wb);
+      if (j == 0) per_iter = (long long)rbfib::g_launches.load() - a0;
+      ck(cudaStreamEndCapture(sb, &body));
+      g->s = sc;
+    }
+    tri_solve_dev(sp.H, m + 1, sp.gv, g->gst, sp.y, sc);
+    multi_axpy_dev<T>(x, K.Z, ld, g->gst, sp.y, 1.0, n, g->nparts, sc);
+    apply_A<T>(g, x, K.w, wb);
+    axpby<T>(K.w, b, 1.0, -1.0, n, sc);
+    multi_dot<T>(K.w, K.w, ld, 1, n, nfl, wf, g->part, g->nparts, g->dpar + 2, sc);
+    ck(cudaStreamEndCapture(sc, &graph));
+    ck(cudaGraphInstantiate(&G.exec, graph, 0));
+  } catch (CudaError&) {
+    ok = false;
+    cudaStreamCaptureStatus cst;
+    if (cudaStreamIsCapturing(sb, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+      cudaGraph_t t; cudaStreamEndCapture(sb, &t);
+    }
+    if (cudaStreamIsCapturing(sc, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+      cudaGraph_t t; cudaStreamEndCapture(sc, &t); if (t) cudaGraphDestroy(t);
+    }
+    cudaGetLastError();
+  }
+  if (graph) cudaGraphDestroy(graph);
+  g->s = s0;
+  g->timer_kind = saved_timer;
+  cudaStreamDestroy(sb);
+  cudaStreamDestroy(sc);
+  const long long captured = (long long)rbfib::g_launches.load() - l0;
+  rbfib::g_launches.fetch_sub((unsigned long long)captured);   // captured, not launched
+  G.per_iter = per_iter;
+  G.fixed = captured - (long long)m * per_iter;
+  G.b = b; G.x = x; G.n = n;
+  return ok;
+}
+
+template <typename T>
+int fgmres_graph(rbfib_grid* g, const T* b, T* x, bool wb, double rtol, int maxit, int& iters, double& relres) {
+  KrylovStore<T>& K = kr_of<T>(g);
+  const i64 n = wb ? g->n_total() : g->nfl, ld = K.n, nfl = g->nfl;
+  const double wf = g->dV;
+  SmallPtrs sp = small_ptrs(g, K.m);
+  rbfib_grid::CycleGraph& G = g->cgraph[sizeof(T) == 8 ? 0 : 1][wb ? 1 : 0];
+  if (G.exec && (G.b != b || G.x != x || G.n != n)) { cudaGraphExecDestroy(G.exec); G = rbfib_grid::CycleGraph(); }
+  if (!G.exec && !build_cycle_graph<T>(g, b, x, wb, G)) {
+    g->use_graphs = false;
+    return fgmres<T>(g, b, x, wb, rtol, maxit, iters, relres);
+  }
+  iters = 0;
+  relres = 0.0;
+  multi_dot<T>(b, b, ld, 1, n, nfl, wf, g->part, g->nparts, sp.bn, g->s);
+  const double bnorm = std::sqrt(std::max(read_scalar(g, sp.bn), 0.0));
+  ck(cudaMemsetAsync(x, 0, sizeof(T) * n, g->s));
+  if (!(bnorm > 0.0)) return std::isnan(bnorm) ? RBFIB_ENAN : 0;
+  double* hp = g->h_pinned + 8;
+  hp[0] = rtol * bnorm;
+  hp[1] = (double)maxit;
+  hp[2] = bnorm * bnorm;
+  ck(cudaMemcpyAsync(g->dpar, hp, sizeof(double) * 3, cudaMemcpyHostToDevice, g->s));
+  ck(cudaMemsetAsync(g->gst, 0, sizeof(int) * 4, g->s));
+  ck(cudaMemcpyAsync(K.w, b, sizeof(T) * n, cudaMemcpyDeviceToDevice, g->s));
+  int* hi = (int*)(g->h_pinned + 16);
+  for (;;) {
+    ck(cudaGraphLaunch(G.exec, g->s));
+    ck(cudaMemcpyAsync(hi, g->gst, sizeof(int) * 4, cudaMemcpyDeviceToHost, g->s));
+    ck(cudaMemcpyAsync(hp + 3, g->dpar + 2, sizeof(double), cudaMemcpyDeviceToHost, g->s));
+    ck(cudaStreamSynchronize(g->s));
+    const int k = hi[0];
+    rbfib::g_launches.fetch_add((unsigned long long)(G.fixed + (long long)k * G.per_iter));
+    iters = hi[1];
+    relres = std::sqrt(std::max(hp[3], 0.0)) / bnorm;
+    if (std::isnan(relres)) return RBFIB_ENAN;
+    if (relres <= rtol) return 0;
+    if (iters >= maxit || k == 0) return RBFIB_ENOCONV;
   }
 }
 
@@ -825,6 +1006,9 @@ int rbfib_create_grid(const rbfib_grid_desc* desc, void* stream, rbfib_grid** ou
     g->part.alloc((size_t)g->nparts * 130 + 8);
     g->small.alloc((size_t)(D.restart + 1) * D.restart + 4 * D.restart + 512);
     ck(cudaMallocHost((void**)&g->h_pinned, 64 * sizeof(double)));
+    g->gst.alloc(8);
+    g->dpar.alloc(8);
+    if (const char* e = std::getenv("RBFIB_NO_GRAPHS")) g->use_graphs = (e[0] == '0');
     g->mg32.build(g->levels);
     g->bcount.alloc(g->nc + 1);
     g->bfill.alloc(g->nc);
@@ -852,6 +1036,7 @@ void rbfib_destroy(rbfib_grid* g) {
   if (!g) return;
   if (g->s) cudaStreamSynchronize(g->s);
   for (cudaEvent_t e : g->tev) cudaEventDestroy(e);
+  drop_graphs(g);
   if (g->h_pinned) cudaFreeHost(g->h_pinned);
   delete g;
 }
@@ -881,6 +1066,7 @@ int rbfib_set_bodies(rbfib_grid* g, int32_t n_bodies, const int32_t* blob_offset
   }
   try {
     ck(cudaStreamSynchronize(g->s));
+    drop_graphs(g);
     g->nb = n_bodies;
     g->nbl = off[n_bodies];
     g->h_boff = off;
@@ -1042,6 +1228,10 @@ int rbfib_apply_saddle(rbfib_grid* g, const void* x, void* y, int32_t dtype) {
 
 namespace {
 
+// Graph-captured restart cycles unless disabled or a kernel timer is active
+// (event records cannot sit inside conditional graph bodies).
+bool use_graph_path(rbfib_grid* g) { return g->use_graphs && g->timer_kind == 0; }
+
 // Right-hand side of the constrained system: fluid forcing + wall terms,
 // -slip + J wall part, forces.  b is FP64 in the saddle layout.
 void build_rhs(rbfib_grid* g, const double* FT, const double* slip, const double* fluid, bool walls, double* b) {
@@ -1066,7 +1256,8 @@ int solve_system(rbfib_grid* g, const double* b, double* x, bool with_bodies, rb
   int iters = 0, st = 0;
   double rel = 0.0;
   if (g->desc.precision == RBFIB_FP64) {
-    st = fgmres<double>(g, b, x, with_bodies, rtol, g->desc.max_iter, iters, rel);
+    st = use_graph_path(g) ? fgmres_graph<double>(g, b, x, with_bodies, rtol, g->desc.max_iter, iters, rel)
+                           : fgmres<double>(g, b, x, with_bodies, rtol, g->desc.max_iter, iters, rel);
     if (info) { info->iterations = iters; info->refinements = 0; info->rel_residual = rel; }
   } else {
     // outer refinement in FP64
@@ -1084,7 +1275,9 @@ int solve_system(rbfib_grid* g, const double* b, double* x, bool with_bodies, rb
       convert<double, float>(r, g->f32a, n, g->s);
       int it = 0;
       double irel = 0.0;
-      int ist = fgmres<float>(g, g->f32a, g->f32b, with_bodies, inner_tol, g->desc.max_iter - total, it, irel);
+      int ist = use_graph_path(g)
+                    ? fgmres_graph<float>(g, g->f32a, g->f32b, with_bodies, inner_tol, g->desc.max_iter - total, it, irel)
+                    : fgmres<float>(g, g->f32a, g->f32b, with_bodies, inner_tol, g->desc.max_iter - total, it, irel);
       total += it;
       ++sweeps;
       if (ist == RBFIB_ENAN) { st = ist; break; }
