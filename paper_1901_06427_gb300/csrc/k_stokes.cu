@@ -115,113 +115,149 @@ __global__ void k_stokes_apply(Dims d, T eta, const T* __restrict__ v, const T* 
   }
 }
 
-// Column-chunked Stokes operator for uniform spacing: each thread owns one
-// (x, y) point of one grid (three face grids, then the cell grid) and marches
-// kKChunk consecutive z-planes, keeping the z-neighbours in registers.
-// blockIdx.z enumerates (grid, z-chunk) pairs, blockIdx.y the rows; no index
-// divisions, 32-bit offsets.
+// Column-chunked Stokes operator for uniform spacing.  A thread owns one
+// (x, y) point and one chunk of kKChunk z-planes and computes, in turn, the
+// three momentum rows (one per face grid) and the divergence row of that
+// column chunk, so the pressure and velocity rows it touches are reused from
+// L1/L2 by all four rows instead of being fetched once per grid.  Along z the
+// neighbours stay in registers.  No index divisions; 32-bit offsets.
 constexpr int kKChunk = 8;
-struct ColMap {
-  unsigned zend[4];     // cumulative z-chunk counts: faces x, y, z, then cells
-};
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_stokes_cols(Dims d, ColMap cm, T eta, const T* __restrict__ v,
-                                                     const T* __restrict__ p, T* __restrict__ yv, T* __restrict__ yp) {
-  const unsigned zc = blockIdx.z;
-  const int a = (zc >= cm.zend[0]) + (zc >= cm.zend[1]) + (zc >= cm.zend[2]);
-  const int k0 = kKChunk * (int)(zc - (a ? cm.zend[a - 1] : 0u));
-  const int j = blockIdx.y;
+RBFIB_DEVFN void momentum_column(const Dims& d, int a, int i, int j, int k0, T eta, T ih, T ih2,
+                                 const T* __restrict__ v, const T* __restrict__ p, T* __restrict__ yv) {
+  const int e0 = d.fe[a][0], e1 = d.fe[a][1], e2 = d.fe[a][2];
+  if (i >= e0 || j >= e1 || k0 >= e2) return;
+  const int k1 = min(k0 + kKChunk, e2);
+  const int nx = d.n[0], ny = d.n[1];
+  const unsigned base = (unsigned)d.fo[a];
+  const unsigned sy = (unsigned)e0, sz = (unsigned)e0 * (unsigned)e1;
+  const T* va = v + base;
+  const bool perz = d.per[2];
+  int dxy = 4;
+  unsigned xm = 0, xp = 0, ym = 0, yq = 0;
+  bool hxm = true, hxp = true, hym = true, hyp = true;
+  if (d.per[0]) { xm = i > 0 ? (unsigned)(i - 1) : (unsigned)(e0 - 1); xp = i < e0 - 1 ? (unsigned)(i + 1) : 0u; }
+  else {
+    xm = (unsigned)(i - 1); xp = (unsigned)(i + 1);
+    if (i == 0) { hxm = false; if (a != 0) ++dxy; }
+    if (i == e0 - 1) { hxp = false; if (a != 0) ++dxy; }
+  }
+  if (d.per[1]) { ym = j > 0 ? (unsigned)(j - 1) : (unsigned)(e1 - 1); yq = j < e1 - 1 ? (unsigned)(j + 1) : 0u; }
+  else {
+    ym = (unsigned)(j - 1); yq = (unsigned)(j + 1);
+    if (j == 0) { hym = false; if (a != 1) ++dxy; }
+    if (j == e1 - 1) { hyp = false; if (a != 1) ++dxy; }
+  }
+  int cxl = i, cxr = i, cyl = j, cyr = j;
+  if (a == 0) { if (d.per[0]) cxl = i > 0 ? i - 1 : nx - 1; else cxr = i + 1; }
+  if (a == 1) { if (d.per[1]) cyl = j > 0 ? j - 1 : ny - 1; else cyr = j + 1; }
+  const unsigned row = (unsigned)i + sy * (unsigned)j;
+  const unsigned rxm = xm + sy * (unsigned)j, rxp = xp + sy * (unsigned)j;
+  const unsigned rym = (unsigned)i + sy * ym, ryp = (unsigned)i + sy * yq;
+  const unsigned pl0 = (unsigned)cxl + (unsigned)nx * (unsigned)cyl, pr0 = (unsigned)cxr + (unsigned)nx * (unsigned)cyr;
+  const unsigned pz = (unsigned)nx * (unsigned)ny;
+  T um = T(0), u0 = va[row + sz * (unsigned)k0];
+  bool hzm = true;
+  if (k0 > 0) um = va[row + sz * (unsigned)(k0 - 1)];
+  else if (perz) um = va[row + sz * (unsigned)(e2 - 1)];
+  else hzm = false;
+  const T s = eta * ih2;
+#pragma unroll
+  for (int kk = 0; kk < kKChunk; ++kk) {
+    const int k = k0 + kk;
+    if (k >= k1) break;
+    T up = T(0);
+    bool hzp = true;
+    if (k < e2 - 1) up = va[row + sz * (unsigned)(k + 1)];
+    else if (perz) up = va[row];
+    else hzp = false;
+    const unsigned zo = sz * (unsigned)k;
+    T nb = um + up;
+    int diag = dxy + 2;
+    if (!perz && a != 2) diag += (!hzm) + (!hzp);
+    if (hxm) nb += va[rxm + zo];
+    if (hxp) nb += va[rxp + zo];
+    if (hym) nb += va[rym + zo];
+    if (hyp) nb += va[ryp + zo];
+    int czl = k, czr = k;
+    if (a == 2) { if (perz) czl = k > 0 ? k - 1 : d.n[2] - 1; else czr = k + 1; }
+    const T gp = (p[pr0 + pz * (unsigned)czr] - p[pl0 + pz * (unsigned)czl]) * ih;
+    yv[base + row + zo] = s * ((T)diag * u0 - nb) + gp;
+    um = u0; u0 = up; hzm = true;
+  }
+}
+
+template <typename T>
+RBFIB_DEVFN void divergence_column(const Dims& d, int i, int j, int k0, T ih, const T* __restrict__ v,
+                                   T* __restrict__ yp) {
+  const int nx = d.n[0], ny = d.n[1], nz = d.n[2];
+  if (i >= nx || j >= ny || k0 >= nz) return;
+  const int k1 = min(k0 + kKChunk, nz);
+  // x faces: compact index along x of the right / left face of cell i
+  const int ex0 = d.fe[0][0], ey1 = d.fe[1][1];
+  const T* vx = v + (unsigned)d.fo[0];
+  const T* vy = v + (unsigned)d.fo[1];
+  const T* vz = v + (unsigned)d.fo[2];
+  int xr, xl; bool hxr, hxl;
+  if (d.per[0]) { xl = i; xr = i + 1 < nx ? i + 1 : 0; hxr = hxl = true; }
+  else { xr = i; xl = i - 1; hxr = i <= nx - 2; hxl = i >= 1; }
+  int yr, yl; bool hyr, hyl;
+  if (d.per[1]) { yl = j; yr = j + 1 < ny ? j + 1 : 0; hyr = hyl = true; }
+  else { yr = j; yl = j - 1; hyr = j <= ny - 2; hyl = j >= 1; }
+  const unsigned sxy = (unsigned)ex0 * (unsigned)ny;            // x-face plane
+  const unsigned syy = (unsigned)nx * (unsigned)ey1;            // y-face plane
+  const unsigned szz = (unsigned)nx * (unsigned)ny;             // z-face plane
+#pragma unroll
+  for (int kk = 0; kk < kKChunk; ++kk) {
+    const int k = k0 + kk;
+    if (k >= k1) break;
+    T div = T(0);
+    if (hxr) div += vx[(unsigned)xr + (unsigned)ex0 * (unsigned)j + sxy * (unsigned)k];
+    if (hxl) div -= vx[(unsigned)xl + (unsigned)ex0 * (unsigned)j + sxy * (unsigned)k];
+    if (hyr) div += vy[(unsigned)i + (unsigned)nx * (unsigned)yr + syy * (unsigned)k];
+    if (hyl) div -= vy[(unsigned)i + (unsigned)nx * (unsigned)yl + syy * (unsigned)k];
+    int zr, zl; bool hzr, hzl;
+    if (d.per[2]) { zl = k; zr = k + 1 < nz ? k + 1 : 0; hzr = hzl = true; }
+    else { zr = k; zl = k - 1; hzr = k <= nz - 2; hzl = k >= 1; }
+    const unsigned cz = (unsigned)i + (unsigned)nx * (unsigned)j;
+    if (hzr) div += vz[cz + szz * (unsigned)zr];
+    if (hzl) div -= vz[cz + szz * (unsigned)zl];
+    yp[(unsigned)i + (unsigned)nx * ((unsigned)j + (unsigned)ny * (unsigned)k)] = -div * ih;
+  }
+}
+
+template <typename T>
+RBFIB_DEVFN void stokes_cols_body(const Dims& d, T eta, const T* __restrict__ v, const T* __restrict__ p,
+                                  T* __restrict__ yv, T* __restrict__ yp) {
+  const int k0 = kKChunk * (int)blockIdx.z;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const T ih = inv_h<T>(d, 0), ih2 = inv_h2<T>(d, 0);
-  const int nx = d.n[0], ny = d.n[1];
-  if (a < 3) {
-    const int e0 = d.fe[a][0], e1 = d.fe[a][1], e2 = d.fe[a][2];
-    if (i >= e0 || j >= e1) return;
-    const int k1 = min(k0 + kKChunk, e2);
-    const unsigned base = (unsigned)d.fo[a];
-    const unsigned sy = (unsigned)e0, sz = (unsigned)e0 * (unsigned)e1;
-    const T* va = v + base;
-    const bool perz = d.per[2];
-    // fixed x/y boundary handling for this column
-    int dxy = 4;
-    unsigned xm, xp, ym, yp_;
-    bool hxm = true, hxp = true, hym = true, hyp = true;
-    {
-      if (d.per[0]) { xm = i > 0 ? (unsigned)(i - 1) : (unsigned)(e0 - 1); xp = i < e0 - 1 ? (unsigned)(i + 1) : 0u; }
-      else {
-        xm = (unsigned)(i - 1); xp = (unsigned)(i + 1);
-        if (i == 0) { hxm = false; if (a != 0) ++dxy; }
-        if (i == e0 - 1) { hxp = false; if (a != 0) ++dxy; }
-      }
-      if (d.per[1]) { ym = j > 0 ? (unsigned)(j - 1) : (unsigned)(e1 - 1); yp_ = j < e1 - 1 ? (unsigned)(j + 1) : 0u; }
-      else {
-        ym = (unsigned)(j - 1); yp_ = (unsigned)(j + 1);
-        if (j == 0) { hym = false; if (a != 1) ++dxy; }
-        if (j == e1 - 1) { hyp = false; if (a != 1) ++dxy; }
-      }
-    }
-    // pressure cells either side along a (x/y part fixed for the column)
-    int cxl = i, cxr = i, cyl = j, cyr = j;
-    if (a == 0) { if (d.per[0]) cxl = i > 0 ? i - 1 : nx - 1; else cxr = i + 1; }
-    if (a == 1) { if (d.per[1]) cyl = j > 0 ? j - 1 : ny - 1; else cyr = j + 1; }
-    const unsigned row = (unsigned)i + sy * (unsigned)j;
-    auto at = [&](int kk) -> T { return va[row + sz * (unsigned)kk]; };
-    T um = T(0), u0 = at(k0);
-    bool hzm = true;
-    if (k0 > 0) um = at(k0 - 1);
-    else if (perz) um = at(e2 - 1);
-    else hzm = false;
-    for (int k = k0; k < k1; ++k) {
-      T up = T(0);
-      bool hzp = true;
-      if (k < e2 - 1) up = at(k + 1);
-      else if (perz) up = at(0);
-      else hzp = false;
-      const unsigned id = row + sz * (unsigned)k;
-      T nb = um + up;
-      int diag = dxy + 2;
-      if (!perz) {
-        if (!hzm && a != 2) ++diag;
-        if (!hzp && a != 2) ++diag;
-      }
-      if (hxm) nb += va[xm + sy * (unsigned)j + sz * (unsigned)k];
-      if (hxp) nb += va[xp + sy * (unsigned)j + sz * (unsigned)k];
-      if (hym) nb += va[(unsigned)i + sy * ym + sz * (unsigned)k];
-      if (hyp) nb += va[(unsigned)i + sy * yp_ + sz * (unsigned)k];
-      int czl = k, czr = k;
-      if (a == 2) { if (perz) czl = k > 0 ? k - 1 : d.n[2] - 1; else czr = k + 1; }
-      const unsigned pl = (unsigned)cxl + (unsigned)nx * ((unsigned)cyl + (unsigned)ny * (unsigned)czl);
-      const unsigned pr = (unsigned)cxr + (unsigned)nx * ((unsigned)cyr + (unsigned)ny * (unsigned)czr);
-      yv[base + id] = (eta * ih2) * ((T)diag * u0 - nb) + (p[pr] - p[pl]) * ih;
-      um = u0; u0 = up; hzm = true;
-    }
-  } else {
-    if (i >= nx || j >= ny) return;
-    const int k1 = min(k0 + kKChunk, d.n[2]);
-    for (int k = k0; k < k1; ++k) {
-      const unsigned id = (unsigned)i + (unsigned)nx * ((unsigned)j + (unsigned)ny * (unsigned)k);
-      const int c[3] = {i, j, k};
-      T div = T(0);
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const int* e = d.fe[b];
-        const T* vb = v + (unsigned)d.fo[b];
-        int f[3] = {i, j, k};
-        T vr = T(0), vl = T(0);
-        if (d.per[b]) {
-          vl = vb[(unsigned)f[0] + (unsigned)e[0] * ((unsigned)f[1] + (unsigned)e[1] * (unsigned)f[2])];
-          f[b] = c[b] + 1; if (f[b] >= d.n[b]) f[b] = 0;
-          vr = vb[(unsigned)f[0] + (unsigned)e[0] * ((unsigned)f[1] + (unsigned)e[1] * (unsigned)f[2])];
-        } else {
-          if (c[b] <= d.n[b] - 2) vr = vb[(unsigned)f[0] + (unsigned)e[0] * ((unsigned)f[1] + (unsigned)e[1] * (unsigned)f[2])];
-          if (c[b] >= 1) { f[b] = c[b] - 1; vl = vb[(unsigned)f[0] + (unsigned)e[0] * ((unsigned)f[1] + (unsigned)e[1] * (unsigned)f[2])]; }
-        }
-        div += vr - vl;
-      }
-      yp[id] = -div * ih;
-    }
-  }
+  momentum_column<T>(d, 0, i, j, k0, eta, ih, ih2, v, p, yv);
+  momentum_column<T>(d, 1, i, j, k0, eta, ih, ih2, v, p, yv);
+  momentum_column<T>(d, 2, i, j, k0, eta, ih, ih2, v, p, yv);
+  divergence_column<T>(d, i, j, k0, ih, v, yp);
+}
+
+// One thread per (i, j) column and kKChunk z-planes, all four grids.
+__global__ void __launch_bounds__(128) k_stokes_cols_f32(Dims d, float eta, const float* __restrict__ v,
+                                                             const float* __restrict__ p, float* __restrict__ yv,
+                                                             float* __restrict__ yp) {
+  stokes_cols_body<float>(d, eta, v, p, yv, yp);
+}
+__global__ void __launch_bounds__(128) k_stokes_cols_f64(Dims d, double eta, const double* __restrict__ v,
+                                                         const double* __restrict__ p, double* __restrict__ yv,
+                                                         double* __restrict__ yp) {
+  stokes_cols_body<double>(d, eta, v, p, yv, yp);
+}
+inline void launch_cols(dim3 gr, cudaStream_t s, const Dims& d, float eta, const float* v, const float* p, float* yv,
+                        float* yp) {
+  k_stokes_cols_f32<<<gr, dim3(d.n[0] >= 96 ? 128 : 32, d.n[0] >= 96 ? 1 : 4), 0, s>>>(d, eta, v, p, yv, yp);
+}
+inline void launch_cols(dim3 gr, cudaStream_t s, const Dims& d, double eta, const double* v, const double* p,
+                        double* yv, double* yp) {
+  k_stokes_cols_f64<<<gr, dim3(d.n[0] >= 96 ? 128 : 32, d.n[0] >= 96 ? 1 : 4), 0, s>>>(d, eta, v, p, yv, yp);
 }
 
 // ------------------------------------------ velocity multigrid (A = -eta LL)
@@ -628,14 +664,9 @@ template <typename T>
 void stokes_apply(const Dims& d, T eta, const T* v, const T* p, T* yv, T* yp, cudaStream_t s, int bs) {
   const bool uniform = d.h[0] == d.h[1] && d.h[1] == d.h[2];
   if (uniform && d.fo[3] + d.nc < ((i64)1 << 31)) {
-    ColMap cm;
-    auto chunks = [](int e) { return (unsigned)((e + kKChunk - 1) / kKChunk); };
-    cm.zend[0] = chunks(d.fe[0][2]);
-    cm.zend[1] = cm.zend[0] + chunks(d.fe[1][2]);
-    cm.zend[2] = cm.zend[1] + chunks(d.fe[2][2]);
-    cm.zend[3] = cm.zend[2] + chunks(d.n[2]);
-    dim3 grid((d.n[0] + 127) / 128, d.n[1], cm.zend[3]);
-    k_stokes_cols<T><<<grid, 128, 0, s>>>(d, cm, eta, v, p, yv, yp);
+    const int bx = d.n[0] >= 96 ? 128 : 32, by = 128 / bx;
+    dim3 grid((d.n[0] + bx - 1) / bx, (d.n[1] + by - 1) / by, (d.n[2] + kKChunk - 1) / kKChunk);
+    launch_cols(grid, s, d, eta, v, p, yv, yp);
   } else {
     const i64 n = d.fo[3] + d.nc;
     k_stokes_apply<T><<<nblk(n, bs), bs, 0, s>>>(d, eta, v, p, yv, yp);
