@@ -266,10 +266,11 @@ uint64_t rbfib_launch_count(void);
 
 /* Kernel timer for roofline reports.  which: 0 off, 1 saddle matvec (Stokes
  * stencil + body rows), 2 finest-level velocity smoothing sweep, 3 Krylov
- * multi-column inner product, 4 Krylov multi-axpy, 5 lower multigrid levels
- * run in one CTA (counted in FP32 operations instead of bytes: 13 per point
- * update, 180 per coarse point of the fused residual-restriction, 16 per
- * prolonged point).  While a class is
+ * multi-column inner product, 4 Krylov multi-axpy, 5 exact solve of the
+ * coarse multigrid level by fast diagonalisation, one CTA per grid (counted
+ * in FP32 operations instead of bytes: per grid of n points and extents
+ * e_x, e_y, e_z, 4 n (e_x + e_y + e_z) for the six 1D transforms plus n
+ * divisions).  While a class is
  * selected, CUDA events are recorded on the grid's stream around each of its
  * launches and the algorithmic bytes of each launch are added up (matvec:
  * 2 n s + 24 N_bl + 56 N_b; smoothing sweep: 2 N_f s; inner product over k

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librbfib.so")
-SOURCES = ["k_stokes.cu", "k_ib.cu", "k_body.cu", "k_krylov.cu", "k_noise.cu", "rbfib.cu", "batch.cu"]
+SOURCES = ["k_stokes.cu", "k_fdsolve.cu", "k_ib.cu", "k_body.cu", "k_krylov.cu", "k_noise.cu", "rbfib.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

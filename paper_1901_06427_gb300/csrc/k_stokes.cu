@@ -2,6 +2,8 @@
 // the geometric multigrid used by the projection preconditioner of the
 // velocity-pressure block.  Templated on the storage/arithmetic type T
 // (double for the FP64 path, float inside FP64 iterative refinement).
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -259,6 +261,238 @@ inline void launch_cols(dim3 gr, cudaStream_t s, const Dims& d, double eta, cons
                         double* yv, double* yp) {
   k_stokes_cols_f64<<<gr, dim3(d.n[0] >= 96 ? 128 : 32, d.n[0] >= 96 ? 1 : 4), 0, s>>>(d, eta, v, p, yv, yp);
 }
+
+// Pipelined 2.5D Stokes operator for large grids (uniform spacing).  A 32 x 8
+// block owns a 32 x 8 tile of all four grids and marches a chunk of kPZ
+// z-planes.  Each plane of the tile, with a one-point halo in x and y, is
+// copied into a ring of kPS shared-memory stages by cp.async, kPD planes ahead
+// of the plane being computed, so every thread keeps several planes of loads
+// in flight instead of waiting on each one.  All neighbours (x, y from the
+// staged halo, z from the neighbouring stages) are read from shared memory;
+// one barrier per plane.  Each staged value is fetched from global memory
+// once per block (halo rows and planes are shared with neighbouring blocks
+// through L2).
+constexpr int kPX = 32, kPY = 8, kPZ = 32;
+constexpr int kPW = kPX + 2, kPH = kPY + 2, kPSlots = kPW * kPH;   // staged plane of one grid
+constexpr int kPLoads = (kPSlots + kPX * kPY - 1) / (kPX * kPY);    // slots per thread
+// planes in flight ahead of the one computed, and ring stages (the planes
+// k - 1, k, k + 1 being read plus the ones in flight): deeper for FP32, whose
+// kernel is bound by bytes in flight; FP64 is bound by its arithmetic.
+template <typename T> __host__ __device__ constexpr int pipe_depth() { return sizeof(T) == 4 ? 6 : 3; }
+template <typename T> __host__ __device__ constexpr int pipe_stages() { return pipe_depth<T>() + 3; }
+template <typename T>
+__host__ __device__ constexpr int pipe_smem_bytes() { return pipe_stages<T>() * 4 * kPSlots * (int)sizeof(T); }
+
+// Copies one element, or writes zero to the slot when nbytes == 0 (the source
+// is then not read).
+template <typename T>
+RBFIB_DEVFN void cp_async_elem(unsigned dst, const T* src, unsigned nbytes) {
+  if constexpr (sizeof(T) == 8) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(nbytes) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(nbytes) : "memory");
+  }
+}
+template <typename T>
+RBFIB_DEVFN void cp_async_elem(unsigned dst, const T* src) {
+  if constexpr (sizeof(T) == 8) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+  }
+}
+RBFIB_DEVFN void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+RBFIB_DEVFN void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename T, bool PX, bool PY, bool PZ>
+RBFIB_DEVFN void stokes_pipe_body(const Dims& d, T eta, const T* __restrict__ v, const T* __restrict__ p,
+                                  T* __restrict__ yv, T* __restrict__ yp, T* sm) {
+  constexpr int kPD = pipe_depth<T>(), kPS = pipe_stages<T>();
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + kPX * ty;
+  const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kPY;
+  const int k0 = blockIdx.z * kPZ;
+  const int nx = d.n[0], ny = d.n[1], nz = d.n[2];
+  const int k1 = min(k0 + kPZ, nz);
+  // grid g = 0, 1, 2: face components; g = 3: pressure cells
+  const T* src[4] = {v + d.fo[0], v + d.fo[1], v + d.fo[2], p};
+  unsigned psz[4];
+  int ezm[4];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const int* e = g < 3 ? d.fe[g] : d.n;
+    ezm[g] = e[2] - 1;
+    psz[g] = (unsigned)e[0] * (unsigned)e[1];
+  }
+  // Staging: thread tid fills slot tid and, for tid < kPSlots - 256, slot
+  // tid + 256 of each grid's (kPH x kPW) plane tile.  Points beyond a wall
+  // (and whole planes beyond a z wall) are staged as zero, so neighbours that
+  // do not exist add nothing to the stencil sums; their source offsets are
+  // clamped onto the grid and not read.
+  unsigned off[kPLoads][4];
+  unsigned okm = 0;
+#pragma unroll
+  for (int l = 0; l < kPLoads; ++l) {
+    const int s = min(tid + kPX * kPY * l, kPSlots - 1);
+    const int ly = s / kPW, lx = s - ly * kPW;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const int* e = g < 3 ? d.fe[g] : d.n;
+      int gx = x0 + lx - 1, gy = y0 + ly - 1;
+      bool ok = true;
+      if (PX) gx = (gx + e[0]) % e[0];
+      else { ok = ok && gx >= 0 && gx < e[0]; gx = min(max(gx, 0), e[0] - 1); }
+      if (PY) gy = (gy + e[1]) % e[1];
+      else { ok = ok && gy >= 0 && gy < e[1]; gy = min(max(gy, 0), e[1] - 1); }
+      off[l][g] = (unsigned)gx + (unsigned)e[0] * (unsigned)gy;
+      if (ok) okm |= 1u << (4 * l + g);
+    }
+  }
+  const bool second = tid + kPX * kPY < kPSlots;
+  constexpr unsigned kGridBytes = kPSlots * sizeof(T), kStageBytes = 4 * kGridBytes;
+  const unsigned dst0 = (unsigned)__cvta_generic_to_shared(sm) + (unsigned)tid * (unsigned)sizeof(T);
+  // a tile whose staged points all lie inside every grid on the x and y walls
+  // (block-uniform), on a plane that exists for all four grids, copies
+  // without per-slot tests
+  const bool tile_in = (PX || (x0 >= 1 && x0 + kPX <= nx - 2)) && (PY || (y0 >= 1 && y0 + kPY <= ny - 2));
+  int ist = 0;   // stage of the next plane to issue
+  auto issue = [&](int kk) {
+    if (kk <= k1) {
+      const unsigned dst = dst0 + (unsigned)ist * kStageBytes;
+      if (tile_in && (PZ || (kk >= 0 && kk <= nz - 2))) {
+        const int zz = PZ ? (kk < 0 ? kk + nz : (kk >= nz ? kk - nz : kk)) : kk;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const T* base = src[g] + psz[g] * (unsigned)zz;
+          cp_async_elem<T>(dst + g * kGridBytes, base + off[0][g]);
+          if (second) cp_async_elem<T>(dst + g * kGridBytes + kPX * kPY * sizeof(T), base + off[1][g]);
+        }
+      } else {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          int zz;
+          unsigned nb = (unsigned)sizeof(T);
+          if (PZ) zz = kk < 0 ? kk + nz : (kk >= nz ? kk - nz : kk);
+          else {
+            if (kk < 0 || kk > ezm[g]) nb = 0u;
+            zz = min(max(kk, 0), ezm[g]);
+          }
+          const T* base = src[g] + psz[g] * (unsigned)zz;
+          cp_async_elem<T>(dst + g * kGridBytes, base + off[0][g], (okm >> g & 1u) ? nb : 0u);
+          if (second)
+            cp_async_elem<T>(dst + g * kGridBytes + kPX * kPY * sizeof(T), base + off[1][g],
+                             (okm >> (4 + g) & 1u) ? nb : 0u);
+        }
+      }
+      ist = ist + 1 < kPS ? ist + 1 : 0;
+    }
+    cp_async_commit();
+  };
+  // prologue: planes k0 - 1 .. k0 + kPD
+#pragma unroll
+  for (int q = 0; q < kPD + 2; ++q) issue(k0 - 1 + q);
+
+  const int i = x0 + tx, j = y0 + ty;
+  const T s = eta * inv_h2<T>(d, 0), ih = inv_h<T>(d, 0);
+  const int c0 = (ty + 1) * kPW + tx + 1;   // this thread's centre slot
+  constexpr bool pxw = !PX, pyw = !PY;
+  // momentum rows: per component, in-plane validity, the diagonal times
+  // eta/h^2 (a missing neighbour across a tangential wall is the ghost -u0,
+  // which adds one to the diagonal), output offset at plane 0
+  bool in[3];
+  T sdiag[3];
+  unsigned obase[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int* e = d.fe[a];
+    in[a] = i < e[0] && j < e[1];
+    int dg = 6;
+    if (a != 0 && pxw) dg += (i == 0) + (i == e[0] - 1);
+    if (a != 1 && pyw) dg += (j == 0) + (j == e[1] - 1);
+    sdiag[a] = s * (T)dg;
+    obase[a] = (unsigned)d.fo[a] + (unsigned)i + (unsigned)e[0] * (unsigned)j;
+  }
+  const bool inc = i < nx && j < ny;
+  const unsigned cbase = (unsigned)i + (unsigned)nx * (unsigned)j;
+  int stm = 0;   // stage of plane k - 1
+  for (int k = k0; k < k1; ++k) {
+    cp_async_wait<kPD - 1>();
+    __syncthreads();
+    issue(k + kPD + 1);
+    const int st0 = stm + 1 < kPS ? stm + 1 : 0;
+    const int stp = st0 + 1 < kPS ? st0 + 1 : 0;
+    const T* Sm = sm + stm * 4 * kPSlots;
+    const T* S0 = sm + st0 * 4 * kPSlots;
+    const T* Sp = sm + stp * 4 * kPSlots;
+    stm = st0;
+    // ghosts across the z walls for the tangential components
+    const T zadj = PZ ? T(0) : s * (T)((k == 0) + (k == nz - 1));
+    const T pc = S0[3 * kPSlots + c0];
+    T uc[3], um[3], ux[3], uy[3], uzm[3], uzp[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const T* U0 = S0 + a * kPSlots;
+      uc[a] = U0[c0];
+      um[a] = U0[c0 - 1];
+      ux[a] = U0[c0 + 1];
+      uy[a] = U0[c0 - kPW];
+      const T yq = U0[c0 + kPW];
+      uzm[a] = Sm[a * kPSlots + c0];
+      uzp[a] = Sp[a * kPSlots + c0];
+      const T nb = ((um[a] + ux[a]) + (uy[a] + yq)) + (uzm[a] + uzp[a]);
+      const T sd = a != 2 ? sdiag[a] + zadj : sdiag[a];
+      T dp;
+      if (a == 0) dp = pxw ? S0[3 * kPSlots + c0 + 1] - pc : pc - S0[3 * kPSlots + c0 - 1];
+      else if (a == 1) dp = pyw ? S0[3 * kPSlots + c0 + kPW] - pc : pc - S0[3 * kPSlots + c0 - kPW];
+      else dp = PZ ? pc - Sm[3 * kPSlots + c0] : Sp[3 * kPSlots + c0] - pc;
+      const T y = sd * uc[a] - s * nb + dp * ih;
+      const bool store = in[a] && (a != 2 || PZ || k < nz - 1);
+      if (store) yv[obase[a] + psz[a] * (unsigned)k] = y;
+      if (a == 1) uy[1] = yq;   // divergence uses the +y neighbour of v_y when y is periodic
+    }
+    // divergence: faces beyond a wall were staged as zero
+    T div = pxw ? uc[0] - um[0] : ux[0] - uc[0];
+    div += pyw ? uc[1] - S0[kPSlots + c0 - kPW] : uy[1] - uc[1];
+    div += PZ ? uzp[2] - uc[2] : uc[2] - uzm[2];
+    if (inc) yp[cbase + psz[3] * (unsigned)k] = -div * ih;
+  }
+  // drain the (empty or unused) groups still in flight before the block exits
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+template <typename T, bool PX, bool PY, bool PZ>
+__global__ void __launch_bounds__(kPX * kPY, sizeof(T) == 4 ? 4 : 3)
+    k_stokes_pipe(Dims d, T eta, const T* __restrict__ v, const T* __restrict__ p, T* __restrict__ yv,
+                  T* __restrict__ yp) {
+  extern __shared__ __align__(16) unsigned char pipe_smem[];
+  stokes_pipe_body<T, PX, PY, PZ>(d, eta, v, p, yv, yp, reinterpret_cast<T*>(pipe_smem));
+}
+template <typename T, bool PX, bool PY, bool PZ>
+void launch_pipe_as(const Dims& d, cudaStream_t s, T eta, const T* v, const T* p, T* yv, T* yp) {
+  static std::once_flag f;
+  std::call_once(f, [] {
+    cudaFuncSetAttribute(k_stokes_pipe<T, PX, PY, PZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         pipe_smem_bytes<T>());
+  });
+  dim3 gr((d.n[0] + kPX - 1) / kPX, (d.n[1] + kPY - 1) / kPY, (d.n[2] + kPZ - 1) / kPZ);
+  k_stokes_pipe<T, PX, PY, PZ><<<gr, dim3(kPX, kPY), pipe_smem_bytes<T>(), s>>>(d, eta, v, p, yv, yp);
+}
+template <typename T>
+void launch_pipe(const Dims& d, cudaStream_t s, T eta, const T* v, const T* p, T* yv, T* yp) {
+  switch ((d.per[0] ? 1 : 0) | (d.per[1] ? 2 : 0) | (d.per[2] ? 4 : 0)) {
+    case 0: launch_pipe_as<T, false, false, false>(d, s, eta, v, p, yv, yp); break;
+    case 1: launch_pipe_as<T, true, false, false>(d, s, eta, v, p, yv, yp); break;
+    case 2: launch_pipe_as<T, false, true, false>(d, s, eta, v, p, yv, yp); break;
+    case 3: launch_pipe_as<T, true, true, false>(d, s, eta, v, p, yv, yp); break;
+    case 4: launch_pipe_as<T, false, false, true>(d, s, eta, v, p, yv, yp); break;
+    case 5: launch_pipe_as<T, true, false, true>(d, s, eta, v, p, yv, yp); break;
+    case 6: launch_pipe_as<T, false, true, true>(d, s, eta, v, p, yv, yp); break;
+    default: launch_pipe_as<T, true, true, true>(d, s, eta, v, p, yv, yp); break;
+  }
+}
+// The pipelined kernel serves grids with at least this many unknowns (the
+// column kernel fills the GPU better on small grids).
+constexpr i64 kPipeMinUnknowns = (i64)2 * 1024 * 1024;
 
 // ------------------------------------------ velocity multigrid (A = -eta LL)
 // Diagonal of -LL at a face (ghost faces across tangential walls add 1/h^2).
@@ -664,9 +898,13 @@ template <typename T>
 void stokes_apply(const Dims& d, T eta, const T* v, const T* p, T* yv, T* yp, cudaStream_t s, int bs) {
   const bool uniform = d.h[0] == d.h[1] && d.h[1] == d.h[2];
   if (uniform && d.fo[3] + d.nc < ((i64)1 << 31)) {
-    const int bx = d.n[0] >= 96 ? 128 : 32, by = 128 / bx;
-    dim3 grid((d.n[0] + bx - 1) / bx, (d.n[1] + by - 1) / by, (d.n[2] + kKChunk - 1) / kKChunk);
-    launch_cols(grid, s, d, eta, v, p, yv, yp);
+    if (d.fo[3] + d.nc >= kPipeMinUnknowns) {
+      launch_pipe(d, s, eta, v, p, yv, yp);
+    } else {
+      const int bx = d.n[0] >= 96 ? 128 : 32, by = 128 / bx;
+      dim3 grid((d.n[0] + bx - 1) / bx, (d.n[1] + by - 1) / by, (d.n[2] + kKChunk - 1) / kKChunk);
+      launch_cols(grid, s, d, eta, v, p, yv, yp);
+    }
   } else {
     const i64 n = d.fo[3] + d.nc;
     k_stokes_apply<T><<<nblk(n, bs), bs, 0, s>>>(d, eta, v, p, yv, yp);
@@ -778,362 +1016,5 @@ void add_grad(const Dims& d, const T* phi, T* v, cudaStream_t s) {
 INST(double)
 INST(float)
 #undef INST
-
-}  // namespace rbfib
-
-// ===================================================================
-// Lower part of a V-cycle in one thread-block cluster.
-// Every level from l0 down to the coarsest is small enough for one cluster
-// of 8 CTAs; the phases of the V-cycle (half sweeps, restriction, coarse
-// solve, prolongation) are separated by hardware cluster barriers instead of
-// kernel launches.  Loads go through L2 (ld.global.cg) so that values written
-// by other CTAs of the cluster before a barrier are seen after it.
-#include <cooperative_groups.h>
-#include <mutex>
-
-namespace rbfib {
-namespace cgx = cooperative_groups;
-
-// Loads of the tail: from L2 (cluster variant, data written by other CTAs)
-// or plain (shared-memory variant).
-template <bool SH, typename T>
-RBFIB_DEVFN T ldt(const T* p) {
-  if constexpr (SH) return *p; else return __ldcg(p);
-}
-template <typename T>
-RBFIB_DEVFN T ldg2(const T* p) { return __ldcg(p); }
-
-template <bool SH, typename T>
-RBFIB_DEVFN void lap_parts_c(const Dims& d, const T* v, int a, const int c[3], T& nbsum, T& diag) {
-  nbsum = T(0);
-  diag = T(0);
-  const i64 base = d.fo[a];
-  const int* e = d.fe[a];
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) {
-    const T ih2 = inv_h2<T>(d, ax);
-    diag += T(2) * ih2;
-    int lo[3] = {c[0], c[1], c[2]}, hi[3] = {c[0], c[1], c[2]};
-    lo[ax] -= 1; hi[ax] += 1;
-    if (d.per[ax]) {
-      if (lo[ax] < 0) lo[ax] += e[ax];
-      if (hi[ax] >= e[ax]) hi[ax] -= e[ax];
-      nbsum += (ldt<SH>(v + base + flat3(e, lo[0], lo[1], lo[2])) + ldt<SH>(v + base + flat3(e, hi[0], hi[1], hi[2]))) * ih2;
-    } else {
-      if (lo[ax] >= 0) nbsum += ldt<SH>(v + base + flat3(e, lo[0], lo[1], lo[2])) * ih2;
-      else if (ax != a) diag += ih2;
-      if (hi[ax] < e[ax]) nbsum += ldt<SH>(v + base + flat3(e, hi[0], hi[1], hi[2])) * ih2;
-      else if (ax != a) diag += ih2;
-    }
-  }
-}
-
-template <bool SH, typename T>
-RBFIB_DEVFN void plap_parts_c(const Dims& d, const T* p, const int c[3], T& nbsum, T& diag) {
-  nbsum = T(0); diag = T(0);
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) {
-    const T ih2 = inv_h2<T>(d, ax);
-    int lo[3] = {c[0], c[1], c[2]}, hi[3] = {c[0], c[1], c[2]};
-    lo[ax] -= 1; hi[ax] += 1;
-    if (d.per[ax]) {
-      if (lo[ax] < 0) lo[ax] += d.n[ax];
-      if (hi[ax] >= d.n[ax]) hi[ax] -= d.n[ax];
-      nbsum += (ldt<SH>(p + flat3(d.n, lo[0], lo[1], lo[2])) + ldt<SH>(p + flat3(d.n, hi[0], hi[1], hi[2]))) * ih2;
-      diag += T(2) * ih2;
-    } else {
-      if (lo[ax] >= 0) { nbsum += ldt<SH>(p + flat3(d.n, lo[0], lo[1], lo[2])) * ih2; diag += ih2; }
-      if (hi[ax] < d.n[ax]) { nbsum += ldt<SH>(p + flat3(d.n, hi[0], hi[1], hi[2])) * ih2; diag += ih2; }
-    }
-  }
-}
-
-constexpr int kTailCtas = 8;
-constexpr int kTailThreads = 1024;
-
-// Body of the lower V-cycle for the face grids.  u[l], rhs[l]: level arrays
-// (global or shared), barrier: cluster or block synchronisation.
-template <bool SH, typename T, typename Sync>
-RBFIB_DEVFN void vel_tail_body(const TailParams& P, T* const* u, T* const* rhs, T eta, unsigned tid, unsigned nthr,
-                               Sync sync) {
-  auto half = [&](int l, int color) {
-    const TailLevel& L = P.lev[l];
-    const unsigned cnt = L.cm.cnt[0] + L.cm.cnt[1] + L.cm.cnt[2];
-    for (unsigned t = tid; t < cnt; t += nthr) {
-      int a, c[3];
-      if (!color_face(L.d, L.cm, t, color, a, c)) continue;
-      T nb, dg;
-      lap_parts_c<SH>(L.d, u[l], a, c, nb, dg);
-      const i64 id = L.d.fo[a] + flat3(L.d.fe[a], c[0], c[1], c[2]);
-      u[l][id] = (ldt<SH>(rhs[l] + id) / eta + nb) / dg;
-    }
-    sync();
-  };
-  for (int l = P.l0; l < P.L - 1; ++l) {
-    const TailLevel& L = P.lev[l];
-    for (unsigned t = tid; t < (unsigned)L.d.fo[3]; t += nthr) {
-      int a, c[3];
-      decode_face(L.d, t, a, c);
-      u[l][t] = (((c[0] + c[1] + c[2]) & 1) == 0) ? ldt<SH>(rhs[l] + t) / (eta * lap_diag<T>(L.d, a, c)) : T(0);
-    }
-    sync();
-    half(l, 1);
-    for (int s = 1; s < P.nu; ++s) { half(l, 0); half(l, 1); }
-    const TailLevel& C = P.lev[l + 1];
-    for (unsigned t = tid; t < (unsigned)C.d.fo[3]; t += nthr) {
-      int a, c[3];
-      decode_face(C.d, t, a, c);
-      const int cf[3] = {L.cz.x, L.cz.y, L.cz.z};
-      T1 s[3];
-#pragma unroll
-      for (int ax = 0; ax < 3; ++ax) {
-        int kind = !cf[ax] ? 0 : (ax == a ? (L.d.per[ax] ? 1 : 2) : 3);
-        restrict_1d(kind, c[ax], L.d.fe[a][ax], s[ax]);
-      }
-      float acc = 0.f;
-      for (int x = 0; x < s[0].cnt; ++x)
-        for (int y = 0; y < s[1].cnt; ++y)
-          for (int z = 0; z < s[2].cnt; ++z) {
-            const int fc[3] = {s[0].idx[x], s[1].idx[y], s[2].idx[z]};
-            T nb, dg;
-            lap_parts_c<SH>(L.d, (const T*)u[l], a, fc, nb, dg);
-            const i64 id = L.d.fo[a] + flat3(L.d.fe[a], fc[0], fc[1], fc[2]);
-            const T r = ldt<SH>(rhs[l] + id) - eta * (dg * ldt<SH>(u[l] + id) - nb);
-            acc += (s[0].w[x] * s[1].w[y] * s[2].w[z]) * (float)r;
-          }
-      rhs[l + 1][t] = (T)acc;
-    }
-    sync();
-  }
-  {
-    const int l = P.L - 1;
-    for (unsigned t = tid; t < (unsigned)P.lev[l].d.fo[3]; t += nthr) u[l][t] = T(0);
-    sync();
-    for (int s = 0; s < P.sweeps; ++s) { half(l, 0); half(l, 1); }
-  }
-  for (int l = P.L - 2; l >= P.l0; --l) {
-    const TailLevel& L = P.lev[l];
-    const TailLevel& C = P.lev[l + 1];
-    for (unsigned t = tid; t < (unsigned)L.d.fo[3]; t += nthr) {
-      int a, c[3];
-      decode_face(L.d, t, a, c);
-      const int cf[3] = {L.cz.x, L.cz.y, L.cz.z};
-      T1 s[3];
-#pragma unroll
-      for (int ax = 0; ax < 3; ++ax) {
-        int kind = !cf[ax] ? 0 : (ax == a ? (L.d.per[ax] ? 1 : 2) : 3);
-        prolong_1d(kind, c[ax], C.d.fe[a][ax], L.d.per[ax] ? 2.0f : -1.0f, s[ax]);
-      }
-      float acc = 0.f;
-      for (int x = 0; x < s[0].cnt; ++x)
-        for (int y = 0; y < s[1].cnt; ++y)
-          for (int z = 0; z < s[2].cnt; ++z)
-            acc += (s[0].w[x] * s[1].w[y] * s[2].w[z]) *
-                   (float)ldt<SH>(u[l + 1] + C.d.fo[a] + flat3(C.d.fe[a], s[0].idx[x], s[1].idx[y], s[2].idx[z]));
-      u[l][t] = ldt<SH>(u[l] + t) + (T)acc;
-    }
-    sync();
-    for (int s = 0; s < P.nu; ++s) { half(l, 1); half(l, 0); }
-  }
-}
-
-template <bool SH, typename T, typename Sync>
-RBFIB_DEVFN void p_tail_body(const TailParams& P, T* const* u, T* const* rhs, unsigned tid, unsigned nthr, Sync sync) {
-  auto half = [&](int l, int color) {
-    const TailLevel& L = P.lev[l];
-    for (unsigned t = tid; t < L.cm.cnt[0]; t += nthr) {
-      int c[3];
-      if (!color_cell(L.d, L.cm, t, color, c)) continue;
-      T nb, dg;
-      plap_parts_c<SH>(L.d, u[l], c, nb, dg);
-      const i64 id = flat3(L.d.n, c[0], c[1], c[2]);
-      u[l][id] = (ldt<SH>(rhs[l] + id) + nb) / dg;
-    }
-    sync();
-  };
-  for (int l = P.l0; l < P.L - 1; ++l) {
-    const TailLevel& L = P.lev[l];
-    for (unsigned t = tid; t < (unsigned)L.d.nc; t += nthr) {
-      int c[3];
-      decode_cell(L.d, t, c);
-      u[l][t] = (((c[0] + c[1] + c[2]) & 1) == 0) ? ldt<SH>(rhs[l] + t) / plap_diag<T>(L.d, c) : T(0);
-    }
-    sync();
-    half(l, 1);
-    for (int s = 1; s < P.nu; ++s) { half(l, 0); half(l, 1); }
-    const TailLevel& C = P.lev[l + 1];
-    for (unsigned t = tid; t < (unsigned)C.d.nc; t += nthr) {
-      int c[3];
-      decode_cell(C.d, t, c);
-      const int cf[3] = {L.cz.x, L.cz.y, L.cz.z};
-      T1 s[3];
-#pragma unroll
-      for (int ax = 0; ax < 3; ++ax) restrict_1d(cf[ax] ? 3 : 0, c[ax], L.d.n[ax], s[ax]);
-      float acc = 0.f;
-      for (int x = 0; x < s[0].cnt; ++x)
-        for (int y = 0; y < s[1].cnt; ++y)
-          for (int z = 0; z < s[2].cnt; ++z) {
-            const int fc[3] = {s[0].idx[x], s[1].idx[y], s[2].idx[z]};
-            T nb, dg;
-            plap_parts_c<SH>(L.d, (const T*)u[l], fc, nb, dg);
-            const i64 id = flat3(L.d.n, fc[0], fc[1], fc[2]);
-            acc += (s[0].w[x] * s[1].w[y] * s[2].w[z]) * (float)(ldt<SH>(rhs[l] + id) - (dg * ldt<SH>(u[l] + id) - nb));
-          }
-      rhs[l + 1][t] = (T)acc;
-    }
-    sync();
-  }
-  {
-    const int l = P.L - 1;
-    const unsigned n = (unsigned)P.lev[l].d.nc;
-    if (tid == 0) {
-      double sm = 0.0;
-      for (unsigned t = 0; t < n; ++t) sm += (double)ldt<SH>(rhs[l] + t);
-      const T mean = (T)(sm / (double)n);
-      for (unsigned t = 0; t < n; ++t) rhs[l][t] = ldt<SH>(rhs[l] + t) - mean;
-    }
-    for (unsigned t = tid; t < n; t += nthr) u[l][t] = T(0);
-    sync();
-    for (int s = 0; s < P.sweeps; ++s) { half(l, 0); half(l, 1); }
-  }
-  for (int l = P.L - 2; l >= P.l0; --l) {
-    const TailLevel& L = P.lev[l];
-    const TailLevel& C = P.lev[l + 1];
-    for (unsigned t = tid; t < (unsigned)L.d.nc; t += nthr) {
-      int c[3];
-      decode_cell(L.d, t, c);
-      const int cf[3] = {L.cz.x, L.cz.y, L.cz.z};
-      T1 s[3];
-#pragma unroll
-      for (int ax = 0; ax < 3; ++ax) prolong_1d(cf[ax] ? 3 : 0, c[ax], C.d.n[ax], L.d.per[ax] ? 2.0f : 1.0f, s[ax]);
-      float acc = 0.f;
-      for (int x = 0; x < s[0].cnt; ++x)
-        for (int y = 0; y < s[1].cnt; ++y)
-          for (int z = 0; z < s[2].cnt; ++z)
-            acc += (s[0].w[x] * s[1].w[y] * s[2].w[z]) *
-                   (float)ldt<SH>(u[l + 1] + flat3(C.d.n, s[0].idx[x], s[1].idx[y], s[2].idx[z]));
-      u[l][t] = ldt<SH>(u[l] + t) + (T)acc;
-    }
-    sync();
-    for (int s = 0; s < P.nu; ++s) { half(l, 1); half(l, 0); }
-  }
-}
-
-// Cluster variant: level arrays in global memory, cluster barriers.
-template <typename T>
-__global__ void __cluster_dims__(kTailCtas, 1, 1) __launch_bounds__(kTailThreads)
-k_vel_tail(TailParams P, T eta) {
-  cgx::cluster_group cl = cgx::this_cluster();
-  T* u[kMaxTail];
-  T* r[kMaxTail];
-  for (int l = 0; l < kMaxTail; ++l) { u[l] = (T*)P.lev[l].u; r[l] = (T*)P.lev[l].rhs; }
-  vel_tail_body<false, T>(P, u, r, eta, blockIdx.x * kTailThreads + threadIdx.x, kTailCtas * kTailThreads,
-                          [&]() { cl.sync(); });
-}
-
-template <typename T>
-__global__ void __cluster_dims__(kTailCtas, 1, 1) __launch_bounds__(kTailThreads)
-k_p_tail(TailParams P) {
-  cgx::cluster_group cl = cgx::this_cluster();
-  T* u[kMaxTail];
-  T* r[kMaxTail];
-  for (int l = 0; l < kMaxTail; ++l) { u[l] = (T*)P.lev[l].u; r[l] = (T*)P.lev[l].rhs; }
-  p_tail_body<false, T>(P, u, r, blockIdx.x * kTailThreads + threadIdx.x, kTailCtas * kTailThreads,
-                        [&]() { cl.sync(); });
-}
-
-// Shared-memory variant (one CTA): every tail level lives in shared memory;
-// the top level's right-hand side is loaded from global memory and its
-// solution written back.
-template <typename T>
-__global__ void __launch_bounds__(kTailThreads) k_vel_tail_smem(TailParams Pg, T eta) {
-  extern __shared__ unsigned char shraw[];
-  __shared__ TailParams P;   // level descriptors in shared memory (indexed by level at run time)
-  for (int i = threadIdx.x; i < (int)(sizeof(TailParams) / 4); i += blockDim.x)
-    ((int*)&P)[i] = ((const int*)&Pg)[i];
-  __syncthreads();
-  __shared__ T* u[kMaxTail];
-  __shared__ T* r[kMaxTail];
-  if (threadIdx.x == 0) {
-    T* p = (T*)shraw;
-    for (int l = P.l0; l < P.L; ++l) {
-      const i64 n = P.lev[l].d.fo[3];
-      u[l] = p; p += n;
-      r[l] = p; p += n;
-    }
-  }
-  __syncthreads();
-  const i64 n0 = P.lev[P.l0].d.fo[3];
-  const T* g_rhs = (const T*)P.lev[P.l0].rhs;
-  for (i64 t = threadIdx.x; t < n0; t += blockDim.x) r[P.l0][t] = g_rhs[t];
-  __syncthreads();
-  vel_tail_body<true, T>(P, u, r, eta, threadIdx.x, blockDim.x, []() { __syncthreads(); });
-  T* g_u = (T*)P.lev[P.l0].u;
-  for (i64 t = threadIdx.x; t < n0; t += blockDim.x) g_u[t] = u[P.l0][t];
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kTailThreads) k_p_tail_smem(TailParams Pg) {
-  extern __shared__ unsigned char shraw[];
-  __shared__ TailParams P;
-  for (int i = threadIdx.x; i < (int)(sizeof(TailParams) / 4); i += blockDim.x)
-    ((int*)&P)[i] = ((const int*)&Pg)[i];
-  __syncthreads();
-  __shared__ T* u[kMaxTail];
-  __shared__ T* r[kMaxTail];
-  if (threadIdx.x == 0) {
-    T* p = (T*)shraw;
-    for (int l = P.l0; l < P.L; ++l) {
-      const i64 n = P.lev[l].d.nc;
-      u[l] = p; p += n;
-      r[l] = p; p += n;
-    }
-  }
-  __syncthreads();
-  const i64 n0 = P.lev[P.l0].d.nc;
-  const T* g_rhs = (const T*)P.lev[P.l0].rhs;
-  for (i64 t = threadIdx.x; t < n0; t += blockDim.x) r[P.l0][t] = g_rhs[t];
-  __syncthreads();
-  p_tail_body<true, T>(P, u, r, threadIdx.x, blockDim.x, []() { __syncthreads(); });
-  T* g_u = (T*)P.lev[P.l0].u;
-  for (i64 t = threadIdx.x; t < n0; t += blockDim.x) g_u[t] = u[P.l0][t];
-}
-
-size_t tail_smem_bytes(const TailParams& P, bool faces, size_t elem) {
-  size_t n = 0;
-  for (int l = P.l0; l < P.L; ++l) n += 2 * (size_t)(faces ? P.lev[l].d.fo[3] : P.lev[l].d.nc);
-  return n * elem;
-}
-
-template <typename T>
-void vel_tail(const TailParams& P, T eta, cudaStream_t s) {
-  const size_t shm = tail_smem_bytes(P, true, sizeof(T));
-  if (shm <= kTailSmemBytes) {
-    static std::once_flag once;
-    std::call_once(once, [] {
-      cudaFuncSetAttribute(k_vel_tail_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemBytes);
-    });
-    k_vel_tail_smem<T><<<1, kTailThreads, shm, s>>>(P, eta);
-  } else {
-    k_vel_tail<T><<<kTailCtas, kTailThreads, 0, s>>>(P, eta);
-  }
-  note_launch();
-}
-template <typename T>
-void p_tail(const TailParams& P, cudaStream_t s) {
-  const size_t shm = tail_smem_bytes(P, false, sizeof(T));
-  if (shm <= kTailSmemBytes) {
-    static std::once_flag once;
-    std::call_once(once, [] {
-      cudaFuncSetAttribute(k_p_tail_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemBytes);
-    });
-    k_p_tail_smem<T><<<1, kTailThreads, shm, s>>>(P);
-  } else {
-    k_p_tail<T><<<kTailCtas, kTailThreads, 0, s>>>(P);
-  }
-  note_launch();
-}
-template void vel_tail<float>(const TailParams&, float, cudaStream_t);
-template void p_tail<float>(const TailParams&, cudaStream_t);
 
 }  // namespace rbfib

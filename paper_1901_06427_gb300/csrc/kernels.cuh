@@ -1,6 +1,9 @@
 // Launchers of the device kernels, grouped by file.  All launches are
 // asynchronous on the given stream.
 #pragma once
+#include <string>
+#include <vector>
+
 #include "common.cuh"
 
 namespace rbfib {
@@ -71,24 +74,29 @@ template <typename T> void p_coarse(const Dims&, T* u, T* rhs, int sweeps, cudaS
 template <typename T> void div_q(const Dims&, T eta, const T* vt, const T* rpi, T* q, T* pi, cudaStream_t);
 template <typename T> void add_grad(const Dims&, const T* phi, T* v, cudaStream_t);
 
-// Lower part of a V-cycle in one 8-CTA cluster (k_stokes.cu)
-struct TailLevel {
-  Dims d;
-  int3 cz;
-  ColorMap cm;
-  void* u;
-  void* rhs;
+// Exact solve on a coarse multigrid level by fast diagonalisation (k_fdsolve.cu).
+// The level operator of each grid (a velocity component of -eta LL, or the
+// pressure operator -D G) is a Kronecker sum of 1D second differences; with
+// orthonormal 1D eigenbases Q_x, Q_y, Q_z and eigenvalues l_x, l_y, l_z,
+// A^-1 = (Q_x (x) Q_y (x) Q_z) diag(1 / (s (l_x + l_y + l_z))) (Q_x (x) Q_y (x) Q_z)^T,
+// the zero mode of a singular operator dropped (pseudo-inverse).
+constexpr int kFDMaxPoints = 4096;   // points of one grid
+constexpr int kFDMaxExtent = 64;     // points along one axis
+struct FDGrid {
+  int e[3];        // extents
+  long long off;   // offset of the grid in the level's solution / rhs arrays
+  int tab0, tabn;  // segment of the basis table: per axis Q (e x e), Q^T (e x e), eigenvalues (e)
+  float scale;     // operator scale (eta for velocity, 1 for pressure)
 };
-constexpr int kMaxTail = 10;
-struct TailParams {
-  int l0, L, nu, sweeps;
-  TailLevel lev[kMaxTail];
+struct FDParams {
+  int ng;          // grids (3 face components or 1 pressure grid), one CTA each
+  FDGrid g[3];
+  const float* tab;
+  int smem;        // dynamic shared memory bytes of the largest grid
 };
-constexpr long long kTailMaxUnknowns = 8LL * 1024 * 4;   // per level, faces or cells (cluster variant)
-constexpr size_t kTailSmemBytes = 190 * 1024;             // shared-memory variant limit (dynamic part)
-size_t tail_smem_bytes(const TailParams& P, bool faces, size_t elem);
-template <typename T> void vel_tail(const TailParams&, T eta, cudaStream_t);
-template <typename T> void p_tail(const TailParams&, cudaStream_t);
+// Bases of every grid of a level; false if some grid exceeds the limits.
+bool fd_plan(const Dims& d, bool faces, double eta, std::vector<float>& tab, FDParams& P, std::string& why);
+void fd_solve(const FDParams& P, float* u, const float* rhs, cudaStream_t s);
 
 // k_ib.cu
 void geometry(int nbl, const int* bob, const double* ref, const double* q, const double* quat,

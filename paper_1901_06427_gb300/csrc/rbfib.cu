@@ -121,6 +121,9 @@ struct rbfib_grid {
   cudaStream_t s = nullptr;
   std::string err;
   std::vector<Level> levels;
+  int fd_vel = -1, fd_p = -1;   // levels solved exactly by fast diagonalisation (-1: none)
+  FDParams fdv{}, fdp{};
+  DBuf<float> fd_tab;
   Dims d{};
   Walls walls{};
   i64 nf = 0, nc = 0, nfl = 0;
@@ -205,7 +208,7 @@ struct TimerScope {
   }
 };
 
-enum { TK_MATVEC = 1, TK_SMOOTH = 2, TK_DOT = 3, TK_AXPY = 4, TK_TAIL = 5 };
+enum { TK_MATVEC = 1, TK_SMOOTH = 2, TK_DOT = 3, TK_AXPY = 4, TK_COARSE = 5 };
 
 void drop_graphs(rbfib_grid* g) {
   for (auto& row : g->cgraph)
@@ -273,64 +276,25 @@ KrylovStore<double>& kr_of<double>(rbfib_grid* g) { return g->kr64; }
 template <>
 KrylovStore<float>& kr_of<float>(rbfib_grid* g) { return g->kr32; }
 
-const int kNu = 2;       // pre- and post-smoothing sweeps on the GPU-wide levels
-const int kNuTail = 1;   // on the small levels run inside one CTA
-const long long kTailStartUnknowns = 4096;
-
+const int kNu = 2;       // pre- and post-smoothing sweeps
 int coarse_sweeps(const Dims& d) { return std::max(d.n[0], std::max(d.n[1], d.n[2])) + 2; }
 
-// First level handled by the cluster tail: the first level whose unknowns
-// fit one 8-CTA cluster (every coarser level then fits too).
-// Prefer the shared-memory tail (levels l.. fit one CTA's shared memory); the
-// cluster tail only when some level still exceeds it.
-int tail_start(const std::vector<Level>& L, bool faces) {
-  const int n = (int)L.size();
-  for (int l = 0; l < n; ++l) {
-    if (n - l > kMaxTail) continue;
-    if ((faces ? L[l].d.fo[3] : L[l].d.nc) > kTailStartUnknowns) continue;   // keep big levels GPU-wide
-    size_t bytes = 0;
-    for (int k = l; k < n; ++k) bytes += 2 * sizeof(float) * (size_t)(faces ? L[k].d.fo[3] : L[k].d.nc);
-    if (bytes <= kTailSmemBytes) return l;
-  }
-  return n - 1;
-}
-
-TailParams tail_params(rbfib_grid* g, int l0, const std::vector<void*>& u, const std::vector<void*>& rhs,
-                       bool faces) {
-  TailParams P{};
-  P.l0 = l0;
-  P.L = (int)g->levels.size();
-  P.nu = kNuTail;
-  P.sweeps = coarse_sweeps(g->levels[P.L - 1].d);
-  for (int l = l0; l < P.L; ++l) {
-    TailLevel& T = P.lev[l];
-    T.d = g->levels[l].d;
-    T.cz = g->levels[l].cz;
-    T.cm = faces ? make_color_map_faces(T.d) : make_color_map_cells(T.d);
-    T.u = u[l];
-    T.rhs = rhs[l];
-  }
-  return P;
-}
-
-// Algorithmic FP32 operations of one tail launch: every point update of a
-// red-black sweep is a 7-point stencil (13 operations); the fused
-// restriction evaluates up to 12 fine residuals per coarse point; the
-// prolongation adds up to 8 weighted coarse values per fine point.
-double tail_flops(const TailParams& P, bool faces) {
+// Algorithmic FP32 operations of one coarse-level solve by fast
+// diagonalisation: per grid six 1D transforms (one FMA per point and
+// transform-axis entry) and one division per point.
+double fd_flops(const FDParams& P) {
   double f = 0.0;
-  auto npts = [&](int l) { return (double)(faces ? P.lev[l].d.fo[3] : P.lev[l].d.nc); };
-  for (int l = P.l0; l < P.L - 1; ++l) {
-    f += 2.0 * P.nu * npts(l) * 13.0 * 2.0;     // pre + post sweeps, both colours
-    f += npts(l + 1) * 12.0 * 15.0;            // fused residual-restriction
-    f += npts(l) * 8.0 * 2.0;                  // prolongation
+  for (int g = 0; g < P.ng; ++g) {
+    const double n = (double)P.g[g].e[0] * P.g[g].e[1] * P.g[g].e[2];
+    f += 2.0 * 2.0 * n * (P.g[g].e[0] + P.g[g].e[1] + P.g[g].e[2]) + n;
   }
-  f += 2.0 * P.sweeps * npts(P.L - 1) * 13.0;  // coarsest sweeps
   return f;
 }
 
 // u0 <- V-cycle approximation of (-eta LL)^{-1} rhs0 (zero initial guess).
-// Levels above the tail run as separate kernels; the rest in one cluster.
+// FP32: the levels above the coarse level are smoothed by red-black
+// Gauss-Seidel and the coarse level is solved exactly (fast
+// diagonalisation); otherwise the coarsest level gets coarse_sweeps sweeps.
 template <typename T>
 void vcycle_vel(rbfib_grid* g, T* u0, const T* rhs0) {
   MGStore<T>& M = mg_of<T>(g);
@@ -345,7 +309,8 @@ void vcycle_vel(rbfib_grid* g, T* u0, const T* rhs0) {
     TimerScope ts(g, l == 0 ? TK_SMOOTH : -1, 2.0 * (double)d.fo[3] * sizeof(T));
     vel_rbgs<T>(d, eta, color, u[l], rhs[l], g->s, l == 0 ? g->tune.vrbgs : 256);
   };
-  const int lt = std::is_same<T, float>::value && L <= kMaxTail ? tail_start(g->levels, true) : L - 1;
+  const bool fd = std::is_same<T, float>::value && g->fd_vel >= 0;
+  const int lt = fd ? g->fd_vel : L - 1;
   for (int l = 0; l < lt; ++l) {
     const Dims& d = g->levels[l].d;
     vel_first<T>(d, eta, u[l], rhs[l], g->s);          // zero guess + first colour-0 update
@@ -354,11 +319,9 @@ void vcycle_vel(rbfib_grid* g, T* u0, const T* rhs0) {
     vel_restrict_res<T>(d, g->levels[l + 1].d, g->levels[l].cz, eta, u[l], rhs[l], rhs[l + 1], g->s);
   }
   if constexpr (std::is_same<T, float>::value) {
-    if (L <= kMaxTail) {
-      std::vector<void*> uu(u.begin(), u.end()), rr(rhs.begin(), rhs.end());
-      const TailParams P = tail_params(g, lt, uu, rr, true);
-      TimerScope ts(g, TK_TAIL, tail_flops(P, true));
-      vel_tail<float>(P, eta, g->s);
+    if (fd) {
+      TimerScope ts(g, TK_COARSE, fd_flops(g->fdv));
+      fd_solve(g->fdv, u[lt], rhs[lt], g->s);
     } else {
       vel_coarse<T>(g->levels[L - 1].d, eta, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
     }
@@ -381,7 +344,8 @@ void vcycle_p(rbfib_grid* g, T* u0, T* rhs0) {
   for (int l = 0; l < L; ++l) { u[l] = *M.pu[l]; rhs[l] = *M.prhs[l]; }
   u[0] = u0;
   rhs[0] = rhs0;
-  const int lt = std::is_same<T, float>::value && L <= kMaxTail ? tail_start(g->levels, false) : L - 1;
+  const bool fd = std::is_same<T, float>::value && g->fd_p >= 0;
+  const int lt = fd ? g->fd_p : L - 1;
   for (int l = 0; l < lt; ++l) {
     const Dims& d = g->levels[l].d;
     const int bs = l == 0 ? g->tune.prbgs : 256;
@@ -391,11 +355,9 @@ void vcycle_p(rbfib_grid* g, T* u0, T* rhs0) {
     p_restrict_res<T>(d, g->levels[l + 1].d, g->levels[l].cz, u[l], rhs[l], rhs[l + 1], g->s);
   }
   if constexpr (std::is_same<T, float>::value) {
-    if (L <= kMaxTail) {
-      std::vector<void*> uu(u.begin(), u.end()), rr(rhs.begin(), rhs.end());
-      const TailParams P = tail_params(g, lt, uu, rr, false);
-      TimerScope ts(g, TK_TAIL, tail_flops(P, false));
-      p_tail<float>(P, g->s);
+    if (fd) {
+      TimerScope ts(g, TK_COARSE, fd_flops(g->fdp));
+      fd_solve(g->fdp, u[lt], rhs[lt], g->s);
     } else {
       p_coarse<T>(g->levels[L - 1].d, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
     }
@@ -722,6 +684,24 @@ void build_levels(rbfib_grid* g) {
   }
 }
 
+// Coarse levels of the FP32 V-cycles: the finest level whose grids all fit
+// one CTA's exact solve, for the velocity components and for the pressure.
+void build_fd(rbfib_grid* g) {
+  std::vector<float> tab;
+  g->fd_vel = g->fd_p = -1;
+  std::string why;
+  for (int l = 0; l < (int)g->levels.size() && g->fd_vel < 0; ++l)
+    if (fd_plan(g->levels[l].d, true, g->desc.eta, tab, g->fdv, why)) g->fd_vel = l;
+  for (int l = 0; l < (int)g->levels.size() && g->fd_p < 0; ++l)
+    if (fd_plan(g->levels[l].d, false, 1.0, tab, g->fdp, why)) g->fd_p = l;
+  if (tab.empty()) return;
+  g->fd_tab.alloc(tab.size());
+  ck(cudaMemcpyAsync(g->fd_tab.p, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, g->s));
+  ck(cudaStreamSynchronize(g->s));
+  g->fdv.tab = g->fd_tab.p;
+  g->fdp.tab = g->fd_tab.p;
+}
+
 void build_stress_layout(rbfib_grid* g) {
   i64 off = 0;
   for (int a = 0; a < 3; ++a) {
@@ -994,6 +974,7 @@ int rbfib_create_grid(const rbfib_grid_desc* desc, void* stream, rbfib_grid** ou
     g->desc = D;
     g->s = (cudaStream_t)stream;
     build_levels(g);
+    build_fd(g);
     g->d = g->levels[0].d;
     for (int w = 0; w < 6; ++w)
       for (int c = 0; c < 3; ++c) g->walls.v[w][c] = D.wall_vel[w][c];

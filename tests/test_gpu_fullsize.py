@@ -82,3 +82,22 @@ def test_two_sphere_sem_step_against_oracle(B):
         assert info8[k]["rel_residual"] <= 1e-8
     dq8 = q8.cpu().numpy() - np.array(gold["q0"])
     assert rel(dq8, np.array(gold["q"]) - np.array(gold["q0"])) < 1e-5
+
+
+@pytest.mark.parametrize("periodic,wall_speed", [((False, False, False), 0.0), ((True, False, False), 0.3),
+                                                 ((False, True, True), 0.0)])
+def test_matvec_large_grid(B, periodic, wall_speed):
+    """Grids above two million unknowns take the pipelined Stokes kernel; the
+    sizes leave ragged tiles in x, y and z."""
+    w = workloads.small_case(n=(100, 90, 76), periodic=periodic, n_bodies=3, blobs=12, seed=1,
+                             wall_speed=wall_speed)
+    g = B.grid_for(w)
+    assert g.n_total > 2 * 1024 * 1024
+    og = oracle.Grid(w.n, periodic=w.periodic, wall_vel=w.wall_vel)
+    ob = saddle.Bodies(w.ref_blobs, w.blob_offsets, w.q, w.quat)
+    x = np.random.default_rng(3).standard_normal(g.n_total)
+    y0 = saddle.apply(og, ob, w.eta, x)
+    y = g.apply_saddle(dev(x)).cpu().numpy()
+    assert rel(y, y0) < 1e-11
+    y32 = g.apply_saddle(torch.tensor(x, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+    assert rel(y32, y0) < 1e-5
