@@ -5,6 +5,8 @@
 // configuration: dense RPY matrix, in-place Gauss-Jordan inverse (FP32, no
 // pivoting: the RPY matrix is symmetric positive definite), P = M^-1 K,
 // N = (K^T M^-1 K)^-1 (FP64).  Applied by one CTA.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -136,33 +138,63 @@ void dense_body_build(int nbl, int nb, const int* boff, const double* r, const d
   note_launch();
 }
 
-// Apply (one block): t = M^-1 s; f = r_U + K^T t; U = N f; y = K U - s;
-// lam = M^-1 y.  s, r_U in, lam, U out (type T; internal FP32 / FP64).
+// Apply on one cluster of kBodyCtas CTAs: t = M^-1 s; f = r_U + K^T t;
+// U = N f; lam = M^-1 (K U - s) = P U - t with P = M^-1 K from the set-up.
+// The rows of t, U and lam are split over the CTAs; t and U are exchanged
+// through distributed shared memory.  s, r_U in, lam, U out (type T;
+// internal FP32 / FP64).
+constexpr int kBodyCtas = 8;
+
 template <typename T>
-__global__ void k_dense_body_apply(int nbl, int nb, const int* __restrict__ boff, const int* __restrict__ bob,
-                                   const double* __restrict__ arm, const float* __restrict__ Mi,
-                                   const double* __restrict__ N, const T* __restrict__ sres, const T* __restrict__ rU,
-                                   T* __restrict__ zlam, T* __restrict__ zU) {
+__global__ void __cluster_dims__(kBodyCtas, 1, 1) __launch_bounds__(512)
+    k_dense_body_apply(int nbl, int nb, const int* __restrict__ boff, const int* __restrict__ bob,
+                       const double* __restrict__ arm, const float* __restrict__ Mi, const float* __restrict__ P,
+                       const double* __restrict__ N, const T* __restrict__ sres, const T* __restrict__ rU,
+                       T* __restrict__ zlam, T* __restrict__ zU) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
   extern __shared__ unsigned char shraw[];
   const int n3 = 3 * nbl, m = 6 * nb;
-  double* f = (double*)shraw;          // m
-  double* U = f + m;                   // m
-  float* tv = (float*)(U + m);         // n3
-  float* sv = tv + n3;                 // n3
+  const int rank = (int)cl.block_rank();
+  const int rpc = (n3 + kBodyCtas - 1) / kBodyCtas, upc = (m + kBodyCtas - 1) / kBodyCtas;
+  const int r0 = rank * rpc, r1 = min(n3, r0 + rpc);
+  const int u0 = rank * upc, u1 = min(m, u0 + upc);
+  double* f = (double*)shraw;      // m
+  double* Uall = f + m;            // m
+  double* Uloc = Uall + m;         // upc (this CTA's rows of U)
+  float* sv = (float*)(Uloc + upc);   // n3
+  float* tloc = sv + n3;              // rpc (this CTA's rows of t)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < n3; i += blockDim.x) sv[i] = (float)sres[i];
   __syncthreads();
-  for (int row = wid; row < n3; row += nw) {
-    float acc = 0.f;
-    for (int c = lane; c < n3; c += 32) acc += Mi[(i64)row * n3 + c] * sv[c];
+  // rows of t = M^-1 s, one warp per row
+  for (int row = r0 + wid; row < r1; row += nw) {
+    const float* Mr = Mi + (i64)row * n3;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int c = lane;
+    for (; c + 96 < n3; c += 128) {
+      a0 = fmaf(Mr[c], sv[c], a0);
+      a1 = fmaf(Mr[c + 32], sv[c + 32], a1);
+      a2 = fmaf(Mr[c + 64], sv[c + 64], a2);
+      a3 = fmaf(Mr[c + 96], sv[c + 96], a3);
+    }
+    for (; c < n3; c += 32) a0 = fmaf(Mr[c], sv[c], a0);
+    float acc = (a0 + a1) + (a2 + a3);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) tv[row] = acc;
+    if (lane == 0) tloc[row - r0] = acc;
   }
-  __syncthreads();
+  cl.sync();
+  // f = r_U + K^T t (every CTA, t read from its owners)
   for (int p = wid; p < nb; p += nw) {
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int i = boff[p] + lane; i < boff[p + 1]; i += 32) {
-      const double x = tv[3 * i], y = tv[3 * i + 1], z = tv[3 * i + 2];
+      double t3[3];
+      for (int a = 0; a < 3; ++a) {
+        const int row = 3 * i + a, owner = row / rpc;
+        const float* tr = cl.map_shared_rank(tloc, owner);
+        t3[a] = tr[row - owner * rpc];
+      }
+      const double x = t3[0], y = t3[1], z = t3[2];
       const double* d = arm + 3 * i;
       acc[0] += x; acc[1] += y; acc[2] += z;
       acc[3] += d[1] * z - d[2] * y;
@@ -174,43 +206,43 @@ __global__ void k_dense_body_apply(int nbl, int nb, const int* __restrict__ boff
     if (lane < 6) f[6 * p + lane] = acc[lane] + (double)rU[6 * p + lane];
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+  // this CTA's rows of U = N f
+  for (int r = u0 + (int)threadIdx.x; r < u1; r += blockDim.x) {
     double acc = 0.0;
-    for (int c = 0; c < m; ++c) acc += N[(i64)r * m + c] * f[c];
-    U[r] = acc;
+    for (int c = 0; c < m; ++c) acc = fma(N[(i64)r * m + c], f[c], acc);
+    Uloc[r - u0] = acc;
+    zU[r] = (T)acc;
+  }
+  cl.sync();
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    const int owner = c / upc;
+    Uall[c] = cl.map_shared_rank(Uloc, owner)[c - owner * upc];
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < n3; t += blockDim.x) {
-    const int i = t / 3, a = t - 3 * i, p = bob[i];
-    const double* d = arm + 3 * i;
-    const double* Up = U + 6 * p;
-    double cr;
-    if (a == 0) cr = Up[4] * d[2] - Up[5] * d[1];
-    else if (a == 1) cr = Up[5] * d[0] - Up[3] * d[2];
-    else cr = Up[3] * d[1] - Up[4] * d[0];
-    tv[t] = (float)(Up[a] + cr) - sv[t];
+  // this CTA's rows of lam = P U - t
+  for (int row = r0 + (int)threadIdx.x; row < r1; row += blockDim.x) {
+    const float* Pr = P + (i64)row * m;
+    float acc = -tloc[row - r0];
+    for (int c = 0; c < m; ++c) acc = fmaf(Pr[c], (float)Uall[c], acc);
+    zlam[row] = (T)acc;
   }
-  __syncthreads();
-  for (int row = wid; row < n3; row += nw) {
-    float acc = 0.f;
-    for (int c = lane; c < n3; c += 32) acc += Mi[(i64)row * n3 + c] * tv[c];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) zlam[row] = (T)acc;
-  }
-  for (int r = threadIdx.x; r < m; r += blockDim.x) zU[r] = (T)U[r];
+  cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
 template <typename T>
 void dense_body_apply(int nbl, int nb, const int* boff, const int* bob, const double* arm, const float* Minv,
-                      const double* N, const T* sres, const T* rU, T* zlam, T* zU, cudaStream_t s) {
-  const size_t shm = sizeof(double) * 12 * (size_t)nb + sizeof(float) * 6 * (size_t)nbl;
-  k_dense_body_apply<T><<<1, 1024, shm, s>>>(nbl, nb, boff, bob, arm, Minv, N, sres, rU, zlam, zU);
+                      const float* P, const double* N, const T* sres, const T* rU, T* zlam, T* zU, cudaStream_t s) {
+  const int n3 = 3 * nbl, m = 6 * nb;
+  const int rpc = (n3 + kBodyCtas - 1) / kBodyCtas, upc = (m + kBodyCtas - 1) / kBodyCtas;
+  const size_t shm = sizeof(double) * (2 * (size_t)m + upc) + sizeof(float) * ((size_t)n3 + rpc);
+  k_dense_body_apply<T><<<kBodyCtas, 512, shm, s>>>(nbl, nb, boff, bob, arm, Minv, P, N, sres, rU, zlam, zU);
   note_launch();
 }
 
-template void dense_body_apply<float>(int, int, const int*, const int*, const double*, const float*, const double*,
-                                      const float*, const float*, float*, float*, cudaStream_t);
-template void dense_body_apply<double>(int, int, const int*, const int*, const double*, const float*, const double*,
-                                       const double*, const double*, double*, double*, cudaStream_t);
+template void dense_body_apply<float>(int, int, const int*, const int*, const double*, const float*, const float*,
+                                      const double*, const float*, const float*, float*, float*, cudaStream_t);
+template void dense_body_apply<double>(int, int, const int*, const int*, const double*, const float*,
+                                       const float*, const double*, const double*, const double*, double*, double*,
+                                       cudaStream_t);
 
 }  // namespace rbfib

@@ -138,6 +138,19 @@ __global__ void k_scale(T* __restrict__ out, const T* __restrict__ in, const dou
     out[i] = (T)((double)in[i] * f);
 }
 
+// Occupies the stream for a fixed number of SM clock cycles (one thread;
+// ends by itself).  Used by the kernel timer so that the host has queued a
+// timed launch and its closing event before the stream reaches them.
+__global__ void k_delay(long long cycles) {
+  const long long t0 = clock64();
+  while (clock64() - t0 < cycles) {
+  }
+}
+void gpu_delay(long long cycles, cudaStream_t s) {
+  k_delay<<<1, 1, 0, s>>>(cycles);
+  note_launch();
+}
+
 template <typename T>
 void scale_by(T* out, const T* in, const double* denom, int invert, i64 n, cudaStream_t s) {
   const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);

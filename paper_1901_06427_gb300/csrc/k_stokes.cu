@@ -118,19 +118,19 @@ __global__ void k_stokes_apply(Dims d, T eta, const T* __restrict__ v, const T* 
 }
 
 // Column-chunked Stokes operator for uniform spacing.  A thread owns one
-// (x, y) point and one chunk of kKChunk z-planes and computes, in turn, the
+// (x, y) point and one chunk of KC z-planes (kKChunk, or 2 on small grids) and computes, in turn, the
 // three momentum rows (one per face grid) and the divergence row of that
 // column chunk, so the pressure and velocity rows it touches are reused from
 // L1/L2 by all four rows instead of being fetched once per grid.  Along z the
 // neighbours stay in registers.  No index divisions; 32-bit offsets.
 constexpr int kKChunk = 8;
 
-template <typename T>
+template <int KC, typename T>
 RBFIB_DEVFN void momentum_column(const Dims& d, int a, int i, int j, int k0, T eta, T ih, T ih2,
                                  const T* __restrict__ v, const T* __restrict__ p, T* __restrict__ yv) {
   const int e0 = d.fe[a][0], e1 = d.fe[a][1], e2 = d.fe[a][2];
   if (i >= e0 || j >= e1 || k0 >= e2) return;
-  const int k1 = min(k0 + kKChunk, e2);
+  const int k1 = min(k0 + KC, e2);
   const int nx = d.n[0], ny = d.n[1];
   const unsigned base = (unsigned)d.fo[a];
   const unsigned sy = (unsigned)e0, sz = (unsigned)e0 * (unsigned)e1;
@@ -166,7 +166,7 @@ RBFIB_DEVFN void momentum_column(const Dims& d, int a, int i, int j, int k0, T e
   else hzm = false;
   const T s = eta * ih2;
 #pragma unroll
-  for (int kk = 0; kk < kKChunk; ++kk) {
+  for (int kk = 0; kk < KC; ++kk) {
     const int k = k0 + kk;
     if (k >= k1) break;
     T up = T(0);
@@ -190,12 +190,12 @@ RBFIB_DEVFN void momentum_column(const Dims& d, int a, int i, int j, int k0, T e
   }
 }
 
-template <typename T>
+template <int KC, typename T>
 RBFIB_DEVFN void divergence_column(const Dims& d, int i, int j, int k0, T ih, const T* __restrict__ v,
                                    T* __restrict__ yp) {
   const int nx = d.n[0], ny = d.n[1], nz = d.n[2];
   if (i >= nx || j >= ny || k0 >= nz) return;
-  const int k1 = min(k0 + kKChunk, nz);
+  const int k1 = min(k0 + KC, nz);
   // x faces: compact index along x of the right / left face of cell i
   const int ex0 = d.fe[0][0], ey1 = d.fe[1][1];
   const T* vx = v + (unsigned)d.fo[0];
@@ -211,7 +211,7 @@ RBFIB_DEVFN void divergence_column(const Dims& d, int i, int j, int k0, T ih, co
   const unsigned syy = (unsigned)nx * (unsigned)ey1;            // y-face plane
   const unsigned szz = (unsigned)nx * (unsigned)ny;             // z-face plane
 #pragma unroll
-  for (int kk = 0; kk < kKChunk; ++kk) {
+  for (int kk = 0; kk < KC; ++kk) {
     const int k = k0 + kk;
     if (k >= k1) break;
     T div = T(0);
@@ -229,37 +229,41 @@ RBFIB_DEVFN void divergence_column(const Dims& d, int i, int j, int k0, T ih, co
   }
 }
 
-template <typename T>
+template <int KC, typename T>
 RBFIB_DEVFN void stokes_cols_body(const Dims& d, T eta, const T* __restrict__ v, const T* __restrict__ p,
                                   T* __restrict__ yv, T* __restrict__ yp) {
-  const int k0 = kKChunk * (int)blockIdx.z;
+  const int k0 = KC * (int)blockIdx.z;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const T ih = inv_h<T>(d, 0), ih2 = inv_h2<T>(d, 0);
-  momentum_column<T>(d, 0, i, j, k0, eta, ih, ih2, v, p, yv);
-  momentum_column<T>(d, 1, i, j, k0, eta, ih, ih2, v, p, yv);
-  momentum_column<T>(d, 2, i, j, k0, eta, ih, ih2, v, p, yv);
-  divergence_column<T>(d, i, j, k0, ih, v, yp);
+  momentum_column<KC, T>(d, 0, i, j, k0, eta, ih, ih2, v, p, yv);
+  momentum_column<KC, T>(d, 1, i, j, k0, eta, ih, ih2, v, p, yv);
+  momentum_column<KC, T>(d, 2, i, j, k0, eta, ih, ih2, v, p, yv);
+  divergence_column<KC, T>(d, i, j, k0, ih, v, yp);
 }
 
-// One thread per (i, j) column and kKChunk z-planes, all four grids.
+// One thread per (i, j) column and KC z-planes, all four grids.
+template <int KC>
 __global__ void __launch_bounds__(128) k_stokes_cols_f32(Dims d, float eta, const float* __restrict__ v,
                                                              const float* __restrict__ p, float* __restrict__ yv,
                                                              float* __restrict__ yp) {
-  stokes_cols_body<float>(d, eta, v, p, yv, yp);
+  stokes_cols_body<KC, float>(d, eta, v, p, yv, yp);
 }
+template <int KC>
 __global__ void __launch_bounds__(128) k_stokes_cols_f64(Dims d, double eta, const double* __restrict__ v,
                                                          const double* __restrict__ p, double* __restrict__ yv,
                                                          double* __restrict__ yp) {
-  stokes_cols_body<double>(d, eta, v, p, yv, yp);
+  stokes_cols_body<KC, double>(d, eta, v, p, yv, yp);
 }
+template <int KC>
 inline void launch_cols(dim3 gr, cudaStream_t s, const Dims& d, float eta, const float* v, const float* p, float* yv,
                         float* yp) {
-  k_stokes_cols_f32<<<gr, dim3(d.n[0] >= 96 ? 128 : 32, d.n[0] >= 96 ? 1 : 4), 0, s>>>(d, eta, v, p, yv, yp);
+  k_stokes_cols_f32<KC><<<gr, dim3(d.n[0] >= 96 ? 128 : 32, d.n[0] >= 96 ? 1 : 4), 0, s>>>(d, eta, v, p, yv, yp);
 }
+template <int KC>
 inline void launch_cols(dim3 gr, cudaStream_t s, const Dims& d, double eta, const double* v, const double* p,
                         double* yv, double* yp) {
-  k_stokes_cols_f64<<<gr, dim3(d.n[0] >= 96 ? 128 : 32, d.n[0] >= 96 ? 1 : 4), 0, s>>>(d, eta, v, p, yv, yp);
+  k_stokes_cols_f64<KC><<<gr, dim3(d.n[0] >= 96 ? 128 : 32, d.n[0] >= 96 ? 1 : 4), 0, s>>>(d, eta, v, p, yv, yp);
 }
 
 // Pipelined 2.5D Stokes operator for large grids (uniform spacing).  A 32 x 8
@@ -551,6 +555,10 @@ __global__ void k_vel_residual(Dims d, T eta, const T* __restrict__ u, const T* 
 // in units of the adjacent interior value (-1 Dirichlet, +1 Neumann).
 struct T1 { int cnt; int idx[3]; float w[3]; };   // weights exact in FP32
 
+// Lanes that share one coarse point of the fused residual-restriction
+// (a power of two dividing 32).
+constexpr int kRestrictLanes = 4;
+
 __device__ inline void restrict_1d(int kind, int ic, int nfext, T1& s) {
   if (kind == 0) { s.cnt = 1; s.idx[0] = ic; s.w[0] = 1.0f; return; }
   if (kind == 3) { s.cnt = 2; s.idx[0] = 2 * ic; s.idx[1] = 2 * ic + 1; s.w[0] = s.w[1] = 0.5f; return; }
@@ -625,29 +633,35 @@ __global__ void k_vel_restrict(Dims df, Dims dc, int3 cz, const T* __restrict__ 
 template <typename T>
 __global__ void k_vel_restrict_res(Dims df, Dims dc, int3 cz, T eta, const T* __restrict__ uf,
                                    const T* __restrict__ rhsf, T* __restrict__ rc) {
-  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= dc.fo[3]) return;
-  int a, c[3];
-  decode_face(dc, t, a, c);
-  const int cf[3] = {cz.x, cz.y, cz.z};
-  T1 s[3];
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) {
-    int kind = !cf[ax] ? 0 : (ax == a ? (df.per[ax] ? 1 : 2) : 3);
-    restrict_1d(kind, c[ax], df.fe[a][ax], s[ax]);
-  }
+  // kRestrictLanes lanes per coarse point share its fine residuals
+  const i64 gt = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  const i64 t = gt / kRestrictLanes;
+  const int sub = (int)(gt % kRestrictLanes);
   float acc = 0.f;
-  for (int x = 0; x < s[0].cnt; ++x)
-    for (int y = 0; y < s[1].cnt; ++y)
-      for (int z = 0; z < s[2].cnt; ++z) {
-        const int fc[3] = {s[0].idx[x], s[1].idx[y], s[2].idx[z]};
-        T nb, dg;
-        lap_parts(df, uf, a, fc, nb, dg);
-        const i64 id = df.fo[a] + flat3(df.fe[a], fc[0], fc[1], fc[2]);
-        const T r = rhsf[id] - eta * (dg * uf[id] - nb);
-        acc += (s[0].w[x] * s[1].w[y] * s[2].w[z]) * (float)r;
-      }
-  rc[t] = (T)acc;
+  if (t < dc.fo[3]) {
+    int a, c[3];
+    decode_face(dc, t, a, c);
+    const int cf[3] = {cz.x, cz.y, cz.z};
+    T1 s[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      int kind = !cf[ax] ? 0 : (ax == a ? (df.per[ax] ? 1 : 2) : 3);
+      restrict_1d(kind, c[ax], df.fe[a][ax], s[ax]);
+    }
+    const int nyz = s[1].cnt * s[2].cnt, tot = s[0].cnt * nyz;
+    for (int q = sub; q < tot; q += kRestrictLanes) {
+      const int x = q / nyz, y = (q - x * nyz) / s[2].cnt, z = q - x * nyz - y * s[2].cnt;
+      const int fc[3] = {s[0].idx[x], s[1].idx[y], s[2].idx[z]};
+      T nb, dg;
+      lap_parts(df, uf, a, fc, nb, dg);
+      const i64 id = df.fo[a] + flat3(df.fe[a], fc[0], fc[1], fc[2]);
+      const T r = rhsf[id] - eta * (dg * uf[id] - nb);
+      acc += (s[0].w[x] * s[1].w[y] * s[2].w[z]) * (float)r;
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < kRestrictLanes; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (t < dc.fo[3] && sub == 0) rc[t] = (T)acc;
 }
 
 template <typename T>
@@ -758,25 +772,30 @@ __global__ void k_p_restrict(Dims df, Dims dc, int3 cz, const T* __restrict__ rf
 template <typename T>
 __global__ void k_p_restrict_res(Dims df, Dims dc, int3 cz, const T* __restrict__ uf, const T* __restrict__ rhsf,
                                  T* __restrict__ rc) {
-  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= dc.nc) return;
-  int c[3];
-  decode_cell(dc, t, c);
-  const int cf[3] = {cz.x, cz.y, cz.z};
-  T1 s[3];
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) restrict_1d(cf[ax] ? 3 : 0, c[ax], df.n[ax], s[ax]);
+  const i64 gt = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  const i64 t = gt / kRestrictLanes;
+  const int sub = (int)(gt % kRestrictLanes);
   float acc = 0.f;
-  for (int x = 0; x < s[0].cnt; ++x)
-    for (int y = 0; y < s[1].cnt; ++y)
-      for (int z = 0; z < s[2].cnt; ++z) {
-        const int fc[3] = {s[0].idx[x], s[1].idx[y], s[2].idx[z]};
-        T nb, dg;
-        plap_parts(df, uf, fc, nb, dg);
-        const i64 id = flat3(df.n, fc[0], fc[1], fc[2]);
-        acc += (s[0].w[x] * s[1].w[y] * s[2].w[z]) * (float)(rhsf[id] - (dg * uf[id] - nb));
-      }
-  rc[t] = (T)acc;
+  if (t < dc.nc) {
+    int c[3];
+    decode_cell(dc, t, c);
+    const int cf[3] = {cz.x, cz.y, cz.z};
+    T1 s[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) restrict_1d(cf[ax] ? 3 : 0, c[ax], df.n[ax], s[ax]);
+    const int nyz = s[1].cnt * s[2].cnt, tot = s[0].cnt * nyz;
+    for (int q = sub; q < tot; q += kRestrictLanes) {
+      const int x = q / nyz, y = (q - x * nyz) / s[2].cnt, z = q - x * nyz - y * s[2].cnt;
+      const int fc[3] = {s[0].idx[x], s[1].idx[y], s[2].idx[z]};
+      T nb, dg;
+      plap_parts(df, uf, fc, nb, dg);
+      const i64 id = flat3(df.n, fc[0], fc[1], fc[2]);
+      acc += (s[0].w[x] * s[1].w[y] * s[2].w[z]) * (float)(rhsf[id] - (dg * uf[id] - nb));
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < kRestrictLanes; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (t < dc.nc && sub == 0) rc[t] = (T)acc;
 }
 
 template <typename T>
@@ -901,9 +920,15 @@ void stokes_apply(const Dims& d, T eta, const T* v, const T* p, T* yv, T* yp, cu
     if (d.fo[3] + d.nc >= kPipeMinUnknowns) {
       launch_pipe(d, s, eta, v, p, yv, yp);
     } else {
+      // small grids: short z-chunks, for enough threads to fill the GPU
       const int bx = d.n[0] >= 96 ? 128 : 32, by = 128 / bx;
-      dim3 grid((d.n[0] + bx - 1) / bx, (d.n[1] + by - 1) / by, (d.n[2] + kKChunk - 1) / kKChunk);
-      launch_cols(grid, s, d, eta, v, p, yv, yp);
+      if (d.fo[3] + d.nc >= kPipeMinUnknowns / 4) {
+        dim3 grid((d.n[0] + bx - 1) / bx, (d.n[1] + by - 1) / by, (d.n[2] + kKChunk - 1) / kKChunk);
+        launch_cols<kKChunk>(grid, s, d, eta, v, p, yv, yp);
+      } else {
+        dim3 grid((d.n[0] + bx - 1) / bx, (d.n[1] + by - 1) / by, (d.n[2] + 1) / 2);
+        launch_cols<2>(grid, s, d, eta, v, p, yv, yp);
+      }
     }
   } else {
     const i64 n = d.fo[3] + d.nc;
@@ -925,7 +950,7 @@ void vel_first(const Dims& d, T eta, T* u, const T* rhs, cudaStream_t s) {
 template <typename T>
 void vel_restrict_res(const Dims& df, const Dims& dc, int3 cz, T eta, const T* uf, const T* rhsf, T* rc,
                       cudaStream_t s) {
-  k_vel_restrict_res<T><<<nblk(dc.fo[3], 256), 256, 0, s>>>(df, dc, cz, eta, uf, rhsf, rc);
+  k_vel_restrict_res<T><<<nblk(kRestrictLanes * dc.fo[3], 256), 256, 0, s>>>(df, dc, cz, eta, uf, rhsf, rc);
   note_launch();
 }
 template <typename T>
@@ -961,7 +986,7 @@ void p_first(const Dims& d, T* u, const T* rhs, cudaStream_t s) {
 }
 template <typename T>
 void p_restrict_res(const Dims& df, const Dims& dc, int3 cz, const T* uf, const T* rhsf, T* rc, cudaStream_t s) {
-  k_p_restrict_res<T><<<nblk(dc.nc, 256), 256, 0, s>>>(df, dc, cz, uf, rhsf, rc);
+  k_p_restrict_res<T><<<nblk(kRestrictLanes * dc.nc, 256), 256, 0, s>>>(df, dc, cz, uf, rhsf, rc);
   note_launch();
 }
 template <typename T>

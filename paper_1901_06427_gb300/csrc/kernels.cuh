@@ -134,8 +134,8 @@ void adjoint_positions(const Dims&, int nbl, const int* bob, const double* r, co
 void dense_body_build(int nbl, int nb, const int* boff, const double* r, const double* arm, double a, double eta,
                       float* Minv, float* P, double* N, int* status, cudaStream_t);
 template <typename T> void dense_body_apply(int nbl, int nb, const int* boff, const int* bob, const double* arm,
-                                            const float* Minv, const double* N, const T* sres, const T* rU,
-                                            T* zlam, T* zU, cudaStream_t);
+                                            const float* Minv, const float* P, const double* N, const T* sres,
+                                            const T* rU, T* zlam, T* zU, cudaStream_t);
 
 // k_krylov.cu
 // Weighted inner products <x, y>_W with weight wf on the first nfl entries
@@ -145,6 +145,7 @@ template <typename T> void multi_dot(const T* w, const T* V, i64 ldv, int ncols,
 template <typename T> void multi_axpy(T* w, const T* V, i64 ldv, int ncols, const double* coef, double sign,
                                       i64 n, i64 nfl, double wf, double* part, int nparts, double* nrm2,
                                       cudaStream_t);
+void gpu_delay(long long cycles, cudaStream_t);
 template <typename T> void scale_by(T* out, const T* in, const double* denom, int invert, i64 n, cudaStream_t);
 void givens_step(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                  const double* hcol2, const double* hnext2, double* res_out, cudaStream_t);

@@ -196,6 +196,9 @@ struct TimerScope {
         g->tev.push_back(e);
       }
     }
+    // the stream waits about 25 us first, so the timed launches are queued
+    // behind the opening event and it measures them, not host launch gaps
+    gpu_delay(50000, g->s);
     ck(cudaEventRecord(g->tev[g->tev_used], g->s));
     g->timer_bytes += bytes;
     g->timer_launches += 1;
@@ -403,7 +406,7 @@ void precond(rbfib_grid* g, const T* r, T* z, bool with_bodies) {
     T* sres = sres_of<T>(g);
     interp_res<T>(d, view_of(g, g->cur), zv, rl, sres, g->s);
     if (g->dense_body)
-      dense_body_apply<T>(g->nbl, g->nb, g->boff, g->bob, g->cur.arm, g->dM, g->dN, sres, rU, zl, zU, g->s);
+      dense_body_apply<T>(g->nbl, g->nb, g->boff, g->bob, g->cur.arm, g->dM, g->dP, g->dN, sres, rU, zl, zU, g->s);
     else
       body_precond<T>(view_of(g, g->cur), pview(g), sres, rU, zl, zU, g->s);
   }
