@@ -12,6 +12,8 @@
 #include <cmath>
 #include <mutex>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -100,59 +102,149 @@ bool basis_ok(AxisKind kind, int m, const std::vector<double>& Q, const std::vec
   return e1 <= 1e-12 * 4.0 * m && e2 <= 1e-13 * m;
 }
 
-// One 1D transform along axis AX: out[.., c, ..] = sum_t M[t * e + c] in[.., t, ..].
+// Basis rows in the table are padded to a multiple of 8 floats (zeros), so
+// that chunks of outputs read whole 16-byte words inside their row.
+RBFIB_DEVFN int fd_pad(int e) { return (e + 7) & ~7; }
+
+// One 1D transform along x (AX = 0) or y (AX = 1) of the planes [0, np) of a
+// slab (e0 x e1 x np, x fastest): out[.., c, ..] = sum_t M[t * ep + c] in[.., t, ..].
+// A thread takes kFDChunk consecutive outputs of one line (chunk-major order,
+// so a warp shares the basis rows, read as broadcast 16-byte loads) and keeps
+// them in registers while it walks the line's inputs once.
+constexpr int kFDChunk = 16;
 template <int AX>
-RBFIB_DEVFN void fd_pass(const float* __restrict__ in, float* __restrict__ out, const float* __restrict__ M, int e0,
-                         int e1, int e2) {
-  const int n = e0 * e1 * e2;
-  const int e = AX == 0 ? e0 : (AX == 1 ? e1 : e2);
-  const int st = AX == 0 ? 1 : (AX == 1 ? e0 : e0 * e1);
-  for (int o = threadIdx.x; o < n; o += blockDim.x) {
-    int c;
-    if (AX == 0) c = o % e0;
-    else if (AX == 1) c = (o / e0) % e1;
-    else c = o / (e0 * e1);
-    const float* src = in + (o - c * st);
-    float acc = 0.f;
-    for (int t = 0; t < e; ++t) acc = fmaf(M[t * e + c], src[t * st], acc);
-    out[o] = acc;
+__device__ __noinline__ void fd_pass_xy(const float* __restrict__ in, float* __restrict__ out,
+                                        const float* __restrict__ M, int e0, int e1, int np) {
+  const int e = AX == 0 ? e0 : e1;
+  const int ep = fd_pad(e);
+  const int st = AX == 0 ? 1 : e0;
+  const int nlines = (AX == 0 ? e1 : e0) * np;
+  const int nchunks = (e + kFDChunk - 1) / kFDChunk;
+  for (int it = threadIdx.x; it < nlines * nchunks; it += blockDim.x) {
+    const int ch = it / nlines, L = it - ch * nlines;
+    const int base = AX == 0 ? L * e0 : (L % e0) + e0 * e1 * (L / e0);
+    const int c0 = ch * kFDChunk;
+    // 16-byte words of the chunk inside the padded row (ep = e rounded up to
+    // 8); outputs past e come from the zero padding and are not stored
+    const int nq = min(kFDChunk, ep - c0) / 4;
+    float acc[kFDChunk];
+#pragma unroll
+    for (int c = 0; c < kFDChunk; ++c) acc[c] = 0.f;
+    const float* row = M + c0;
+    const float* src = in + base;
+#pragma unroll 2
+    for (int t = 0; t < e; ++t) {
+      const float xt = src[t * st];
+      const float4* r4 = reinterpret_cast<const float4*>(row + t * ep);
+#pragma unroll
+      for (int q = 0; q < kFDChunk / 4; ++q) {
+        if (q < nq) {
+          const float4 m = r4[q];
+          acc[4 * q] = fmaf(m.x, xt, acc[4 * q]);
+          acc[4 * q + 1] = fmaf(m.y, xt, acc[4 * q + 1]);
+          acc[4 * q + 2] = fmaf(m.z, xt, acc[4 * q + 2]);
+          acc[4 * q + 3] = fmaf(m.w, xt, acc[4 * q + 3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kFDChunk; ++c)
+      if (c0 + c < e) out[base + (c0 + c) * st] = acc[c];
   }
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(1024) k_fd_solve(FDParams P, float* __restrict__ u, const float* __restrict__ rhs) {
-  extern __shared__ float fsm[];
-  const FDGrid& G = P.g[blockIdx.x];
-  const int e0 = G.e[0], e1 = G.e[1], e2 = G.e[2], n = e0 * e1 * e2;
-  float* A = fsm;
-  float* B = A + n;
-  float* M = B + n;
-  for (int t = threadIdx.x; t < G.tabn; t += blockDim.x) M[t] = P.tab[G.tab0 + t];
-  for (int t = threadIdx.x; t < n; t += blockDim.x) A[t] = rhs[G.off + t];
-  __syncthreads();
-  // per axis: Q (forward uses M[t][c] = q_c(t)), Q^T (backward), eigenvalues
-  const float* Q0 = M;
-  const float* QT0 = Q0 + e0 * e0;
-  const float* L0 = QT0 + e0 * e0;
-  const float* Q1 = L0 + e0;
-  const float* QT1 = Q1 + e1 * e1;
-  const float* L1 = QT1 + e1 * e1;
-  const float* Q2 = L1 + e1;
-  const float* QT2 = Q2 + e2 * e2;
-  const float* L2 = QT2 + e2 * e2;
-  fd_pass<0>(A, B, Q0, e0, e1, e2);
-  fd_pass<1>(B, A, Q1, e0, e1, e2);
-  fd_pass<2>(A, B, Q2, e0, e1, e2);
-  for (int o = threadIdx.x; o < n; o += blockDim.x) {
-    const int i = o % e0, j = (o / e0) % e1, k = o / (e0 * e1);
-    const float s = G.scale * (L0[i] + L1[j] + L2[k]);
-    B[o] = s > 0.f ? B[o] / s : 0.f;   // the zero mode of a singular grid is dropped
+// The z-columns of one grid (e_z <= E, E a multiple of 8), spread over the
+// threads of the cluster: each column is read from the CTAs owning its
+// planes, transformed forward, scaled by the inverse eigenvalues, transformed
+// back and written to the same places.
+template <int E>
+__device__ __noinline__ void fd_columns(cooperative_groups::cluster_group& cl, float* A, const float* Q2,
+                                        const float* QT2, const float* L0, const float* L1, const float* L2,
+                                        float scale, int e0, int e1, int e2, int pz, int rank) {
+  const int pl = e0 * e1, p2 = fd_pad(e2);
+  for (int col = rank * blockDim.x + threadIdx.x; col < pl; col += kFDCtas * blockDim.x) {
+    const int i = col % e0, j = col / e0;
+    float x[E], y[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      x[k] = 0.f;
+      if (k < e2) {
+        const int owner = k / pz;
+        x[k] = cl.map_shared_rank(A, owner)[(k - owner * pz) * pl + col];
+      }
+    }
+    const float sxy = L0[i] + L1[j];
+#pragma unroll
+    for (int c = 0; c < E; ++c) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < E; ++k) acc = fmaf(Q2[min(k, e2 - 1) * p2 + c], x[k], acc);   // x[k] = 0 past e2
+      const float s = scale * (sxy + L2[c]);
+      y[c] = (c < e2 && s > 0.f) ? acc / s : 0.f;   // the zero mode of a singular grid is dropped
+    }
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      float acc = 0.f;
+#pragma unroll
+      for (int c = 0; c < E; ++c) acc = fmaf(QT2[min(c, e2 - 1) * p2 + k], y[c], acc);   // y[c] = 0 past e2
+      if (k < e2) {
+        const int owner = k / pz;
+        cl.map_shared_rank(A, owner)[(k - owner * pz) * pl + col] = acc;
+      }
+    }
   }
+}
+
+// One cluster of kFDCtas CTAs per grid.  CTA r owns the z-planes
+// [r pz, (r + 1) pz) of its grid in shared memory.  Forward x and y
+// transforms on the own planes; cluster barrier; each thread then takes whole
+// z-columns (read through distributed shared memory into registers), applies
+// the forward z transform, the eigenvalue scaling and the backward z
+// transform, and writes the column back; cluster barrier; backward y and x
+// transforms on the own planes.
+__global__ void __cluster_dims__(kFDCtas, 1, 1) __launch_bounds__(kFDThreads)
+    k_fd_solve(FDParams P, float* __restrict__ u, const float* __restrict__ rhs) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) float fsm[];
+  const FDGrid& G = P.g[blockIdx.x / kFDCtas];
+  const int rank = (int)cl.block_rank();
+  const int e0 = G.e[0], e1 = G.e[1], e2 = G.e[2], pl = e0 * e1;
+  const int pz = (e2 + kFDCtas - 1) / kFDCtas;
+  const int z0 = min(e2, rank * pz), np = min(e2, z0 + pz) - z0;
+  // table (16-byte aligned rows), then the two slab buffers
+  float* M = fsm;
+  float* A = M + ((G.tabn + 3) & ~3);
+  float* B = A + ((pz * pl + 3) & ~3);
+  for (int t = threadIdx.x; t < G.tabn; t += blockDim.x) M[t] = P.tab[G.tab0 + t];
+  for (int t = threadIdx.x; t < np * pl; t += blockDim.x) A[t] = rhs[G.off + (long long)z0 * pl + t];
   __syncthreads();
-  fd_pass<2>(B, A, QT2, e0, e1, e2);
-  fd_pass<1>(A, B, QT1, e0, e1, e2);
-  fd_pass<0>(B, A, QT0, e0, e1, e2);
-  for (int t = threadIdx.x; t < n; t += blockDim.x) u[G.off + t] = A[t];
+  // per axis: Q (forward uses M[t][c] = q_c(t)), Q^T (backward), both e x ep,
+  // then the eigenvalues (padded to ep); ep = e rounded up to 8
+  const int p0 = fd_pad(e0), p1 = fd_pad(e1), p2 = fd_pad(e2);
+  const float* Q0 = M;
+  const float* QT0 = Q0 + e0 * p0;
+  const float* L0 = QT0 + e0 * p0;
+  const float* Q1 = L0 + p0;
+  const float* QT1 = Q1 + e1 * p1;
+  const float* L1 = QT1 + e1 * p1;
+  const float* Q2 = L1 + p1;
+  const float* QT2 = Q2 + e2 * p2;
+  const float* L2 = QT2 + e2 * p2;
+  fd_pass_xy<0>(A, B, Q0, e0, e1, np);
+  fd_pass_xy<1>(B, A, Q1, e0, e1, np);
+  cl.sync();
+  // z-columns: forward transform, scaling, backward transform, in registers
+  const int rz = (e2 + 7) & ~7;
+  if (rz == 8) fd_columns<8>(cl, A, Q2, QT2, L0, L1, L2, G.scale, e0, e1, e2, pz, rank);
+  else if (rz == 16) fd_columns<16>(cl, A, Q2, QT2, L0, L1, L2, G.scale, e0, e1, e2, pz, rank);
+  else if (rz == 24) fd_columns<24>(cl, A, Q2, QT2, L0, L1, L2, G.scale, e0, e1, e2, pz, rank);
+  else fd_columns<32>(cl, A, Q2, QT2, L0, L1, L2, G.scale, e0, e1, e2, pz, rank);
+  cl.sync();
+  fd_pass_xy<1>(A, B, QT1, e0, e1, np);
+  fd_pass_xy<0>(B, A, QT0, e0, e1, np);
+  for (int t = threadIdx.x; t < np * pl; t += blockDim.x) u[G.off + (long long)z0 * pl + t] = A[t];
 }
 
 }  // namespace
@@ -170,7 +262,7 @@ bool fd_plan(const Dims& d, bool faces, double eta, std::vector<float>& tab, FDP
     for (int ax = 0; ax < 3; ++ax) {
       G.e[ax] = e[ax];
       n *= e[ax];
-      if (e[ax] < 1 || e[ax] > kFDMaxExtent) return fail("extent");
+      if (e[ax] < 1 || e[ax] > kFDLine) return fail("extent");
     }
     if (n > kFDMaxPoints) return fail("points");
     G.off = faces ? d.fo[g] : 0;
@@ -184,16 +276,19 @@ bool fd_plan(const Dims& d, bool faces, double eta, std::vector<float>& tab, FDP
       std::vector<double> Q, lam;
       axis_basis(kind, e[ax], Q, lam);
       if (!basis_ok(kind, e[ax], Q, lam)) return fail("basis check");
-      const int m = e[ax];
+      const int m = e[ax], mp = (m + 7) & ~7;
       const double ih2 = 1.0 / (d.h[ax] * d.h[ax]);
       for (int t = 0; t < m; ++t)
-        for (int c = 0; c < m; ++c) tab.push_back((float)Q[(size_t)t * m + c]);
+        for (int c = 0; c < mp; ++c) tab.push_back(c < m ? (float)Q[(size_t)t * m + c] : 0.f);
       for (int t = 0; t < m; ++t)
-        for (int c = 0; c < m; ++c) tab.push_back((float)Q[(size_t)c * m + t]);
-      for (int k = 0; k < m; ++k) tab.push_back((float)(lam[k] * ih2));
+        for (int c = 0; c < mp; ++c) tab.push_back(c < m ? (float)Q[(size_t)c * m + t] : 0.f);
+      for (int c = 0; c < mp; ++c) tab.push_back(c < m ? (float)(lam[c] * ih2) : 0.f);
     }
     G.tabn = (int)tab.size() - G.tab0;
-    smem = std::max(smem, (int)((2 * n + G.tabn) * sizeof(float)));
+    // every grid's segment starts on a 16-byte boundary of the table
+    while (tab.size() % 4) tab.push_back(0.f);
+    const long long slab = (long long)((e[2] + kFDCtas - 1) / kFDCtas) * e[0] * e[1];
+    smem = std::max(smem, (int)((((G.tabn + 3) & ~3) + 2 * ((slab + 3) & ~3)) * sizeof(float)));
   }
   P.smem = smem;
   return true;
@@ -202,10 +297,9 @@ bool fd_plan(const Dims& d, bool faces, double eta, std::vector<float>& tab, FDP
 void fd_solve(const FDParams& P, float* u, const float* rhs, cudaStream_t s) {
   static std::once_flag f;
   std::call_once(f, [] {
-    cudaFuncSetAttribute(k_fd_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)((2 * kFDMaxPoints + 3 * (2 * kFDMaxExtent * kFDMaxExtent + kFDMaxExtent)) * sizeof(float)));
+    cudaFuncSetAttribute(k_fd_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, kFDMaxSmem);
   });
-  k_fd_solve<<<P.ng, 1024, P.smem, s>>>(P, u, rhs);
+  k_fd_solve<<<P.ng * kFDCtas, kFDThreads, P.smem, s>>>(P, u, rhs);
   note_launch();
 }
 

@@ -80,8 +80,14 @@ template <typename T> void add_grad(const Dims&, const T* phi, T* v, cudaStream_
 // orthonormal 1D eigenbases Q_x, Q_y, Q_z and eigenvalues l_x, l_y, l_z,
 // A^-1 = (Q_x (x) Q_y (x) Q_z) diag(1 / (s (l_x + l_y + l_z))) (Q_x (x) Q_y (x) Q_z)^T,
 // the zero mode of a singular operator dropped (pseudo-inverse).
-constexpr int kFDMaxPoints = 4096;   // points of one grid
-constexpr int kFDMaxExtent = 64;     // points along one axis
+constexpr int kFDMaxPoints = 32768;  // points of one grid
+constexpr int kFDLine = 32;          // points along one axis
+constexpr int kFDCtas = 8;           // CTAs (one cluster) per grid
+constexpr int kFDThreads = 256;
+// shared memory bound per CTA: table (3 axes, two padded e x e bases and e
+// eigenvalues each) and two slab buffers of ceil(e_z / kFDCtas) planes
+constexpr int kFDMaxSmem = (int)sizeof(float) * (3 * (2 * kFDLine * kFDLine + kFDLine) + 4 +
+                                                 2 * (((kFDLine + kFDCtas - 1) / kFDCtas) * kFDLine * kFDLine + 4));
 struct FDGrid {
   int e[3];        // extents
   long long off;   // offset of the grid in the level's solution / rhs arrays
