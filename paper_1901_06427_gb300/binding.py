@@ -415,7 +415,7 @@ class Batch:
             pass
 
 
-def grid_for(workload, precision=None, restart=30, max_iter=4000, rtol=None):
+def grid_for(workload, precision=None, restart=48, max_iter=4000, rtol=None):
     """A Grid with the workload's bodies set."""
     prec = precision if precision is not None else (FP32_REFINED if workload.precision == "f32-refined" else FP64)
     g = Grid(workload.n, h=workload.h, eta=workload.eta, periodic=workload.periodic, wall_vel=workload.wall_vel,
