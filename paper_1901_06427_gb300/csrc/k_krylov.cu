@@ -3,6 +3,8 @@
 // products with FP64 accumulation (warp shuffles -> block -> fixed-order
 // final sum, deterministic), fused multi-axpy with the norm of the result,
 // Givens rotations and the small triangular solve on the device.
+#include <cstdint>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -29,44 +31,90 @@ RBFIB_DEVFN double block_sum(double v) {
   return v;
 }
 
-// part[col * gridDim.x + blockIdx.x] = sum over this block's chunk of W w V_col
+// Whether a multi-column sweep can use 16-byte loads: both arrays 16-byte
+// aligned and every column start too.
 template <typename T>
-__global__ void k_dot_part(const T* __restrict__ w, const T* __restrict__ V, i64 ldv, i64 n, i64 nfl, double wf,
-                           double* __restrict__ part) {
+inline int vec_ok(const T* a, const T* b, i64 ld, int ncols) {
+  auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  return al(a) && al(b) && (ncols <= 1 || ((ld * (i64)sizeof(T)) & 15) == 0) ? 1 : 0;
+}
+
+// part[col * gridDim.x + blockIdx.x] = this block's share of the unweighted
+// sum w . V_col over [0, n) (16-byte loads when vec); the finish kernel
+// applies the weights.  FP32: FP32 products and per-thread FP32 sums, FP64
+// across threads and blocks (enough for the FP32 inner solve of the
+// refinement).
+template <typename T>
+__global__ void k_dot_part(const T* __restrict__ w, const T* __restrict__ V, i64 ldv, i64 n,
+                           double* __restrict__ part, int vec) {
   const int col = blockIdx.y;
   const T* v = V + (i64)col * ldv;
-  double af = 0.0, ab = 0.0;   // fluid and body parts; the weight is applied once
-  if constexpr (sizeof(T) == 4) {
-    // FP32 products and per-thread FP32 sums (about 16 terms), FP64 across
-    // threads and blocks: enough for the FP32 inner solve of the refinement
-    float sf = 0.f, sb = 0.f;
-    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-      if (i < nfl) sf = fmaf((float)w[i], (float)v[i], sf);
-      else sb = fmaf((float)w[i], (float)v[i], sb);
+  const i64 stride = (i64)gridDim.x * blockDim.x, t0 = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc;
+  if constexpr (sizeof(T) == 8) {
+    double a0 = 0.0, a1 = 0.0;
+    if (vec) {
+      const double2* w2 = reinterpret_cast<const double2*>(w);
+      const double2* v2 = reinterpret_cast<const double2*>(v);
+      for (i64 i = t0; i < (n >> 1); i += stride) {
+        const double2 x = w2[i], y = v2[i];
+        a0 = fma(x.x, y.x, a0);
+        a1 = fma(x.y, y.y, a1);
+      }
+      if ((n & 1) && t0 == 0) a0 = fma(w[n - 1], v[n - 1], a0);
+    } else {
+      for (i64 i = t0; i < n; i += stride) a0 = fma(w[i], v[i], a0);
     }
-    af = sf; ab = sb;
+    acc = a0 + a1;
   } else {
-    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-      if (i < nfl) af = fma((double)w[i], (double)v[i], af);
-      else ab = fma((double)w[i], (double)v[i], ab);
+    float s0 = 0.f, s1 = 0.f;
+    if (vec) {
+      const float4* w4 = reinterpret_cast<const float4*>(w);
+      const float4* v4 = reinterpret_cast<const float4*>(v);
+      for (i64 i = t0; i < (n >> 2); i += stride) {
+        const float4 x = w4[i], y = v4[i];
+        s0 = fmaf(x.x, y.x, fmaf(x.y, y.y, s0));
+        s1 = fmaf(x.z, y.z, fmaf(x.w, y.w, s1));
+      }
+      if (t0 < (n & 3)) s0 = fmaf((float)w[(n & ~(i64)3) + t0], (float)v[(n & ~(i64)3) + t0], s0);
+    } else {
+      for (i64 i = t0; i < n; i += stride) s0 = fmaf((float)w[i], (float)v[i], s0);
     }
+    acc = (double)s0 + (double)s1;
   }
-  double acc = block_sum(wf * af + ab);
+  acc = block_sum(acc);
   if (threadIdx.x == 0) part[(i64)col * gridDim.x + blockIdx.x] = acc;
 }
 
-__global__ void k_dot_finish(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+// out[col] = wf * (sum of the parts) + (1 - wf) * sum_{nfl <= i < n} w_i V_col,i:
+// the weighted inner product with weight wf on the fluid entries [0, nfl)
+// and 1 on the body entries (re-read here, they are few).
+template <typename T>
+__global__ void k_dot_finish(const double* __restrict__ part, int nparts, double* __restrict__ out,
+                             const T* __restrict__ w, const T* __restrict__ V, i64 ldv, i64 nfl, i64 n, double wf) {
   const int col = blockIdx.x;
-  double acc = 0.0;
+  double acc = 0.0, body = 0.0;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[(i64)col * nparts + i];
-  acc = block_sum(acc);
+  if (wf != 1.0) {
+    const T* v = V + (i64)col * ldv;
+    for (i64 i = nfl + threadIdx.x; i < n; i += blockDim.x) body = fma((double)w[i], (double)v[i], body);
+  }
+  acc = block_sum(wf * acc + (1.0 - wf) * body);
   if (threadIdx.x == 0) out[col] = acc;
 }
 
-// About 16 elements per thread: enough work per block to amortise its
-// reduction, while the columns still give several blocks per SM.
+// plain sum of nparts partials
+__global__ void k_sum_finish(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) out[0] = acc;
+}
+
+// About 32 elements per thread: few blocks, each with long independent
+// FP64 FMA chains (FP64 throughput is the bound).
 inline int dot_blocks(i64 n, int nparts) {
-  const i64 b = (n + 256 * 16 - 1) / (256 * 16);
+  const i64 b = (n + 256 * 32 - 1) / (256 * 32);
   return (int)std::max<i64>(1, std::min<i64>(b, nparts));
 }
 
@@ -75,46 +123,88 @@ void multi_dot(const T* w, const T* V, i64 ldv, int ncols, i64 n, i64 nfl, doubl
                double* out, cudaStream_t s) {
   const int nb = dot_blocks(n, nparts);
   dim3 grid(nb, ncols);
-  k_dot_part<T><<<grid, 256, 0, s>>>(w, V, ldv, n, nfl, wf, part);
+  k_dot_part<T><<<grid, 256, 0, s>>>(w, V, ldv, n, part, vec_ok(w, V, ldv, ncols));
   note_launch();
-  k_dot_finish<<<ncols, 256, 0, s>>>(part, nb, out);
+  k_dot_finish<T><<<ncols, 256, 0, s>>>(part, nb, out, w, V, ldv, nfl, n, wf);
   note_launch();
 }
 
-// w += sign * sum_c coef[c] V_c ; part[blockIdx.x] = partial ||w||_W^2
+// w += sign * sum_c coef[c] V_c (16-byte loads when vec, two rows per thread
+// step in FP64, four in FP32); part[blockIdx.x] = partial unweighted ||w||^2
 template <typename T>
 __global__ void k_multi_axpy(T* __restrict__ w, const T* __restrict__ V, i64 ldv, int ncols,
-                             const double* __restrict__ coef, double sign, i64 n, i64 nfl, double wf,
-                             double* __restrict__ part) {
+                             const double* __restrict__ coef, double sign, i64 n, double* __restrict__ part,
+                             int vec) {
   __shared__ double c[128];
   for (int i = threadIdx.x; i < ncols; i += blockDim.x) c[i] = sign * coef[i];
   __syncthreads();
-  double af = 0.0, ab = 0.0;
-  if constexpr (sizeof(T) == 4) {
+  const i64 stride = (i64)gridDim.x * blockDim.x, t0 = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  double nrm = 0.0;
+  if constexpr (sizeof(T) == 8) {
+    if (vec) {
+      double2* w2 = reinterpret_cast<double2*>(w);
+      for (i64 i = t0; i < (n >> 1); i += stride) {
+        double2 x = w2[i];
+        for (int k = 0; k < ncols; ++k) {
+          const double2 y = reinterpret_cast<const double2*>(V + (i64)k * ldv)[i];
+          x.x = fma(c[k], y.x, x.x);
+          x.y = fma(c[k], y.y, x.y);
+        }
+        w2[i] = x;
+        nrm = fma(x.x, x.x, fma(x.y, x.y, nrm));
+      }
+      if ((n & 1) && t0 == 0) {
+        double x = w[n - 1];
+        for (int k = 0; k < ncols; ++k) x = fma(c[k], V[(i64)k * ldv + n - 1], x);
+        w[n - 1] = x;
+        nrm = fma(x, x, nrm);
+      }
+    } else {
+      for (i64 i = t0; i < n; i += stride) {
+        double x = w[i];
+        for (int k = 0; k < ncols; ++k) x = fma(c[k], V[(i64)k * ldv + i], x);
+        w[i] = x;
+        nrm = fma(x, x, nrm);
+      }
+    }
+  } else {
     __shared__ float c32[128];
     for (int i = threadIdx.x; i < ncols; i += blockDim.x) c32[i] = (float)c[i];
     __syncthreads();
-    float sf = 0.f, sb = 0.f;
-    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-      float x = (float)w[i];
-      for (int k = 0; k < ncols; ++k) x = fmaf(c32[k], (float)V[(i64)k * ldv + i], x);
-      w[i] = (T)x;
-      if (i < nfl) sf = fmaf(x, x, sf);
-      else sb = fmaf(x, x, sb);
+    float s0 = 0.f;
+    if (vec) {
+      float4* w4 = reinterpret_cast<float4*>(w);
+      for (i64 i = t0; i < (n >> 2); i += stride) {
+        float4 x = w4[i];
+        for (int k = 0; k < ncols; ++k) {
+          const float4 y = reinterpret_cast<const float4*>(V + (i64)k * ldv)[i];
+          x.x = fmaf(c32[k], y.x, x.x);
+          x.y = fmaf(c32[k], y.y, x.y);
+          x.z = fmaf(c32[k], y.z, x.z);
+          x.w = fmaf(c32[k], y.w, x.w);
+        }
+        w4[i] = x;
+        s0 = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, s0))));
+      }
+      if (t0 < (n & 3)) {
+        const i64 i = (n & ~(i64)3) + t0;
+        float x = (float)w[i];
+        for (int k = 0; k < ncols; ++k) x = fmaf(c32[k], (float)V[(i64)k * ldv + i], x);
+        w[i] = (T)x;
+        s0 = fmaf(x, x, s0);
+      }
+    } else {
+      for (i64 i = t0; i < n; i += stride) {
+        float x = (float)w[i];
+        for (int k = 0; k < ncols; ++k) x = fmaf(c32[k], (float)V[(i64)k * ldv + i], x);
+        w[i] = (T)x;
+        s0 = fmaf(x, x, s0);
+      }
     }
-    af = sf; ab = sb;
-  } else {
-    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-      double x = (double)w[i];
-      for (int k = 0; k < ncols; ++k) x = fma(c[k], (double)V[(i64)k * ldv + i], x);
-      const T xt = (T)x;
-      w[i] = xt;
-      if (i < nfl) af = fma((double)xt, (double)xt, af);
-      else ab = fma((double)xt, (double)xt, ab);
-    }
+    nrm = s0;
   }
   if (part) {
-    double acc = block_sum(wf * af + ab);
+    const double acc = block_sum(nrm);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
   }
 }
@@ -122,9 +212,14 @@ __global__ void k_multi_axpy(T* __restrict__ w, const T* __restrict__ V, i64 ldv
 template <typename T>
 void multi_axpy(T* w, const T* V, i64 ldv, int ncols, const double* coef, double sign, i64 n, i64 nfl, double wf,
                 double* part, int nparts, double* nrm2, cudaStream_t s) {
-  k_multi_axpy<T><<<nparts, 256, 0, s>>>(w, V, ldv, ncols, coef, sign, n, nfl, wf, nrm2 ? part : nullptr);
+  k_multi_axpy<T><<<nparts, 256, 0, s>>>(w, V, ldv, ncols, coef, sign, n, nrm2 ? part : nullptr,
+                                         vec_ok(w, V, ldv, ncols));
   note_launch();
-  if (nrm2) { k_dot_finish<<<1, 256, 0, s>>>(part, nparts, nrm2); note_launch(); }
+  if (nrm2) {
+    // weighted norm: the same finish as an inner product of w with itself
+    k_dot_finish<T><<<1, 256, 0, s>>>(part, nparts, nrm2, w, w, 0, nfl, n, wf);
+    note_launch();
+  }
 }
 
 // mode 0: out = in * d[0]; mode 1: out = in / d[0]; mode 2: out = in / sqrt(d[0])
@@ -132,8 +227,15 @@ void multi_axpy(T* w, const T* V, i64 ldv, int ncols, const double* coef, double
 template <typename T>
 __global__ void k_scale(T* __restrict__ out, const T* __restrict__ in, const double* __restrict__ denom, int invert,
                         i64 n) {
-  const double dv = invert == 2 ? sqrt(fmax(denom[0], 0.0)) : denom[0];
-  const double f = invert ? (dv != 0.0 ? 1.0 / dv : 0.0) : dv;
+  // one thread per block forms the factor (FP64 square root and division
+  // are long instruction sequences)
+  __shared__ double fs;
+  if (threadIdx.x == 0) {
+    const double dv = invert == 2 ? sqrt(fmax(denom[0], 0.0)) : denom[0];
+    fs = invert ? (dv != 0.0 ? 1.0 / dv : 0.0) : dv;
+  }
+  __syncthreads();
+  const double f = fs;
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
     out[i] = (T)((double)in[i] * f);
 }
@@ -243,7 +345,7 @@ void project_mean(double* x, i64 n, double* part, int nparts, cudaStream_t s) {
   if (n == 0) return;
   k_sum_part<<<nparts, 256, 0, s>>>(x, n, part);
   note_launch();
-  k_dot_finish<<<1, 256, 0, s>>>(part, nparts, part + nparts);
+  k_sum_finish<<<1, 256, 0, s>>>(part, nparts, part + nparts);
   note_launch();
   k_sub<<<nparts, 256, 0, s>>>(x, n, part + nparts);
   note_launch();
@@ -296,8 +398,13 @@ namespace rbfib {
 template <typename T>
 __global__ void k_fg_start(T* __restrict__ V0, const T* __restrict__ w, i64 n, double* __restrict__ gvec, int m,
                            int* __restrict__ ist, const double* __restrict__ dpar) {
-  const double beta = sqrt(fmax(dpar[2], 0.0));
-  const double f = beta > 0.0 ? 1.0 / beta : 0.0;
+  __shared__ double bs, fs;   // one thread per block forms beta and 1 / beta
+  if (threadIdx.x == 0) {
+    bs = sqrt(fmax(dpar[2], 0.0));
+    fs = bs > 0.0 ? 1.0 / bs : 0.0;
+  }
+  __syncthreads();
+  const double beta = bs, f = fs;
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
     V0[i] = (T)((double)w[i] * f);
   if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -93,7 +93,8 @@ struct KrylovStore {
   i64 n = 0;
   DBuf<T> V, Z, w;
   void build(int m_, i64 n_) {
-    m = m_; n = n_;
+    // columns start on 32-byte boundaries (16-byte vector loads in FP64 and FP32)
+    m = m_; n = (n_ + 3) & ~(i64)3;
     V.alloc((size_t)(m + 1) * n);
     Z.alloc((size_t)m * n);
     w.alloc(n);
