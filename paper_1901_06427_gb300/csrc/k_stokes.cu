@@ -527,6 +527,83 @@ __global__ void k_vel_rbgs(Dims d, ColorMap m, T eta, int color, T* __restrict__
   u[id] = (rhs[id] / eta + nb) / dg;
 }
 
+// Red-black half sweep for one spacing h on every axis: blockIdx.z -> (face
+// component a, plane k), y -> row j, x -> half-row index, so the point is
+// ((2 h' + parity), j, k) with no divisions.  The update is
+// u = (rhs h^2 / eta + sum of neighbours) / count, where count = 6 plus one
+// per tangential wall ghost; missing wall-normal neighbours are zero.
+template <typename T>
+RBFIB_DEVFN T smooth_div(T a, int c);
+template <>
+RBFIB_DEVFN float smooth_div<float>(float a, int c) { return __fdividef(a, (float)c); }
+template <>
+RBFIB_DEVFN double smooth_div<double>(double a, int c) { return a / (double)c; }
+
+template <typename T>
+__global__ void k_vel_rbgs_u(Dims d, T sh, int color, T* __restrict__ u, const T* __restrict__ rhs) {
+  const int nz = d.n[2];
+  const int a = (int)blockIdx.z / nz, k = (int)blockIdx.z - a * nz;
+  const int e0 = d.fe[a][0], e1 = d.fe[a][1], e2 = d.fe[a][2];
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + color) & 1);
+  if (k >= e2 || j >= e1 || i >= e0) return;
+  T* ua = u + (unsigned)d.fo[a];
+  const unsigned sy = (unsigned)e0, sz = (unsigned)e0 * (unsigned)e1;
+  const unsigned id = (unsigned)i + sy * (unsigned)j + sz * (unsigned)k;
+  T nb = T(0);
+  int cnt = 6;
+  // x
+  if (d.per[0]) nb += ua[i > 0 ? id - 1 : id + (e0 - 1)] + ua[i < e0 - 1 ? id + 1 : id - (e0 - 1)];
+  else {
+    if (i > 0) nb += ua[id - 1]; else if (a != 0) ++cnt;
+    if (i < e0 - 1) nb += ua[id + 1]; else if (a != 0) ++cnt;
+  }
+  // y
+  if (d.per[1]) nb += ua[j > 0 ? id - sy : id + sy * (e1 - 1)] + ua[j < e1 - 1 ? id + sy : id - sy * (e1 - 1)];
+  else {
+    if (j > 0) nb += ua[id - sy]; else if (a != 1) ++cnt;
+    if (j < e1 - 1) nb += ua[id + sy]; else if (a != 1) ++cnt;
+  }
+  // z
+  if (d.per[2]) nb += ua[k > 0 ? id - sz : id + sz * (e2 - 1)] + ua[k < e2 - 1 ? id + sz : id - sz * (e2 - 1)];
+  else {
+    if (k > 0) nb += ua[id - sz]; else if (a != 2) ++cnt;
+    if (k < e2 - 1) nb += ua[id + sz]; else if (a != 2) ++cnt;
+  }
+  ua[id] = smooth_div<T>(rhs[(unsigned)d.fo[a] + id] * sh + nb, cnt);
+}
+
+// Same for the Neumann pressure operator -D G: count = number of existing
+// neighbours (6 on periodic axes).
+template <typename T>
+__global__ void k_p_rbgs_u(Dims d, T sh, int color, T* __restrict__ u, const T* __restrict__ rhs) {
+  const int n0 = d.n[0], n1 = d.n[1], n2 = d.n[2];
+  const int k = blockIdx.z;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x) + ((j + k + color) & 1);
+  if (j >= n1 || i >= n0) return;
+  const unsigned sy = (unsigned)n0, sz = (unsigned)n0 * (unsigned)n1;
+  const unsigned id = (unsigned)i + sy * (unsigned)j + sz * (unsigned)k;
+  T nb = T(0);
+  int cnt = 0;
+  if (d.per[0]) { nb += u[i > 0 ? id - 1 : id + (n0 - 1)] + u[i < n0 - 1 ? id + 1 : id - (n0 - 1)]; cnt += 2; }
+  else {
+    if (i > 0) { nb += u[id - 1]; ++cnt; }
+    if (i < n0 - 1) { nb += u[id + 1]; ++cnt; }
+  }
+  if (d.per[1]) { nb += u[j > 0 ? id - sy : id + sy * (n1 - 1)] + u[j < n1 - 1 ? id + sy : id - sy * (n1 - 1)]; cnt += 2; }
+  else {
+    if (j > 0) { nb += u[id - sy]; ++cnt; }
+    if (j < n1 - 1) { nb += u[id + sy]; ++cnt; }
+  }
+  if (d.per[2]) { nb += u[k > 0 ? id - sz : id + sz * (n2 - 1)] + u[k < n2 - 1 ? id + sz : id - sz * (n2 - 1)]; cnt += 2; }
+  else {
+    if (k > 0) { nb += u[id - sz]; ++cnt; }
+    if (k < n2 - 1) { nb += u[id + sz]; ++cnt; }
+  }
+  u[id] = cnt > 0 ? smooth_div<T>(rhs[id] * sh + nb, cnt) : u[id];
+}
+
 // First half sweep from a zero initial guess: colour 0 gets rhs / (eta diag),
 // colour 1 is zeroed.
 template <typename T>
@@ -938,8 +1015,15 @@ void stokes_apply(const Dims& d, T eta, const T* v, const T* p, T* yv, T* yp, cu
 }
 template <typename T>
 void vel_rbgs(const Dims& d, T eta, int color, T* u, const T* rhs, cudaStream_t s, int bs) {
-  const ColorMap m = make_color_map_faces(d);
-  k_vel_rbgs<T><<<nblk((i64)m.cnt[0] + m.cnt[1] + m.cnt[2], bs), bs, 0, s>>>(d, m, eta, color, u, rhs);
+  if (d.h[0] == d.h[1] && d.h[1] == d.h[2] && d.fo[3] < ((i64)1 << 31)) {
+    // 32 half-row points x bs / 32 rows per block
+    const int by = std::max(1, bs / 32);
+    dim3 grid((d.n[0] / 2 + 1 + 31) / 32, (d.n[1] + by - 1) / by, 3 * d.n[2]);
+    k_vel_rbgs_u<T><<<grid, dim3(32, by), 0, s>>>(d, (T)(d.h[0] * d.h[0] / (double)eta), color, u, rhs);
+  } else {
+    const ColorMap m = make_color_map_faces(d);
+    k_vel_rbgs<T><<<nblk((i64)m.cnt[0] + m.cnt[1] + m.cnt[2], bs), bs, 0, s>>>(d, m, eta, color, u, rhs);
+  }
   note_launch();
 }
 template <typename T>
@@ -975,8 +1059,14 @@ void vel_coarse(const Dims& d, T eta, T* u, const T* rhs, int sweeps, cudaStream
 }
 template <typename T>
 void p_rbgs(const Dims& d, int color, T* u, const T* rhs, cudaStream_t s, int bs) {
-  const ColorMap m = make_color_map_cells(d);
-  k_p_rbgs<T><<<nblk(m.cnt[0], bs), bs, 0, s>>>(d, m, color, u, rhs);
+  if (d.h[0] == d.h[1] && d.h[1] == d.h[2] && d.nc < ((i64)1 << 31)) {
+    const int by = std::max(1, bs / 32);
+    dim3 grid((d.n[0] / 2 + 1 + 31) / 32, (d.n[1] + by - 1) / by, d.n[2]);
+    k_p_rbgs_u<T><<<grid, dim3(32, by), 0, s>>>(d, (T)(d.h[0] * d.h[0]), color, u, rhs);
+  } else {
+    const ColorMap m = make_color_map_cells(d);
+    k_p_rbgs<T><<<nblk(m.cnt[0], bs), bs, 0, s>>>(d, m, color, u, rhs);
+  }
   note_launch();
 }
 template <typename T>
