@@ -38,6 +38,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--roofline-kernel", default="auto", choices=["auto"] + list(TIMER_NAMES))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sem-only", action="store_true",
+                    help="only the SEM-step line (no refined, large-matvec or adjoint legs); for profiling")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="run the solves launch by launch instead of as CUDA graphs (profilers do not see "
+                         "kernels inside graphs with conditional nodes)")
     ap.add_argument("--cpu-sample-rhs", type=int, default=16)
     ap.add_argument("--ensemble", type=int, default=0,
                     help="also time a batched ensemble of this many systems (0: skip)")
@@ -193,6 +198,56 @@ def run_matvec_large(B, torch, hbm, n=256, reps=20):
     return out
 
 
+# ------------------------------------------------------------------ roofline
+# Kernels of each timed class, the arithmetic they run in on the FP64
+# two-sphere solve, and the SMs they occupy.
+CLASS_INFO = {
+    "matvec": ("k_stokes_cols_f64 + k_saddle_bodies (saddle matvec)", "fp64", 152),
+    "smooth": ("k_vel_rbgs_u (red-black half sweep, finest velocity level)", "fp32", 152),
+    "dot": ("k_dot_part + k_dot_finish (CGS2 inner products)", "fp64", 152),
+    "axpy": ("k_multi_axpy (+ k_dot_finish for the norm)", "fp64", 152),
+    "coarse": ("k_fd_solve (exact coarse-level solve, one 8-CTA cluster per grid)", "fp32", 16),
+}
+# DRAM bytes per algorithmic byte from the ncu captures summarised under
+# profiles/ (kernel as it stands); traffic is reported for these classes only.
+TRAFFIC_RATIO = {}
+
+
+def roofline_for(top, kms, klaunch, kbytes, kflops):
+    """Binding roof of the dominant class: achieved algorithmic bytes/s
+    against the measured HBM copy rate, and achieved operations/s against the
+    arithmetic peak of the SMs the kernel occupies, derived from unit counts
+    and the maximum SM clock (FP64: 2 FMA per SM per clock; FP32: 128 lanes);
+    the larger fraction is the bound."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    name, arith, sms = CLASS_INFO[top]
+    lanes = 2 if arith == "fp64" else 128
+    alu_peak = sms * lanes * 2 * sm_mhz * 1e6 / 1e9   # GFLOP/s
+    avg_s = (kms / max(klaunch, 1)) * 1e-3
+    bw = (kbytes / klaunch) / avg_s / 1e9 if klaunch else 0.0
+    fl = (kflops / klaunch) / avg_s / 1e9 if klaunch else 0.0
+    f_bw, f_fl = bw / hbm, fl / alu_peak
+    mem = {"achieved": bw, "peak": hbm, "unit": "GB/s", "frac": f_bw,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"}
+    alu = {"achieved": fl, "peak": alu_peak, "unit": "GFLOP/s", "frac": f_fl,
+           "peak_source": f"derived: {sms} SMs x {lanes} {arith.upper()} FMA lanes x 2 x {sm_mhz:.0f} MHz"}
+    bound = "hbm" if f_bw >= f_fl else "alu"
+    r = dict(mem if bound == "hbm" else alu)
+    r.update({"kernel": name, "bound": bound, "arith": arith,
+              "other_roof": alu if bound == "hbm" else mem,
+              "traffic": (TRAFFIC_RATIO[top] * kbytes / klaunch) if (top in TRAFFIC_RATIO and klaunch) else None,
+              "launches": klaunch, "avg_launch_us": 1e6 * avg_s,
+              "alg_bytes_per_launch": kbytes / klaunch if klaunch else None,
+              "alg_flops_per_launch": kflops / klaunch if klaunch else None})
+    return r
+
+
 # ----------------------------------------------------------- adjoint leg
 def run_adjoint(B, torch, reps=2):
     """Adjoint workload: 64 42-blob spheres with active slip in a 128x128x64
@@ -276,6 +331,8 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.no_graphs:
+        os.environ["RBFIB_NO_GRAPHS"] = "1"   # read when a grid is created
     w = workloads.two_sphere_cavity(steps=args.steps)
     g = B.grid_for(w, rtol=1e-8)
     p = B.sem_params(w.potentials, dt=w.dt, kT=w.kT)
@@ -343,7 +400,7 @@ def run_ours(args):
         shares[cname] = g.kernel_timer_read()
         g.kernel_timer(0)
     top = max(shares, key=lambda c: shares[c][0])
-    kms, klaunch, kbytes = shares[top]
+    kms, klaunch, kbytes, kflops = shares[top]
     state["iters"] = iters_timed
     if world > 1:
         import torch.distributed as dist
@@ -379,33 +436,7 @@ def run_ours(args):
     e2e = {"value": world * args.steps / (e2e_ms / 1000.0), "unit": "SEM steps/s",
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
     # ----------------------------------------------------------- roofline
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    avg_s = (kms / max(klaunch, 1)) * 1e-3
-    if top == "coarse":
-        # one CTA per grid (3 velocity grids, then 1 pressure grid: 2 SMs per
-        # launch on average): FP32 operations against those SMs' FP32 rate
-        # (128 lanes x 2 operations per FMA x max SM clock each)
-        peak = 2 * 128 * 2 * sm_mhz * 1e6 / 1e9
-        achieved = (kbytes / max(klaunch, 1)) / avg_s / 1e9 if klaunch else None
-        roofline = {"kernel": "k_fd_solve (exact coarse-level solve, one CTA per grid)", "bound": "alu",
-                    "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
-                    "frac": (achieved / peak) if achieved else None, "traffic": None,
-                    "peak_source": "derived: 128 FP32 lanes x 2 x max SM clock x 2 SMs (mean CTAs per launch)",
-                    "launches": klaunch, "avg_launch_us": 1e6 * avg_s,
-                    "alg_flops_per_launch": (kbytes / klaunch) if klaunch else None}
-    else:
-        achieved = (kbytes / max(klaunch, 1)) / avg_s / 1e9 if klaunch else None
-        roofline = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": (achieved / hbm) if achieved else None, "traffic": None,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
-                    "launches": klaunch, "avg_launch_us": 1e6 * avg_s,
-                    "alg_bytes_per_launch": (kbytes / klaunch) if klaunch else None}
+    roofline = roofline_for(top, kms, klaunch, kbytes, kflops)
     roofline["time_share_ms_per_step"] = {c: v[0] / nrep for c, v in shares.items()}
     if rank != 0:
         return
@@ -416,6 +447,9 @@ def run_ours(args):
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
             "krylov_iterations_per_step": [list(map(int, np.mean(np.array(state["iters"]), axis=0)))] if state["iters"] else None,
             "rejected_steps": state["rejects"], "wall_s": t_wall}
+    if args.sem_only:
+        print(json.dumps(line), flush=True)
+        return
     # same workload with FP32 kernels inside FP64 refinement (same 1e-8)
     gr = B.grid_for(w, precision=B.FP32_REFINED, rtol=1e-8)
     qr, quatr = torch.tensor(w.q.ravel(), device="cuda"), torch.tensor(w.quat.ravel(), device="cuda")
@@ -430,6 +464,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     line["refined_vs_fp64"] = {"fp32_refined_steps_per_s": args.steps / (er0.elapsed_time(er1) / 1000.0),
                                "fp64_steps_per_s": value / world, "rtol": 1e-8}
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
+    except Exception:
+        hbm = 6800.0
     line["matvec_hbm"] = run_matvec_large(B, torch, hbm)
     line["adjoint"] = run_adjoint(B, torch)
     line["autotuned_blocks"] = dict(zip(["stokes_fp64", "stokes_fp32", "vel_sweep", "p_sweep"], g.tuned_blocks()))

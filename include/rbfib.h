@@ -265,20 +265,26 @@ int rbfib_stochastic_forcing_static(const rbfib_grid_desc* desc, double kT, doub
 uint64_t rbfib_launch_count(void);
 
 /* Kernel timer for roofline reports.  which: 0 off, 1 saddle matvec (Stokes
- * stencil + body rows), 2 finest-level velocity smoothing sweep, 3 Krylov
- * multi-column inner product, 4 Krylov multi-axpy, 5 exact solve of the
- * coarse multigrid level by fast diagonalisation, one CTA per grid (counted
- * in FP32 operations instead of bytes: per grid of n points and extents
- * e_x, e_y, e_z, 4 n (e_x + e_y + e_z) for the six 1D transforms plus n
- * divisions).  While a class is
- * selected, CUDA events are recorded on the grid's stream around each of its
- * launches and the algorithmic bytes of each launch are added up (matvec:
- * 2 n s + 24 N_bl + 56 N_b; smoothing sweep: 2 N_f s; inner product over k
- * columns: (k + 1) n s; multi-axpy over k columns: (k + 2) n s; s = element
- * size).  Selecting resets the counters.  _read synchronises the stream and
- * returns the summed event time (ms), the launch count and the bytes. */
+ * stencil + body rows), 2 finest-level velocity smoothing half sweep, 3
+ * Krylov multi-column inner product, 4 Krylov multi-axpy, 5 exact solve of
+ * the coarse multigrid level by fast diagonalisation (one 8-CTA cluster per
+ * grid).  While a class is selected, the stream first idles for about 25 us
+ * before each of its launches (so that the host has queued the launch and its
+ * closing event), CUDA events are recorded on the grid's stream around each
+ * launch, and the algorithmic bytes and floating-point operations of each
+ * launch are added up:
+ *   matvec: 2 n s + 24 N_bl + 56 N_b bytes; 10 N_f + 6 N_c + 400 N_bl operations
+ *   smoothing half sweep: 2 N_f s bytes; 4.5 N_f operations
+ *   inner product over k columns: (k + 1) n s bytes; 2 k n operations
+ *   multi-axpy over k columns: (k + 2) n s bytes; 2 (k + 1) n operations
+ *   coarse solve: per grid of P points and basis table of t floats,
+ *     4 (2 P + t) bytes; 4 P (e_x + e_y + e_z) + P operations
+ * (s = element size, n = vector length).  Selecting resets the counters.
+ * _read synchronises the stream and returns the summed event time (ms), the
+ * launch count, the bytes and the operations (each pointer may be NULL). */
 int rbfib_kernel_timer(rbfib_grid* g, int32_t which);
-int rbfib_kernel_timer_read(rbfib_grid* g, double* total_ms, int64_t* launches, double* alg_bytes);
+int rbfib_kernel_timer_read(rbfib_grid* g, double* total_ms, int64_t* launches, double* alg_bytes,
+                            double* alg_flops);
 
 #ifdef __cplusplus
 }

@@ -95,7 +95,7 @@ def lib():
                                       ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(StepInfo),
                                       ctypes.POINTER(ctypes.c_int32)], I32),
             "rbfib_kernel_timer": ([P, I32], I32),
-            "rbfib_kernel_timer_read": ([P, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D)], I32),
+            "rbfib_kernel_timer_read": ([P, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -320,9 +320,11 @@ class Grid:
         self._check(lib().rbfib_kernel_timer(self._h, int(which)))
 
     def kernel_timer_read(self):
-        ms, n, b = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
-        self._check(lib().rbfib_kernel_timer_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
-        return ms.value, n.value, b.value
+        """(total ms, launches, algorithmic bytes, algorithmic operations)"""
+        ms, n, b, f = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        self._check(lib().rbfib_kernel_timer_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b),
+                                                  ctypes.byref(f)))
+        return ms.value, n.value, b.value, f.value
 
     def tuned_blocks(self):
         out = (ctypes.c_int32 * 4)()

@@ -175,7 +175,7 @@ struct rbfib_grid {
   int timer_kind = 0;
   std::vector<cudaEvent_t> tev;
   size_t tev_used = 0;
-  double timer_bytes = 0.0;
+  double timer_bytes = 0.0, timer_flops = 0.0;
   int64_t timer_launches = 0;
 
   i64 n_total() const { return nfl + 3 * (i64)nbl + 6 * (i64)nb; }
@@ -187,7 +187,7 @@ namespace {
 struct TimerScope {
   rbfib_grid* g;
   bool on;
-  TimerScope(rbfib_grid* g_, int kind, double bytes) : g(g_), on(g_->timer_kind == kind) {
+  TimerScope(rbfib_grid* g_, int kind, double bytes, double flops) : g(g_), on(g_->timer_kind == kind) {
     if (!on) return;
     if (g->tev_used + 2 > g->tev.size()) {
       if (g->tev.size() >= 400000) { on = false; return; }
@@ -202,6 +202,7 @@ struct TimerScope {
     gpu_delay(50000, g->s);
     ck(cudaEventRecord(g->tev[g->tev_used], g->s));
     g->timer_bytes += bytes;
+    g->timer_flops += flops;
     g->timer_launches += 1;
   }
   ~TimerScope() {
@@ -286,6 +287,15 @@ int coarse_sweeps(const Dims& d) { return std::max(d.n[0], std::max(d.n[1], d.n[
 // Algorithmic FP32 operations of one coarse-level solve by fast
 // diagonalisation: per grid six 1D transforms (one FMA per point and
 // transform-axis entry) and one division per point.
+// Algorithmic bytes of one coarse-level solve: per grid the right-hand
+// side read and the solution written (FP32), and its basis table read.
+double fd_bytes(const FDParams& P) {
+  double b = 0.0;
+  for (int g = 0; g < P.ng; ++g)
+    b += 4.0 * (2.0 * P.g[g].e[0] * P.g[g].e[1] * P.g[g].e[2] + P.g[g].tabn);
+  return b;
+}
+
 double fd_flops(const FDParams& P) {
   double f = 0.0;
   for (int g = 0; g < P.ng; ++g) {
@@ -310,7 +320,7 @@ void vcycle_vel(rbfib_grid* g, T* u0, const T* rhs0) {
   rhs[0] = const_cast<T*>(rhs0);
   auto smooth = [&](int l, int color) {
     const Dims& d = g->levels[l].d;
-    TimerScope ts(g, l == 0 ? TK_SMOOTH : -1, 2.0 * (double)d.fo[3] * sizeof(T));
+    TimerScope ts(g, l == 0 ? TK_SMOOTH : -1, 2.0 * (double)d.fo[3] * sizeof(T), 4.5 * (double)d.fo[3]);
     vel_rbgs<T>(d, eta, color, u[l], rhs[l], g->s, l == 0 ? g->tune.vrbgs : 256);
   };
   const bool fd = std::is_same<T, float>::value && g->fd_vel >= 0;
@@ -324,7 +334,7 @@ void vcycle_vel(rbfib_grid* g, T* u0, const T* rhs0) {
   }
   if constexpr (std::is_same<T, float>::value) {
     if (fd) {
-      TimerScope ts(g, TK_COARSE, fd_flops(g->fdv));
+      TimerScope ts(g, TK_COARSE, fd_bytes(g->fdv), fd_flops(g->fdv));
       fd_solve(g->fdv, u[lt], rhs[lt], g->s);
     } else {
       vel_coarse<T>(g->levels[L - 1].d, eta, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
@@ -360,7 +370,7 @@ void vcycle_p(rbfib_grid* g, T* u0, T* rhs0) {
   }
   if constexpr (std::is_same<T, float>::value) {
     if (fd) {
-      TimerScope ts(g, TK_COARSE, fd_flops(g->fdp));
+      TimerScope ts(g, TK_COARSE, fd_bytes(g->fdp), fd_flops(g->fdp));
       fd_solve(g->fdp, u[lt], rhs[lt], g->s);
     } else {
       p_coarse<T>(g->levels[L - 1].d, u[L - 1], rhs[L - 1], coarse_sweeps(g->levels[L - 1].d), g->s);
@@ -430,7 +440,10 @@ template <typename T>
 void apply_A(rbfib_grid* g, const T* x, T* y, bool with_bodies) {
   const double nbytes = 2.0 * (double)(with_bodies ? g->n_total() : g->nfl) * sizeof(T) +
                         (with_bodies ? 24.0 * g->nbl + 56.0 * g->nb : 0.0);
-  TimerScope ts(g, TK_MATVEC, nbytes);
+  // operations: 10 per momentum row, 6 per divergence row, about 400 per blob
+  // (interpolation and spreading, 3 x 27 weighted terms each, and K, K^T)
+  const double nflops = 10.0 * g->nf + 6.0 * g->nc + (with_bodies ? 400.0 * g->nbl : 0.0);
+  TimerScope ts(g, TK_MATVEC, nbytes, nflops);
   stokes_apply<T>(g->d, (T)g->desc.eta, x, x + g->nf, y, y + g->nf, g->s,
                   sizeof(T) == 8 ? g->tune.stokes64 : g->tune.stokes32);
   if (with_bodies && g->nb > 0) {
@@ -487,10 +500,11 @@ int fgmres(rbfib_grid* g, const T* b, T* x, bool with_bodies, double rtol, int m
       precond_any(g, vj, zj, with_bodies);
       apply_A<T>(g, zj, w, with_bodies);
       const double bd = (double)(j + 2) * n * sizeof(T), ba = (double)(j + 3) * n * sizeof(T);
-      { TimerScope ts(g, TK_DOT, bd); multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol, g->s); }
-      { TimerScope ts(g, TK_AXPY, ba); multi_axpy<T>(w, V, ld, j + 1, sp.hcol, -1.0, n, nfl, wf, g->part, g->nparts, nullptr, g->s); }
-      { TimerScope ts(g, TK_DOT, bd); multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol2, g->s); }
-      { TimerScope ts(g, TK_AXPY, ba); multi_axpy<T>(w, V, ld, j + 1, sp.hcol2, -1.0, n, nfl, wf, g->part, g->nparts, sp.nrm2, g->s); }
+      const double fd = 2.0 * (j + 1) * n, fa = 2.0 * (j + 2) * n;
+      { TimerScope ts(g, TK_DOT, bd, fd); multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol, g->s); }
+      { TimerScope ts(g, TK_AXPY, ba, fa); multi_axpy<T>(w, V, ld, j + 1, sp.hcol, -1.0, n, nfl, wf, g->part, g->nparts, nullptr, g->s); }
+      { TimerScope ts(g, TK_DOT, bd, fd); multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol2, g->s); }
+      { TimerScope ts(g, TK_AXPY, ba, fa); multi_axpy<T>(w, V, ld, j + 1, sp.hcol2, -1.0, n, nfl, wf, g->part, g->nparts, sp.nrm2, g->s); }
       givens_step(sp.H, m + 1, sp.cs, sp.sn, sp.gv, j, sp.hcol, sp.hcol2, sp.nrm2, sp.res, g->s);
       scale_by<T>(V + (i64)(j + 1) * ld, w, sp.nrm2, 2, n, g->s);
       ++iters;
@@ -938,11 +952,12 @@ int rbfib_kernel_timer(rbfib_grid* g, int32_t which) {
   g->timer_kind = which;
   g->tev_used = 0;
   g->timer_bytes = 0.0;
+  g->timer_flops = 0.0;
   g->timer_launches = 0;
   return RBFIB_OK;
 }
 
-int rbfib_kernel_timer_read(rbfib_grid* g, double* total_ms, int64_t* launches, double* alg_bytes) {
+int rbfib_kernel_timer_read(rbfib_grid* g, double* total_ms, int64_t* launches, double* alg_bytes, double* alg_flops) {
   if (!g) return RBFIB_EINVAL;
   double tot = 0.0;
   try {
@@ -958,6 +973,7 @@ int rbfib_kernel_timer_read(rbfib_grid* g, double* total_ms, int64_t* launches, 
   if (total_ms) *total_ms = tot;
   if (launches) *launches = g->timer_launches;
   if (alg_bytes) *alg_bytes = g->timer_bytes;
+  if (alg_flops) *alg_flops = g->timer_flops;
   return RBFIB_OK;
 }
 
