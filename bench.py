@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sem-only", action="store_true",
                     help="only the SEM-step line (no refined, large-matvec or adjoint legs); for profiling")
+    ap.add_argument("--matvec-only", action="store_true",
+                    help="only the large-grid saddle matvec leg (prints its JSON); for profiling")
+    ap.add_argument("--matvec-n", type=int, default=256, help="cells per axis of the large-grid matvec leg")
     ap.add_argument("--no-graphs", action="store_true",
                     help="run the solves launch by launch instead of as CUDA graphs (profilers do not see "
                          "kernels inside graphs with conditional nodes)")
@@ -333,6 +336,14 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     if args.no_graphs:
         os.environ["RBFIB_NO_GRAPHS"] = "1"   # read when a grid is created
+    if args.matvec_only:
+        try:
+            hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
+        except Exception:
+            hbm = 6800.0
+        if rank == 0:
+            print(json.dumps({"matvec_hbm": run_matvec_large(B, torch, hbm, n=args.matvec_n)}), flush=True)
+        return
     w = workloads.two_sphere_cavity(steps=args.steps)
     g = B.grid_for(w, rtol=1e-8)
     p = B.sem_params(w.potentials, dt=w.dt, kT=w.kT)
@@ -468,7 +479,7 @@ def run_ours(args):
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
     except Exception:
         hbm = 6800.0
-    line["matvec_hbm"] = run_matvec_large(B, torch, hbm)
+    line["matvec_hbm"] = run_matvec_large(B, torch, hbm, n=args.matvec_n)
     line["adjoint"] = run_adjoint(B, torch)
     line["autotuned_blocks"] = dict(zip(["stokes_fp64", "stokes_fp32", "vel_sweep", "p_sweep"], g.tuned_blocks()))
     if args.ensemble:

@@ -419,46 +419,57 @@ RBFIB_DEVFN void stokes_pipe_body(const Dims& d, T eta, const T* __restrict__ v,
   const bool inc = i < nx && j < ny;
   const unsigned cbase = (unsigned)i + (unsigned)nx * (unsigned)j;
   int stm = 0;   // stage of plane k - 1
+  // this thread's column values of the four grids on planes k - 1, k, k + 1
+  // stay in registers; each plane brings one new value per grid
+  T zm[4], zc[4], zp[4];
   for (int k = k0; k < k1; ++k) {
     cp_async_wait<kPD - 1>();
     __syncthreads();
     issue(k + kPD + 1);
     const int st0 = stm + 1 < kPS ? stm + 1 : 0;
     const int stp = st0 + 1 < kPS ? st0 + 1 : 0;
-    const T* Sm = sm + stm * 4 * kPSlots;
     const T* S0 = sm + st0 * 4 * kPSlots;
     const T* Sp = sm + stp * 4 * kPSlots;
+    if (k == k0) {
+      const T* Sm = sm + stm * 4 * kPSlots;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        zm[g] = Sm[g * kPSlots + c0];
+        zc[g] = S0[g * kPSlots + c0];
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < 4; ++g) zp[g] = Sp[g * kPSlots + c0];
     stm = st0;
     // ghosts across the z walls for the tangential components
     const T zadj = PZ ? T(0) : s * (T)((k == 0) + (k == nz - 1));
-    const T pc = S0[3 * kPSlots + c0];
-    T uc[3], um[3], ux[3], uy[3], uzm[3], uzp[3];
+    const T pc = zc[3];
+    T um[3], ux[3], uy[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const T* U0 = S0 + a * kPSlots;
-      uc[a] = U0[c0];
       um[a] = U0[c0 - 1];
       ux[a] = U0[c0 + 1];
       uy[a] = U0[c0 - kPW];
       const T yq = U0[c0 + kPW];
-      uzm[a] = Sm[a * kPSlots + c0];
-      uzp[a] = Sp[a * kPSlots + c0];
-      const T nb = ((um[a] + ux[a]) + (uy[a] + yq)) + (uzm[a] + uzp[a]);
+      const T nb = ((um[a] + ux[a]) + (uy[a] + yq)) + (zm[a] + zp[a]);
       const T sd = a != 2 ? sdiag[a] + zadj : sdiag[a];
       T dp;
       if (a == 0) dp = pxw ? S0[3 * kPSlots + c0 + 1] - pc : pc - S0[3 * kPSlots + c0 - 1];
       else if (a == 1) dp = pyw ? S0[3 * kPSlots + c0 + kPW] - pc : pc - S0[3 * kPSlots + c0 - kPW];
-      else dp = PZ ? pc - Sm[3 * kPSlots + c0] : Sp[3 * kPSlots + c0] - pc;
-      const T y = sd * uc[a] - s * nb + dp * ih;
+      else dp = PZ ? pc - zm[3] : zp[3] - pc;
+      const T y = sd * zc[a] - s * nb + dp * ih;
       const bool store = in[a] && (a != 2 || PZ || k < nz - 1);
       if (store) yv[obase[a] + psz[a] * (unsigned)k] = y;
       if (a == 1) uy[1] = yq;   // divergence uses the +y neighbour of v_y when y is periodic
     }
     // divergence: faces beyond a wall were staged as zero
-    T div = pxw ? uc[0] - um[0] : ux[0] - uc[0];
-    div += pyw ? uc[1] - S0[kPSlots + c0 - kPW] : uy[1] - uc[1];
-    div += PZ ? uzp[2] - uc[2] : uc[2] - uzm[2];
+    T div = pxw ? zc[0] - um[0] : ux[0] - zc[0];
+    div += pyw ? zc[1] - S0[kPSlots + c0 - kPW] : uy[1] - zc[1];
+    div += PZ ? zp[2] - zc[2] : zc[2] - zm[2];
     if (inc) yp[cbase + psz[3] * (unsigned)k] = -div * ih;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) { zm[g] = zc[g]; zc[g] = zp[g]; }
   }
   // drain the (empty or unused) groups still in flight before the block exits
   asm volatile("cp.async.wait_all;\n" ::: "memory");
