@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--ensemble", type=int, default=0,
                     help="also time a batched ensemble of this many systems (0: skip)")
     ap.add_argument("--ensemble-steps", type=int, default=2)
-    ap.add_argument("--workers", type=int, default=16)
+    ap.add_argument("--workers", type=int, default=8)
     return ap.parse_args()
 
 

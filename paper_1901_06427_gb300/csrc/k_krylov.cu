@@ -39,14 +39,39 @@ inline int vec_ok(const T* a, const T* b, i64 ld, int ncols) {
   return al(a) && al(b) && (ncols <= 1 || ((ld * (i64)sizeof(T)) & 15) == 0) ? 1 : 0;
 }
 
-// part[col * gridDim.x + blockIdx.x] = this block's share of the unweighted
-// sum w . V_col over [0, n) (16-byte loads when vec); the finish kernel
-// applies the weights.  FP32: FP32 products and per-thread FP32 sums, FP64
-// across threads and blocks (enough for the FP32 inner solve of the
-// refinement).
+// Block-level completion of a grid-wide reduction: thread 0 stores this
+// block's value, then counts the block in; the last block (the one that
+// brings the counter to gridDim.x) gets true, with the other blocks' values
+// visible, and resets the counter for the next launch.  No block waits.
+RBFIB_DEVFN bool finish_last(double* slots, double v, unsigned* counter) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    slots[blockIdx.x] = v;
+    __threadfence();
+    const unsigned done = atomicAdd(counter, 1u);
+    last = done == gridDim.x - 1;
+    if (last) *counter = 0u;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
 template <typename T>
-__global__ void k_dot_part(const T* __restrict__ w, const T* __restrict__ V, i64 ldv, i64 n,
-                           double* __restrict__ part, int vec) {
+RBFIB_DEVFN T ldcg_t(const T* p) { return __ldcg(p); }
+
+// Per column: the blocks' shares of the unweighted sum w . V_col over [0, n)
+// (16-byte loads when vec) go to part[col * gridDim.x + block]; the last
+// block to finish a column (atomic counter, reset afterwards) adds them up
+// and forms out[col] = wf * sum + (1 - wf) * sum_{nfl <= i < n} w_i V_col,i:
+// the inner product with weight wf on the fluid entries and 1 on the body
+// entries (re-read here, they are few).  FP32: FP32 products and per-thread
+// FP32 sums, FP64 across threads and blocks (enough for the FP32 inner solve
+// of the refinement).
+template <typename T>
+__global__ void k_dot_part(const T* __restrict__ w, const T* __restrict__ V, i64 ldv, i64 n, i64 nfl, double wf,
+                           double* __restrict__ part, unsigned* __restrict__ cnt, double* __restrict__ out,
+                           int vec) {
   const int col = blockIdx.y;
   const T* v = V + (i64)col * ldv;
   const i64 stride = (i64)gridDim.x * blockDim.x, t0 = (i64)blockIdx.x * blockDim.x + threadIdx.x;
@@ -83,24 +108,13 @@ __global__ void k_dot_part(const T* __restrict__ w, const T* __restrict__ V, i64
     acc = (double)s0 + (double)s1;
   }
   acc = block_sum(acc);
-  if (threadIdx.x == 0) part[(i64)col * gridDim.x + blockIdx.x] = acc;
-}
-
-// out[col] = wf * (sum of the parts) + (1 - wf) * sum_{nfl <= i < n} w_i V_col,i:
-// the weighted inner product with weight wf on the fluid entries [0, nfl)
-// and 1 on the body entries (re-read here, they are few).
-template <typename T>
-__global__ void k_dot_finish(const double* __restrict__ part, int nparts, double* __restrict__ out,
-                             const T* __restrict__ w, const T* __restrict__ V, i64 ldv, i64 nfl, i64 n, double wf) {
-  const int col = blockIdx.x;
-  double acc = 0.0, body = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[(i64)col * nparts + i];
-  if (wf != 1.0) {
-    const T* v = V + (i64)col * ldv;
+  if (!finish_last(part + (i64)col * gridDim.x, acc, cnt + col)) return;
+  double s = 0.0, body = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(part + (i64)col * gridDim.x + i);
+  if (wf != 1.0)
     for (i64 i = nfl + threadIdx.x; i < n; i += blockDim.x) body = fma((double)w[i], (double)v[i], body);
-  }
-  acc = block_sum(wf * acc + (1.0 - wf) * body);
-  if (threadIdx.x == 0) out[col] = acc;
+  s = block_sum(wf * s + (1.0 - wf) * body);
+  if (threadIdx.x == 0) out[col] = s;
 }
 
 // plain sum of nparts partials
@@ -123,9 +137,8 @@ void multi_dot(const T* w, const T* V, i64 ldv, int ncols, i64 n, i64 nfl, doubl
                double* out, cudaStream_t s) {
   const int nb = dot_blocks(n, nparts);
   dim3 grid(nb, ncols);
-  k_dot_part<T><<<grid, 256, 0, s>>>(w, V, ldv, n, part, vec_ok(w, V, ldv, ncols));
-  note_launch();
-  k_dot_finish<T><<<ncols, 256, 0, s>>>(part, nb, out, w, V, ldv, nfl, n, wf);
+  k_dot_part<T><<<grid, 256, 0, s>>>(w, V, ldv, n, nfl, wf, part, part_counters(part, nparts), out,
+                                     vec_ok(w, V, ldv, ncols));
   note_launch();
 }
 
@@ -133,7 +146,8 @@ void multi_dot(const T* w, const T* V, i64 ldv, int ncols, i64 n, i64 nfl, doubl
 // step in FP64, four in FP32); part[blockIdx.x] = partial unweighted ||w||^2
 template <typename T>
 __global__ void k_multi_axpy(T* __restrict__ w, const T* __restrict__ V, i64 ldv, int ncols,
-                             const double* __restrict__ coef, double sign, i64 n, double* __restrict__ part,
+                             const double* __restrict__ coef, double sign, i64 n, i64 nfl, double wf,
+                             double* __restrict__ part, unsigned* __restrict__ cnt, double* __restrict__ nrm2,
                              int vec) {
   __shared__ double c[128];
   for (int i = threadIdx.x; i < ncols; i += blockDim.x) c[i] = sign * coef[i];
@@ -203,23 +217,28 @@ __global__ void k_multi_axpy(T* __restrict__ w, const T* __restrict__ V, i64 ldv
     }
     nrm = s0;
   }
-  if (part) {
-    const double acc = block_sum(nrm);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
-  }
+  if (!nrm2) return;
+  // weighted norm of the result: the last block adds up the blocks' sums and
+  // the body-block correction (1 - wf) sum_{i >= nfl} w_i^2
+  const double acc = block_sum(nrm);
+  if (!finish_last(part, acc, cnt)) return;
+  double s = 0.0, body = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(part + i);
+  if (wf != 1.0)
+    for (i64 i = nfl + threadIdx.x; i < n; i += blockDim.x) {
+      const double x = (double)ldcg_t(w + i);
+      body = fma(x, x, body);
+    }
+  s = block_sum(wf * s + (1.0 - wf) * body);
+  if (threadIdx.x == 0) nrm2[0] = s;
 }
 
 template <typename T>
 void multi_axpy(T* w, const T* V, i64 ldv, int ncols, const double* coef, double sign, i64 n, i64 nfl, double wf,
                 double* part, int nparts, double* nrm2, cudaStream_t s) {
-  k_multi_axpy<T><<<nparts, 256, 0, s>>>(w, V, ldv, ncols, coef, sign, n, nrm2 ? part : nullptr,
-                                         vec_ok(w, V, ldv, ncols));
+  k_multi_axpy<T><<<nparts, 256, 0, s>>>(w, V, ldv, ncols, coef, sign, n, nfl, wf, part,
+                                         part_counters(part, nparts) + kAxpyCounter, nrm2, vec_ok(w, V, ldv, ncols));
   note_launch();
-  if (nrm2) {
-    // weighted norm: the same finish as an inner product of w with itself
-    k_dot_finish<T><<<1, 256, 0, s>>>(part, nparts, nrm2, w, w, 0, nfl, n, wf);
-    note_launch();
-  }
 }
 
 // mode 0: out = in * d[0]; mode 1: out = in / d[0]; mode 2: out = in / sqrt(d[0])
@@ -262,30 +281,57 @@ void scale_by(T* out, const T* in, const double* denom, int invert, i64 n, cudaS
 
 // Hessenberg column j: H[0..j] = hcol (CGS2 sum), H[j+1] = sqrt(hnext2); apply
 // the previous rotations, form rotation j, update g; res_out = |g[j+1]|.
+// Givens update of Hessenberg column j (64 threads): the column (CGS sums
+// hcol + hcol2, then ||w||), the previous rotations and g are staged in
+// shared memory by all threads; one thread applies the j previous rotations
+// with the carried entry in a register (FP64 latency is long on this GPU, so
+// the chain must not go through memory), forms rotation j and updates g; all
+// threads write the column back.  Returns |g[j+1]|; r_out = the new
+// diagonal entry (every thread).
+constexpr int kGivensMax = 128;
+RBFIB_DEVFN double givens_core(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
+                               const double* hcol2, const double* hnext2, double& r_out) {
+  __shared__ double h[kGivensMax + 2], c[kGivensMax], s[kGivensMax];
+  __shared__ double res, rdiag;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) h[i] = hcol[i] + (hcol2 ? hcol2[i] : 0.0);
+  for (int i = threadIdx.x; i < j; i += blockDim.x) { c[i] = cs[i]; s[i] = sn[i]; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double carry = h[0];
+    for (int i = 0; i < j; ++i) {
+      const double hi1 = h[i + 1];
+      h[i] = c[i] * carry + s[i] * hi1;
+      carry = -s[i] * carry + c[i] * hi1;
+    }
+    const double a = carry, b = sqrt(fmax(hnext2[0], 0.0));
+    const double r = hypot(a, b);
+    const double cj = r > 0 ? a / r : 1.0, sj = r > 0 ? b / r : 0.0;
+    cs[j] = cj; sn[j] = sj;
+    h[j] = r;
+    h[j + 1] = 0.0;
+    rdiag = r;
+    const double gj = g[j];
+    g[j + 1] = -sj * gj;
+    g[j] = cj * gj;
+    res = fabs(sj * gj);
+  }
+  __syncthreads();
+  double* hc = H + (i64)j * ldh;
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) hc[i] = h[i];
+  r_out = rdiag;
+  return res;
+}
+
 __global__ void k_givens(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                          const double* hcol2, const double* hnext2, double* res_out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double* h = H + (i64)j * ldh;
-  for (int i = 0; i <= j; ++i) h[i] = hcol[i] + (hcol2 ? hcol2[i] : 0.0);
-  h[j + 1] = sqrt(fmax(hnext2[0], 0.0));
-  for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * h[i] + sn[i] * h[i + 1];
-    h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
-    h[i] = t;
-  }
-  const double a = h[j], b = h[j + 1];
-  const double r = hypot(a, b);
-  const double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
-  cs[j] = c; sn[j] = s;
-  h[j] = r; h[j + 1] = 0.0;
-  g[j + 1] = -s * g[j];
-  g[j] = c * g[j];
-  res_out[0] = fabs(g[j + 1]);
+  double r;
+  const double res = givens_core(H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, r);
+  if (threadIdx.x == 0) res_out[0] = res;
 }
 
 void givens_step(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                  const double* hcol2, const double* hnext2, double* res_out, cudaStream_t s) {
-  k_givens<<<1, 32, 0, s>>>(H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, res_out);
+  k_givens<<<1, 64, 0, s>>>(H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, res_out);
   note_launch();
 }
 
@@ -435,23 +481,9 @@ void set_condition(cudaGraphConditionalHandle h, const int* ist, cudaStream_t s)
 __global__ void k_givens_flag(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                               const double* hcol2, const double* hnext2, double* res_out, int* ist,
                               const double* dpar) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double* h = H + (i64)j * ldh;
-  for (int i = 0; i <= j; ++i) h[i] = hcol[i] + (hcol2 ? hcol2[i] : 0.0);
-  h[j + 1] = sqrt(fmax(hnext2[0], 0.0));
-  for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * h[i] + sn[i] * h[i + 1];
-    h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
-    h[i] = t;
-  }
-  const double a = h[j], b = h[j + 1];
-  const double r = hypot(a, b);
-  const double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
-  cs[j] = c; sn[j] = s;
-  h[j] = r; h[j + 1] = 0.0;
-  g[j + 1] = -s * g[j];
-  g[j] = c * g[j];
-  const double res = fabs(g[j + 1]);
+  double r;
+  const double res = givens_core(H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, r);
+  if (threadIdx.x != 0) return;
   res_out[0] = res;
   ist[0] = j + 1;
   ist[1] += 1;
@@ -462,7 +494,7 @@ __global__ void k_givens_flag(double* H, int ldh, double* cs, double* sn, double
 void givens_flag(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                  const double* hcol2, const double* hnext2, double* res_out, int* ist, const double* dpar,
                  cudaStream_t s) {
-  k_givens_flag<<<1, 32, 0, s>>>(H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, res_out, ist, dpar);
+  k_givens_flag<<<1, 64, 0, s>>>(H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, res_out, ist, dpar);
   note_launch();
 }
 

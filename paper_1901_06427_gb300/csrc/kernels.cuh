@@ -144,6 +144,17 @@ template <typename T> void dense_body_apply(int nbl, int nb, const int* boff, co
                                             const T* rU, T* zlam, T* zU, cudaStream_t);
 
 // k_krylov.cu
+// A grid's partial-sum buffer: nparts x kPartCols doubles, 8 spare doubles,
+// then kPartCounters counters (unsigned) of the last-block reductions:
+// [0, kPartCols) one per inner-product column, kAxpyCounter for the norm of
+// a multi-axpy.  The counters start at zero and every reduction resets its own.
+constexpr int kPartCols = 130;
+constexpr int kPartCounters = 160;
+constexpr int kAxpyCounter = 140;
+inline size_t part_buffer_doubles(int nparts) { return (size_t)nparts * kPartCols + 8 + kPartCounters / 2; }
+inline unsigned* part_counters(double* part, int nparts) {
+  return reinterpret_cast<unsigned*>(part + (size_t)nparts * kPartCols + 8);
+}
 // Weighted inner products <x, y>_W with weight wf on the first nfl entries
 // and 1 on the rest.
 template <typename T> void multi_dot(const T* w, const T* V, i64 ldv, int ncols, i64 n, i64 nfl, double wf,

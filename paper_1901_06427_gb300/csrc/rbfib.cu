@@ -1004,7 +1004,8 @@ int rbfib_create_grid(const rbfib_grid_desc* desc, void* stream, rbfib_grid** ou
     g->dV = D.h * D.h * D.h;
     build_stress_layout(g);
     g->nparts = 152 * 4;
-    g->part.alloc((size_t)g->nparts * 130 + 8);
+    g->part.alloc(part_buffer_doubles(g->nparts));
+    ck(cudaMemsetAsync(g->part.p, 0, sizeof(double) * part_buffer_doubles(g->nparts), g->s));
     g->small.alloc((size_t)(D.restart + 1) * D.restart + 4 * D.restart + 512);
     ck(cudaMallocHost((void**)&g->h_pinned, 64 * sizeof(double)));
     g->gst.alloc(8);
