@@ -230,3 +230,28 @@ def test_refined_sem_step(B):
         assert info[k]["rel_residual"] <= 1e-11
     dq = q.cpu().numpy().reshape(-1, 3) - w.q
     assert rel(dq, ref["q"] - w.q) < 1e-7
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_preconditioner_fluid_block_exact(B, name):
+    """On grids with at most 32 points per axis the V-cycles reduce to the exact
+    coarse-level solve (fast diagonalisation), so the fluid block of the
+    preconditioner is the projection method with exact inner solves:
+    v~ = (-eta LL)^-1 r_v, q = r_pi + D v~, phi = (-DG)^+ q, v = v~ + G phi,
+    pi = -eta q.  The preconditioner computes in FP32."""
+    from scipy.sparse.linalg import cg
+    from oracle import operators
+    w, og, ob = case(name)
+    g = B.grid_for(w)
+    lay = g.layout()
+    nf, nc = lay[3], lay[4] - lay[3]
+    r = np.random.default_rng(11).standard_normal(g.n_total)
+    z = g.apply_preconditioner(dev(r)).cpu().numpy()
+    vt = solve.viscous_solve(og, w.eta, r[None, :nf])[0]
+    D, G = operators.divergence(og), operators.gradient(og)
+    q = r[nf:nf + nc] + D @ vt
+    phi, info = cg(-(D @ G), q - q.mean(), rtol=1e-13, maxiter=20000)
+    assert info == 0
+    v = vt + G @ phi
+    assert rel(z[:nf], v) < 1e-4
+    assert rel(z[nf:nf + nc], -w.eta * q) < 1e-4
