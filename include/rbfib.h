@@ -202,8 +202,10 @@ int rbfib_batch_sem_step(rbfib_batch* b, const rbfib_sem_params* params, const u
                          int32_t* status);
 
 /* Threads per block the autotuner picked for this grid's finest-level
- * kernels: out[0] FP64 Stokes operator, out[1] FP32 Stokes operator, out[2]
- * velocity smoothing sweep, out[3] pressure smoothing sweep. */
+ * kernels: out[0] FP64 Stokes operator, out[1] FP32 Stokes operator (0 on
+ * uniform spacing, whose Stokes kernels have fixed tile shapes), out[2]
+ * velocity smoothing sweep, out[3] pressure smoothing sweep (as 32 x n/32
+ * blocks on uniform spacing). */
 int rbfib_tuned_blocks(const rbfib_grid* g, int32_t out[4]);
 
 /* ---- building blocks of the hot path, exposed for parity checks ---------- */

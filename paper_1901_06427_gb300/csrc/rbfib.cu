@@ -444,8 +444,8 @@ void apply_A(rbfib_grid* g, const T* x, T* y, bool with_bodies) {
   // (interpolation and spreading, 3 x 27 weighted terms each, and K, K^T)
   const double nflops = 10.0 * g->nf + 6.0 * g->nc + (with_bodies ? 400.0 * g->nbl : 0.0);
   TimerScope ts(g, TK_MATVEC, nbytes, nflops);
-  stokes_apply<T>(g->d, (T)g->desc.eta, x, x + g->nf, y, y + g->nf, g->s,
-                  sizeof(T) == 8 ? g->tune.stokes64 : g->tune.stokes32);
+  const int sbs = sizeof(T) == 8 ? g->tune.stokes64 : g->tune.stokes32;
+  stokes_apply<T>(g->d, (T)g->desc.eta, x, x + g->nf, y, y + g->nf, g->s, sbs > 0 ? sbs : 256);
   if (with_bodies && g->nb > 0) {
     const T* xl = x + g->nfl;
     const T* xU = xl + 3 * (i64)g->nbl;
@@ -918,8 +918,15 @@ void autotune(rbfib_grid* g) {
   ck(cudaMemsetAsync(x32, 0, sizeof(float) * g->nfl, g->s));
   ck(cudaMemsetAsync(y32, 0, sizeof(float) * g->nfl, g->s));
   const double eta = g->desc.eta;
-  t.stokes64 = pick_block(g->s, [&](int bs) { stokes_apply<double>(d, eta, x64, x64 + g->nf, y64, y64 + g->nf, g->s, bs); });
-  t.stokes32 = pick_block(g->s, [&](int bs) { stokes_apply<float>(d, (float)eta, x32, x32 + g->nf, y32, y32 + g->nf, g->s, bs); });
+  // the Stokes operator takes the block size only on non-uniform spacing (the
+  // uniform-spacing kernels have fixed tile shapes): 0 = not tuned
+  const bool uniform = d.h[0] == d.h[1] && d.h[1] == d.h[2];
+  t.stokes64 = uniform ? 0 : pick_block(g->s, [&](int bs) {
+    stokes_apply<double>(d, eta, x64, x64 + g->nf, y64, y64 + g->nf, g->s, bs);
+  });
+  t.stokes32 = uniform ? 0 : pick_block(g->s, [&](int bs) {
+    stokes_apply<float>(d, (float)eta, x32, x32 + g->nf, y32, y32 + g->nf, g->s, bs);
+  });
   t.vrbgs = pick_block(g->s, [&](int bs) { vel_rbgs<float>(d, (float)eta, 0, x32, y32, g->s, bs); });
   t.prbgs = pick_block(g->s, [&](int bs) { p_rbgs<float>(d, 0, x32 + g->nf, y32 + g->nf, g->s, bs); });
   g->tune = t;

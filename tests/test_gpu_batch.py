@@ -66,4 +66,7 @@ def test_autotuner_picks_a_candidate(B):
     w = workloads.small_case(n=(24, 20, 16), n_bodies=1)
     g = B.grid_for(w)
     t = g.tuned_blocks()
-    assert all(v in (64, 128, 256, 512) for v in t)
+    # uniform spacing: the Stokes kernels have fixed tile shapes (0 = not tuned);
+    # the smoothing sweeps take one of the candidate block sizes
+    assert t[0] == 0 and t[1] == 0
+    assert all(v in (64, 128, 256, 512) for v in t[2:])
