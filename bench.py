@@ -242,6 +242,11 @@ def roofline_for(top, kms, klaunch, kbytes, kflops):
            "peak_source": f"derived: {sms} SMs x {lanes} {arith.upper()} FMA lanes x 2 x {sm_mhz:.0f} MHz"}
     bound = "hbm" if f_bw >= f_fl else "alu"
     r = dict(mem if bound == "hbm" else alu)
+    per_launch = kbytes / klaunch if klaunch else 0.0
+    if per_launch < 64e6:
+        # the launch's working set sits in the 129 MB L2: the HBM fraction is an
+        # effective rate, and these short launches are bound by latency
+        r["resident"] = "L2 (working set per launch below half the 129 MB L2; effective GB/s)"
     r.update({"kernel": name, "bound": bound, "arith": arith,
               "other_roof": alu if bound == "hbm" else mem,
               "traffic": (TRAFFIC_RATIO[top] * kbytes / klaunch) if (top in TRAFFIC_RATIO and klaunch) else None,

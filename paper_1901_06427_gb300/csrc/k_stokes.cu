@@ -615,6 +615,109 @@ __global__ void k_p_rbgs_u(Dims d, T sh, int color, T* __restrict__ u, const T* 
   u[id] = cnt > 0 ? smooth_div<T>(rhs[id] * sh + nb, cnt) : u[id];
 }
 
+// Diagonal count of face (a; i, j, k) of the uniform-spacing velocity
+// operator: 6 plus one per tangential wall ghost.
+RBFIB_DEVFN int face_count(const Dims& d, int a, int i, int j, int k, int e0, int e1, int e2) {
+  int c = 6;
+  if (a != 0 && !d.per[0]) c += (i == 0) + (i == e0 - 1);
+  if (a != 1 && !d.per[1]) c += (j == 0) + (j == e1 - 1);
+  if (a != 2 && !d.per[2]) c += (k == 0) + (k == e2 - 1);
+  return c;
+}
+
+// The first two half sweeps of a V-cycle from a zero initial guess in one
+// launch (uniform spacing): colour-0 faces get u = rhs h^2 / (eta count);
+// a colour-1 face adds its colour-0 neighbours' values, formed on the fly
+// from their right-hand sides, in the same order as k_vel_rbgs_u.
+template <typename T>
+__global__ void k_vel_first2_u(Dims d, T sh, T* __restrict__ u, const T* __restrict__ rhs) {
+  const int nz = d.n[2];
+  const int a = (int)blockIdx.z / nz, k = (int)blockIdx.z - a * nz;
+  const int e0 = d.fe[a][0], e1 = d.fe[a][1], e2 = d.fe[a][2];
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= e2 || j >= e1 || i >= e0) return;
+  const T* ra = rhs + (unsigned)d.fo[a];
+  const unsigned sy = (unsigned)e0, sz = (unsigned)e0 * (unsigned)e1;
+  const unsigned id = (unsigned)i + sy * (unsigned)j + sz * (unsigned)k;
+  const int cnt = face_count(d, a, i, j, k, e0, e1, e2);
+  if (((i + j + k) & 1) == 0) {
+    u[(unsigned)d.fo[a] + id] = smooth_div<T>(ra[id] * sh, cnt);
+    return;
+  }
+  auto first = [&](int ii, int jj, int kk) {
+    const unsigned nid = (unsigned)ii + sy * (unsigned)jj + sz * (unsigned)kk;
+    return smooth_div<T>(ra[nid] * sh, face_count(d, a, ii, jj, kk, e0, e1, e2));
+  };
+  T nb = T(0);
+  // x
+  if (d.per[0]) nb += first(i > 0 ? i - 1 : e0 - 1, j, k) + first(i < e0 - 1 ? i + 1 : 0, j, k);
+  else {
+    if (i > 0) nb += first(i - 1, j, k);
+    if (i < e0 - 1) nb += first(i + 1, j, k);
+  }
+  // y
+  if (d.per[1]) nb += first(i, j > 0 ? j - 1 : e1 - 1, k) + first(i, j < e1 - 1 ? j + 1 : 0, k);
+  else {
+    if (j > 0) nb += first(i, j - 1, k);
+    if (j < e1 - 1) nb += first(i, j + 1, k);
+  }
+  // z
+  if (d.per[2]) nb += first(i, j, k > 0 ? k - 1 : e2 - 1) + first(i, j, k < e2 - 1 ? k + 1 : 0);
+  else {
+    if (k > 0) nb += first(i, j, k - 1);
+    if (k < e2 - 1) nb += first(i, j, k + 1);
+  }
+  u[(unsigned)d.fo[a] + id] = smooth_div<T>(ra[id] * sh + nb, cnt);
+}
+
+// Neumann pressure analogue: count = number of existing neighbours.
+RBFIB_DEVFN int cell_count(const Dims& d, int i, int j, int k) {
+  int c = 0;
+  c += d.per[0] ? 2 : (i > 0) + (i < d.n[0] - 1);
+  c += d.per[1] ? 2 : (j > 0) + (j < d.n[1] - 1);
+  c += d.per[2] ? 2 : (k > 0) + (k < d.n[2] - 1);
+  return c;
+}
+template <typename T>
+__global__ void k_p_first2_u(Dims d, T sh, T* __restrict__ u, const T* __restrict__ rhs) {
+  const int n0 = d.n[0], n1 = d.n[1], n2 = d.n[2];
+  const int k = blockIdx.z;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n1 || i >= n0) return;
+  const unsigned sy = (unsigned)n0, sz = (unsigned)n0 * (unsigned)n1;
+  const unsigned id = (unsigned)i + sy * (unsigned)j + sz * (unsigned)k;
+  const int cnt = cell_count(d, i, j, k);
+  if (cnt == 0) { u[id] = T(0); return; }
+  if (((i + j + k) & 1) == 0) {
+    u[id] = smooth_div<T>(rhs[id] * sh, cnt);
+    return;
+  }
+  auto first = [&](int ii, int jj, int kk) {
+    const unsigned nid = (unsigned)ii + sy * (unsigned)jj + sz * (unsigned)kk;
+    const int c = cell_count(d, ii, jj, kk);
+    return c > 0 ? smooth_div<T>(rhs[nid] * sh, c) : T(0);
+  };
+  T nb = T(0);
+  if (d.per[0]) nb += first(i > 0 ? i - 1 : n0 - 1, j, k) + first(i < n0 - 1 ? i + 1 : 0, j, k);
+  else {
+    if (i > 0) nb += first(i - 1, j, k);
+    if (i < n0 - 1) nb += first(i + 1, j, k);
+  }
+  if (d.per[1]) nb += first(i, j > 0 ? j - 1 : n1 - 1, k) + first(i, j < n1 - 1 ? j + 1 : 0, k);
+  else {
+    if (j > 0) nb += first(i, j - 1, k);
+    if (j < n1 - 1) nb += first(i, j + 1, k);
+  }
+  if (d.per[2]) nb += first(i, j, k > 0 ? k - 1 : n2 - 1) + first(i, j, k < n2 - 1 ? k + 1 : 0);
+  else {
+    if (k > 0) nb += first(i, j, k - 1);
+    if (k < n2 - 1) nb += first(i, j, k + 1);
+  }
+  u[id] = smooth_div<T>(rhs[id] * sh + nb, cnt);
+}
+
 // First half sweep from a zero initial guess: colour 0 gets rhs / (eta diag),
 // colour 1 is zeroed.
 template <typename T>
@@ -1042,6 +1145,26 @@ void vel_first(const Dims& d, T eta, T* u, const T* rhs, cudaStream_t s) {
   k_vel_first<T><<<nblk(d.fo[3], 256), 256, 0, s>>>(d, eta, u, rhs);
   note_launch();
 }
+// First two half sweeps from a zero guess in one launch on uniform spacing;
+// false (nothing launched) otherwise.
+template <typename T>
+bool vel_first2(const Dims& d, T eta, T* u, const T* rhs, cudaStream_t s, int bs) {
+  if (!(d.h[0] == d.h[1] && d.h[1] == d.h[2] && d.fo[3] < ((i64)1 << 31))) return false;
+  const int by = std::max(1, bs / 32);
+  dim3 grid((d.n[0] + 31) / 32, (d.n[1] + by - 1) / by, 3 * d.n[2]);
+  k_vel_first2_u<T><<<grid, dim3(32, by), 0, s>>>(d, (T)(d.h[0] * d.h[0] / (double)eta), u, rhs);
+  note_launch();
+  return true;
+}
+template <typename T>
+bool p_first2(const Dims& d, T* u, const T* rhs, cudaStream_t s, int bs) {
+  if (!(d.h[0] == d.h[1] && d.h[1] == d.h[2] && d.nc < ((i64)1 << 31))) return false;
+  const int by = std::max(1, bs / 32);
+  dim3 grid((d.n[0] + 31) / 32, (d.n[1] + by - 1) / by, d.n[2]);
+  k_p_first2_u<T><<<grid, dim3(32, by), 0, s>>>(d, (T)(d.h[0] * d.h[0]), u, rhs);
+  note_launch();
+  return true;
+}
 template <typename T>
 void vel_restrict_res(const Dims& df, const Dims& dc, int3 cz, T eta, const T* uf, const T* rhsf, T* rc,
                       cudaStream_t s) {
@@ -1125,6 +1248,8 @@ void add_grad(const Dims& d, const T* phi, T* v, cudaStream_t s) {
   template void stokes_apply<T>(const Dims&, T, const T*, const T*, T*, T*, cudaStream_t, int);  \
   template void vel_rbgs<T>(const Dims&, T, int, T*, const T*, cudaStream_t, int);               \
   template void vel_first<T>(const Dims&, T, T*, const T*, cudaStream_t);                         \
+  template bool vel_first2<T>(const Dims&, T, T*, const T*, cudaStream_t, int);                   \
+  template bool p_first2<T>(const Dims&, T*, const T*, cudaStream_t, int);                        \
   template void vel_restrict_res<T>(const Dims&, const Dims&, int3, T, const T*, const T*, T*, cudaStream_t); \
   template void p_first<T>(const Dims&, T*, const T*, cudaStream_t);                              \
   template void p_restrict_res<T>(const Dims&, const Dims&, int3, const T*, const T*, T*, cudaStream_t); \

@@ -56,6 +56,10 @@ struct StressLayout {
 template <typename T> void stokes_apply(const Dims&, T eta, const T* v, const T* p, T* yv, T* yp, cudaStream_t,
                                         int block = 256);
 template <typename T> void vel_rbgs(const Dims&, T eta, int color, T* u, const T* rhs, cudaStream_t, int block = 256);
+// The first two half sweeps (colours 0 then 1) from a zero guess in one
+// launch; false, with nothing launched, when the spacing is not uniform.
+template <typename T> bool vel_first2(const Dims&, T eta, T* u, const T* rhs, cudaStream_t, int bs);
+template <typename T> bool p_first2(const Dims&, T* u, const T* rhs, cudaStream_t, int bs);
 template <typename T> void vel_first(const Dims&, T eta, T* u, const T* rhs, cudaStream_t);
 template <typename T> void vel_restrict_res(const Dims&, const Dims&, int3, T eta, const T* uf, const T* rhsf,
                                             T* rc, cudaStream_t);

@@ -327,8 +327,16 @@ void vcycle_vel(rbfib_grid* g, T* u0, const T* rhs0) {
   const int lt = fd ? g->fd_vel : L - 1;
   for (int l = 0; l < lt; ++l) {
     const Dims& d = g->levels[l].d;
-    vel_first<T>(d, eta, u[l], rhs[l], g->s);          // zero guess + first colour-0 update
-    smooth(l, 1);
+    // zero guess, then colours 0 and 1 (one launch on uniform spacing)
+    bool fused;
+    {
+      TimerScope ts(g, l == 0 ? TK_SMOOTH : -1, 2.0 * (double)d.fo[3] * sizeof(T), 4.5 * (double)d.fo[3]);
+      fused = vel_first2<T>(d, eta, u[l], rhs[l], g->s, l == 0 ? g->tune.vrbgs : 256);
+    }
+    if (!fused) {
+      vel_first<T>(d, eta, u[l], rhs[l], g->s);
+      smooth(l, 1);
+    }
     for (int s = 1; s < kNu; ++s) { smooth(l, 0); smooth(l, 1); }
     vel_restrict_res<T>(d, g->levels[l + 1].d, g->levels[l].cz, eta, u[l], rhs[l], rhs[l + 1], g->s);
   }
@@ -363,8 +371,10 @@ void vcycle_p(rbfib_grid* g, T* u0, T* rhs0) {
   for (int l = 0; l < lt; ++l) {
     const Dims& d = g->levels[l].d;
     const int bs = l == 0 ? g->tune.prbgs : 256;
-    p_first<T>(d, u[l], rhs[l], g->s);
-    p_rbgs<T>(d, 1, u[l], rhs[l], g->s, bs);
+    if (!p_first2<T>(d, u[l], rhs[l], g->s, bs)) {   // zero guess, then colours 0 and 1
+      p_first<T>(d, u[l], rhs[l], g->s);
+      p_rbgs<T>(d, 1, u[l], rhs[l], g->s, bs);
+    }
     for (int s = 1; s < kNu; ++s) { p_rbgs<T>(d, 0, u[l], rhs[l], g->s, bs); p_rbgs<T>(d, 1, u[l], rhs[l], g->s, bs); }
     p_restrict_res<T>(d, g->levels[l + 1].d, g->levels[l].cz, u[l], rhs[l], rhs[l + 1], g->s);
   }
