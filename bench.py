@@ -58,6 +58,28 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def replica_seed(seed, rank):
+    """Each rank advances its own independent replica (replicas only: the
+    single-system solve has no exchange step to distribute)."""
+    return seed + 7919 * rank
+
+
+def max_over_ranks(ms, world, device="cuda"):
+    """The slowest rank's time (all ranks take part)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, max_ms):
+    """Steps of all ranks per second of the slowest rank ("scaling": "weak")."""
+    return world * steps / (max_ms / 1000.0)
+
+
 def workload_config(w):
     return {"workload": w.name, "grid": list(w.n), "bodies": w.n_bodies, "blobs_per_body": 42,
             "kernel": "3-point Peskin", "dt": w.dt, "kT": w.kT, "rtol": 1e-8, "precision": "fp64",
@@ -354,7 +376,7 @@ def run_ours(args):
     p = B.sem_params(w.potentials, dt=w.dt, kT=w.kT)
     q = torch.tensor(w.q.ravel(), device="cuda")
     quat = torch.tensor(w.quat.ravel(), device="cuda")
-    seed = w.seed + 7919 * rank
+    seed = replica_seed(w.seed, rank)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     state = {"step": 0, "rejects": 0, "iters": []}
@@ -418,13 +440,9 @@ def run_ours(args):
     top = max(shares, key=lambda c: shares[c][0])
     kms, klaunch, kbytes, kflops = shares[top]
     state["iters"] = iters_timed
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(step_ms, world)
     ms_per_step = step_ms / args.steps
-    value = world * args.steps / (step_ms / 1000.0)
+    value = whole_job_rate(world, args.steps, step_ms)
     # ----------------------------------------------------- end-to-end (host)
     qh = torch.tensor(w.q.ravel(), dtype=torch.float64).pin_memory()
     quath = torch.tensor(w.quat.ravel(), dtype=torch.float64).pin_memory()
@@ -443,13 +461,9 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, world)
     nbytes = (qh.numel() + quath.numel()) * 8
-    e2e = {"value": world * args.steps / (e2e_ms / 1000.0), "unit": "SEM steps/s",
+    e2e = {"value": whole_job_rate(world, args.steps, e2e_ms), "unit": "SEM steps/s",
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
     # ----------------------------------------------------------- roofline
     roofline = roofline_for(top, kms, klaunch, kbytes, kflops)

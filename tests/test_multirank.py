@@ -1,0 +1,61 @@
+"""Host logic of the multi-rank bench path on CPU: two gloo ranks agree on the
+slowest rank's time, the whole-job rate counts every rank's steps, replicas
+get distinct seeds, and a non-zero rank of the reference arm exits without
+work.  (One process per GPU with independent replicas; no data-path
+collective.)"""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        my_ms = 100.0 + 37.0 * rank
+        got = bench.max_over_ranks(my_ms, world, device="cpu")
+        out[rank] = (got, bench.whole_job_rate(world, 10, got), bench.replica_seed(1234, rank))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_agree_on_max_time_and_rate():
+    world = 2
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.start_processes(_rank_main, args=(world, _free_port(), out), nprocs=world, start_method="spawn")
+        res = dict(out)
+    assert set(res) == {0, 1}
+    assert res[0][0] == res[1][0] == 137.0
+    assert res[0][1] == res[1][1] == pytest.approx(2 * 10 / 0.137)
+    assert res[0][2] != res[1][2]
+
+
+def test_single_rank_needs_no_process_group():
+    assert bench.max_over_ranks(12.5, 1) == 12.5
+    assert bench.whole_job_rate(1, 4, 2000.0) == pytest.approx(2.0)
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
