@@ -42,32 +42,38 @@ __global__ void k_rpy_full(int nbl, const double* __restrict__ r, double a, doub
   M[t] = (float)v;
 }
 
-// In-place Gauss-Jordan inverse of an n x n matrix by one block.  status is
-// set to 1 on a zero pivot.
+// In-place Gauss-Jordan inverse of an n x n matrix by one block (no
+// pivoting; the matrices are symmetric positive definite).  Per pivot k the
+// pivot column and row are staged in shared memory, then each warp updates
+// whole rows (lanes along the row).  status is set to 1 on a zero pivot.
 template <typename R>
 __global__ void k_gj_inverse(R* __restrict__ A, int n, int* __restrict__ status) {
   extern __shared__ unsigned char shraw[];
-  R* col = (R*)shraw;
+  R* col = (R*)shraw;   // column k
+  R* prow = col + n;    // row k
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int k = 0; k < n; ++k) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      col[i] = A[(i64)i * n + k];
+      prow[i] = A[(i64)k * n + i];
+    }
     __syncthreads();
-    const R p = A[(i64)k * n + k];
+    const R p = prow[k];
     if (!(p > R(0) || p < R(0))) {
       if (threadIdx.x == 0) *status = 1;
       return;
     }
     const R ip = R(1) / p;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = A[(i64)i * n + k];
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) A[(i64)k * n + j] = (j == k) ? ip : A[(i64)k * n + j] * ip;
-    __syncthreads();
-    const i64 nn = (i64)n * n;
-    for (i64 t = threadIdx.x; t < nn; t += blockDim.x) {
-      const int i = (int)(t / n), j = (int)(t - (i64)i * n);
-      if (i == k) continue;
-      const R f = col[i];
-      if (j == k) A[t] = -f * ip;
-      else A[t] -= f * A[(i64)k * n + j];
+    for (int i = wid; i < n; i += nw) {
+      R* Ai = A + (i64)i * n;
+      if (i == k) {
+        for (int j = lane; j < n; j += 32) Ai[j] = (j == k) ? ip : prow[j] * ip;
+      } else {
+        const R f = col[i] * ip;
+        for (int j = lane; j < n; j += 32) Ai[j] = (j == k) ? -f : Ai[j] - f * prow[j];
+      }
     }
+    __syncthreads();
   }
 }
 
@@ -128,13 +134,13 @@ void dense_body_build(int nbl, int nb, const int* boff, const double* r, const d
   cudaMemsetAsync(status, 0, sizeof(int), s);
   k_rpy_full<<<nblk(n3 * n3, 256), 256, 0, s>>>(nbl, r, a, eta, Minv);
   note_launch();
-  k_gj_inverse<float><<<1, 1024, sizeof(float) * n3, s>>>(Minv, (int)n3, status);
+  k_gj_inverse<float><<<1, 1024, 2 * sizeof(float) * n3, s>>>(Minv, (int)n3, status);
   note_launch();
   k_mk<<<nblk(n3 * m, 256), 256, 0, s>>>(nbl, nb, boff, arm, Minv, P);
   note_launch();
   k_ktp<<<nblk(m * m, 256), 256, 0, s>>>(nbl, nb, boff, arm, P, N);
   note_launch();
-  k_gj_inverse<double><<<1, 1024, sizeof(double) * m, s>>>(N, (int)m, status);
+  k_gj_inverse<double><<<1, 1024, 2 * sizeof(double) * m, s>>>(N, (int)m, status);
   note_launch();
 }
 
