@@ -83,7 +83,7 @@ def whole_job_rate(world, steps, max_ms):
 def workload_config(w):
     return {"workload": w.name, "grid": list(w.n), "bodies": w.n_bodies, "blobs_per_body": 42,
             "kernel": "3-point Peskin", "dt": w.dt, "kT": w.kT, "rtol": 1e-8, "precision": "fp64",
-            "krylov": "FGMRES(48), CGS2; preconditioner: projection with multigrid V(1,2) velocity and "
+            "krylov": "FGMRES(48), CGS2; preconditioner: projection with multigrid V(2,2) velocity and "
                       "pressure cycles, exact coarse-level solves, dense RPY body block",
             "l2": "flushed (512 MiB write) between timed steps", "data": "synthetic, seeded"}
 

@@ -281,10 +281,11 @@ KrylovStore<double>& kr_of<double>(rbfib_grid* g) { return g->kr64; }
 template <>
 KrylovStore<float>& kr_of<float>(rbfib_grid* g) { return g->kr32; }
 
-// Smoothing sweeps before and after the coarse correction, V(1,2): on the
-// two-sphere grid V(1,2) beats V(2,2) slightly (45 vs 44 iterations, fewer
-// launches); V(2,1) and V(1,1) cost more iterations than they save.
-const int kNuPre = 1;
+// Smoothing sweeps before and after the coarse correction, V(2,2).  V(1,2)
+// is marginally faster on the two-sphere grid (one GPU-wide level above the
+// coarse solve) but costs 10% more iterations on the 128x128x64 grid (two
+// levels); V(2,1) and V(1,1) cost more iterations than they save.
+const int kNuPre = 2;
 const int kNuPost = 2;
 int coarse_sweeps(const Dims& d) { return std::max(d.n[0], std::max(d.n[1], d.n[2])) + 2; }
 
