@@ -14,6 +14,7 @@ independent replica (different seed); value = all ranks' steps / max time.
 The reference arm times the FP64 CPU oracle on the host cores.
 """
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -23,6 +24,10 @@ import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+# The CUDA runtime maps streams onto this many hardware queues (8 by default);
+# the ensemble's worker streams would otherwise share queues and serialise.
+# Read when the CUDA context is created, so it is set before torch is imported.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 sys.path.insert(0, ROOT)
 
 METRIC = "SEM steps/s at GMRES rel.res 1e-8; Stokes-IB matvec HBM GB/s; refined vs FP64"
@@ -50,7 +55,7 @@ def parse():
     ap.add_argument("--ensemble", type=int, default=0,
                     help="also time a batched ensemble of this many systems (0: skip)")
     ap.add_argument("--ensemble-steps", type=int, default=2)
-    ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--workers", type=int, default=16)
     return ap.parse_args()
 
 
@@ -229,8 +234,8 @@ def run_matvec_large(B, torch, hbm, n=256, reps=20):
 CLASS_INFO = {
     "matvec": ("k_stokes_cols_f64 + k_saddle_bodies (saddle matvec)", "fp64", 152),
     "smooth": ("k_vel_rbgs_u (red-black half sweep, finest velocity level)", "fp32", 152),
-    "dot": ("k_dot_part + k_dot_finish (CGS2 inner products)", "fp64", 152),
-    "axpy": ("k_multi_axpy (+ k_dot_finish for the norm)", "fp64", 152),
+    "dot": ("k_dot_part (CGS2 inner products, column sums finished in its last block)", "fp64", 152),
+    "axpy": ("k_multi_axpy (norm of the result finished in its last block)", "fp64", 152),
     "coarse": ("k_fd_solve (exact coarse-level solve, one 8-CTA cluster per grid)", "fp32", 16),
 }
 # DRAM bytes per algorithmic byte from the ncu captures summarised under
@@ -345,6 +350,7 @@ def run_ensemble(args, B, torch):
         torch.cuda.empty_cache()
     out["systems"] = args.ensemble
     out["workers"] = args.workers
+    out["hardware_queues"] = int(os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8"))
     out["mean_cells"] = float(sum(w.n[0] * w.n[1] * w.n[2] for w in ws) / len(ws))
     return out
 
@@ -411,6 +417,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     l0 = B.launch_count()
     state["iters"].clear()
+    gc.disable()   # no collector pauses inside the timed steps
     t_wall = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(float(k))
@@ -420,6 +427,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     t_wall = time.perf_counter() - t_wall
+    gc.enable()
     launches = B.launch_count() - l0
     clk = clocks.stop()
     step_ms = sum(a.elapsed_time(b) for a, b in ev)
@@ -448,18 +456,25 @@ def run_ours(args):
     quath = torch.tensor(w.quat.ravel(), dtype=torch.float64).pin_memory()
     qd = torch.empty_like(q)
     quatd = torch.empty_like(quat)
-    torch.cuda.synchronize()
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(args.steps):
+
+    def host_step():
         qd.copy_(qh, non_blocking=True)
         quatd.copy_(quath, non_blocking=True)
         one_step(qd, quatd)
         qh.copy_(qd, non_blocking=True)
         quath.copy_(quatd, non_blocking=True)
+
+    host_step()   # untimed: first use of these buffers
+    torch.cuda.synchronize()
+    barrier()
+    gc.disable()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        host_step()
     e1.record(stream)
     torch.cuda.synchronize()
+    gc.enable()
     e2e_ms = e0.elapsed_time(e1)
     e2e_ms = max_over_ranks(e2e_ms, world)
     nbytes = (qh.numel() + quath.numel()) * 8
@@ -487,13 +502,28 @@ def run_ours(args):
         gr.sem_step(p, seed, 10_000 + k, 0, qr, quatr)
     torch.cuda.synchronize()
     er0, er1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r_iters = []
     er0.record(stream)
     for k in range(args.steps):
-        gr.sem_step(p, seed, 20_000 + k, 0, qr, quatr)
+        _, info = gr.sem_step(p, seed, 20_000 + k, 0, qr, quatr)
+        r_iters.append([(info[key]["iterations"], info[key]["refinements"])
+                        for key in ("solve_rfd", "solve_stokes", "solve_main")])
     er1.record(stream)
     torch.cuda.synchronize()
+    r_shares = {}
+    for cname in TIMER_NAMES:
+        gr.kernel_timer(TIMER_NAMES[cname])
+        for k in range(nrep):
+            gr.sem_step(p, seed, 30_000 + k, 0, qr, quatr)
+        torch.cuda.synchronize()
+        r_shares[cname] = gr.kernel_timer_read()[0] / nrep
+        gr.kernel_timer(0)
+    ri = np.array(r_iters, dtype=float)
     line["refined_vs_fp64"] = {"fp32_refined_steps_per_s": args.steps / (er0.elapsed_time(er1) / 1000.0),
-                               "fp64_steps_per_s": value / world, "rtol": 1e-8}
+                               "fp64_steps_per_s": value / world, "rtol": 1e-8,
+                               "fp32_refined_krylov_iterations_per_step": [int(round(x)) for x in ri[:, :, 0].mean(0)],
+                               "fp32_refined_refinements_per_step": [round(float(x), 2) for x in ri[:, :, 1].mean(0)],
+                               "fp32_refined_time_share_ms_per_step": r_shares}
     try:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
     except Exception:

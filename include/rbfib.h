@@ -182,9 +182,12 @@ int rbfib_sem_step(rbfib_grid* g, const rbfib_sem_params* p, uint64_t seed, uint
 
 /* An ensemble of independent suspensions (the many independent trajectories
  * of Sec. V), e.g. cuboids of different sizes.  System i gets a grid created
- * from descs[i] (host array of n_sys descriptors) and bound to worker stream
- * i % n_workers; the batch owns the streams and the grids.  Set each
- * system's bodies with rbfib_set_bodies(rbfib_batch_grid(b, i), ...). */
+ * from descs[i] (host array of n_sys descriptors); the batch owns the grids
+ * and n_workers streams.  Set each system's bodies with
+ * rbfib_set_bodies(rbfib_batch_grid(b, i), ...).  The CUDA runtime maps
+ * streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware queues (8 unless that
+ * variable is set before the context is created); more workers than queues
+ * share queues and serialise. */
 typedef struct rbfib_batch rbfib_batch;
 int rbfib_create_batch(int32_t n_sys, const rbfib_grid_desc* descs, int32_t n_workers, rbfib_batch** out);
 void rbfib_destroy_batch(rbfib_batch* b);
@@ -193,7 +196,11 @@ rbfib_grid* rbfib_batch_grid(rbfib_batch* b, int32_t sys);   /* NULL if out of r
 /* One Split-Euler-Maruyama step of every system (Algorithm 1): system i uses
  * params[i], seeds[i], attempts[i] (NULL = 0) and its device configuration
  * q[i], quat[i] (host arrays of device pointers).  Workers run concurrently
- * on their own host threads and streams.  status[i] receives each system's
+ * on their own host threads and streams and take systems from a shared queue,
+ * longest first by each system's duration in the previous call (by unknown
+ * count before the first); a system's grid is bound to the stream of the
+ * worker that takes it, so a call made on a batch grid between batch steps
+ * runs on one of the batch's streams.  status[i] receives each system's
  * rbfib_sem_step status (RBFIB_EREJECT leaves that system unchanged); infos
  * may be NULL.  Returns the first status other than OK / EREJECT, else OK.
  * Synchronises every worker stream. */

@@ -368,9 +368,13 @@ def _desc(n, h=1.0, eta=1.0, periodic=(False, False, False), wall_vel=None, prec
 
 class Batch:
     """An ensemble of independent systems advanced together (C ABI
-    rbfib_create_batch / rbfib_batch_sem_step)."""
+    rbfib_create_batch / rbfib_batch_sem_step).
 
-    def __init__(self, workloads_, precision=None, workers=8, restart=30, max_iter=4000):
+    The workers' streams overlap on the GPU only as far as the CUDA runtime
+    gives them separate hardware queues: CUDA_DEVICE_MAX_CONNECTIONS (8 unless
+    set in the environment before the CUDA context is created; at most 32)."""
+
+    def __init__(self, workloads_, precision=None, workers=16, restart=30, max_iter=4000):
         n = len(workloads_)
         descs = (GridDesc * n)()
         for i, w in enumerate(workloads_):

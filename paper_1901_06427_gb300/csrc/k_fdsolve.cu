@@ -5,10 +5,11 @@
 // wall-normal boundary faces) and the Neumann pressure operator -D G are
 // Kronecker sums of 1D second differences, one per axis.  Their eigenvectors
 // are sine / cosine / Fourier bases in closed form, so the level solve is
-// three 1D transforms, a diagonal scaling and three transforms back, done by
-// one CTA per grid in shared memory.  This is the coarsest solve of the
+// three 1D transforms, a diagonal scaling and three transforms back, done in
+// shared memory.  This is the coarsest solve of the
 // V-cycles; the bases are built on the host once per grid and checked
-// against the explicit 1D matrices.
+// against the explicit 1D matrices.  Each grid is solved by one cluster of
+// CTAs that split its z-planes (see k_fd_solve).
 #include <cmath>
 #include <mutex>
 
@@ -217,8 +218,25 @@ __global__ void __cluster_dims__(kFDCtas, 1, 1) __launch_bounds__(kFDThreads)
   float* M = fsm;
   float* A = M + ((G.tabn + 3) & ~3);
   float* B = A + ((pz * pl + 3) & ~3);
-  for (int t = threadIdx.x; t < G.tabn; t += blockDim.x) M[t] = P.tab[G.tab0 + t];
-  for (int t = threadIdx.x; t < np * pl; t += blockDim.x) A[t] = rhs[G.off + (long long)z0 * pl + t];
+  // Staging by asynchronous copies, all issued before the one wait: the table
+  // in 16-byte words (every grid's segment starts on a 16-byte boundary of
+  // the table and is zero-padded to whole words; M and A are 16-byte aligned)
+  // and the own planes of the right-hand side element by element.
+  {
+    const unsigned msm = (unsigned)__cvta_generic_to_shared(M);
+    const float4* tab4 = reinterpret_cast<const float4*>(P.tab + G.tab0);
+    const int nw = (G.tabn + 3) >> 2;
+    for (int t = threadIdx.x; t < nw; t += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(msm + 16u * (unsigned)t), "l"(tab4 + t)
+                   : "memory");
+    const unsigned asm0 = (unsigned)__cvta_generic_to_shared(A);
+    const float* src = rhs + G.off + (long long)z0 * pl;
+    for (int t = threadIdx.x; t < np * pl; t += blockDim.x)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(asm0 + 4u * (unsigned)t), "l"(src + t)
+                   : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  }
   __syncthreads();
   // per axis: Q (forward uses M[t][c] = q_c(t)), Q^T (backward), both e x ep,
   // then the eigenvalues (padded to ep); ep = e rounded up to 8

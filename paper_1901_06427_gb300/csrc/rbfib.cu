@@ -718,7 +718,7 @@ void build_levels(rbfib_grid* g) {
 }
 
 // Coarse levels of the FP32 V-cycles: the finest level whose grids all fit
-// one CTA's exact solve, for the velocity components and for the pressure.
+// one cluster's exact solve, for the velocity components and for the pressure.
 void build_fd(rbfib_grid* g) {
   std::vector<float> tab;
   g->fd_vel = g->fd_p = -1;
@@ -998,6 +998,14 @@ int rbfib_kernel_timer_read(rbfib_grid* g, double* total_ms, int64_t* launches, 
   if (alg_flops) *alg_flops = g->timer_flops;
   return RBFIB_OK;
 }
+
+}  // extern "C"
+
+// Used by the ensemble work queue between calls: every call on a grid ends
+// with its stream synchronised, so the next call may run on another stream.
+void rbfib_grid_bind_stream(rbfib_grid* g, cudaStream_t s) { g->s = s; }
+
+extern "C" {
 
 int rbfib_create_grid(const rbfib_grid_desc* desc, void* stream, rbfib_grid** out) {
   if (!desc || !out) return RBFIB_EINVAL;
