@@ -295,6 +295,15 @@ int rbfib_kernel_timer(rbfib_grid* g, int32_t which);
 int rbfib_kernel_timer_read(rbfib_grid* g, double* total_ms, int64_t* launches, double* alg_bytes,
                             double* alg_flops);
 
+/* Per-launch overhead of the timer's event bracket: the median (us, over reps
+ * in [1, 10000]) of the event time that the same bracket (idle wait, opening
+ * event, one launch, closing event) records around an empty kernel on the
+ * grid's stream.  Each timed launch's event time exceeds the kernel's own
+ * duration by about this much; subtracting it gives a lower bound on that
+ * duration (the empty kernel's own run time is subtracted too).
+ * Synchronises the stream. */
+int rbfib_kernel_timer_overhead(rbfib_grid* g, int32_t reps, double* median_us);
+
 #ifdef __cplusplus
 }
 #endif

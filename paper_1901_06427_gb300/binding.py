@@ -96,6 +96,7 @@ def lib():
                                       ctypes.POINTER(ctypes.c_int32)], I32),
             "rbfib_kernel_timer": ([P, I32], I32),
             "rbfib_kernel_timer_read": ([P, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)], I32),
+            "rbfib_kernel_timer_overhead": ([P, I32, ctypes.POINTER(D)], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -325,6 +326,13 @@ class Grid:
         self._check(lib().rbfib_kernel_timer_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b),
                                                   ctypes.byref(f)))
         return ms.value, n.value, b.value, f.value
+
+    def kernel_timer_overhead(self, reps=200):
+        """Median event-bracket time (us) of an empty kernel timed the way the
+        kernel timer times each launch."""
+        us = ctypes.c_double()
+        self._check(lib().rbfib_kernel_timer_overhead(self._h, int(reps), ctypes.byref(us)))
+        return us.value
 
     def tuned_blocks(self):
         out = (ctypes.c_int32 * 4)()

@@ -272,6 +272,13 @@ void gpu_delay(long long cycles, cudaStream_t s) {
   note_launch();
 }
 
+// An empty kernel: calibrates the kernel timer's per-launch event overhead.
+__global__ void k_empty() {}
+void gpu_empty(cudaStream_t s) {
+  k_empty<<<1, 32, 0, s>>>();
+  note_launch();
+}
+
 template <typename T>
 void scale_by(T* out, const T* in, const double* denom, int invert, i64 n, cudaStream_t s) {
   const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);

@@ -167,6 +167,7 @@ template <typename T> void multi_axpy(T* w, const T* V, i64 ldv, int ncols, cons
                                       i64 n, i64 nfl, double wf, double* part, int nparts, double* nrm2,
                                       cudaStream_t);
 void gpu_delay(long long cycles, cudaStream_t);
+void gpu_empty(cudaStream_t);
 template <typename T> void scale_by(T* out, const T* in, const double* denom, int invert, i64 n, cudaStream_t);
 void givens_step(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                  const double* hcol2, const double* hnext2, double* res_out, cudaStream_t);
