@@ -229,6 +229,46 @@ __device__ inline void philox_normals4(unsigned long long seed, unsigned long lo
 
 #define RBFIB_DEVFN __device__ __forceinline__
 
+// Programmatic dependent launch.  Every kernel of the library begins with
+// pdl_entry(), before it touches global memory: griddepcontrol.wait returns
+// once the kernels this grid depends on have completed and their memory
+// operations are visible (at once for a normal launch).  A kernel launched
+// by launch_k carries the programmatic-serialization attribute, so it may be
+// launched as soon as every block of its predecessor has exited, without
+// waiting for the predecessor's completion to be processed; since its own
+// first instruction is the wait, neither read-after-write nor
+// write-after-read order between the two kernels changes.  No kernel
+// releases its dependents early (griddepcontrol.launch_dependents): on
+// GB300 that placed the blocks of the next short grid while the current one
+// still occupied SMs, and the two-sphere SEM step ran 6% slower, against
+// 1.8% faster with the release at block exit.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
+namespace rbfib {
+// false when RBFIB_NO_PDL is set in the environment (read once)
+bool pdl_enabled();
+}  // namespace rbfib
+
+// Launches kernel k on stream s with programmatic stream serialization (a
+// plain launch when it is disabled).  Launch errors are left to
+// cudaGetLastError, as with the <<<>>> syntax.
+template <typename... P, typename... A>
+inline void launch_k(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = rbfib::pdl_enabled() ? 1 : 0;
+  (void)cudaLaunchKernelEx(&cfg, k, static_cast<A&&>(args)...);
+}
+
 #include <atomic>
 namespace rbfib {
 // Count of kernel launches issued by the library (host side, all grids and

@@ -15,6 +15,7 @@ namespace rbfib {
 static inline unsigned nblk(i64 n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 __global__ void k_rpy_full(int nbl, const double* __restrict__ r, double a, double eta, float* __restrict__ M) {
+  pdl_entry();
   const i64 n3 = 3 * (i64)nbl;
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n3 * n3) return;
@@ -48,6 +49,7 @@ __global__ void k_rpy_full(int nbl, const double* __restrict__ r, double a, doub
 // whole rows (lanes along the row).  status is set to 1 on a zero pivot.
 template <typename R>
 __global__ void k_gj_inverse(R* __restrict__ A, int n, int* __restrict__ status) {
+  pdl_entry();
   extern __shared__ unsigned char shraw[];
   R* col = (R*)shraw;   // column k
   R* prow = col + n;    // row k
@@ -81,6 +83,7 @@ __global__ void k_gj_inverse(R* __restrict__ A, int n, int* __restrict__ status)
 // only: identity for c < 3, w x arm for c >= 3.
 __global__ void k_mk(int nbl, int nb, const int* __restrict__ boff, const double* __restrict__ arm,
                      const float* __restrict__ Mi, float* __restrict__ P) {
+  pdl_entry();
   const i64 n3 = 3 * (i64)nbl, m = 6 * (i64)nb;
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n3 * m) return;
@@ -107,6 +110,7 @@ __global__ void k_mk(int nbl, int nb, const int* __restrict__ boff, const double
 // A = K^T P (6 nb x 6 nb, FP64)
 __global__ void k_ktp(int nbl, int nb, const int* __restrict__ boff, const double* __restrict__ arm,
                       const float* __restrict__ P, double* __restrict__ A) {
+  pdl_entry();
   const int m = 6 * nb;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= m * m) return;
@@ -132,15 +136,15 @@ void dense_body_build(int nbl, int nb, const int* boff, const double* r, const d
                       float* Minv, float* P, double* N, int* status, cudaStream_t s) {
   const i64 n3 = 3 * (i64)nbl, m = 6 * (i64)nb;
   cudaMemsetAsync(status, 0, sizeof(int), s);
-  k_rpy_full<<<nblk(n3 * n3, 256), 256, 0, s>>>(nbl, r, a, eta, Minv);
+  launch_k(k_rpy_full, nblk(n3 * n3, 256), 256, 0, s, nbl, r, a, eta, Minv);
   note_launch();
-  k_gj_inverse<float><<<1, 1024, 2 * sizeof(float) * n3, s>>>(Minv, (int)n3, status);
+  launch_k(k_gj_inverse<float>, 1, 1024, 2 * sizeof(float) * n3, s, Minv, (int)n3, status);
   note_launch();
-  k_mk<<<nblk(n3 * m, 256), 256, 0, s>>>(nbl, nb, boff, arm, Minv, P);
+  launch_k(k_mk, nblk(n3 * m, 256), 256, 0, s, nbl, nb, boff, arm, Minv, P);
   note_launch();
-  k_ktp<<<nblk(m * m, 256), 256, 0, s>>>(nbl, nb, boff, arm, P, N);
+  launch_k(k_ktp, nblk(m * m, 256), 256, 0, s, nbl, nb, boff, arm, P, N);
   note_launch();
-  k_gj_inverse<double><<<1, 1024, 2 * sizeof(double) * m, s>>>(N, (int)m, status);
+  launch_k(k_gj_inverse<double>, 1, 1024, 2 * sizeof(double) * m, s, N, (int)m, status);
   note_launch();
 }
 
@@ -157,6 +161,7 @@ __global__ void __cluster_dims__(kBodyCtas, 1, 1) __launch_bounds__(512)
                        const double* __restrict__ arm, const float* __restrict__ Mi, const float* __restrict__ P,
                        const double* __restrict__ N, const T* __restrict__ sres, const T* __restrict__ rU,
                        T* __restrict__ zlam, T* __restrict__ zU) {
+  pdl_entry();
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ unsigned char shraw[];

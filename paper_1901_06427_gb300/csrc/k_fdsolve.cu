@@ -206,6 +206,7 @@ __device__ __noinline__ void fd_columns(cooperative_groups::cluster_group& cl, f
 // transforms on the own planes.
 __global__ void __cluster_dims__(kFDCtas, 1, 1) __launch_bounds__(kFDThreads)
     k_fd_solve(FDParams P, float* __restrict__ u, const float* __restrict__ rhs) {
+  pdl_entry();
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) float fsm[];

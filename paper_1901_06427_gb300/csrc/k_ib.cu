@@ -20,6 +20,7 @@ RBFIB_DEVFN void quat_rot(const double* qt, double R[9]) {
 __global__ void k_geometry(int nbl, const int* __restrict__ bob, const double* __restrict__ ref,
                            const double* __restrict__ q, const double* __restrict__ quat,
                            double* __restrict__ r, double* __restrict__ arm) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nbl) return;
   const int p = bob[i];
@@ -35,12 +36,13 @@ __global__ void k_geometry(int nbl, const int* __restrict__ bob, const double* _
 
 void geometry(int nbl, const int* bob, const double* ref, const double* q, const double* quat,
               double* r, double* arm, cudaStream_t s) {
-  if (nbl > 0) { k_geometry<<<nblk(nbl, 128), 128, 0, s>>>(nbl, bob, ref, q, quat, r, arm); note_launch(); }
+  if (nbl > 0) { launch_k(k_geometry, nblk(nbl, 128), 128, 0, s, nbl, bob, ref, q, quat, r, arm); note_launch(); }
 }
 
 // -------------------------------------------------------------- binning
 __global__ void k_bin_keys(Dims d, int nbl, const double* __restrict__ r, int* __restrict__ key,
                            int* __restrict__ count) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nbl) return;
   int c[3];
@@ -57,6 +59,7 @@ __global__ void k_bin_keys(Dims d, int nbl, const double* __restrict__ r, int* _
 
 // exclusive scan, three phases
 __global__ void k_scan_blocks(const int* __restrict__ in, int n, int* __restrict__ out, int* __restrict__ bsum) {
+  pdl_entry();
   __shared__ int sh[1024];
   const int i = blockIdx.x * 1024 + threadIdx.x;
   int v = i < n ? in[i] : 0;
@@ -72,18 +75,21 @@ __global__ void k_scan_blocks(const int* __restrict__ in, int n, int* __restrict
   if (threadIdx.x == 1023) bsum[blockIdx.x] = sh[1023];
 }
 __global__ void k_scan_sums(int* bsum, int nb) {
+  pdl_entry();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     int acc = 0;
     for (int b = 0; b < nb; ++b) { int v = bsum[b]; bsum[b] = acc; acc += v; }
   }
 }
 __global__ void k_scan_add(int* out, int n, const int* __restrict__ bsum) {
+  pdl_entry();
   const int i = blockIdx.x * 1024 + threadIdx.x;
   if (i < n) out[i] += bsum[blockIdx.x];
 }
 
 __global__ void k_bin_scatter(int nbl, const int* __restrict__ key, const int* __restrict__ off,
                               int* __restrict__ fill, int* __restrict__ perm) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nbl) return;
   const int k = key[i];
@@ -92,6 +98,7 @@ __global__ void k_bin_scatter(int nbl, const int* __restrict__ key, const int* _
 
 // stable order inside each bin: insertion sort by blob id
 __global__ void k_bin_sort(i64 nc, const int* __restrict__ off, int* __restrict__ perm) {
+  pdl_entry();
   const i64 c = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const int b = off[c], e = off[c + 1];
@@ -108,18 +115,18 @@ void binning(const Dims& d, int nbl, const double* r, int* perm, int* off, int* 
   const i64 n1 = d.nc + 1;
   cudaMemsetAsync(count, 0, sizeof(int) * n1, s);
   cudaMemsetAsync(fill, 0, sizeof(int) * d.nc, s);
-  if (nbl > 0) { k_bin_keys<<<nblk(nbl, 128), 128, 0, s>>>(d, nbl, r, key, count); note_launch(); }
+  if (nbl > 0) { launch_k(k_bin_keys, nblk(nbl, 128), 128, 0, s, d, nbl, r, key, count); note_launch(); }
   const int nb = (int)((n1 + 1023) / 1024);
-  k_scan_blocks<<<nb, 1024, 0, s>>>(count, (int)n1, off, bsum);
+  launch_k(k_scan_blocks, nb, 1024, 0, s, count, (int)n1, off, bsum);
   note_launch();
-  k_scan_sums<<<1, 32, 0, s>>>(bsum, nb);
+  launch_k(k_scan_sums, 1, 32, 0, s, bsum, nb);
   note_launch();
-  k_scan_add<<<nb, 1024, 0, s>>>(off, (int)n1, bsum);
+  launch_k(k_scan_add, nb, 1024, 0, s, off, (int)n1, bsum);
   note_launch();
   if (nbl > 0) {
-    k_bin_scatter<<<nblk(nbl, 128), 128, 0, s>>>(nbl, key, off, fill, perm);
+    launch_k(k_bin_scatter, nblk(nbl, 128), 128, 0, s, nbl, key, off, fill, perm);
     note_launch();
-    k_bin_sort<<<nblk(d.nc, 256), 256, 0, s>>>(d.nc, off, perm);
+    launch_k(k_bin_sort, nblk(d.nc, 256), 256, 0, s, d.nc, off, perm);
     note_launch();
   }
 }
@@ -141,6 +148,7 @@ RBFIB_DEVFN void load_stencil(const Dims& d, int a, const double* x, Stencil27& 
 template <typename T>
 __global__ void k_spread(Dims d, int nbl, const int* __restrict__ perm, const double* __restrict__ r,
                          const T* __restrict__ lam, double scale, T* __restrict__ f) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * nbl) return;
   const int s = t / 3, a = t - 3 * s;
@@ -199,6 +207,7 @@ RBFIB_DEVFN void interp_one(const Dims& d, const Walls& wl, int a, const double*
 template <typename T>
 __global__ void k_interp(Dims d, Walls wl, int nbl, const double* __restrict__ r, const T* __restrict__ v,
                          double alpha, double beta, double gamma, T* __restrict__ out) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * nbl) return;
   const int i = t / 3, a = t - 3 * i;
@@ -216,6 +225,7 @@ __global__ void k_interp(Dims d, Walls wl, int nbl, const double* __restrict__ r
 // scatter.
 __global__ void k_stencil_build(Dims d, int nbl, const double* __restrict__ r, BlobStencil<double>* __restrict__ s64,
                                 BlobStencil<float>* __restrict__ s32) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * nbl) return;
   const int i = t / 3, a = t - 3 * i;
@@ -238,7 +248,7 @@ __global__ void k_stencil_build(Dims d, int nbl, const double* __restrict__ r, B
 
 void stencil_build(const Dims& d, int nbl, const double* r, BlobStencil<double>* s64, BlobStencil<float>* s32,
                    cudaStream_t s) {
-  if (nbl > 0) { k_stencil_build<<<nblk(3 * (i64)nbl, 128), 128, 0, s>>>(d, nbl, r, s64, s32); note_launch(); }
+  if (nbl > 0) { launch_k(k_stencil_build, nblk(3 * (i64)nbl, 128), 128, 0, s, d, nbl, r, s64, s32); note_launch(); }
 }
 
 template <typename T> RBFIB_DEVFN const BlobStencil<T>* table_of(const BodyView& b);
@@ -275,6 +285,7 @@ RBFIB_DEVFN void warp_spread(const Dims& d, int a, const BlobStencil<T>* __restr
 template <typename T>
 __global__ void k_interp_res(Dims d, int nbl, const BlobStencil<T>* __restrict__ tab, const T* __restrict__ v,
                              const T* __restrict__ rl, T* __restrict__ out) {
+  pdl_entry();
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (gw >= 3 * nbl) return;
   const T jv = warp_interp<T>(d, gw % 3, tab + gw, v, lane);
@@ -286,7 +297,7 @@ void interp_res(const Dims& d, const BodyView& b, const T* v, const T* rl, T* ou
   if (b.nbl > 0) {
     const BlobStencil<T>* tab = nullptr;
     if constexpr (sizeof(T) == 8) tab = (const BlobStencil<T>*)b.st64; else tab = (const BlobStencil<T>*)b.st32;
-    k_interp_res<T><<<nblk(32 * 3 * (i64)b.nbl, 128), 128, 0, s>>>(d, b.nbl, tab, v, rl, out);
+    launch_k(k_interp_res<T>, nblk(32 * 3 * (i64)b.nbl, 128), 128, 0, s, d, b.nbl, tab, v, rl, out);
     note_launch();
   }
 }
@@ -295,6 +306,7 @@ void interp_res(const Dims& d, const BodyView& b, const T* v, const T* rl, T* ou
 template <typename T>
 __global__ void k_interp_tab(Dims d, int nbl, const BlobStencil<T>* __restrict__ tab, const T* __restrict__ v,
                              double alpha, double beta, T* __restrict__ out) {
+  pdl_entry();
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (gw >= 3 * nbl) return;
   const T jv = warp_interp<T>(d, gw % 3, tab + gw, v, lane);
@@ -308,7 +320,7 @@ __global__ void k_interp_tab(Dims d, int nbl, const BlobStencil<T>* __restrict__
 void interp_tab(const Dims& d, const BodyView& b, const double* v, double alpha, double beta, double* out,
                 cudaStream_t s) {
   if (b.nbl > 0) {
-    k_interp_tab<double><<<nblk(32 * 3 * (i64)b.nbl, 128), 128, 0, s>>>(d, b.nbl, b.st64, v, alpha, beta, out);
+    launch_k(k_interp_tab<double>, nblk(32 * 3 * (i64)b.nbl, 128), 128, 0, s, d, b.nbl, b.st64, v, alpha, beta, out);
     note_launch();
   }
 }
@@ -316,6 +328,7 @@ void interp_tab(const Dims& d, const BodyView& b, const double* v, double alpha,
 // f += scale * S-like scatter of lam with the configuration's table (no 1/dV)
 __global__ void k_spread_tab(Dims d, int nbl, const int* __restrict__ perm, const BlobStencil<double>* __restrict__ tab,
                              const double* __restrict__ lam, double scale, double* __restrict__ f) {
+  pdl_entry();
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (gw >= 3 * nbl) return;
   const int s = gw / 3, a = gw - 3 * s;
@@ -325,7 +338,7 @@ __global__ void k_spread_tab(Dims d, int nbl, const int* __restrict__ perm, cons
 
 void spread_tab(const Dims& d, const BodyView& b, const double* lam, double scale, double* f, cudaStream_t s) {
   if (b.nbl > 0) {
-    k_spread_tab<<<nblk(32 * 3 * (i64)b.nbl, 128), 128, 0, s>>>(d, b.nbl, b.perm, b.st64, lam, scale, f);
+    launch_k(k_spread_tab, nblk(32 * 3 * (i64)b.nbl, 128), 128, 0, s, d, b.nbl, b.perm, b.st64, lam, scale, f);
     note_launch();
   }
 }
@@ -338,6 +351,7 @@ template <typename T>
 __global__ void k_saddle_bodies(Dims d, BodyView b, const T* __restrict__ v, const T* __restrict__ lam,
                                 const T* __restrict__ U, T* __restrict__ yv, T* __restrict__ ylam, T* __restrict__ yU,
                                 double inv_dV) {
+  pdl_entry();
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int nA = 3 * b.nbl, nB = b.nb;
   const BlobStencil<T>* tab = table_of<T>(b);
@@ -383,26 +397,35 @@ void saddle_bodies(const Dims& d, const BodyView& b, const T* v, const T* lam, c
   if (b.nbl == 0) return;
   const i64 warps = 2 * 3 * (i64)b.nbl + b.nb;
   const double inv_dV = 1.0 / (d.h[0] * d.h[1] * d.h[2]);
-  k_saddle_bodies<T><<<nblk(32 * warps, 128), 128, 0, s>>>(d, b, v, lam, U, yv, ylam, yU, inv_dV);
+  launch_k(k_saddle_bodies<T>, nblk(32 * warps, 128), 128, 0, s, d, b, v, lam, U, yv, ylam, yU, inv_dV);
   note_launch();
 }
 
 template <typename T>
 void spread(const Dims& d, int nbl, const int* perm, const double* r, const T* lam, double scale, T* f,
             cudaStream_t s) {
-  if (nbl > 0) { k_spread<T><<<nblk(3 * (i64)nbl, 128), 128, 0, s>>>(d, nbl, perm, r, lam, scale, f); note_launch(); }
+  if (nbl > 0) {
+    launch_k(k_spread<T>, nblk(3 * (i64)nbl, 128), 128, 0, s,
+             d, nbl, perm, r, lam, scale, f);
+    note_launch();
+  }
 }
 
 template <typename T>
 void interp(const Dims& d, const Walls& wl, int nbl, const double* r, const T* v, double alpha,
             double beta, double gamma, T* out, cudaStream_t s) {
-  if (nbl > 0) { k_interp<T><<<nblk(3 * (i64)nbl, 128), 128, 0, s>>>(d, wl, nbl, r, v, alpha, beta, gamma, out); note_launch(); }
+  if (nbl > 0) {
+    launch_k(k_interp<T>, nblk(3 * (i64)nbl, 128), 128, 0, s,
+             d, wl, nbl, r, v, alpha, beta, gamma, out);
+    note_launch();
+  }
 }
 
 // K^T lam per body (FP64): out = alpha * K^T lam + beta * out
 template <typename T>
 __global__ void k_kt(int nb, const int* __restrict__ boff, const double* __restrict__ arm,
                      const T* __restrict__ lam, double alpha, double beta, double* __restrict__ out) {
+  pdl_entry();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= nb) return;
@@ -426,12 +449,17 @@ __global__ void k_kt(int nb, const int* __restrict__ boff, const double* __restr
 
 void kt_apply(int nb, const int* boff, const double* arm, const double* lam, double alpha, double beta,
               double* out, cudaStream_t s) {
-  if (nb > 0) { k_kt<double><<<nblk(32 * (i64)nb, 128), 128, 0, s>>>(nb, boff, arm, lam, alpha, beta, out); note_launch(); }
+  if (nb > 0) {
+    launch_k(k_kt<double>, nblk(32 * (i64)nb, 128), 128, 0, s,
+             nb, boff, arm, lam, alpha, beta, out);
+    note_launch();
+  }
 }
 
 // K U per blob: out = alpha * (u + w x arm) + beta * out
 __global__ void k_k(int nbl, const int* __restrict__ bob, const double* __restrict__ arm,
                     const double* __restrict__ U, double alpha, double beta, double* __restrict__ out) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * nbl) return;
   const int i = t / 3, a = t - 3 * i;
@@ -449,7 +477,7 @@ __global__ void k_k(int nbl, const int* __restrict__ bob, const double* __restri
 
 void k_apply(int nbl, const int* bob, const double* arm, const double* U, double alpha, double beta,
              double* out, cudaStream_t s) {
-  if (nbl > 0) { k_k<<<nblk(3 * (i64)nbl, 128), 128, 0, s>>>(nbl, bob, arm, U, alpha, beta, out); note_launch(); }
+  if (nbl > 0) { launch_k(k_k, nblk(3 * (i64)nbl, 128), 128, 0, s, nbl, bob, arm, U, alpha, beta, out); note_launch(); }
 }
 
 // ------------------------------------------------ body-block preconditioner
@@ -467,6 +495,7 @@ __global__ void k_body_precond(int nb, const int* __restrict__ boff, const int* 
                                const double* __restrict__ ref, const double* __restrict__ quat,
                                const T* __restrict__ sres, const T* __restrict__ rU,
                                T* __restrict__ zlam, T* __restrict__ zU) {
+  pdl_entry();
   extern __shared__ unsigned char shraw[];
   T* sh = (T*)shraw;
   const int p = blockIdx.x;
@@ -554,8 +583,8 @@ void body_precond(const BodyView& b, const PrecondView& pv, const T* sres, const
   const size_t shm = sizeof(T) * (2 * 3 * (size_t)pv.max_blobs + 8);
   const T* mi = nullptr;
   if constexpr (sizeof(T) == 8) mi = (const T*)pv.minv; else mi = (const T*)pv.minv32;
-  k_body_precond<T><<<b.nb, 256, shm, s>>>(b.nb, b.boff, pv.shape_of, pv.minv_off, mi, pv.nmat,
-                                          pv.shape_ref_blob, b.ref, b.quat, sres, rU, zlam, zU);
+  launch_k(k_body_precond<T>, b.nb, 256, shm, s, b.nb, b.boff, pv.shape_of, pv.minv_off, mi, pv.nmat,
+           pv.shape_ref_blob, b.ref, b.quat, sres, rU, zlam, zU);
   note_launch();
 }
 
@@ -568,6 +597,7 @@ __global__ void k_forces(Dims d, Potentials P, int nb, const int* __restrict__ b
                          const double* __restrict__ q, const double* __restrict__ r,
                          const double* __restrict__ arm, const double* __restrict__ fext,
                          double* __restrict__ out) {
+  pdl_entry();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nb) return;
   double F[6] = {0, 0, 0, 0, 0, 0};
@@ -632,7 +662,11 @@ __global__ void k_forces(Dims d, Potentials P, int nb, const int* __restrict__ b
 
 void body_forces(const Dims& d, const Potentials& P, const BodyView& b, const double* fext, double* out,
                  cudaStream_t s) {
-  if (b.nb > 0) { k_forces<<<nblk(b.nb, 64), 64, 0, s>>>(d, P, b.nb, b.boff, b.q, b.r, b.arm, fext, out); note_launch(); }
+  if (b.nb > 0) {
+    launch_k(k_forces, nblk(b.nb, 64), 64, 0, s,
+             d, P, b.nb, b.boff, b.q, b.r, b.arm, fext, out);
+    note_launch();
+  }
 }
 
 // ----------------------------------------------------------- SEM helpers
@@ -658,6 +692,7 @@ RBFIB_DEVFN void rotate_quat(const double* quat, const double phi[3], double* ou
 // W^FT = kT [W^f / L_p ; W^tau]
 __global__ void k_wft(int nb, const double* __restrict__ wn, const double* __restrict__ Lp, double kT,
                       double* __restrict__ wft) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 6 * nb) return;
   const int p = t / 6, c = t % 6;
@@ -665,13 +700,14 @@ __global__ void k_wft(int nb, const double* __restrict__ wn, const double* __res
 }
 
 void wft(int nb, const double* wn, const double* Lp, double kT, double* out, cudaStream_t s) {
-  if (nb > 0) { k_wft<<<nblk(6 * (i64)nb, 128), 128, 0, s>>>(nb, wn, Lp, kT, out); note_launch(); }
+  if (nb > 0) { launch_k(k_wft, nblk(6 * (i64)nb, 128), 128, 0, s, nb, wn, Lp, kT, out); note_launch(); }
 }
 
 // q' = q + a * (scale_t L_p W^f)  or  q' = q + a * U_trans;  quat' = Rotate(quat, a * W^tau | a * w)
 __global__ void k_move(int nb, const double* __restrict__ q, const double* __restrict__ quat,
                        const double* __restrict__ vec6, const double* __restrict__ Lp, double a,
                        double* __restrict__ qo, double* __restrict__ quato) {
+  pdl_entry();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nb) return;
   const double lp = Lp ? Lp[p] : 1.0;
@@ -682,10 +718,11 @@ __global__ void k_move(int nb, const double* __restrict__ q, const double* __res
 
 void move_bodies(int nb, const double* q, const double* quat, const double* vec6, const double* Lp, double a,
                  double* qo, double* quato, cudaStream_t s) {
-  if (nb > 0) { k_move<<<nblk(nb, 64), 64, 0, s>>>(nb, q, quat, vec6, Lp, a, qo, quato); note_launch(); }
+  if (nb > 0) { launch_k(k_move, nblk(nb, 64), 64, 0, s, nb, q, quat, vec6, Lp, a, qo, quato); note_launch(); }
 }
 
 __global__ void k_outside(Dims d, int nbl, const double* __restrict__ r, int* __restrict__ flag) {
+  pdl_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nbl) return;
   for (int a = 0; a < 3; ++a) {
@@ -696,7 +733,7 @@ __global__ void k_outside(Dims d, int nbl, const double* __restrict__ r, int* __
 }
 
 void outside_check(const Dims& d, int nbl, const double* r, int* flag, cudaStream_t s) {
-  if (nbl > 0) { k_outside<<<nblk(nbl, 128), 128, 0, s>>>(d, nbl, r, flag); note_launch(); }
+  if (nbl > 0) { launch_k(k_outside, nblk(nbl, 128), 128, 0, s, d, nbl, r, flag); note_launch(); }
 }
 
 #define INST(T)                                                                                          \
@@ -720,13 +757,18 @@ namespace rbfib {
 // arm_i = r_i - q_p for blob positions given as independent inputs
 __global__ void k_arms_from_positions(int nbl, const int* __restrict__ bob, const double* __restrict__ r,
                                       const double* __restrict__ q, double* __restrict__ arm) {
+  pdl_entry();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * nbl) return;
   arm[t] = r[t] - q[3 * bob[t / 3] + t % 3];
 }
 
 void arms_from_positions(int nbl, const int* bob, const double* r, const double* q, double* arm, cudaStream_t s) {
-  if (nbl > 0) { k_arms_from_positions<<<nblk(3 * (i64)nbl, 128), 128, 0, s>>>(nbl, bob, r, q, arm); note_launch(); }
+  if (nbl > 0) {
+    launch_k(k_arms_from_positions, nblk(3 * (i64)nbl, 128), 128, 0, s,
+             nbl, bob, r, q, arm);
+    note_launch();
+  }
 }
 
 // dL/dr_i = sum_a lam_ia D(zv)_ia + sum_a zl_ia D(v)_ia - zl_i x w_p - lam_i x tau_p,
@@ -737,6 +779,7 @@ __global__ void k_adjoint_positions(Dims d, int nbl, const int* __restrict__ bob
                                     const double* __restrict__ U, const double* __restrict__ zv,
                                     const double* __restrict__ zl, const double* __restrict__ zU,
                                     double* __restrict__ dr) {
+  pdl_entry();
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= nbl) return;
   double g[3] = {0.0, 0.0, 0.0};
@@ -786,7 +829,7 @@ void adjoint_positions(const Dims& d, int nbl, const int* bob, const double* r, 
                        const double* U, const double* zv, const double* zl, const double* zU, double* dr,
                        cudaStream_t s) {
   if (nbl > 0) {
-    k_adjoint_positions<<<nblk(32 * (i64)nbl, 128), 128, 0, s>>>(d, nbl, bob, r, v, lam, U, zv, zl, zU, dr);
+    launch_k(k_adjoint_positions, nblk(32 * (i64)nbl, 128), 128, 0, s, d, nbl, bob, r, v, lam, U, zv, zl, zU, dr);
     note_launch();
   }
 }

@@ -72,6 +72,7 @@ template <typename T>
 __global__ void k_dot_part(const T* __restrict__ w, const T* __restrict__ V, i64 ldv, i64 n, i64 nfl, double wf,
                            double* __restrict__ part, unsigned* __restrict__ cnt, double* __restrict__ out,
                            int vec) {
+  pdl_entry();
   const int col = blockIdx.y;
   const T* v = V + (i64)col * ldv;
   const i64 stride = (i64)gridDim.x * blockDim.x, t0 = (i64)blockIdx.x * blockDim.x + threadIdx.x;
@@ -119,6 +120,7 @@ __global__ void k_dot_part(const T* __restrict__ w, const T* __restrict__ V, i64
 
 // plain sum of nparts partials
 __global__ void k_sum_finish(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+  pdl_entry();
   double acc = 0.0;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i];
   acc = block_sum(acc);
@@ -137,8 +139,8 @@ void multi_dot(const T* w, const T* V, i64 ldv, int ncols, i64 n, i64 nfl, doubl
                double* out, cudaStream_t s) {
   const int nb = dot_blocks(n, nparts);
   dim3 grid(nb, ncols);
-  k_dot_part<T><<<grid, 256, 0, s>>>(w, V, ldv, n, nfl, wf, part, part_counters(part, nparts), out,
-                                     vec_ok(w, V, ldv, ncols));
+  launch_k(k_dot_part<T>, grid, 256, 0, s, w, V, ldv, n, nfl, wf, part, part_counters(part, nparts), out,
+           vec_ok(w, V, ldv, ncols));
   note_launch();
 }
 
@@ -149,6 +151,7 @@ __global__ void k_multi_axpy(T* __restrict__ w, const T* __restrict__ V, i64 ldv
                              const double* __restrict__ coef, double sign, i64 n, i64 nfl, double wf,
                              double* __restrict__ part, unsigned* __restrict__ cnt, double* __restrict__ nrm2,
                              int vec) {
+  pdl_entry();
   __shared__ double c[128];
   for (int i = threadIdx.x; i < ncols; i += blockDim.x) c[i] = sign * coef[i];
   __syncthreads();
@@ -236,8 +239,8 @@ __global__ void k_multi_axpy(T* __restrict__ w, const T* __restrict__ V, i64 ldv
 template <typename T>
 void multi_axpy(T* w, const T* V, i64 ldv, int ncols, const double* coef, double sign, i64 n, i64 nfl, double wf,
                 double* part, int nparts, double* nrm2, cudaStream_t s) {
-  k_multi_axpy<T><<<nparts, 256, 0, s>>>(w, V, ldv, ncols, coef, sign, n, nfl, wf, part,
-                                         part_counters(part, nparts) + kAxpyCounter, nrm2, vec_ok(w, V, ldv, ncols));
+  launch_k(k_multi_axpy<T>, nparts, 256, 0, s, w, V, ldv, ncols, coef, sign, n, nfl, wf, part,
+           part_counters(part, nparts) + kAxpyCounter, nrm2, vec_ok(w, V, ldv, ncols));
   note_launch();
 }
 
@@ -246,6 +249,7 @@ void multi_axpy(T* w, const T* V, i64 ldv, int ncols, const double* coef, double
 template <typename T>
 __global__ void k_scale(T* __restrict__ out, const T* __restrict__ in, const double* __restrict__ denom, int invert,
                         i64 n) {
+  pdl_entry();
   // one thread per block forms the factor (FP64 square root and division
   // are long instruction sequences)
   __shared__ double fs;
@@ -263,6 +267,7 @@ __global__ void k_scale(T* __restrict__ out, const T* __restrict__ in, const dou
 // ends by itself).  Used by the kernel timer so that the host has queued a
 // timed launch and its closing event before the stream reaches them.
 __global__ void k_delay(long long cycles) {
+  pdl_entry();
   const long long t0 = clock64();
   while (clock64() - t0 < cycles) {
   }
@@ -273,7 +278,7 @@ void gpu_delay(long long cycles, cudaStream_t s) {
 }
 
 // An empty kernel: calibrates the kernel timer's per-launch event overhead.
-__global__ void k_empty() {}
+__global__ void k_empty() { pdl_entry(); }
 void gpu_empty(cudaStream_t s) {
   k_empty<<<1, 32, 0, s>>>();
   note_launch();
@@ -282,7 +287,7 @@ void gpu_empty(cudaStream_t s) {
 template <typename T>
 void scale_by(T* out, const T* in, const double* denom, int invert, i64 n, cudaStream_t s) {
   const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);
-  k_scale<T><<<nb, 256, 0, s>>>(out, in, denom, invert, n);
+  launch_k(k_scale<T>, nb, 256, 0, s, out, in, denom, invert, n);
   note_launch();
 }
 
@@ -331,6 +336,7 @@ RBFIB_DEVFN double givens_core(double* H, int ldh, double* cs, double* sn, doubl
 
 __global__ void k_givens(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                          const double* hcol2, const double* hnext2, double* res_out) {
+  pdl_entry();
   double r;
   const double res = givens_core(H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, r);
   if (threadIdx.x == 0) res_out[0] = res;
@@ -338,12 +344,13 @@ __global__ void k_givens(double* H, int ldh, double* cs, double* sn, double* g, 
 
 void givens_step(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                  const double* hcol2, const double* hnext2, double* res_out, cudaStream_t s) {
-  k_givens<<<1, 64, 0, s>>>(H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, res_out);
+  launch_k(k_givens, 1, 64, 0, s, H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, res_out);
   note_launch();
 }
 
 // y = H[0:k,0:k]^{-1} g (upper triangular, column-major with leading dim ldh)
 __global__ void k_tri(const double* H, int ldh, const double* g, int k, double* y) {
+  pdl_entry();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int i = k - 1; i >= 0; --i) {
     double acc = g[i];
@@ -353,24 +360,26 @@ __global__ void k_tri(const double* H, int ldh, const double* g, int k, double* 
 }
 
 void tri_solve(const double* H, int ldh, const double* g, int k, double* y, cudaStream_t s) {
-  k_tri<<<1, 32, 0, s>>>(H, ldh, g, k, y);
+  launch_k(k_tri, 1, 32, 0, s, H, ldh, g, k, y);
   note_launch();
 }
 
 template <typename A, typename B>
 __global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, i64 n) {
+  pdl_entry();
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
     out[i] = (B)in[i];
 }
 template <typename A, typename B>
 void convert(const A* in, B* out, i64 n, cudaStream_t s) {
   const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);
-  if (n > 0) { k_convert<A, B><<<nb, 256, 0, s>>>(in, out, n); note_launch(); }
+  if (n > 0) { launch_k(k_convert<A, B>, nb, 256, 0, s, in, out, n); note_launch(); }
 }
 
 // y = a x + b y
 template <typename T>
 __global__ void k_axpby(T* __restrict__ y, const T* __restrict__ x, double a, double b, i64 n) {
+  pdl_entry();
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
     double v = a * (double)x[i];
     if (b != 0.0) v += b * (double)y[i];
@@ -380,15 +389,17 @@ __global__ void k_axpby(T* __restrict__ y, const T* __restrict__ x, double a, do
 template <typename T>
 void axpby(T* y, const T* x, double a, double b, i64 n, cudaStream_t s) {
   const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);
-  if (n > 0) { k_axpby<T><<<nb, 256, 0, s>>>(y, x, a, b, n); note_launch(); }
+  if (n > 0) { launch_k(k_axpby<T>, nb, 256, 0, s, y, x, a, b, n); note_launch(); }
 }
 
 // x -= mean(x)  (two passes, deterministic)
 __global__ void k_sub(double* x, i64 n, const double* mean_sum) {
+  pdl_entry();
   const double m = mean_sum[0] / (double)n;
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) x[i] -= m;
 }
 __global__ void k_sum_part(const double* __restrict__ x, i64 n, double* part) {
+  pdl_entry();
   double acc = 0.0;
   for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) acc += x[i];
   acc = block_sum(acc);
@@ -396,17 +407,18 @@ __global__ void k_sum_part(const double* __restrict__ x, i64 n, double* part) {
 }
 void project_mean(double* x, i64 n, double* part, int nparts, cudaStream_t s) {
   if (n == 0) return;
-  k_sum_part<<<nparts, 256, 0, s>>>(x, n, part);
+  launch_k(k_sum_part, nparts, 256, 0, s, x, n, part);
   note_launch();
-  k_sum_finish<<<1, 256, 0, s>>>(part, nparts, part + nparts);
+  launch_k(k_sum_finish, 1, 256, 0, s, part, nparts, part + nparts);
   note_launch();
-  k_sub<<<nparts, 256, 0, s>>>(x, n, part + nparts);
+  launch_k(k_sub, nparts, 256, 0, s, x, n, part + nparts);
   note_launch();
 }
 
 // bv += eta * 2 u_w / h^2 on faces adjacent (along a tangential axis) to a moving wall
 template <typename T>
 __global__ void k_wall_rhs(Dims d, Walls wl, double eta, T* __restrict__ bv) {
+  pdl_entry();
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.fo[3]) return;
   int a, c[3];
@@ -422,7 +434,7 @@ __global__ void k_wall_rhs(Dims d, Walls wl, double eta, T* __restrict__ bv) {
 }
 template <typename T>
 void wall_rhs(const Dims& d, const Walls& wl, double eta, T* bv, cudaStream_t s) {
-  k_wall_rhs<T><<<nblk(d.fo[3], 256), 256, 0, s>>>(d, wl, eta, bv);
+  launch_k(k_wall_rhs<T>, nblk(d.fo[3], 256), 256, 0, s, d, wl, eta, bv);
   note_launch();
 }
 
@@ -451,6 +463,7 @@ namespace rbfib {
 template <typename T>
 __global__ void k_fg_start(T* __restrict__ V0, const T* __restrict__ w, i64 n, double* __restrict__ gvec, int m,
                            int* __restrict__ ist, const double* __restrict__ dpar) {
+  pdl_entry();
   __shared__ double bs, fs;   // one thread per block forms beta and 1 / beta
   if (threadIdx.x == 0) {
     bs = sqrt(fmax(dpar[2], 0.0));
@@ -471,16 +484,17 @@ __global__ void k_fg_start(T* __restrict__ V0, const T* __restrict__ w, i64 n, d
 template <typename T>
 void fg_start(T* V0, const T* w, i64 n, double* gvec, int m, int* ist, const double* dpar, cudaStream_t s) {
   const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);
-  k_fg_start<T><<<nb, 256, 0, s>>>(V0, w, n, gvec, m, ist, dpar);
+  launch_k(k_fg_start<T>, nb, 256, 0, s, V0, w, n, gvec, m, ist, dpar);
   note_launch();
 }
 
 __global__ void k_setcond(cudaGraphConditionalHandle h, const int* __restrict__ ist) {
+  pdl_entry();
   if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, ist[2] ? 1u : 0u);
 }
 
 void set_condition(cudaGraphConditionalHandle h, const int* ist, cudaStream_t s) {
-  k_setcond<<<1, 32, 0, s>>>(h, ist);
+  launch_k(k_setcond, 1, 32, 0, s, h, ist);
   note_launch();
 }
 
@@ -488,6 +502,7 @@ void set_condition(cudaGraphConditionalHandle h, const int* ist, cudaStream_t s)
 __global__ void k_givens_flag(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                               const double* hcol2, const double* hnext2, double* res_out, int* ist,
                               const double* dpar) {
+  pdl_entry();
   double r;
   const double res = givens_core(H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, r);
   if (threadIdx.x != 0) return;
@@ -501,11 +516,12 @@ __global__ void k_givens_flag(double* H, int ldh, double* cs, double* sn, double
 void givens_flag(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                  const double* hcol2, const double* hnext2, double* res_out, int* ist, const double* dpar,
                  cudaStream_t s) {
-  k_givens_flag<<<1, 64, 0, s>>>(H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, res_out, ist, dpar);
+  launch_k(k_givens_flag, 1, 64, 0, s, H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, res_out, ist, dpar);
   note_launch();
 }
 
 __global__ void k_tri_dev(const double* H, int ldh, const double* g, const int* ist, double* y) {
+  pdl_entry();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int k = ist[0];
   for (int i = k - 1; i >= 0; --i) {
@@ -516,7 +532,7 @@ __global__ void k_tri_dev(const double* H, int ldh, const double* g, const int* 
 }
 
 void tri_solve_dev(const double* H, int ldh, const double* g, const int* ist, double* y, cudaStream_t s) {
-  k_tri_dev<<<1, 32, 0, s>>>(H, ldh, g, ist, y);
+  launch_k(k_tri_dev, 1, 32, 0, s, H, ldh, g, ist, y);
   note_launch();
 }
 
@@ -524,6 +540,7 @@ void tri_solve_dev(const double* H, int ldh, const double* g, const int* ist, do
 template <typename T>
 __global__ void k_multi_axpy_dev(T* __restrict__ w, const T* __restrict__ V, i64 ldv, const int* __restrict__ ist,
                                  const double* __restrict__ coef, double sign, i64 n) {
+  pdl_entry();
   __shared__ double c[128];
   const int ncols = ist[0];
   for (int i = threadIdx.x; i < ncols; i += blockDim.x) c[i] = sign * coef[i];
@@ -549,7 +566,7 @@ __global__ void k_multi_axpy_dev(T* __restrict__ w, const T* __restrict__ V, i64
 template <typename T>
 void multi_axpy_dev(T* w, const T* V, i64 ldv, const int* ist, const double* coef, double sign, i64 n, int nparts,
                     cudaStream_t s) {
-  k_multi_axpy_dev<T><<<nparts, 256, 0, s>>>(w, V, ldv, ist, coef, sign, n);
+  launch_k(k_multi_axpy_dev<T>, nparts, 256, 0, s, w, V, ldv, ist, coef, sign, n);
   note_launch();
 }
 

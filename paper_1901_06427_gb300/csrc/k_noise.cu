@@ -9,6 +9,7 @@ static inline unsigned nblk(i64 n, int bs) { return (unsigned)((n + bs - 1) / bs
 
 __global__ void k_philox_normals(unsigned long long seed, unsigned long long step, unsigned attempt,
                                  unsigned purpose, i64 count, double* __restrict__ out) {
+  pdl_entry();
   const i64 b = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (4 * b >= count) return;
   double z[4];
@@ -21,12 +22,17 @@ __global__ void k_philox_normals(unsigned long long seed, unsigned long long ste
 void philox_normals(unsigned long long seed, unsigned long long step, unsigned attempt, unsigned purpose,
                     i64 count, double* out, cudaStream_t s) {
   const i64 nb = (count + 3) / 4;
-  if (nb > 0) { k_philox_normals<<<nblk(nb, 128), 128, 0, s>>>(seed, step, attempt, purpose, count, out); note_launch(); }
+  if (nb > 0) {
+    launch_k(k_philox_normals, nblk(nb, 128), 128, 0, s,
+             seed, step, attempt, purpose, count, out);
+    note_launch();
+  }
 }
 
 // out(face of component a) = c * [ (W_aa(right) - W_aa(left)) / h_a
 //                                  + sum_{b != a} (c+ W_ab(node j+1) - c- W_ab(node j)) / h_b ]
 __global__ void k_stress_div(Dims d, StressLayout L, const double* __restrict__ W, double c, double* __restrict__ out) {
+  pdl_entry();
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.fo[3]) return;
   int a, f[3];
@@ -55,7 +61,7 @@ __global__ void k_stress_div(Dims d, StressLayout L, const double* __restrict__ 
 }
 
 void stress_divergence(const Dims& d, const StressLayout& L, const double* W, double c, double* out, cudaStream_t s) {
-  k_stress_div<<<nblk(d.fo[3], 256), 256, 0, s>>>(d, L, W, c, out);
+  launch_k(k_stress_div, nblk(d.fo[3], 256), 256, 0, s, d, L, W, c, out);
   note_launch();
 }
 

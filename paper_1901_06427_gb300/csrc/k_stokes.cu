@@ -71,6 +71,7 @@ RBFIB_DEVFN void lap_parts_uniform(const Dims& d, const T* __restrict__ v, int a
 template <typename T>
 __global__ void k_stokes_apply(Dims d, T eta, const T* __restrict__ v, const T* __restrict__ p,
                                T* __restrict__ yv, T* __restrict__ yp) {
+  pdl_entry();
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   const i64 nf = d.fo[3];
   if (t < nf) {
@@ -247,23 +248,25 @@ template <int KC>
 __global__ void __launch_bounds__(128) k_stokes_cols_f32(Dims d, float eta, const float* __restrict__ v,
                                                              const float* __restrict__ p, float* __restrict__ yv,
                                                              float* __restrict__ yp) {
+  pdl_entry();
   stokes_cols_body<KC, float>(d, eta, v, p, yv, yp);
 }
 template <int KC>
 __global__ void __launch_bounds__(128) k_stokes_cols_f64(Dims d, double eta, const double* __restrict__ v,
                                                          const double* __restrict__ p, double* __restrict__ yv,
                                                          double* __restrict__ yp) {
+  pdl_entry();
   stokes_cols_body<KC, double>(d, eta, v, p, yv, yp);
 }
 template <int KC>
 inline void launch_cols(dim3 gr, cudaStream_t s, const Dims& d, float eta, const float* v, const float* p, float* yv,
                         float* yp) {
-  k_stokes_cols_f32<KC><<<gr, dim3(d.n[0] >= 96 ? 128 : 32, d.n[0] >= 96 ? 1 : 4), 0, s>>>(d, eta, v, p, yv, yp);
+  launch_k(k_stokes_cols_f32<KC>, gr, dim3(d.n[0] >= 96 ? 128 : 32, d.n[0] >= 96 ? 1 : 4), 0, s, d, eta, v, p, yv, yp);
 }
 template <int KC>
 inline void launch_cols(dim3 gr, cudaStream_t s, const Dims& d, double eta, const double* v, const double* p,
                         double* yv, double* yp) {
-  k_stokes_cols_f64<KC><<<gr, dim3(d.n[0] >= 96 ? 128 : 32, d.n[0] >= 96 ? 1 : 4), 0, s>>>(d, eta, v, p, yv, yp);
+  launch_k(k_stokes_cols_f64<KC>, gr, dim3(d.n[0] >= 96 ? 128 : 32, d.n[0] >= 96 ? 1 : 4), 0, s, d, eta, v, p, yv, yp);
 }
 
 // Pipelined 2.5D Stokes operator for large grids (uniform spacing).  A 32 x 8
@@ -479,6 +482,7 @@ template <typename T, bool PX, bool PY, bool PZ>
 __global__ void __launch_bounds__(kPX * kPY, sizeof(T) == 4 ? 4 : 3)
     k_stokes_pipe(Dims d, T eta, const T* __restrict__ v, const T* __restrict__ p, T* __restrict__ yv,
                   T* __restrict__ yp) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char pipe_smem[];
   stokes_pipe_body<T, PX, PY, PZ>(d, eta, v, p, yv, yp, reinterpret_cast<T*>(pipe_smem));
 }
@@ -490,7 +494,7 @@ void launch_pipe_as(const Dims& d, cudaStream_t s, T eta, const T* v, const T* p
                          pipe_smem_bytes<T>());
   });
   dim3 gr((d.n[0] + kPX - 1) / kPX, (d.n[1] + kPY - 1) / kPY, (d.n[2] + kPZ - 1) / kPZ);
-  k_stokes_pipe<T, PX, PY, PZ><<<gr, dim3(kPX, kPY), pipe_smem_bytes<T>(), s>>>(d, eta, v, p, yv, yp);
+  launch_k(k_stokes_pipe<T, PX, PY, PZ>, gr, dim3(kPX, kPY), pipe_smem_bytes<T>(), s, d, eta, v, p, yv, yp);
 }
 template <typename T>
 void launch_pipe(const Dims& d, cudaStream_t s, T eta, const T* v, const T* p, T* yv, T* yp) {
@@ -529,6 +533,7 @@ RBFIB_DEVFN T lap_diag(const Dims& d, int a, const int c[3]) {
 // One red-black Gauss-Seidel half sweep: threads map to the points of one colour.
 template <typename T>
 __global__ void k_vel_rbgs(Dims d, ColorMap m, T eta, int color, T* __restrict__ u, const T* __restrict__ rhs) {
+  pdl_entry();
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   int a, c[3];
   if (!color_face(d, m, t, color, a, c)) return;
@@ -552,6 +557,7 @@ RBFIB_DEVFN double smooth_div<double>(double a, int c) { return a / (double)c; }
 
 template <typename T>
 __global__ void k_vel_rbgs_u(Dims d, T sh, int color, T* __restrict__ u, const T* __restrict__ rhs) {
+  pdl_entry();
   const int nz = d.n[2];
   const int a = (int)blockIdx.z / nz, k = (int)blockIdx.z - a * nz;
   const int e0 = d.fe[a][0], e1 = d.fe[a][1], e2 = d.fe[a][2];
@@ -588,6 +594,7 @@ __global__ void k_vel_rbgs_u(Dims d, T sh, int color, T* __restrict__ u, const T
 // neighbours (6 on periodic axes).
 template <typename T>
 __global__ void k_p_rbgs_u(Dims d, T sh, int color, T* __restrict__ u, const T* __restrict__ rhs) {
+  pdl_entry();
   const int n0 = d.n[0], n1 = d.n[1], n2 = d.n[2];
   const int k = blockIdx.z;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -631,6 +638,7 @@ RBFIB_DEVFN int face_count(const Dims& d, int a, int i, int j, int k, int e0, in
 // from their right-hand sides, in the same order as k_vel_rbgs_u.
 template <typename T>
 __global__ void k_vel_first2_u(Dims d, T sh, T* __restrict__ u, const T* __restrict__ rhs) {
+  pdl_entry();
   const int nz = d.n[2];
   const int a = (int)blockIdx.z / nz, k = (int)blockIdx.z - a * nz;
   const int e0 = d.fe[a][0], e1 = d.fe[a][1], e2 = d.fe[a][2];
@@ -681,6 +689,7 @@ RBFIB_DEVFN int cell_count(const Dims& d, int i, int j, int k) {
 }
 template <typename T>
 __global__ void k_p_first2_u(Dims d, T sh, T* __restrict__ u, const T* __restrict__ rhs) {
+  pdl_entry();
   const int n0 = d.n[0], n1 = d.n[1], n2 = d.n[2];
   const int k = blockIdx.z;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -722,6 +731,7 @@ __global__ void k_p_first2_u(Dims d, T sh, T* __restrict__ u, const T* __restric
 // colour 1 is zeroed.
 template <typename T>
 __global__ void k_vel_first(Dims d, T eta, T* __restrict__ u, const T* __restrict__ rhs) {
+  pdl_entry();
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.fo[3]) return;
   int a, c[3];
@@ -731,6 +741,7 @@ __global__ void k_vel_first(Dims d, T eta, T* __restrict__ u, const T* __restric
 
 template <typename T>
 __global__ void k_vel_residual(Dims d, T eta, const T* __restrict__ u, const T* __restrict__ rhs, T* __restrict__ res) {
+  pdl_entry();
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.fo[3]) return;
   int a, c[3];
@@ -800,6 +811,7 @@ __device__ inline void prolong_1d(int kind, int jf, int ncext, float ghost_sign,
 // face-centred axis, averaging of the two children along cell-centred axes.
 template <typename T>
 __global__ void k_vel_restrict(Dims df, Dims dc, int3 cz, const T* __restrict__ rf, T* __restrict__ rc) {
+  pdl_entry();
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= dc.fo[3]) return;
   int a, c[3];
@@ -824,6 +836,7 @@ __global__ void k_vel_restrict(Dims df, Dims dc, int3 cz, const T* __restrict__ 
 template <typename T>
 __global__ void k_vel_restrict_res(Dims df, Dims dc, int3 cz, T eta, const T* __restrict__ uf,
                                    const T* __restrict__ rhsf, T* __restrict__ rc) {
+  pdl_entry();
   // kRestrictLanes lanes per coarse point share its fine residuals
   const i64 gt = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   const i64 t = gt / kRestrictLanes;
@@ -857,6 +870,7 @@ __global__ void k_vel_restrict_res(Dims df, Dims dc, int3 cz, T eta, const T* __
 
 template <typename T>
 __global__ void k_vel_prolong(Dims df, Dims dc, int3 cz, const T* __restrict__ uc, T* __restrict__ uf) {
+  pdl_entry();
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= df.fo[3]) return;
   int a, c[3];
@@ -901,6 +915,7 @@ RBFIB_DEVFN void plap_parts(const Dims& d, const T* __restrict__ p, const int c[
 
 template <typename T>
 __global__ void k_p_rbgs(Dims d, ColorMap m, int color, T* __restrict__ u, const T* __restrict__ rhs) {
+  pdl_entry();
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   int c[3];
   if (!color_cell(d, m, t, color, c)) return;
@@ -924,6 +939,7 @@ RBFIB_DEVFN T plap_diag(const Dims& d, const int c[3]) {
 
 template <typename T>
 __global__ void k_p_first(Dims d, T* __restrict__ u, const T* __restrict__ rhs) {
+  pdl_entry();
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.nc) return;
   int c[3];
@@ -933,6 +949,7 @@ __global__ void k_p_first(Dims d, T* __restrict__ u, const T* __restrict__ rhs) 
 
 template <typename T>
 __global__ void k_p_residual(Dims d, const T* __restrict__ u, const T* __restrict__ rhs, T* __restrict__ res) {
+  pdl_entry();
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.nc) return;
   int c[3];
@@ -944,6 +961,7 @@ __global__ void k_p_residual(Dims d, const T* __restrict__ u, const T* __restric
 
 template <typename T>
 __global__ void k_p_restrict(Dims df, Dims dc, int3 cz, const T* __restrict__ rf, T* __restrict__ rc) {
+  pdl_entry();
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= dc.nc) return;
   int c[3];
@@ -963,6 +981,7 @@ __global__ void k_p_restrict(Dims df, Dims dc, int3 cz, const T* __restrict__ rf
 template <typename T>
 __global__ void k_p_restrict_res(Dims df, Dims dc, int3 cz, const T* __restrict__ uf, const T* __restrict__ rhsf,
                                  T* __restrict__ rc) {
+  pdl_entry();
   const i64 gt = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   const i64 t = gt / kRestrictLanes;
   const int sub = (int)(gt % kRestrictLanes);
@@ -991,6 +1010,7 @@ __global__ void k_p_restrict_res(Dims df, Dims dc, int3 cz, const T* __restrict_
 
 template <typename T>
 __global__ void k_p_prolong(Dims df, Dims dc, int3 cz, const T* __restrict__ uc, T* __restrict__ uf) {
+  pdl_entry();
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= df.nc) return;
   int c[3];
@@ -1010,6 +1030,7 @@ __global__ void k_p_prolong(Dims df, Dims dc, int3 cz, const T* __restrict__ uc,
 // Coarsest-level solves: one block, red-black sweeps with block barriers.
 template <typename T>
 __global__ void k_vel_coarse(Dims d, T eta, T* __restrict__ u, const T* __restrict__ rhs, int sweeps) {
+  pdl_entry();
   const i64 n = d.fo[3];
   for (i64 t = threadIdx.x; t < n; t += blockDim.x) u[t] = T(0);
   __syncthreads();
@@ -1030,6 +1051,7 @@ __global__ void k_vel_coarse(Dims d, T eta, T* __restrict__ u, const T* __restri
 
 template <typename T>
 __global__ void k_p_coarse(Dims d, T* __restrict__ u, T* __restrict__ rhs, int sweeps) {
+  pdl_entry();
   __shared__ double red[1024];
   const i64 n = d.nc;
   double s = 0.0;
@@ -1064,6 +1086,7 @@ __global__ void k_p_coarse(Dims d, T* __restrict__ u, T* __restrict__ rhs, int s
 template <typename T>
 __global__ void k_div_q(Dims d, T eta, const T* __restrict__ vt, const T* __restrict__ rpi,
                         T* __restrict__ q, T* __restrict__ pi) {
+  pdl_entry();
   const i64 l = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= d.nc) return;
   int c[3];
@@ -1091,6 +1114,7 @@ __global__ void k_div_q(Dims d, T eta, const T* __restrict__ vt, const T* __rest
 // v += G phi
 template <typename T>
 __global__ void k_add_grad(Dims d, const T* __restrict__ phi, T* __restrict__ v) {
+  pdl_entry();
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.fo[3]) return;
   int a, c[3];
@@ -1123,7 +1147,7 @@ void stokes_apply(const Dims& d, T eta, const T* v, const T* p, T* yv, T* yp, cu
     }
   } else {
     const i64 n = d.fo[3] + d.nc;
-    k_stokes_apply<T><<<nblk(n, bs), bs, 0, s>>>(d, eta, v, p, yv, yp);
+    launch_k(k_stokes_apply<T>, nblk(n, bs), bs, 0, s, d, eta, v, p, yv, yp);
   }
   note_launch();
 }
@@ -1133,16 +1157,16 @@ void vel_rbgs(const Dims& d, T eta, int color, T* u, const T* rhs, cudaStream_t 
     // 32 half-row points x bs / 32 rows per block
     const int by = std::max(1, bs / 32);
     dim3 grid((d.n[0] / 2 + 1 + 31) / 32, (d.n[1] + by - 1) / by, 3 * d.n[2]);
-    k_vel_rbgs_u<T><<<grid, dim3(32, by), 0, s>>>(d, (T)(d.h[0] * d.h[0] / (double)eta), color, u, rhs);
+    launch_k(k_vel_rbgs_u<T>, grid, dim3(32, by), 0, s, d, (T)(d.h[0] * d.h[0] / (double)eta), color, u, rhs);
   } else {
     const ColorMap m = make_color_map_faces(d);
-    k_vel_rbgs<T><<<nblk((i64)m.cnt[0] + m.cnt[1] + m.cnt[2], bs), bs, 0, s>>>(d, m, eta, color, u, rhs);
+    launch_k(k_vel_rbgs<T>, nblk((i64)m.cnt[0] + m.cnt[1] + m.cnt[2], bs), bs, 0, s, d, m, eta, color, u, rhs);
   }
   note_launch();
 }
 template <typename T>
 void vel_first(const Dims& d, T eta, T* u, const T* rhs, cudaStream_t s) {
-  k_vel_first<T><<<nblk(d.fo[3], 256), 256, 0, s>>>(d, eta, u, rhs);
+  launch_k(k_vel_first<T>, nblk(d.fo[3], 256), 256, 0, s, d, eta, u, rhs);
   note_launch();
 }
 // First two half sweeps from a zero guess in one launch on uniform spacing;
@@ -1152,7 +1176,7 @@ bool vel_first2(const Dims& d, T eta, T* u, const T* rhs, cudaStream_t s, int bs
   if (!(d.h[0] == d.h[1] && d.h[1] == d.h[2] && d.fo[3] < ((i64)1 << 31))) return false;
   const int by = std::max(1, bs / 32);
   dim3 grid((d.n[0] + 31) / 32, (d.n[1] + by - 1) / by, 3 * d.n[2]);
-  k_vel_first2_u<T><<<grid, dim3(32, by), 0, s>>>(d, (T)(d.h[0] * d.h[0] / (double)eta), u, rhs);
+  launch_k(k_vel_first2_u<T>, grid, dim3(32, by), 0, s, d, (T)(d.h[0] * d.h[0] / (double)eta), u, rhs);
   note_launch();
   return true;
 }
@@ -1161,34 +1185,34 @@ bool p_first2(const Dims& d, T* u, const T* rhs, cudaStream_t s, int bs) {
   if (!(d.h[0] == d.h[1] && d.h[1] == d.h[2] && d.nc < ((i64)1 << 31))) return false;
   const int by = std::max(1, bs / 32);
   dim3 grid((d.n[0] + 31) / 32, (d.n[1] + by - 1) / by, d.n[2]);
-  k_p_first2_u<T><<<grid, dim3(32, by), 0, s>>>(d, (T)(d.h[0] * d.h[0]), u, rhs);
+  launch_k(k_p_first2_u<T>, grid, dim3(32, by), 0, s, d, (T)(d.h[0] * d.h[0]), u, rhs);
   note_launch();
   return true;
 }
 template <typename T>
 void vel_restrict_res(const Dims& df, const Dims& dc, int3 cz, T eta, const T* uf, const T* rhsf, T* rc,
                       cudaStream_t s) {
-  k_vel_restrict_res<T><<<nblk(kRestrictLanes * dc.fo[3], 256), 256, 0, s>>>(df, dc, cz, eta, uf, rhsf, rc);
+  launch_k(k_vel_restrict_res<T>, nblk(kRestrictLanes * dc.fo[3], 256), 256, 0, s, df, dc, cz, eta, uf, rhsf, rc);
   note_launch();
 }
 template <typename T>
 void vel_residual(const Dims& d, T eta, const T* u, const T* rhs, T* res, cudaStream_t s) {
-  k_vel_residual<T><<<nblk(d.fo[3], 256), 256, 0, s>>>(d, eta, u, rhs, res);
+  launch_k(k_vel_residual<T>, nblk(d.fo[3], 256), 256, 0, s, d, eta, u, rhs, res);
   note_launch();
 }
 template <typename T>
 void vel_restrict(const Dims& df, const Dims& dc, int3 cz, const T* rf, T* rc, cudaStream_t s) {
-  k_vel_restrict<T><<<nblk(dc.fo[3], 256), 256, 0, s>>>(df, dc, cz, rf, rc);
+  launch_k(k_vel_restrict<T>, nblk(dc.fo[3], 256), 256, 0, s, df, dc, cz, rf, rc);
   note_launch();
 }
 template <typename T>
 void vel_prolong(const Dims& df, const Dims& dc, int3 cz, const T* uc, T* uf, cudaStream_t s) {
-  k_vel_prolong<T><<<nblk(df.fo[3], 256), 256, 0, s>>>(df, dc, cz, uc, uf);
+  launch_k(k_vel_prolong<T>, nblk(df.fo[3], 256), 256, 0, s, df, dc, cz, uc, uf);
   note_launch();
 }
 template <typename T>
 void vel_coarse(const Dims& d, T eta, T* u, const T* rhs, int sweeps, cudaStream_t s) {
-  k_vel_coarse<T><<<1, 1024, 0, s>>>(d, eta, u, rhs, sweeps);
+  launch_k(k_vel_coarse<T>, 1, 1024, 0, s, d, eta, u, rhs, sweeps);
   note_launch();
 }
 template <typename T>
@@ -1196,51 +1220,51 @@ void p_rbgs(const Dims& d, int color, T* u, const T* rhs, cudaStream_t s, int bs
   if (d.h[0] == d.h[1] && d.h[1] == d.h[2] && d.nc < ((i64)1 << 31)) {
     const int by = std::max(1, bs / 32);
     dim3 grid((d.n[0] / 2 + 1 + 31) / 32, (d.n[1] + by - 1) / by, d.n[2]);
-    k_p_rbgs_u<T><<<grid, dim3(32, by), 0, s>>>(d, (T)(d.h[0] * d.h[0]), color, u, rhs);
+    launch_k(k_p_rbgs_u<T>, grid, dim3(32, by), 0, s, d, (T)(d.h[0] * d.h[0]), color, u, rhs);
   } else {
     const ColorMap m = make_color_map_cells(d);
-    k_p_rbgs<T><<<nblk(m.cnt[0], bs), bs, 0, s>>>(d, m, color, u, rhs);
+    launch_k(k_p_rbgs<T>, nblk(m.cnt[0], bs), bs, 0, s, d, m, color, u, rhs);
   }
   note_launch();
 }
 template <typename T>
 void p_first(const Dims& d, T* u, const T* rhs, cudaStream_t s) {
-  k_p_first<T><<<nblk(d.nc, 256), 256, 0, s>>>(d, u, rhs);
+  launch_k(k_p_first<T>, nblk(d.nc, 256), 256, 0, s, d, u, rhs);
   note_launch();
 }
 template <typename T>
 void p_restrict_res(const Dims& df, const Dims& dc, int3 cz, const T* uf, const T* rhsf, T* rc, cudaStream_t s) {
-  k_p_restrict_res<T><<<nblk(kRestrictLanes * dc.nc, 256), 256, 0, s>>>(df, dc, cz, uf, rhsf, rc);
+  launch_k(k_p_restrict_res<T>, nblk(kRestrictLanes * dc.nc, 256), 256, 0, s, df, dc, cz, uf, rhsf, rc);
   note_launch();
 }
 template <typename T>
 void p_residual(const Dims& d, const T* u, const T* rhs, T* res, cudaStream_t s) {
-  k_p_residual<T><<<nblk(d.nc, 256), 256, 0, s>>>(d, u, rhs, res);
+  launch_k(k_p_residual<T>, nblk(d.nc, 256), 256, 0, s, d, u, rhs, res);
   note_launch();
 }
 template <typename T>
 void p_restrict(const Dims& df, const Dims& dc, int3 cz, const T* rf, T* rc, cudaStream_t s) {
-  k_p_restrict<T><<<nblk(dc.nc, 256), 256, 0, s>>>(df, dc, cz, rf, rc);
+  launch_k(k_p_restrict<T>, nblk(dc.nc, 256), 256, 0, s, df, dc, cz, rf, rc);
   note_launch();
 }
 template <typename T>
 void p_prolong(const Dims& df, const Dims& dc, int3 cz, const T* uc, T* uf, cudaStream_t s) {
-  k_p_prolong<T><<<nblk(df.nc, 256), 256, 0, s>>>(df, dc, cz, uc, uf);
+  launch_k(k_p_prolong<T>, nblk(df.nc, 256), 256, 0, s, df, dc, cz, uc, uf);
   note_launch();
 }
 template <typename T>
 void p_coarse(const Dims& d, T* u, T* rhs, int sweeps, cudaStream_t s) {
-  k_p_coarse<T><<<1, 1024, 0, s>>>(d, u, rhs, sweeps);
+  launch_k(k_p_coarse<T>, 1, 1024, 0, s, d, u, rhs, sweeps);
   note_launch();
 }
 template <typename T>
 void div_q(const Dims& d, T eta, const T* vt, const T* rpi, T* q, T* pi, cudaStream_t s) {
-  k_div_q<T><<<nblk(d.nc, 256), 256, 0, s>>>(d, eta, vt, rpi, q, pi);
+  launch_k(k_div_q<T>, nblk(d.nc, 256), 256, 0, s, d, eta, vt, rpi, q, pi);
   note_launch();
 }
 template <typename T>
 void add_grad(const Dims& d, const T* phi, T* v, cudaStream_t s) {
-  k_add_grad<T><<<nblk(d.fo[3], 256), 256, 0, s>>>(d, phi, v);
+  launch_k(k_add_grad<T>, nblk(d.fo[3], 256), 256, 0, s, d, phi, v);
   note_launch();
 }
 

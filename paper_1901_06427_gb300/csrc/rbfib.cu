@@ -20,6 +20,11 @@ using namespace rbfib;
 
 std::atomic<unsigned long long> rbfib::g_launches{0};
 
+bool rbfib::pdl_enabled() {
+  static const bool on = std::getenv("RBFIB_NO_PDL") == nullptr;
+  return on;
+}
+
 namespace {
 
 const double kDeltaDefault = 6.0554544523933395e-06;   // eps^(1/3), eps = 2^-52
