@@ -238,9 +238,11 @@ CLASS_INFO = {
     "axpy": ("k_multi_axpy (norm of the result finished in its last block)", "fp64", 152),
     "coarse": ("k_fd_solve (exact coarse-level solve, one 8-CTA cluster per grid)", "fp32", 16),
 }
-# DRAM bytes per algorithmic byte from the ncu captures summarised under
-# profiles/ (kernel as it stands); traffic is reported for these classes only.
-TRAFFIC_RATIO = {}
+# DRAM bytes (read + write) per algorithmic byte from the ncu captures
+# summarised under profiles/ (kernel as it stands); traffic is reported for
+# these classes only.  dot: k_dot_part<double> on the two-sphere grid, 37-38
+# columns, cold caches (profiles/k_dot_part_fp64_two_sphere_48x48x32.md).
+TRAFFIC_RATIO = {"dot": 1.03}
 
 
 def roofline_for(top, kms, klaunch, kbytes, kflops):

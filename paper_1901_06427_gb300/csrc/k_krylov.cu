@@ -248,7 +248,7 @@ void multi_axpy(T* w, const T* V, i64 ldv, int ncols, const double* coef, double
 // (a zero divisor gives zeros)
 template <typename T>
 __global__ void k_scale(T* __restrict__ out, const T* __restrict__ in, const double* __restrict__ denom, int invert,
-                        i64 n) {
+                        i64 n, float* __restrict__ out32) {
   pdl_entry();
   // one thread per block forms the factor (FP64 square root and division
   // are long instruction sequences)
@@ -259,8 +259,11 @@ __global__ void k_scale(T* __restrict__ out, const T* __restrict__ in, const dou
   }
   __syncthreads();
   const double f = fs;
-  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
-    out[i] = (T)((double)in[i] * f);
+  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+    const T v = (T)((double)in[i] * f);
+    out[i] = v;
+    if (out32) out32[i] = (float)v;
+  }
 }
 
 // Occupies the stream for a fixed number of SM clock cycles (one thread;
@@ -285,9 +288,9 @@ void gpu_empty(cudaStream_t s) {
 }
 
 template <typename T>
-void scale_by(T* out, const T* in, const double* denom, int invert, i64 n, cudaStream_t s) {
+void scale_by(T* out, const T* in, const double* denom, int invert, i64 n, cudaStream_t s, float* out32) {
   const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);
-  launch_k(k_scale<T>, nb, 256, 0, s, out, in, denom, invert, n);
+  launch_k(k_scale<T>, nb, 256, 0, s, out, in, denom, invert, n, out32);
   note_launch();
 }
 
@@ -442,7 +445,7 @@ void wall_rhs(const Dims& d, const Walls& wl, double eta, T* bv, cudaStream_t s)
   template void multi_dot<T>(const T*, const T*, i64, int, i64, i64, double, double*, int, double*, cudaStream_t); \
   template void multi_axpy<T>(T*, const T*, i64, int, const double*, double, i64, i64, double, double*, int,    \
                               double*, cudaStream_t);                                                            \
-  template void scale_by<T>(T*, const T*, const double*, int, i64, cudaStream_t);                               \
+  template void scale_by<T>(T*, const T*, const double*, int, i64, cudaStream_t, float*);                       \
   template void axpby<T>(T*, const T*, double, double, i64, cudaStream_t);                                      \
   template void wall_rhs<T>(const Dims&, const Walls&, double, T*, cudaStream_t);
 INST(double)
@@ -462,7 +465,7 @@ namespace rbfib {
 
 template <typename T>
 __global__ void k_fg_start(T* __restrict__ V0, const T* __restrict__ w, i64 n, double* __restrict__ gvec, int m,
-                           int* __restrict__ ist, const double* __restrict__ dpar) {
+                           int* __restrict__ ist, const double* __restrict__ dpar, float* __restrict__ V0_32) {
   pdl_entry();
   __shared__ double bs, fs;   // one thread per block forms beta and 1 / beta
   if (threadIdx.x == 0) {
@@ -471,8 +474,11 @@ __global__ void k_fg_start(T* __restrict__ V0, const T* __restrict__ w, i64 n, d
   }
   __syncthreads();
   const double beta = bs, f = fs;
-  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
-    V0[i] = (T)((double)w[i] * f);
+  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+    const T v = (T)((double)w[i] * f);
+    V0[i] = v;
+    if (V0_32) V0_32[i] = (float)v;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     gvec[0] = beta;
     for (int i = 1; i <= m; ++i) gvec[i] = 0.0;
@@ -482,9 +488,10 @@ __global__ void k_fg_start(T* __restrict__ V0, const T* __restrict__ w, i64 n, d
 }
 
 template <typename T>
-void fg_start(T* V0, const T* w, i64 n, double* gvec, int m, int* ist, const double* dpar, cudaStream_t s) {
+void fg_start(T* V0, const T* w, i64 n, double* gvec, int m, int* ist, const double* dpar, cudaStream_t s,
+              float* V0_32) {
   const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);
-  launch_k(k_fg_start<T>, nb, 256, 0, s, V0, w, n, gvec, m, ist, dpar);
+  launch_k(k_fg_start<T>, nb, 256, 0, s, V0, w, n, gvec, m, ist, dpar, V0_32);
   note_launch();
 }
 
@@ -499,10 +506,9 @@ void set_condition(cudaGraphConditionalHandle h, const int* ist, cudaStream_t s)
 }
 
 // Givens update of column j (as k_givens) plus the continue decision.
-__global__ void k_givens_flag(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
-                              const double* hcol2, const double* hnext2, double* res_out, int* ist,
-                              const double* dpar) {
-  pdl_entry();
+RBFIB_DEVFN void givens_flag_body(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
+                                  const double* hcol2, const double* hnext2, double* res_out, int* ist,
+                                  const double* dpar) {
   double r;
   const double res = givens_core(H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, r);
   if (threadIdx.x != 0) return;
@@ -512,6 +518,59 @@ __global__ void k_givens_flag(double* H, int ldh, double* cs, double* sn, double
   const bool cont = (res > dpar[0]) && ((double)ist[1] < dpar[1]) && isfinite(res) && (r > 0.0);
   ist[2] = cont ? 1 : 0;
 }
+__global__ void k_givens_flag(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
+                              const double* hcol2, const double* hnext2, double* res_out, int* ist,
+                              const double* dpar) {
+  pdl_entry();
+  givens_flag_body(H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, res_out, ist, dpar);
+}
+
+// The last two steps of a captured Arnoldi iteration in one launch, since
+// neither needs the other: blocks [0, gridDim.x - 1) normalise the new basis
+// vector, v = w / sqrt(nrm2) (and its FP32 copy when out32 is not null);
+// the last block applies the Givens update of column j and sets the continue
+// flag.  The update's FP64 recurrence then runs beside the scaling instead of
+// in a launch of its own.
+template <typename T>
+__global__ void k_scale_givens(T* __restrict__ out, const T* __restrict__ in, i64 n, float* __restrict__ out32,
+                               double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
+                               const double* hcol2, const double* nrm2, double* res_out, int* ist,
+                               const double* dpar) {
+  pdl_entry();
+  if (blockIdx.x == gridDim.x - 1) {
+    givens_flag_body(H, ldh, cs, sn, g, j, hcol, hcol2, nrm2, res_out, ist, dpar);
+    return;
+  }
+  __shared__ double fs;
+  if (threadIdx.x == 0) {
+    const double dv = sqrt(fmax(nrm2[0], 0.0));
+    fs = dv != 0.0 ? 1.0 / dv : 0.0;
+  }
+  __syncthreads();
+  const double f = fs;
+  const i64 stride = (i64)(gridDim.x - 1) * blockDim.x;
+  for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const T v = (T)((double)in[i] * f);
+    out[i] = v;
+    if (out32) out32[i] = (float)v;
+  }
+}
+
+template <typename T>
+void scale_givens(T* out, const T* in, i64 n, float* out32, double* H, int ldh, double* cs, double* sn, double* g,
+                  int j, const double* hcol, const double* hcol2, const double* nrm2, double* res_out, int* ist,
+                  const double* dpar, cudaStream_t s) {
+  const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);
+  launch_k(k_scale_givens<T>, nb + 1, 256, 0, s, out, in, n, out32, H, ldh, cs, sn, g, j, hcol, hcol2, nrm2,
+           res_out, ist, dpar);
+  note_launch();
+}
+template void scale_givens<double>(double*, const double*, i64, float*, double*, int, double*, double*, double*,
+                                   int, const double*, const double*, const double*, double*, int*, const double*,
+                                   cudaStream_t);
+template void scale_givens<float>(float*, const float*, i64, float*, double*, int, double*, double*, double*, int,
+                                  const double*, const double*, const double*, double*, int*, const double*,
+                                  cudaStream_t);
 
 void givens_flag(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                  const double* hcol2, const double* hnext2, double* res_out, int* ist, const double* dpar,
@@ -570,8 +629,9 @@ void multi_axpy_dev(T* w, const T* V, i64 ldv, const int* ist, const double* coe
   note_launch();
 }
 
-template void fg_start<double>(double*, const double*, i64, double*, int, int*, const double*, cudaStream_t);
-template void fg_start<float>(float*, const float*, i64, double*, int, int*, const double*, cudaStream_t);
+template void fg_start<double>(double*, const double*, i64, double*, int, int*, const double*, cudaStream_t,
+                               float*);
+template void fg_start<float>(float*, const float*, i64, double*, int, int*, const double*, cudaStream_t, float*);
 template void multi_axpy_dev<double>(double*, const double*, i64, const int*, const double*, double, i64, int,
                                      cudaStream_t);
 template void multi_axpy_dev<float>(float*, const float*, i64, const int*, const double*, double, i64, int,

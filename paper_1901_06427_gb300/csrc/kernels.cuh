@@ -168,7 +168,10 @@ template <typename T> void multi_axpy(T* w, const T* V, i64 ldv, int ncols, cons
                                       cudaStream_t);
 void gpu_delay(long long cycles, cudaStream_t);
 void gpu_empty(cudaStream_t);
-template <typename T> void scale_by(T* out, const T* in, const double* denom, int invert, i64 n, cudaStream_t);
+// out = in * f with f = denom (invert 0), 1 / denom (1) or 1 / sqrt(denom) (2);
+// out32, if not null, receives the same values rounded to FP32.
+template <typename T> void scale_by(T* out, const T* in, const double* denom, int invert, i64 n, cudaStream_t,
+                                    float* out32 = nullptr);
 void givens_step(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                  const double* hcol2, const double* hnext2, double* res_out, cudaStream_t);
 void tri_solve(const double* H, int ldh, const double* g, int k, double* y, cudaStream_t);
@@ -179,8 +182,12 @@ void project_mean(double* x, i64 n, double* part, int nparts, cudaStream_t);
 
 // FGMRES restart cycle as a graph (k_krylov.cu)
 template <typename T> void fg_start(T* V0, const T* w, i64 n, double* gvec, int m, int* ist, const double* dpar,
-                                    cudaStream_t);
+                                    cudaStream_t, float* V0_32 = nullptr);
 void set_condition(cudaGraphConditionalHandle h, const int* ist, cudaStream_t);
+template <typename T>
+void scale_givens(T* out, const T* in, i64 n, float* out32, double* H, int ldh, double* cs, double* sn, double* g,
+                  int j, const double* hcol, const double* hcol2, const double* nrm2, double* res_out, int* ist,
+                  const double* dpar, cudaStream_t s);
 void givens_flag(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                  const double* hcol2, const double* hnext2, double* res_out, int* ist, const double* dpar,
                  cudaStream_t);

@@ -447,13 +447,21 @@ void precond(rbfib_grid* g, const T* r, T* z, bool with_bodies) {
 // (FGMRES is flexible), and FP32 halves the bytes of every multigrid sweep and
 // avoids GB300's narrow FP64 pipe.  FP64 vectors are converted on the way in
 // and out.
-void precond_any(rbfib_grid* g, const double* r, double* z, bool with_bodies) {
+// The FP32 preconditioner applied to an FP64 vector.  r32_ready: the Krylov
+// basis kernels already wrote r rounded to FP32 into f32a (normalising a new
+// basis vector writes both copies, which saves a conversion launch).
+void precond_any(rbfib_grid* g, const double* r, double* z, bool with_bodies, bool r32_ready = false) {
   const i64 n = with_bodies ? g->n_total() : g->nfl;
-  convert<double, float>(r, g->f32a, n, g->s);
+  if (!r32_ready) convert<double, float>(r, g->f32a, n, g->s);
   precond<float>(g, g->f32a, g->f32b, with_bodies);
   convert<float, double>(g->f32b, z, n, g->s);
 }
-void precond_any(rbfib_grid* g, const float* r, float* z, bool with_bodies) { precond<float>(g, r, z, with_bodies); }
+void precond_any(rbfib_grid* g, const float* r, float* z, bool with_bodies, bool = false) {
+  precond<float>(g, r, z, with_bodies);
+}
+// Where the basis kernels put the FP32 copy of a new FP64 basis vector (the
+// FP32 Krylov mode keeps f32a for the right-hand side of its inner solve).
+template <typename T> float* basis32(rbfib_grid* g) { return sizeof(T) == 8 ? g->f32a.p : nullptr; }
 
 // y = A x (saddle operator; fluid-only when with_bodies is false)
 template <typename T>
@@ -512,12 +520,12 @@ int fgmres(rbfib_grid* g, const T* b, T* x, bool with_bodies, double rtol, int m
     ck(cudaMemsetAsync(sp.gv, 0, sizeof(double) * (m + 1), g->s));
     g->h_pinned[1] = beta;
     ck(cudaMemcpyAsync(sp.gv, g->h_pinned + 1, sizeof(double), cudaMemcpyHostToDevice, g->s));
-    scale_by<T>(V, w, sp.gv, 1, n, g->s);
+    scale_by<T>(V, w, sp.gv, 1, n, g->s, basis32<T>(g));
     int k = 0;
     for (int j = 0; j < m; ++j) {
       T* vj = V + (i64)j * ld;
       T* zj = Z + (i64)j * ld;
-      precond_any(g, vj, zj, with_bodies);
+      precond_any(g, vj, zj, with_bodies, true);
       apply_A<T>(g, zj, w, with_bodies);
       const double bd = (double)(j + 2) * n * sizeof(T), ba = (double)(j + 3) * n * sizeof(T);
       const double fd = 2.0 * (j + 1) * n, fa = 2.0 * (j + 2) * n;
@@ -526,7 +534,7 @@ int fgmres(rbfib_grid* g, const T* b, T* x, bool with_bodies, double rtol, int m
       { TimerScope ts(g, TK_DOT, bd, fd); multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol2, g->s); }
       { TimerScope ts(g, TK_AXPY, ba, fa); multi_axpy<T>(w, V, ld, j + 1, sp.hcol2, -1.0, n, nfl, wf, g->part, g->nparts, sp.nrm2, g->s); }
       givens_step(sp.H, m + 1, sp.cs, sp.sn, sp.gv, j, sp.hcol, sp.hcol2, sp.nrm2, sp.res, g->s);
-      scale_by<T>(V + (i64)(j + 1) * ld, w, sp.nrm2, 2, n, g->s);
+      scale_by<T>(V + (i64)(j + 1) * ld, w, sp.nrm2, 2, n, g->s, basis32<T>(g));
       ++iters;
       k = j + 1;
       const double res = read_scalar(g, sp.res);
@@ -563,14 +571,14 @@ void capture_iteration(rbfib_grid* g, int j, const T* /*b*/, bool wb) {
   T* V = K.V;
   T* Z = K.Z;
   T* w = K.w;
-  precond_any(g, V + (i64)j * ld, Z + (i64)j * ld, wb);
+  precond_any(g, V + (i64)j * ld, Z + (i64)j * ld, wb, true);
   apply_A<T>(g, Z + (i64)j * ld, w, wb);
   multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol, g->s);
   multi_axpy<T>(w, V, ld, j + 1, sp.hcol, -1.0, n, nfl, wf, g->part, g->nparts, nullptr, g->s);
   multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol2, g->s);
   multi_axpy<T>(w, V, ld, j + 1, sp.hcol2, -1.0, n, nfl, wf, g->part, g->nparts, sp.nrm2, g->s);
-  scale_by<T>(V + (i64)(j + 1) * ld, w, sp.nrm2, 2, n, g->s);
-  givens_flag(sp.H, m + 1, sp.cs, sp.sn, sp.gv, j, sp.hcol, sp.hcol2, sp.nrm2, sp.res, g->gst, g->dpar, g->s);
+  scale_givens<T>(V + (i64)(j + 1) * ld, w, n, basis32<T>(g), sp.H, m + 1, sp.cs, sp.sn, sp.gv, j, sp.hcol,
+                  sp.hcol2, sp.nrm2, sp.res, g->gst, g->dpar, g->s);
 }
 
 template <typename T>
@@ -592,7 +600,7 @@ bool build_cycle_graph(rbfib_grid* g, const T* b, T* x, bool wb, rbfib_grid::Cyc
   g->s = sc;
   try {
     ck(cudaStreamBeginCapture(sc, cudaStreamCaptureModeRelaxed));
-    fg_start<T>(K.V, K.w, n, sp.gv, m, g->gst, g->dpar, sc);
+    fg_start<T>(K.V, K.w, n, sp.gv, m, g->gst, g->dpar, sc, basis32<T>(g));
     for (int j = 0; j < m; ++j) {
       cudaStreamCaptureStatus cst;
       cudaGraph_t capg = nullptr;
