@@ -446,10 +446,9 @@ void precond(rbfib_grid* g, const T* r, T* z, bool with_bodies) {
 // The preconditioner always runs in FP32: it only has to approximate A^{-1}
 // (FGMRES is flexible), and FP32 halves the bytes of every multigrid sweep and
 // avoids GB300's narrow FP64 pipe.  FP64 vectors are converted on the way in
-// and out.
-// The FP32 preconditioner applied to an FP64 vector.  r32_ready: the Krylov
-// basis kernels already wrote r rounded to FP32 into f32a (normalising a new
-// basis vector writes both copies, which saves a conversion launch).
+// and out.  r32_ready: the Krylov basis kernels already wrote r rounded to
+// FP32 into f32a (normalising a new basis vector writes both copies, which
+// saves a conversion launch).
 void precond_any(rbfib_grid* g, const double* r, double* z, bool with_bodies, bool r32_ready = false) {
   const i64 n = with_bodies ? g->n_total() : g->nfl;
   if (!r32_ready) convert<double, float>(r, g->f32a, n, g->s);
