@@ -2,14 +2,9 @@
 // the Schur complement [-M K; K^T 0] of the saddle operator with the blob
 // mobility M replaced by the free-space Rotne-Prager-Yamakawa mobility of all
 // blobs of all bodies (inter-body coupling included).  Built once per
-// configuration: dense RPY matrix; its inverse (FP32) by in-place
-// Gauss-Jordan (no pivoting: the RPY matrix is symmetric positive definite)
-// or, when the previous configuration's inverse is close, by two
-// Newton-Schulz steps from it; P = M^-1 K; N = (K^T M^-1 K)^-1 (FP64).
-// Applied by one cluster of CTAs.
-#include <algorithm>
-#include <cmath>
-
+// configuration: dense RPY matrix, in-place Gauss-Jordan inverse (FP32, no
+// pivoting: the RPY matrix is symmetric positive definite), P = M^-1 K,
+// N = (K^T M^-1 K)^-1 (FP64).  Applied by one CTA.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -135,127 +130,22 @@ __global__ void k_ktp(int nbl, int nb, const int* __restrict__ boff, const doubl
   A[t] = acc;
 }
 
-// Square FP32 products for the Newton-Schulz update of the inverse
-// (n x n, row-major): MODE 0 forms C = I - A B and adds sum(C_ij^2) to
-// *ss; MODE 1 forms C = D + A B.  32 x 32 output tiles, 256 threads (four
-// outputs each), A and B staged through shared memory in 32-wide k-slices;
-// entries past n are zero-filled.  n <= 1536: these products take
-// microseconds, so they stay on the FP32 pipe.
-constexpr int kNSTile = 32;
-template <int MODE>
-__global__ void __launch_bounds__(256) k_ns_gemm(int n, const float* __restrict__ A, const float* __restrict__ B,
-                                                 const float* __restrict__ D, float* __restrict__ C,
-                                                 double* __restrict__ ss) {
-  pdl_entry();
-  __shared__ float As[kNSTile][kNSTile + 1], Bs[kNSTile][kNSTile + 1];
-  __shared__ double red[8];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int r0 = blockIdx.y * kNSTile, c0 = blockIdx.x * kNSTile;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int k0 = 0; k0 < n; k0 += kNSTile) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int rr = ty + 8 * q;
-      const int ar = r0 + rr, ac = k0 + tx, br = k0 + rr, bc = c0 + tx;
-      As[rr][tx] = (ar < n && ac < n) ? A[(i64)ar * n + ac] : 0.f;
-      Bs[rr][tx] = (br < n && bc < n) ? B[(i64)br * n + bc] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < kNSTile; ++kk) {
-      const float b = Bs[kk][tx];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fmaf(As[ty + 8 * q][kk], b, acc[q]);
-    }
-    __syncthreads();
-  }
-  double sq = 0.0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int row = r0 + ty + 8 * q, col = c0 + tx;
-    if (row >= n || col >= n) continue;
-    const i64 o = (i64)row * n + col;
-    float v;
-    if (MODE == 0) {
-      v = (row == col ? 1.f : 0.f) - acc[q];
-      sq += (double)v * (double)v;
-    } else {
-      v = D[o] + acc[q];
-    }
-    C[o] = v;
-  }
-  if (MODE == 0) {
-    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-    if (tx == 0) red[ty] = sq;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < 8; ++w) t += red[w];
-      atomicAdd(ss, t);
-    }
-  }
-}
-
-template <int MODE>
-void ns_gemm(int n, const float* A, const float* B, const float* D, float* C, double* ss, cudaStream_t s) {
-  const unsigned nt = (unsigned)((n + kNSTile - 1) / kNSTile);
-  launch_k(k_ns_gemm<MODE>, dim3(nt, nt), 256, 0, s, n, A, B, D, C, ss);
-  note_launch();
-}
-
-// Build the coupled body block for a new configuration: M^-1, P = M^-1 K and
-// N = (K^T M^-1 K)^-1.
-//  - warm: Minv holds the inverse of the previous configuration's M.  The
-//    configuration moves little between SEM steps, so that inverse is a
-//    close start for the Newton-Schulz iteration X <- X + X (I - M X), which
-//    converges quadratically while ||I - M X|| < 1.  With the residual
-//    R0 = I - M X0 at most kNSMaxStart in Frobenius norm, two iterations
-//    leave a residual of at most kNSMaxStart^4 (about 4e-3), below what the
-//    preconditioner needs; each iteration is two n x n products on the whole
-//    GPU, against n sequential pivot steps on one SM for Gauss-Jordan.
-//  - otherwise, or when R0 is larger (a first configuration, a large move):
-//    in-place Gauss-Jordan.
-// Mw, Tw, Uw: n3 x n3 FP32 work matrices; ss: one device double; ss_host:
-// pinned host double (the choice needs one read of ||R0||).  Returns true
-// when the warm start was taken.
-constexpr double kNSMaxStart = 0.25;
-bool dense_body_build(int nbl, int nb, const int* boff, const double* r, const double* arm, double a, double eta,
-                      float* Minv, float* P, double* N, int* status, float* Mw, float* Tw, float* Uw, double* ss,
-                      double* ss_host, bool warm, cudaStream_t s) {
+// Build: M (float n3^2) -> M^-1, P, N (double (6nb)^2).  scratch: P (n3 x 6nb
+// floats), status word.
+void dense_body_build(int nbl, int nb, const int* boff, const double* r, const double* arm, double a, double eta,
+                      float* Minv, float* P, double* N, int* status, cudaStream_t s) {
   const i64 n3 = 3 * (i64)nbl, m = 6 * (i64)nb;
   cudaMemsetAsync(status, 0, sizeof(int), s);
-  bool used = false;
-  if (warm) {
-    launch_k(k_rpy_full, nblk(n3 * n3, 256), 256, 0, s, nbl, r, a, eta, Mw);
-    note_launch();
-    cudaMemsetAsync(ss, 0, sizeof(double), s);
-    ns_gemm<0>((int)n3, Mw, Minv, nullptr, Tw, ss, s);          // R0 = I - M X0
-    cudaMemcpyAsync(ss_host, ss, sizeof(double), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    const double r0 = std::sqrt(std::max(ss_host[0], 0.0));
-    if (r0 <= kNSMaxStart) {
-      ns_gemm<1>((int)n3, Minv, Tw, Minv, Uw, nullptr, s);      // X1 = X0 + X0 R0
-      ns_gemm<0>((int)n3, Mw, Uw, nullptr, Tw, ss, s);          // R1 = I - M X1
-      ns_gemm<1>((int)n3, Uw, Tw, Uw, Minv, nullptr, s);        // X2 = X1 + X1 R1
-      used = true;
-    } else {
-      cudaMemcpyAsync(Minv, Mw, sizeof(float) * n3 * n3, cudaMemcpyDeviceToDevice, s);
-    }
-  } else {
-    launch_k(k_rpy_full, nblk(n3 * n3, 256), 256, 0, s, nbl, r, a, eta, Minv);
-    note_launch();
-  }
-  if (!used) {
-    launch_k(k_gj_inverse<float>, 1, 1024, 2 * sizeof(float) * n3, s, Minv, (int)n3, status);
-    note_launch();
-  }
+  launch_k(k_rpy_full, nblk(n3 * n3, 256), 256, 0, s, nbl, r, a, eta, Minv);
+  note_launch();
+  launch_k(k_gj_inverse<float>, 1, 1024, 2 * sizeof(float) * n3, s, Minv, (int)n3, status);
+  note_launch();
   launch_k(k_mk, nblk(n3 * m, 256), 256, 0, s, nbl, nb, boff, arm, Minv, P);
   note_launch();
   launch_k(k_ktp, nblk(m * m, 256), 256, 0, s, nbl, nb, boff, arm, P, N);
   note_launch();
   launch_k(k_gj_inverse<double>, 1, 1024, 2 * sizeof(double) * m, s, N, (int)m, status);
   note_launch();
-  return used;
 }
 
 // Apply on one cluster of kBodyCtas CTAs: t = M^-1 s; f = r_U + K^T t;
