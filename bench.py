@@ -506,7 +506,8 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
             "krylov_iterations_per_step": [list(map(int, np.mean(np.array(state["iters"]), axis=0)))] if state["iters"] else None,
-            "rejected_steps": state["rejects"], "wall_s": t_wall}
+            "rejected_steps": state["rejects"], "wall_s": t_wall,
+            "body_block_warm_starts": g.body_block_info()[1]}
     if args.sem_only:
         print(json.dumps(line), flush=True)
         return

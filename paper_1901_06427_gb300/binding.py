@@ -97,6 +97,7 @@ def lib():
             "rbfib_kernel_timer": ([P, I32], I32),
             "rbfib_kernel_timer_read": ([P, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)], I32),
             "rbfib_kernel_timer_overhead": ([P, I32, ctypes.POINTER(D)], I32),
+            "rbfib_body_block_info": ([P, ctypes.POINTER(I32), ctypes.POINTER(I64)], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -326,6 +327,12 @@ class Grid:
         self._check(lib().rbfib_kernel_timer_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b),
                                                   ctypes.byref(f)))
         return ms.value, n.value, b.value, f.value
+
+    def body_block_info(self):
+        """(coupled all-blob body block in use, Newton-Schulz warm starts taken)"""
+        dense, warm = ctypes.c_int32(), ctypes.c_int64()
+        self._check(lib().rbfib_body_block_info(self._h, ctypes.byref(dense), ctypes.byref(warm)))
+        return bool(dense.value), int(warm.value)
 
     def kernel_timer_overhead(self, reps=200):
         """Median event-bracket time (us) of an empty kernel timed the way the

@@ -229,6 +229,14 @@ __device__ inline void philox_normals4(unsigned long long seed, unsigned long lo
 
 #define RBFIB_DEVFN __device__ __forceinline__
 
+// Rotation matrix (row-major) of a unit quaternion (w, x, y, z).
+RBFIB_DEVFN void quat_rot(const double* qt, double R[9]) {
+  const double w = qt[0], x = qt[1], y = qt[2], z = qt[3];
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+}
+
 // Programmatic dependent launch.  Every kernel of the library begins with
 // pdl_entry(), before it touches global memory: griddepcontrol.wait returns
 // once the kernels this grid depends on have completed and their memory

@@ -2,9 +2,14 @@
 // the Schur complement [-M K; K^T 0] of the saddle operator with the blob
 // mobility M replaced by the free-space Rotne-Prager-Yamakawa mobility of all
 // blobs of all bodies (inter-body coupling included).  Built once per
-// configuration: dense RPY matrix, in-place Gauss-Jordan inverse (FP32, no
-// pivoting: the RPY matrix is symmetric positive definite), P = M^-1 K,
-// N = (K^T M^-1 K)^-1 (FP64).  Applied by one CTA.
+// configuration: dense RPY matrix; its inverse (FP32) by in-place
+// Gauss-Jordan (no pivoting: the RPY matrix is symmetric positive definite)
+// or, when the previous configuration's inverse is close, by two
+// Newton-Schulz steps from it; P = M^-1 K; N = (K^T M^-1 K)^-1 (FP64).
+// Applied by one cluster of CTAs.
+#include <algorithm>
+#include <cmath>
+
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -130,22 +135,178 @@ __global__ void k_ktp(int nbl, int nb, const int* __restrict__ boff, const doubl
   A[t] = acc;
 }
 
-// Build: M (float n3^2) -> M^-1, P, N (double (6nb)^2).  scratch: P (n3 x 6nb
-// floats), status word.
-void dense_body_build(int nbl, int nb, const int* boff, const double* r, const double* arm, double a, double eta,
-                      float* Minv, float* P, double* N, int* status, cudaStream_t s) {
+// Square FP32 products for the Newton-Schulz update of the inverse
+// (n x n, row-major): MODE 0 forms C = I - A B and adds sum(C_ij^2) to
+// *ss; MODE 1 forms C = D + A B.  32 x 32 output tiles, 256 threads (four
+// outputs each), A and B staged through shared memory in 32-wide k-slices;
+// entries past n are zero-filled.  n <= 1536: these products take
+// microseconds, so they stay on the FP32 pipe.
+constexpr int kNSTile = 32;
+template <int MODE>
+__global__ void __launch_bounds__(256) k_ns_gemm(int n, const float* __restrict__ A, const float* __restrict__ B,
+                                                 const float* __restrict__ D, float* __restrict__ C,
+                                                 double* __restrict__ ss) {
+  pdl_entry();
+  __shared__ float As[kNSTile][kNSTile + 1], Bs[kNSTile][kNSTile + 1];
+  __shared__ double red[8];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int r0 = blockIdx.y * kNSTile, c0 = blockIdx.x * kNSTile;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k0 = 0; k0 < n; k0 += kNSTile) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int rr = ty + 8 * q;
+      const int ar = r0 + rr, ac = k0 + tx, br = k0 + rr, bc = c0 + tx;
+      As[rr][tx] = (ar < n && ac < n) ? A[(i64)ar * n + ac] : 0.f;
+      Bs[rr][tx] = (br < n && bc < n) ? B[(i64)br * n + bc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kNSTile; ++kk) {
+      const float b = Bs[kk][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(As[ty + 8 * q][kk], b, acc[q]);
+    }
+    __syncthreads();
+  }
+  double sq = 0.0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int row = r0 + ty + 8 * q, col = c0 + tx;
+    if (row >= n || col >= n) continue;
+    const i64 o = (i64)row * n + col;
+    float v;
+    if (MODE == 0) {
+      v = (row == col ? 1.f : 0.f) - acc[q];
+      sq += (double)v * (double)v;
+    } else {
+      v = D[o] + acc[q];
+    }
+    C[o] = v;
+  }
+  if (MODE == 0) {
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (tx == 0) red[ty] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      atomicAdd(ss, t);
+    }
+  }
+}
+
+template <int MODE>
+void ns_gemm(int n, const float* A, const float* B, const float* D, float* C, double* ss, cudaStream_t s) {
+  const unsigned nt = (unsigned)((n + kNSTile - 1) / kNSTile);
+  launch_k(k_ns_gemm<MODE>, dim3(nt, nt), 256, 0, s, n, A, B, D, C, ss);
+  note_launch();
+}
+
+// Rotates the previous configuration's inverse with each body's rotation
+// since then: X_ij <- D_b(i) X_ij D_b(j)^T for the 3 x 3 blocks (blobs i, j
+// of bodies b(i), b(j)), D_p = R(quat_new_p) R(quat_old_p)^T.  The RPY matrix
+// of a blob set rotated rigidly about each body's centre has exactly these
+// intra-body blocks (the RPY tensor is rotation-covariant), so only the
+// inter-body blocks of the start are off.  One thread per block, in place.
+__global__ void k_rotate_inverse(int nbl, const int* __restrict__ bob, const double* __restrict__ qnew,
+                                 const double* __restrict__ qold, float* __restrict__ X) {
+  pdl_entry();
+  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (i64)nbl * nbl) return;
+  const int i = (int)(t / nbl), j = (int)(t - (i64)i * nbl);
+  double D[2][9];
+  const int body[2] = {bob[i], bob[j]};
+  for (int s = 0; s < 2; ++s) {
+    double Rn[9], Ro[9];
+    quat_rot(qnew + 4 * body[s], Rn);
+    quat_rot(qold + 4 * body[s], Ro);
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        D[s][3 * a + b] = Rn[3 * a] * Ro[3 * b] + Rn[3 * a + 1] * Ro[3 * b + 1] + Rn[3 * a + 2] * Ro[3 * b + 2];
+  }
+  const i64 n3 = 3 * (i64)nbl;
+  float* Xb = X + (3 * (i64)i) * n3 + 3 * (i64)j;
+  double x[9], y[9];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) x[3 * a + b] = (double)Xb[a * n3 + b];
+  // y = D_i x D_j^T
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double acc = 0.0;
+      for (int c = 0; c < 3; ++c)
+        for (int e = 0; e < 3; ++e) acc += D[0][3 * a + c] * x[3 * c + e] * D[1][3 * b + e];
+      y[3 * a + b] = acc;
+    }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Xb[a * n3 + b] = (float)y[3 * a + b];
+}
+
+// Build the coupled body block for a new configuration: M^-1, P = M^-1 K and
+// N = (K^T M^-1 K)^-1.
+//  - warm: Minv holds the inverse of the previous configuration's M, built
+//    at the body orientations qold (NULL: unknown).  The start X0 is that
+//    inverse rotated with each body's rotation since (k_rotate_inverse).
+//    The configuration moves little between SEM steps, so X0 is a close
+//    start for the Newton-Schulz iteration X <- X + X (I - M X), which
+//    converges quadratically while ||I - M X|| < 1.  With ||R0||_F =
+//    ||I - M X0||_F at most kNSMaxStart, four iterations leave a residual of
+//    at most kNSMaxStart^16 (FP32 roundoff in practice); each iteration is two
+//    n x n products on the whole GPU, against n sequential pivot steps on one
+//    SM for Gauss-Jordan.
+//  - otherwise, or when R0 is larger (a first configuration, a large move):
+//    in-place Gauss-Jordan.
+// Mw, Tw, Uw: n3 x n3 FP32 work matrices; ss: one device double; ss_host:
+// pinned host double (the choice needs one read of ||R0||).  Returns true
+// when the warm start was taken.
+constexpr double kNSMaxStart = 0.5;
+constexpr int kNSIters = 4;   // even: the result lands in Minv
+bool dense_body_build(int nbl, int nb, const int* boff, const int* bob, const double* r, const double* arm,
+                      const double* qnew, const double* qold, double a, double eta, float* Minv, float* P,
+                      double* N, int* status, float* Mw, float* Tw, float* Uw, double* ss, double* ss_host,
+                      bool warm, cudaStream_t s) {
   const i64 n3 = 3 * (i64)nbl, m = 6 * (i64)nb;
   cudaMemsetAsync(status, 0, sizeof(int), s);
-  launch_k(k_rpy_full, nblk(n3 * n3, 256), 256, 0, s, nbl, r, a, eta, Minv);
-  note_launch();
-  launch_k(k_gj_inverse<float>, 1, 1024, 2 * sizeof(float) * n3, s, Minv, (int)n3, status);
-  note_launch();
+  bool used = false;
+  if (warm) {
+    launch_k(k_rpy_full, nblk(n3 * n3, 256), 256, 0, s, nbl, r, a, eta, Mw);
+    note_launch();
+    if (qnew && qold) {
+      launch_k(k_rotate_inverse, nblk((i64)nbl * nbl, 128), 128, 0, s, nbl, bob, qnew, qold, Minv);
+      note_launch();
+    }
+    cudaMemsetAsync(ss, 0, sizeof(double), s);
+    ns_gemm<0>((int)n3, Mw, Minv, nullptr, Tw, ss, s);          // R0 = I - M X0
+    cudaMemcpyAsync(ss_host, ss, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    const double r0 = std::sqrt(std::max(ss_host[0], 0.0));
+    if (r0 <= kNSMaxStart) {
+      float* X = Minv;
+      float* Y = Uw;
+      for (int it = 0; it < kNSIters; ++it) {
+        if (it > 0) ns_gemm<0>((int)n3, Mw, X, nullptr, Tw, ss, s);   // R = I - M X
+        ns_gemm<1>((int)n3, X, Tw, X, Y, nullptr, s);                 // X' = X + X R
+        float* t = X; X = Y; Y = t;
+      }
+      used = true;
+    } else {
+      cudaMemcpyAsync(Minv, Mw, sizeof(float) * n3 * n3, cudaMemcpyDeviceToDevice, s);
+    }
+  } else {
+    launch_k(k_rpy_full, nblk(n3 * n3, 256), 256, 0, s, nbl, r, a, eta, Minv);
+    note_launch();
+  }
+  if (!used) {
+    launch_k(k_gj_inverse<float>, 1, 1024, 2 * sizeof(float) * n3, s, Minv, (int)n3, status);
+    note_launch();
+  }
   launch_k(k_mk, nblk(n3 * m, 256), 256, 0, s, nbl, nb, boff, arm, Minv, P);
   note_launch();
   launch_k(k_ktp, nblk(m * m, 256), 256, 0, s, nbl, nb, boff, arm, P, N);
   note_launch();
   launch_k(k_gj_inverse<double>, 1, 1024, 2 * sizeof(double) * m, s, N, (int)m, status);
   note_launch();
+  return used;
 }
 
 // Apply on one cluster of kBodyCtas CTAs: t = M^-1 s; f = r_U + K^T t;

@@ -10,12 +10,6 @@ namespace rbfib {
 static inline unsigned nblk(i64 n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 // ------------------------------------------------------------- geometry
-RBFIB_DEVFN void quat_rot(const double* qt, double R[9]) {
-  const double w = qt[0], x = qt[1], y = qt[2], z = qt[3];
-  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
-  R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
-  R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
-}
 
 __global__ void k_geometry(int nbl, const int* __restrict__ bob, const double* __restrict__ ref,
                            const double* __restrict__ q, const double* __restrict__ quat,

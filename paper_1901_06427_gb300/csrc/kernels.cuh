@@ -141,8 +141,10 @@ void adjoint_positions(const Dims&, int nbl, const int* bob, const double* r, co
                        cudaStream_t);
 
 // k_body.cu
-void dense_body_build(int nbl, int nb, const int* boff, const double* r, const double* arm, double a, double eta,
-                      float* Minv, float* P, double* N, int* status, cudaStream_t);
+bool dense_body_build(int nbl, int nb, const int* boff, const int* bob, const double* r, const double* arm,
+                      const double* qnew, const double* qold, double a, double eta, float* Minv, float* P,
+                      double* N, int* status, float* Mw, float* Tw, float* Uw, double* ss, double* ss_host,
+                      bool warm, cudaStream_t);
 template <typename T> void dense_body_apply(int nbl, int nb, const int* boff, const int* bob, const double* arm,
                                             const float* Minv, const float* P, const double* N, const T* sres,
                                             const T* rU, T* zlam, T* zU, cudaStream_t);

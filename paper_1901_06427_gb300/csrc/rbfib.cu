@@ -152,6 +152,13 @@ struct rbfib_grid {
   DBuf<float> dM, dP;
   DBuf<double> dN;
   DBuf<int> dstatus;
+  // Newton-Schulz update of dM from the previous configuration's inverse:
+  // work matrices, the residual norm, whether dM holds a valid inverse, and
+  // how many builds took the warm start
+  DBuf<float> dMw, dTw, dUw;
+  DBuf<double> dss, dquat;   // dquat: body orientations dM was built at
+  bool dM_valid = false, dquat_valid = false;
+  long long ns_warm = 0;
   // work vectors (FP64)
   DBuf<double> part, scal, bvec, xvec, xrfd, rres, sres, fsharp, vsharp, fnoise, Wst;
   DBuf<double> bodyA, bodyB, bodyF, bodyW, bodyWn, blobA, blobB, blobC, blobD, blobS;
@@ -849,14 +856,27 @@ bool inverse6(double A[36]) {
   return true;
 }
 
+// Coupled body block for the blob positions r (arms arm) of bodies with
+// orientations quat (NULL: not known, as after rbfib_set_blob_positions):
+// warm-started from the current inverse when there is one
+// (dense_body_build).
+void build_body_block(rbfib_grid* g, const double* r, const double* arm, const double* quat) {
+  const double* qold = (quat && g->dquat_valid) ? g->dquat.p : nullptr;
+  const bool used = dense_body_build(g->nbl, g->nb, g->boff, g->bob, r, arm, quat, qold, kBlobRadius * g->desc.h,
+                                     g->desc.eta, g->dM, g->dP, g->dN, g->dstatus, g->dMw, g->dTw, g->dUw, g->dss,
+                                     g->h_pinned + 40, g->dM_valid, g->s);
+  g->dM_valid = true;
+  g->dquat_valid = quat != nullptr;
+  if (quat) ck(cudaMemcpyAsync(g->dquat.p, quat, sizeof(double) * 4 * g->nb, cudaMemcpyDeviceToDevice, g->s));
+  if (used) ++g->ns_warm;
+}
+
 void refresh_config(rbfib_grid* g, Config& c, bool bin) {
   geometry(g->nbl, g->bob, g->ref, c.q, c.quat, c.r, c.arm, g->s);
   if (bin) {
     binning(g->d, g->nbl, c.r, c.perm, g->celloff, g->bkey, g->bcount, g->bfill, g->bbsum, g->s);
     stencil_build(g->d, g->nbl, c.r, c.st64, c.st32, g->s);
-    if (g->dense_body)
-      dense_body_build(g->nbl, g->nb, g->boff, c.r, c.arm, kBlobRadius * g->desc.h, g->desc.eta, g->dM, g->dP,
-                       g->dN, g->dstatus, g->s);
+    if (g->dense_body) build_body_block(g, c.r, c.arm, c.quat);
   }
 }
 
@@ -969,6 +989,13 @@ extern "C" {
 const char* rbfib_last_error(const rbfib_grid* g) { return g ? g->err.c_str() : "null grid"; }
 
 uint64_t rbfib_launch_count(void) { return rbfib::g_launches.load(); }
+
+int rbfib_body_block_info(const rbfib_grid* g, int32_t* dense, int64_t* warm_starts) {
+  if (!g) return RBFIB_EINVAL;
+  if (dense) *dense = g->dense_body ? 1 : 0;
+  if (warm_starts) *warm_starts = g->ns_warm;
+  return RBFIB_OK;
+}
 
 int rbfib_tuned_blocks(const rbfib_grid* g, int32_t out[4]) {
   if (!g || !out) return RBFIB_EINVAL;
@@ -1165,8 +1192,15 @@ int rbfib_set_bodies(rbfib_grid* g, int32_t n_bodies, const int32_t* blob_offset
     g->bkey.alloc(std::max(nbl, 1));
     // coupled body block when every blob pair fits a small dense matrix
     g->dense_body = nb >= 2 && 3 * nbl <= kDenseBodyMaxRows && 6 * nb <= kDenseBodyMaxBodyRows;
+    g->dM_valid = false;
+    g->dquat_valid = false;
     if (g->dense_body) {
       g->dM.alloc((size_t)9 * nbl * nbl);
+      g->dMw.alloc((size_t)9 * nbl * nbl);
+      g->dTw.alloc((size_t)9 * nbl * nbl);
+      g->dUw.alloc((size_t)9 * nbl * nbl);
+      g->dss.alloc(1);
+      g->dquat.alloc(4 * (size_t)nb);
       g->dP.alloc((size_t)18 * nbl * nb);
       g->dN.alloc((size_t)36 * nb * nb);
       g->dstatus.alloc(1);
@@ -1529,9 +1563,7 @@ int rbfib_set_blob_positions(rbfib_grid* g, const double* r) {
     arms_from_positions(g->nbl, g->bob, g->cur.r, g->cur.q, g->cur.arm, g->s);
     binning(g->d, g->nbl, g->cur.r, g->cur.perm, g->celloff, g->bkey, g->bcount, g->bfill, g->bbsum, g->s);
     stencil_build(g->d, g->nbl, g->cur.r, g->cur.st64, g->cur.st32, g->s);
-    if (g->dense_body)
-      dense_body_build(g->nbl, g->nb, g->boff, g->cur.r, g->cur.arm, kBlobRadius * g->desc.h, g->desc.eta, g->dM,
-                       g->dP, g->dN, g->dstatus, g->s);
+    if (g->dense_body) build_body_block(g, g->cur.r, g->cur.arm, nullptr);
     ck(cudaGetLastError());
   } catch (CudaError& e) {
     return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
