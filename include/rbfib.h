@@ -213,10 +213,10 @@ int rbfib_batch_sem_step(rbfib_batch* b, const rbfib_sem_params* params, const u
  * else 0 (per-shape blocks).  The coupled block's inverse RPY matrix is
  * rebuilt for every new configuration (rbfib_set_bodies,
  * rbfib_set_blob_positions, each SEM step): by Gauss-Jordan after
- * rbfib_set_bodies; otherwise by four Newton-Schulz steps from the previous
+ * rbfib_set_bodies; otherwise by eight Newton-Schulz steps from the previous
  * inverse, rotated with each body's rotation since it was built (when the
  * orientations are known: not after rbfib_set_blob_positions), if that
- * start's residual ||I - M X||_F is at most 0.5, else by Gauss-Jordan.
+ * start's residual ||I - M X||_F is at most 0.95, else by Gauss-Jordan.
  * warm_starts counts the builds that took the Newton-Schulz path.  Either
  * pointer may be NULL. */
 int rbfib_body_block_info(const rbfib_grid* g, int32_t* dense, int64_t* warm_starts);

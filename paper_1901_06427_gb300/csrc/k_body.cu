@@ -249,18 +249,19 @@ __global__ void k_rotate_inverse(int nbl, const int* __restrict__ bob, const dou
 //    inverse rotated with each body's rotation since (k_rotate_inverse).
 //    The configuration moves little between SEM steps, so X0 is a close
 //    start for the Newton-Schulz iteration X <- X + X (I - M X), which
-//    converges quadratically while ||I - M X|| < 1.  With ||R0||_F =
-//    ||I - M X0||_F at most kNSMaxStart, four iterations leave a residual of
-//    at most kNSMaxStart^16 (FP32 roundoff in practice); each iteration is two
-//    n x n products on the whole GPU, against n sequential pivot steps on one
-//    SM for Gauss-Jordan.
+//    converges quadratically while ||I - M X|| < 1 (the spectral norm, which
+//    the Frobenius norm bounds).  With ||R0||_F = ||I - M X0||_F at most
+//    kNSMaxStart, kNSIters iterations leave a residual of at most
+//    kNSMaxStart^(2^kNSIters) (FP32 roundoff in practice); each iteration is
+//    two n x n products on the whole GPU, against n sequential pivot steps on
+//    one SM for Gauss-Jordan.
 //  - otherwise, or when R0 is larger (a first configuration, a large move):
 //    in-place Gauss-Jordan.
 // Mw, Tw, Uw: n3 x n3 FP32 work matrices; ss: one device double; ss_host:
 // pinned host double (the choice needs one read of ||R0||).  Returns true
 // when the warm start was taken.
-constexpr double kNSMaxStart = 0.5;
-constexpr int kNSIters = 4;   // even: the result lands in Minv
+constexpr double kNSMaxStart = 0.95;
+constexpr int kNSIters = 8;   // even: the result lands in Minv
 bool dense_body_build(int nbl, int nb, const int* boff, const int* bob, const double* r, const double* arm,
                       const double* qnew, const double* qold, double a, double eta, float* Minv, float* P,
                       double* N, int* status, float* Mw, float* Tw, float* Uw, double* ss, double* ss_host,
