@@ -518,12 +518,6 @@ RBFIB_DEVFN void givens_flag_body(double* H, int ldh, double* cs, double* sn, do
   const bool cont = (res > dpar[0]) && ((double)ist[1] < dpar[1]) && isfinite(res) && (r > 0.0);
   ist[2] = cont ? 1 : 0;
 }
-__global__ void k_givens_flag(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
-                              const double* hcol2, const double* hnext2, double* res_out, int* ist,
-                              const double* dpar) {
-  pdl_entry();
-  givens_flag_body(H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, res_out, ist, dpar);
-}
 
 // The last two steps of a captured Arnoldi iteration in one launch, since
 // neither needs the other: blocks [0, gridDim.x - 1) normalise the new basis
@@ -571,13 +565,6 @@ template void scale_givens<double>(double*, const double*, i64, float*, double*,
 template void scale_givens<float>(float*, const float*, i64, float*, double*, int, double*, double*, double*, int,
                                   const double*, const double*, const double*, double*, int*, const double*,
                                   cudaStream_t);
-
-void givens_flag(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
-                 const double* hcol2, const double* hnext2, double* res_out, int* ist, const double* dpar,
-                 cudaStream_t s) {
-  launch_k(k_givens_flag, 1, 64, 0, s, H, ldh, cs, sn, g, j, hcol, hcol2, hnext2, res_out, ist, dpar);
-  note_launch();
-}
 
 __global__ void k_tri_dev(const double* H, int ldh, const double* g, const int* ist, double* y) {
   pdl_entry();

@@ -739,18 +739,6 @@ __global__ void k_vel_first(Dims d, T eta, T* __restrict__ u, const T* __restric
   u[t] = (((c[0] + c[1] + c[2]) & 1) == 0) ? rhs[t] / (eta * lap_diag<T>(d, a, c)) : T(0);
 }
 
-template <typename T>
-__global__ void k_vel_residual(Dims d, T eta, const T* __restrict__ u, const T* __restrict__ rhs, T* __restrict__ res) {
-  pdl_entry();
-  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= d.fo[3]) return;
-  int a, c[3];
-  decode_face(d, t, a, c);
-  T nb, dg;
-  lap_parts(d, u, a, c, nb, dg);
-  res[t] = rhs[t] - eta * (dg * u[t] - nb);
-}
-
 // One-dimensional transfer stencils.  kind: 0 = not coarsened,
 // 1 = face-centred on a periodic axis, 2 = face-centred on a wall axis,
 // 3 = cell-centred.  ghost_sign: value of a cell-centred ghost beyond a wall
@@ -807,32 +795,9 @@ __device__ inline void prolong_1d(int kind, int jf, int ncext, float ghost_sign,
   } else { s.idx[1] = nb; s.w[1] = 0.25f; }
 }
 
-// Restriction of face residuals to the coarse level: full weighting along a
-// face-centred axis, averaging of the two children along cell-centred axes.
-template <typename T>
-__global__ void k_vel_restrict(Dims df, Dims dc, int3 cz, const T* __restrict__ rf, T* __restrict__ rc) {
-  pdl_entry();
-  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= dc.fo[3]) return;
-  int a, c[3];
-  decode_face(dc, t, a, c);
-  const int cf[3] = {cz.x, cz.y, cz.z};
-  T1 s[3];
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) {
-    int kind = !cf[ax] ? 0 : (ax == a ? (df.per[ax] ? 1 : 2) : 3);
-    restrict_1d(kind, c[ax], df.fe[a][ax], s[ax]);
-  }
-  T acc = T(0);
-  for (int x = 0; x < s[0].cnt; ++x)
-    for (int y = 0; y < s[1].cnt; ++y)
-      for (int z = 0; z < s[2].cnt; ++z)
-        acc += (T)(s[0].w[x] * s[1].w[y] * s[2].w[z]) *
-               rf[df.fo[a] + flat3(df.fe[a], s[0].idx[x], s[1].idx[y], s[2].idx[z])];
-  rc[t] = (T)acc;
-}
-
-// Restriction of the residual rhs - A u, computed on the fly at the fine points.
+// Restriction of the face residuals rhs - A u, computed on the fly at the fine
+// points, to the coarse level: full weighting along a face-centred axis,
+// averaging of the two children along cell-centred axes.
 template <typename T>
 __global__ void k_vel_restrict_res(Dims df, Dims dc, int3 cz, T eta, const T* __restrict__ uf,
                                    const T* __restrict__ rhsf, T* __restrict__ rc) {
@@ -945,37 +910,6 @@ __global__ void k_p_first(Dims d, T* __restrict__ u, const T* __restrict__ rhs) 
   int c[3];
   decode_cell(d, t, c);
   u[t] = (((c[0] + c[1] + c[2]) & 1) == 0) ? rhs[t] / plap_diag<T>(d, c) : T(0);
-}
-
-template <typename T>
-__global__ void k_p_residual(Dims d, const T* __restrict__ u, const T* __restrict__ rhs, T* __restrict__ res) {
-  pdl_entry();
-  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= d.nc) return;
-  int c[3];
-  decode_cell(d, t, c);
-  T nb, dg;
-  plap_parts(d, u, c, nb, dg);
-  res[t] = rhs[t] - (dg * u[t] - nb);
-}
-
-template <typename T>
-__global__ void k_p_restrict(Dims df, Dims dc, int3 cz, const T* __restrict__ rf, T* __restrict__ rc) {
-  pdl_entry();
-  const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= dc.nc) return;
-  int c[3];
-  decode_cell(dc, t, c);
-  const int cf[3] = {cz.x, cz.y, cz.z};
-  T1 s[3];
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) restrict_1d(cf[ax] ? 3 : 0, c[ax], df.n[ax], s[ax]);
-  T acc = T(0);
-  for (int x = 0; x < s[0].cnt; ++x)
-    for (int y = 0; y < s[1].cnt; ++y)
-      for (int z = 0; z < s[2].cnt; ++z)
-        acc += (T)(s[0].w[x] * s[1].w[y] * s[2].w[z]) * rf[flat3(df.n, s[0].idx[x], s[1].idx[y], s[2].idx[z])];
-  rc[t] = (T)acc;
 }
 
 template <typename T>
@@ -1196,16 +1130,6 @@ void vel_restrict_res(const Dims& df, const Dims& dc, int3 cz, T eta, const T* u
   note_launch();
 }
 template <typename T>
-void vel_residual(const Dims& d, T eta, const T* u, const T* rhs, T* res, cudaStream_t s) {
-  launch_k(k_vel_residual<T>, nblk(d.fo[3], 256), 256, 0, s, d, eta, u, rhs, res);
-  note_launch();
-}
-template <typename T>
-void vel_restrict(const Dims& df, const Dims& dc, int3 cz, const T* rf, T* rc, cudaStream_t s) {
-  launch_k(k_vel_restrict<T>, nblk(dc.fo[3], 256), 256, 0, s, df, dc, cz, rf, rc);
-  note_launch();
-}
-template <typename T>
 void vel_prolong(const Dims& df, const Dims& dc, int3 cz, const T* uc, T* uf, cudaStream_t s) {
   launch_k(k_vel_prolong<T>, nblk(df.fo[3], 256), 256, 0, s, df, dc, cz, uc, uf);
   note_launch();
@@ -1238,16 +1162,6 @@ void p_restrict_res(const Dims& df, const Dims& dc, int3 cz, const T* uf, const 
   note_launch();
 }
 template <typename T>
-void p_residual(const Dims& d, const T* u, const T* rhs, T* res, cudaStream_t s) {
-  launch_k(k_p_residual<T>, nblk(d.nc, 256), 256, 0, s, d, u, rhs, res);
-  note_launch();
-}
-template <typename T>
-void p_restrict(const Dims& df, const Dims& dc, int3 cz, const T* rf, T* rc, cudaStream_t s) {
-  launch_k(k_p_restrict<T>, nblk(dc.nc, 256), 256, 0, s, df, dc, cz, rf, rc);
-  note_launch();
-}
-template <typename T>
 void p_prolong(const Dims& df, const Dims& dc, int3 cz, const T* uc, T* uf, cudaStream_t s) {
   launch_k(k_p_prolong<T>, nblk(df.nc, 256), 256, 0, s, df, dc, cz, uc, uf);
   note_launch();
@@ -1277,13 +1191,9 @@ void add_grad(const Dims& d, const T* phi, T* v, cudaStream_t s) {
   template void vel_restrict_res<T>(const Dims&, const Dims&, int3, T, const T*, const T*, T*, cudaStream_t); \
   template void p_first<T>(const Dims&, T*, const T*, cudaStream_t);                              \
   template void p_restrict_res<T>(const Dims&, const Dims&, int3, const T*, const T*, T*, cudaStream_t); \
-  template void vel_residual<T>(const Dims&, T, const T*, const T*, T*, cudaStream_t);           \
-  template void vel_restrict<T>(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);     \
   template void vel_prolong<T>(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);      \
   template void vel_coarse<T>(const Dims&, T, T*, const T*, int, cudaStream_t);                  \
   template void p_rbgs<T>(const Dims&, int, T*, const T*, cudaStream_t, int);                    \
-  template void p_residual<T>(const Dims&, const T*, const T*, T*, cudaStream_t);                \
-  template void p_restrict<T>(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);       \
   template void p_prolong<T>(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);        \
   template void p_coarse<T>(const Dims&, T*, T*, int, cudaStream_t);                             \
   template void div_q<T>(const Dims&, T, const T*, const T*, T*, T*, cudaStream_t);              \

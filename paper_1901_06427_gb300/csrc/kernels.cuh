@@ -66,13 +66,9 @@ template <typename T> void vel_restrict_res(const Dims&, const Dims&, int3, T et
 template <typename T> void p_first(const Dims&, T* u, const T* rhs, cudaStream_t);
 template <typename T> void p_restrict_res(const Dims&, const Dims&, int3, const T* uf, const T* rhsf, T* rc,
                                           cudaStream_t);
-template <typename T> void vel_residual(const Dims&, T eta, const T* u, const T* rhs, T* res, cudaStream_t);
-template <typename T> void vel_restrict(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);
 template <typename T> void vel_prolong(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);
 template <typename T> void vel_coarse(const Dims&, T eta, T* u, const T* rhs, int sweeps, cudaStream_t);
 template <typename T> void p_rbgs(const Dims&, int color, T* u, const T* rhs, cudaStream_t, int block = 256);
-template <typename T> void p_residual(const Dims&, const T* u, const T* rhs, T* res, cudaStream_t);
-template <typename T> void p_restrict(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);
 template <typename T> void p_prolong(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);
 template <typename T> void p_coarse(const Dims&, T* u, T* rhs, int sweeps, cudaStream_t);
 template <typename T> void div_q(const Dims&, T eta, const T* vt, const T* rpi, T* q, T* pi, cudaStream_t);
@@ -190,9 +186,6 @@ template <typename T>
 void scale_givens(T* out, const T* in, i64 n, float* out32, double* H, int ldh, double* cs, double* sn, double* g,
                   int j, const double* hcol, const double* hcol2, const double* nrm2, double* res_out, int* ist,
                   const double* dpar, cudaStream_t s);
-void givens_flag(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
-                 const double* hcol2, const double* hnext2, double* res_out, int* ist, const double* dpar,
-                 cudaStream_t);
 void tri_solve_dev(const double* H, int ldh, const double* g, const int* ist, double* y, cudaStream_t);
 template <typename T> void multi_axpy_dev(T* w, const T* V, i64 ldv, const int* ist, const double* coef,
                                           double sign, i64 n, int nparts, cudaStream_t);
