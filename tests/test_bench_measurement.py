@@ -14,8 +14,14 @@ import bench  # noqa: E402
 
 
 def _peaks():
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-        return json.load(f)
+    """The measured peaks bench.py reads, with its fallbacks when the file
+    (written per GPU pool) is absent."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+    except OSError:
+        p = {}
+    return {"hbm_gbs": p.get("hbm_gbs", 6800.0), "sm_max_mhz": p.get("sm_max_mhz", 2070.0)}
 
 
 def test_every_timer_class_has_roofline_info():
