@@ -205,10 +205,12 @@ void ns_gemm(int n, const float* A, const float* B, const float* D, float* C, do
 
 // Rotates the previous configuration's inverse with each body's rotation
 // since then: X_ij <- D_b(i) X_ij D_b(j)^T for the 3 x 3 blocks (blobs i, j
-// of bodies b(i), b(j)), D_p = R(quat_new_p) R(quat_old_p)^T.  The RPY matrix
-// of a blob set rotated rigidly about each body's centre has exactly these
-// intra-body blocks (the RPY tensor is rotation-covariant), so only the
-// inter-body blocks of the start are off.  One thread per block, in place.
+// of bodies b(i), b(j)), D_p = R(quat_new_p) R(quat_old_p)^T.  The RPY tensor
+// is rotation-covariant, so rotating each body rigidly about its centre turns
+// the intra-body blocks of M into exactly these; for a single body the
+// rotated inverse is exact.  With several bodies the start's error comes from
+// the inter-body blocks of M, which the move also changes.  One thread per
+// block, in place.
 __global__ void k_rotate_inverse(int nbl, const int* __restrict__ bob, const double* __restrict__ qnew,
                                  const double* __restrict__ qold, float* __restrict__ X) {
   pdl_entry();
