@@ -24,7 +24,13 @@ DELTA = 6.0554544523933395e-06
 
 
 def sem_step(g: Grid, b, eta, kT, dt, potentials, seed, step, attempt=0, delta=DELTA,
-             F_ext=None, slip=None, op=None, parts=False):
+             F_ext=None, slip=None, op=None, parts=False, normals=None, fluid_noise=True, M=None):
+    """One SEM step from configuration b.  The random draws are Philox
+    normals of (seed, step, attempt) unless injected: ``normals`` = (W^f,
+    W^tau), each (N_b, 3), replaces the body draw of step 1, and
+    ``fluid_noise=False`` drops the stochastic stress of step 6 (the drift
+    tests drive the step with basis vectors).  ``M`` may pass a precomputed
+    blob mobility of b."""
     op = op or solve.StokesOperator(g, eta)
     nb, nbl = b.n_bodies, b.n_blobs
     o = saddle.layout(g, b)
@@ -33,14 +39,18 @@ def sem_step(g: Grid, b, eta, kT, dt, potentials, seed, step, attempt=0, delta=D
     if F_ext is not None:
         F = F + np.asarray(F_ext).reshape(nb, 6)
     # step 1: random forces and torques
-    Wf, Wt = noise.body_normals(nb, seed, step, attempt)
+    if normals is None:
+        Wf, Wt = noise.body_normals(nb, seed, step, attempt)
+    else:
+        Wf, Wt = (np.asarray(x, dtype=float).reshape(nb, 3) for x in normals)
     Lp = rigid.body_length(b.ref, b.offsets)
     WFT = noise.random_force_torque(Wf, Wt, Lp, kT)
-    M = solve.blob_mobility(g, b, eta, op=op)
+    if M is None:
+        M = solve.blob_mobility(g, b, eta, op=op)
     rfd = rfd_terms(g, b, eta, kT, Wf, Wt, Lp, delta, M=M, op=op)
     D_KT, D_K, D_J, D_S = rfd["D_KT"], rfd["D_K"], rfd["D_J"], rfd["D_S"]
     # step 6: fluctuating constrained solve
-    f_noise = noise.fluid_forcing(g, eta, kT, dt, seed, step, attempt)
+    f_noise = noise.fluid_forcing(g, eta, kT, dt, seed, step, attempt) if fluid_noise else np.zeros(g.N_f)
     slip_tot = (np.zeros(3 * nbl) if slip is None else np.asarray(slip).ravel()) + D_K - D_J - D_S
     f2 = saddle.rhs(g, b, eta, F=F.ravel() - D_KT, slip=slip_tot, f_fluid=f_noise, walls=True)
     x2 = solve.constrained(g, b, eta, f2, M=M, op=op)

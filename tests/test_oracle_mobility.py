@@ -126,11 +126,15 @@ def _N_of(g, b, eta):
     return solve.body_mobility(M, rigid.K_matrix(b.ref, b.offsets, b.quat))
 
 
-@pytest.mark.slow
-def test_drift_expectation_by_basis_enumeration():
-    """<U_drift> = sum_k U_drift(xi = e_k) equals kT div_Q N from central
-    differences of N in positions and lab-frame rotation angles (Eq. DriDef,
-    App. B); with the RFD terms dropped the drift would vanish."""
+_DRIFT = {}
+
+
+def _drift_case():
+    """Two 12-blob shells in an 8x7x7 walled box, their blob mobility, and
+    kT div_Q N from central differences of N in positions and lab-frame
+    rotation angles (computed once per test session)."""
+    if _DRIFT:
+        return _DRIFT
     n = (8, 7, 7)
     g = Grid(n)
     shell = workloads.icosahedral_shell(12, 1.0)
@@ -141,14 +145,7 @@ def test_drift_expectation_by_basis_enumeration():
     eta, kT = 1.0, 1.0
     op = solve.StokesOperator(g, eta)
     M = solve.blob_mobility(g, b, eta, op=op)
-    Lp = rigid.body_length(b.ref, b.offsets)
     nb = b.n_bodies
-    drift = np.zeros(6 * nb)
-    for k in range(6 * nb):
-        xi = np.zeros((nb, 6)); xi.flat[k] = 1.0
-        t = sem.rfd_terms(g, b, eta, kT, xi[:, :3], xi[:, 3:], Lp, M=M, op=op)
-        f = saddle.rhs(g, b, eta, F=-t["D_KT"], slip=t["D_K"] - t["D_J"] - t["D_S"], walls=False)
-        drift += solve.constrained(g, b, eta, f, M=M, op=op)[-6 * nb:]
     eps = 1e-4
     div = np.zeros(6 * nb)
     for p in range(nb):
@@ -165,5 +162,44 @@ def test_drift_expectation_by_basis_enumeration():
             Nm = _N_of(g, b.moved(qm, tm), eta)
             div += (Np[:, k] - Nm[:, k]) / (2 * eps)
     div *= kT
+    _DRIFT.update(g=g, b=b, eta=eta, kT=kT, op=op, M=M, nb=nb, div=div, q=q, quat=quat)
+    return _DRIFT
+
+
+@pytest.mark.slow
+def test_drift_expectation_by_basis_enumeration():
+    """<U_drift> = sum_k U_drift(xi = e_k) equals kT div_Q N from central
+    differences of N in positions and lab-frame rotation angles (Eq. DriDef,
+    App. B); with the RFD terms dropped the drift would vanish."""
+    c = _drift_case()
+    g, b, eta, kT, op, M, nb, div = (c[k] for k in ("g", "b", "eta", "kT", "op", "M", "nb", "div"))
+    Lp = rigid.body_length(b.ref, b.offsets)
+    drift = np.zeros(6 * nb)
+    for k in range(6 * nb):
+        xi = np.zeros((nb, 6)); xi.flat[k] = 1.0
+        t = sem.rfd_terms(g, b, eta, kT, xi[:, :3], xi[:, 3:], Lp, M=M, op=op)
+        f = saddle.rhs(g, b, eta, F=-t["D_KT"], slip=t["D_K"] - t["D_J"] - t["D_S"], walls=False)
+        drift += solve.constrained(g, b, eta, f, M=M, op=op)[-6 * nb:]
     assert np.linalg.norm(div) > 1e-3       # a real drift, which plain EM would miss
     np.testing.assert_allclose(drift, div, rtol=0, atol=2e-6 * np.linalg.norm(div))
+
+
+@pytest.mark.slow
+def test_sem_step_mean_drift_by_basis_enumeration():
+    """The same expectation through oracle.sem.sem_step itself: with no
+    forces, no fluid noise and the body normals injected as xi = e_k, the
+    step's body velocity is the drift alone (its step-6 solve with force
+    F - D^{K^T} and slip D^K - D^J - D^S), so sum_k U(e_k) = kT div_Q N
+    (Eq. DriDef, App. B), and the step moves every body by dt U.  A sign slip
+    in the step-6 assembly or a dropped RFD term fails this."""
+    c = _drift_case()
+    g, b, eta, kT, op, M, nb, div = (c[k] for k in ("g", "b", "eta", "kT", "op", "M", "nb", "div"))
+    dt = 0.01
+    mean_U = np.zeros(6 * nb)
+    for k in range(6 * nb):
+        xi = np.zeros((nb, 6)); xi.flat[k] = 1.0
+        out = sem.sem_step(g, b, eta, kT, dt, {}, seed=0, step=0, normals=(xi[:, :3], xi[:, 3:]),
+                           fluid_noise=False, op=op, M=M)
+        np.testing.assert_allclose(out["q"] - b.q, dt * out["U"][:, :3], rtol=0, atol=1e-15)
+        mean_U += out["U"].ravel()
+    np.testing.assert_allclose(mean_U, div, rtol=0, atol=2e-6 * np.linalg.norm(div))
