@@ -239,6 +239,16 @@ int rbfib_binning(rbfib_grid* g, int32_t* perm, int32_t* cell_offsets);
 /* Current blob positions r (device, N_bl x 3, FP64). */
 int rbfib_blob_positions(rbfib_grid* g, double* r);
 
+/* Raw random words of the counter-based generator behind every random draw
+ * of the method (the noise of Sec. IV.B and Eq. LangevinD1 is drawn from it):
+ * Philox4x64-10 (Salmon et al., SC11) with key (seed, 0) and counter
+ * (block, step, (attempt << 32) | purpose, 0), for the n_blocks blocks
+ * first_block, first_block + 1, ...; out (device, 16-byte aligned,
+ * 4 n_blocks uint64) receives each block's four words in order.  A null or
+ * misaligned out with n_blocks > 0 gives RBFIB_EINVAL. */
+int rbfib_philox_words(rbfib_grid* g, uint64_t seed, uint64_t step, uint32_t attempt, uint32_t purpose,
+                       uint64_t first_block, int64_t n_blocks, uint64_t* out);
+
 /* count standard normals of the Philox stream (seed, step, attempt, purpose)
  * into out (device FP64): normal g is lane g%4 of block g/4 (Box-Muller on the
  * block's uniforms u = (2 (word >> 12) + 1) 2^-53, lanes (0,1) and (2,3)). */
@@ -271,8 +281,14 @@ int rbfib_body_forces(rbfib_grid* g, const rbfib_sem_params* p, double* out);
  *    (8 MiB) that is part of the library image; every device that loads the
  *    library holds it until the process exits.  Grids whose stress field has
  *    more values (about 9 per cell) are rejected with RBFIB_EINVAL.
- *  - The first call on each device looks up the array's device address (with
- *    that device current); make that first call before any stream capture.
+ *  - Each call made outside stream capture looks up the array's device
+ *    address on the current device (so a context that was reset and
+ *    re-created is handled); a call made while the stream is capturing uses
+ *    the address found by the last call outside capture on that device, so
+ *    make the first call on each device before any stream capture (a first
+ *    call during capture returns RBFIB_EINVAL).
+ *  - desc->periodic values other than 0 and 1 give RBFIB_EINVAL, as in
+ *    rbfib_create_grid.
  *  - Every call shares the array and overwrites all of it that it uses; calls
  *    that overlap on the GPU (other streams, other threads) race.
  *  - errbuf (optional, errlen bytes) receives a one-line message.

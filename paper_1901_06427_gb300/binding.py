@@ -79,6 +79,7 @@ def lib():
             "rbfib_sem_step": ([P, ctypes.POINTER(SemParams), U64, U64, U32, P, P, ctypes.POINTER(StepInfo)], I32),
             "rbfib_binning": ([P, P, P], I32),
             "rbfib_blob_positions": ([P, P], I32),
+            "rbfib_philox_words": ([P, U64, U64, U32, U32, U64, I64, P], I32),
             "rbfib_philox_normals": ([P, U64, U64, U32, U32, I64, P], I32),
             "rbfib_stochastic_forcing": ([P, D, D, U64, U64, U32, P], I32),
             "rbfib_spread": ([P, P, P], I32),
@@ -296,6 +297,13 @@ class Grid:
         r = torch.empty(3 * max(self.n_blobs, 1), dtype=torch.float64, device="cuda")
         self._check(lib().rbfib_blob_positions(self._h, _ptr(r)))
         return r[:3 * self.n_blobs]
+
+    def philox_words(self, seed, step, attempt, purpose, n_blocks, first_block=0):
+        """(n_blocks, 4) int64 tensor holding the raw uint64 words bit for bit."""
+        out = torch.empty((max(n_blocks, 1), 4), dtype=torch.int64, device="cuda")
+        self._check(lib().rbfib_philox_words(self._h, seed, step, attempt, purpose, first_block, n_blocks,
+                                             _ptr(out, torch.int64)))
+        return out[:n_blocks]
 
     def philox_normals(self, seed, step, attempt, purpose, count):
         out = torch.empty(max(count, 1), dtype=torch.float64, device="cuda")

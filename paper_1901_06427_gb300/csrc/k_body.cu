@@ -264,13 +264,17 @@ __global__ void k_rotate_inverse(int nbl, const int* __restrict__ bob, const dou
 // when the warm start was taken.
 constexpr double kNSMaxStart = 0.95;
 constexpr int kNSIters = 8;   // even: the result lands in Minv
-bool dense_body_build(int nbl, int nb, const int* boff, const int* bob, const double* r, const double* arm,
-                      const double* qnew, const double* qold, double a, double eta, float* Minv, float* P,
-                      double* N, int* status, float* Mw, float* Tw, float* Uw, double* ss, double* ss_host,
-                      bool warm, cudaStream_t s) {
+cudaError_t dense_body_build(int nbl, int nb, const int* boff, const int* bob, const double* r, const double* arm,
+                             const double* qnew, const double* qold, double a, double eta, float* Minv, float* P,
+                             double* N, int* status, float* Mw, float* Tw, float* Uw, double* ss, double* ss_host,
+                             bool warm, cudaStream_t s, bool* used_out) {
   const i64 n3 = 3 * (i64)nbl, m = 6 * (i64)nb;
-  cudaMemsetAsync(status, 0, sizeof(int), s);
+  cudaError_t e;
+#define RB_CK(call)                      \
+  if ((e = (call)) != cudaSuccess) return e
+  RB_CK(cudaMemsetAsync(status, 0, sizeof(int), s));
   bool used = false;
+  *used_out = false;
   if (warm) {
     launch_k(k_rpy_full, nblk(n3 * n3, 256), 256, 0, s, nbl, r, a, eta, Mw);
     note_launch();
@@ -278,10 +282,10 @@ bool dense_body_build(int nbl, int nb, const int* boff, const int* bob, const do
       launch_k(k_rotate_inverse, nblk((i64)nbl * nbl, 128), 128, 0, s, nbl, bob, qnew, qold, Minv);
       note_launch();
     }
-    cudaMemsetAsync(ss, 0, sizeof(double), s);
+    RB_CK(cudaMemsetAsync(ss, 0, sizeof(double), s));
     ns_gemm<0>((int)n3, Mw, Minv, nullptr, Tw, ss, s);          // R0 = I - M X0
-    cudaMemcpyAsync(ss_host, ss, sizeof(double), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
+    RB_CK(cudaMemcpyAsync(ss_host, ss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    RB_CK(cudaStreamSynchronize(s));
     const double r0 = std::sqrt(std::max(ss_host[0], 0.0));
     if (r0 <= kNSMaxStart) {
       float* X = Minv;
@@ -293,7 +297,7 @@ bool dense_body_build(int nbl, int nb, const int* boff, const int* bob, const do
       }
       used = true;
     } else {
-      cudaMemcpyAsync(Minv, Mw, sizeof(float) * n3 * n3, cudaMemcpyDeviceToDevice, s);
+      RB_CK(cudaMemcpyAsync(Minv, Mw, sizeof(float) * n3 * n3, cudaMemcpyDeviceToDevice, s));
     }
   } else {
     launch_k(k_rpy_full, nblk(n3 * n3, 256), 256, 0, s, nbl, r, a, eta, Minv);
@@ -309,7 +313,9 @@ bool dense_body_build(int nbl, int nb, const int* boff, const int* bob, const do
   note_launch();
   launch_k(k_gj_inverse<double>, 1, 1024, 2 * sizeof(double) * m, s, N, (int)m, status);
   note_launch();
-  return used;
+  *used_out = used;
+  return cudaGetLastError();
+#undef RB_CK
 }
 
 // Apply on one cluster of kBodyCtas CTAs: t = M^-1 s; f = r_U + K^T t;

@@ -29,6 +29,28 @@ void philox_normals(unsigned long long seed, unsigned long long step, unsigned a
   }
 }
 
+// The raw words of n_blocks consecutive Philox4x64-10 blocks of the stream
+// (seed, step, attempt, purpose), four 64-bit words per block.
+__global__ void k_philox_words(unsigned long long seed, unsigned long long step, unsigned attempt, unsigned purpose,
+                               unsigned long long first, i64 n_blocks, unsigned long long* __restrict__ out) {
+  pdl_entry();
+  const i64 b = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_blocks) return;
+  unsigned long long c[4] = {first + (unsigned long long)b, step, ((unsigned long long)attempt << 32) | purpose, 0ULL};
+  philox4x64_10(c, seed, 0ULL);
+  ulonglong2* o = reinterpret_cast<ulonglong2*>(out + 4 * b);
+  o[0] = make_ulonglong2(c[0], c[1]);
+  o[1] = make_ulonglong2(c[2], c[3]);
+}
+
+void philox_words(unsigned long long seed, unsigned long long step, unsigned attempt, unsigned purpose,
+                  unsigned long long first, i64 n_blocks, unsigned long long* out, cudaStream_t s) {
+  if (n_blocks > 0) {
+    launch_k(k_philox_words, nblk(n_blocks, 128), 128, 0, s, seed, step, attempt, purpose, first, n_blocks, out);
+    note_launch();
+  }
+}
+
 // out(face of component a) = c * [ (W_aa(right) - W_aa(left)) / h_a
 //                                  + sum_{b != a} (c+ W_ab(node j+1) - c- W_ab(node j)) / h_b ]
 __global__ void k_stress_div(Dims d, StressLayout L, const double* __restrict__ W, double c, double* __restrict__ out) {
@@ -111,12 +133,34 @@ extern "C" int rbfib_stochastic_forcing_static(const rbfib_grid_desc* desc, doub
   int per[3], n[3];
   for (int a = 0; a < 3; ++a) {
     n[a] = desc->n[a];
-    per[a] = desc->periodic[a] ? 1 : 0;
+    if (desc->periodic[a] != 0 && desc->periodic[a] != 1) {
+      set_msg(errbuf, errlen, "stochastic_forcing_static: periodic must be 0 or 1");
+      return RBFIB_EINVAL;
+    }
+    per[a] = desc->periodic[a];
     if (n[a] < 2) { set_msg(errbuf, errlen, "stochastic_forcing_static: n < 2"); return RBFIB_EINVAL; }
   }
   if (per[0] && per[1] && per[2]) {
     set_msg(errbuf, errlen, "stochastic_forcing_static: every axis periodic");
     return RBFIB_EINVAL;
+  }
+  // Bound the cell count before any product of extents is formed: the
+  // stress field holds about nine values per cell, so a grid with more cells
+  // than the scratch has values can never fit (and the 64-bit products below
+  // cannot overflow once each extent and the cell count are bounded).
+  {
+    long long cells = 1;
+    for (int a = 0; a < 3; ++a) {
+      if ((long long)n[a] > kStaticStressMax || cells > kStaticStressMax / n[a]) {
+        cells = kStaticStressMax + 1;
+        break;
+      }
+      cells *= n[a];
+    }
+    if (cells > kStaticStressMax) {
+      set_msg(errbuf, errlen, "stochastic_forcing_static: grid exceeds the static scratch");
+      return RBFIB_EINVAL;
+    }
   }
   const double h3[3] = {desc->h, desc->h, desc->h};
   const Dims d = make_dims(n, per, h3);
@@ -146,16 +190,28 @@ extern "C" int rbfib_stochastic_forcing_static(const rbfib_grid_desc* desc, doub
     set_msg(errbuf, errlen, msg);
     return RBFIB_EINVAL;
   }
-  // set-up once per device, with that device current
+  // Device address of the scratch, with the target device current.  Outside
+  // stream capture it is looked up on every call (a cheap query), so a
+  // primary context that was reset and re-created since the last call (which
+  // reloads the module at a new address) never gets a stale pointer; during
+  // capture the address cached by the last call outside capture on this
+  // device is used, so the first call on a device must come before any
+  // capture.
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     set_msg(errbuf, errlen, "stochastic_forcing_static: no usable current device");
     return RBFIB_ECUDA;
   }
+  const cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    set_msg(errbuf, errlen, "stochastic_forcing_static: cudaStreamIsCapturing failed");
+    return RBFIB_ECUDA;
+  }
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
       void* p = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&p, g_static_stress);
       if (e != cudaSuccess || !p) {
@@ -163,10 +219,12 @@ extern "C" int rbfib_stochastic_forcing_static(const rbfib_grid_desc* desc, doub
         return RBFIB_ECUDA;
       }
       g_static_ptr[dev] = (double*)p;
+    } else if (!g_static_ptr[dev]) {
+      set_msg(errbuf, errlen, "stochastic_forcing_static: first call on this device made during stream capture");
+      return RBFIB_EINVAL;
     }
     scratch = g_static_ptr[dev];
   }
-  const cudaStream_t s = (cudaStream_t)cuda_stream;
   philox_normals(seed, step, attempt, 1u, L.total, scratch, s);
   stress_divergence(d, L, scratch, std::sqrt(2.0 * desc->eta * kT / (d.h[0] * d.h[1] * d.h[2] * dt)), out, s);
   const cudaError_t e = cudaGetLastError();

@@ -137,10 +137,10 @@ void adjoint_positions(const Dims&, int nbl, const int* bob, const double* r, co
                        cudaStream_t);
 
 // k_body.cu
-bool dense_body_build(int nbl, int nb, const int* boff, const int* bob, const double* r, const double* arm,
-                      const double* qnew, const double* qold, double a, double eta, float* Minv, float* P,
-                      double* N, int* status, float* Mw, float* Tw, float* Uw, double* ss, double* ss_host,
-                      bool warm, cudaStream_t);
+cudaError_t dense_body_build(int nbl, int nb, const int* boff, const int* bob, const double* r, const double* arm,
+                             const double* qnew, const double* qold, double a, double eta, float* Minv, float* P,
+                             double* N, int* status, float* Mw, float* Tw, float* Uw, double* ss, double* ss_host,
+                             bool warm, cudaStream_t, bool* used);
 template <typename T> void dense_body_apply(int nbl, int nb, const int* boff, const int* bob, const double* arm,
                                             const float* Minv, const float* P, const double* N, const T* sres,
                                             const T* rU, T* zlam, T* zU, cudaStream_t);
@@ -193,6 +193,8 @@ template <typename T> void multi_axpy_dev(T* w, const T* V, i64 ldv, const int* 
 // k_noise.cu
 void philox_normals(unsigned long long seed, unsigned long long step, unsigned attempt, unsigned purpose,
                     i64 count, double* out, cudaStream_t);
+void philox_words(unsigned long long seed, unsigned long long step, unsigned attempt, unsigned purpose,
+                  unsigned long long first, i64 n_blocks, unsigned long long* out, cudaStream_t);
 void stress_divergence(const Dims&, const StressLayout&, const double* W, double c, double* out, cudaStream_t);
 
 }  // namespace rbfib

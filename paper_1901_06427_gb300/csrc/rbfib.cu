@@ -32,8 +32,14 @@ const double kBlobRadius = 0.91;                         // hydrodynamic radius 
 const int kDenseBodyMaxRows = 1536;                      // 3 N_bl limit of the coupled body block
 const int kDenseBodyMaxBodyRows = 384;                   // 6 N_b limit of the coupled body block
 
+// A failed CUDA runtime call, or (code other than RBFIB_ECUDA) an
+// inconsistency found on the host after a device step, such as a singular
+// pivot in the body block's set-up.
 struct CudaError {
   cudaError_t e;
+  int code = RBFIB_ECUDA;
+  const char* msg = nullptr;
+  const char* what() const { return msg ? msg : cudaGetErrorString(e); }
 };
 
 inline void ck(cudaError_t e) {
@@ -860,11 +866,27 @@ bool inverse6(double A[36]) {
 // orientations quat (NULL: not known, as after rbfib_set_blob_positions):
 // warm-started from the current inverse when there is one
 // (dense_body_build).
+// A zero pivot in either Gauss-Jordan inversion (the FP32 blob block or the
+// FP64 body block) leaves the block invalid and fails the calling entry
+// point with RBFIB_EINTERNAL.
 void build_body_block(rbfib_grid* g, const double* r, const double* arm, const double* quat) {
   const double* qold = (quat && g->dquat_valid) ? g->dquat.p : nullptr;
-  const bool used = dense_body_build(g->nbl, g->nb, g->boff, g->bob, r, arm, quat, qold, kBlobRadius * g->desc.h,
-                                     g->desc.eta, g->dM, g->dP, g->dN, g->dstatus, g->dMw, g->dTw, g->dUw, g->dss,
-                                     g->h_pinned + 40, g->dM_valid, g->s);
+  bool used = false;
+  const bool warm = g->dM_valid;
+  g->dM_valid = false;
+  ck(dense_body_build(g->nbl, g->nb, g->boff, g->bob, r, arm, quat, qold, kBlobRadius * g->desc.h, g->desc.eta,
+                      g->dM, g->dP, g->dN, g->dstatus, g->dMw, g->dTw, g->dUw, g->dss, g->h_pinned + 40, warm, g->s,
+                      &used));
+  int* hstat = (int*)(g->h_pinned + 42);
+  ck(cudaMemcpyAsync(hstat, g->dstatus, sizeof(int), cudaMemcpyDeviceToHost, g->s));
+  ck(cudaStreamSynchronize(g->s));
+  if (*hstat != 0) {
+    g->dquat_valid = false;
+    CudaError err{cudaSuccess};
+    err.code = RBFIB_EINTERNAL;
+    err.msg = "body block: zero pivot in the Gauss-Jordan inversion";
+    throw err;
+  }
   g->dM_valid = true;
   g->dquat_valid = quat != nullptr;
   if (quat) ck(cudaMemcpyAsync(g->dquat.p, quat, sizeof(double) * 4 * g->nb, cudaMemcpyDeviceToDevice, g->s));
@@ -1008,7 +1030,7 @@ int rbfib_kernel_timer(rbfib_grid* g, int32_t which) {
   try {
     ck(cudaStreamSynchronize(g->s));
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+    return fail(g, e.code, e.what());
   }
   g->timer_kind = which;
   g->tev_used = 0;
@@ -1045,7 +1067,7 @@ int rbfib_kernel_timer_overhead(rbfib_grid* g, int32_t reps, double* median_us) 
     std::sort(t.begin(), t.end());
     *median_us = t[reps / 2];
   } catch (CudaError& e) {
-    st = fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+    st = fail(g, e.code, e.what());
   }
   for (cudaEvent_t e : ev) cudaEventDestroy(e);
   return st;
@@ -1062,7 +1084,7 @@ int rbfib_kernel_timer_read(rbfib_grid* g, double* total_ms, int64_t* launches, 
       tot += ms;
     }
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+    return fail(g, e.code, e.what());
   }
   if (total_ms) *total_ms = tot;
   if (launches) *launches = g->timer_launches;
@@ -1127,7 +1149,7 @@ int rbfib_create_grid(const rbfib_grid_desc* desc, void* stream, rbfib_grid** ou
     autotune(g);
     ck(cudaStreamSynchronize(g->s));
   } catch (CudaError& e) {
-    std::string msg = std::string("create_grid: ") + cudaGetErrorString(e.e);
+    std::string msg = std::string("create_grid: ") + e.what();
     delete g;
     (void)msg;
     return RBFIB_ECUDA;
@@ -1306,7 +1328,7 @@ int rbfib_set_bodies(rbfib_grid* g, int32_t n_bodies, const int32_t* blob_offset
     ck(cudaStreamSynchronize(g->s));
     ck(cudaGetLastError());
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, std::string("set_bodies: ") + cudaGetErrorString(e.e));
+    return fail(g, e.code, std::string("set_bodies: ") + e.what());
   }
   return RBFIB_OK;
 }
@@ -1317,7 +1339,7 @@ int rbfib_apply_preconditioner(rbfib_grid* g, const double* r, double* z) {
     precond_any(g, r, z, true);
     ck(cudaGetLastError());
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, std::string("apply_preconditioner: ") + cudaGetErrorString(e.e));
+    return fail(g, e.code, std::string("apply_preconditioner: ") + e.what());
   }
   return RBFIB_OK;
 }
@@ -1330,7 +1352,7 @@ int rbfib_apply_saddle(rbfib_grid* g, const void* x, void* y, int32_t dtype) {
     else return fail(g, RBFIB_EINVAL, "apply_saddle: dtype");
     ck(cudaGetLastError());
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, std::string("apply_saddle: ") + cudaGetErrorString(e.e));
+    return fail(g, e.code, std::string("apply_saddle: ") + e.what());
   }
   return RBFIB_OK;
 }
@@ -1431,7 +1453,7 @@ int rbfib_mobility_solve(rbfib_grid* g, const double* FT, const double* slip, co
     ck(cudaGetLastError());
     if (st) return fail(g, st, st == RBFIB_ENOCONV ? "mobility_solve: no convergence" : "mobility_solve: NaN");
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, std::string("mobility_solve: ") + cudaGetErrorString(e.e));
+    return fail(g, e.code, std::string("mobility_solve: ") + e.what());
   }
   return RBFIB_OK;
 }
@@ -1448,7 +1470,7 @@ int rbfib_stokes_solve(rbfib_grid* g, const double* f, double* v, double* pi, rb
     ck(cudaGetLastError());
     if (st) return fail(g, st, "stokes_solve: no convergence");
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, std::string("stokes_solve: ") + cudaGetErrorString(e.e));
+    return fail(g, e.code, std::string("stokes_solve: ") + e.what());
   }
   return RBFIB_OK;
 }
@@ -1461,7 +1483,7 @@ int rbfib_binning(rbfib_grid* g, int32_t* perm, int32_t* cell_offsets) {
       ck(cudaMemcpyAsync(cell_offsets, g->celloff, sizeof(int) * (g->nc + 1), cudaMemcpyDeviceToDevice, g->s));
     ck(cudaGetLastError());
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, std::string("binning: ") + cudaGetErrorString(e.e));
+    return fail(g, e.code, std::string("binning: ") + e.what());
   }
   return RBFIB_OK;
 }
@@ -1471,7 +1493,20 @@ int rbfib_blob_positions(rbfib_grid* g, double* r) {
   try {
     if (g->nbl) ck(cudaMemcpyAsync(r, g->cur.r, sizeof(double) * 3 * g->nbl, cudaMemcpyDeviceToDevice, g->s));
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+    return fail(g, e.code, e.what());
+  }
+  return RBFIB_OK;
+}
+
+int rbfib_philox_words(rbfib_grid* g, uint64_t seed, uint64_t step, uint32_t attempt, uint32_t purpose,
+                       uint64_t first_block, int64_t n_blocks, uint64_t* out) {
+  if (!g || n_blocks < 0 || (n_blocks > 0 && (!out || (reinterpret_cast<uintptr_t>(out) & 15))))
+    return fail(g, RBFIB_EINVAL, "philox_words: bad argument");
+  try {
+    philox_words(seed, step, attempt, purpose, first_block, n_blocks, (unsigned long long*)out, g->s);
+    ck(cudaGetLastError());
+  } catch (CudaError& e) {
+    return fail(g, e.code, e.what());
   }
   return RBFIB_OK;
 }
@@ -1483,7 +1518,7 @@ int rbfib_philox_normals(rbfib_grid* g, uint64_t seed, uint64_t step, uint32_t a
     philox_normals(seed, step, attempt, purpose, count, out, g->s);
     ck(cudaGetLastError());
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+    return fail(g, e.code, e.what());
   }
   return RBFIB_OK;
 }
@@ -1497,7 +1532,7 @@ int rbfib_stochastic_forcing(rbfib_grid* g, double kT, double dt, uint64_t seed,
     stress_divergence(g->d, g->stress, g->Wst, c, out, g->s);
     ck(cudaGetLastError());
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+    return fail(g, e.code, e.what());
   }
   return RBFIB_OK;
 }
@@ -1509,7 +1544,7 @@ int rbfib_spread(rbfib_grid* g, const double* lambda, double* f) {
     spread_tab(g->d, view_of(g, g->cur), lambda, 1.0 / g->dV, f, g->s);
     ck(cudaGetLastError());
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+    return fail(g, e.code, e.what());
   }
   return RBFIB_OK;
 }
@@ -1522,7 +1557,7 @@ int rbfib_interpolate(rbfib_grid* g, const double* v, double* u, int32_t with_wa
       interp<double>(g->d, g->walls, g->nbl, g->cur.r, (const double*)nullptr, 0.0, 1.0, 1.0, u, g->s);
     ck(cudaGetLastError());
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+    return fail(g, e.code, e.what());
   }
   return RBFIB_OK;
 }
@@ -1551,7 +1586,7 @@ int rbfib_body_forces(rbfib_grid* g, const rbfib_sem_params* p, double* out) {
     body_forces(g->d, potentials_of(p), view_of(g, g->cur), p->force_ext, out, g->s);
     ck(cudaGetLastError());
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+    return fail(g, e.code, e.what());
   }
   return RBFIB_OK;
 }
@@ -1566,7 +1601,7 @@ int rbfib_set_blob_positions(rbfib_grid* g, const double* r) {
     if (g->dense_body) build_body_block(g, g->cur.r, g->cur.arm, nullptr);
     ck(cudaGetLastError());
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, cudaGetErrorString(e.e));
+    return fail(g, e.code, e.what());
   }
   return RBFIB_OK;
 }
@@ -1594,7 +1629,7 @@ int rbfib_mobility_solve_adjoint(rbfib_grid* g, const double* dL_dU, const doubl
     ck(cudaGetLastError());
     if (st) return fail(g, st, "mobility_solve_adjoint: adjoint solve did not converge");
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, std::string("mobility_solve_adjoint: ") + cudaGetErrorString(e.e));
+    return fail(g, e.code, std::string("mobility_solve_adjoint: ") + e.what());
   }
   return RBFIB_OK;
 }
@@ -1690,7 +1725,7 @@ int rbfib_sem_step(rbfib_grid* g, const rbfib_sem_params* p, uint64_t seed, uint
     ck(cudaStreamSynchronize(s));
     ck(cudaGetLastError());
   } catch (CudaError& e) {
-    return fail(g, RBFIB_ECUDA, std::string("sem_step: ") + cudaGetErrorString(e.e));
+    return fail(g, e.code, std::string("sem_step: ") + e.what());
   }
   if (info) *info = loc;
   if (st) return fail(g, st, "sem_step: a solve did not converge");

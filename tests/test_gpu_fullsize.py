@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 import oracle  # noqa: E402
 from oracle import saddle  # noqa: E402
 import workloads  # noqa: E402
-from gpu_common import rel  # noqa: E402
+from gpu_common import rel, assert_close, assert_close_blocks, F64_MATVEC, F32_MATVEC, SOLVED, SEM_STEP  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
@@ -39,9 +39,10 @@ def test_fullsize_matvec(B, make):
     x = np.random.default_rng(0).standard_normal(g.n_total)
     y = g.apply_saddle(dev(x)).cpu().numpy()
     y0 = saddle.apply(og, ob, w.eta, x)
-    assert rel(y, y0) < 1e-11
-    y32 = g.apply_saddle(torch.tensor(x, dtype=torch.float32, device="cuda")).double().cpu().numpy()
-    assert rel(y32, y0) < 1e-5
+    assert_close_blocks(y, y0, g.layout(), F64_MATVEC, "FP64 matvec")
+    x32 = x.astype(np.float32).astype(np.float64)
+    y32 = g.apply_saddle(torch.tensor(x32, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+    assert_close_blocks(y32, saddle.apply(og, ob, w.eta, x32), g.layout(), F32_MATVEC, "FP32 matvec")
 
 
 def test_single_sphere_mobility_against_oracle(B):
@@ -51,7 +52,7 @@ def test_single_sphere_mobility_against_oracle(B):
     U, info = g.mobility_solve(dev(w.force_torque))
     U = U.cpu().numpy()
     assert info["rel_residual"] <= 1e-12
-    assert rel(U, gold["U"]) < 1e-8
+    assert_close(U, gold["U"], SOLVED, "U")
     # symmetry of the centred shell in the cube: no coupling between axes
     assert np.all(np.abs(U[[1, 2, 3, 4]]) < 1e-8 * np.abs(U).max())
     # at the benchmark tolerance (1e-10) the answer stays within the tolerance band
@@ -70,9 +71,9 @@ def test_two_sphere_sem_step_against_oracle(B):
     st, info = g.sem_step(p, w.seed, 0, 0, q, quat)
     assert st == 0
     dq = q.cpu().numpy() - np.array(gold["q0"])
-    assert rel(dq, np.array(gold["q"]) - np.array(gold["q0"])) < 1e-8
+    assert_close(dq, np.array(gold["q"]) - np.array(gold["q0"]), SEM_STEP, "SEM displacement")
     dquat = quat.cpu().numpy() - np.array(gold["quat0"])
-    assert rel(dquat, np.array(gold["quat"]) - np.array(gold["quat0"])) < 1e-8
+    assert_close(dquat, np.array(gold["quat"]) - np.array(gold["quat0"]), SEM_STEP, "SEM orientation increment")
     # benchmark configuration (rel. residual 1e-8): every solve meets it and the
     # step stays within the tolerance band of the oracle's
     g8 = B.grid_for(w, rtol=1e-8)
@@ -98,6 +99,7 @@ def test_matvec_large_grid(B, periodic, wall_speed):
     x = np.random.default_rng(3).standard_normal(g.n_total)
     y0 = saddle.apply(og, ob, w.eta, x)
     y = g.apply_saddle(dev(x)).cpu().numpy()
-    assert rel(y, y0) < 1e-11
-    y32 = g.apply_saddle(torch.tensor(x, dtype=torch.float32, device="cuda")).double().cpu().numpy()
-    assert rel(y32, y0) < 1e-5
+    assert_close_blocks(y, y0, g.layout(), F64_MATVEC, "FP64 matvec")
+    x32 = x.astype(np.float32).astype(np.float64)
+    y32 = g.apply_saddle(torch.tensor(x32, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+    assert_close_blocks(y32, saddle.apply(og, ob, w.eta, x32), g.layout(), F32_MATVEC, "FP32 matvec")

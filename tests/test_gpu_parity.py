@@ -2,10 +2,12 @@
 C ABI (paper_1901_06427_gb300.binding), on small seeded cases that span
 several thread blocks with ragged tails and every boundary combination.
 
-Gates: binning bit-exact; Philox normals to a few ulps (words are identical:
-the normals differ only through log/sincos rounding); FP64 operators within
-1e-11 relative (the saddle matvec) or 1e-13 (single operators); FP32 matvec
-within 1e-5; solved body velocities within 1e-8 relative."""
+Gates, all element by element (gpu_common.assert_close: |a_i - b_i| <= rtol
+|b_i| + floor ||b||_inf, per block of the saddle layout): binning and Philox
+words bit-exact; Philox normals to a few ulps (they differ only through
+log/sincos rounding); FP64 single operators rtol 1e-12, the FP64 saddle matvec
+1e-11; the FP32 matvec 1e-5 on the same FP32-rounded input; solved
+quantities 1e-8."""
 import numpy as np
 import pytest
 
@@ -13,7 +15,8 @@ torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
 from oracle import saddle, solve, ib, binning, philox, noise, forces, sem  # noqa: E402
-from gpu_common import case, rel, CASES  # noqa: E402
+from gpu_common import (case, rel, CASES, assert_close, assert_close_blocks, F64_OP, F64_MATVEC,  # noqa: E402
+                        F32_MATVEC, SOLVED, SEM_STEP)
 
 pytestmark = pytest.mark.gpu
 
@@ -51,6 +54,18 @@ def test_binning_exact_cell_boundaries(B):
     assert np.array_equal(perm.cpu().numpy(), p0) and np.array_equal(off.cpu().numpy(), o0)
 
 
+@pytest.mark.parametrize("n_blocks,first", [(1, 0), (3, 5), (1001, 0), (65536 + 7, 123456789)])
+def test_philox_words_bit_exact(B, n_blocks, first):
+    """Raw Philox4x64-10 words of the GPU equal the oracle's bit for bit
+    (the oracle's words are themselves pinned to numpy's Philox)."""
+    w, og, ob = case("walls")
+    g = B.grid_for(w)
+    for seed, step, attempt, purpose in ((0xDEADBEEF12345, 77, 3, 1), (2 ** 64 - 1, 2 ** 63 + 5, 2 ** 32 - 1, 2)):
+        got = g.philox_words(seed, step, attempt, purpose, n_blocks, first).cpu().numpy().view(np.uint64)
+        want = philox.words(seed, step, attempt, purpose, n_blocks, first_block=first)
+        assert np.array_equal(got, want)
+
+
 @pytest.mark.parametrize("count", [1, 3, 4, 1001, 65536 + 7])
 def test_philox_normals(B, count):
     w, og, ob = case("walls")
@@ -67,7 +82,7 @@ def test_stochastic_forcing(B, name):
     g = B.grid_for(w)
     f = g.stochastic_forcing(1.3, 0.02, 99, 5, 1).cpu().numpy()
     f0 = noise.fluid_forcing(og, w.eta, 1.3, 0.02, 99, 5, 1)
-    assert rel(f, f0) < 1e-13
+    assert_close(f, f0, F64_OP, "fluid forcing")
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -78,10 +93,11 @@ def test_spread_and_interpolate(B, name):
     lam = rng.standard_normal(3 * w.n_blobs)
     v = rng.standard_normal(og.N_f)
     r = ob.positions()
-    assert rel(g.blob_positions().cpu().numpy(), r) < 1e-15
-    assert rel(g.spread(dev(lam)).cpu().numpy(), ib.spread(og, r, lam)) < 1e-13
-    assert rel(g.interpolate(dev(v)).cpu().numpy(), ib.interpolate(og, r, v)) < 1e-13
-    assert rel(g.interpolate(dev(v), with_walls=True).cpu().numpy(), ib.interpolate(og, r, v, with_walls=True)) < 1e-13
+    assert_close(g.blob_positions().cpu().numpy(), r, (1e-15, 1e-15), "blob positions")
+    assert_close(g.spread(dev(lam)).cpu().numpy(), ib.spread(og, r, lam), F64_OP, "spread")
+    assert_close(g.interpolate(dev(v)).cpu().numpy(), ib.interpolate(og, r, v), F64_OP, "interpolate")
+    assert_close(g.interpolate(dev(v), with_walls=True).cpu().numpy(), ib.interpolate(og, r, v, with_walls=True),
+                 F64_OP, "interpolate with moving-wall ghosts")
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -91,20 +107,18 @@ def test_apply_saddle_fp64(B, name):
     x = np.random.default_rng(3).standard_normal(g.n_total)
     y = g.apply_saddle(dev(x)).cpu().numpy()
     y0 = saddle.apply(og, ob, w.eta, x)
-    assert rel(y, y0) < 1e-11
     lay = g.layout()
     assert lay == saddle.layout(og, ob)
-    for i in range(6):
-        assert rel(y[lay[i]:lay[i + 1]], y0[lay[i]:lay[i + 1]]) < 1e-11
+    assert_close_blocks(y, y0, lay, F64_MATVEC, "FP64 matvec")
 
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_apply_saddle_fp32(B, name):
     w, og, ob = case(name)
     g = B.grid_for(w)
-    x = np.random.default_rng(4).standard_normal(g.n_total)
+    x = np.random.default_rng(4).standard_normal(g.n_total).astype(np.float32).astype(np.float64)
     y = g.apply_saddle(dev(x, torch.float32)).double().cpu().numpy()
-    assert rel(y, saddle.apply(og, ob, w.eta, x)) < 1e-5
+    assert_close_blocks(y, saddle.apply(og, ob, w.eta, x), g.layout(), F32_MATVEC, "FP32 matvec")
 
 
 @pytest.mark.parametrize("name", ["walls", "xper_moving"])
@@ -117,7 +131,7 @@ def test_body_forces(B, name):
     g = B.grid_for(w)
     F = g.body_forces(B.sem_params(pot)).cpu().numpy()
     F0 = forces.body_forces(og, ob, pot).ravel()
-    assert rel(F, F0) < 1e-13
+    assert_close(F, F0, F64_OP, "body forces")
 
 
 @pytest.mark.parametrize("name", ["walls", "xper_moving", "yzper"])
@@ -128,8 +142,8 @@ def test_stokes_solve(B, name):
     v, pi, info = g.stokes_solve(dev(f))
     v0, p0 = solve.stokes(og, w.eta, f)
     assert info["rel_residual"] <= 1e-12
-    assert rel(v.cpu().numpy(), v0) < 1e-9
-    assert rel(pi.cpu().numpy(), p0) < 1e-9
+    assert_close(v.cpu().numpy(), v0, SOLVED, "Stokes velocity")
+    assert_close(pi.cpu().numpy(), p0, SOLVED, "Stokes pressure")
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -140,10 +154,10 @@ def test_mobility_solve(B, name):
     f = saddle.rhs(og, ob, w.eta, F=w.force_torque, slip=w.slip)
     x0 = solve.constrained(og, ob, w.eta, f)
     assert info["rel_residual"] <= 1e-12
-    assert rel(U.cpu().numpy(), x0[-6 * w.n_bodies:]) < 1e-8
+    assert_close(U.cpu().numpy(), x0[-6 * w.n_bodies:], SOLVED, "U")
     xg = x.cpu().numpy()
     assert np.linalg.norm(saddle.apply(og, ob, w.eta, xg) - f) <= 1e-11 * np.linalg.norm(f)
-    assert rel(xg, x0) < 1e-8
+    assert_close_blocks(xg, x0, g.layout(), SOLVED, "solution")
 
 
 def test_mobility_solve_with_fluid_forcing(B):
@@ -153,7 +167,7 @@ def test_mobility_solve_with_fluid_forcing(B):
     U, info = g.mobility_solve(dev(w.force_torque), fluid_rhs=dev(fl))
     f = saddle.rhs(og, ob, w.eta, F=w.force_torque, f_fluid=fl)
     x0 = solve.constrained(og, ob, w.eta, f)
-    assert rel(U.cpu().numpy(), x0[-6 * w.n_bodies:]) < 1e-8
+    assert_close(U.cpu().numpy(), x0[-6 * w.n_bodies:], SOLVED, "U")
 
 
 @pytest.mark.parametrize("name", ["walls", "xper_moving", "ragged42"])
@@ -165,8 +179,9 @@ def test_sem_step(B, name):
     ref = sem.sem_step(og, ob, w.eta, 1.0, 0.05, w.potentials, seed=11, step=2, attempt=1)
     assert st == 0 and not ref["reject"]
     dq = q.cpu().numpy().reshape(-1, 3) - w.q
-    assert rel(dq, ref["q"] - w.q) < 1e-8
-    assert rel(quat.cpu().numpy() - w.quat.ravel(), ref["quat"].ravel() - w.quat.ravel()) < 1e-8
+    assert_close(dq, ref["q"] - w.q, SEM_STEP, "SEM displacement")
+    assert_close(quat.cpu().numpy() - w.quat.ravel(), ref["quat"].ravel() - w.quat.ravel(), SEM_STEP,
+                 "SEM orientation increment")
 
 
 def test_sem_step_rejects_unphysical_configuration(B):
