@@ -52,8 +52,13 @@ def parse():
                     help="run the solves launch by launch instead of as CUDA graphs (profilers do not see "
                          "kernels inside graphs with conditional nodes)")
     ap.add_argument("--cpu-sample-rhs", type=int, default=16)
-    ap.add_argument("--ensemble", type=int, default=0,
+    ap.add_argument("--timed-only", action="store_true",
+                    help="stop after the timed SEM steps (for launch-list profiles of the step alone)")
+    ap.add_argument("--no-monolayer", action="store_true", help="skip the driven-monolayer leg")
+    ap.add_argument("--monolayer-only", action="store_true", help="run only the driven-monolayer leg")
+    ap.add_argument("--ensemble", type=int, default=256,
                     help="also time a batched ensemble of this many systems (0: skip)")
+    ap.add_argument("--ensemble-only", action="store_true", help="run only the ensemble leg")
     ap.add_argument("--ensemble-steps", type=int, default=2)
     ap.add_argument("--workers", type=int, default=16)
     return ap.parse_args()
@@ -234,15 +239,16 @@ def run_matvec_large(B, torch, hbm, n=256, reps=20):
 CLASS_INFO = {
     "matvec": ("k_stokes_cols_f64 + k_saddle_bodies (saddle matvec)", "fp64", 152),
     "smooth": ("k_vel_rbgs_u (red-black half sweep, finest velocity level)", "fp32", 152),
-    "dot": ("k_dot_part (CGS2 inner products, column sums finished in its last block)", "fp64", 152),
-    "axpy": ("k_multi_axpy (norm of the result finished in its last block)", "fp64", 152),
-    "coarse": ("k_fd_solve (exact coarse-level solve, one 8-CTA cluster per grid)", "fp32", 16),
+    "dot": ("k_gs_dot (Gram-Schmidt inner products, register-blocked over 8 columns, sums finished in the "
+            "last block)", "fp64", 152),
+    "axpy": ("k_gs_axpy (Gram-Schmidt multi-axpy, norm of the result finished in the last block)", "fp64", 152),
+    "coarse": ("k_fdw_xy + k_fdw_z + k_fdw_xy (exact level solve by fast diagonalisation over the whole GPU: "
+               "x/y transforms per plane, z transform per column)", "fp32", 152),
 }
 # DRAM bytes (read + write) per algorithmic byte from the ncu captures
 # summarised under profiles/ (kernel as it stands); traffic is reported for
-# these classes only.  dot: k_dot_part<double> on the two-sphere grid, 37-38
-# columns, cold caches (profiles/k_dot_part_fp64_two_sphere_48x48x32.md).
-TRAFFIC_RATIO = {"dot": 1.03}
+# these classes only, and is null for a class whose kernel changed since.
+TRAFFIC_RATIO = {}
 
 
 def roofline_for(top, kms, klaunch, kbytes, kflops):
@@ -319,6 +325,67 @@ def run_adjoint(B, torch, reps=2):
     return out
 
 
+# --------------------------------------------------------- monolayer leg
+def _step_error(a, b):
+    """Relative error of an increment a against b: max element-wise
+    |a - b| / max|b| and the 2-norm ratio."""
+    import numpy as np
+    a = np.asarray(a, dtype=float).ravel()
+    b = np.asarray(b, dtype=float).ravel()
+    sc = max(float(np.abs(b).max()), 1e-300)
+    return {"max_abs_over_max": float(np.abs(a - b).max() / sc),
+            "norm": float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))}
+
+
+def run_monolayer(B, torch, steps=5, warmup=2, wall_speed=0.5):
+    """Driven monolayer (Sec. V.B): 1024 12-blob spheres in a 384x96x12
+    channel periodic in x, top wall at (U, 0, 0), U = 0.5, Yukawa + per-blob
+    wall + substrate potentials, dt = 0.02, rel. res. 1e-8; SEM steps/s with
+    FP32 kernels inside FP64 refinement and in plain FP64, and the refined
+    step's error against the FP64 step from the same state and noise."""
+    import numpy as np
+    import workloads
+    w = workloads.driven_monolayer(wall_speed=wall_speed)
+    p = B.sem_params(w.potentials, dt=w.dt, kT=w.kT)
+    out = {"workload": w.name, "grid": list(w.n), "bodies": w.n_bodies, "blobs": w.n_blobs,
+           "wall_speed": wall_speed, "dt": w.dt, "rtol": 1e-8}
+    stream = torch.cuda.current_stream()
+    first = {}
+    for label, prec in (("fp32_refined", B.FP32_REFINED), ("fp64", B.FP64)):
+        g = B.grid_for(w, precision=prec, rtol=1e-8)
+        q = torch.tensor(w.q.ravel(), device="cuda")
+        quat = torch.tensor(w.quat.ravel(), device="cuda")
+        # one step from the initial state with fixed noise, for the error
+        st, info = g.sem_step(p, w.seed, 0, 0, q, quat)
+        first[label] = (q.cpu().numpy() - w.q.ravel(), quat.cpu().numpy() - w.quat.ravel(), st)
+        for k in range(warmup - 1):
+            g.sem_step(p, w.seed, 1 + k, 0, q, quat)
+        torch.cuda.synchronize()
+        iters, refs, rejected = [], [], 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(steps):
+            st, info = g.sem_step(p, w.seed, 100 + k, 0, q, quat)
+            rejected += int(st == B.EREJECT)
+            iters.append([info[key]["iterations"] for key in ("solve_rfd", "solve_stokes", "solve_main")])
+            refs.append([info[key]["refinements"] for key in ("solve_rfd", "solve_stokes", "solve_main")])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[label] = {"steps_per_s": 1000.0 / ms, "ms_per_step": ms, "steps": steps,
+                      "krylov_iterations_per_step": [int(round(x)) for x in np.mean(iters, axis=0)],
+                      "refinements_per_step": [round(float(x), 2) for x in np.mean(refs, axis=0)],
+                      "rejected_steps": rejected}
+        g.close()
+        del q, quat
+        torch.cuda.empty_cache()
+    out["refined_over_fp64"] = out["fp32_refined"]["steps_per_s"] / out["fp64"]["steps_per_s"]
+    dq_r, dqt_r, _ = first["fp32_refined"]
+    dq_f, dqt_f, _ = first["fp64"]
+    out["refined_error_vs_fp64_step"] = {"dq": _step_error(dq_r, dq_f), "dquat": _step_error(dqt_r, dqt_f)}
+    return out
+
+
 # ---------------------------------------------------------------- ensemble
 def run_ensemble(args, B, torch):
     """Batched ensemble: independent cuboids n ~ U{16, 20, ..., 48} with 1-16
@@ -379,6 +446,14 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"matvec_hbm": run_matvec_large(B, torch, hbm, n=args.matvec_n)}), flush=True)
         return
+    if args.monolayer_only:
+        if rank == 0:
+            print(json.dumps({"monolayer": run_monolayer(B, torch)}), flush=True)
+        return
+    if args.ensemble_only:
+        if rank == 0:
+            print(json.dumps({"ensemble": run_ensemble(args, B, torch)}), flush=True)
+        return
     w = workloads.two_sphere_cavity(steps=args.steps)
     g = B.grid_for(w, rtol=1e-8)
     p = B.sem_params(w.potentials, dt=w.dt, kT=w.kT)
@@ -437,6 +512,11 @@ def run_ours(args):
     # roofline pass: the same steps with CUDA events around every launch of one
     # kernel class (the restart cycles then run launch by launch, because event
     # records cannot sit inside the captured conditional graph bodies)
+    if args.timed_only:
+        if rank == 0:
+            print(json.dumps({"value": whole_job_rate(world, args.steps, step_ms), "unit": "SEM steps/s",
+                              "ms_per_step": step_ms / args.steps, "gpu_launches": launches}), flush=True)
+        return
     shares = {}
     classes = list(TIMER_NAMES) if args.roofline_kernel == "auto" else [args.roofline_kernel]
     nrep = 2
@@ -507,7 +587,8 @@ def run_ours(args):
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
             "krylov_iterations_per_step": [list(map(int, np.mean(np.array(state["iters"]), axis=0)))] if state["iters"] else None,
             "rejected_steps": state["rejects"], "wall_s": t_wall,
-            "body_block_warm_starts": g.body_block_info()[1]}
+            "body_block_warm_starts": g.body_block_info()[1],
+            "gram_schmidt": dict(zip(["arnoldi_iterations", "second_passes"], g.krylov_stats()))}
     if args.sem_only:
         print(json.dumps(line), flush=True)
         return
@@ -546,6 +627,8 @@ def run_ours(args):
         hbm = 6800.0
     line["matvec_hbm"] = run_matvec_large(B, torch, hbm, n=args.matvec_n)
     line["adjoint"] = run_adjoint(B, torch)
+    if not args.no_monolayer:
+        line["monolayer"] = run_monolayer(B, torch)
     line["autotuned_blocks"] = dict(zip(["stokes_fp64", "stokes_fp32", "vel_sweep", "p_sweep"], g.tuned_blocks()))
     if args.ensemble:
         line["ensemble"] = run_ensemble(args, B, torch)

@@ -221,6 +221,15 @@ int rbfib_batch_sem_step(rbfib_batch* b, const rbfib_sem_params* params, const u
  * pointer may be NULL. */
 int rbfib_body_block_info(const rbfib_grid* g, int32_t* dense, int64_t* warm_starts);
 
+/* Gram-Schmidt statistics of the grid's Krylov solves since it was created:
+ * Arnoldi iterations and how many of them took the second (re-
+ * orthogonalising) pass of classical Gram-Schmidt.  The second pass runs only
+ * when the first leaves less than a fraction tau of the new vector's norm
+ * (tau = 1e-3 for FP64 bases, 1/sqrt(2) for FP32 ones); otherwise the
+ * orthogonality lost is at most about eps / tau.  Either pointer may be
+ * NULL. */
+int rbfib_krylov_stats(const rbfib_grid* g, int64_t* iterations, int64_t* second_passes);
+
 /* Threads per block the autotuner picked for this grid's finest-level
  * kernels: out[0] FP64 Stokes operator, out[1] FP32 Stokes operator (0 on
  * uniform spacing, whose Stokes kernels have fixed tile shapes), out[2]

@@ -89,6 +89,7 @@ def lib():
                                                  ctypes.c_char_p, ctypes.c_size_t], I32),
             "rbfib_launch_count": ([], U64),
             "rbfib_tuned_blocks": ([P, ctypes.POINTER(ctypes.c_int32)], I32),
+            "rbfib_krylov_stats": ([P, ctypes.POINTER(I64), ctypes.POINTER(I64)], I32),
             "rbfib_create_batch": ([I32, ctypes.POINTER(GridDesc), I32, ctypes.POINTER(P)], I32),
             "rbfib_destroy_batch": ([P], None),
             "rbfib_batch_grid": ([P, I32], P),
@@ -353,6 +354,12 @@ class Grid:
         out = (ctypes.c_int32 * 4)()
         self._check(lib().rbfib_tuned_blocks(self._h, out))
         return list(out)
+
+    def krylov_stats(self):
+        """(Arnoldi iterations, second Gram-Schmidt passes taken) since creation."""
+        it, sp = ctypes.c_int64(), ctypes.c_int64()
+        self._check(lib().rbfib_krylov_stats(self._h, ctypes.byref(it), ctypes.byref(sp)))
+        return it.value, sp.value
 
     def body_forces(self, params):
         out = torch.empty(6 * max(self.n_bodies, 1), dtype=torch.float64, device="cuda")

@@ -10,7 +10,9 @@
 // V-cycles; the bases are built on the host once per grid and checked
 // against the explicit 1D matrices.  Each grid is solved by one cluster of
 // CTAs that split its z-planes (see k_fd_solve).
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 
 #include <cooperative_groups.h>
@@ -259,14 +261,253 @@ __global__ void __cluster_dims__(kFDCtas, 1, 1) __launch_bounds__(kFDThreads)
   if (rz == 8) fd_columns<8>(cl, A, Q2, QT2, L0, L1, L2, G.scale, e0, e1, e2, pz, rank);
   else if (rz == 16) fd_columns<16>(cl, A, Q2, QT2, L0, L1, L2, G.scale, e0, e1, e2, pz, rank);
   else if (rz == 24) fd_columns<24>(cl, A, Q2, QT2, L0, L1, L2, G.scale, e0, e1, e2, pz, rank);
-  else fd_columns<32>(cl, A, Q2, QT2, L0, L1, L2, G.scale, e0, e1, e2, pz, rank);
+  else if (rz == 32) fd_columns<32>(cl, A, Q2, QT2, L0, L1, L2, G.scale, e0, e1, e2, pz, rank);
+  else if (rz == 40) fd_columns<40>(cl, A, Q2, QT2, L0, L1, L2, G.scale, e0, e1, e2, pz, rank);
+  else fd_columns<48>(cl, A, Q2, QT2, L0, L1, L2, G.scale, e0, e1, e2, pz, rank);
   cl.sync();
   fd_pass_xy<1>(A, B, QT1, e0, e1, np);
   fd_pass_xy<0>(B, A, QT0, e0, e1, np);
   for (int t = threadIdx.x; t < np * pl; t += blockDim.x) u[G.off + (long long)z0 * pl + t] = A[t];
 }
 
+// ------------------------------------------------------------------------
+// The same solve spread over the whole GPU, in three launches: the forward x
+// and y transforms of every z-plane (one CTA per plane of every grid), the z
+// transform, eigenvalue scaling and backward z transform of every column
+// (one CTA per 32 adjacent columns), and the backward y and x transforms of
+// every plane.  The level arrays stay in L2 between the launches.  On a fine
+// level (up to kFDLine points per axis: the whole two-sphere grid) the
+// cluster kernel above leaves most SMs idle; this form uses a CTA per plane.
+
+// 16 x 16 threads per plane, each owning a 3 x 3 register tile of the (at
+// most 48 x 48) plane.
+constexpr int kFWT = 16;
+constexpr int kFWR = kFDLine / kFWT;
+static_assert(kFWT * kFWR == kFDLine, "register tile covers a line");
+
+RBFIB_DEVFN int fd_planes(const FDGrid& G) { return G.e[2]; }
+RBFIB_DEVFN int fd_col_tiles(const FDGrid& G) { return (G.e[0] * G.e[1] + 31) / 32; }
+
+// Block index -> (grid gi, item k within the grid), items counted by f.
+template <int (*F)(const FDGrid&)>
+RBFIB_DEVFN void fd_item(const FDParams& P, int& k, int& gi) {
+  gi = 0;
+  while (gi < P.ng - 1 && k >= F(P.g[gi])) { k -= F(P.g[gi]); ++gi; }
+}
+
+// One plane: out = A_y (in A_x), the 1D transforms along x then y, with the
+// forward bases (dir 0) or their transposes (dir 1).
+// cp.async helpers: 16-byte and 4-byte global -> shared copies, one wait.
+RBFIB_DEVFN void fdw_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src) : "memory");
+}
+RBFIB_DEVFN void fdw_cp4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src) : "memory");
+}
+RBFIB_DEVFN void fdw_wait() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// Stages the first e columns of the e rows of a basis table (rows padded to
+// fd_pad(e) floats, 16-byte aligned) into M[kFDLine][kFDLine] by 16-byte
+// copies (the words past e carry the table's zero padding, or a neighbouring
+// column that is never read).
+RBFIB_DEVFN void fdw_stage_basis(float (*M)[kFDLine], const float* tab, int e) {
+  const int ep = fd_pad(e), wpr = (e + 3) >> 2;
+  for (int t = threadIdx.x; t < e * wpr; t += blockDim.x) {
+    const int r = t / wpr, w = t - r * wpr;
+    fdw_cp16(&M[r][4 * w], tab + r * ep + 4 * w);
+  }
+}
+
+__global__ void __launch_bounds__(kFWT * kFWT) k_fdw_xy(FDParams P, const float* __restrict__ in,
+                                                         float* __restrict__ out, int dir) {
+  pdl_entry();
+  __shared__ float X[kFDLine][kFDLine + 1];
+  __shared__ float T[kFDLine][kFDLine + 1];
+  __shared__ __align__(16) float Mx[kFDLine][kFDLine];
+  __shared__ __align__(16) float My[kFDLine][kFDLine];
+  int k = blockIdx.x, gi;
+  fd_item<fd_planes>(P, k, gi);
+  const FDGrid& G = P.g[gi];
+  const int e0 = G.e[0], e1 = G.e[1], p0 = fd_pad(e0), p1 = fd_pad(e1);
+  const float* Q0 = P.tab + G.tab0;
+  const float* QT0 = Q0 + e0 * p0;
+  const float* Q1 = QT0 + e0 * p0 + p0;
+  const float* QT1 = Q1 + e1 * p1;
+  // every copy issued before the one wait
+  fdw_stage_basis(Mx, dir ? QT0 : Q0, e0);
+  fdw_stage_basis(My, dir ? QT1 : Q1, e1);
+  const int tx = threadIdx.x % kFWT, ty = threadIdx.x / kFWT;
+  const float* src = in + G.off + (long long)k * e0 * e1;
+  for (int r = ty; r < e1; r += kFWT)
+    for (int c = tx; c < e0; c += kFWT) fdw_cp4(&X[r][c], src + r * e0 + c);
+  fdw_wait();
+  __syncthreads();
+  // T[j][c] = sum_i X[j][i] A_x[i][c]; tile rows j >= e1 and columns c >= e0
+  // hold values that are never read back (the y pass sums j < e1, only
+  // c < e0 is stored)
+  float acc[kFWR][kFWR];
+#pragma unroll
+  for (int a = 0; a < kFWR; ++a)
+#pragma unroll
+    for (int b = 0; b < kFWR; ++b) acc[a][b] = 0.f;
+#pragma unroll 4
+  for (int i = 0; i < e0; ++i) {
+    float xv[kFWR], mv[kFWR];
+#pragma unroll
+    for (int a = 0; a < kFWR; ++a) xv[a] = X[ty + kFWT * a][i];
+#pragma unroll
+    for (int b = 0; b < kFWR; ++b) mv[b] = Mx[i][tx + kFWT * b];
+#pragma unroll
+    for (int a = 0; a < kFWR; ++a)
+#pragma unroll
+      for (int b = 0; b < kFWR; ++b) acc[a][b] = fmaf(xv[a], mv[b], acc[a][b]);
+  }
+#pragma unroll
+  for (int a = 0; a < kFWR; ++a)
+#pragma unroll
+    for (int b = 0; b < kFWR; ++b) {
+      T[ty + kFWT * a][tx + kFWT * b] = acc[a][b];
+      acc[a][b] = 0.f;
+    }
+  __syncthreads();
+  // out[r][c] = sum_j A_y[j][r] T[j][c]
+#pragma unroll 4
+  for (int j = 0; j < e1; ++j) {
+    float mv[kFWR], tv[kFWR];
+#pragma unroll
+    for (int a = 0; a < kFWR; ++a) mv[a] = My[j][ty + kFWT * a];
+#pragma unroll
+    for (int b = 0; b < kFWR; ++b) tv[b] = T[j][tx + kFWT * b];
+#pragma unroll
+    for (int a = 0; a < kFWR; ++a)
+#pragma unroll
+      for (int b = 0; b < kFWR; ++b) acc[a][b] = fmaf(mv[a], tv[b], acc[a][b]);
+  }
+  float* dst = out + G.off + (long long)k * e0 * e1;
+#pragma unroll
+  for (int a = 0; a < kFWR; ++a)
+#pragma unroll
+    for (int b = 0; b < kFWR; ++b) {
+      const int r = ty + kFWT * a, c = tx + kFWT * b;
+      if (r < e1 && c < e0) dst[r * e0 + c] = acc[a][b];
+    }
+}
+
+// 32 adjacent columns (fixed x, y; all z) of one grid, in place: forward z
+// transform, division by s (l_x + l_y + l_z) (the zero mode of a singular
+// grid dropped), backward z transform.  Thread (column ci, group gr) forms
+// the coefficients gr, gr + 8, ... of its column.
+__global__ void __launch_bounds__(256) k_fdw_z(FDParams P, float* __restrict__ data) {
+  pdl_entry();
+  __shared__ float Z[kFDLine][33];
+  __shared__ __align__(16) float Mz[kFDLine][kFDLine];
+  __shared__ __align__(16) float MzT[kFDLine][kFDLine];
+  int tile = blockIdx.x, gi;
+  fd_item<fd_col_tiles>(P, tile, gi);
+  const FDGrid& G = P.g[gi];
+  const int e0 = G.e[0], e1 = G.e[1], e2 = G.e[2], pl = e0 * e1;
+  const int p0 = fd_pad(e0), p1 = fd_pad(e1), p2 = fd_pad(e2);
+  const float* L0 = P.tab + G.tab0 + 2 * e0 * p0;
+  const float* L1 = L0 + p0 + 2 * e1 * p1;
+  const float* Q2 = L1 + p1;
+  const float* QT2 = Q2 + e2 * p2;
+  const float* L2 = QT2 + e2 * p2;
+  fdw_stage_basis(Mz, Q2, e2);
+  fdw_stage_basis(MzT, QT2, e2);
+  const int col0 = tile * 32;
+  float* base = data + G.off;
+  {
+    const int c = threadIdx.x & 31;
+    if (col0 + c < pl)
+      for (int kk = threadIdx.x >> 5; kk < e2; kk += 8) fdw_cp4(&Z[kk][c], base + (long long)kk * pl + col0 + c);
+  }
+  fdw_wait();
+  __syncthreads();
+  const int ci = threadIdx.x & 31, gr = threadIdx.x >> 5;
+  const int col = col0 + ci;
+  const bool live = col < pl;
+  const float sxy = live ? L0[col % e0] + L1[col / e0] : 0.f;
+  float y[kFDLine / 8];
+#pragma unroll
+  for (int q = 0; q < kFDLine / 8; ++q) {
+    const int c = gr + 8 * q;
+    float acc = 0.f;
+    if (c < e2 && live) {
+#pragma unroll 4
+      for (int kk = 0; kk < e2; ++kk) acc = fmaf(Mz[kk][c], Z[kk][ci], acc);
+      const float s = G.scale * (sxy + L2[c]);
+      acc = s > 0.f ? acc / s : 0.f;
+    }
+    y[q] = acc;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kFDLine / 8; ++q) {
+    const int c = gr + 8 * q;
+    if (c < e2) Z[c][ci] = y[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kFDLine / 8; ++q) {
+    const int kk = gr + 8 * q;
+    if (kk < e2 && live) {
+      float acc = 0.f;
+#pragma unroll 4
+      for (int c = 0; c < e2; ++c) acc = fmaf(MzT[c][kk], Z[c][ci], acc);
+      base[(long long)kk * pl + col] = acc;
+    }
+  }
+}
+
 }  // namespace
+
+// Whole-GPU form of fd_solve: tmp holds the level's transformed coefficients
+// (as many floats as u).
+void fd_solve_wide(const FDParams& P, float* u, const float* rhs, float* tmp, cudaStream_t s) {
+  int planes = 0, tiles = 0;
+  for (int g = 0; g < P.ng; ++g) {
+    planes += P.g[g].e[2];
+    tiles += (P.g[g].e[0] * P.g[g].e[1] + 31) / 32;
+  }
+  launch_k(k_fdw_xy, planes, kFWT * kFWT, 0, s, P, rhs, tmp, 0);
+  note_launch();
+  launch_k(k_fdw_z, tiles, 256, 0, s, P, tmp);
+  note_launch();
+  launch_k(k_fdw_xy, planes, kFWT * kFWT, 0, s, P, (const float*)tmp, u, 1);
+  note_launch();
+}
+
+// The whole-GPU form for levels whose largest grid has more than
+// kFDWideMin points (the cluster kernel is faster on the small coarse levels,
+// e.g. 17 against 19 us at 24 x 24 x 16); RBFIB_FD_WIDE_MIN overrides the
+// threshold (read once).
+constexpr long long kFDWideMin = 32768;
+bool fd_use_wide(const FDParams& P) {
+  static const long long lim = [] {
+    const char* e = std::getenv("RBFIB_FD_WIDE_MIN");
+    return e ? std::atoll(e) : kFDWideMin;
+  }();
+  long long m = 0;
+  for (int g = 0; g < P.ng; ++g) m = std::max(m, (long long)P.g[g].e[0] * P.g[g].e[1] * P.g[g].e[2]);
+  return m > lim;
+}
+
+// Longest line solved by fast diagonalisation: kFDLine, or a smaller value
+// from RBFIB_FD_LINE (read once; for measurements of the multigrid levels
+// above the exact solve).
+int fd_line_limit() {
+  static const int lim = [] {
+    const char* e = std::getenv("RBFIB_FD_LINE");
+    const int v = e ? std::atoi(e) : kFDLine;
+    return (v >= 1 && v <= kFDLine) ? v : kFDLine;
+  }();
+  return lim;
+}
 
 bool fd_plan(const Dims& d, bool faces, double eta, std::vector<float>& tab, FDParams& P, std::string& why) {
   P = FDParams{};
@@ -281,7 +522,7 @@ bool fd_plan(const Dims& d, bool faces, double eta, std::vector<float>& tab, FDP
     for (int ax = 0; ax < 3; ++ax) {
       G.e[ax] = e[ax];
       n *= e[ax];
-      if (e[ax] < 1 || e[ax] > kFDLine) return fail("extent");
+      if (e[ax] < 1 || e[ax] > fd_line_limit()) return fail("extent");
     }
     if (n > kFDMaxPoints) return fail("points");
     G.off = faces ? d.fo[g] : 0;

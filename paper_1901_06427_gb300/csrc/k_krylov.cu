@@ -4,6 +4,7 @@
 // final sum, deterministic), fused multi-axpy with the norm of the result,
 // Givens rotations and the small triangular solve on the device.
 #include <cstdint>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -60,6 +61,25 @@ RBFIB_DEVFN bool finish_last(double* slots, double v, unsigned* counter) {
 template <typename T>
 RBFIB_DEVFN T ldcg_t(const T* p) { return __ldcg(p); }
 
+// In the last block of a first-pass multi-axpy (all threads): with
+// nrm2w = ||w'||^2 and the projection coefficients coef[0..k), decide whether
+// the second pass is needed and reset its coefficients (see ReorthCtl).
+RBFIB_DEVFN void reorth_decide(const ReorthCtl& ctl, double nrm2w, const double* coef, int k) {
+  double hh = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const double c = coef[i];
+    hh = fma(c, c, hh);
+    ctl.h2[i] = 0.0;
+  }
+  hh = block_sum(hh);
+  if (threadIdx.x == 0) {
+    const int again = (nrm2w < ctl.tau2 * (nrm2w + hh)) ? 1 : 0;
+    ctl.flag[0] = again;
+    ctl.flag[1] += again;   // second passes taken (reset by the solver)
+    if (ctl.use_handle) cudaGraphSetConditional(ctl.handle, (unsigned)again);
+  }
+}
+
 // Per column: the blocks' shares of the unweighted sum w . V_col over [0, n)
 // (16-byte loads when vec) go to part[col * gridDim.x + block]; the last
 // block to finish a column (atomic counter, reset afterwards) adds them up
@@ -71,8 +91,9 @@ RBFIB_DEVFN T ldcg_t(const T* p) { return __ldcg(p); }
 template <typename T>
 __global__ void k_dot_part(const T* __restrict__ w, const T* __restrict__ V, i64 ldv, i64 n, i64 nfl, double wf,
                            double* __restrict__ part, unsigned* __restrict__ cnt, double* __restrict__ out,
-                           int vec) {
+                           int vec, const int* __restrict__ gate) {
   pdl_entry();
+  if (gate && *gate == 0) return;
   const int col = blockIdx.y;
   const T* v = V + (i64)col * ldv;
   const i64 stride = (i64)gridDim.x * blockDim.x, t0 = (i64)blockIdx.x * blockDim.x + threadIdx.x;
@@ -118,6 +139,265 @@ __global__ void k_dot_part(const T* __restrict__ w, const T* __restrict__ V, i64
   if (threadIdx.x == 0) out[col] = s;
 }
 
+// ---------------------------------------------------------------------------
+// Register-blocked Gram-Schmidt sweeps (16-byte aligned vectors).
+//
+// A block covers chunks of 256 * R 16-byte vectors (R per thread, kept in
+// registers) of the rows; blockIdx.y picks a group of kCG basis columns.  w
+// is loaded once per chunk and column group (not once per column), so a
+// thread issues R independent loads per column and kCG columns per group
+// before it needs their products: enough loads in flight to keep the FP64
+// pipe, the bound of these sweeps on GB300, busy.  The per-column sums of a
+// block are reduced by a butterfly transpose within each warp (each lane
+// ends with one column's warp total after kCG + 1 additions instead of
+// 5 kCG) and across warps through shared memory.
+constexpr int kCG = 8;
+
+template <typename T> struct Vec16;
+template <> struct Vec16<double> { typedef double2 t; static constexpr int w = 2; typedef double acc; };
+template <> struct Vec16<float> { typedef float4 t; static constexpr int w = 4; typedef float acc; };
+
+RBFIB_DEVFN double dot16(const double2& a, const double2& b, double c) { return fma(a.y, b.y, fma(a.x, b.x, c)); }
+RBFIB_DEVFN float dot16(const float4& a, const float4& b, float c) {
+  return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, c))));
+}
+RBFIB_DEVFN void axpy16(double f, const double2& v, double2& x) { x.x = fma(f, v.x, x.x); x.y = fma(f, v.y, x.y); }
+RBFIB_DEVFN void axpy16(float f, const float4& v, float4& x) {
+  x.x = fmaf(f, v.x, x.x); x.y = fmaf(f, v.y, x.y); x.z = fmaf(f, v.z, x.z); x.w = fmaf(f, v.w, x.w);
+}
+RBFIB_DEVFN double fma_a(double a, double b, double c) { return fma(a, b, c); }
+RBFIB_DEVFN float fma_a(float a, float b, float c) { return fmaf(a, b, c); }
+constexpr int kGivensMaxCols = 128;   // largest column count of one sweep
+RBFIB_DEVFN void zero16(double2& a) { a = make_double2(0.0, 0.0); }
+RBFIB_DEVFN void zero16(float4& a) { a = make_float4(0.f, 0.f, 0.f, 0.f); }
+
+// v[0..8) per lane -> the warp total of column col = 4 b4 + 2 b3 + b2 (b =
+// bits of the lane) in every lane; lanes with (lane & 3) == 0 hold the eight
+// totals.  Works on A = float or double.
+template <typename A>
+RBFIB_DEVFN A warp_transpose_sum8(A v[kCG]) {
+  const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const A send = b4 ? v[j] : v[j + 4];
+    const A keep = b4 ? v[j + 4] : v[j];
+    v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const A send = b3 ? v[j] : v[j + 2];
+    const A keep = b3 ? v[j + 2] : v[j];
+    v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  {
+    const A send = b2 ? v[0] : v[1];
+    const A keep = b2 ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  A t = v[0];
+  t += __shfl_xor_sync(0xffffffffu, t, 2);
+  t += __shfl_xor_sync(0xffffffffu, t, 1);
+  return t;
+}
+
+// Per block: sums over the block's threads of acc[0..kCG), in FP64; the
+// result for column c is returned by thread c (c < kCG).
+template <typename A>
+RBFIB_DEVFN double block_transpose_sum8(A acc[kCG]) {
+  __shared__ double sh[8][kCG];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const A t = warp_transpose_sum8<A>(acc);
+  if ((lane & 3) == 0) sh[wid][lane >> 2] = (double)t;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < kCG) {
+    const int nw = blockDim.x >> 5;
+    for (int i = 0; i < nw; ++i) s += sh[i][threadIdx.x];
+  }
+  __syncthreads();
+  return s;
+}
+
+// out[c] = <w, V_c>_W for c < k (weight wf on the first nfl entries, 1 on the
+// rest); nv = n / Vec16::w whole vectors, the n - nv Vec16::w trailing
+// elements added by the first chunk.  Partials: part[c * gridDim.x + bx];
+// the last block to finish (one counter for the launch) adds them up with
+// the body-entry weight correction.
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_gs_dot(const T* __restrict__ w, const T* __restrict__ V, i64 ldv, int k,
+                                                i64 n, i64 nfl, double wf, double* __restrict__ part,
+                                                unsigned* __restrict__ cnt, double* __restrict__ out,
+                                                const int* __restrict__ gate) {
+  pdl_entry();
+  if (gate && *gate == 0) return;
+  typedef typename Vec16<T>::t VT;
+  typedef typename Vec16<T>::acc A;
+  constexpr int W = Vec16<T>::w;
+  const i64 nv = n / W;
+  const i64 chunk = 256 * (i64)R;
+  const i64 nchunks = (nv + chunk - 1) / chunk;
+  const int c0 = blockIdx.y * kCG;
+  const VT* w4 = reinterpret_cast<const VT*>(w);
+  A acc[kCG];
+#pragma unroll
+  for (int c = 0; c < kCG; ++c) acc[c] = (A)0;
+  for (i64 ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const i64 base = ch * chunk + threadIdx.x;
+    VT wr[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const i64 i = base + (i64)r * 256;
+      if (i < nv) wr[r] = w4[i]; else zero16(wr[r]);
+    }
+#pragma unroll
+    for (int c = 0; c < kCG; ++c) {
+      if (c0 + c < k) {
+        const VT* v4 = reinterpret_cast<const VT*>(V + (i64)(c0 + c) * ldv);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const i64 i = base + (i64)r * 256;
+          if (i < nv) acc[c] = dot16(wr[r], v4[i], acc[c]);
+        }
+      }
+    }
+  }
+  if (blockIdx.x == 0) {   // trailing elements that do not fill a 16-byte vector
+    const i64 i = nv * W + threadIdx.x;
+    if (i < n) {
+      const A x = (A)w[i];
+#pragma unroll
+      for (int c = 0; c < kCG; ++c)
+        if (c0 + c < k) acc[c] += x * (A)V[(i64)(c0 + c) * ldv + i];
+    }
+  }
+  const double s = block_transpose_sum8<A>(acc);
+  __shared__ bool last;
+  if (threadIdx.x < kCG && c0 + (int)threadIdx.x < k) {
+    part[(i64)(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(cnt, 1u);
+    last = done == gridDim.x * gridDim.y - 1;
+    if (last) *cnt = 0u;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // one warp per column: partials of the blocks, then the body entries
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = wid; c < k; c += nw) {
+    double t = 0.0, body = 0.0;
+    for (int i = lane; i < (int)gridDim.x; i += 32) t += __ldcg(part + (i64)c * gridDim.x + i);
+    if (wf != 1.0)
+      for (i64 i = nfl + lane; i < n; i += 32) body = fma((double)w[i], (double)V[(i64)c * ldv + i], body);
+    t = warp_sum(wf * t + (1.0 - wf) * body);
+    if (lane == 0) out[c] = t;
+  }
+}
+
+// w += sign * sum_{c < k} coef[c] V_c over 16-byte vectors (R per thread
+// per chunk), then, when nrm2 is not null, nrm2[0] = ||w||_W^2 of the result
+// (block sums, the last block adds them up with the body correction).
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_gs_axpy(T* __restrict__ w, const T* __restrict__ V, i64 ldv, int k,
+                                                 const double* __restrict__ coef, double sign, i64 n, i64 nfl,
+                                                 double wf, double* __restrict__ part, unsigned* __restrict__ cnt,
+                                                 double* __restrict__ nrm2, ReorthCtl ctl,
+                                                 const int* __restrict__ gate) {
+  pdl_entry();
+  if (gate && *gate == 0) return;
+  typedef typename Vec16<T>::t VT;
+  typedef typename Vec16<T>::acc A;
+  constexpr int W = Vec16<T>::w;
+  __shared__ A cf[kGivensMaxCols];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) cf[i] = (A)(sign * coef[i]);
+  __syncthreads();
+  const i64 nv = n / W;
+  const i64 chunk = 256 * (i64)R;
+  const i64 nchunks = (nv + chunk - 1) / chunk;
+  VT* w4 = reinterpret_cast<VT*>(w);
+  A nrm = (A)0;
+  for (i64 ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const i64 base = ch * chunk + threadIdx.x;
+    VT x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const i64 i = base + (i64)r * 256;
+      if (i < nv) x[r] = w4[i]; else zero16(x[r]);
+    }
+    int c = 0;
+    for (; c + 4 <= k; c += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const VT* v4 = reinterpret_cast<const VT*>(V + (i64)(c + u) * ldv);
+        const A f = cf[c + u];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const i64 i = base + (i64)r * 256;
+          if (i < nv) axpy16(f, v4[i], x[r]);
+        }
+      }
+    }
+    for (; c < k; ++c) {
+      const VT* v4 = reinterpret_cast<const VT*>(V + (i64)c * ldv);
+      const A f = cf[c];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const i64 i = base + (i64)r * 256;
+        if (i < nv) axpy16(f, v4[i], x[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const i64 i = base + (i64)r * 256;
+      if (i < nv) {
+        w4[i] = x[r];
+        nrm = dot16(x[r], x[r], nrm);
+      }
+    }
+  }
+  if (blockIdx.x == 0) {
+    const i64 i = nv * W + threadIdx.x;
+    if (i < n) {
+      A x = (A)w[i];
+      for (int c = 0; c < k; ++c) x = fma_a(cf[c], (A)V[(i64)c * ldv + i], x);
+      w[i] = (T)x;
+      nrm = fma_a(x, x, nrm);
+    }
+  }
+  if (!nrm2) return;
+  const double acc = block_sum((double)nrm);
+  if (!finish_last(part, acc, cnt)) return;
+  double t = 0.0, body = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(part + i);
+  if (wf != 1.0)
+    for (i64 i = nfl + threadIdx.x; i < n; i += blockDim.x) {
+      const double x = (double)ldcg_t(w + i);
+      body = fma(x, x, body);
+    }
+  t = block_sum(wf * t + (1.0 - wf) * body);
+  if (threadIdx.x == 0) nrm2[0] = t;
+  if (ctl.flag) {
+    __shared__ double tt;
+    if (threadIdx.x == 0) tt = t;
+    __syncthreads();
+    reorth_decide(ctl, tt, coef, k);
+  }
+}
+
+// Row blocks of a register-blocked sweep: one per chunk of 256 R vectors, so
+// that no block carries a second chunk while others idle (a block that does
+// finishes last and sets the launch's duration), capped by the partial
+// buffer's nparts slots per column on large grids.
+inline int gs_blocks(i64 nv, int R, int nparts) {
+  const i64 chunks = (nv + 256 * (i64)R - 1) / (256 * (i64)R);
+  return (int)std::max<i64>(1, std::min<i64>(chunks, nparts));
+}
+
 // plain sum of nparts partials
 __global__ void k_sum_finish(const double* __restrict__ part, int nparts, double* __restrict__ out) {
   pdl_entry();
@@ -136,11 +416,20 @@ inline int dot_blocks(i64 n, int nparts) {
 
 template <typename T>
 void multi_dot(const T* w, const T* V, i64 ldv, int ncols, i64 n, i64 nfl, double wf, double* part, int nparts,
-               double* out, cudaStream_t s) {
+               double* out, cudaStream_t s, const int* gate) {
+  if (vec_ok(w, V, ldv, ncols) && ncols <= kGivensMaxCols) {
+    constexpr int R = 4;
+    const int groups = (ncols + kCG - 1) / kCG;
+    const int nb = gs_blocks(n / Vec16<T>::w, R, nparts);
+    launch_k(k_gs_dot<T, R>, dim3(nb, groups), 256, 0, s, w, V, ldv, ncols, n, nfl, wf, part,
+             part_counters(part, nparts) + kDotCounter, out, gate);
+    note_launch();
+    return;
+  }
   const int nb = dot_blocks(n, nparts);
   dim3 grid(nb, ncols);
   launch_k(k_dot_part<T>, grid, 256, 0, s, w, V, ldv, n, nfl, wf, part, part_counters(part, nparts), out,
-           vec_ok(w, V, ldv, ncols));
+           vec_ok(w, V, ldv, ncols), gate);
   note_launch();
 }
 
@@ -150,8 +439,9 @@ template <typename T>
 __global__ void k_multi_axpy(T* __restrict__ w, const T* __restrict__ V, i64 ldv, int ncols,
                              const double* __restrict__ coef, double sign, i64 n, i64 nfl, double wf,
                              double* __restrict__ part, unsigned* __restrict__ cnt, double* __restrict__ nrm2,
-                             int vec) {
+                             int vec, ReorthCtl ctl, const int* __restrict__ gate) {
   pdl_entry();
+  if (gate && *gate == 0) return;
   __shared__ double c[128];
   for (int i = threadIdx.x; i < ncols; i += blockDim.x) c[i] = sign * coef[i];
   __syncthreads();
@@ -234,13 +524,28 @@ __global__ void k_multi_axpy(T* __restrict__ w, const T* __restrict__ V, i64 ldv
     }
   s = block_sum(wf * s + (1.0 - wf) * body);
   if (threadIdx.x == 0) nrm2[0] = s;
+  if (ctl.flag) {
+    __shared__ double tt;
+    if (threadIdx.x == 0) tt = s;
+    __syncthreads();
+    reorth_decide(ctl, tt, coef, ncols);
+  }
 }
 
 template <typename T>
 void multi_axpy(T* w, const T* V, i64 ldv, int ncols, const double* coef, double sign, i64 n, i64 nfl, double wf,
-                double* part, int nparts, double* nrm2, cudaStream_t s) {
+                double* part, int nparts, double* nrm2, cudaStream_t s, const ReorthCtl* ctl, const int* gate) {
+  const ReorthCtl c = (ctl && nrm2) ? *ctl : ReorthCtl{nullptr, nullptr, 0.0, 0, 0};
+  if (vec_ok(w, V, ldv, ncols) && ncols <= kGivensMaxCols) {
+    constexpr int R = 2;
+    const int nb = gs_blocks(n / Vec16<T>::w, R, nparts);
+    launch_k(k_gs_axpy<T, R>, nb, 256, 0, s, w, V, ldv, ncols, coef, sign, n, nfl, wf, part,
+             part_counters(part, nparts) + kAxpyCounter, nrm2, c, gate);
+    note_launch();
+    return;
+  }
   launch_k(k_multi_axpy<T>, nparts, 256, 0, s, w, V, ldv, ncols, coef, sign, n, nfl, wf, part,
-           part_counters(part, nparts) + kAxpyCounter, nrm2, vec_ok(w, V, ldv, ncols));
+           part_counters(part, nparts) + kAxpyCounter, nrm2, vec_ok(w, V, ldv, ncols), c, gate);
   note_launch();
 }
 
@@ -442,9 +747,10 @@ void wall_rhs(const Dims& d, const Walls& wl, double eta, T* bv, cudaStream_t s)
 }
 
 #define INST(T)                                                                                              \
-  template void multi_dot<T>(const T*, const T*, i64, int, i64, i64, double, double*, int, double*, cudaStream_t); \
+  template void multi_dot<T>(const T*, const T*, i64, int, i64, i64, double, double*, int, double*, cudaStream_t, \
+                             const int*);                                                                        \
   template void multi_axpy<T>(T*, const T*, i64, int, const double*, double, i64, i64, double, double*, int,    \
-                              double*, cudaStream_t);                                                            \
+                              double*, cudaStream_t, const ReorthCtl*, const int*);                              \
   template void scale_by<T>(T*, const T*, const double*, int, i64, cudaStream_t, float*);                       \
   template void axpby<T>(T*, const T*, double, double, i64, cudaStream_t);                                      \
   template void wall_rhs<T>(const Dims&, const Walls&, double, T*, cudaStream_t);

@@ -80,8 +80,8 @@ template <typename T> void add_grad(const Dims&, const T* phi, T* v, cudaStream_
 // orthonormal 1D eigenbases Q_x, Q_y, Q_z and eigenvalues l_x, l_y, l_z,
 // A^-1 = (Q_x (x) Q_y (x) Q_z) diag(1 / (s (l_x + l_y + l_z))) (Q_x (x) Q_y (x) Q_z)^T,
 // the zero mode of a singular operator dropped (pseudo-inverse).
-constexpr int kFDMaxPoints = 32768;  // points of one grid
-constexpr int kFDLine = 32;          // points along one axis
+constexpr int kFDMaxPoints = 48 * 48 * 48;  // points of one grid
+constexpr int kFDLine = 48;                 // points along one axis
 constexpr int kFDCtas = 8;           // CTAs (one cluster) per grid
 constexpr int kFDThreads = 256;
 // shared memory bound per CTA: table (3 axes, two padded e x e bases and e
@@ -103,6 +103,8 @@ struct FDParams {
 // Bases of every grid of a level; false if some grid exceeds the limits.
 bool fd_plan(const Dims& d, bool faces, double eta, std::vector<float>& tab, FDParams& P, std::string& why);
 void fd_solve(const FDParams& P, float* u, const float* rhs, cudaStream_t s);
+void fd_solve_wide(const FDParams& P, float* u, const float* rhs, float* tmp, cudaStream_t s);
+bool fd_use_wide(const FDParams& P);
 
 // k_ib.cu
 void geometry(int nbl, const int* bob, const double* ref, const double* q, const double* quat,
@@ -149,21 +151,40 @@ template <typename T> void dense_body_apply(int nbl, int nb, const int* boff, co
 // A grid's partial-sum buffer: nparts x kPartCols doubles, 8 spare doubles,
 // then kPartCounters counters (unsigned) of the last-block reductions:
 // [0, kPartCols) one per inner-product column, kAxpyCounter for the norm of
-// a multi-axpy.  The counters start at zero and every reduction resets its own.
+// a multi-axpy, kDotCounter for the register-blocked inner products.  The counters start at zero and every reduction resets its own.
 constexpr int kPartCols = 130;
 constexpr int kPartCounters = 160;
 constexpr int kAxpyCounter = 140;
+constexpr int kDotCounter = 141;     // the register-blocked multi-column inner product
 inline size_t part_buffer_doubles(int nparts) { return (size_t)nparts * kPartCols + 8 + kPartCounters / 2; }
 inline unsigned* part_counters(double* part, int nparts) {
   return reinterpret_cast<unsigned*>(part + (size_t)nparts * kPartCols + 8);
 }
 // Weighted inner products <x, y>_W with weight wf on the first nfl entries
 // and 1 on the rest.
+// Selective re-orthogonalisation in the Gram-Schmidt of FGMRES.  A first
+// projection w' = w - V h (h = V^T w) whose result keeps at least a fraction
+// tau of w (||w'||^2 >= tau2 (||w'||^2 + ||h||^2), Pythagoras for an
+// orthonormal V) lost at most about eps / tau of orthogonality, and its
+// second projection is skipped: the multi-axpy that forms w' writes
+// *flag = 1 when the second pass is needed (else 0) and zeroes its
+// coefficients h2[0..k), which the second pass overwrites when it runs.
+struct ReorthCtl {
+  int* flag;        // [0] the decision, [1] count of second passes taken
+  double* h2;
+  double tau2;
+  // inside a captured graph: the handle of the IF node around the second
+  // pass, set to the decision as well (use_handle = 1)
+  cudaGraphConditionalHandle handle;
+  int use_handle;
+};
+// gate (may be null): device flag; the launch does nothing when it is 0.
 template <typename T> void multi_dot(const T* w, const T* V, i64 ldv, int ncols, i64 n, i64 nfl, double wf,
-                                     double* part, int nparts, double* out, cudaStream_t);
+                                     double* part, int nparts, double* out, cudaStream_t,
+                                     const int* gate = nullptr);
 template <typename T> void multi_axpy(T* w, const T* V, i64 ldv, int ncols, const double* coef, double sign,
                                       i64 n, i64 nfl, double wf, double* part, int nparts, double* nrm2,
-                                      cudaStream_t);
+                                      cudaStream_t, const ReorthCtl* ctl = nullptr, const int* gate = nullptr);
 void gpu_delay(long long cycles, cudaStream_t);
 void gpu_empty(cudaStream_t);
 // out = in * f with f = denom (invert 0), 1 / denom (1) or 1 / sqrt(denom) (2);

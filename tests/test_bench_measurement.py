@@ -42,8 +42,12 @@ def test_fp64_class_is_bound_by_the_derived_fp64_peak():
     assert r["achieved"] == pytest.approx(12e6 / avg_s / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / peak)
     assert r["other_roof"]["unit"] == "GB/s" and r["other_roof"]["peak"] == pytest.approx(p["hbm_gbs"])
-    # traffic from the committed ncu ratio, per launch like achieved
-    assert r["traffic"] == pytest.approx(bench.TRAFFIC_RATIO["dot"] * 50e6)
+    # traffic from the committed ncu ratio, per launch like achieved (null
+    # while the kernel has changed since its counters were taken)
+    if "dot" in bench.TRAFFIC_RATIO:
+        assert r["traffic"] == pytest.approx(bench.TRAFFIC_RATIO["dot"] * 50e6)
+    else:
+        assert r["traffic"] is None
     # a 50 MB working set per launch fits the L2
     assert "resident" in r
 

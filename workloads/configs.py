@@ -118,27 +118,31 @@ def two_sphere_cavity(steps=2000):
     return w
 
 
-def driven_monolayer(wall_speed=0.5, steps=500):
+def driven_monolayer(wall_speed=0.5, steps=500, cols=64, rows=16, nz=12, z=6.0):
     """1024 12-blob spheres (R = 1h) on a jittered lattice (64 columns x 16
     rows, spacing 6h, odd rows shifted 3h, z = 6h) in a 384x96x12 channel
     periodic in x; no-slip side and bottom walls, top wall moving at
     (wall_speed, 0, 0); Yukawa pair repulsion, per-blob soft wall repulsion and
-    a commensurate substrate potential of amplitude 4kT; dt = 0.02."""
+    a commensurate substrate potential of amplitude 4kT; dt = 0.02.  Smaller
+    monolayers of the same shape: cols x rows spheres in a
+    (6 cols) x (6 rows) x nz channel at height z."""
     rng = _rng(2)
     shell = icosahedral_shell(12, 1.0)
-    w = Workload(name="monolayer-384x96x12", n=(384, 96, 12), periodic=(True, False, False),
+    full = (cols, rows, nz) == (64, 16, 12)
+    name = "monolayer-384x96x12" if full else f"monolayer-{6 * cols}x{6 * rows}x{nz}"
+    w = Workload(name=name, n=(6 * cols, 6 * rows, nz), periodic=(True, False, False),
                  dt=0.02, steps=steps, rtol=1e-8, precision="f32-refined",
                  seed=WORKLOAD_SEED_BASE + 2)
     w.wall_vel = np.zeros((6, 3))
     w.wall_vel[5, 0] = wall_speed          # +z wall moves along x
-    quats = random_unit_quaternions(rng, 1024)
+    quats = random_unit_quaternions(rng, cols * rows)
     bodies = []
-    for r in range(16):
-        for c in range(64):
+    for r in range(rows):
+        for c in range(cols):
             x = 6.0 * c + (3.0 if r % 2 else 0.0) + 1.5
             y = 6.0 * r + 3.0
             jit = rng.uniform(-0.1, 0.1, size=3)
-            bodies.append(Body(shell, np.array([x, y, 6.0]) + jit, quats[len(bodies)]))
+            bodies.append(Body(shell, np.array([x, y, z]) + jit, quats[len(bodies)]))
     w.bodies = bodies
     s_lat = 6.0
     w.potentials = {
