@@ -170,7 +170,13 @@ int rbfib_stokes_solve(rbfib_grid* g, const double* f, double* v, double* pi,
                        rbfib_solve_info* info);
 
 /* One Split-Euler-Maruyama step (Algorithm 1, steps 1-7) from the
- * configuration (q, quat) (device, in/out).  Random numbers come from
+ * configuration (q, quat) (device, in/out).  The whole step runs as one
+ * device-driven CUDA graph (restart cycles and refinement sweeps in WHILE
+ * nodes, the rejection test on the device) captured at the first call and
+ * again whenever p's contents or the q / quat pointers change; the call
+ * synchronises once at the end.  With RBFIB_NO_GRAPHS=1 or
+ * RBFIB_NO_STEP_GRAPH=1 in the environment (read when the grid is created),
+ * or while a kernel timer is active, the host orchestrates the step.  Random numbers come from
  * Philox4x64-10 with key (seed, 0) and counter (block, step,
  * (attempt << 32) | purpose, 0).  On an unphysical new configuration (a blob
  * outside the domain along a wall axis) q and quat are left unchanged and the
@@ -195,15 +201,17 @@ rbfib_grid* rbfib_batch_grid(rbfib_batch* b, int32_t sys);   /* NULL if out of r
 
 /* One Split-Euler-Maruyama step of every system (Algorithm 1): system i uses
  * params[i], seeds[i], attempts[i] (NULL = 0) and its device configuration
- * q[i], quat[i] (host arrays of device pointers).  Workers run concurrently
- * on their own host threads and streams and take systems from a shared queue,
- * longest first by each system's duration in the previous call (by unknown
- * count before the first); a system's grid is bound to the stream of the
- * worker that takes it, so a call made on a batch grid between batch steps
- * runs on one of the batch's streams.  status[i] receives each system's
- * rbfib_sem_step status (RBFIB_EREJECT leaves that system unchanged); infos
- * may be NULL.  Returns the first status other than OK / EREJECT, else OK.
- * Synchronises every worker stream. */
+ * q[i], quat[i] (host arrays of device pointers).  Each system's step is one
+ * launch of its device-driven step graph (see rbfib_sem_step), captured at
+ * its first step and again whenever its params or q / quat pointers change.
+ * Systems, largest first, are dealt round-robin to the worker streams; the
+ * workers' host threads launch in parallel without waiting, then every
+ * stream is synchronised once.  A system's grid stays bound to the stream of
+ * its worker, so a call made on a batch grid between batch steps runs on one
+ * of the batch's streams.  status[i] receives each system's rbfib_sem_step
+ * status (RBFIB_EREJECT leaves that system unchanged); infos may be NULL.
+ * Returns the first status other than OK / EREJECT, else OK.  Synchronises
+ * every worker stream. */
 int rbfib_batch_sem_step(rbfib_batch* b, const rbfib_sem_params* params, const uint64_t* seeds, uint64_t step,
                          const uint32_t* attempts, double* const* q, double* const* quat, rbfib_step_info* infos,
                          int32_t* status);
@@ -221,11 +229,15 @@ int rbfib_batch_sem_step(rbfib_batch* b, const rbfib_sem_params* params, const u
  * pointer may be NULL. */
 int rbfib_body_block_info(const rbfib_grid* g, int32_t* dense, int64_t* warm_starts);
 
+/* *device_driven = 1 if the grid's last SEM step ran as the device-driven
+ * step graph (see rbfib_sem_step), 0 if the host orchestrated it. */
+int rbfib_step_mode(const rbfib_grid* g, int32_t* device_driven);
+
 /* Gram-Schmidt statistics of the grid's Krylov solves since it was created:
  * Arnoldi iterations and how many of them took the second (re-
  * orthogonalising) pass of classical Gram-Schmidt.  The second pass runs only
  * when the first leaves less than a fraction tau of the new vector's norm
- * (tau = 1e-3 for FP64 bases, 1/sqrt(2) for FP32 ones); otherwise the
+ * (tau = 1e-3 for FP64 bases, 1e-2 for the FP32 bases of the refinement's inner solves); otherwise the
  * orthogonality lost is at most about eps / tau.  Either pointer may be
  * NULL. */
 int rbfib_krylov_stats(const rbfib_grid* g, int64_t* iterations, int64_t* second_passes);

@@ -90,6 +90,7 @@ def lib():
             "rbfib_launch_count": ([], U64),
             "rbfib_tuned_blocks": ([P, ctypes.POINTER(ctypes.c_int32)], I32),
             "rbfib_krylov_stats": ([P, ctypes.POINTER(I64), ctypes.POINTER(I64)], I32),
+            "rbfib_step_mode": ([P, ctypes.POINTER(I32)], I32),
             "rbfib_create_batch": ([I32, ctypes.POINTER(GridDesc), I32, ctypes.POINTER(P)], I32),
             "rbfib_destroy_batch": ([P], None),
             "rbfib_batch_grid": ([P, I32], P),
@@ -354,6 +355,12 @@ class Grid:
         out = (ctypes.c_int32 * 4)()
         self._check(lib().rbfib_tuned_blocks(self._h, out))
         return list(out)
+
+    def step_mode(self):
+        """1 if the last SEM step ran as the device-driven step graph, else 0."""
+        v = ctypes.c_int32()
+        self._check(lib().rbfib_step_mode(self._h, ctypes.byref(v)))
+        return v.value
 
     def krylov_stats(self):
         """(Arnoldi iterations, second Gram-Schmidt passes taken) since creation."""

@@ -1,12 +1,13 @@
 // Ensembles of independent confined suspensions (the equilibrium-ensemble
 // runs of Sec. V: many independent trajectories).  Each system is a grid
-// object with its own workspaces.  One SEM step of the whole ensemble is a
-// work queue: a fixed number of worker threads, each with its own stream,
-// take the next system from a shared counter, rebind its grid to their
-// stream and run its step, so the small kernels of different systems overlap
-// on the GPU.  The queue is ordered longest first by each system's duration
-// in the previous batch step (by its unknown count before the first), which
-// keeps the workers evenly loaded over systems of uneven size.
+// object with its own workspaces and its own device-driven SEM-step graph
+// (the whole step, restart cycles and refinement sweeps included, runs on
+// the device without host round trips).  One SEM step of the whole ensemble
+// launches every system's graph: systems are sorted by unknown count and
+// dealt round-robin to a fixed number of worker streams (so each stream gets
+// an even share of large and small systems), the workers' host threads
+// launch in parallel, and the small kernels of different systems overlap on
+// the GPU.  Then every stream is synchronised once.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -19,8 +20,13 @@
 #include "common.cuh"
 
 // Defined with the grid (rbfib.cu): rebinds a grid to another stream between
-// calls.
+// calls; launches a grid's device-driven SEM step without waiting (false:
+// not available, run rbfib_sem_step instead) and, once its stream has been
+// synchronised, returns the step's status and information.
 void rbfib_grid_bind_stream(rbfib_grid* g, cudaStream_t s);
+bool rbfib_grid_step_launch(rbfib_grid* g, const rbfib_sem_params* p, uint64_t seed, uint64_t step,
+                            uint32_t attempt, double* q, double* quat);
+int rbfib_grid_step_finish(rbfib_grid* g, rbfib_step_info* info);
 
 struct rbfib_batch {
   int n = 0;
@@ -84,12 +90,9 @@ int rbfib_batch_sem_step(rbfib_batch* b, const rbfib_sem_params* params, const u
                          const uint32_t* attempts, double* const* q, double* const* quat, rbfib_step_info* infos,
                          int32_t* status) {
   if (!b || !params || !seeds || !q || !quat || !status) return RBFIB_EINVAL;
-  // queue order: longest first; systems not yet timed by their unknown count
+  // largest systems first, dealt round-robin to the worker streams
   std::vector<double> key(b->n);
-  bool timed = true;
-  for (int i = 0; i < b->n; ++i) timed = timed && b->cost[i] > 0.0;
   for (int i = 0; i < b->n; ++i) {
-    if (timed) { key[i] = b->cost[i]; continue; }
     int64_t off[7] = {0, 0, 0, 0, 0, 0, 0};
     rbfib_saddle_layout(b->grids[i], off);
     key[i] = (double)off[6];
@@ -97,15 +100,25 @@ int rbfib_batch_sem_step(rbfib_batch* b, const rbfib_sem_params* params, const u
   std::vector<int> order(b->n);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return key[a] > key[c]; });
-  std::atomic<int> next{0};
+  // Worker w launches the device-driven step graphs of systems w, w + W, ...
+  // of that order on its stream without waiting (a system whose graph is not
+  // available runs its host-orchestrated step there and then); then every
+  // stream is synchronised and the launched steps report.  A system's first
+  // step captures its graph, which the workers do in parallel.
+  std::vector<char> launched(b->n, 0);
   auto work = [&](int w) {
     cudaSetDevice(b->device);
-    for (int t = next.fetch_add(1); t < b->n; t = next.fetch_add(1)) {
+    for (int t = w; t < b->n; t += b->workers) {
       const int i = order[t];
       rbfib_grid_bind_stream(b->grids[i], b->streams[w]);
       const auto t0 = std::chrono::steady_clock::now();
-      status[i] = rbfib_sem_step(b->grids[i], &params[i], seeds[i], step, attempts ? attempts[i] : 0u, q[i], quat[i],
-                                 infos ? &infos[i] : nullptr);
+      const uint32_t att = attempts ? attempts[i] : 0u;
+      if (rbfib_grid_step_launch(b->grids[i], &params[i], seeds[i], step, att, q[i], quat[i])) {
+        launched[i] = 1;
+      } else {
+        status[i] = rbfib_sem_step(b->grids[i], &params[i], seeds[i], step, att, q[i], quat[i],
+                                   infos ? &infos[i] : nullptr);
+      }
       b->cost[i] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
   };
@@ -113,6 +126,10 @@ int rbfib_batch_sem_step(rbfib_batch* b, const rbfib_sem_params* params, const u
   for (int w = 1; w < b->workers; ++w) th.emplace_back(work, w);
   work(0);
   for (auto& t : th) t.join();
+  for (cudaStream_t s : b->streams)
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RBFIB_ECUDA;
+  for (int i = 0; i < b->n; ++i)
+    if (launched[i]) status[i] = rbfib_grid_step_finish(b->grids[i], infos ? &infos[i] : nullptr);
   int first = RBFIB_OK;
   for (int i = 0; i < b->n; ++i)
     if (status[i] != RBFIB_OK && status[i] != RBFIB_EREJECT && first == RBFIB_OK) first = status[i];

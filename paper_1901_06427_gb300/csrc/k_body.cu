@@ -264,11 +264,74 @@ __global__ void k_rotate_inverse(int nbl, const int* __restrict__ bob, const dou
 // when the warm start was taken.
 constexpr double kNSMaxStart = 0.95;
 constexpr int kNSIters = 8;   // even: the result lands in Minv
+// The pieces of the set-up, also used one by one by the device-driven SEM
+// step (where the warm-start decision is an IF/ELSE graph node).
+// Warm start: Mw = M of the new configuration, X0 = Minv rotated with each
+// body's rotation since it was built (when qnew and qold are known), and
+// Tw = R0 = I - M X0 with ss[0] = ||R0||_F^2.
+void dense_body_warm_start(int nbl, const int* bob, const double* r, const double* qnew, const double* qold,
+                           double a, double eta, float* Minv, float* Mw, float* Tw, double* ss, cudaStream_t s) {
+  const i64 n3 = 3 * (i64)nbl;
+  launch_k(k_rpy_full, nblk(n3 * n3, 256), 256, 0, s, nbl, r, a, eta, Mw);
+  note_launch();
+  if (qnew && qold) {
+    launch_k(k_rotate_inverse, nblk((i64)nbl * nbl, 128), 128, 0, s, nbl, bob, qnew, qold, Minv);
+    note_launch();
+  }
+  cudaMemsetAsync(ss, 0, sizeof(double), s);
+  ns_gemm<0>((int)n3, Mw, Minv, nullptr, Tw, ss, s);
+}
+// kNSIters Newton-Schulz steps from X0 = Minv with R0 in Tw; the result
+// lands in Minv (kNSIters is even).
+void dense_body_ns(int nbl, float* Minv, const float* Mw, float* Tw, float* Uw, double* ss, cudaStream_t s) {
+  const int n3 = 3 * nbl;
+  float* X = Minv;
+  float* Y = Uw;
+  for (int it = 0; it < kNSIters; ++it) {
+    if (it > 0) ns_gemm<0>(n3, Mw, X, nullptr, Tw, ss, s);   // R = I - M X
+    ns_gemm<1>(n3, X, Tw, X, Y, nullptr, s);                 // X' = X + X R
+    float* t = X; X = Y; Y = t;
+  }
+}
+// Gauss-Jordan inverse of M into Minv (from Mw when it is not null, else
+// Minv holds M); status = 1 on a zero pivot.
+void dense_body_gj(int nbl, float* Minv, const float* Mw, int* status, cudaStream_t s) {
+  const i64 n3 = 3 * (i64)nbl;
+  if (Mw) cudaMemcpyAsync(Minv, Mw, sizeof(float) * n3 * n3, cudaMemcpyDeviceToDevice, s);
+  launch_k(k_gj_inverse<float>, 1, 1024, 2 * sizeof(float) * n3, s, Minv, (int)n3, status);
+  note_launch();
+}
+// P = M^-1 K and N = (K^T P)^-1 (FP64 Gauss-Jordan; status = 1 on a zero pivot).
+void dense_body_finish(int nbl, int nb, const int* boff, const double* arm, const float* Minv, float* P, double* N,
+                       int* status, cudaStream_t s) {
+  const i64 n3 = 3 * (i64)nbl, m = 6 * (i64)nb;
+  launch_k(k_mk, nblk(n3 * m, 256), 256, 0, s, nbl, nb, boff, arm, Minv, P);
+  note_launch();
+  launch_k(k_ktp, nblk(m * m, 256), 256, 0, s, nbl, nb, boff, arm, P, N);
+  note_launch();
+  launch_k(k_gj_inverse<double>, 1, 1024, 2 * sizeof(double) * m, s, N, (int)m, status);
+  note_launch();
+}
+
+// IF/ELSE condition of the device-driven warm start: ||R0||_F <= kNSMaxStart;
+// warm[0] counts the builds that take the Newton-Schulz branch.
+__global__ void k_ns_decide(const double* ss, cudaGraphConditionalHandle h, long long* warm) {
+  pdl_entry();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const bool ok = ss[0] <= kNSMaxStart * kNSMaxStart;
+  if (ok) warm[0] += 1;
+  cudaGraphSetConditional(h, ok ? 1u : 0u);
+}
+void ns_decide(const double* ss, cudaGraphConditionalHandle h, long long* warm, cudaStream_t s) {
+  launch_k(k_ns_decide, 1, 32, 0, s, ss, h, warm);
+  note_launch();
+}
+
 cudaError_t dense_body_build(int nbl, int nb, const int* boff, const int* bob, const double* r, const double* arm,
                              const double* qnew, const double* qold, double a, double eta, float* Minv, float* P,
                              double* N, int* status, float* Mw, float* Tw, float* Uw, double* ss, double* ss_host,
                              bool warm, cudaStream_t s, bool* used_out) {
-  const i64 n3 = 3 * (i64)nbl, m = 6 * (i64)nb;
+  const i64 n3 = 3 * (i64)nbl;
   cudaError_t e;
 #define RB_CK(call)                      \
   if ((e = (call)) != cudaSuccess) return e
@@ -276,43 +339,22 @@ cudaError_t dense_body_build(int nbl, int nb, const int* boff, const int* bob, c
   bool used = false;
   *used_out = false;
   if (warm) {
-    launch_k(k_rpy_full, nblk(n3 * n3, 256), 256, 0, s, nbl, r, a, eta, Mw);
-    note_launch();
-    if (qnew && qold) {
-      launch_k(k_rotate_inverse, nblk((i64)nbl * nbl, 128), 128, 0, s, nbl, bob, qnew, qold, Minv);
-      note_launch();
-    }
-    RB_CK(cudaMemsetAsync(ss, 0, sizeof(double), s));
-    ns_gemm<0>((int)n3, Mw, Minv, nullptr, Tw, ss, s);          // R0 = I - M X0
+    dense_body_warm_start(nbl, bob, r, qnew, qold, a, eta, Minv, Mw, Tw, ss, s);
     RB_CK(cudaMemcpyAsync(ss_host, ss, sizeof(double), cudaMemcpyDeviceToHost, s));
     RB_CK(cudaStreamSynchronize(s));
     const double r0 = std::sqrt(std::max(ss_host[0], 0.0));
     if (r0 <= kNSMaxStart) {
-      float* X = Minv;
-      float* Y = Uw;
-      for (int it = 0; it < kNSIters; ++it) {
-        if (it > 0) ns_gemm<0>((int)n3, Mw, X, nullptr, Tw, ss, s);   // R = I - M X
-        ns_gemm<1>((int)n3, X, Tw, X, Y, nullptr, s);                 // X' = X + X R
-        float* t = X; X = Y; Y = t;
-      }
+      dense_body_ns(nbl, Minv, Mw, Tw, Uw, ss, s);
       used = true;
     } else {
-      RB_CK(cudaMemcpyAsync(Minv, Mw, sizeof(float) * n3 * n3, cudaMemcpyDeviceToDevice, s));
+      dense_body_gj(nbl, Minv, Mw, status, s);
     }
   } else {
     launch_k(k_rpy_full, nblk(n3 * n3, 256), 256, 0, s, nbl, r, a, eta, Minv);
     note_launch();
+    dense_body_gj(nbl, Minv, nullptr, status, s);
   }
-  if (!used) {
-    launch_k(k_gj_inverse<float>, 1, 1024, 2 * sizeof(float) * n3, s, Minv, (int)n3, status);
-    note_launch();
-  }
-  launch_k(k_mk, nblk(n3 * m, 256), 256, 0, s, nbl, nb, boff, arm, Minv, P);
-  note_launch();
-  launch_k(k_ktp, nblk(m * m, 256), 256, 0, s, nbl, nb, boff, arm, P, N);
-  note_launch();
-  launch_k(k_gj_inverse<double>, 1, 1024, 2 * sizeof(double) * m, s, N, (int)m, status);
-  note_launch();
+  dense_body_finish(nbl, nb, boff, arm, Minv, P, N, status, s);
   *used_out = used;
   return cudaGetLastError();
 #undef RB_CK

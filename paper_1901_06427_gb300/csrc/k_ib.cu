@@ -726,6 +726,27 @@ __global__ void k_outside(Dims d, int nbl, const double* __restrict__ r, int* __
   }
 }
 
+// End of a device-driven SEM step: (q, quat) take the new configuration
+// unless a blob left the domain (flag) or a status word is nonzero (a
+// failed solve or body-block set-up); rejected[0] records the rejection.
+__global__ void k_accept(int nb, const int* __restrict__ flag, const int* __restrict__ st, int nst, int st_stride,
+                         const double* __restrict__ qn, const double* __restrict__ quatn, double* __restrict__ q,
+                         double* __restrict__ quat, int* __restrict__ rejected) {
+  pdl_entry();
+  bool ok = flag[0] == 0;
+  for (int i = 0; i < nst; ++i) ok = ok && st[i * st_stride] == 0;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) rejected[0] = flag[0] != 0 ? 1 : 0;
+  if (!ok) return;
+  for (int i = t; i < 3 * nb; i += gridDim.x * blockDim.x) q[i] = qn[i];
+  for (int i = t; i < 4 * nb; i += gridDim.x * blockDim.x) quat[i] = quatn[i];
+}
+void accept_step(int nb, const int* flag, const int* st, int nst, int st_stride, const double* qn,
+                 const double* quatn, double* q, double* quat, int* rejected, cudaStream_t s) {
+  launch_k(k_accept, 1, 128, 0, s, nb, flag, st, nst, st_stride, qn, quatn, q, quat, rejected);
+  note_launch();
+}
+
 void outside_check(const Dims& d, int nbl, const double* r, int* flag, cudaStream_t s) {
   if (nbl > 0) { launch_k(k_outside, nblk(nbl, 128), 128, 0, s, d, nbl, r, flag); note_launch(); }
 }

@@ -931,3 +931,144 @@ template void multi_axpy_dev<float>(float*, const float*, i64, const int*, const
                                     cudaStream_t);
 
 }  // namespace rbfib
+
+// =================================================================
+// Control of device-driven solves (a whole SEM step captured as one graph:
+// the restart cycles of a solve inside a WHILE node, the refinement sweeps
+// inside another).  One thread each; dpar and ist as for the cycle graphs,
+// plus dpar[3] = ||b||^2 of the solve.  info: [0] iterations, [1] status
+// (RBFIB_OK, RBFIB_ENOCONV, RBFIB_ENAN), [2] restart cycles run, [3] second
+// Gram-Schmidt passes taken; rel: the true relative residual.
+namespace rbfib {
+
+constexpr int kStOk = 0, kStNoConv = -2, kStNaN = -3;
+
+// Start of a solve: tolerance, budget and residual of x = 0; the WHILE
+// condition is whether any cycle is needed.  rtol_p / maxit_p (may be null)
+// override the constants (the refinement's inner solves set them per sweep).
+__global__ void k_solve_init(double* dpar, int* ist, double rtol, int maxit, const double* rtol_p,
+                             const int* maxit_p, cudaGraphConditionalHandle h, int* info, double* rel) {
+  pdl_entry();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double bn2 = dpar[3];
+  const double rt = rtol_p ? rtol_p[0] : rtol;
+  const int mi = maxit_p ? maxit_p[0] : maxit;
+  dpar[0] = rt * sqrt(fmax(bn2, 0.0));
+  dpar[1] = (double)mi;
+  dpar[2] = bn2;
+  dpar[4] = rt;
+  for (int i = 0; i < 8; ++i) ist[i] = 0;
+  const bool go = bn2 > 0.0 && isfinite(bn2) && mi > 0;
+  info[0] = 0;
+  info[1] = isfinite(bn2) ? (go || bn2 == 0.0 ? kStOk : kStNoConv) : kStNaN;
+  info[2] = 0;
+  info[3] = 0;
+  rel[0] = 0.0;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// After a restart cycle: the true relative residual decides whether another
+// cycle runs (no convergence yet, budget left, the cycle made progress).
+__global__ void k_solve_check(const double* dpar, const int* ist, cudaGraphConditionalHandle h, int* info,
+                              double* rel) {
+  pdl_entry();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double r = sqrt(fmax(dpar[2], 0.0) / dpar[3]);
+  const bool nan = !isfinite(r);
+  const bool conv = !nan && r <= dpar[4];
+  const int k = ist[0], it = ist[1];
+  const bool more = !nan && !conv && (double)it < dpar[1] && k > 0;
+  info[0] = it;
+  info[1] = conv ? kStOk : (nan ? kStNaN : kStNoConv);
+  info[2] += 1;
+  info[3] = ist[5];
+  rel[0] = r;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+void solve_init(double* dpar, int* ist, double rtol, int maxit, const double* rtol_p, const int* maxit_p,
+                cudaGraphConditionalHandle h, int* info, double* rel, cudaStream_t s) {
+  launch_k(k_solve_init, 1, 32, 0, s, dpar, ist, rtol, maxit, rtol_p, maxit_p, h, info, rel);
+  note_launch();
+}
+void solve_check(const double* dpar, const int* ist, cudaGraphConditionalHandle h, int* info, double* rel,
+                 cudaStream_t s) {
+  launch_k(k_solve_check, 1, 32, 0, s, dpar, ist, h, info, rel);
+  note_launch();
+}
+
+// Refinement state rst: [0] ||b||^2, [1] relative residual, [2] inner
+// tolerance of the next sweep; rsi: [0] inner iterations so far, [1] sweeps,
+// [2] status, [3] inner iteration cap of the next sweep.
+__global__ void k_refine_init(double* rst, int* rsi, cudaGraphConditionalHandle h, int* info, double* rel) {
+  pdl_entry();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double bn2 = rst[0];
+  const bool go = bn2 > 0.0 && isfinite(bn2);
+  rst[1] = go ? 1.0 : 0.0;
+  rsi[0] = 0;
+  rsi[1] = 0;
+  rsi[2] = isfinite(bn2) ? kStOk : kStNaN;
+  info[0] = 0;
+  info[1] = rsi[2];
+  info[2] = 0;
+  info[3] = 0;
+  rel[0] = 0.0;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// Before a sweep: its inner tolerance max(inner_tol, rtol / (2 rel)) and
+// iteration cap min(budget left, m).
+__global__ void k_refine_sweep(double* rst, int* rsi, double rtol, double inner_tol, int maxit, int m) {
+  pdl_entry();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  rst[2] = fmax(inner_tol, 0.5 * rtol / rst[1]);
+  rsi[3] = min(maxit - rsi[0], m);
+}
+
+// After a sweep: rn2 = ||b - A x||^2 (FP64); inner = the inner solve's info.
+__global__ void k_refine_check(const double* rn2, double* rst, int* rsi, const int* inner, double rtol, int maxit,
+                               cudaGraphConditionalHandle h, int* info, double* rel) {
+  pdl_entry();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double r = sqrt(fmax(rn2[0], 0.0) / rst[0]);
+  rst[1] = r;
+  rsi[0] += inner[0];
+  rsi[1] += 1;
+  const bool nan = !isfinite(r) || inner[1] == kStNaN;
+  const bool conv = !nan && r <= rtol;
+  const bool more = !nan && !conv && rsi[0] < maxit && rsi[1] < 50;
+  rsi[2] = conv ? kStOk : (nan ? kStNaN : kStNoConv);
+  info[0] = rsi[0];
+  info[1] = rsi[2];
+  info[2] = rsi[1];
+  info[3] += inner[3];
+  rel[0] = r;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+void refine_init(double* rst, int* rsi, cudaGraphConditionalHandle h, int* info, double* rel, cudaStream_t s) {
+  launch_k(k_refine_init, 1, 32, 0, s, rst, rsi, h, info, rel);
+  note_launch();
+}
+void refine_sweep(double* rst, int* rsi, double rtol, double inner_tol, int maxit, int m, cudaStream_t s) {
+  launch_k(k_refine_sweep, 1, 32, 0, s, rst, rsi, rtol, inner_tol, maxit, m);
+  note_launch();
+}
+void refine_check(const double* rn2, double* rst, int* rsi, const int* inner, double rtol, int maxit,
+                  cudaGraphConditionalHandle h, int* info, double* rel, cudaStream_t s) {
+  launch_k(k_refine_check, 1, 32, 0, s, rn2, rst, rsi, inner, rtol, maxit, h, info, rel);
+  note_launch();
+}
+
+// Condition of an IF node from a device int (nonzero -> 1).
+__global__ void k_cond_from(const int* flag, cudaGraphConditionalHandle h) {
+  pdl_entry();
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, flag[0] ? 1u : 0u);
+}
+void cond_from(const int* flag, cudaGraphConditionalHandle h, cudaStream_t s) {
+  launch_k(k_cond_from, 1, 32, 0, s, flag, h);
+  note_launch();
+}
+
+}  // namespace rbfib

@@ -29,6 +29,28 @@ void philox_normals(unsigned long long seed, unsigned long long step, unsigned a
   }
 }
 
+// The same normals with (seed, step, attempt) read from device memory
+// sp[0..2] (the device-driven SEM step's graph reads them at run time).
+__global__ void k_philox_normals_p(const unsigned long long* __restrict__ sp, unsigned purpose, i64 count,
+                                   double* __restrict__ out) {
+  pdl_entry();
+  const i64 b = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (4 * b >= count) return;
+  double z[4];
+  philox_normals4(sp[0], sp[1], (unsigned)sp[2], purpose, (unsigned long long)b, z);
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+    if (4 * b + l < count) out[4 * b + l] = z[l];
+}
+
+void philox_normals_p(const unsigned long long* sp, unsigned purpose, i64 count, double* out, cudaStream_t s) {
+  const i64 nb = (count + 3) / 4;
+  if (nb > 0) {
+    launch_k(k_philox_normals_p, nblk(nb, 128), 128, 0, s, sp, purpose, count, out);
+    note_launch();
+  }
+}
+
 // The raw words of n_blocks consecutive Philox4x64-10 blocks of the stream
 // (seed, step, attempt, purpose), four 64-bit words per block.
 __global__ void k_philox_words(unsigned long long seed, unsigned long long step, unsigned attempt, unsigned purpose,

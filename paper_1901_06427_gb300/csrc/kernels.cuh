@@ -133,6 +133,8 @@ void wft(int nb, const double* wn, const double* Lp, double kT, double* out, cud
 void move_bodies(int nb, const double* q, const double* quat, const double* vec6, const double* Lp, double a,
                  double* qo, double* quato, cudaStream_t);
 void outside_check(const Dims&, int nbl, const double* r, int* flag, cudaStream_t);
+void accept_step(int nb, const int* flag, const int* st, int nst, int st_stride, const double* qn,
+                 const double* quatn, double* q, double* quat, int* rejected, cudaStream_t);
 void arms_from_positions(int nbl, const int* bob, const double* r, const double* q, double* arm, cudaStream_t);
 void adjoint_positions(const Dims&, int nbl, const int* bob, const double* r, const double* v, const double* lam,
                        const double* U, const double* zv, const double* zl, const double* zU, double* dr,
@@ -143,6 +145,13 @@ cudaError_t dense_body_build(int nbl, int nb, const int* boff, const int* bob, c
                              const double* qnew, const double* qold, double a, double eta, float* Minv, float* P,
                              double* N, int* status, float* Mw, float* Tw, float* Uw, double* ss, double* ss_host,
                              bool warm, cudaStream_t, bool* used);
+void dense_body_warm_start(int nbl, const int* bob, const double* r, const double* qnew, const double* qold,
+                           double a, double eta, float* Minv, float* Mw, float* Tw, double* ss, cudaStream_t);
+void dense_body_ns(int nbl, float* Minv, const float* Mw, float* Tw, float* Uw, double* ss, cudaStream_t);
+void dense_body_gj(int nbl, float* Minv, const float* Mw, int* status, cudaStream_t);
+void dense_body_finish(int nbl, int nb, const int* boff, const double* arm, const float* Minv, float* P, double* N,
+                       int* status, cudaStream_t);
+void ns_decide(const double* ss, cudaGraphConditionalHandle h, long long* warm, cudaStream_t);
 template <typename T> void dense_body_apply(int nbl, int nb, const int* boff, const int* bob, const double* arm,
                                             const float* Minv, const float* P, const double* N, const T* sres,
                                             const T* rU, T* zlam, T* zU, cudaStream_t);
@@ -208,12 +217,23 @@ void scale_givens(T* out, const T* in, i64 n, float* out32, double* H, int ldh, 
                   int j, const double* hcol, const double* hcol2, const double* nrm2, double* res_out, int* ist,
                   const double* dpar, cudaStream_t s);
 void tri_solve_dev(const double* H, int ldh, const double* g, const int* ist, double* y, cudaStream_t);
+// control of device-driven solves (k_krylov.cu)
+void solve_init(double* dpar, int* ist, double rtol, int maxit, const double* rtol_p, const int* maxit_p,
+                cudaGraphConditionalHandle h, int* info, double* rel, cudaStream_t);
+void solve_check(const double* dpar, const int* ist, cudaGraphConditionalHandle h, int* info, double* rel,
+                 cudaStream_t);
+void refine_init(double* rst, int* rsi, cudaGraphConditionalHandle h, int* info, double* rel, cudaStream_t);
+void refine_sweep(double* rst, int* rsi, double rtol, double inner_tol, int maxit, int m, cudaStream_t);
+void refine_check(const double* rn2, double* rst, int* rsi, const int* inner, double rtol, int maxit,
+                  cudaGraphConditionalHandle h, int* info, double* rel, cudaStream_t);
+void cond_from(const int* flag, cudaGraphConditionalHandle h, cudaStream_t);
 template <typename T> void multi_axpy_dev(T* w, const T* V, i64 ldv, const int* ist, const double* coef,
                                           double sign, i64 n, int nparts, cudaStream_t);
 
 // k_noise.cu
 void philox_normals(unsigned long long seed, unsigned long long step, unsigned attempt, unsigned purpose,
                     i64 count, double* out, cudaStream_t);
+void philox_normals_p(const unsigned long long* sp, unsigned purpose, i64 count, double* out, cudaStream_t);
 void philox_words(unsigned long long seed, unsigned long long step, unsigned attempt, unsigned purpose,
                   unsigned long long first, i64 n_blocks, unsigned long long* out, cudaStream_t);
 void stress_divergence(const Dims&, const StressLayout&, const double* W, double c, double* out, cudaStream_t);

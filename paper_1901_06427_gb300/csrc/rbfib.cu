@@ -28,6 +28,7 @@ bool rbfib::pdl_enabled() {
 namespace {
 
 const double kDeltaDefault = 6.0554544523933395e-06;   // eps^(1/3), eps = 2^-52
+const double kInnerTol = 1e-4;   // relative reduction asked of each FP32 refinement sweep
 const double kBlobRadius = 0.91;                         // hydrodynamic radius of a 3-point blob, units of h
 const int kDenseBodyMaxRows = 1536;                      // 3 N_bl limit of the coupled body block
 const int kDenseBodyMaxBodyRows = 384;                   // 6 N_b limit of the coupled body block
@@ -188,7 +189,35 @@ struct rbfib_grid {
     long long per_iter = 0, fixed = 0;
   } cgraph[2][2];
   bool use_graphs = true;
-  cudaStream_t s_aux = nullptr;   // captures the nested IF bodies while a cycle graph is built
+  int cap_depth = 0;                       // nesting depth of the conditional body being captured
+  cudaStream_t cap_streams[8] = {};         // capture streams, one per nesting depth
+  // Device-driven SEM step: the whole step captured as one graph per grid
+  // (restart cycles and refinement sweeps in WHILE nodes, the body block's
+  // warm-start choice in an IF/ELSE node), run with no host round trip.
+  // dstep: seed, step, attempt; dinfo: per solve (rfd, stokes, main) 4 ints
+  // (iterations, status, cycles or sweeps, second Gram-Schmidt passes), then
+  // [12] rejected, [13] outside flag, [16..19] the refinement's inner solve;
+  // drel: per solve relative residual, [3] inner; drst / drsi: refinement
+  // state; dwarm: Newton-Schulz builds.
+  bool dev = false;
+  bool step_graphs = true;      // RBFIB_NO_STEP_GRAPH=1: host-orchestrated steps
+  int last_step_dev = 0;        // whether the last SEM step ran as the step graph
+  // launch accounting of the step graph: per solve slot the fixed launches of
+  // one pass of its WHILE body (a restart cycle, or a refinement sweep with
+  // its one-cycle inner solve) and one iteration's launches; the launches
+  // outside every WHILE body
+  long long cap_body_fixed[3] = {}, cap_per_iter[3] = {}, cap_bodies = 0, cap_outside = 0;
+  long long ns_warm_dev = 0;    // Newton-Schulz builds of device-driven steps
+  DBuf<unsigned long long> dstep;
+  DBuf<int> dinfo, drsi;
+  DBuf<double> drel, drst;
+  DBuf<long long> dwarm;
+  struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    double* q = nullptr;
+    double* quat = nullptr;
+    rbfib_sem_params p{};
+  } sgraph;
   DBuf<int> gst;
   DBuf<double> dpar;
   // kernel timer (roofline reports): events around launches of one class
@@ -241,6 +270,8 @@ void drop_graphs(rbfib_grid* g) {
       if (c.exec) cudaGraphExecDestroy(c.exec);
       c = rbfib_grid::CycleGraph();
     }
+  if (g->sgraph.exec) cudaGraphExecDestroy(g->sgraph.exec);
+  g->sgraph = rbfib_grid::StepGraph();
 }
 
 int fail(rbfib_grid* g, int code, const std::string& msg) {
@@ -504,16 +535,24 @@ void apply_A(rbfib_grid* g, const T* x, T* y, bool with_bodies) {
 // solve to 1e-8 (or the tests' 1e-12) can notice, and the true residual
 // checked at the end of every restart cycle guards the result; on the
 // two-sphere solves the first pass keeps well above that, so the FP64 sweeps
-// halve.  FP32 (the refinement's inner solve, where eps is 6e-8): the usual
-// DGKS constant 1/sqrt(2).  RBFIB_REORTH_TAU64 overrides the FP64 value
-// (1 re-orthogonalises always).
+// halve.  FP32 (the refinement's inner solves to 1e-4, where eps is 6e-8):
+// tau = 1e-2 (at most about 6e-6 lost per vector); the DGKS constant
+// 1/sqrt(2) re-orthogonalised nearly always and made the refined two-sphere
+// step 10% slower (68.7 against 76.5 steps/s) with the same iterations.
+// RBFIB_REORTH_TAU64 and RBFIB_REORTH_TAU32 override the values (1
+// re-orthogonalises always).
 double reorth_tau2(bool fp64) {
   static const double t64 = [] {
     const char* e = std::getenv("RBFIB_REORTH_TAU64");
     const double t = e ? std::atof(e) : 1e-3;
     return t * t;
   }();
-  return fp64 ? t64 : 0.5;
+  static const double t32 = [] {
+    const char* e = std::getenv("RBFIB_REORTH_TAU32");
+    const double t = e ? std::atof(e) : 1e-2;
+    return t * t;
+  }();
+  return fp64 ? t64 : t32;
 }
 
 int read_int(rbfib_grid* g, const int* dev) {
@@ -604,14 +643,73 @@ int fgmres(rbfib_grid* g, const T* b, T* x, bool with_bodies, double rtol, int m
   }
 }
 
-// One restart cycle of FGMRES(m) as a CUDA graph: the cycle start, then m
-// Arnoldi iterations, iteration j inside an IF node whose condition a small
-// kernel sets from the device continue-flag written by iteration j-1's
-// Givens update (so at most m iterations run per launch, whatever the
-// flags), then the solution update and the true residual w = b - A x with its
-// norm.  The host launches one graph per restart and reads three numbers.
+// ------------------------------------------------------- graph capture
+// Conditional nodes are added to the graph being captured on g->s; each body
+// graph is captured on a stream of a small pool indexed by nesting depth
+// (a cycle graph nests the reorthogonalisation IF inside the iteration IF;
+// the device-driven SEM step puts cycles inside WHILE nodes, and the
+// refinement's inner solve inside another WHILE).
+constexpr int kCapDepth = 8;
+
+cudaStream_t cap_stream(rbfib_grid* g, int depth) {
+  if (depth >= kCapDepth) throw CudaError{cudaErrorInvalidValue};
+  if (!g->cap_streams[depth]) ck(cudaStreamCreateWithFlags(&g->cap_streams[depth], cudaStreamNonBlocking));
+  return g->cap_streams[depth];
+}
+
+cudaGraphConditionalHandle new_handle(rbfib_grid* g, unsigned dflt) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t capg = nullptr;
+  ck(cudaStreamGetCaptureInfo(g->s, &cst, nullptr, &capg, nullptr, nullptr, nullptr));
+  cudaGraphConditionalHandle h;
+  ck(cudaGraphConditionalHandleCreate(&h, capg, dflt, cudaGraphCondAssignDefault));
+  return h;
+}
+
+// Adds a conditional node (IF with one or two bodies, or WHILE) after the
+// work captured so far on g->s and captures body b with fill(b).
+template <typename F>
+void cond_node(rbfib_grid* g, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, int nbody, F fill) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t capg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  ck(cudaStreamGetCaptureInfo(g->s, &cst, nullptr, &capg, &deps, nullptr, &nd));
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = type;
+  p.conditional.size = nbody;
+  cudaGraphNode_t node;
+  ck(cudaGraphAddNode(&node, capg, deps, nullptr, nd, &p));
+  ck(cudaStreamUpdateCaptureDependencies(g->s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaStream_t outer = g->s;
+  const int depth = ++g->cap_depth;
+  for (int bi = 0; bi < nbody; ++bi) {
+    cudaGraph_t body = p.conditional.phGraph_out[bi];
+    cudaStream_t sb = cap_stream(g, depth);
+    ck(cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    g->s = sb;
+    try {
+      fill(bi);
+    } catch (...) {
+      cudaGraph_t t;
+      cudaStreamEndCapture(sb, &t);
+      g->s = outer;
+      --g->cap_depth;
+      throw;
+    }
+    ck(cudaStreamEndCapture(sb, &body));
+    g->s = outer;
+  }
+  --g->cap_depth;
+}
+
+// Iteration j of a captured restart cycle (the body of its IF node).  The
+// second Gram-Schmidt pass sits in a nested IF node whose condition the
+// first pass's multi-axpy sets (ReorthCtl).
 template <typename T>
-void capture_iteration(rbfib_grid* g, int j, const T* /*b*/, bool wb) {
+void capture_iteration(rbfib_grid* g, int j, bool wb) {
   KrylovStore<T>& K = kr_of<T>(g);
   const int m = K.m;
   const i64 n = wb ? g->n_total() : g->nfl, ld = K.n, nfl = g->nfl;
@@ -622,124 +720,88 @@ void capture_iteration(rbfib_grid* g, int j, const T* /*b*/, bool wb) {
   T* w = K.w;
   precond_any(g, V + (i64)j * ld, Z + (i64)j * ld, wb, true);
   apply_A<T>(g, Z + (i64)j * ld, w, wb);
-  // The second Gram-Schmidt pass sits in an IF node whose condition the
-  // first pass's multi-axpy sets (ReorthCtl); g->s is the stream capturing
-  // this iteration's body graph.
-  cudaStreamCaptureStatus cst;
-  cudaGraph_t capg = nullptr;
-  ck(cudaStreamGetCaptureInfo(g->s, &cst, nullptr, &capg, nullptr, nullptr, nullptr));
-  cudaGraphConditionalHandle h2;
-  ck(cudaGraphConditionalHandleCreate(&h2, capg, 0u, cudaGraphCondAssignDefault));
+  const cudaGraphConditionalHandle h2 = new_handle(g, 0u);
   const ReorthCtl rc{g->gst.p + 4, sp.hcol2, reorth_tau2(sizeof(T) == 8), h2, 1};
   multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol, g->s);
   multi_axpy<T>(w, V, ld, j + 1, sp.hcol, -1.0, n, nfl, wf, g->part, g->nparts, sp.nrm2, g->s, &rc);
-  {
-    const cudaGraphNode_t* deps = nullptr;
-    size_t nd = 0;
-    ck(cudaStreamGetCaptureInfo(g->s, &cst, nullptr, &capg, &deps, nullptr, &nd));
-    cudaGraphNodeParams p = {};
-    p.type = cudaGraphNodeTypeConditional;
-    p.conditional.handle = h2;
-    p.conditional.type = cudaGraphCondTypeIf;
-    p.conditional.size = 1;
-    cudaGraphNode_t node;
-    ck(cudaGraphAddNode(&node, capg, deps, nullptr, nd, &p));
-    ck(cudaStreamUpdateCaptureDependencies(g->s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-    cudaGraph_t body = p.conditional.phGraph_out[0];
-    cudaStream_t outer = g->s, s2 = g->s_aux;
-    ck(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    g->s = s2;
+  cond_node(g, h2, cudaGraphCondTypeIf, 1, [&](int) {
     multi_dot<T>(w, V, ld, j + 1, n, nfl, wf, g->part, g->nparts, sp.hcol2, g->s);
     multi_axpy<T>(w, V, ld, j + 1, sp.hcol2, -1.0, n, nfl, wf, g->part, g->nparts, sp.nrm2, g->s);
-    ck(cudaStreamEndCapture(s2, &body));
-    g->s = outer;
-  }
+  });
   scale_givens<T>(V + (i64)(j + 1) * ld, w, n, basis32<T>(g), sp.H, m + 1, sp.cs, sp.sn, sp.gv, j, sp.hcol,
                   sp.hcol2, sp.nrm2, sp.res, g->gst, g->dpar, g->s);
 }
 
+// One restart cycle of FGMRES(m), captured on g->s: the cycle start, then m
+// Arnoldi iterations, iteration j inside an IF node whose condition a small
+// kernel sets from the device continue-flag written by iteration j-1's
+// Givens update (so at most m iterations run, whatever the flags), then the
+// solution update and the true residual w = b - A x with its norm in
+// dpar[2].  per_iter (if not null) receives the launches of one iteration
+// with its gated second pass (two launches).
 template <typename T>
-bool build_cycle_graph(rbfib_grid* g, const T* b, T* x, bool wb, rbfib_grid::CycleGraph& G) {
+void capture_cycle(rbfib_grid* g, const T* b, T* x, bool wb, long long* per_iter) {
   KrylovStore<T>& K = kr_of<T>(g);
   const int m = K.m;
   const i64 n = wb ? g->n_total() : g->nfl, ld = K.n, nfl = g->nfl;
   const double wf = g->dV;
   SmallPtrs sp = small_ptrs(g, m);
-  cudaStream_t s0 = g->s, sc = nullptr, sb = nullptr;
+  fg_start<T>(K.V, K.w, n, sp.gv, m, g->gst, g->dpar, g->s, basis32<T>(g));
+  for (int j = 0; j < m; ++j) {
+    const cudaGraphConditionalHandle h = new_handle(g, j == 0 ? 1u : 0u);
+    if (j > 0) set_condition(h, g->gst, g->s);
+    const long long a0 = rbfib::g_launches.load();
+    cond_node(g, h, cudaGraphCondTypeIf, 1, [&](int) { capture_iteration<T>(g, j, wb); });
+    if (j == 0 && per_iter) *per_iter = (long long)rbfib::g_launches.load() - a0;
+  }
+  tri_solve_dev(sp.H, m + 1, sp.gv, g->gst, sp.y, g->s);
+  multi_axpy_dev<T>(x, K.Z, ld, g->gst, sp.y, 1.0, n, g->nparts, g->s);
+  apply_A<T>(g, x, K.w, wb);
+  axpby<T>(K.w, b, 1.0, -1.0, n, g->s);
+  multi_dot<T>(K.w, K.w, ld, 1, n, nfl, wf, g->part, g->nparts, g->dpar + 2, g->s);
+}
+
+// A restart cycle as a graph of its own (the host-orchestrated solves launch
+// one per restart and read three numbers).
+template <typename T>
+bool build_cycle_graph(rbfib_grid* g, const T* b, T* x, bool wb, rbfib_grid::CycleGraph& G) {
+  const int m = kr_of<T>(g).m;
+  const i64 n = wb ? g->n_total() : g->nfl;
+  cudaStream_t s0 = g->s, sc = nullptr;
   const int saved_timer = g->timer_kind;
   bool ok = true;
   const long long l0 = rbfib::g_launches.load();
   long long per_iter = 0;
   cudaGraph_t graph = nullptr;
   if (cudaStreamCreateWithFlags(&sc, cudaStreamNonBlocking) != cudaSuccess) return false;
-  if (cudaStreamCreateWithFlags(&sb, cudaStreamNonBlocking) != cudaSuccess) { cudaStreamDestroy(sc); return false; }
-  if (cudaStreamCreateWithFlags(&g->s_aux, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaStreamDestroy(sb); cudaStreamDestroy(sc); g->s_aux = nullptr; return false;
-  }
   g->timer_kind = 0;
   g->s = sc;
+  g->cap_depth = 0;
   try {
     ck(cudaStreamBeginCapture(sc, cudaStreamCaptureModeRelaxed));
-    fg_start<T>(K.V, K.w, n, sp.gv, m, g->gst, g->dpar, sc, basis32<T>(g));
-    for (int j = 0; j < m; ++j) {
-      cudaStreamCaptureStatus cst;
-      cudaGraph_t capg = nullptr;
-      ck(cudaStreamGetCaptureInfo(sc, &cst, nullptr, &capg, nullptr, nullptr, nullptr));
-      cudaGraphConditionalHandle h;
-      ck(cudaGraphConditionalHandleCreate(&h, capg, j == 0 ? 1u : 0u, cudaGraphCondAssignDefault));
-      if (j > 0) set_condition(h, g->gst, sc);
-      const cudaGraphNode_t* deps = nullptr;
-      size_t nd = 0;
-      ck(cudaStreamGetCaptureInfo(sc, &cst, nullptr, &capg, &deps, nullptr, &nd));
-      cudaGraphNodeParams p = {};
-      p.type = cudaGraphNodeTypeConditional;
-      p.conditional.handle = h;
-      p.conditional.type = cudaGraphCondTypeIf;
-      p.conditional.size = 1;
-      cudaGraphNode_t node;
-      ck(cudaGraphAddNode(&node, capg, deps, nullptr, nd, &p));
-      ck(cudaStreamUpdateCaptureDependencies(sc, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-      cudaGraph_t body = p.conditional.phGraph_out[0];
-      g->s = sb;
-      ck(cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-      const long long a0 = rbfib::g_launches.load();
-      capture_iteration<T>(g, j, b, wb);
-      if (j == 0) per_iter = (long long)rbfib::g_launches.load() - a0;
-      ck(cudaStreamEndCapture(sb, &body));
-      g->s = sc;
-    }
-    tri_solve_dev(sp.H, m + 1, sp.gv, g->gst, sp.y, sc);
-    multi_axpy_dev<T>(x, K.Z, ld, g->gst, sp.y, 1.0, n, g->nparts, sc);
-    apply_A<T>(g, x, K.w, wb);
-    axpby<T>(K.w, b, 1.0, -1.0, n, sc);
-    multi_dot<T>(K.w, K.w, ld, 1, n, nfl, wf, g->part, g->nparts, g->dpar + 2, sc);
+    capture_cycle<T>(g, b, x, wb, &per_iter);
     ck(cudaStreamEndCapture(sc, &graph));
     ck(cudaGraphInstantiate(&G.exec, graph, 0));
   } catch (CudaError&) {
     ok = false;
     cudaStreamCaptureStatus cst;
-    if (cudaStreamIsCapturing(g->s_aux, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
-      cudaGraph_t t; cudaStreamEndCapture(g->s_aux, &t);
-    }
-    if (cudaStreamIsCapturing(sb, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
-      cudaGraph_t t; cudaStreamEndCapture(sb, &t);
-    }
     if (cudaStreamIsCapturing(sc, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
-      cudaGraph_t t; cudaStreamEndCapture(sc, &t); if (t) cudaGraphDestroy(t);
+      cudaGraph_t t = nullptr;
+      cudaStreamEndCapture(sc, &t);
+      if (t) cudaGraphDestroy(t);
     }
     cudaGetLastError();
   }
   if (graph) cudaGraphDestroy(graph);
   g->s = s0;
   g->timer_kind = saved_timer;
-  cudaStreamDestroy(g->s_aux);
-  g->s_aux = nullptr;
-  cudaStreamDestroy(sb);
+  g->cap_depth = 0;
   cudaStreamDestroy(sc);
   const long long captured = (long long)rbfib::g_launches.load() - l0;
   rbfib::g_launches.fetch_sub((unsigned long long)captured);   // captured, not launched
+  // an iteration's launches, counting its gated second pass (two launches)
   G.per_iter = per_iter;
-  G.fixed = captured - (long long)m * per_iter;
+  G.fixed = captured - (long long)m * G.per_iter;
   G.b = b; G.x = x; G.n = n;
   return ok;
 }
@@ -958,6 +1020,24 @@ bool inverse6(double A[36]) {
 // point with RBFIB_EINTERNAL.
 void build_body_block(rbfib_grid* g, const double* r, const double* arm, const double* quat) {
   const double* qold = (quat && g->dquat_valid) ? g->dquat.p : nullptr;
+  if (g->dev) {
+    // captured: the warm start (the step graph is built only when the block
+    // holds a valid inverse) with the choice between Newton-Schulz and
+    // Gauss-Jordan made on the device; the status goes to dinfo[13]
+    const double a = kBlobRadius * g->desc.h;
+    ck(cudaMemsetAsync(g->dstatus, 0, sizeof(int), g->s));
+    dense_body_warm_start(g->nbl, g->bob, r, quat, qold, a, g->desc.eta, g->dM, g->dMw, g->dTw, g->dss, g->s);
+    const cudaGraphConditionalHandle h = new_handle(g, 0u);
+    ns_decide(g->dss, h, g->dwarm, g->s);
+    cond_node(g, h, cudaGraphCondTypeIf, 2, [&](int branch) {
+      if (branch == 0) dense_body_ns(g->nbl, g->dM, g->dMw, g->dTw, g->dUw, g->dss, g->s);
+      else dense_body_gj(g->nbl, g->dM, g->dMw, g->dstatus, g->s);
+    });
+    dense_body_finish(g->nbl, g->nb, g->boff, arm, g->dM, g->dP, g->dN, g->dstatus, g->s);
+    ck(cudaMemcpyAsync(g->dinfo.p + 13, g->dstatus.p, sizeof(int), cudaMemcpyDeviceToDevice, g->s));
+    if (quat) ck(cudaMemcpyAsync(g->dquat.p, quat, sizeof(double) * 4 * g->nb, cudaMemcpyDeviceToDevice, g->s));
+    return;
+  }
   bool used = false;
   const bool warm = g->dM_valid;
   g->dM_valid = false;
@@ -1102,7 +1182,13 @@ uint64_t rbfib_launch_count(void) { return rbfib::g_launches.load(); }
 int rbfib_body_block_info(const rbfib_grid* g, int32_t* dense, int64_t* warm_starts) {
   if (!g) return RBFIB_EINVAL;
   if (dense) *dense = g->dense_body ? 1 : 0;
-  if (warm_starts) *warm_starts = g->ns_warm;
+  if (warm_starts) *warm_starts = g->ns_warm + g->ns_warm_dev;
+  return RBFIB_OK;
+}
+
+int rbfib_step_mode(const rbfib_grid* g, int32_t* device_driven) {
+  if (!g || !device_driven) return RBFIB_EINVAL;
+  *device_driven = g->last_step_dev;
   return RBFIB_OK;
 }
 
@@ -1193,6 +1279,8 @@ int rbfib_kernel_timer_read(rbfib_grid* g, double* total_ms, int64_t* launches, 
 // with its stream synchronised, so the next call may run on another stream.
 void rbfib_grid_bind_stream(rbfib_grid* g, cudaStream_t s) { g->s = s; }
 
+
+
 extern "C" {
 
 int rbfib_create_grid(const rbfib_grid_desc* desc, void* stream, rbfib_grid** out) {
@@ -1228,7 +1316,15 @@ int rbfib_create_grid(const rbfib_grid_desc* desc, void* stream, rbfib_grid** ou
     ck(cudaMallocHost((void**)&g->h_pinned, 64 * sizeof(double)));
     g->gst.alloc(8);
     g->dpar.alloc(8);
+    g->dstep.alloc(4);
+    g->dinfo.alloc(32);
+    g->drsi.alloc(8);
+    g->drel.alloc(8);
+    g->drst.alloc(8);
+    g->dwarm.alloc(1);
+    ck(cudaMemsetAsync(g->dwarm.p, 0, sizeof(long long), g->s));
     if (const char* e = std::getenv("RBFIB_NO_GRAPHS")) g->use_graphs = (e[0] == '0');
+    if (const char* e = std::getenv("RBFIB_NO_STEP_GRAPH")) g->step_graphs = (e[0] == '0');
     g->mg32.build(g->levels);
     g->bcount.alloc(g->nc + 1);
     g->bfill.alloc(g->nc);
@@ -1258,6 +1354,8 @@ void rbfib_destroy(rbfib_grid* g) {
   for (cudaEvent_t e : g->tev) cudaEventDestroy(e);
   drop_graphs(g);
   if (g->h_pinned) cudaFreeHost(g->h_pinned);
+  for (cudaStream_t& cs : g->cap_streams)
+    if (cs) cudaStreamDestroy(cs);
   delete g;
 }
 
@@ -1475,9 +1573,83 @@ void build_rhs(rbfib_grid* g, const double* FT, const double* slip, const double
     ck(cudaMemcpyAsync(b + g->nfl + 3 * (i64)g->nbl, FT, sizeof(double) * 6 * g->nb, cudaMemcpyDeviceToDevice, g->s));
 }
 
+// ------------------------------------------------- device-driven solves
+// Captured on g->s (the step graph being built): no host reads.  The restart
+// cycles of a solve run in a WHILE node whose condition the check after each
+// cycle sets; info / rel receive iterations, status, cycles, second passes
+// and the true relative residual.  rtol_p / maxit_p (device, may be null)
+// override rtol / maxit (the refinement's inner solves).
+// Returns the launches captured in the WHILE body; per_iter (may be null)
+// receives one iteration's launches with its gated second pass.
+template <typename T>
+long long solve_dev(rbfib_grid* g, const T* b, T* x, bool wb, double rtol, int maxit, const double* rtol_p,
+                    const int* maxit_p, int* info, double* rel, long long* per_iter) {
+  KrylovStore<T>& K = kr_of<T>(g);
+  const i64 n = wb ? g->n_total() : g->nfl, ld = K.n, nfl = g->nfl;
+  multi_dot<T>(b, b, ld, 1, n, nfl, g->dV, g->part, g->nparts, g->dpar + 3, g->s);
+  ck(cudaMemsetAsync(x, 0, sizeof(T) * n, g->s));
+  ck(cudaMemcpyAsync(K.w, b, sizeof(T) * n, cudaMemcpyDeviceToDevice, g->s));
+  const cudaGraphConditionalHandle h = new_handle(g, 0u);
+  solve_init(g->dpar, g->gst, rtol, maxit, rtol_p, maxit_p, h, info, rel, g->s);
+  const long long a0 = rbfib::g_launches.load();
+  cond_node(g, h, cudaGraphCondTypeWhile, 1, [&](int) {
+    capture_cycle<T>(g, b, x, wb, per_iter);
+    solve_check(g->dpar, g->gst, h, info, rel, g->s);
+  });
+  return (long long)rbfib::g_launches.load() - a0;
+}
+
+// FP32 kernels inside FP64 refinement, device-driven: the sweeps run in a
+// WHILE node around the inner FP32 solve's own WHILE node.
+long long refine_dev(rbfib_grid* g, const double* b, double* x, bool wb, int* info, double* rel, long long* per_iter) {
+  const i64 n = wb ? g->n_total() : g->nfl;
+  const double rtol = g->desc.rtol;
+  double* r = g->rres;
+  int* inner = g->dinfo.p + 16;
+  multi_dot<double>(b, b, n, 1, n, g->nfl, g->dV, g->part, g->nparts, g->drst.p + 0, g->s);
+  ck(cudaMemsetAsync(x, 0, sizeof(double) * n, g->s));
+  ck(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->s));
+  const cudaGraphConditionalHandle h = new_handle(g, 0u);
+  refine_init(g->drst, g->drsi, h, info, rel, g->s);
+  const long long a0 = rbfib::g_launches.load();
+  cond_node(g, h, cudaGraphCondTypeWhile, 1, [&](int) {
+    refine_sweep(g->drst, g->drsi, rtol, kInnerTol, g->desc.max_iter, kr_of<float>(g).m, g->s);
+    convert<double, float>(r, g->f32a, n, g->s);
+    solve_dev<float>(g, g->f32a, g->f32b, wb, 0.0, 0, g->drst.p + 2, g->drsi.p + 3, inner, g->drel.p + 3,
+                     per_iter);
+    convert<float, double>(g->f32b, r, n, g->s);
+    axpby<double>(x, r, 1.0, 1.0, n, g->s);
+    apply_A<double>(g, x, r, wb);
+    axpby<double>(r, b, 1.0, -1.0, n, g->s);
+    multi_dot<double>(r, r, n, 1, n, g->nfl, g->dV, g->part, g->nparts, g->drst.p + 3, g->s);
+    refine_check(g->drst.p + 3, g->drst, g->drsi, inner, rtol, g->desc.max_iter, h, info, rel, g->s);
+  });
+  return (long long)rbfib::g_launches.load() - a0;
+}
+
 // Solve A x = b (FP64 in and out).  FP64 mode: FGMRES in FP64.  FP32 mode:
-// iterative refinement, r = b - A x in FP64, inner FGMRES in FP32.
-int solve_system(rbfib_grid* g, const double* b, double* x, bool with_bodies, rbfib_solve_info* info) {
+// iterative refinement, r = b - A x in FP64, inner FGMRES in FP32.  While the
+// device-driven step is captured (g->dev), the solve is captured instead,
+// reporting into slot `which` of dinfo / drel.
+int solve_system(rbfib_grid* g, const double* b, double* x, bool with_bodies, rbfib_solve_info* info,
+                 int which = -1) {
+  if (g->dev) {
+    int* di = g->dinfo.p + 4 * which;
+    double* dr = g->drel.p + which;
+    long long per_iter = 0, body = 0;
+    if (g->desc.precision == RBFIB_FP64)
+      body = solve_dev<double>(g, b, x, with_bodies, g->desc.rtol, g->desc.max_iter, nullptr, nullptr, di, dr,
+                               &per_iter);
+    else
+      body = refine_dev(g, b, x, with_bodies, di, dr, &per_iter);
+    // one pass of the WHILE body: its fixed part plus m iterations
+    const int m = g->desc.precision == RBFIB_FP64 ? kr_of<double>(g).m : kr_of<float>(g).m;
+    g->cap_body_fixed[which] = body - (long long)m * per_iter;
+    g->cap_per_iter[which] = per_iter;
+    g->cap_bodies += body;
+    project_mean(x + g->nf, g->nc, g->part, g->nparts, g->s);
+    return 0;
+  }
   const i64 n = with_bodies ? g->n_total() : g->nfl;
   const double rtol = g->desc.rtol;
   int iters = 0, st = 0;
@@ -1497,18 +1669,25 @@ int solve_system(rbfib_grid* g, const double* b, double* x, bool with_bodies, rb
     ck(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->s));
     int sweeps = 0, total = 0;
     rel = 1.0;
-    // Each FP32 sweep reduces the residual by 1e-4.  Deeper sweeps do not pay
-    // on GB300: 1e-5 costs more iterations in total on the two-sphere grid,
-    // and 1e-6 stalls on a 128 x 128 x 64 grid (FP32 loses the orthogonality
-    // it would need).
-    const double inner_tol = 1e-4;
+    // Each FP32 sweep asks for a reduction of inner_tol relative to its own
+    // right-hand side, but at most the remaining factor to rtol (halved,
+    // so the last sweep lands below it), and runs at most one restart
+    // cycle: an FP32 solve whose residual estimate stalls near FP32
+    // roundoff then hands back after m iterations instead of running on.
+    // Measured on the two-sphere SEM step (iterations of the three solves,
+    // steps/s): 1e-4: 39/19/38, 76.5; 1e-5: 43/21/41, 71.9; 1e-6: 39/20/40,
+    // 73.6 (every solve takes two sweeps in each case).
+    const double inner_tol = kInnerTol;
+    const int inner_cap = kr_of<float>(g).m;
     while (rel > rtol && total < g->desc.max_iter && sweeps < 50) {
       convert<double, float>(r, g->f32a, n, g->s);
       int it = 0;
       double irel = 0.0;
+      const double tol_s = std::max(inner_tol, 0.5 * rtol / rel);
+      const int cap = std::min(g->desc.max_iter - total, inner_cap);
       int ist = use_graph_path(g)
-                    ? fgmres_graph<float>(g, g->f32a, g->f32b, with_bodies, inner_tol, g->desc.max_iter - total, it, irel)
-                    : fgmres<float>(g, g->f32a, g->f32b, with_bodies, inner_tol, g->desc.max_iter - total, it, irel);
+                    ? fgmres_graph<float>(g, g->f32a, g->f32b, with_bodies, tol_s, cap, it, irel)
+                    : fgmres<float>(g, g->f32a, g->f32b, with_bodies, tol_s, cap, it, irel);
       total += it;
       ++sweeps;
       if (ist == RBFIB_ENAN) { st = ist; break; }
@@ -1728,96 +1907,271 @@ int rbfib_mobility_solve_adjoint(rbfib_grid* g, const double* dL_dU, const doubl
   return RBFIB_OK;
 }
 
-// Algorithm 1 (Split-Euler-Maruyama), steps 1-7.
+}  // extern "C"
+
+namespace {
+
+// The body of one SEM step (Algorithm 1, steps 1-7).  Host-orchestrated
+// (g->dev false): solves return their status and the rejection test is read
+// on the host.  Captured for the device-driven step (g->dev true): the
+// random-stream counters come from g->dstep, every solve is device-driven
+// and the accept kernel copies the new configuration to (q, quat) unless a
+// blob left the domain or a status word is set.  Returns the first nonzero
+// solve status (host-orchestrated).
+int sem_step_body(rbfib_grid* g, const rbfib_sem_params* p, uint64_t seed, uint64_t step, uint32_t attempt,
+                  double* q, double* quat, rbfib_step_info& loc) {
+  const int nb = g->nb, nbl = g->nbl;
+  const double delta = p->delta > 0 ? p->delta : kDeltaDefault;
+  const bool dev = g->dev;
+  int st = 0;
+  const i64 n = g->n_total();
+  const cudaStream_t s = g->s;
+  auto normals = [&](unsigned purpose, i64 count, double* out) {
+    if (dev) philox_normals_p(g->dstep, purpose, count, out, g->s);
+    else philox_normals(seed, step, attempt, purpose, count, out, g->s);
+  };
+  if (dev) ck(cudaMemsetAsync(g->dinfo.p, 0, sizeof(int) * 32, s));
+  // current configuration
+  if (nb) {
+    ck(cudaMemcpyAsync(g->cur.q, q, sizeof(double) * 3 * nb, cudaMemcpyDeviceToDevice, s));
+    ck(cudaMemcpyAsync(g->cur.quat, quat, sizeof(double) * 4 * nb, cudaMemcpyDeviceToDevice, s));
+  }
+  refresh_config(g, g->cur, true);
+  // forces F^n
+  body_forces(g->d, potentials_of(p), view_of(g, g->cur), p->force_ext, g->bodyF, s);
+  // step 1: random forces and torques W^FT = kT [W^f / L_p ; W^tau]
+  normals(2u, 6 * (i64)nb, g->bodyWn);
+  wft(nb, g->bodyWn, g->Lp, p->kT, g->bodyW, s);
+  // step 2: constrained solve with W^FT (homogeneous)
+  build_rhs(g, g->bodyW, nullptr, nullptr, false, g->bvec);
+  int st1 = solve_system(g, g->bvec, g->xvec, true, &loc.solve_rfd, 0);
+  if (st1) st = st1;
+  ck(cudaMemcpyAsync(g->xrfd, g->xvec, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  const double* v_rfd = g->xrfd;
+  const double* lam_rfd = g->xrfd.p + g->nfl;
+  const double* U_rfd = lam_rfd + 3 * (i64)nbl;
+  // step 3: displaced configurations Q+- (lab-frame rotations by +-(delta/2) W^tau)
+  move_bodies(nb, g->cur.q, g->cur.quat, g->bodyWn, g->Lp, 0.5 * delta, g->plus.q, g->plus.quat, s);
+  move_bodies(nb, g->cur.q, g->cur.quat, g->bodyWn, g->Lp, -0.5 * delta, g->minus.q, g->minus.quat, s);
+  refresh_config(g, g->plus, false);
+  refresh_config(g, g->minus, false);
+  // step 4: unconstrained Stokes solve with (S(Q+) - S(Q-)) lambda / delta
+  ck(cudaMemsetAsync(g->fsharp, 0, sizeof(double) * g->nf, s));
+  spread<double>(g->d, nbl, nullptr, g->plus.r, lam_rfd, 1.0 / (delta * g->dV), g->fsharp, s);
+  spread<double>(g->d, nbl, nullptr, g->minus.r, lam_rfd, -1.0 / (delta * g->dV), g->fsharp, s);
+  ck(cudaMemsetAsync(g->bvec, 0, sizeof(double) * g->nfl, s));
+  ck(cudaMemcpyAsync(g->bvec, g->fsharp, sizeof(double) * g->nf, cudaMemcpyDeviceToDevice, s));
+  int st2 = solve_system(g, g->bvec, g->xvec, false, &loc.solve_stokes, 1);
+  if (st2 && !st) st = st2;
+  ck(cudaMemcpyAsync(g->vsharp, g->xvec, sizeof(double) * g->nf, cudaMemcpyDeviceToDevice, s));
+  // step 5: random finite differences
+  Walls w0 = {};
+  kt_apply(nb, g->boff, g->plus.arm, lam_rfd, 1.0, 0.0, g->bodyA, s);
+  kt_apply(nb, g->boff, g->minus.arm, lam_rfd, 1.0, 0.0, g->bodyB, s);
+  axpby<double>(g->bodyA, g->bodyB, -1.0, 1.0, 6 * (i64)nb, s);          // A = KT+ - KT-
+  axpby<double>(g->bodyA, g->bodyA, 0.0, 1.0 / delta, 6 * (i64)nb, s);   // D^{K^T}
+  k_apply(nbl, g->bob, g->plus.arm, U_rfd, 1.0, 0.0, g->blobA, s);
+  k_apply(nbl, g->bob, g->minus.arm, U_rfd, 1.0, 0.0, g->blobB, s);
+  axpby<double>(g->blobA, g->blobB, -1.0, 1.0, 3 * (i64)nbl, s);
+  axpby<double>(g->blobA, g->blobA, 0.0, 1.0 / delta, 3 * (i64)nbl, s);  // D^K
+  interp<double>(g->d, w0, nbl, g->plus.r, v_rfd, 1.0, 0.0, 0.0, g->blobC, s);
+  interp<double>(g->d, w0, nbl, g->minus.r, v_rfd, 1.0, 0.0, 0.0, g->blobD, s);
+  axpby<double>(g->blobC, g->blobD, -1.0, 1.0, 3 * (i64)nbl, s);
+  axpby<double>(g->blobC, g->blobC, 0.0, 1.0 / delta, 3 * (i64)nbl, s);  // D^J
+  interp_tab(g->d, view_of(g, g->cur), g->vsharp, 1.0, 0.0, g->blobD, s);                          // D^S
+  // slip_tot = slip + D^K - D^J - D^S ; F_tot = F - D^{K^T}
+  if (p->slip) ck(cudaMemcpyAsync(g->blobS, p->slip, sizeof(double) * 3 * nbl, cudaMemcpyDeviceToDevice, s));
+  else ck(cudaMemsetAsync(g->blobS, 0, sizeof(double) * 3 * std::max(nbl, 1), s));
+  axpby<double>(g->blobS, g->blobA, 1.0, 1.0, 3 * (i64)nbl, s);
+  axpby<double>(g->blobS, g->blobC, -1.0, 1.0, 3 * (i64)nbl, s);
+  axpby<double>(g->blobS, g->blobD, -1.0, 1.0, 3 * (i64)nbl, s);
+  axpby<double>(g->bodyF, g->bodyA, -1.0, 1.0, 6 * (i64)nb, s);
+  // step 6: fluctuating constrained solve
+  normals(1u, g->stress.total, g->Wst);
+  stress_divergence(g->d, g->stress, g->Wst, std::sqrt(2.0 * g->desc.eta * p->kT / (g->dV * p->dt)), g->fnoise, s);
+  build_rhs(g, g->bodyF, g->blobS, g->fnoise, true, g->bvec);
+  int st3 = solve_system(g, g->bvec, g->xvec, true, &loc.solve_main, 2);
+  if (st3 && !st) st = st3;
+  // step 7: update and rejection test
+  const double* Un = g->xvec.p + g->nfl + 3 * (i64)nbl;
+  move_bodies(nb, g->cur.q, g->cur.quat, Un, nullptr, p->dt, g->next.q, g->next.quat, s);
+  refresh_config(g, g->next, false);
+  if (dev) {
+    int* flag = g->dinfo.p + 12;
+    outside_check(g->d, nbl, g->next.r, flag, s);
+    accept_step(nb, flag, g->dinfo.p + 1, 4, 4, g->next.q, g->next.quat, q, quat, g->dinfo.p + 14, s);
+    return 0;
+  }
+  int* flag = (int*)g->part.p;   // scratch word
+  ck(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  outside_check(g->d, nbl, g->next.r, flag, s);
+  int hflag = 0;
+  ck(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ck(cudaStreamSynchronize(s));
+  loc.rejected = hflag ? 1 : 0;
+  if (!hflag && !st && nb) {
+    ck(cudaMemcpyAsync(q, g->next.q, sizeof(double) * 3 * nb, cudaMemcpyDeviceToDevice, s));
+    ck(cudaMemcpyAsync(quat, g->next.quat, sizeof(double) * 4 * nb, cudaMemcpyDeviceToDevice, s));
+  }
+  ck(cudaStreamSynchronize(s));
+  ck(cudaGetLastError());
+  return st;
+}
+
+// Whether the step graph can be used: a coupled body block needs a valid
+// inverse at known orientations to warm-start from.
+bool step_graph_ok(rbfib_grid* g) {
+  return g->use_graphs && g->timer_kind == 0 && (!g->dense_body || (g->dM_valid && g->dquat_valid));
+}
+
+// Captures the device-driven step for (p, q, quat).  Returns false when the
+// capture or instantiation failed (the host-orchestrated step is used then).
+bool build_step_graph(rbfib_grid* g, const rbfib_sem_params* p, double* q, double* quat) {
+  if (g->sgraph.exec) cudaGraphExecDestroy(g->sgraph.exec);
+  g->sgraph = rbfib_grid::StepGraph();
+  cudaStream_t s0 = g->s;
+  const long long l0 = rbfib::g_launches.load();
+  cudaGraph_t graph = nullptr;
+  bool ok = true;
+  g->dev = true;
+  g->cap_depth = 0;
+  g->cap_bodies = 0;
+  g->s = cap_stream(g, 0);
+  try {
+    ck(cudaStreamBeginCapture(g->s, cudaStreamCaptureModeRelaxed));
+    rbfib_step_info loc{};
+    sem_step_body(g, p, 0, 0, 0, q, quat, loc);
+    ck(cudaStreamEndCapture(g->s, &graph));
+    ck(cudaGraphInstantiate(&g->sgraph.exec, graph, 0));
+  } catch (CudaError&) {
+    ok = false;
+    cudaStreamCaptureStatus cst;
+    if (cudaStreamIsCapturing(g->s, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+      cudaGraph_t t = nullptr;
+      cudaStreamEndCapture(g->s, &t);
+      if (t) cudaGraphDestroy(t);
+    }
+    cudaGetLastError();
+  }
+  if (graph) cudaGraphDestroy(graph);
+  g->dev = false;
+  g->cap_depth = 0;
+  g->s = s0;
+  const long long captured = (long long)rbfib::g_launches.load() - l0;
+  g->cap_outside = captured - g->cap_bodies;
+  rbfib::g_launches.fetch_sub((unsigned long long)captured);   // captured, not launched
+  if (!ok) {
+    g->sgraph = rbfib_grid::StepGraph();
+    return false;
+  }
+  g->sgraph.q = q;
+  g->sgraph.quat = quat;
+  g->sgraph.p = *p;
+  return true;
+}
+
+bool same_params(const rbfib_sem_params& a, const rbfib_sem_params& b) {
+  return std::memcmp(&a, &b, sizeof(rbfib_sem_params)) == 0;
+}
+
+// Launches the device-driven step on g->s (no host synchronisation).
+// Returns false if it could not be built (use the host-orchestrated step).
+bool step_graph_launch(rbfib_grid* g, const rbfib_sem_params* p, uint64_t seed, uint64_t step, uint32_t attempt,
+                       double* q, double* quat) {
+  if (!step_graph_ok(g)) return false;
+  if (!g->sgraph.exec || g->sgraph.q != q || g->sgraph.quat != quat || !same_params(g->sgraph.p, *p))
+    if (!build_step_graph(g, p, q, quat)) { g->use_graphs = false; return false; }
+  unsigned long long* hs = (unsigned long long*)(g->h_pinned + 48);
+  hs[0] = seed; hs[1] = step; hs[2] = attempt;
+  ck(cudaMemcpyAsync(g->dstep.p, hs, sizeof(unsigned long long) * 3, cudaMemcpyHostToDevice, g->s));
+  ck(cudaGraphLaunch(g->sgraph.exec, g->s));
+  int* hi = (int*)(g->h_pinned + 24);     // 32 ints: h_pinned[24..39]
+  ck(cudaMemcpyAsync(hi, g->dinfo.p, sizeof(int) * 32, cudaMemcpyDeviceToHost, g->s));
+  ck(cudaMemcpyAsync(g->h_pinned + 52, g->drel.p, sizeof(double) * 4, cudaMemcpyDeviceToHost, g->s));
+  ck(cudaMemcpyAsync(g->h_pinned + 56, g->dwarm.p, sizeof(long long), cudaMemcpyDeviceToHost, g->s));
+  return true;
+}
+
+// After the stream has been synchronised: the step's information and status.
+int step_graph_finish(rbfib_grid* g, rbfib_step_info* info) {
+  const int* hi = (const int*)(g->h_pinned + 24);
+  const double* hr = g->h_pinned + 52;
+  rbfib_step_info loc{};
+  rbfib_solve_info* si[3] = {&loc.solve_rfd, &loc.solve_stokes, &loc.solve_main};
+  int st = 0;
+  long long launches = g->cap_outside;
+  for (int k = 0; k < 3; ++k) {
+    si[k]->iterations = hi[4 * k];
+    si[k]->refinements = g->desc.precision == RBFIB_FP64 ? 0 : hi[4 * k + 2];
+    si[k]->rel_residual = hr[k];
+    if (hi[4 * k + 1] && !st) st = hi[4 * k + 1];
+    g->gs_iters += hi[4 * k];
+    g->reorth_passes += hi[4 * k + 3];
+    // launches that ran: per pass of the WHILE body its fixed part, per
+    // iteration its launches without the gated second pass, two per second
+    // pass taken
+    launches += (long long)hi[4 * k + 2] * g->cap_body_fixed[k] + (long long)hi[4 * k] * (g->cap_per_iter[k] - 2) +
+                2LL * hi[4 * k + 3];
+  }
+  rbfib::g_launches.fetch_add((unsigned long long)std::max(launches, 0LL));
+  g->ns_warm_dev = *(const long long*)(g->h_pinned + 56);
+  loc.rejected = hi[14];
+  if (info) *info = loc;
+  if (hi[13]) {
+    g->dM_valid = false;
+    g->dquat_valid = false;
+    drop_graphs(g);
+    return fail(g, RBFIB_EINTERNAL, "sem_step: body block: zero pivot in the Gauss-Jordan inversion");
+  }
+  if (st) return fail(g, st, "sem_step: a solve did not converge");
+  if (loc.rejected) return fail(g, RBFIB_EREJECT, "sem_step: unphysical configuration rejected");
+  return RBFIB_OK;
+}
+
+}  // namespace
+
+// Device-driven steps of ensemble systems (batch.cu).
+bool rbfib_grid_step_launch(rbfib_grid* g, const rbfib_sem_params* p, uint64_t seed, uint64_t step,
+                            uint32_t attempt, double* q, double* quat) {
+  if (!g || !p || (g->nb > 0 && (!q || !quat)) || !(p->dt > 0) || !(p->kT >= 0) || !g->step_graphs) return false;
+  try {
+    g->last_step_dev = step_graph_launch(g, p, seed, step, attempt, q, quat) ? 1 : 0;
+    return g->last_step_dev != 0;
+  } catch (CudaError&) {
+    cudaGetLastError();
+    return false;
+  }
+}
+
+int rbfib_grid_step_finish(rbfib_grid* g, rbfib_step_info* info) {
+  try {
+    ck(cudaGetLastError());
+    return step_graph_finish(g, info);
+  } catch (CudaError& e) {
+    return fail(g, e.code, std::string("sem_step: ") + e.what());
+  }
+}
+
+extern "C" {
+
+// Algorithm 1 (Split-Euler-Maruyama), steps 1-7.  With graphs (the
+// default) the whole step is one device-driven graph launch and one
+// synchronisation; otherwise the host orchestrates it.
 int rbfib_sem_step(rbfib_grid* g, const rbfib_sem_params* p, uint64_t seed, uint64_t step, uint32_t attempt,
                    double* q, double* quat, rbfib_step_info* info) {
   if (!g || !p || (g->nb > 0 && (!q || !quat)) || !(p->dt > 0) || !(p->kT >= 0))
     return fail(g, RBFIB_EINVAL, "sem_step: bad argument");
-  const int nb = g->nb, nbl = g->nbl;
-  const double delta = p->delta > 0 ? p->delta : kDeltaDefault;
   rbfib_step_info loc{};
   int st = 0;
   try {
-    const i64 n = g->n_total();
-    const cudaStream_t s = g->s;
-    // current configuration
-    if (nb) {
-      ck(cudaMemcpyAsync(g->cur.q, q, sizeof(double) * 3 * nb, cudaMemcpyDeviceToDevice, s));
-      ck(cudaMemcpyAsync(g->cur.quat, quat, sizeof(double) * 4 * nb, cudaMemcpyDeviceToDevice, s));
+    if (g->step_graphs && step_graph_launch(g, p, seed, step, attempt, q, quat)) {
+      g->last_step_dev = 1;
+      ck(cudaStreamSynchronize(g->s));
+      ck(cudaGetLastError());
+      return step_graph_finish(g, info);
     }
-    refresh_config(g, g->cur, true);
-    // forces F^n
-    body_forces(g->d, potentials_of(p), view_of(g, g->cur), p->force_ext, g->bodyF, s);
-    // step 1: random forces and torques W^FT = kT [W^f / L_p ; W^tau]
-    philox_normals(seed, step, attempt, 2u, 6 * (i64)nb, g->bodyWn, s);
-    wft(nb, g->bodyWn, g->Lp, p->kT, g->bodyW, s);
-    // step 2: constrained solve with W^FT (homogeneous)
-    build_rhs(g, g->bodyW, nullptr, nullptr, false, g->bvec);
-    int st1 = solve_system(g, g->bvec, g->xvec, true, &loc.solve_rfd);
-    if (st1) st = st1;
-    ck(cudaMemcpyAsync(g->xrfd, g->xvec, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    const double* v_rfd = g->xrfd;
-    const double* lam_rfd = g->xrfd.p + g->nfl;
-    const double* U_rfd = lam_rfd + 3 * (i64)nbl;
-    // step 3: displaced configurations Q+- (lab-frame rotations by +-(delta/2) W^tau)
-    move_bodies(nb, g->cur.q, g->cur.quat, g->bodyWn, g->Lp, 0.5 * delta, g->plus.q, g->plus.quat, s);
-    move_bodies(nb, g->cur.q, g->cur.quat, g->bodyWn, g->Lp, -0.5 * delta, g->minus.q, g->minus.quat, s);
-    refresh_config(g, g->plus, false);
-    refresh_config(g, g->minus, false);
-    // step 4: unconstrained Stokes solve with (S(Q+) - S(Q-)) lambda / delta
-    ck(cudaMemsetAsync(g->fsharp, 0, sizeof(double) * g->nf, s));
-    spread<double>(g->d, nbl, nullptr, g->plus.r, lam_rfd, 1.0 / (delta * g->dV), g->fsharp, s);
-    spread<double>(g->d, nbl, nullptr, g->minus.r, lam_rfd, -1.0 / (delta * g->dV), g->fsharp, s);
-    ck(cudaMemsetAsync(g->bvec, 0, sizeof(double) * g->nfl, s));
-    ck(cudaMemcpyAsync(g->bvec, g->fsharp, sizeof(double) * g->nf, cudaMemcpyDeviceToDevice, s));
-    int st2 = solve_system(g, g->bvec, g->xvec, false, &loc.solve_stokes);
-    if (st2 && !st) st = st2;
-    ck(cudaMemcpyAsync(g->vsharp, g->xvec, sizeof(double) * g->nf, cudaMemcpyDeviceToDevice, s));
-    // step 5: random finite differences
-    Walls w0 = {};
-    kt_apply(nb, g->boff, g->plus.arm, lam_rfd, 1.0, 0.0, g->bodyA, s);
-    kt_apply(nb, g->boff, g->minus.arm, lam_rfd, 1.0, 0.0, g->bodyB, s);
-    axpby<double>(g->bodyA, g->bodyB, -1.0, 1.0, 6 * (i64)nb, s);          // A = KT+ - KT-
-    axpby<double>(g->bodyA, g->bodyA, 0.0, 1.0 / delta, 6 * (i64)nb, s);   // D^{K^T}
-    k_apply(nbl, g->bob, g->plus.arm, U_rfd, 1.0, 0.0, g->blobA, s);
-    k_apply(nbl, g->bob, g->minus.arm, U_rfd, 1.0, 0.0, g->blobB, s);
-    axpby<double>(g->blobA, g->blobB, -1.0, 1.0, 3 * (i64)nbl, s);
-    axpby<double>(g->blobA, g->blobA, 0.0, 1.0 / delta, 3 * (i64)nbl, s);  // D^K
-    interp<double>(g->d, w0, nbl, g->plus.r, v_rfd, 1.0, 0.0, 0.0, g->blobC, s);
-    interp<double>(g->d, w0, nbl, g->minus.r, v_rfd, 1.0, 0.0, 0.0, g->blobD, s);
-    axpby<double>(g->blobC, g->blobD, -1.0, 1.0, 3 * (i64)nbl, s);
-    axpby<double>(g->blobC, g->blobC, 0.0, 1.0 / delta, 3 * (i64)nbl, s);  // D^J
-    interp_tab(g->d, view_of(g, g->cur), g->vsharp, 1.0, 0.0, g->blobD, s);                          // D^S
-    // slip_tot = slip + D^K - D^J - D^S ; F_tot = F - D^{K^T}
-    if (p->slip) ck(cudaMemcpyAsync(g->blobS, p->slip, sizeof(double) * 3 * nbl, cudaMemcpyDeviceToDevice, s));
-    else ck(cudaMemsetAsync(g->blobS, 0, sizeof(double) * 3 * std::max(nbl, 1), s));
-    axpby<double>(g->blobS, g->blobA, 1.0, 1.0, 3 * (i64)nbl, s);
-    axpby<double>(g->blobS, g->blobC, -1.0, 1.0, 3 * (i64)nbl, s);
-    axpby<double>(g->blobS, g->blobD, -1.0, 1.0, 3 * (i64)nbl, s);
-    axpby<double>(g->bodyF, g->bodyA, -1.0, 1.0, 6 * (i64)nb, s);
-    // step 6: fluctuating constrained solve
-    philox_normals(seed, step, attempt, 1u, g->stress.total, g->Wst, s);
-    stress_divergence(g->d, g->stress, g->Wst, std::sqrt(2.0 * g->desc.eta * p->kT / (g->dV * p->dt)), g->fnoise, s);
-    build_rhs(g, g->bodyF, g->blobS, g->fnoise, true, g->bvec);
-    int st3 = solve_system(g, g->bvec, g->xvec, true, &loc.solve_main);
-    if (st3 && !st) st = st3;
-    // step 7: update and rejection test
-    const double* Un = g->xvec.p + g->nfl + 3 * (i64)nbl;
-    move_bodies(nb, g->cur.q, g->cur.quat, Un, nullptr, p->dt, g->next.q, g->next.quat, s);
-    refresh_config(g, g->next, false);
-    int* flag = (int*)g->part.p;   // scratch word
-    ck(cudaMemsetAsync(flag, 0, sizeof(int), s));
-    outside_check(g->d, nbl, g->next.r, flag, s);
-    int hflag = 0;
-    ck(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    ck(cudaStreamSynchronize(s));
-    loc.rejected = hflag ? 1 : 0;
-    if (!hflag && !st && nb) {
-      ck(cudaMemcpyAsync(q, g->next.q, sizeof(double) * 3 * nb, cudaMemcpyDeviceToDevice, s));
-      ck(cudaMemcpyAsync(quat, g->next.quat, sizeof(double) * 4 * nb, cudaMemcpyDeviceToDevice, s));
-    }
-    ck(cudaStreamSynchronize(s));
-    ck(cudaGetLastError());
+    g->last_step_dev = 0;
+    st = sem_step_body(g, p, seed, step, attempt, q, quat, loc);
   } catch (CudaError& e) {
     return fail(g, e.code, std::string("sem_step: ") + e.what());
   }

@@ -42,6 +42,7 @@ def test_batch_step_matches_single_grids_and_oracle(B, precision):
     seeds = [1000 + i for i in range(len(ws))]
     status, infos = batch.sem_step(params, seeds, 3, q, quat)
     assert all(s == 0 for s in status)
+    assert all(m.step_mode() == 1 for m in batch.systems)   # each system ran its device-driven step graph
     for i, w in enumerate(ws):
         # the same system through a single grid
         g = B.grid_for(w, precision=prec, rtol=1e-11)
