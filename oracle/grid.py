@@ -18,8 +18,13 @@ import numpy as np
 
 
 class Grid:
-    def __init__(self, n, h=1.0, periodic=(False, False, False), wall_vel=None):
+    def __init__(self, n, h=1.0, periodic=(False, False, False), wall_vel=None, kernel=3):
+        """kernel: points per axis of the immersed-boundary kernel (3: the
+        three-point Peskin kernel; 6: the six-point kernel of Sec. III.B)."""
         self.n = tuple(int(v) for v in n)
+        if kernel not in (3, 6):
+            raise ValueError("kernel must be 3 or 6")
+        self.kernel = int(kernel)
         self.h = float(h)
         self.periodic = tuple(bool(p) for p in periodic)
         if all(self.periodic):

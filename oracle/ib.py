@@ -1,12 +1,13 @@
 """Immersed-boundary spreading S and interpolation J of Sec. III.B with the
-three-point kernel, including the wall treatment.
+three-point or the six-point kernel (Grid.kernel), including the wall
+treatment.
 
   (J v)_i = sum_alpha delta_h(x_alpha - r_i) v(x_alpha) dV      (= sum w v)
   (S l)_alpha = (1/dV) sum_i delta_h(x_alpha - r_i) l_i dV     (= sum w l / dV)
 
-with w = phi(dx/h) phi(dy/h) phi(dz/h).  For velocity component a the three
-kernel points along each axis are the three grid points nearest to the blob
-on that component's staggered grid (faces along a, cell centres otherwise).
+with w = phi(dx/h) phi(dy/h) phi(dz/h).  For velocity component a the kernel
+points along each axis are the 3 (or 6) grid points nearest to the blob on
+that component's staggered grid (faces along a, cell centres otherwise).
 
 Walls (our reading of the ghost-point treatment the paper cites): a point on a
 wall-normal boundary face holds the prescribed normal velocity (zero) and is
@@ -20,17 +21,20 @@ same folded weights, so J = dV S^T exactly (Sec. III.B).
 import numpy as np
 
 from .grid import Grid
-from .kernel import phi
+from .kernel import kernel
 
 
-def _axis_points(g: Grid, a, ax, x):
-    """For coordinates x (N,) along axis ax of component a: three candidate
-    points per blob -> (index p (N,3), weight (N,3))."""
+def _axis_points(g: Grid, a, ax, x, deriv=False):
+    """For coordinates x (N,) along axis ax of component a: the kernel's
+    candidate points per blob -> (index p (N,k), weight (N,k)) and, with
+    deriv, the weights' derivative with respect to x."""
+    phi, dphi, k, first = kernel(g.kernel)
     o = 0.0 if ax == a else 0.5
     s = x / g.h - o
-    i0 = np.floor(s + 0.5).astype(np.int64)
-    p = i0[:, None] + np.array([-1, 0, 1])[None, :]
+    p = first(s)[:, None] + np.arange(k)[None, :]
     w = phi(s[:, None] - p)
+    if deriv:
+        return p, w, dphi(s[:, None] - p) / g.h
     return p, w
 
 
@@ -63,25 +67,27 @@ def _fold(g: Grid, a, ax, p):
 
 
 def stencil(g: Grid, r, a):
-    """Folded 27-point stencils of blobs r (N,3) for velocity component a.
+    """Folded k^3-point stencils (k = Grid.kernel) of blobs r (N,3) for
+    velocity component a.
 
-    Returns (idx (N,27) flat index within the component, coef (N,27) folded
-    weight, affine (N,27) ghost boundary value times weight)."""
+    Returns (idx (N,k^3) flat index within the component, coef (N,k^3) folded
+    weight, affine (N,k^3) ghost boundary value times weight)."""
     r = np.asarray(r, dtype=np.float64).reshape(-1, 3)
     N = r.shape[0]
     ext = g.face_ext(a)
+    k = g.kernel
     per_axis = []
     for ax in range(3):
         p, w = _axis_points(g, a, ax, r[:, ax])
         comp, sign, wall, keep = _fold(g, a, ax, p)
         per_axis.append((comp, sign, wall, keep, w))
-    idx = np.zeros((N, 27), dtype=np.int64)
-    coef = np.zeros((N, 27))
-    aff = np.zeros((N, 27))
+    idx = np.zeros((N, k ** 3), dtype=np.int64)
+    coef = np.zeros((N, k ** 3))
+    aff = np.zeros((N, k ** 3))
     t = 0
-    for dz in range(3):
-        for dy in range(3):
-            for dx in range(3):
+    for dz in range(k):
+        for dy in range(k):
+            for dx in range(k):
                 d = (dx, dy, dz)
                 comps = [per_axis[ax][0][:, d[ax]] for ax in range(3)]
                 keep = np.ones(N, dtype=bool)
@@ -148,7 +154,7 @@ def J_matrix(g: Grid, r):
     rows, cols, vals = [], [], []
     for a in range(3):
         idx, coef, _ = stencil(g, r, a)
-        rr = np.repeat(3 * np.arange(r.shape[0]) + a, 27)
+        rr = np.repeat(3 * np.arange(r.shape[0]) + a, g.kernel ** 3)
         rows.append(rr); cols.append(idx.ravel() + g.face_offset(a)); vals.append(coef.ravel())
     return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                          shape=(3 * r.shape[0], g.N_f))
@@ -168,29 +174,24 @@ def S_matrix(g: Grid, r):
 
 def stencil_grad(g: Grid, r, a):
     """Derivatives of the folded weights of component a with respect to the
-    blob position: (idx (N,27), coef (N,27), dcoef (N,27,3)) where
+    blob position: (idx (N,k^3), coef (N,k^3), dcoef (N,k^3,3)) where
     dcoef[..., b] = d coef / d r_b = phi'(s_b - p_b)/h * prod_{c != b} phi * sign."""
-    from .kernel import dphi
     r = np.asarray(r, dtype=np.float64).reshape(-1, 3)
     N = r.shape[0]
     ext = g.face_ext(a)
+    k = g.kernel
     per_axis = []
     for ax in range(3):
-        o = 0.0 if ax == a else 0.5
-        s = r[:, ax] / g.h - o
-        i0 = np.floor(s + 0.5).astype(np.int64)
-        p = i0[:, None] + np.array([-1, 0, 1])[None, :]
-        w = phi(s[:, None] - p)
-        dw = dphi(s[:, None] - p) / g.h
+        p, w, dw = _axis_points(g, a, ax, r[:, ax], deriv=True)
         comp, sign, wall, keep = _fold(g, a, ax, p)
         per_axis.append((comp, sign, keep, w, dw))
-    idx = np.zeros((N, 27), dtype=np.int64)
-    coef = np.zeros((N, 27))
-    dcoef = np.zeros((N, 27, 3))
+    idx = np.zeros((N, k ** 3), dtype=np.int64)
+    coef = np.zeros((N, k ** 3))
+    dcoef = np.zeros((N, k ** 3, 3))
     t = 0
-    for dz in range(3):
-        for dy in range(3):
-            for dx in range(3):
+    for dz in range(k):
+        for dy in range(k):
+            for dx in range(k):
                 d = (dx, dy, dz)
                 comps = [per_axis[ax][0][:, d[ax]] for ax in range(3)]
                 keep = np.ones(N, dtype=bool)
