@@ -386,6 +386,37 @@ def run_monolayer(B, torch, steps=5, warmup=2, wall_speed=0.5):
     return out
 
 
+# ------------------------------------------------------ six-point kernel leg
+def run_kernel6(B, torch, steps=10, warmup=3):
+    """The two-sphere workload with the paper's six-point kernel (Sec. III.B):
+    SEM steps/s at rel. res. 1e-8 in FP64, and Krylov iterations per step."""
+    import numpy as np
+    import workloads
+    w = workloads.two_sphere_cavity(steps=steps, kernel=6)
+    g = B.grid_for(w, rtol=1e-8)
+    p = B.sem_params(w.potentials, dt=w.dt, kT=w.kT)
+    q = torch.tensor(w.q.ravel(), device="cuda")
+    quat = torch.tensor(w.quat.ravel(), device="cuda")
+    for k in range(warmup):
+        g.sem_step(p, w.seed, k, 0, q, quat)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    its = []
+    e0.record(stream)
+    for k in range(steps):
+        st, info = g.sem_step(p, w.seed, 1000 + k, 0, q, quat)
+        its.append([info[key]["iterations"] for key in ("solve_rfd", "solve_stokes", "solve_main")])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out = {"workload": w.name, "kernel": "six-point (three continuous derivatives)", "precision": "fp64",
+           "rtol": 1e-8, "steps_per_s": 1000.0 / ms, "ms_per_step": ms,
+           "krylov_iterations_per_step": [int(round(x)) for x in np.mean(its, axis=0)]}
+    g.close()
+    return out
+
+
 # ---------------------------------------------------------------- ensemble
 def run_ensemble(args, B, torch):
     """Batched ensemble: independent cuboids n ~ U{16, 20, ..., 48} with 1-16
@@ -629,6 +660,7 @@ def run_ours(args):
     line["adjoint"] = run_adjoint(B, torch)
     if not args.no_monolayer:
         line["monolayer"] = run_monolayer(B, torch)
+    line["kernel6"] = run_kernel6(B, torch)
     line["autotuned_blocks"] = dict(zip(["stokes_fp64", "stokes_fp32", "vel_sweep", "p_sweep"], g.tuned_blocks()))
     if args.ensemble:
         line["ensemble"] = run_ensemble(args, B, torch)

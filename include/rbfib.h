@@ -61,7 +61,9 @@ typedef struct {
   int32_t periodic[3];       /* 1: periodic axis, 0: no-slip walls on both ends */
   double  wall_vel[6][3];    /* walls -x,+x,-y,+y,-z,+z; tangential components  */
                              /* only (a normal component gives EINVAL)          */
-  int32_t kernel;            /* 3 = three-point Peskin kernel (only value)      */
+  int32_t kernel;            /* immersed-boundary kernel (Sec. III.B): 3 = the  */
+                             /* three-point Peskin kernel, 6 = the six-point    */
+                             /* kernel with three continuous derivatives        */
   int32_t precision;         /* RBFIB_FP64 or RBFIB_FP32_REFINED                */
   int32_t restart;           /* FGMRES restart length m (1..64)                 */
   int32_t max_iter;          /* total Krylov iterations allowed per solve       */

@@ -166,7 +166,7 @@ class Grid:
     """A MAC grid with its solver workspaces, bound to torch's current stream."""
 
     def __init__(self, n, h=1.0, eta=1.0, periodic=(False, False, False), wall_vel=None,
-                 precision=FP64, restart=30, max_iter=2000, rtol=1e-8):
+                 precision=FP64, restart=30, max_iter=2000, rtol=1e-8, kernel=3):
         d = GridDesc()
         for a in range(3):
             d.n[a] = int(n[a])
@@ -176,7 +176,8 @@ class Grid:
         for w in range(6):
             for c in range(3):
                 d.wall_vel[w][c] = float(wv[w, c])
-        d.kernel, d.precision, d.restart, d.max_iter, d.rtol = 3, int(precision), int(restart), int(max_iter), float(rtol)
+        d.kernel, d.precision, d.restart, d.max_iter, d.rtol = (int(kernel), int(precision), int(restart),
+                                                                int(max_iter), float(rtol))
         self.desc = d
         self.n = tuple(int(v) for v in n)
         self.stream = torch.cuda.current_stream()
@@ -389,7 +390,7 @@ class _BatchMember(Grid):
 
 
 def _desc(n, h=1.0, eta=1.0, periodic=(False, False, False), wall_vel=None, precision=FP64, restart=30,
-          max_iter=2000, rtol=1e-8):
+          max_iter=2000, rtol=1e-8, kernel=3):
     d = GridDesc()
     for a in range(3):
         d.n[a] = int(n[a])
@@ -399,7 +400,8 @@ def _desc(n, h=1.0, eta=1.0, periodic=(False, False, False), wall_vel=None, prec
     for w in range(6):
         for c in range(3):
             d.wall_vel[w][c] = float(wv[w, c])
-    d.kernel, d.precision, d.restart, d.max_iter, d.rtol = 3, int(precision), int(restart), int(max_iter), float(rtol)
+    d.kernel, d.precision, d.restart, d.max_iter, d.rtol = (int(kernel), int(precision), int(restart),
+                                                            int(max_iter), float(rtol))
     return d
 
 
@@ -416,7 +418,8 @@ class Batch:
         descs = (GridDesc * n)()
         for i, w in enumerate(workloads_):
             prec = precision if precision is not None else (FP32_REFINED if w.precision == "f32-refined" else FP64)
-            descs[i] = _desc(w.n, w.h, w.eta, w.periodic, w.wall_vel, prec, restart, max_iter, w.rtol)
+            descs[i] = _desc(w.n, w.h, w.eta, w.periodic, w.wall_vel, prec, restart, max_iter, w.rtol,
+                             getattr(w, "kernel", 3))
         h = ctypes.c_void_p()
         st = lib().rbfib_create_batch(n, descs, int(workers), ctypes.byref(h))
         if st != OK:
@@ -462,6 +465,7 @@ def grid_for(workload, precision=None, restart=48, max_iter=4000, rtol=None):
     """A Grid with the workload's bodies set."""
     prec = precision if precision is not None else (FP32_REFINED if workload.precision == "f32-refined" else FP64)
     g = Grid(workload.n, h=workload.h, eta=workload.eta, periodic=workload.periodic, wall_vel=workload.wall_vel,
-             precision=prec, restart=restart, max_iter=max_iter, rtol=workload.rtol if rtol is None else rtol)
+             precision=prec, restart=restart, max_iter=max_iter, rtol=workload.rtol if rtol is None else rtol,
+             kernel=getattr(workload, "kernel", 3))
     g.set_bodies(workload.blob_offsets, workload.ref_blobs, workload.q, workload.quat)
     return g

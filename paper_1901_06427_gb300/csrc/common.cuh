@@ -17,6 +17,7 @@ struct Dims {
   i64 nc;            // N_c
   double ih[3], ih2[3];   // 1/h, 1/h^2 per axis (precomputed: no divisions in kernels)
   float ihf[3], ih2f[3];
+  int kw;            // immersed-boundary kernel points per axis (3 or 6)
 };
 
 template <typename T> __host__ __device__ inline T inv_h(const Dims& d, int ax);
@@ -38,6 +39,7 @@ inline Dims make_dims(const int n[3], const int per[3], const double h[3]) {
   }
   d.fo[3] = off;
   d.nc = (i64)n[0] * n[1] * n[2];
+  d.kw = 3;
   for (int a = 0; a < 3; ++a) {
     d.ih[a] = 1.0 / h[a];
     d.ih2[a] = 1.0 / (h[a] * h[a]);
@@ -117,13 +119,16 @@ __device__ inline bool color_cell(const Dims& d, const ColorMap& m, unsigned t, 
   return c[0] < d.n[0];
 }
 
+// Largest kernel width (points per axis).
+constexpr int kKMax = 6;
+
 // Per-configuration kernel stencil of one blob and velocity component:
-// indices along x, y, z (3 each) and the folded weights (sign included, zero
-// for dropped points).
+// indices along x, y, z (kw each, at [kKMax * axis + t]) and the folded
+// weights (sign included, zero for dropped points).
 template <typename W>
 struct BlobStencil {
-  int idx[9];
-  W w[9];
+  int idx[3 * kKMax];
+  W w[3 * kKMax];
 };
 
 // Three-point Peskin kernel: the unique phi on |r| < 3/2 with partition of
@@ -149,7 +154,39 @@ __device__ inline double dphi3(double r) {
   return 0.0;
 }
 
-// The three kernel points of a blob coordinate x along axis ax for velocity
+// Six-point kernel of three continuous derivatives (support |r| < 3): the
+// six weights phi(r + 2 - t), t = 0..5, at a shift r in [0, 1), and their
+// derivatives d/dr.  The weights are the solution of the kernel's defining
+// conditions (even and odd sums 1/2, first and third moments 0, second
+// moment K = 59/60 - sqrt(29)/20, sum of squares C = 5431/19200 +
+// 51 sqrt(29)/6400): affine in the root t(r) = phi(r - 3) of
+// 28 t^2 + beta(r) t + gamma(r) = 0 that vanishes at r = 0.
+__device__ inline void six_weights(double r, double w[6], double dw[6]) {
+  const double s29 = 5.385164807134504;   // sqrt(29)
+  const double r2 = r * r, r3 = r2 * r;
+  const double beta = -7.0 / 3.0 * r3 - 1.5 * r2 + (9.0 + 7.0 * s29) / 20.0 * r + (31.0 + 3.0 * s29) / 40.0;
+  const double gq = 1.0 / 32.0 - s29 / 48.0;
+  const double gamma = 5.0 / 72.0 * r3 * r3 + gq * r2 * r2;
+  const double t = -2.0 * gamma / (beta + sqrt(beta * beta - 112.0 * gamma));
+  const double dbeta = -7.0 * r2 - 3.0 * r + (9.0 + 7.0 * s29) / 20.0;
+  const double dgamma = 5.0 / 12.0 * r2 * r3 + 4.0 * gq * r3;
+  const double dt = -(dbeta * t + dgamma) / (56.0 * t + beta);
+  const double c1 = (13.0 - s29) / 80.0, c2 = (7.0 + s29) / 40.0, c0 = 29.0 / 480.0 - s29 / 160.0;
+  w[0] = -r3 / 12.0 + r2 / 8.0 - c1 * r + c0 + t;
+  w[1] = r3 / 6.0 - c2 * r + 0.25 - 3.0 * t;
+  w[2] = -r2 / 4.0 + 91.0 / 240.0 + s29 / 80.0 + 2.0 * t;
+  w[3] = -r3 / 6.0 + c2 * r + 0.25 + 2.0 * t;
+  w[4] = r3 / 12.0 + r2 / 8.0 + c1 * r + c0 - 3.0 * t;
+  w[5] = t;
+  dw[0] = -r2 / 4.0 + r / 4.0 - c1 + dt;
+  dw[1] = r2 / 2.0 - c2 - 3.0 * dt;
+  dw[2] = -r / 2.0 + 2.0 * dt;
+  dw[3] = -r2 / 2.0 + c2 + 2.0 * dt;
+  dw[4] = r2 / 4.0 + r / 4.0 + c1 - 3.0 * dt;
+  dw[5] = dt;
+}
+
+// The kw kernel points of a blob coordinate x along axis ax for velocity
 // component a, folded at walls:
 //   - a point on a wall-normal boundary face is dropped (zero normal velocity);
 //   - a point beyond a wall mirrors onto the reflected interior point with
@@ -157,23 +194,34 @@ __device__ inline double dphi3(double r) {
 //     affine ghost value is 2 u_w);
 //   - a point whose mirror is not an unknown is dropped.
 struct AxisStencil {
-  int idx[3];      // compact index along the axis
-  double w[3];     // kernel weight phi(s - p)
-  double dw[3];    // dphi/dx (derivative with respect to the blob coordinate)
-  signed char sgn[3];
-  signed char wall[3];   // tangential ghost wall id (2 ax or 2 ax + 1) or -1
-  bool keep[3];
+  int idx[kKMax];      // compact index along the axis
+  double w[kKMax];     // kernel weight phi(s - p)
+  double dw[kKMax];    // dphi/dx (derivative with respect to the blob coordinate)
+  signed char sgn[kKMax];
+  signed char wall[kKMax];   // tangential ghost wall id (2 ax or 2 ax + 1) or -1
+  bool keep[kKMax];
 };
 
+// Points p = p0 + t (t < kw) of a coordinate s in grid units: three points
+// from p0 = floor(s + 1/2) - 1, six from p0 = floor(s) - 2.
 __device__ inline void axis_stencil(const Dims& d, int a, int ax, double x, AxisStencil& S) {
   const double o = (ax == a) ? 0.0 : 0.5;
   const double s = x / d.h[ax] - o;
-  const int i0 = (int)floor(s + 0.5);
+  const int kw = d.kw;
+  const double fl = floor(s);
+  const int i0 = kw == 6 ? (int)fl - 2 : (int)floor(s + 0.5) - 1;
+  double w6[6], dw6[6];
+  if (kw == 6) six_weights(s - fl, w6, dw6);
   const int n = d.n[ax];
-  for (int t = 0; t < 3; ++t) {
-    const int p = i0 - 1 + t;
-    S.w[t] = phi3(s - (double)p);
-    S.dw[t] = dphi3(s - (double)p) / d.h[ax];
+  for (int t = 0; t < kw; ++t) {
+    const int p = i0 + t;
+    if (kw == 6) {
+      S.w[t] = w6[t];
+      S.dw[t] = dw6[t] / d.h[ax];
+    } else {
+      S.w[t] = phi3(s - (double)p);
+      S.dw[t] = dphi3(s - (double)p) / d.h[ax];
+    }
     S.sgn[t] = 1;
     S.wall[t] = -1;
     if (d.per[ax]) {

@@ -126,7 +126,7 @@ void binning(const Dims& d, int nbl, const double* r, int* perm, int* off, int* 
 }
 
 // ----------------------------------------------------- spread / interpolate
-// Folded 27-point stencil of one blob and component.  For each point: flat
+// Folded kw^3-point stencil of one blob and component.  For each point: flat
 // face index (within component a), folded weight, and affine ghost weight
 // (sum over folded tangential axes, in x,y,z order, of sign * 2 u_w).
 struct Stencil27 {
@@ -152,13 +152,14 @@ __global__ void k_spread(Dims d, int nbl, const int* __restrict__ perm, const do
   Stencil27 S;
   load_stencil(d, a, r + 3 * i, S);
   T* fa = f + d.fo[a];
-  for (int z = 0; z < 3; ++z) {
+  const int kw = d.kw;
+  for (int z = 0; z < kw; ++z) {
     if (!S.ax[2].keep[z]) continue;
     const double wz = S.ax[2].w[z] * S.ax[2].sgn[z];
-    for (int y = 0; y < 3; ++y) {
+    for (int y = 0; y < kw; ++y) {
       if (!S.ax[1].keep[y]) continue;
       const double wyz = wz * S.ax[1].w[y] * S.ax[1].sgn[y];
-      for (int x = 0; x < 3; ++x) {
+      for (int x = 0; x < kw; ++x) {
         if (!S.ax[0].keep[x]) continue;
         const double w = wyz * S.ax[0].w[x] * S.ax[0].sgn[x];
         atomicAdd(fa + flat3(d.fe[a], S.ax[0].idx[x], S.ax[1].idx[y], S.ax[2].idx[z]), (T)(w * val));
@@ -175,11 +176,12 @@ RBFIB_DEVFN void interp_one(const Dims& d, const Walls& wl, int a, const double*
   load_stencil(d, a, x, S);
   const T* va = v + d.fo[a];
   jv = 0.0; aff = 0.0;
-  for (int z = 0; z < 3; ++z) {
+  const int kw = d.kw;
+  for (int z = 0; z < kw; ++z) {
     if (!S.ax[2].keep[z]) continue;
-    for (int y = 0; y < 3; ++y) {
+    for (int y = 0; y < kw; ++y) {
       if (!S.ax[1].keep[y]) continue;
-      for (int xx = 0; xx < 3; ++xx) {
+      for (int xx = 0; xx < kw; ++xx) {
         if (!S.ax[0].keep[xx]) continue;
         const int pt[3] = {xx, y, z};
         double w = 1.0, sg = 1.0, af = 0.0;
@@ -228,12 +230,13 @@ __global__ void k_stencil_build(Dims d, int nbl, const double* __restrict__ r, B
   for (int ax = 0; ax < 3; ++ax) {
     AxisStencil A;
     axis_stencil(d, a, ax, r[3 * i + ax], A);
-    for (int k = 0; k < 3; ++k) {
-      const double w = A.keep[k] ? A.w[k] * (double)A.sgn[k] : 0.0;
-      S.idx[3 * ax + k] = A.keep[k] ? A.idx[k] : 0;
-      S.w[3 * ax + k] = w;
-      F.idx[3 * ax + k] = S.idx[3 * ax + k];
-      F.w[3 * ax + k] = (float)w;
+    for (int k = 0; k < kKMax; ++k) {
+      const bool in = k < d.kw && A.keep[k];
+      const double w = in ? A.w[k] * (double)A.sgn[k] : 0.0;
+      S.idx[kKMax * ax + k] = in ? A.idx[k] : 0;
+      S.w[kKMax * ax + k] = w;
+      F.idx[kKMax * ax + k] = S.idx[kKMax * ax + k];
+      F.w[kKMax * ax + k] = (float)w;
     }
   }
   s64[t] = S;
@@ -249,29 +252,43 @@ template <typename T> RBFIB_DEVFN const BlobStencil<T>* table_of(const BodyView&
 template <> RBFIB_DEVFN const BlobStencil<double>* table_of<double>(const BodyView& b) { return b.st64; }
 template <> RBFIB_DEVFN const BlobStencil<float>* table_of<float>(const BodyView& b) { return b.st32; }
 
-// (J v)_ia by one warp: lane l < 27 takes kernel point (l % 3, l / 3 % 3, l / 9).
+// (J v)_ia by one warp.  Three-point kernel: lane l < 27 takes kernel point
+// (l % 3, l / 3 % 3, l / 9).  Six-point kernel: the 216 points p = l, l + 32,
+// ... are (p % 6, p / 6 % 6, p / 36).
 template <typename T>
 RBFIB_DEVFN T warp_interp(const Dims& d, int a, const BlobStencil<T>* __restrict__ S, const T* __restrict__ v,
                           int lane) {
   T val = T(0);
-  if (lane < 27) {
-    const int x = lane % 3, y = (lane / 3) % 3, z = lane / 9;
-    const T w = S->w[x] * S->w[3 + y] * S->w[6 + z];
-    if (w != T(0)) val = w * v[d.fo[a] + flat3(d.fe[a], S->idx[x], S->idx[3 + y], S->idx[6 + z])];
+  const T* va = v + d.fo[a];
+  if (d.kw == 3) {
+    if (lane < 27) {
+      const int x = lane % 3, y = (lane / 3) % 3, z = lane / 9;
+      const T w = S->w[x] * S->w[kKMax + y] * S->w[2 * kKMax + z];
+      if (w != T(0)) val = w * va[flat3(d.fe[a], S->idx[x], S->idx[kKMax + y], S->idx[2 * kKMax + z])];
+    }
+  } else {
+    for (int p = lane; p < 216; p += 32) {
+      const int x = p % 6, y = (p / 6) % 6, z = p / 36;
+      const T w = S->w[x] * S->w[kKMax + y] * S->w[2 * kKMax + z];
+      if (w != T(0)) val += w * va[flat3(d.fe[a], S->idx[x], S->idx[kKMax + y], S->idx[2 * kKMax + z])];
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
   return val;
 }
 
-// f_a += val * w at the 27 kernel points, one atomic per lane.
+// f_a += val * w at the kernel points, one atomic per point.
 template <typename T>
 RBFIB_DEVFN void warp_spread(const Dims& d, int a, const BlobStencil<T>* __restrict__ S, T val, T* __restrict__ f,
                              int lane) {
-  if (lane < 27 && val != T(0)) {
-    const int x = lane % 3, y = (lane / 3) % 3, z = lane / 9;
-    const T w = S->w[x] * S->w[3 + y] * S->w[6 + z];
-    if (w != T(0)) atomicAdd(f + d.fo[a] + flat3(d.fe[a], S->idx[x], S->idx[3 + y], S->idx[6 + z]), w * val);
+  if (val == T(0)) return;
+  T* fa = f + d.fo[a];
+  const int kw = d.kw, np = kw * kw * kw;
+  for (int p = lane; p < np; p += 32) {
+    const int x = p % kw, y = (p / kw) % kw, z = p / (kw * kw);
+    const T w = S->w[x] * S->w[kKMax + y] * S->w[2 * kKMax + z];
+    if (w != T(0)) atomicAdd(fa + flat3(d.fe[a], S->idx[x], S->idx[kKMax + y], S->idx[2 * kKMax + z]), w * val);
   }
 }
 
@@ -804,8 +821,9 @@ __global__ void k_adjoint_positions(Dims d, int nbl, const int* __restrict__ bob
     axis_stencil(d, a, 1, r[3 * i + 1], S[1]);
     axis_stencil(d, a, 2, r[3 * i + 2], S[2]);
     double A[3] = {0.0, 0.0, 0.0}, Bv[3] = {0.0, 0.0, 0.0};
-    if (lane < 27) {
-      const int pt[3] = {lane % 3, (lane / 3) % 3, lane / 9};
+    const int kw = d.kw, np = kw * kw * kw;
+    for (int q = lane; q < np; q += 32) {
+      const int pt[3] = {q % kw, (q / kw) % kw, q / (kw * kw)};
       bool keep = true;
       double sg = 1.0;
       for (int ax = 0; ax < 3; ++ax) { keep = keep && S[ax].keep[pt[ax]]; sg *= (double)S[ax].sgn[pt[ax]]; }
@@ -815,8 +833,8 @@ __global__ void k_adjoint_positions(Dims d, int nbl, const int* __restrict__ bob
         for (int b = 0; b < 3; ++b) {
           const int c1 = (b + 1) % 3, c2 = (b + 2) % 3;
           const double dw = S[b].dw[pt[b]] * S[c1].w[pt[c1]] * S[c2].w[pt[c2]] * sg;
-          A[b] = dw * fz;
-          Bv[b] = dw * fv;
+          A[b] += dw * fz;
+          Bv[b] += dw * fv;
         }
       }
     }

@@ -29,7 +29,10 @@ namespace {
 
 const double kDeltaDefault = 6.0554544523933395e-06;   // eps^(1/3), eps = 2^-52
 const double kInnerTol = 1e-4;   // relative reduction asked of each FP32 refinement sweep
-const double kBlobRadius = 0.91;                         // hydrodynamic radius of a 3-point blob, units of h
+// Hydrodynamic radius of a blob in units of h, for the free-space RPY
+// mobilities of the body-block preconditioner only: 0.91 for the
+// three-point kernel; 1.47 for the six-point kernel (Sec. III.C).
+double blob_radius(int kw) { return kw == 6 ? 1.47 : 0.91; }
 const int kDenseBodyMaxRows = 1536;                      // 3 N_bl limit of the coupled body block
 const int kDenseBodyMaxBodyRows = 384;                   // 6 N_b limit of the coupled body block
 
@@ -1024,7 +1027,7 @@ void build_body_block(rbfib_grid* g, const double* r, const double* arm, const d
     // captured: the warm start (the step graph is built only when the block
     // holds a valid inverse) with the choice between Newton-Schulz and
     // Gauss-Jordan made on the device; the status goes to dinfo[13]
-    const double a = kBlobRadius * g->desc.h;
+    const double a = blob_radius(g->d.kw) * g->desc.h;
     ck(cudaMemsetAsync(g->dstatus, 0, sizeof(int), g->s));
     dense_body_warm_start(g->nbl, g->bob, r, quat, qold, a, g->desc.eta, g->dM, g->dMw, g->dTw, g->dss, g->s);
     const cudaGraphConditionalHandle h = new_handle(g, 0u);
@@ -1041,7 +1044,7 @@ void build_body_block(rbfib_grid* g, const double* r, const double* arm, const d
   bool used = false;
   const bool warm = g->dM_valid;
   g->dM_valid = false;
-  ck(dense_body_build(g->nbl, g->nb, g->boff, g->bob, r, arm, quat, qold, kBlobRadius * g->desc.h, g->desc.eta,
+  ck(dense_body_build(g->nbl, g->nb, g->boff, g->bob, r, arm, quat, qold, blob_radius(g->d.kw) * g->desc.h, g->desc.eta,
                       g->dM, g->dP, g->dN, g->dstatus, g->dMw, g->dTw, g->dUw, g->dss, g->h_pinned + 40, warm, g->s,
                       &used));
   int* hstat = (int*)(g->h_pinned + 42);
@@ -1290,7 +1293,7 @@ int rbfib_create_grid(const rbfib_grid_desc* desc, void* stream, rbfib_grid** ou
   for (int a = 0; a < 3; ++a)
     if (D.n[a] < 2 || (D.periodic[a] != 0 && D.periodic[a] != 1)) return RBFIB_EINVAL;
   if (D.periodic[0] && D.periodic[1] && D.periodic[2]) return RBFIB_EINVAL;
-  if (!(D.h > 0) || !(D.eta > 0) || D.kernel != 3 || D.restart < 1 || D.restart > 64 || D.max_iter < 1 ||
+  if (!(D.h > 0) || !(D.eta > 0) || (D.kernel != 3 && D.kernel != 6) || D.restart < 1 || D.restart > 64 || D.max_iter < 1 ||
       !(D.rtol > 0) || (D.precision != RBFIB_FP64 && D.precision != RBFIB_FP32_REFINED))
     return RBFIB_EINVAL;
   for (int a = 0; a < 3; ++a)
@@ -1301,6 +1304,7 @@ int rbfib_create_grid(const rbfib_grid_desc* desc, void* stream, rbfib_grid** ou
     g->s = (cudaStream_t)stream;
     build_levels(g);
     build_fd(g);
+    g->levels[0].d.kw = D.kernel;
     g->d = g->levels[0].d;
     for (int w = 0; w < 6; ++w)
       for (int c = 0; c < 3; ++c) g->walls.v[w][c] = D.wall_vel[w][c];
@@ -1460,7 +1464,7 @@ int rbfib_set_bodies(rbfib_grid* g, int32_t n_bodies, const int32_t* blob_offset
       const int n = off[p + 1] - off[p];
       const double* x = href.data() + 3 * (size_t)off[p];
       std::vector<double> M;
-      rpy_matrix(x, n, kBlobRadius * g->desc.h, g->desc.eta, M);
+      rpy_matrix(x, n, blob_radius(g->d.kw) * g->desc.h, g->desc.eta, M);
       if (!spd_inverse(M, 3 * n)) return fail(g, RBFIB_EINVAL, "set_bodies: blob mobility of a shape is singular");
       moff[s] = (i64)minv_all.size();
       srep[s] = off[p];

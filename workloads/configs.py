@@ -40,6 +40,7 @@ class Workload:
     slip: np.ndarray = None            # (N_bl, 3) active slip
     potentials: dict = field(default_factory=dict)
     seed: int = 0
+    kernel: int = 3                    # immersed-boundary kernel width (3 or 6 points per axis)
 
     # flat views used by both implementations -------------------------
     @property
@@ -98,15 +99,16 @@ def single_sphere_box():
     return w
 
 
-def two_sphere_cavity(steps=2000):
+def two_sphere_cavity(steps=2000, kernel=3):
     """Two 42-blob spheres (R = 2.5h) 6h apart along x in a 48x48x32 no-slip
     cuboid; kT = 1, eta = 1, dt = 0.05; gravity plus soft wall and pair
-    repulsion of the form of Eq. (Usoft); orientations seeded."""
+    repulsion of the form of Eq. (Usoft); orientations seeded.  kernel = 6:
+    the same setup with the paper's six-point kernel."""
     rng = _rng(1)
     shell = icosahedral_shell(42, 2.5)
     quats = random_unit_quaternions(rng, 2)
-    w = Workload(name="two-sphere-48x48x32", n=(48, 48, 32), dt=0.05, steps=steps,
-                 rtol=1e-8, seed=WORKLOAD_SEED_BASE + 1)
+    w = Workload(name="two-sphere-48x48x32" + ("" if kernel == 3 else "-6pt"), n=(48, 48, 32), dt=0.05,
+                 steps=steps, rtol=1e-8, seed=WORKLOAD_SEED_BASE + 1, kernel=kernel)
     w.bodies = [Body(shell, np.array([21.0, 24.0, 16.0]), quats[0]),
                 Body(shell, np.array([27.0, 24.0, 16.0]), quats[1])]
     R = 2.5
@@ -207,7 +209,7 @@ def adjoint_suspension():
 
 
 def small_case(n=(12, 10, 8), periodic=(False, False, False), n_bodies=2, blobs=12,
-               radius=1.0, seed=7, wall_speed=0.0, near_wall=False):
+               radius=1.0, seed=7, wall_speed=0.0, near_wall=False, kernel=3):
     """A small seeded problem for parity tests: a few shells placed at random
     (optionally hugging a wall) in a box of the given size."""
     rng = np.random.Generator(np.random.Philox(WORKLOAD_SEED_BASE + 100 + seed))
@@ -224,7 +226,7 @@ def small_case(n=(12, 10, 8), periodic=(False, False, False), n_bodies=2, blobs=
                 break
     quats = random_unit_quaternions(rng, len(centres))
     w = Workload(name=f"small-{n[0]}x{n[1]}x{n[2]}", n=tuple(n), periodic=tuple(periodic),
-                 seed=WORKLOAD_SEED_BASE + 100 + seed, rtol=1e-10)
+                 seed=WORKLOAD_SEED_BASE + 100 + seed, rtol=1e-10, kernel=kernel)
     w.bodies = [Body(shell, centres[i], quats[i]) for i in range(len(centres))]
     if wall_speed:
         w.wall_vel = np.zeros((6, 3))
