@@ -248,7 +248,7 @@ CLASS_INFO = {
 # DRAM bytes (read + write) per algorithmic byte from the ncu captures
 # summarised under profiles/ (kernel as it stands); traffic is reported for
 # these classes only, and is null for a class whose kernel changed since.
-TRAFFIC_RATIO = {}
+TRAFFIC_RATIO = {"dot": 0.97}   # k_gs_dot, profiles/hot_kernels_two_sphere_48x48x32.md
 
 
 def roofline_for(top, kms, klaunch, kbytes, kflops):
@@ -647,11 +647,34 @@ def run_ours(args):
         r_shares[cname] = gr.kernel_timer_read()[0] / nrep
         gr.kernel_timer(0)
     ri = np.array(r_iters, dtype=float)
+    # error of the refined step against the FP64 GPU step and the oracle's
+    # stored step (tests/golden/two_sphere_step0.json: the same initial state,
+    # seed, step 0, attempt 0), per output (displacement, orientation)
+    errs = {}
+    try:
+        gold = json.load(open(os.path.join(ROOT, "tests", "golden", "two_sphere_step0.json")))
+        steps = {}
+        for label, gg in (("fp32_refined", gr), ("fp64", g)):
+            q0 = torch.tensor(w.q.ravel(), device="cuda")
+            t0 = torch.tensor(w.quat.ravel(), device="cuda")
+            gg.sem_step(p, w.seed, 0, 0, q0, t0)
+            steps[label] = (q0.cpu().numpy() - w.q.ravel(), t0.cpu().numpy() - w.quat.ravel())
+        gq = np.array(gold["q"]) - np.array(gold["q0"])
+        gt = np.array(gold["quat"]) - np.array(gold["quat0"])
+        errs = {"vs_fp64_gpu_step": {"dq": _step_error(steps["fp32_refined"][0], steps["fp64"][0]),
+                                     "dquat": _step_error(steps["fp32_refined"][1], steps["fp64"][1])},
+                "vs_oracle_step": {"dq": _step_error(steps["fp32_refined"][0], gq),
+                                   "dquat": _step_error(steps["fp32_refined"][1], gt)},
+                "fp64_vs_oracle_step": {"dq": _step_error(steps["fp64"][0], gq),
+                                        "dquat": _step_error(steps["fp64"][1], gt)}}
+    except Exception as e:   # the stored values are test data; report their absence
+        errs = {"unavailable": str(e)[:200]}
     line["refined_vs_fp64"] = {"fp32_refined_steps_per_s": args.steps / (er0.elapsed_time(er1) / 1000.0),
                                "fp64_steps_per_s": value / world, "rtol": 1e-8,
                                "fp32_refined_krylov_iterations_per_step": [int(round(x)) for x in ri[:, :, 0].mean(0)],
                                "fp32_refined_refinements_per_step": [round(float(x), 2) for x in ri[:, :, 1].mean(0)],
-                               "fp32_refined_time_share_ms_per_step": r_shares}
+                               "fp32_refined_time_share_ms_per_step": r_shares,
+                               "errors": errs}
     try:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
     except Exception:

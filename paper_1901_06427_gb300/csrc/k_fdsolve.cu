@@ -295,8 +295,6 @@ RBFIB_DEVFN void fd_item(const FDParams& P, int& k, int& gi) {
   while (gi < P.ng - 1 && k >= F(P.g[gi])) { k -= F(P.g[gi]); ++gi; }
 }
 
-// One plane: out = A_y (in A_x), the 1D transforms along x then y, with the
-// forward bases (dir 0) or their transposes (dir 1).
 // cp.async helpers: 16-byte and 4-byte global -> shared copies, one wait.
 RBFIB_DEVFN void fdw_cp16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
@@ -323,79 +321,75 @@ RBFIB_DEVFN void fdw_stage_basis(float (*M)[kFDLine], const float* tab, int e) {
   }
 }
 
+// One plane, one chunk of kFWT output columns (blockIdx.y): out = A_y (in
+// A_x), the 1D transforms along x then y, with the forward bases (dir 0) or
+// their transposes (dir 1).  Both transforms keep the output column: column
+// c of A_x acts on the rows of the plane, and the y transform mixes rows of
+// the same column, so a plane's columns split over independent CTAs (three
+// per plane of 48 points, which keeps more SMs busy than one CTA per plane).
+// 16 x 16 threads: thread (tx, ty) owns column c0 + tx of rows ty + 16 a.
 __global__ void __launch_bounds__(kFWT * kFWT) k_fdw_xy(FDParams P, const float* __restrict__ in,
                                                          float* __restrict__ out, int dir) {
   pdl_entry();
   __shared__ float X[kFDLine][kFDLine + 1];
-  __shared__ float T[kFDLine][kFDLine + 1];
-  __shared__ __align__(16) float Mx[kFDLine][kFDLine];
+  __shared__ float T[kFDLine][kFWT + 1];
+  __shared__ __align__(16) float Mx[kFDLine][kFWT];
   __shared__ __align__(16) float My[kFDLine][kFDLine];
   int k = blockIdx.x, gi;
   fd_item<fd_planes>(P, k, gi);
   const FDGrid& G = P.g[gi];
   const int e0 = G.e[0], e1 = G.e[1], p0 = fd_pad(e0), p1 = fd_pad(e1);
+  const int c0 = blockIdx.y * kFWT;
+  if (c0 >= e0) return;
   const float* Q0 = P.tab + G.tab0;
   const float* QT0 = Q0 + e0 * p0;
   const float* Q1 = QT0 + e0 * p0 + p0;
   const float* QT1 = Q1 + e1 * p1;
-  // every copy issued before the one wait
-  fdw_stage_basis(Mx, dir ? QT0 : Q0, e0);
-  fdw_stage_basis(My, dir ? QT1 : Q1, e1);
+  const float* ax = dir ? QT0 : Q0;
   const int tx = threadIdx.x % kFWT, ty = threadIdx.x / kFWT;
+  // every copy issued before the one wait: the chunk's columns of A_x (rows
+  // padded to 8 floats, so the 16 columns from c0 are four whole 16-byte
+  // words inside the row), A_y and the plane
+  for (int t = threadIdx.x; t < e0 * (kFWT / 4); t += blockDim.x) {
+    const int r = t / (kFWT / 4), w = t - r * (kFWT / 4);
+    if (c0 + 4 * w < p0) fdw_cp16(&Mx[r][4 * w], ax + r * p0 + c0 + 4 * w);
+  }
+  fdw_stage_basis(My, dir ? QT1 : Q1, e1);
   const float* src = in + G.off + (long long)k * e0 * e1;
   for (int r = ty; r < e1; r += kFWT)
     for (int c = tx; c < e0; c += kFWT) fdw_cp4(&X[r][c], src + r * e0 + c);
   fdw_wait();
   __syncthreads();
-  // T[j][c] = sum_i X[j][i] A_x[i][c]; tile rows j >= e1 and columns c >= e0
-  // hold values that are never read back (the y pass sums j < e1, only
-  // c < e0 is stored)
-  float acc[kFWR][kFWR];
+  // T[j][c] = sum_i X[j][i] A_x[i][c0 + c]  (rows j >= e1 are never read back)
+  float acc[kFWR];
 #pragma unroll
-  for (int a = 0; a < kFWR; ++a)
-#pragma unroll
-    for (int b = 0; b < kFWR; ++b) acc[a][b] = 0.f;
+  for (int a = 0; a < kFWR; ++a) acc[a] = 0.f;
 #pragma unroll 4
   for (int i = 0; i < e0; ++i) {
-    float xv[kFWR], mv[kFWR];
+    const float m = Mx[i][tx];
 #pragma unroll
-    for (int a = 0; a < kFWR; ++a) xv[a] = X[ty + kFWT * a][i];
-#pragma unroll
-    for (int b = 0; b < kFWR; ++b) mv[b] = Mx[i][tx + kFWT * b];
-#pragma unroll
-    for (int a = 0; a < kFWR; ++a)
-#pragma unroll
-      for (int b = 0; b < kFWR; ++b) acc[a][b] = fmaf(xv[a], mv[b], acc[a][b]);
+    for (int a = 0; a < kFWR; ++a) acc[a] = fmaf(X[ty + kFWT * a][i], m, acc[a]);
   }
 #pragma unroll
-  for (int a = 0; a < kFWR; ++a)
-#pragma unroll
-    for (int b = 0; b < kFWR; ++b) {
-      T[ty + kFWT * a][tx + kFWT * b] = acc[a][b];
-      acc[a][b] = 0.f;
-    }
+  for (int a = 0; a < kFWR; ++a) {
+    T[ty + kFWT * a][tx] = acc[a];
+    acc[a] = 0.f;
+  }
   __syncthreads();
   // out[r][c] = sum_j A_y[j][r] T[j][c]
 #pragma unroll 4
   for (int j = 0; j < e1; ++j) {
-    float mv[kFWR], tv[kFWR];
+    const float t = T[j][tx];
 #pragma unroll
-    for (int a = 0; a < kFWR; ++a) mv[a] = My[j][ty + kFWT * a];
-#pragma unroll
-    for (int b = 0; b < kFWR; ++b) tv[b] = T[j][tx + kFWT * b];
-#pragma unroll
-    for (int a = 0; a < kFWR; ++a)
-#pragma unroll
-      for (int b = 0; b < kFWR; ++b) acc[a][b] = fmaf(mv[a], tv[b], acc[a][b]);
+    for (int a = 0; a < kFWR; ++a) acc[a] = fmaf(My[j][ty + kFWT * a], t, acc[a]);
   }
   float* dst = out + G.off + (long long)k * e0 * e1;
+  const int c = c0 + tx;
 #pragma unroll
-  for (int a = 0; a < kFWR; ++a)
-#pragma unroll
-    for (int b = 0; b < kFWR; ++b) {
-      const int r = ty + kFWT * a, c = tx + kFWT * b;
-      if (r < e1 && c < e0) dst[r * e0 + c] = acc[a][b];
-    }
+  for (int a = 0; a < kFWR; ++a) {
+    const int r = ty + kFWT * a;
+    if (r < e1 && c < e0) dst[r * e0 + c] = acc[a];
+  }
 }
 
 // 32 adjacent columns (fixed x, y; all z) of one grid, in place: forward z
@@ -474,11 +468,13 @@ void fd_solve_wide(const FDParams& P, float* u, const float* rhs, float* tmp, cu
     planes += P.g[g].e[2];
     tiles += (P.g[g].e[0] * P.g[g].e[1] + 31) / 32;
   }
-  launch_k(k_fdw_xy, planes, kFWT * kFWT, 0, s, P, rhs, tmp, 0);
+  int chunks = 1;
+  for (int g = 0; g < P.ng; ++g) chunks = std::max(chunks, (P.g[g].e[0] + kFWT - 1) / kFWT);
+  launch_k(k_fdw_xy, dim3(planes, chunks), kFWT * kFWT, 0, s, P, rhs, tmp, 0);
   note_launch();
   launch_k(k_fdw_z, tiles, 256, 0, s, P, tmp);
   note_launch();
-  launch_k(k_fdw_xy, planes, kFWT * kFWT, 0, s, P, (const float*)tmp, u, 1);
+  launch_k(k_fdw_xy, dim3(planes, chunks), kFWT * kFWT, 0, s, P, (const float*)tmp, u, 1);
   note_launch();
 }
 
