@@ -25,7 +25,8 @@ def _peaks():
 
 
 def test_every_timer_class_has_roofline_info():
-    assert set(bench.CLASS_INFO) == set(bench.TIMER_NAMES)
+    # every timed class, and the Gram-Schmidt projection formed from two of them
+    assert set(bench.CLASS_INFO) == set(bench.TIMER_NAMES) | {"gram_schmidt"}
     for name, arith, sms in bench.CLASS_INFO.values():
         assert arith in ("fp32", "fp64") and 1 <= sms <= 152 and name
 
