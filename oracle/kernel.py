@@ -50,7 +50,7 @@ def dphi(r):
 # with K = 59/60 - sqrt(29)/20 (the value that makes phi three times
 # continuously differentiable) and C fixed by phi(+-3) = 0.  Solving the five
 # linear conditions for the other weights in terms of t = phi(r - 3) (our
-# derivation; the pins in tests/test_oracle_kernel_ib.py re-solve the system
+# derivation; the pins in tests/test_oracle_kernel6.py re-solve the system
 # numerically and check the smoothness):
 #   phi(r - 2) = r^3/12 + r^2/8 + (13 - sqrt29) r / 80 + 29/480 - sqrt29/160 - 3 t
 #   phi(r - 1) = -r^3/6 + (7 + sqrt29) r / 40 + 1/4 + 2 t
