@@ -13,14 +13,22 @@ Layout (also the layout of the CUDA library's saddle vector):
     centres and, for b != a, W_ab on the edges at the a-face positions (along a),
     the nodes 0..n_b (wall) or 0..n_b-1 (periodic) along b, and cell centres
     along the third axis.
+
+Walls (Introduction: any combination of periodic, no-slip and free-slip
+boundaries along the axes).  Each wall of a bounded axis is no-slip (the
+velocity equals the wall's, which may move tangentially) or free-slip (zero
+normal velocity and zero tangential stress; it cannot drive the fluid, so its
+velocity must be zero).
 """
 import numpy as np
 
 
 class Grid:
-    def __init__(self, n, h=1.0, periodic=(False, False, False), wall_vel=None, kernel=3):
+    def __init__(self, n, h=1.0, periodic=(False, False, False), wall_vel=None, kernel=3, free_slip=None):
         """kernel: points per axis of the immersed-boundary kernel (3: the
-        three-point Peskin kernel; 6: the six-point kernel of Sec. III.B)."""
+        three-point Peskin kernel; 6: the six-point kernel of Sec. III.B).
+        free_slip: six flags for the walls -x, +x, -y, +y, -z, +z (True =
+        free-slip, False = no-slip; ignored on periodic axes)."""
         self.n = tuple(int(v) for v in n)
         if kernel not in (3, 6):
             raise ValueError("kernel must be 3 or 6")
@@ -34,6 +42,25 @@ class Grid:
             if wv[2 * ax, ax] != 0.0 or wv[2 * ax + 1, ax] != 0.0:
                 raise ValueError("walls move tangentially only")
         self.wall_vel = wv
+        fs = [False] * 6 if free_slip is None else [bool(v) for v in free_slip]
+        if len(fs) != 6:
+            raise ValueError("free_slip needs one flag per wall")
+        self.free_slip = tuple(fs[w] and not self.periodic[w // 2] for w in range(6))
+        for w in range(6):
+            if self.free_slip[w] and np.any(wv[w] != 0.0):
+                raise ValueError("a free-slip wall cannot move")
+        for a in range(3):
+            if self.velocity_null_mode(a):
+                raise ValueError(f"velocity component {a} has a constant null mode (no no-slip wall acts on it)")
+
+    def velocity_null_mode(self, a):
+        """True when a constant v_a satisfies every boundary condition, i.e.
+        axis a is periodic and every other axis is periodic or free-slip at
+        both walls; the viscous operator of v_a is then singular."""
+        if not self.periodic[a]:
+            return False
+        return all(self.periodic[b] or (self.free_slip[2 * b] and self.free_slip[2 * b + 1])
+                   for b in range(3) if b != a)
 
     # sizes -------------------------------------------------------------
     @property

@@ -13,7 +13,10 @@ Walls (our reading of the ghost-point treatment the paper cites): a point on a
 wall-normal boundary face holds the prescribed normal velocity (zero) and is
 dropped; a point beyond a wall is a ghost that mirrors onto the interior point
 reflected about the wall with coefficient -1; a tangential ghost also carries
-the affine part 2 u_w of the ghost-reflection boundary condition.  When a
+the affine part 2 u_w of the ghost-reflection boundary condition.  Across a
+free-slip wall a tangential ghost mirrors with coefficient +1 (the tangential
+velocity is even about the wall) and carries no affine part; the normal
+component stays odd.  When a
 point is a ghost along several axes the reflections are applied in x, y, z
 order.  A point whose mirror is not an unknown is dropped.  S and J use the
 same folded weights, so J = dV S^T exactly (Sec. III.B).
@@ -57,11 +60,14 @@ def _fold(g: Grid, a, ax, p):
         keep = keep | (lo & (m_lo >= 1) & (m_lo <= n - 1)) | (hi & (m_hi >= 1) & (m_hi <= n - 1))
         return comp, sign, np.full(p.shape, -1), keep
     # tangential: cell-centred points 0..n-1, ghosts reflect about the wall
+    # (odd at a no-slip wall, even at a free-slip wall)
     lo = p < 0
     hi = p > n - 1
     comp = np.where(lo, -1 - p, np.where(hi, 2 * n - 1 - p, p))
-    sign = np.where(lo | hi, -1.0, 1.0)
-    wall = np.where(lo, 2 * ax, np.where(hi, 2 * ax + 1, -1))
+    s_lo = 1.0 if g.free_slip[2 * ax] else -1.0
+    s_hi = 1.0 if g.free_slip[2 * ax + 1] else -1.0
+    sign = np.where(lo, s_lo, np.where(hi, s_hi, 1.0))
+    wall = np.where(lo & (s_lo < 0), 2 * ax, np.where(hi & (s_hi < 0), 2 * ax + 1, -1))
     keep = (comp >= 0) & (comp <= n - 1)
     return comp, sign, wall, keep
 

@@ -3,13 +3,16 @@
   D   : faces -> cells, (Dv)_c = sum_a (v_a(right face) - v_a(left face)) / h
   G   : cells -> faces, defined as G = -D^T (the adjoint relation of Sec. III.A)
   DD  : stress -> faces, the tensor divergence with the boundary conditions
-        built in: across a wall edge the stress enters with weight sqrt(2)
+        built in: across a no-slip wall edge the stress enters with weight
+        sqrt(2), across a free-slip wall edge with weight 0 (no shear stress)
   LL  : faces -> faces, the vector Laplacian LL = DD GG with GG = -DD^T
         (Sec. III.A), so LL = -DD DD^T
 
 With sqrt(2) wall-edge weights, LL is the ghost-reflection Laplacian: a face
 next to a wall along a tangential axis has the row (u_1 - 3 u_0 + 2 u_w)/h^2,
-whose affine part 2 u_w / h^2 is returned by ``wall_velocity_rhs``.
+whose affine part 2 u_w / h^2 is returned by ``wall_velocity_rhs``; next to
+a free-slip wall the row is (u_1 - u_0)/h^2 (ghost u_{-1} = u_0, zero normal
+derivative of the tangential velocity).
 """
 import numpy as np
 import scipy.sparse as sp
@@ -85,7 +88,9 @@ def tensor_divergence(g: Grid):
                     c = np.ones(node.size)
                 else:
                     nd = node
-                    c = np.where((node == 0) | (node == g.n[b]), SQRT2, 1.0)
+                    c_lo = 0.0 if g.free_slip[2 * b] else SQRT2
+                    c_hi = 0.0 if g.free_slip[2 * b + 1] else SQRT2
+                    c = np.where(node == 0, c_lo, np.where(node == g.n[b], c_hi, 1.0))
                 si = [nd if ax == b else comp[ax] for ax in range(3)]
                 rows.append(fidx); cols.append(offs[(a, b)] + g.flat(sext, *si))
                 vals.append(sgn * c / g.h)

@@ -7,8 +7,10 @@ Eqs. (LangevinD1-D4), so the oracle computes that solution by other means:
     sum(pi) = 0 (tiny grids only);
   * ``stokes``: the discrete Stokes solution operator of Sec. III.A.  The
     vector Laplacian acts on each velocity component separately and is
-    diagonalised by sine transforms (DST-I along the component's own wall axis,
-    DST-II along tangential wall axes) and Fourier transforms on periodic axes,
+    diagonalised by sine and cosine transforms (DST-I along the component's own
+    wall axis; along a tangential wall axis DST-II between no-slip walls, DCT-II
+    between free-slip walls, DST-IV / DCT-IV with one of each) and Fourier
+    transforms on periodic axes,
     so (-eta LL)^{-1} is applied exactly; the pressure then solves the Schur
     complement G^T (-eta LL)^{-1} G pi = ... by conjugate gradients to 1e-14;
   * ``constrained``: the reduced form of Sec. III.C, Eq. (incompleteN),
@@ -39,6 +41,9 @@ def direct(g: Grid, b, eta, f):
 
 # ------------------------------------------------- exact Laplacian inverse
 def _axis_modes(g: Grid, a, ax):
+    """Transform kind and eigenvalues of the 1D second difference of component
+    a along axis ax.  Along a tangential wall axis the ghost is odd at a
+    no-slip wall and even at a free-slip wall."""
     n, h = g.n[ax], g.h
     if g.periodic[ax]:
         k = np.arange(n)
@@ -46,8 +51,21 @@ def _axis_modes(g: Grid, a, ax):
     if ax == a:
         k = np.arange(1, n)
         return "dst1", -4.0 * np.sin(np.pi * k / (2 * n)) ** 2 / h ** 2
-    k = np.arange(1, n + 1)
-    return "dst2", -4.0 * np.sin(np.pi * k / (2 * n)) ** 2 / h ** 2
+    even_lo, even_hi = g.free_slip[2 * ax], g.free_slip[2 * ax + 1]
+    if not even_lo and not even_hi:
+        k = np.arange(1, n + 1)
+        return "dst2", -4.0 * np.sin(np.pi * k / (2 * n)) ** 2 / h ** 2
+    if even_lo and even_hi:
+        k = np.arange(n)
+        return "dct2", -4.0 * np.sin(np.pi * k / (2 * n)) ** 2 / h ** 2
+    k = np.arange(n) + 0.5
+    return ("dst4" if even_hi else "dct4"), -4.0 * np.sin(np.pi * k / (2 * n)) ** 2 / h ** 2
+
+
+_FWD = {"dst1": (sfft.dst, 1), "dst2": (sfft.dst, 2), "dst4": (sfft.dst, 4),
+        "dct2": (sfft.dct, 2), "dct4": (sfft.dct, 4)}
+_INV = {"dst1": (sfft.idst, 1), "dst2": (sfft.idst, 2), "dst4": (sfft.idst, 4),
+        "dct2": (sfft.idct, 2), "dct4": (sfft.idct, 4)}
 
 
 def laplacian_solve(g: Grid, a, f):
@@ -66,10 +84,9 @@ def laplacian_solve(g: Grid, a, f):
         eig = eig + lam.reshape(shape)
     t = arr.astype(np.float64)
     for ax in range(3):
-        if kinds[ax] == "dst1":
-            t = sfft.dst(t, type=1, axis=axis_of[ax], norm="ortho")
-        elif kinds[ax] == "dst2":
-            t = sfft.dst(t, type=2, axis=axis_of[ax], norm="ortho")
+        if kinds[ax] in _FWD:
+            fn, typ = _FWD[kinds[ax]]
+            t = fn(t, type=typ, axis=axis_of[ax], norm="ortho")
     per = [ax for ax in range(3) if kinds[ax] == "fft"]
     if per:
         t = sfft.fftn(t, axes=[axis_of[ax] for ax in per])
@@ -77,10 +94,9 @@ def laplacian_solve(g: Grid, a, f):
     if per:
         t = sfft.ifftn(t, axes=[axis_of[ax] for ax in per]).real
     for ax in range(3):
-        if kinds[ax] == "dst1":
-            t = sfft.idst(t, type=1, axis=axis_of[ax], norm="ortho")
-        elif kinds[ax] == "dst2":
-            t = sfft.idst(t, type=2, axis=axis_of[ax], norm="ortho")
+        if kinds[ax] in _INV:
+            fn, typ = _INV[kinds[ax]]
+            t = fn(t, type=typ, axis=axis_of[ax], norm="ortho")
     return t.reshape(lead + (g.n_face(a),))
 
 
