@@ -58,9 +58,17 @@ typedef struct {
   int32_t n[3];              /* cells per axis                                  */
   double  h;                 /* grid spacing; cell volume dV = h^3              */
   double  eta;               /* viscosity                                       */
-  int32_t periodic[3];       /* 1: periodic axis, 0: no-slip walls on both ends */
+  int32_t periodic[3];       /* 1: periodic axis, 0: walls on both ends         */
   double  wall_vel[6][3];    /* walls -x,+x,-y,+y,-z,+z; tangential components  */
                              /* only (a normal component gives EINVAL)          */
+  int32_t free_slip[6];      /* walls -x,+x,-y,+y,-z,+z: 0 = no-slip, 1 =       */
+                             /* free-slip (zero normal velocity and zero        */
+                             /* tangential stress; Introduction).  Ignored on   */
+                             /* periodic axes.  EINVAL: a value other than 0/1, */
+                             /* a moving free-slip wall, or a velocity          */
+                             /* component that no no-slip wall acts on (a       */
+                             /* periodic axis a whose other axes are all        */
+                             /* periodic or free-slip at both ends)             */
   int32_t kernel;            /* immersed-boundary kernel (Sec. III.B): 3 = the  */
                              /* three-point Peskin kernel, 6 = the six-point    */
                              /* kernel with three continuous derivatives        */

@@ -23,7 +23,7 @@ PURPOSE_FLUID, PURPOSE_BODY = 1, 2
 class GridDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32 * 3), ("h", ctypes.c_double), ("eta", ctypes.c_double),
                 ("periodic", ctypes.c_int32 * 3), ("wall_vel", (ctypes.c_double * 3) * 6),
-                ("kernel", ctypes.c_int32), ("precision", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("free_slip", ctypes.c_int32 * 6), ("kernel", ctypes.c_int32), ("precision", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("rtol", ctypes.c_double)]
 
 
@@ -166,18 +166,8 @@ class Grid:
     """A MAC grid with its solver workspaces, bound to torch's current stream."""
 
     def __init__(self, n, h=1.0, eta=1.0, periodic=(False, False, False), wall_vel=None,
-                 precision=FP64, restart=30, max_iter=2000, rtol=1e-8, kernel=3):
-        d = GridDesc()
-        for a in range(3):
-            d.n[a] = int(n[a])
-            d.periodic[a] = int(bool(periodic[a]))
-        d.h, d.eta = float(h), float(eta)
-        wv = np.zeros((6, 3)) if wall_vel is None else np.asarray(wall_vel, dtype=np.float64).reshape(6, 3)
-        for w in range(6):
-            for c in range(3):
-                d.wall_vel[w][c] = float(wv[w, c])
-        d.kernel, d.precision, d.restart, d.max_iter, d.rtol = (int(kernel), int(precision), int(restart),
-                                                                int(max_iter), float(rtol))
+                 precision=FP64, restart=30, max_iter=2000, rtol=1e-8, kernel=3, free_slip=None):
+        d = _desc(n, h, eta, periodic, wall_vel, precision, restart, max_iter, rtol, kernel, free_slip)
         self.desc = d
         self.n = tuple(int(v) for v in n)
         self.stream = torch.cuda.current_stream()
@@ -390,7 +380,9 @@ class _BatchMember(Grid):
 
 
 def _desc(n, h=1.0, eta=1.0, periodic=(False, False, False), wall_vel=None, precision=FP64, restart=30,
-          max_iter=2000, rtol=1e-8, kernel=3):
+          max_iter=2000, rtol=1e-8, kernel=3, free_slip=None):
+    """The C descriptor; free_slip: six flags for the walls -x, +x, -y, +y,
+    -z, +z (True = free-slip)."""
     d = GridDesc()
     for a in range(3):
         d.n[a] = int(n[a])
@@ -400,6 +392,11 @@ def _desc(n, h=1.0, eta=1.0, periodic=(False, False, False), wall_vel=None, prec
     for w in range(6):
         for c in range(3):
             d.wall_vel[w][c] = float(wv[w, c])
+    fs = [False] * 6 if free_slip is None else list(free_slip)
+    if len(fs) != 6:
+        raise ValueError("free_slip needs one flag per wall")
+    for w in range(6):
+        d.free_slip[w] = int(bool(fs[w]))
     d.kernel, d.precision, d.restart, d.max_iter, d.rtol = (int(kernel), int(precision), int(restart),
                                                             int(max_iter), float(rtol))
     return d
@@ -419,7 +416,7 @@ class Batch:
         for i, w in enumerate(workloads_):
             prec = precision if precision is not None else (FP32_REFINED if w.precision == "f32-refined" else FP64)
             descs[i] = _desc(w.n, w.h, w.eta, w.periodic, w.wall_vel, prec, restart, max_iter, w.rtol,
-                             getattr(w, "kernel", 3))
+                             getattr(w, "kernel", 3), getattr(w, "free_slip", None))
         h = ctypes.c_void_p()
         st = lib().rbfib_create_batch(n, descs, int(workers), ctypes.byref(h))
         if st != OK:
@@ -466,6 +463,6 @@ def grid_for(workload, precision=None, restart=48, max_iter=4000, rtol=None):
     prec = precision if precision is not None else (FP32_REFINED if workload.precision == "f32-refined" else FP64)
     g = Grid(workload.n, h=workload.h, eta=workload.eta, periodic=workload.periodic, wall_vel=workload.wall_vel,
              precision=prec, restart=restart, max_iter=max_iter, rtol=workload.rtol if rtol is None else rtol,
-             kernel=getattr(workload, "kernel", 3))
+             kernel=getattr(workload, "kernel", 3), free_slip=getattr(workload, "free_slip", None))
     g.set_bodies(workload.blob_offsets, workload.ref_blobs, workload.q, workload.quat)
     return g

@@ -18,7 +18,16 @@ struct Dims {
   double ih[3], ih2[3];   // 1/h, 1/h^2 per axis (precomputed: no divisions in kernels)
   float ihf[3], ih2f[3];
   int kw;            // immersed-boundary kernel points per axis (3 or 6)
+  // Walls -x, +x, -y, +y, -z, +z: change of the Laplacian's diagonal (in
+  // units of 1/h^2) when a tangential velocity's neighbour lies beyond the
+  // wall.  +1 at a no-slip wall (ghost = -self), -1 at a free-slip wall
+  // (ghost = +self: zero tangential stress), 0 on periodic axes.
+  int gd[6];
 };
+
+// Value of a tangential ghost beyond wall w in units of its mirror point:
+// -1 (no-slip) or +1 (free-slip).
+__host__ __device__ inline int ghost_sign(const Dims& d, int w) { return -d.gd[w]; }
 
 template <typename T> __host__ __device__ inline T inv_h(const Dims& d, int ax);
 template <> __host__ __device__ inline double inv_h<double>(const Dims& d, int ax) { return d.ih[ax]; }
@@ -40,6 +49,7 @@ inline Dims make_dims(const int n[3], const int per[3], const double h[3]) {
   d.fo[3] = off;
   d.nc = (i64)n[0] * n[1] * n[2];
   d.kw = 3;
+  for (int w = 0; w < 6; ++w) d.gd[w] = per[w / 2] ? 0 : 1;
   for (int a = 0; a < 3; ++a) {
     d.ih[a] = 1.0 / h[a];
     d.ih2[a] = 1.0 / (h[a] * h[a]);
@@ -47,6 +57,12 @@ inline Dims make_dims(const int n[3], const int per[3], const double h[3]) {
     d.ih2f[a] = (float)d.ih2[a];
   }
   return d;
+}
+
+// Marks free-slip walls (fs[w] != 0 for wall w on a bounded axis).
+inline void set_free_slip(Dims& d, const int fs[6]) {
+  for (int w = 0; w < 6; ++w)
+    if (!d.per[w / 2]) d.gd[w] = fs[w] ? -1 : 1;
 }
 
 __host__ __device__ inline i64 flat3(const int e[3], int i, int j, int k) {
@@ -190,8 +206,9 @@ __device__ inline void six_weights(double r, double w[6], double dw[6]) {
 // component a, folded at walls:
 //   - a point on a wall-normal boundary face is dropped (zero normal velocity);
 //   - a point beyond a wall mirrors onto the reflected interior point with
-//     sign -1; a tangential ghost also records which wall it came from (its
-//     affine ghost value is 2 u_w);
+//     sign -1, or +1 for a tangential component at a free-slip wall; a
+//     tangential ghost of a no-slip wall also records which wall it came from
+//     (its affine ghost value is 2 u_w);
 //   - a point whose mirror is not an unknown is dropped.
 struct AxisStencil {
   int idx[kKMax];      // compact index along the axis
@@ -233,9 +250,13 @@ __device__ inline void axis_stencil(const Dims& d, int a, int ax, double x, Axis
       else if (p > n) { int m = 2 * n - p; S.idx[t] = m - 1; S.sgn[t] = -1; S.keep[t] = (m >= 1 && m <= n - 1); }
       else { S.idx[t] = 0; S.keep[t] = false; }
     } else {                       // tangential: cell centres 0..n-1
-      if (p < 0) { int m = -1 - p; S.idx[t] = m; S.sgn[t] = -1; S.wall[t] = 2 * ax; S.keep[t] = (m <= n - 1); }
-      else if (p > n - 1) { int m = 2 * n - 1 - p; S.idx[t] = m; S.sgn[t] = -1; S.wall[t] = 2 * ax + 1; S.keep[t] = (m >= 0); }
-      else { S.idx[t] = p; S.keep[t] = true; }
+      if (p < 0) {
+        const int m = -1 - p, gs = ghost_sign(d, 2 * ax);
+        S.idx[t] = m; S.sgn[t] = (signed char)gs; S.wall[t] = gs < 0 ? 2 * ax : -1; S.keep[t] = (m <= n - 1);
+      } else if (p > n - 1) {
+        const int m = 2 * n - 1 - p, gs = ghost_sign(d, 2 * ax + 1);
+        S.idx[t] = m; S.sgn[t] = (signed char)gs; S.wall[t] = gs < 0 ? 2 * ax + 1 : -1; S.keep[t] = (m >= 0);
+      } else { S.idx[t] = p; S.keep[t] = true; }
     }
   }
 }

@@ -1,8 +1,9 @@
 // Exact solve of a coarse multigrid level by fast diagonalisation.  On a
 // uniform box level every grid of the projection preconditioner has a
 // separable operator: a velocity component of -eta LL (Sec. III.A; the
-// ghost-reflection rows at tangential walls and the Dirichlet rows at the
-// wall-normal boundary faces) and the Neumann pressure operator -D G are
+// ghost-reflection rows at tangential walls, odd at a no-slip and even at a
+// free-slip wall, and the Dirichlet rows at the wall-normal boundary faces)
+// and the Neumann pressure operator -D G are
 // Kronecker sums of 1D second differences, one per axis.  Their eigenvectors
 // are sine / cosine / Fourier bases in closed form, so the level solve is
 // three 1D transforms, a diagonal scaling and three transforms back, done in
@@ -23,7 +24,10 @@
 namespace rbfib {
 namespace {
 
-enum AxisKind { kDirichlet, kGhost, kNeumann, kPeriodic };
+// kGhost: odd ghost at both ends (no-slip walls); kNeumann: even ghost at
+// both ends (free-slip walls, and the pressure); kGhostNeumann /
+// kNeumannGhost: odd at the low end and even at the high end, or the reverse.
+enum AxisKind { kDirichlet, kGhost, kNeumann, kPeriodic, kGhostNeumann, kNeumannGhost };
 
 // The 1D second-difference matrix (times h^2) of one kind: 2 on the
 // diagonal, -1 off it; a missing neighbour adds +1 (ghost = -self),
@@ -36,16 +40,19 @@ void axis_matrix(AxisKind kind, int m, std::vector<double>& T) {
     for (int s = -1; s <= 1; s += 2) {
       int nb = j + s;
       if (kind == kPeriodic) { nb = (nb + m) % m; T[(size_t)j * m + nb] -= 1.0; continue; }
-      if (nb >= 0 && nb < m) T[(size_t)j * m + nb] -= 1.0;
-      else if (kind == kGhost) T[(size_t)j * m + j] += 1.0;
-      else if (kind == kNeumann) T[(size_t)j * m + j] -= 1.0;
+      if (nb >= 0 && nb < m) { T[(size_t)j * m + nb] -= 1.0; continue; }
+      const bool odd = kind == kGhost || (kind == kGhostNeumann && s < 0) || (kind == kNeumannGhost && s > 0);
+      const bool even = kind == kNeumann || (kind == kGhostNeumann && s > 0) || (kind == kNeumannGhost && s < 0);
+      if (odd) T[(size_t)j * m + j] += 1.0;
+      else if (even) T[(size_t)j * m + j] -= 1.0;
     }
   }
 }
 
 // Orthonormal eigenvectors Q[j * m + k] = q_k(j) and eigenvalues of the
-// matrix above: DST-I (Dirichlet), DST-II (ghost), DCT-II (Neumann), real
-// Fourier (periodic).  lam_0 = 0 exactly for the Neumann and periodic kinds.
+// matrix above: DST-I (Dirichlet), DST-II (ghost), DCT-II (Neumann), DST-IV
+// (odd low end, even high end), DCT-IV (the reverse), real Fourier
+// (periodic).  lam_0 = 0 exactly for the Neumann and periodic kinds.
 void axis_basis(AxisKind kind, int m, std::vector<double>& Q, std::vector<double>& lam) {
   const double pi = 3.14159265358979323846;
   Q.assign((size_t)m * m, 0.0);
@@ -69,6 +76,14 @@ void axis_basis(AxisKind kind, int m, std::vector<double>& Q, std::vector<double
           th = pi * k / m;
           c = std::sqrt((k == 0 ? 1.0 : 2.0) / m);
           v = c * std::cos(th * (j + 0.5));
+          break;
+        case kGhostNeumann:
+          th = pi * (k + 0.5) / m;
+          v = std::sqrt(2.0 / m) * std::sin(th * (j + 0.5));
+          break;
+        case kNeumannGhost:
+          th = pi * (k + 0.5) / m;
+          v = std::sqrt(2.0 / m) * std::cos(th * (j + 0.5));
           break;
         case kPeriodic: {
           // columns: constant; cos / sin pairs of frequency r; (-1)^j for even m
@@ -528,7 +543,11 @@ bool fd_plan(const Dims& d, bool faces, double eta, std::vector<float>& tab, FDP
       AxisKind kind;
       if (d.per[ax]) kind = kPeriodic;
       else if (!faces) kind = kNeumann;
-      else kind = (ax == g) ? kDirichlet : kGhost;
+      else if (ax == g) kind = kDirichlet;
+      else {
+        const bool even_lo = ghost_sign(d, 2 * ax) > 0, even_hi = ghost_sign(d, 2 * ax + 1) > 0;
+        kind = even_lo ? (even_hi ? kNeumann : kNeumannGhost) : (even_hi ? kGhostNeumann : kGhost);
+      }
       std::vector<double> Q, lam;
       axis_basis(kind, e[ax], Q, lam);
       if (!basis_ok(kind, e[ax], Q, lam)) return fail("basis check");

@@ -1,5 +1,6 @@
 // Fluctuating stress (Sec. III.A, Eq. LangevinD1): Philox4x64-10 normals and
-// the tensor divergence DD W with sqrt(2) weights on wall edges.
+// the tensor divergence DD W with sqrt(2) weights on no-slip wall edges and
+// zero weights on free-slip wall edges.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -96,8 +97,10 @@ __global__ void k_stress_div(Dims d, StressLayout L, const double* __restrict__ 
     double clo = 1.0, chi = 1.0;
     if (d.per[b]) { if (hi[b] >= d.n[b]) hi[b] = 0; }
     else {
-      if (lo[b] == 0) clo = 1.4142135623730951;
-      if (hi[b] == d.n[b]) chi = 1.4142135623730951;
+      // wall edges: sqrt(2) at a no-slip wall, 0 at a free-slip wall (no
+      // shear stress), so that DD DD^T = -LL with either ghost
+      if (lo[b] == 0) clo = d.gd[2 * b] > 0 ? 1.4142135623730951 : 0.0;
+      if (hi[b] == d.n[b]) chi = d.gd[2 * b + 1] > 0 ? 1.4142135623730951 : 0.0;
     }
     acc += (chi * Wab[flat3(e, hi[0], hi[1], hi[2])] - clo * Wab[flat3(e, lo[0], lo[1], lo[2])]) / d.h[b];
   }
@@ -166,6 +169,11 @@ extern "C" int rbfib_stochastic_forcing_static(const rbfib_grid_desc* desc, doub
     set_msg(errbuf, errlen, "stochastic_forcing_static: every axis periodic");
     return RBFIB_EINVAL;
   }
+  for (int w = 0; w < 6; ++w)
+    if (desc->free_slip[w] != 0 && desc->free_slip[w] != 1) {
+      set_msg(errbuf, errlen, "stochastic_forcing_static: free_slip must be 0 or 1");
+      return RBFIB_EINVAL;
+    }
   // Bound the cell count before any product of extents is formed: the
   // stress field holds about nine values per cell, so a grid with more cells
   // than the scratch has values can never fit (and the 64-bit products below
@@ -185,7 +193,8 @@ extern "C" int rbfib_stochastic_forcing_static(const rbfib_grid_desc* desc, doub
     }
   }
   const double h3[3] = {desc->h, desc->h, desc->h};
-  const Dims d = make_dims(n, per, h3);
+  Dims d = make_dims(n, per, h3);
+  set_free_slip(d, desc->free_slip);
   // stress layout: for a = x,y,z: W_aa (cells), then W_ab for b != a in increasing order
   StressLayout L;
   long long off = 0;

@@ -17,7 +17,8 @@ RBFIB_DEVFN T face_at(const Dims& d, const T* __restrict__ v, int a, const int c
 
 // Laplacian of component a at compact face c with the ghost-reflection
 // boundary conditions: Dirichlet zero at wall-normal boundary faces along a,
-// ghost = -self across walls along tangential axes, wrap on periodic axes.
+// ghost = -self across no-slip and +self across free-slip walls along
+// tangential axes (d.gd), wrap on periodic axes.
 // Returns sum_nb u_nb / h^2 (neighbours) and the diagonal coefficient.
 template <typename T>
 RBFIB_DEVFN void lap_parts(const Dims& d, const T* __restrict__ v, int a, const int c[3], T& nbsum, T& diag) {
@@ -37,9 +38,9 @@ RBFIB_DEVFN void lap_parts(const Dims& d, const T* __restrict__ v, int a, const 
       nbsum += (v[base + flat3(e, lo[0], lo[1], lo[2])] + v[base + flat3(e, hi[0], hi[1], hi[2])]) * ih2;
     } else {
       if (lo[ax] >= 0) nbsum += v[base + flat3(e, lo[0], lo[1], lo[2])] * ih2;
-      else if (ax != a) diag += ih2;
+      else if (ax != a) diag += T(d.gd[2 * ax]) * ih2;
       if (hi[ax] < e[ax]) nbsum += v[base + flat3(e, hi[0], hi[1], hi[2])] * ih2;
-      else if (ax != a) diag += ih2;
+      else if (ax != a) diag += T(d.gd[2 * ax + 1]) * ih2;
     }
   }
 }
@@ -62,8 +63,8 @@ RBFIB_DEVFN void lap_parts_uniform(const Dims& d, const T* __restrict__ v, int a
       nbsum += v[lo < 0 ? id + (e[ax] - 1) * str[ax] : id - str[ax]];
       nbsum += v[hi >= e[ax] ? id - (e[ax] - 1) * str[ax] : id + str[ax]];
     } else {
-      if (lo >= 0) nbsum += v[id - str[ax]]; else if (ax != a) ++diag;
-      if (hi < e[ax]) nbsum += v[id + str[ax]]; else if (ax != a) ++diag;
+      if (lo >= 0) nbsum += v[id - str[ax]]; else if (ax != a) diag += d.gd[2 * ax];
+      if (hi < e[ax]) nbsum += v[id + str[ax]]; else if (ax != a) diag += d.gd[2 * ax + 1];
     }
   }
 }
@@ -143,14 +144,14 @@ RBFIB_DEVFN void momentum_column(const Dims& d, int a, int i, int j, int k0, T e
   if (d.per[0]) { xm = i > 0 ? (unsigned)(i - 1) : (unsigned)(e0 - 1); xp = i < e0 - 1 ? (unsigned)(i + 1) : 0u; }
   else {
     xm = (unsigned)(i - 1); xp = (unsigned)(i + 1);
-    if (i == 0) { hxm = false; if (a != 0) ++dxy; }
-    if (i == e0 - 1) { hxp = false; if (a != 0) ++dxy; }
+    if (i == 0) { hxm = false; if (a != 0) dxy += d.gd[0]; }
+    if (i == e0 - 1) { hxp = false; if (a != 0) dxy += d.gd[1]; }
   }
   if (d.per[1]) { ym = j > 0 ? (unsigned)(j - 1) : (unsigned)(e1 - 1); yq = j < e1 - 1 ? (unsigned)(j + 1) : 0u; }
   else {
     ym = (unsigned)(j - 1); yq = (unsigned)(j + 1);
-    if (j == 0) { hym = false; if (a != 1) ++dxy; }
-    if (j == e1 - 1) { hyp = false; if (a != 1) ++dxy; }
+    if (j == 0) { hym = false; if (a != 1) dxy += d.gd[2]; }
+    if (j == e1 - 1) { hyp = false; if (a != 1) dxy += d.gd[3]; }
   }
   int cxl = i, cxr = i, cyl = j, cyr = j;
   if (a == 0) { if (d.per[0]) cxl = i > 0 ? i - 1 : nx - 1; else cxr = i + 1; }
@@ -178,7 +179,7 @@ RBFIB_DEVFN void momentum_column(const Dims& d, int a, int i, int j, int k0, T e
     const unsigned zo = sz * (unsigned)k;
     T nb = um + up;
     int diag = dxy + 2;
-    if (!perz && a != 2) diag += (!hzm) + (!hzp);
+    if (!perz && a != 2) diag += (hzm ? 0 : d.gd[4]) + (hzp ? 0 : d.gd[5]);
     if (hxm) nb += va[rxm + zo];
     if (hxp) nb += va[rxp + zo];
     if (hym) nb += va[rym + zo];
@@ -404,8 +405,9 @@ RBFIB_DEVFN void stokes_pipe_body(const Dims& d, T eta, const T* __restrict__ v,
   const int c0 = (ty + 1) * kPW + tx + 1;   // this thread's centre slot
   constexpr bool pxw = !PX, pyw = !PY;
   // momentum rows: per component, in-plane validity, the diagonal times
-  // eta/h^2 (a missing neighbour across a tangential wall is the ghost -u0,
-  // which adds one to the diagonal), output offset at plane 0
+  // eta/h^2 (a missing neighbour across a tangential wall is the ghost -u0
+  // of a no-slip wall, which adds one to the diagonal, or +u0 of a free-slip
+  // wall, which takes one off), output offset at plane 0
   bool in[3];
   T sdiag[3];
   unsigned obase[3];
@@ -414,8 +416,8 @@ RBFIB_DEVFN void stokes_pipe_body(const Dims& d, T eta, const T* __restrict__ v,
     const int* e = d.fe[a];
     in[a] = i < e[0] && j < e[1];
     int dg = 6;
-    if (a != 0 && pxw) dg += (i == 0) + (i == e[0] - 1);
-    if (a != 1 && pyw) dg += (j == 0) + (j == e[1] - 1);
+    if (a != 0 && pxw) dg += (i == 0 ? d.gd[0] : 0) + (i == e[0] - 1 ? d.gd[1] : 0);
+    if (a != 1 && pyw) dg += (j == 0 ? d.gd[2] : 0) + (j == e[1] - 1 ? d.gd[3] : 0);
     sdiag[a] = s * (T)dg;
     obase[a] = (unsigned)d.fo[a] + (unsigned)i + (unsigned)e[0] * (unsigned)j;
   }
@@ -445,7 +447,7 @@ RBFIB_DEVFN void stokes_pipe_body(const Dims& d, T eta, const T* __restrict__ v,
     for (int g = 0; g < 4; ++g) zp[g] = Sp[g * kPSlots + c0];
     stm = st0;
     // ghosts across the z walls for the tangential components
-    const T zadj = PZ ? T(0) : s * (T)((k == 0) + (k == nz - 1));
+    const T zadj = PZ ? T(0) : s * (T)((k == 0 ? d.gd[4] : 0) + (k == nz - 1 ? d.gd[5] : 0));
     const T pc = zc[3];
     T um[3], ux[3], uy[3];
 #pragma unroll
@@ -514,7 +516,8 @@ void launch_pipe(const Dims& d, cudaStream_t s, T eta, const T* v, const T* p, T
 constexpr i64 kPipeMinUnknowns = (i64)2 * 1024 * 1024;
 
 // ------------------------------------------ velocity multigrid (A = -eta LL)
-// Diagonal of -LL at a face (ghost faces across tangential walls add 1/h^2).
+// Diagonal of -LL at a face (a ghost across a tangential no-slip wall adds
+// 1/h^2, across a free-slip wall takes 1/h^2 off).
 template <typename T>
 RBFIB_DEVFN T lap_diag(const Dims& d, int a, const int c[3]) {
   T dg = T(0);
@@ -523,8 +526,8 @@ RBFIB_DEVFN T lap_diag(const Dims& d, int a, const int c[3]) {
     const T ih2 = inv_h2<T>(d, ax);
     dg += T(2) * ih2;
     if (!d.per[ax] && ax != a) {
-      if (c[ax] == 0) dg += ih2;
-      if (c[ax] == d.fe[a][ax] - 1) dg += ih2;
+      if (c[ax] == 0) dg += T(d.gd[2 * ax]) * ih2;
+      if (c[ax] == d.fe[a][ax] - 1) dg += T(d.gd[2 * ax + 1]) * ih2;
     }
   }
   return dg;
@@ -547,7 +550,8 @@ __global__ void k_vel_rbgs(Dims d, ColorMap m, T eta, int color, T* __restrict__
 // component a, plane k), y -> row j, x -> half-row index, so the point is
 // ((2 h' + parity), j, k) with no divisions.  The update is
 // u = (rhs h^2 / eta + sum of neighbours) / count, where count = 6 plus one
-// per tangential wall ghost; missing wall-normal neighbours are zero.
+// per tangential no-slip ghost and minus one per free-slip ghost; missing
+// wall-normal neighbours are zero.
 template <typename T>
 RBFIB_DEVFN T smooth_div(T a, int c);
 template <>
@@ -572,20 +576,20 @@ __global__ void k_vel_rbgs_u(Dims d, T sh, int color, T* __restrict__ u, const T
   // x
   if (d.per[0]) nb += ua[i > 0 ? id - 1 : id + (e0 - 1)] + ua[i < e0 - 1 ? id + 1 : id - (e0 - 1)];
   else {
-    if (i > 0) nb += ua[id - 1]; else if (a != 0) ++cnt;
-    if (i < e0 - 1) nb += ua[id + 1]; else if (a != 0) ++cnt;
+    if (i > 0) nb += ua[id - 1]; else if (a != 0) cnt += d.gd[0];
+    if (i < e0 - 1) nb += ua[id + 1]; else if (a != 0) cnt += d.gd[1];
   }
   // y
   if (d.per[1]) nb += ua[j > 0 ? id - sy : id + sy * (e1 - 1)] + ua[j < e1 - 1 ? id + sy : id - sy * (e1 - 1)];
   else {
-    if (j > 0) nb += ua[id - sy]; else if (a != 1) ++cnt;
-    if (j < e1 - 1) nb += ua[id + sy]; else if (a != 1) ++cnt;
+    if (j > 0) nb += ua[id - sy]; else if (a != 1) cnt += d.gd[2];
+    if (j < e1 - 1) nb += ua[id + sy]; else if (a != 1) cnt += d.gd[3];
   }
   // z
   if (d.per[2]) nb += ua[k > 0 ? id - sz : id + sz * (e2 - 1)] + ua[k < e2 - 1 ? id + sz : id - sz * (e2 - 1)];
   else {
-    if (k > 0) nb += ua[id - sz]; else if (a != 2) ++cnt;
-    if (k < e2 - 1) nb += ua[id + sz]; else if (a != 2) ++cnt;
+    if (k > 0) nb += ua[id - sz]; else if (a != 2) cnt += d.gd[4];
+    if (k < e2 - 1) nb += ua[id + sz]; else if (a != 2) cnt += d.gd[5];
   }
   ua[id] = smooth_div<T>(rhs[(unsigned)d.fo[a] + id] * sh + nb, cnt);
 }
@@ -623,12 +627,13 @@ __global__ void k_p_rbgs_u(Dims d, T sh, int color, T* __restrict__ u, const T* 
 }
 
 // Diagonal count of face (a; i, j, k) of the uniform-spacing velocity
-// operator: 6 plus one per tangential wall ghost.
+// operator: 6 plus one per tangential no-slip ghost, minus one per
+// free-slip ghost.
 RBFIB_DEVFN int face_count(const Dims& d, int a, int i, int j, int k, int e0, int e1, int e2) {
   int c = 6;
-  if (a != 0 && !d.per[0]) c += (i == 0) + (i == e0 - 1);
-  if (a != 1 && !d.per[1]) c += (j == 0) + (j == e1 - 1);
-  if (a != 2 && !d.per[2]) c += (k == 0) + (k == e2 - 1);
+  if (a != 0 && !d.per[0]) c += (i == 0 ? d.gd[0] : 0) + (i == e0 - 1 ? d.gd[1] : 0);
+  if (a != 1 && !d.per[1]) c += (j == 0 ? d.gd[2] : 0) + (j == e1 - 1 ? d.gd[3] : 0);
+  if (a != 2 && !d.per[2]) c += (k == 0 ? d.gd[4] : 0) + (k == e2 - 1 ? d.gd[5] : 0);
   return c;
 }
 
@@ -741,8 +746,9 @@ __global__ void k_vel_first(Dims d, T eta, T* __restrict__ u, const T* __restric
 
 // One-dimensional transfer stencils.  kind: 0 = not coarsened,
 // 1 = face-centred on a periodic axis, 2 = face-centred on a wall axis,
-// 3 = cell-centred.  ghost_sign: value of a cell-centred ghost beyond a wall
-// in units of the adjacent interior value (-1 Dirichlet, +1 Neumann).
+// 3 = cell-centred.  gs_lo, gs_hi: value of a cell-centred ghost beyond the
+// low / high wall in units of the adjacent interior value (-1 Dirichlet,
+// +1 Neumann), or 2 on a periodic axis.
 struct T1 { int cnt; int idx[3]; float w[3]; };   // weights exact in FP32
 
 // Lanes that share one coarse point of the fused residual-restriction
@@ -768,7 +774,7 @@ __device__ inline void restrict_1d(int kind, int ic, int nfext, T1& s) {
   s.idx[2] = P;     s.w[2] = 0.25f;    // physical P+1
 }
 
-__device__ inline void prolong_1d(int kind, int jf, int ncext, float ghost_sign, T1& s) {
+__device__ inline void prolong_1d(int kind, int jf, int ncext, float gs_lo, float gs_hi, T1& s) {
   if (kind == 0) { s.cnt = 1; s.idx[0] = jf; s.w[0] = 1.0f; return; }
   if (kind == 1) {
     if ((jf & 1) == 0) { s.cnt = 1; s.idx[0] = jf / 2; s.w[0] = 1.0f; return; }
@@ -790,6 +796,7 @@ __device__ inline void prolong_1d(int kind, int jf, int ncext, float ghost_sign,
   s.cnt = 2;
   s.idx[0] = jc; s.w[0] = 0.75f;
   if (nb < 0 || nb >= ncext) {
+    const float ghost_sign = nb < 0 ? gs_lo : gs_hi;
     if (ghost_sign == 2.0f) { nb = (nb + ncext) % ncext; s.idx[1] = nb; s.w[1] = 0.25f; }   // periodic
     else { s.cnt = 1; s.w[0] = 0.75f + 0.25f * ghost_sign; }
   } else { s.idx[1] = nb; s.w[1] = 0.25f; }
@@ -845,8 +852,9 @@ __global__ void k_vel_prolong(Dims df, Dims dc, int3 cz, const T* __restrict__ u
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
     int kind = !cf[ax] ? 0 : (ax == a ? (df.per[ax] ? 1 : 2) : 3);
-    float gs = df.per[ax] ? 2.0f : -1.0f;
-    prolong_1d(kind, c[ax], dc.fe[a][ax], gs, s[ax]);
+    const float gs_lo = df.per[ax] ? 2.0f : (float)ghost_sign(df, 2 * ax);
+    const float gs_hi = df.per[ax] ? 2.0f : (float)ghost_sign(df, 2 * ax + 1);
+    prolong_1d(kind, c[ax], dc.fe[a][ax], gs_lo, gs_hi, s[ax]);
   }
   T acc = T(0);
   for (int x = 0; x < s[0].cnt; ++x)
@@ -952,7 +960,10 @@ __global__ void k_p_prolong(Dims df, Dims dc, int3 cz, const T* __restrict__ uc,
   const int cf[3] = {cz.x, cz.y, cz.z};
   T1 s[3];
 #pragma unroll
-  for (int ax = 0; ax < 3; ++ax) prolong_1d(cf[ax] ? 3 : 0, c[ax], dc.n[ax], df.per[ax] ? 2.0f : 1.0f, s[ax]);
+  for (int ax = 0; ax < 3; ++ax) {
+    const float gs = df.per[ax] ? 2.0f : 1.0f;
+    prolong_1d(cf[ax] ? 3 : 0, c[ax], dc.n[ax], gs, gs, s[ax]);
+  }
   T acc = T(0);
   for (int x = 0; x < s[0].cnt; ++x)
     for (int y = 0; y < s[1].cnt; ++y)

@@ -863,6 +863,7 @@ void build_levels(rbfib_grid* g) {
   Level L0;
   double h3[3] = {g->desc.h, g->desc.h, g->desc.h};
   L0.d = make_dims(g->desc.n, g->desc.periodic, h3);
+  set_free_slip(L0.d, g->desc.free_slip);
   g->levels.push_back(L0);
   for (;;) {
     Level& cur = g->levels.back();
@@ -883,6 +884,7 @@ void build_levels(rbfib_grid* g) {
     }
     Level nx;
     nx.d = make_dims(n2, per, h2);
+    for (int w = 0; w < 6; ++w) nx.d.gd[w] = cur.d.gd[w];
     g->levels.push_back(nx);
   }
 }
@@ -1298,6 +1300,21 @@ int rbfib_create_grid(const rbfib_grid_desc* desc, void* stream, rbfib_grid** ou
     return RBFIB_EINVAL;
   for (int a = 0; a < 3; ++a)
     if (D.wall_vel[2 * a][a] != 0.0 || D.wall_vel[2 * a + 1][a] != 0.0) return RBFIB_EINVAL;
+  // free-slip walls: flags 0 / 1, no wall velocity, and no velocity component
+  // left without a no-slip wall (a constant null mode of its viscous operator)
+  for (int w = 0; w < 6; ++w) {
+    if (D.free_slip[w] != 0 && D.free_slip[w] != 1) return RBFIB_EINVAL;
+    if (D.free_slip[w] && !D.periodic[w / 2])
+      for (int c = 0; c < 3; ++c)
+        if (D.wall_vel[w][c] != 0.0) return RBFIB_EINVAL;
+  }
+  for (int a = 0; a < 3; ++a) {
+    if (!D.periodic[a]) continue;
+    bool pinned = false;
+    for (int b = 0; b < 3; ++b)
+      if (b != a && !D.periodic[b] && !(D.free_slip[2 * b] && D.free_slip[2 * b + 1])) pinned = true;
+    if (!pinned) return RBFIB_EINVAL;
+  }
   rbfib_grid* g = new rbfib_grid();
   try {
     g->desc = D;

@@ -38,7 +38,9 @@ def _static(B, desc, kT, dt, seed, step, out):
 
 
 @pytest.mark.parametrize("make", [lambda: workloads.two_sphere_cavity(steps=1),
-                                  lambda: workloads.small_case(n=(16, 10, 9), periodic=(True, False, False))])
+                                  lambda: workloads.small_case(n=(16, 10, 9), periodic=(True, False, False)),
+                                  lambda: workloads.small_case(n=(16, 10, 9), periodic=(True, False, False),
+                                                               free_slip=(False, False, True, False, False, True))])
 def test_static_forcing_matches_grid_entry_point(B, make):
     w = make()
     g = B.grid_for(w)

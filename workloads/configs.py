@@ -41,6 +41,7 @@ class Workload:
     potentials: dict = field(default_factory=dict)
     seed: int = 0
     kernel: int = 3                    # immersed-boundary kernel width (3 or 6 points per axis)
+    free_slip: tuple = (False,) * 6    # walls -x, +x, -y, +y, -z, +z: True = free-slip
 
     # flat views used by both implementations -------------------------
     @property
@@ -209,9 +210,10 @@ def adjoint_suspension():
 
 
 def small_case(n=(12, 10, 8), periodic=(False, False, False), n_bodies=2, blobs=12,
-               radius=1.0, seed=7, wall_speed=0.0, near_wall=False, kernel=3):
+               radius=1.0, seed=7, wall_speed=0.0, near_wall=False, kernel=3, free_slip=None):
     """A small seeded problem for parity tests: a few shells placed at random
-    (optionally hugging a wall) in a box of the given size."""
+    (optionally hugging a wall) in a box of the given size; free_slip marks
+    free-slip walls (which do not move)."""
     rng = np.random.Generator(np.random.Philox(WORKLOAD_SEED_BASE + 100 + seed))
     shell = icosahedral_shell(blobs, radius)
     L = np.asarray(n, dtype=np.float64)
@@ -226,15 +228,18 @@ def small_case(n=(12, 10, 8), periodic=(False, False, False), n_bodies=2, blobs=
                 break
     quats = random_unit_quaternions(rng, len(centres))
     w = Workload(name=f"small-{n[0]}x{n[1]}x{n[2]}", n=tuple(n), periodic=tuple(periodic),
-                 seed=WORKLOAD_SEED_BASE + 100 + seed, rtol=1e-10, kernel=kernel)
+                 seed=WORKLOAD_SEED_BASE + 100 + seed, rtol=1e-10, kernel=kernel,
+                 free_slip=tuple(bool(v) for v in free_slip) if free_slip is not None else (False,) * 6)
     w.bodies = [Body(shell, centres[i], quats[i]) for i in range(len(centres))]
     if wall_speed:
         w.wall_vel = np.zeros((6, 3))
         for ax in range(3):
             if not periodic[ax]:
                 t = (ax + 1) % 3
-                w.wall_vel[2 * ax + 1, t] = wall_speed
-                w.wall_vel[2 * ax, (ax + 2) % 3] = -0.5 * wall_speed
+                if not w.free_slip[2 * ax + 1]:
+                    w.wall_vel[2 * ax + 1, t] = wall_speed
+                if not w.free_slip[2 * ax]:
+                    w.wall_vel[2 * ax, (ax + 2) % 3] = -0.5 * wall_speed
     w.force_torque = rng.standard_normal((len(centres), 6))
     w.slip = 0.1 * rng.standard_normal((w.n_blobs, 3))
     w.potentials = {"gravity": 1.0,
