@@ -100,16 +100,21 @@ def single_sphere_box():
     return w
 
 
-def two_sphere_cavity(steps=2000, kernel=3):
+def two_sphere_cavity(steps=2000, kernel=3, free_slip=None):
     """Two 42-blob spheres (R = 2.5h) 6h apart along x in a 48x48x32 no-slip
     cuboid; kT = 1, eta = 1, dt = 0.05; gravity plus soft wall and pair
     repulsion of the form of Eq. (Usoft); orientations seeded.  kernel = 6:
-    the same setup with the paper's six-point kernel."""
+    the same setup with the paper's six-point kernel; free_slip: the same box
+    with the flagged walls (-x, +x, -y, +y, -z, +z) free-slip."""
     rng = _rng(1)
     shell = icosahedral_shell(42, 2.5)
     quats = random_unit_quaternions(rng, 2)
-    w = Workload(name="two-sphere-48x48x32" + ("" if kernel == 3 else "-6pt"), n=(48, 48, 32), dt=0.05,
-                 steps=steps, rtol=1e-8, seed=WORKLOAD_SEED_BASE + 1, kernel=kernel)
+    fs = (False,) * 6 if free_slip is None else tuple(bool(v) for v in free_slip)
+    name = "two-sphere-48x48x32" + ("" if kernel == 3 else "-6pt")
+    if any(fs):
+        name += "-free-slip-" + "".join(wn for wn, f in zip(("-x", "+x", "-y", "+y", "-z", "+z"), fs) if f)
+    w = Workload(name=name, n=(48, 48, 32), dt=0.05,
+                 steps=steps, rtol=1e-8, seed=WORKLOAD_SEED_BASE + 1, kernel=kernel, free_slip=fs)
     w.bodies = [Body(shell, np.array([21.0, 24.0, 16.0]), quats[0]),
                 Body(shell, np.array([27.0, 24.0, 16.0]), quats[1])]
     R = 2.5
