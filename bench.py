@@ -61,6 +61,15 @@ def parse():
     ap.add_argument("--ensemble-only", action="store_true", help="run only the ensemble leg")
     ap.add_argument("--ensemble-steps", type=int, default=2)
     ap.add_argument("--workers", type=int, default=16)
+    ap.add_argument("--msd", action="store_true",
+                    help="run only the two-sphere MSD experiment of Sec. V.A (12- and 42-blob spheres)")
+    ap.add_argument("--msd-replicas", type=int, default=64)
+    ap.add_argument("--msd-steps", type=int, default=1200)
+    ap.add_argument("--boomerang", action="store_true",
+                    help="run only the boomerang equilibrium experiment of App. A")
+    ap.add_argument("--boomerang-replicas", type=int, default=64)
+    ap.add_argument("--boomerang-steps", type=int, default=1500)
+    ap.add_argument("--boomerang-dtau", type=float, nargs="+", default=[0.14])
     return ap.parse_args()
 
 
@@ -477,6 +486,158 @@ def run_ensemble(args, B, torch):
     return out
 
 
+# ------------------------------------------------- equilibrium experiments
+def _replicas(B, torch, ws, steps, rfd=True, record_quat=False):
+    """Batched trajectories of the systems ws (one SEM step of each per batch
+    step, rejected steps retried with a new attempt, Sec. V).  Returns the
+    tracking points (steps + 1, n, 3 N_b), optionally the orientations, the
+    rejections and the system-steps/s of the stepping loop."""
+    import numpy as np
+    batch = B.Batch(ws, precision=B.FP64, workers=16)
+    q = [torch.tensor(x.q.ravel(), device="cuda") for x in ws]
+    quat = [torch.tensor(x.quat.ravel(), device="cuda") for x in ws]
+    params = [B.sem_params(x.potentials, dt=x.dt, kT=x.kT, rfd=rfd) for x in ws]
+    seeds = [x.seed + 101 * r for r, x in enumerate(ws)]
+    hq, ht = [torch.stack(q)], [torch.stack(quat)]
+    rejects = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        status, _ = batch.sem_step(params, seeds, k, q, quat)
+        for r, st in enumerate(status):
+            attempt = 0
+            while st == B.EREJECT and attempt < 50:
+                rejects += 1
+                attempt += 1
+                st, _ = batch.systems[r].sem_step(params[r], seeds[r], k, attempt, q[r], quat[r])
+            if st != B.OK:
+                raise RuntimeError(f"system {r} step {k}: status {st}")
+        hq.append(torch.stack(q))
+        if record_quat:
+            ht.append(torch.stack(quat))
+    torch.cuda.synchronize()
+    rate = len(ws) * steps / (time.perf_counter() - t0)
+    batch.close()
+    Q = torch.stack(hq).cpu().numpy()
+    T = torch.stack(ht).cpu().numpy() if record_quat else None
+    return Q, T, rejects, rate
+
+
+def _with_starts(make, starts, count):
+    import numpy as np
+    ws = []
+    for r in range(count):
+        w = make()
+        nb = w.n_bodies
+        for p, body in enumerate(w.bodies):
+            body.q = np.array(starts["q"][r % len(starts["q"])]).reshape(nb, 3)[p]
+            body.quat = np.array(starts["quat"][r % len(starts["quat"])]).reshape(nb, 4)[p]
+        ws.append(w)
+    return ws
+
+
+def run_msd(B, torch, blobs, n_rep, steps):
+    """Sec. V.A: equilibrium MSD blocks of the two confined spheres (self and
+    cross, along x and perpendicular), from n_rep trajectories started at
+    stored Gibbs-Boltzmann samples, against the short-time limit 2 kT <N^tt>
+    (Eq. SErel; <N^tt> from the GPU's solves at the same samples) and the
+    long-time limit twice the Gibbs-Boltzmann covariance (Eq. asymRef;
+    stored).  Lengths in units of R_h^2, times in 6 pi eta R_h^3 / kT."""
+    import numpy as np
+    import workloads
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", f"gb_two_sphere_msd_{blobs}.json")))
+    w0 = workloads.two_sphere_msd(blobs)
+    Rh, nb = w0.hydrodynamic_radius, w0.n_bodies
+    # <N^tt> over the stored samples
+    g = B.grid_for(w0, rtol=1e-10)
+    Nt = np.zeros((3 * nb, 3 * nb))
+    for qs, ts in zip(gold["starts"]["q"], gold["starts"]["quat"]):
+        g.set_bodies(w0.blob_offsets, w0.ref_blobs, np.array(qs).reshape(nb, 3), np.array(ts).reshape(nb, 4))
+        for p in range(nb):
+            for c in range(3):
+                F = np.zeros(6 * nb)
+                F[6 * p + c] = 1.0
+                U, _ = g.mobility_solve(torch.tensor(F, device="cuda"))
+                Nt[:, 3 * p + c] += U.cpu().numpy().reshape(nb, 6)[:, :3].ravel()
+    Nt /= len(gold["starts"]["q"])
+    g.close()
+    ws = _with_starts(lambda: workloads.two_sphere_msd(blobs), gold["starts"], n_rep)
+    X, _, rejects, rate = _replicas(B, torch, ws, steps)
+    tau = 6.0 * np.pi * Rh ** 3
+    lags = [l for l in (1, 2, 5, 10, 20, 50, 100, 200, 400, 700, 1000) if l < steps]
+
+    def blocks(M):
+        return {"self_par": 0.5 * (M[0, 0] + M[3, 3]), "self_perp": 0.25 * (M[1, 1] + M[2, 2] + M[4, 4] + M[5, 5]),
+                "cross_par": 0.5 * (M[0, 3] + M[3, 0]), "cross_perp": 0.25 * (M[1, 4] + M[4, 1] + M[2, 5] + M[5, 2])}
+    curve = []
+    for L in lags:
+        D = X[L:] - X[:-L]
+        per = np.einsum("trj,trk->rjk", D, D) / D.shape[0]
+        b_mean = blocks(per.mean(axis=0))
+        b_rep = [blocks(m) for m in per]
+        row = {"lag_steps": L, "t_over_tau": L * w0.dt / tau}
+        for k, v in b_mean.items():
+            row[k] = v / Rh ** 2
+            row[k + "_se"] = float(np.std([b[k] for b in b_rep], ddof=1) / np.sqrt(n_rep)) / Rh ** 2
+        curve.append(row)
+    se_want = blocks(2.0 * w0.kT * w0.dt * Nt)
+    first = curve[0]
+    asym = blocks(2.0 * np.array(gold["cov_q"]))
+    asym_err = blocks(2.0 * np.array(gold["cov_q_err"]))
+    last = curve[-1]
+    return {"workload": w0.name, "replicas": n_rep, "steps": steps, "dtau": 0.0044, "rejected_steps": rejects,
+            "system_steps_per_s": rate, "curve": curve,
+            "short_time": {k: {"msd_first_step": first[k], "stokes_einstein": se_want[k] / Rh ** 2,
+                               "ratio": first[k] / (se_want[k] / Rh ** 2) if se_want[k] != 0 else None}
+                           for k in se_want},
+            "long_time": {k: {"msd_last_lag": last[k], "se": last[k + "_se"], "gibbs_boltzmann": asym[k] / Rh ** 2,
+                              "gb_err": asym_err[k] / Rh ** 2} for k in asym}}
+
+
+def run_boomerang(B, torch, dtau, rfd, n_rep, steps, burn=None):
+    """App. A: the cross-point height and the bisector angle of the confined
+    boomerang over n_rep equilibrium trajectories (started at stored
+    Gibbs-Boltzmann samples), with or without the RFD drift, against the
+    stored Gibbs-Boltzmann densities: L2 distance of the densities and its
+    size for the Gibbs-Boltzmann histogram of the same number of samples."""
+    import numpy as np
+    import workloads
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "gb_boomerang.json")))
+    ws = _with_starts(lambda: workloads.boomerang_slit(dtau), gold["starts"], n_rep)
+    X, T, rejects, rate = _replicas(B, torch, ws, steps, rfd=rfd, record_quat=True)
+    if burn is None:
+        burn = steps // 5
+    z = X[burn:, :, 2].ravel()
+    w = T[burn:].reshape(-1, 4)
+    x_, y_, z_ = w[:, 1], w[:, 2], w[:, 3]
+    w_ = w[:, 0]
+    pb = np.array(gold["bisector_body_frame"])
+    # third row of R(quat) applied to the body-frame bisector
+    r20 = 2 * (x_ * z_ - w_ * y_)
+    r21 = 2 * (y_ * z_ + w_ * x_)
+    r22 = 1 - 2 * (x_ * x_ + y_ * y_)
+    theta = np.arccos(np.clip(r20 * pb[0] + r21 * pb[1] + r22 * pb[2], -1.0, 1.0))
+    ez, et = np.array(gold["height_edges"]), np.array(gold["angle_edges"])
+    hz, _ = np.histogram(z, bins=ez, density=True)
+    ht, _ = np.histogram(theta, bins=et, density=True)
+    gz, gt = np.array(gold["height_density"]), np.array(gold["angle_density"])
+    l2 = lambda a, b, e: float(np.sqrt(np.sum((a - b) ** 2 * np.diff(e))))
+    # sampling noise of the L2 error: half the distance between the
+    # histograms of the even and the odd replicas
+    zr = X[burn:, :, 2]
+    tr = theta.reshape(zr.shape)
+    hz0, _ = np.histogram(zr[:, 0::2].ravel(), bins=ez, density=True)
+    hz1, _ = np.histogram(zr[:, 1::2].ravel(), bins=ez, density=True)
+    ht0, _ = np.histogram(tr[:, 0::2].ravel(), bins=et, density=True)
+    ht1, _ = np.histogram(tr[:, 1::2].ravel(), bins=et, density=True)
+    return {"workload": ws[0].name, "rfd": rfd, "replicas": n_rep, "steps": steps, "burn_in_steps": burn,
+            "rejected_steps": rejects, "system_steps_per_s": rate,
+            "height_l2_error": l2(hz, gz, ez), "angle_l2_error": l2(ht, gt, et),
+            "height_l2_noise": 0.5 * l2(hz0, hz1, ez), "angle_l2_noise": 0.5 * l2(ht0, ht1, et),
+            "mean_height": float(z.mean()), "gb_mean_height": float(np.sum(gz * 0.5 * (ez[1:] + ez[:-1]) * np.diff(ez))),
+            "height_density": hz.tolist(), "angle_density": ht.tolist()}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import numpy as np
@@ -506,6 +667,20 @@ def run_ours(args):
     if args.ensemble_only:
         if rank == 0:
             print(json.dumps({"ensemble": run_ensemble(args, B, torch)}), flush=True)
+        return
+    if args.msd:
+        if rank == 0:
+            print(json.dumps({"msd": {str(b): run_msd(B, torch, b, args.msd_replicas, args.msd_steps)
+                                      for b in (12, 42)}}), flush=True)
+        return
+    if args.boomerang:
+        if rank == 0:
+            out = {}
+            for dtau in args.boomerang_dtau:
+                for rfd in (True, False):
+                    out[f"dtau{dtau:g}_{'rfd' if rfd else 'no_rfd'}"] = run_boomerang(
+                        B, torch, dtau, rfd, args.boomerang_replicas, args.boomerang_steps)
+            print(json.dumps({"boomerang": out}), flush=True)
         return
     w = workloads.two_sphere_cavity(steps=args.steps)
     g = B.grid_for(w, rtol=1e-8)

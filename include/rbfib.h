@@ -92,6 +92,9 @@ typedef struct {
   double dt, kT;
   double delta;              /* RFD step; <= 0 selects eps^(1/3), eps = 2^-52    */
   double gravity;            /* force -gravity * z on every body                */
+  double blob_gravity;       /* force -blob_gravity * z on every blob (the      */
+                             /* buoyant weight of App. A's boomerang blobs),   */
+                             /* with its torque about the tracking point       */
   double pair_phi0, pair_b, pair_d;      /* Usoft between body centres          */
   double wall_phi0, wall_b, wall_d;      /* Usoft between centres and walls     */
   double blob_wall_phi0, blob_wall_b, blob_wall_d;   /* Usoft blob-wall         */
@@ -99,6 +102,11 @@ typedef struct {
   double substrate_u0, substrate_s;                  /* substrate potential     */
   const double* force_ext;   /* device (N_b, 6) extra force/torque or NULL      */
   const double* slip;        /* device (N_bl, 3) active slip or NULL            */
+  int32_t no_rfd;            /* 0: Algorithm 1.  1: steps 1-5 skipped and the   */
+                             /* drift terms of step 6 set to zero (the naive   */
+                             /* Euler-Maruyama scheme whose biased equilibrium */
+                             /* App. A shows)                                  */
+  int32_t reserved;          /* must be 0                                       */
 } rbfib_sem_params;
 
 typedef struct {

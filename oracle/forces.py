@@ -1,7 +1,9 @@
 """External forces and torques on the bodies from the potentials of Sec. V:
 the soft repulsion of Eq. (Usoft) between body centres and between centres or
 blobs and the walls, the Yukawa pair repulsion of Eq. (YukawaPot), the
-commensurate substrate potential of Sec. V.B.1 and gravity.
+commensurate substrate potential of Sec. V.B.1, gravity on every body
+("gravity") and on every blob ("blob_gravity": the buoyant weight of the
+boomerang blobs of App. A, with its torque about the tracking point).
 
   Usoft:  Phi(r) = Phi0 (1 + (d - r)/b) for r < d, Phi0 exp((d - r)/b) for r >= d
           -dPhi/dr = (Phi0/b) * (1 if r < d else exp((d - r)/b))
@@ -59,6 +61,13 @@ def body_forces(g, b, potentials):
                 continue
             F[:, a] += _soft(q[:, a], p["phi0"], p["b"], p["d"])
             F[:, a] -= _soft(L[a] - q[:, a], p["phi0"], p["b"], p["d"])
+    if "blob_gravity" in potentials:
+        arm = rigid.arms(b.ref, b.offsets, b.quat)
+        f = np.zeros_like(arm)
+        f[:, 2] = -potentials["blob_gravity"]
+        bb = rigid.body_of_blob(b.offsets)
+        np.add.at(F[:, :3], bb, f)
+        np.add.at(F[:, 3:], bb, np.cross(arm, f))
     if "blob_wall_soft" in potentials:
         p = potentials["blob_wall_soft"]
         r = b.positions()

@@ -24,13 +24,15 @@ DELTA = 6.0554544523933395e-06
 
 
 def sem_step(g: Grid, b, eta, kT, dt, potentials, seed, step, attempt=0, delta=DELTA,
-             F_ext=None, slip=None, op=None, parts=False, normals=None, fluid_noise=True, M=None):
+             F_ext=None, slip=None, op=None, parts=False, normals=None, fluid_noise=True, M=None, rfd=True):
     """One SEM step from configuration b.  The random draws are Philox
     normals of (seed, step, attempt) unless injected: ``normals`` = (W^f,
     W^tau), each (N_b, 3), replaces the body draw of step 1, and
     ``fluid_noise=False`` drops the stochastic stress of step 6 (the drift
     tests drive the step with basis vectors).  ``M`` may pass a precomputed
-    blob mobility of b."""
+    blob mobility of b.  ``rfd=False`` skips steps 1-5 and sets the drift
+    terms of step 6 to zero: the naive Euler-Maruyama scheme whose biased
+    equilibrium App. A shows."""
     op = op or solve.StokesOperator(g, eta)
     nb, nbl = b.n_bodies, b.n_blobs
     o = saddle.layout(g, b)
@@ -38,17 +40,21 @@ def sem_step(g: Grid, b, eta, kT, dt, potentials, seed, step, attempt=0, delta=D
     F = forces.body_forces(g, b, potentials)
     if F_ext is not None:
         F = F + np.asarray(F_ext).reshape(nb, 6)
-    # step 1: random forces and torques
-    if normals is None:
-        Wf, Wt = noise.body_normals(nb, seed, step, attempt)
-    else:
-        Wf, Wt = (np.asarray(x, dtype=float).reshape(nb, 3) for x in normals)
-    Lp = rigid.body_length(b.ref, b.offsets)
-    WFT = noise.random_force_torque(Wf, Wt, Lp, kT)
     if M is None:
         M = solve.blob_mobility(g, b, eta, op=op)
-    rfd = rfd_terms(g, b, eta, kT, Wf, Wt, Lp, delta, M=M, op=op)
-    D_KT, D_K, D_J, D_S = rfd["D_KT"], rfd["D_K"], rfd["D_J"], rfd["D_S"]
+    if rfd:
+        # step 1: random forces and torques
+        if normals is None:
+            Wf, Wt = noise.body_normals(nb, seed, step, attempt)
+        else:
+            Wf, Wt = (np.asarray(x, dtype=float).reshape(nb, 3) for x in normals)
+        Lp = rigid.body_length(b.ref, b.offsets)
+        WFT = noise.random_force_torque(Wf, Wt, Lp, kT)
+        terms = rfd_terms(g, b, eta, kT, Wf, Wt, Lp, delta, M=M, op=op)
+        D_KT, D_K, D_J, D_S = terms["D_KT"], terms["D_K"], terms["D_J"], terms["D_S"]
+    else:
+        terms = {}
+        D_KT, D_K, D_J, D_S = np.zeros(6 * nb), np.zeros(3 * nbl), np.zeros(3 * nbl), np.zeros(3 * nbl)
     # step 6: fluctuating constrained solve
     f_noise = noise.fluid_forcing(g, eta, kT, dt, seed, step, attempt) if fluid_noise else np.zeros(g.N_f)
     slip_tot = (np.zeros(3 * nbl) if slip is None else np.asarray(slip).ravel()) + D_K - D_J - D_S
@@ -66,9 +72,10 @@ def sem_step(g: Grid, b, eta, kT, dt, potentials, seed, step, attempt=0, delta=D
             reject = True
     out = {"q": q_new, "quat": quat_new, "U": U, "reject": reject}
     if parts:
-        out.update(rfd)
-        out.update({"F": F, "WFT": WFT, "Wf": Wf, "Wt": Wt, "Lp": Lp, "x": x2,
-                    "f_noise": f_noise, "M": M})
+        out.update(terms)
+        out.update({"F": F, "x": x2, "f_noise": f_noise, "M": M})
+        if rfd:
+            out.update({"WFT": WFT, "Wf": Wf, "Wt": Wt, "Lp": Lp})
     return out
 
 

@@ -38,9 +38,10 @@ class SolveInfo(ctypes.Structure):
 
 class SemParams(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
-        "dt", "kT", "delta", "gravity", "pair_phi0", "pair_b", "pair_d", "wall_phi0", "wall_b", "wall_d",
+        "dt", "kT", "delta", "gravity", "blob_gravity", "pair_phi0", "pair_b", "pair_d", "wall_phi0", "wall_b", "wall_d",
         "blob_wall_phi0", "blob_wall_b", "blob_wall_d", "yukawa_u0", "yukawa_dh", "yukawa_lambda",
-        "substrate_u0", "substrate_s")] + [("force_ext", ctypes.c_void_p), ("slip", ctypes.c_void_p)]
+        "substrate_u0", "substrate_s")] + [("force_ext", ctypes.c_void_p), ("slip", ctypes.c_void_p),
+                                           ("no_rfd", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class StepInfo(ctypes.Structure):
@@ -141,12 +142,15 @@ def _ptr(t, dtype=torch.float64, numel=None, name="tensor"):
     return t.data_ptr()
 
 
-def sem_params(workload_potentials=None, dt=0.05, kT=1.0, delta=0.0, force_ext=None, slip=None):
-    """SemParams from a potentials dict of the seeded workloads."""
+def sem_params(workload_potentials=None, dt=0.05, kT=1.0, delta=0.0, force_ext=None, slip=None, rfd=True):
+    """SemParams from a potentials dict of the seeded workloads; rfd=False
+    runs the step without its drift terms (naive Euler-Maruyama)."""
     p = SemParams()
     p.dt, p.kT, p.delta = dt, kT, delta
     pot = workload_potentials or {}
     p.gravity = pot.get("gravity", 0.0)
+    p.blob_gravity = pot.get("blob_gravity", 0.0)
+    p.no_rfd = 0 if rfd else 1
     if "pair_soft" in pot:
         p.pair_phi0, p.pair_b, p.pair_d = (pot["pair_soft"][k] for k in ("phi0", "b", "d"))
     if "wall_soft" in pot:

@@ -639,14 +639,15 @@ __global__ void k_forces(Dims d, Potentials P, int nb, const int* __restrict__ b
       F[a] -= soft(L[a] - qp[a], P.wall_phi0, P.wall_b, P.wall_d);
     }
   }
-  if (P.bw_phi0 != 0.0) {
+  if (P.bw_phi0 != 0.0 || P.blob_g != 0.0) {
     for (int i = boff[p]; i < boff[p + 1]; ++i) {
-      double f[3] = {0, 0, 0};
-      for (int a = 0; a < 3; ++a) {
-        if (d.per[a]) continue;
-        f[a] += soft(r[3 * i + a], P.bw_phi0, P.bw_b, P.bw_d);
-        f[a] -= soft(L[a] - r[3 * i + a], P.bw_phi0, P.bw_b, P.bw_d);
-      }
+      double f[3] = {0, 0, -P.blob_g};
+      if (P.bw_phi0 != 0.0)
+        for (int a = 0; a < 3; ++a) {
+          if (d.per[a]) continue;
+          f[a] += soft(r[3 * i + a], P.bw_phi0, P.bw_b, P.bw_d);
+          f[a] -= soft(L[a] - r[3 * i + a], P.bw_phi0, P.bw_b, P.bw_d);
+        }
       const double* ar = arm + 3 * i;
       F[0] += f[0]; F[1] += f[1]; F[2] += f[2];
       F[3] += ar[1] * f[2] - ar[2] * f[1];

@@ -37,6 +37,7 @@ struct PrecondView {
 
 struct Potentials {
   double gravity;
+  double blob_g;     // force -blob_g z on every blob
   double pair_phi0, pair_b, pair_d;
   double wall_phi0, wall_b, wall_d;
   double bw_phi0, bw_b, bw_d;

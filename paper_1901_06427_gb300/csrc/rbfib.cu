@@ -1862,6 +1862,7 @@ namespace {
 Potentials potentials_of(const rbfib_sem_params* p) {
   Potentials P;
   P.gravity = p->gravity;
+  P.blob_g = p->blob_gravity;
   P.pair_phi0 = p->pair_phi0; P.pair_b = p->pair_b; P.pair_d = p->pair_d;
   P.wall_phi0 = p->wall_phi0; P.wall_b = p->wall_b; P.wall_d = p->wall_d;
   P.bw_phi0 = p->blob_wall_phi0; P.bw_b = p->blob_wall_b; P.bw_d = p->blob_wall_d;
@@ -1960,53 +1961,59 @@ int sem_step_body(rbfib_grid* g, const rbfib_sem_params* p, uint64_t seed, uint6
   refresh_config(g, g->cur, true);
   // forces F^n
   body_forces(g->d, potentials_of(p), view_of(g, g->cur), p->force_ext, g->bodyF, s);
-  // step 1: random forces and torques W^FT = kT [W^f / L_p ; W^tau]
-  normals(2u, 6 * (i64)nb, g->bodyWn);
-  wft(nb, g->bodyWn, g->Lp, p->kT, g->bodyW, s);
-  // step 2: constrained solve with W^FT (homogeneous)
-  build_rhs(g, g->bodyW, nullptr, nullptr, false, g->bvec);
-  int st1 = solve_system(g, g->bvec, g->xvec, true, &loc.solve_rfd, 0);
-  if (st1) st = st1;
-  ck(cudaMemcpyAsync(g->xrfd, g->xvec, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  const double* v_rfd = g->xrfd;
-  const double* lam_rfd = g->xrfd.p + g->nfl;
-  const double* U_rfd = lam_rfd + 3 * (i64)nbl;
-  // step 3: displaced configurations Q+- (lab-frame rotations by +-(delta/2) W^tau)
-  move_bodies(nb, g->cur.q, g->cur.quat, g->bodyWn, g->Lp, 0.5 * delta, g->plus.q, g->plus.quat, s);
-  move_bodies(nb, g->cur.q, g->cur.quat, g->bodyWn, g->Lp, -0.5 * delta, g->minus.q, g->minus.quat, s);
-  refresh_config(g, g->plus, false);
-  refresh_config(g, g->minus, false);
-  // step 4: unconstrained Stokes solve with (S(Q+) - S(Q-)) lambda / delta
-  ck(cudaMemsetAsync(g->fsharp, 0, sizeof(double) * g->nf, s));
-  spread<double>(g->d, nbl, nullptr, g->plus.r, lam_rfd, 1.0 / (delta * g->dV), g->fsharp, s);
-  spread<double>(g->d, nbl, nullptr, g->minus.r, lam_rfd, -1.0 / (delta * g->dV), g->fsharp, s);
-  ck(cudaMemsetAsync(g->bvec, 0, sizeof(double) * g->nfl, s));
-  ck(cudaMemcpyAsync(g->bvec, g->fsharp, sizeof(double) * g->nf, cudaMemcpyDeviceToDevice, s));
-  int st2 = solve_system(g, g->bvec, g->xvec, false, &loc.solve_stokes, 1);
-  if (st2 && !st) st = st2;
-  ck(cudaMemcpyAsync(g->vsharp, g->xvec, sizeof(double) * g->nf, cudaMemcpyDeviceToDevice, s));
-  // step 5: random finite differences
-  Walls w0 = {};
-  kt_apply(nb, g->boff, g->plus.arm, lam_rfd, 1.0, 0.0, g->bodyA, s);
-  kt_apply(nb, g->boff, g->minus.arm, lam_rfd, 1.0, 0.0, g->bodyB, s);
-  axpby<double>(g->bodyA, g->bodyB, -1.0, 1.0, 6 * (i64)nb, s);          // A = KT+ - KT-
-  axpby<double>(g->bodyA, g->bodyA, 0.0, 1.0 / delta, 6 * (i64)nb, s);   // D^{K^T}
-  k_apply(nbl, g->bob, g->plus.arm, U_rfd, 1.0, 0.0, g->blobA, s);
-  k_apply(nbl, g->bob, g->minus.arm, U_rfd, 1.0, 0.0, g->blobB, s);
-  axpby<double>(g->blobA, g->blobB, -1.0, 1.0, 3 * (i64)nbl, s);
-  axpby<double>(g->blobA, g->blobA, 0.0, 1.0 / delta, 3 * (i64)nbl, s);  // D^K
-  interp<double>(g->d, w0, nbl, g->plus.r, v_rfd, 1.0, 0.0, 0.0, g->blobC, s);
-  interp<double>(g->d, w0, nbl, g->minus.r, v_rfd, 1.0, 0.0, 0.0, g->blobD, s);
-  axpby<double>(g->blobC, g->blobD, -1.0, 1.0, 3 * (i64)nbl, s);
-  axpby<double>(g->blobC, g->blobC, 0.0, 1.0 / delta, 3 * (i64)nbl, s);  // D^J
-  interp_tab(g->d, view_of(g, g->cur), g->vsharp, 1.0, 0.0, g->blobD, s);                          // D^S
-  // slip_tot = slip + D^K - D^J - D^S ; F_tot = F - D^{K^T}
-  if (p->slip) ck(cudaMemcpyAsync(g->blobS, p->slip, sizeof(double) * 3 * nbl, cudaMemcpyDeviceToDevice, s));
-  else ck(cudaMemsetAsync(g->blobS, 0, sizeof(double) * 3 * std::max(nbl, 1), s));
-  axpby<double>(g->blobS, g->blobA, 1.0, 1.0, 3 * (i64)nbl, s);
-  axpby<double>(g->blobS, g->blobC, -1.0, 1.0, 3 * (i64)nbl, s);
-  axpby<double>(g->blobS, g->blobD, -1.0, 1.0, 3 * (i64)nbl, s);
-  axpby<double>(g->bodyF, g->bodyA, -1.0, 1.0, 6 * (i64)nb, s);
+  if (p->no_rfd) {
+    // naive Euler-Maruyama: no drift terms, step 6 only
+    if (p->slip) ck(cudaMemcpyAsync(g->blobS, p->slip, sizeof(double) * 3 * nbl, cudaMemcpyDeviceToDevice, s));
+    else ck(cudaMemsetAsync(g->blobS, 0, sizeof(double) * 3 * std::max(nbl, 1), s));
+  } else {
+    // step 1: random forces and torques W^FT = kT [W^f / L_p ; W^tau]
+    normals(2u, 6 * (i64)nb, g->bodyWn);
+    wft(nb, g->bodyWn, g->Lp, p->kT, g->bodyW, s);
+    // step 2: constrained solve with W^FT (homogeneous)
+    build_rhs(g, g->bodyW, nullptr, nullptr, false, g->bvec);
+    int st1 = solve_system(g, g->bvec, g->xvec, true, &loc.solve_rfd, 0);
+    if (st1) st = st1;
+    ck(cudaMemcpyAsync(g->xrfd, g->xvec, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    const double* v_rfd = g->xrfd;
+    const double* lam_rfd = g->xrfd.p + g->nfl;
+    const double* U_rfd = lam_rfd + 3 * (i64)nbl;
+    // step 3: displaced configurations Q+- (lab-frame rotations by +-(delta/2) W^tau)
+    move_bodies(nb, g->cur.q, g->cur.quat, g->bodyWn, g->Lp, 0.5 * delta, g->plus.q, g->plus.quat, s);
+    move_bodies(nb, g->cur.q, g->cur.quat, g->bodyWn, g->Lp, -0.5 * delta, g->minus.q, g->minus.quat, s);
+    refresh_config(g, g->plus, false);
+    refresh_config(g, g->minus, false);
+    // step 4: unconstrained Stokes solve with (S(Q+) - S(Q-)) lambda / delta
+    ck(cudaMemsetAsync(g->fsharp, 0, sizeof(double) * g->nf, s));
+    spread<double>(g->d, nbl, nullptr, g->plus.r, lam_rfd, 1.0 / (delta * g->dV), g->fsharp, s);
+    spread<double>(g->d, nbl, nullptr, g->minus.r, lam_rfd, -1.0 / (delta * g->dV), g->fsharp, s);
+    ck(cudaMemsetAsync(g->bvec, 0, sizeof(double) * g->nfl, s));
+    ck(cudaMemcpyAsync(g->bvec, g->fsharp, sizeof(double) * g->nf, cudaMemcpyDeviceToDevice, s));
+    int st2 = solve_system(g, g->bvec, g->xvec, false, &loc.solve_stokes, 1);
+    if (st2 && !st) st = st2;
+    ck(cudaMemcpyAsync(g->vsharp, g->xvec, sizeof(double) * g->nf, cudaMemcpyDeviceToDevice, s));
+    // step 5: random finite differences
+    Walls w0 = {};
+    kt_apply(nb, g->boff, g->plus.arm, lam_rfd, 1.0, 0.0, g->bodyA, s);
+    kt_apply(nb, g->boff, g->minus.arm, lam_rfd, 1.0, 0.0, g->bodyB, s);
+    axpby<double>(g->bodyA, g->bodyB, -1.0, 1.0, 6 * (i64)nb, s);          // A = KT+ - KT-
+    axpby<double>(g->bodyA, g->bodyA, 0.0, 1.0 / delta, 6 * (i64)nb, s);   // D^{K^T}
+    k_apply(nbl, g->bob, g->plus.arm, U_rfd, 1.0, 0.0, g->blobA, s);
+    k_apply(nbl, g->bob, g->minus.arm, U_rfd, 1.0, 0.0, g->blobB, s);
+    axpby<double>(g->blobA, g->blobB, -1.0, 1.0, 3 * (i64)nbl, s);
+    axpby<double>(g->blobA, g->blobA, 0.0, 1.0 / delta, 3 * (i64)nbl, s);  // D^K
+    interp<double>(g->d, w0, nbl, g->plus.r, v_rfd, 1.0, 0.0, 0.0, g->blobC, s);
+    interp<double>(g->d, w0, nbl, g->minus.r, v_rfd, 1.0, 0.0, 0.0, g->blobD, s);
+    axpby<double>(g->blobC, g->blobD, -1.0, 1.0, 3 * (i64)nbl, s);
+    axpby<double>(g->blobC, g->blobC, 0.0, 1.0 / delta, 3 * (i64)nbl, s);  // D^J
+    interp_tab(g->d, view_of(g, g->cur), g->vsharp, 1.0, 0.0, g->blobD, s);                          // D^S
+    // slip_tot = slip + D^K - D^J - D^S ; F_tot = F - D^{K^T}
+    if (p->slip) ck(cudaMemcpyAsync(g->blobS, p->slip, sizeof(double) * 3 * nbl, cudaMemcpyDeviceToDevice, s));
+    else ck(cudaMemsetAsync(g->blobS, 0, sizeof(double) * 3 * std::max(nbl, 1), s));
+    axpby<double>(g->blobS, g->blobA, 1.0, 1.0, 3 * (i64)nbl, s);
+    axpby<double>(g->blobS, g->blobC, -1.0, 1.0, 3 * (i64)nbl, s);
+    axpby<double>(g->blobS, g->blobD, -1.0, 1.0, 3 * (i64)nbl, s);
+    axpby<double>(g->bodyF, g->bodyA, -1.0, 1.0, 6 * (i64)nb, s);
+  }
   // step 6: fluctuating constrained solve
   normals(1u, g->stress.total, g->Wst);
   stress_divergence(g->d, g->stress, g->Wst, std::sqrt(2.0 * g->desc.eta * p->kT / (g->dV * p->dt)), g->fnoise, s);
@@ -2154,7 +2161,9 @@ int step_graph_finish(rbfib_grid* g, rbfib_step_info* info) {
 // Device-driven steps of ensemble systems (batch.cu).
 bool rbfib_grid_step_launch(rbfib_grid* g, const rbfib_sem_params* p, uint64_t seed, uint64_t step,
                             uint32_t attempt, double* q, double* quat) {
-  if (!g || !p || (g->nb > 0 && (!q || !quat)) || !(p->dt > 0) || !(p->kT >= 0) || !g->step_graphs) return false;
+  if (!g || !p || (g->nb > 0 && (!q || !quat)) || !(p->dt > 0) || !(p->kT >= 0) || !g->step_graphs ||
+      (p->no_rfd != 0 && p->no_rfd != 1) || p->reserved != 0)
+    return false;
   try {
     g->last_step_dev = step_graph_launch(g, p, seed, step, attempt, q, quat) ? 1 : 0;
     return g->last_step_dev != 0;
@@ -2180,7 +2189,8 @@ extern "C" {
 // synchronisation; otherwise the host orchestrates it.
 int rbfib_sem_step(rbfib_grid* g, const rbfib_sem_params* p, uint64_t seed, uint64_t step, uint32_t attempt,
                    double* q, double* quat, rbfib_step_info* info) {
-  if (!g || !p || (g->nb > 0 && (!q || !quat)) || !(p->dt > 0) || !(p->kT >= 0))
+  if (!g || !p || (g->nb > 0 && (!q || !quat)) || !(p->dt > 0) || !(p->kT >= 0) || (p->no_rfd != 0 && p->no_rfd != 1) ||
+      p->reserved != 0)
     return fail(g, RBFIB_EINVAL, "sem_step: bad argument");
   rbfib_step_info loc{};
   int st = 0;

@@ -2,8 +2,8 @@
 central finite differences of the potential ENERGIES, written out here from
 the paper: the soft repulsion of Eq. (Usoft) (between body centres, between
 centres and walls, and between blobs and walls), the Yukawa pair repulsion of
-Eq. (YukawaPot), the commensurate substrate potential of Sec. V.B.1 and
-gravity.  The force on body p is -dE/dq_p; the torque is -dE/dphi_p, with
+Eq. (YukawaPot), the commensurate substrate potential of Sec. V.B.1, gravity
+on the bodies and on every blob (App. A).  The force on body p is -dE/dq_p; the torque is -dE/dphi_p, with
 phi_p a lab-frame rotation angle applied to body p's arms (blob positions
 q_p + R(phi_p) R(quat_p) r_ref), computed with scipy's rotations rather than
 the oracle's quaternion code.  Pair distances use the minimum image along
@@ -52,6 +52,8 @@ def energy(L, per, q, arms, pot):
     E = 0.0
     if "gravity" in pot:
         E += pot["gravity"] * np.sum(q[:, 2])
+    if "blob_gravity" in pot:                     # weight of every blob at its height
+        E += pot["blob_gravity"] * sum(np.sum(q[p, 2] + arms[p][:, 2]) for p in range(nb))
     for p in range(nb):
         for s in range(p + 1, nb):
             r = np.linalg.norm(min_image(q[p] - q[s], L, per))
@@ -170,3 +172,24 @@ def test_periodic_image_pair_force():
     F = forces.body_forces(g, b, pot)
     np.testing.assert_allclose(F[0], [4.0 / 0.5, 0, 0, 0, 0, 0], atol=1e-12)
     np.testing.assert_allclose(F[1], [-4.0 / 0.5, 0, 0, 0, 0, 0], atol=1e-12)
+
+
+def test_blob_gravity_force_and_torque():
+    """Gravity on every blob of bodies whose tracking point is off the blob
+    centroid (an L-shaped arm, as the boomerang of App. A): the force is the
+    total weight and the torque is that of the weight at the centroid."""
+    n, per = (10, 9, 8), (False, False, False)
+    rng = np.random.default_rng(4)
+    arm = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.5, 0.0], [0.0, 1.0, 0.0]])
+    quat = rng.standard_normal((2, 4))
+    quat /= np.linalg.norm(quat, axis=1, keepdims=True)
+    g = Grid(n, periodic=per)
+    b = saddle.Bodies(np.vstack([arm, arm]), [0, 5, 10], np.array([[3.0, 3.0, 3.0], [6.0, 5.0, 4.0]]), quat)
+    pot = {"blob_gravity": 0.7}
+    L = np.asarray(g.length(), dtype=float)
+    arms = lab_arms(b.ref, b.offsets, b.quat)
+    F_fd = fd_forces(L, per, b.q, arms, pot)
+    F = forces.body_forces(g, b, pot)
+    np.testing.assert_allclose(F, F_fd, rtol=0, atol=2e-7)
+    assert np.abs(F[:, 3:]).max() > 0.1              # the torque is exercised
+    np.testing.assert_allclose(F[:, 2], -0.7 * 5, atol=1e-12)

@@ -13,9 +13,9 @@ made here.
 from .shells import icosahedral_shell, shell_12, shell_42
 from .configs import (Workload, Body, two_sphere_cavity, single_sphere_box,
                       driven_monolayer, batched_ensemble, adjoint_suspension,
-                      small_case, matvec_box, WORKLOAD_SEED_BASE)
+                      small_case, matvec_box, two_sphere_msd, boomerang_slit, WORKLOAD_SEED_BASE)
 
 __all__ = ["icosahedral_shell", "shell_12", "shell_42", "Workload", "Body",
            "two_sphere_cavity", "single_sphere_box", "driven_monolayer",
            "batched_ensemble", "adjoint_suspension", "small_case", "matvec_box",
-           "WORKLOAD_SEED_BASE"]
+           "two_sphere_msd", "boomerang_slit", "WORKLOAD_SEED_BASE"]

@@ -264,3 +264,60 @@ def matvec_box(n=256, n_bodies=64):
     w = Workload(name=f"matvec-box-{n}c", n=(n, n, n), rtol=1e-8, seed=WORKLOAD_SEED_BASE + 5)
     w.bodies = [Body(shell, centres[i], quats[i]) for i in range(centres.shape[0])]
     return w
+
+
+# The six-point kernel's blob hydrodynamic radius in grid units (Sec. V.A).
+BLOB_RADIUS_6PT = 1.47
+
+
+def two_sphere_msd(blobs=12):
+    """The tight cavity of Sec. V.A: two neutrally buoyant spheres of
+    hydrodynamic radius R_h = 0.656 um in a 3.478 x 1.739 x 1.739 um no-slip
+    box, discretised with the six-point kernel at h = 0.0543 (4, 2) um for
+    12- and 42-blob spheres: 16 x 8 x 8 or 32 x 16 x 16 cells, R_h = 3.02h or
+    6.04h.  The geometric radius is R_h - a, a = 1.47h the blob radius (our
+    reading; the paper takes it from a table of the cited multiblob work).
+    Soft pair (d = 2 R_h) and wall (d = R_h) repulsion of Eq. (Usoft) with
+    b = 0.1 R_h, Phi0 = 4 kT; kT = eta = 1; dt from the dimensionless step
+    dtau = kT dt / (6 pi eta R_h^3) = 0.0044.  The spheres start side by side
+    along x at mid-height (equilibrium starts come from Gibbs-Boltzmann
+    samples)."""
+    scale = {12: 1, 42: 2}[blobs]
+    n = (16 * scale, 8 * scale, 8 * scale)
+    Rh = 0.656 / (0.0543 * 4 / scale)
+    Rg = Rh - BLOB_RADIUS_6PT
+    shell = icosahedral_shell(blobs, Rg)
+    w = Workload(name=f"two-sphere-msd-{blobs}blob-{n[0]}x{n[1]}x{n[2]}", n=n, kernel=6, rtol=1e-8,
+                 seed=WORKLOAD_SEED_BASE + 20 + blobs)
+    w.dt = 0.0044 * 6.0 * np.pi * Rh ** 3
+    L = np.asarray(n, dtype=np.float64)
+    w.bodies = [Body(shell, np.array([L[0] / 4, L[1] / 2, L[2] / 2]), np.array([1.0, 0, 0, 0])),
+                Body(shell, np.array([3 * L[0] / 4, L[1] / 2, L[2] / 2]), np.array([1.0, 0, 0, 0]))]
+    w.potentials = {"pair_soft": {"phi0": 4.0, "b": 0.1 * Rh, "d": 2.0 * Rh},
+                    "wall_soft": {"phi0": 4.0, "b": 0.1 * Rh, "d": Rh}}
+    w.hydrodynamic_radius = Rh
+    return w
+
+
+def boomerang_slit(dtau=0.14, n=(64, 64, 16)):
+    """The confined boomerang of App. A: an L of 15 blobs (the cross point
+    and two arms of 7 blobs, spacing s = 0.3 um = 0.925 a, so the six-point
+    kernel's a = 1.47h gives h = 0.2208 um and s = 1.359h) in a 64h x 64h x 16h
+    slit (n: a smaller slit for parity tests), periodic in x and y, no-slip
+    walls in z; blob-wall repulsion of
+    Eq. (Usoft) with d = a, b = 0.1 a, Phi0 = 4 kT; the buoyant weight
+    m_e g = 1.57e-11 mg x 9.81 m/s^2 of every blob, 0.00819 kT/h at 300 K;
+    kT = eta = 1 and dt from dtau = kT dt / (6 pi eta a^3).  The tracking
+    point is the cross point; the body starts flat at mid-height."""
+    a = BLOB_RADIUS_6PT
+    s = 0.925 * a
+    arm = [np.array([k * s, 0.0, 0.0]) for k in range(1, 8)] + [np.array([0.0, k * s, 0.0]) for k in range(1, 8)]
+    ref = np.vstack([np.zeros((1, 3))] + [x[None, :] for x in arm])
+    w = Workload(name=f"boomerang-slit-{n[0]}x{n[1]}x{n[2]}-dtau{dtau:g}", n=tuple(n), periodic=(True, True, False),
+                 kernel=6, rtol=1e-8, seed=WORKLOAD_SEED_BASE + 30)
+    w.dt = dtau * 6.0 * np.pi * a ** 3
+    w.bodies = [Body(ref, np.array([n[0] / 2 - 2.0, n[1] / 2 - 2.0, n[2] / 2]), np.array([1.0, 0, 0, 0]))]
+    kT_300K = 1.380649e-23 * 300.0
+    weight = 1.57e-17 * 9.81 * 0.2208e-6 / kT_300K          # kT per h, per blob
+    w.potentials = {"blob_wall_soft": {"phi0": 4.0, "b": 0.1 * a, "d": a}, "blob_gravity": weight}
+    return w
