@@ -298,6 +298,33 @@ __device__ inline void philox_normals4(unsigned long long seed, unsigned long lo
 
 #define RBFIB_DEVFN __device__ __forceinline__
 
+// (J v)_ia by one warp.  Three-point kernel: lane l < 27 takes kernel point
+// (l % 3, l / 3 % 3, l / 9).  Six-point kernel: the 216 points p = l, l + 32,
+// ... are (p % 6, p / 6 % 6, p / 36).
+template <typename T>
+RBFIB_DEVFN T warp_interp(const Dims& d, int a, const BlobStencil<T>* __restrict__ S, const T* __restrict__ v,
+                          int lane) {
+  T val = T(0);
+  const T* va = v + d.fo[a];
+  if (d.kw == 3) {
+    if (lane < 27) {
+      const int x = lane % 3, y = (lane / 3) % 3, z = lane / 9;
+      const T w = S->w[x] * S->w[kKMax + y] * S->w[2 * kKMax + z];
+      if (w != T(0)) val = w * va[flat3(d.fe[a], S->idx[x], S->idx[kKMax + y], S->idx[2 * kKMax + z])];
+    }
+  } else {
+    for (int p = lane; p < 216; p += 32) {
+      const int x = p % 6, y = (p / 6) % 6, z = p / 36;
+      const T w = S->w[x] * S->w[kKMax + y] * S->w[2 * kKMax + z];
+      if (w != T(0)) val += w * va[flat3(d.fe[a], S->idx[x], S->idx[kKMax + y], S->idx[2 * kKMax + z])];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+  return val;
+}
+
+
 // Rotation matrix (row-major) of a unit quaternion (w, x, y, z).
 RBFIB_DEVFN void quat_rot(const double* qt, double R[9]) {
   const double w = qt[0], x = qt[1], y = qt[2], z = qt[3];

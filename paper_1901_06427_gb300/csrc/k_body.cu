@@ -364,7 +364,9 @@ cudaError_t dense_body_build(int nbl, int nb, const int* boff, const int* bob, c
 // U = N f; lam = M^-1 (K U - s) = P U - t with P = M^-1 K from the set-up.
 // The rows of t, U and lam are split over the CTAs; t and U are exchanged
 // through distributed shared memory.  s, r_U in, lam, U out (type T;
-// internal FP32 / FP64).
+// internal FP32 / FP64).  With tab set, the kernel first forms
+// s = r_lam + J v itself (one warp per blob component over the cluster,
+// written to sres, then a cluster barrier), which saves a launch.
 constexpr int kBodyCtas = 8;
 
 template <typename T>
@@ -372,7 +374,9 @@ __global__ void __cluster_dims__(kBodyCtas, 1, 1) __launch_bounds__(512)
     k_dense_body_apply(int nbl, int nb, const int* __restrict__ boff, const int* __restrict__ bob,
                        const double* __restrict__ arm, const float* __restrict__ Mi, const float* __restrict__ P,
                        const double* __restrict__ N, const T* __restrict__ sres, const T* __restrict__ rU,
-                       T* __restrict__ zlam, T* __restrict__ zU) {
+                       T* __restrict__ zlam, T* __restrict__ zU, double* __restrict__ zlam64,
+                       double* __restrict__ zU64, Dims d, const BlobStencil<T>* __restrict__ tab,
+                       const T* __restrict__ v, const T* __restrict__ rl, T* __restrict__ sres_out) {
   pdl_entry();
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
@@ -388,7 +392,16 @@ __global__ void __cluster_dims__(kBodyCtas, 1, 1) __launch_bounds__(512)
   float* sv = (float*)(Uloc + upc);   // n3
   float* tloc = sv + n3;              // rpc (this CTA's rows of t)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = threadIdx.x; i < n3; i += blockDim.x) sv[i] = (float)sres[i];
+  if (tab) {
+    for (int c = rank * nw + wid; c < n3; c += kBodyCtas * nw) {
+      const T jv = warp_interp<T>(d, c % 3, tab + c, v, lane);
+      if (lane == 0) sres_out[c] = rl[c] + jv;
+    }
+    cl.sync();   // release / acquire at cluster scope: every CTA's rows of s are visible
+    for (int i = threadIdx.x; i < n3; i += blockDim.x) sv[i] = (float)__ldcg(sres_out + i);
+  } else {
+    for (int i = threadIdx.x; i < n3; i += blockDim.x) sv[i] = (float)sres[i];
+  }
   __syncthreads();
   // rows of t = M^-1 s, one warp per row
   for (int row = r0 + wid; row < r1; row += nw) {
@@ -435,6 +448,7 @@ __global__ void __cluster_dims__(kBodyCtas, 1, 1) __launch_bounds__(512)
     for (int c = 0; c < m; ++c) acc = fma(N[(i64)r * m + c], f[c], acc);
     Uloc[r - u0] = acc;
     zU[r] = (T)acc;
+    if (zU64) zU64[r] = (double)(T)acc;
   }
   cl.sync();
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
@@ -448,24 +462,31 @@ __global__ void __cluster_dims__(kBodyCtas, 1, 1) __launch_bounds__(512)
     float acc = -tloc[row - r0];
     for (int c = 0; c < m; ++c) acc = fmaf(Pr[c], (float)Uall[c], acc);
     zlam[row] = (T)acc;
+    if (zlam64) zlam64[row] = (double)(T)acc;
   }
   cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
 template <typename T>
 void dense_body_apply(int nbl, int nb, const int* boff, const int* bob, const double* arm, const float* Minv,
-                      const float* P, const double* N, const T* sres, const T* rU, T* zlam, T* zU, cudaStream_t s) {
+                      const float* P, const double* N, const T* sres, const T* rU, T* zlam, T* zU, double* zlam64,
+                      double* zU64, cudaStream_t s, const Dims* d, const BlobStencil<T>* tab, const T* v,
+                      const T* rl, T* sres_out) {
   const int n3 = 3 * nbl, m = 6 * nb;
   const int rpc = (n3 + kBodyCtas - 1) / kBodyCtas, upc = (m + kBodyCtas - 1) / kBodyCtas;
   const size_t shm = sizeof(double) * (2 * (size_t)m + upc) + sizeof(float) * ((size_t)n3 + rpc);
-  k_dense_body_apply<T><<<kBodyCtas, 512, shm, s>>>(nbl, nb, boff, bob, arm, Minv, P, N, sres, rU, zlam, zU);
+  launch_k(k_dense_body_apply<T>, kBodyCtas, 512, shm, s, nbl, nb, boff, bob, arm, Minv, P, N, sres, rU, zlam, zU,
+           zlam64, zU64, d ? *d : Dims{}, tab, v, rl, sres_out);
   note_launch();
 }
 
 template void dense_body_apply<float>(int, int, const int*, const int*, const double*, const float*, const float*,
-                                      const double*, const float*, const float*, float*, float*, cudaStream_t);
+                                      const double*, const float*, const float*, float*, float*, double*, double*,
+                                      cudaStream_t, const Dims*, const BlobStencil<float>*, const float*, const float*,
+                                      float*);
 template void dense_body_apply<double>(int, int, const int*, const int*, const double*, const float*,
                                        const float*, const double*, const double*, const double*, double*, double*,
-                                       cudaStream_t);
+                                       double*, double*, cudaStream_t, const Dims*, const BlobStencil<double>*,
+                                       const double*, const double*, double*);
 
 }  // namespace rbfib

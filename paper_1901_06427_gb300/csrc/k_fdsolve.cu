@@ -574,7 +574,7 @@ void fd_solve(const FDParams& P, float* u, const float* rhs, cudaStream_t s) {
   std::call_once(f, [] {
     cudaFuncSetAttribute(k_fd_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, kFDMaxSmem);
   });
-  k_fd_solve<<<P.ng * kFDCtas, kFDThreads, P.smem, s>>>(P, u, rhs);
+  launch_k(k_fd_solve, P.ng * kFDCtas, kFDThreads, P.smem, s, P, u, rhs);
   note_launch();
 }
 

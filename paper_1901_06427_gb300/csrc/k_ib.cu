@@ -252,32 +252,6 @@ template <typename T> RBFIB_DEVFN const BlobStencil<T>* table_of(const BodyView&
 template <> RBFIB_DEVFN const BlobStencil<double>* table_of<double>(const BodyView& b) { return b.st64; }
 template <> RBFIB_DEVFN const BlobStencil<float>* table_of<float>(const BodyView& b) { return b.st32; }
 
-// (J v)_ia by one warp.  Three-point kernel: lane l < 27 takes kernel point
-// (l % 3, l / 3 % 3, l / 9).  Six-point kernel: the 216 points p = l, l + 32,
-// ... are (p % 6, p / 6 % 6, p / 36).
-template <typename T>
-RBFIB_DEVFN T warp_interp(const Dims& d, int a, const BlobStencil<T>* __restrict__ S, const T* __restrict__ v,
-                          int lane) {
-  T val = T(0);
-  const T* va = v + d.fo[a];
-  if (d.kw == 3) {
-    if (lane < 27) {
-      const int x = lane % 3, y = (lane / 3) % 3, z = lane / 9;
-      const T w = S->w[x] * S->w[kKMax + y] * S->w[2 * kKMax + z];
-      if (w != T(0)) val = w * va[flat3(d.fe[a], S->idx[x], S->idx[kKMax + y], S->idx[2 * kKMax + z])];
-    }
-  } else {
-    for (int p = lane; p < 216; p += 32) {
-      const int x = p % 6, y = (p / 6) % 6, z = p / 36;
-      const T w = S->w[x] * S->w[kKMax + y] * S->w[2 * kKMax + z];
-      if (w != T(0)) val += w * va[flat3(d.fe[a], S->idx[x], S->idx[kKMax + y], S->idx[2 * kKMax + z])];
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
-  return val;
-}
-
 // f_a += val * w at the kernel points, one atomic per point.
 template <typename T>
 RBFIB_DEVFN void warp_spread(const Dims& d, int a, const BlobStencil<T>* __restrict__ S, T val, T* __restrict__ f,
@@ -505,7 +479,8 @@ __global__ void k_body_precond(int nb, const int* __restrict__ boff, const int* 
                                const double* __restrict__ nmat, const int* __restrict__ shape_ref_blob,
                                const double* __restrict__ ref, const double* __restrict__ quat,
                                const T* __restrict__ sres, const T* __restrict__ rU,
-                               T* __restrict__ zlam, T* __restrict__ zU) {
+                               T* __restrict__ zlam, T* __restrict__ zU, double* __restrict__ zlam64,
+                               double* __restrict__ zU64) {
   pdl_entry();
   extern __shared__ unsigned char shraw[];
   T* sh = (T*)shraw;
@@ -578,24 +553,29 @@ __global__ void k_body_precond(int nb, const int* __restrict__ boff, const int* 
   __syncthreads();
   for (int i = threadIdx.x; i < nbp; i += blockDim.x) {
     const T* l = sp + 3 * i;
-    for (int a = 0; a < 3; ++a)
-      zlam[3 * (b0 + i) + a] = (T)(R[3 * a] * (double)l[0] + R[3 * a + 1] * (double)l[1] + R[3 * a + 2] * (double)l[2]);
+    for (int a = 0; a < 3; ++a) {
+      const T x = (T)(R[3 * a] * (double)l[0] + R[3 * a + 1] * (double)l[1] + R[3 * a + 2] * (double)l[2]);
+      zlam[3 * (b0 + i) + a] = x;
+      if (zlam64) zlam64[3 * (b0 + i) + a] = (double)x;
+    }
   }
   if (threadIdx.x < 6) {
     const int h = threadIdx.x / 3, a = threadIdx.x % 3;
-    zU[6 * p + threadIdx.x] = (T)(R[3 * a] * w6[3 * h] + R[3 * a + 1] * w6[3 * h + 1] + R[3 * a + 2] * w6[3 * h + 2]);
+    const T u = (T)(R[3 * a] * w6[3 * h] + R[3 * a + 1] * w6[3 * h + 1] + R[3 * a + 2] * w6[3 * h + 2]);
+    zU[6 * p + threadIdx.x] = u;
+    if (zU64) zU64[6 * p + threadIdx.x] = (double)u;
   }
 }
 
 template <typename T>
 void body_precond(const BodyView& b, const PrecondView& pv, const T* sres, const T* rU, T* zlam, T* zU,
-                  cudaStream_t s) {
+                  double* zlam64, double* zU64, cudaStream_t s) {
   if (b.nb == 0) return;
   const size_t shm = sizeof(T) * (2 * 3 * (size_t)pv.max_blobs + 8);
   const T* mi = nullptr;
   if constexpr (sizeof(T) == 8) mi = (const T*)pv.minv; else mi = (const T*)pv.minv32;
   launch_k(k_body_precond<T>, b.nb, 256, shm, s, b.nb, b.boff, pv.shape_of, pv.minv_off, mi, pv.nmat,
-           pv.shape_ref_blob, b.ref, b.quat, sres, rU, zlam, zU);
+           pv.shape_ref_blob, b.ref, b.quat, sres, rU, zlam, zU, zlam64, zU64);
   note_launch();
 }
 
@@ -775,7 +755,7 @@ void outside_check(const Dims& d, int nbl, const double* r, int* flag, cudaStrea
   template void spread<T>(const Dims&, int, const int*, const double*, const T*, double, T*, cudaStream_t); \
   template void interp<T>(const Dims&, const Walls&, int, const double*, const T*, double, double, double, \
                           T*, cudaStream_t);                                                             \
-  template void body_precond<T>(const BodyView&, const PrecondView&, const T*, const T*, T*, T*,        \
+  template void body_precond<T>(const BodyView&, const PrecondView&, const T*, const T*, T*, T*, double*, double*,        \
                                 cudaStream_t);                                                          \
   template void interp_res<T>(const Dims&, const BodyView&, const T*, const T*, T*, cudaStream_t);
 INST(double)

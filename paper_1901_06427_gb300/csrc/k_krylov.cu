@@ -801,16 +801,6 @@ void fg_start(T* V0, const T* w, i64 n, double* gvec, int m, int* ist, const dou
   note_launch();
 }
 
-__global__ void k_setcond(cudaGraphConditionalHandle h, const int* __restrict__ ist) {
-  pdl_entry();
-  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, ist[2] ? 1u : 0u);
-}
-
-void set_condition(cudaGraphConditionalHandle h, const int* ist, cudaStream_t s) {
-  launch_k(k_setcond, 1, 32, 0, s, h, ist);
-  note_launch();
-}
-
 // Givens update of column j (as k_givens) plus the continue decision.
 RBFIB_DEVFN void givens_flag_body(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                                   const double* hcol2, const double* hnext2, double* res_out, int* ist,
@@ -829,16 +819,18 @@ RBFIB_DEVFN void givens_flag_body(double* H, int ldh, double* cs, double* sn, do
 // neither needs the other: blocks [0, gridDim.x - 1) normalise the new basis
 // vector, v = w / sqrt(nrm2) (and its FP32 copy when out32 is not null);
 // the last block applies the Givens update of column j and sets the continue
-// flag.  The update's FP64 recurrence then runs beside the scaling instead of
-// in a launch of its own.
+// flag, and with use_next also the condition of the next iteration's IF node
+// (so no launch of its own sets it).  The update's FP64 recurrence then runs
+// beside the scaling instead of in a launch of its own.
 template <typename T>
 __global__ void k_scale_givens(T* __restrict__ out, const T* __restrict__ in, i64 n, float* __restrict__ out32,
                                double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                                const double* hcol2, const double* nrm2, double* res_out, int* ist,
-                               const double* dpar) {
+                               const double* dpar, cudaGraphConditionalHandle next, int use_next) {
   pdl_entry();
   if (blockIdx.x == gridDim.x - 1) {
     givens_flag_body(H, ldh, cs, sn, g, j, hcol, hcol2, nrm2, res_out, ist, dpar);
+    if (use_next && threadIdx.x == 0) cudaGraphSetConditional(next, ist[2] ? 1u : 0u);
     return;
   }
   __shared__ double fs;
@@ -859,18 +851,18 @@ __global__ void k_scale_givens(T* __restrict__ out, const T* __restrict__ in, i6
 template <typename T>
 void scale_givens(T* out, const T* in, i64 n, float* out32, double* H, int ldh, double* cs, double* sn, double* g,
                   int j, const double* hcol, const double* hcol2, const double* nrm2, double* res_out, int* ist,
-                  const double* dpar, cudaStream_t s) {
+                  const double* dpar, cudaStream_t s, const cudaGraphConditionalHandle* next) {
   const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);
   launch_k(k_scale_givens<T>, nb + 1, 256, 0, s, out, in, n, out32, H, ldh, cs, sn, g, j, hcol, hcol2, nrm2,
-           res_out, ist, dpar);
+           res_out, ist, dpar, next ? *next : cudaGraphConditionalHandle{}, next ? 1 : 0);
   note_launch();
 }
 template void scale_givens<double>(double*, const double*, i64, float*, double*, int, double*, double*, double*,
                                    int, const double*, const double*, const double*, double*, int*, const double*,
-                                   cudaStream_t);
+                                   cudaStream_t, const cudaGraphConditionalHandle*);
 template void scale_givens<float>(float*, const float*, i64, float*, double*, int, double*, double*, double*, int,
                                   const double*, const double*, const double*, double*, int*, const double*,
-                                  cudaStream_t);
+                                  cudaStream_t, const cudaGraphConditionalHandle*);
 
 __global__ void k_tri_dev(const double* H, int ldh, const double* g, const int* ist, double* y) {
   pdl_entry();

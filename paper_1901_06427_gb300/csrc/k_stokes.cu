@@ -1027,10 +1027,10 @@ __global__ void k_p_coarse(Dims d, T* __restrict__ u, T* __restrict__ rhs, int s
 }
 
 // ------------------------------------------------ projection preconditioner
-// q = r_pi + D v~ ; pi = -eta q
+// q = r_pi + D v~ ; pi = -eta q (and its FP64 copy pi64 unless null)
 template <typename T>
 __global__ void k_div_q(Dims d, T eta, const T* __restrict__ vt, const T* __restrict__ rpi,
-                        T* __restrict__ q, T* __restrict__ pi) {
+                        T* __restrict__ q, T* __restrict__ pi, double* __restrict__ pi64) {
   pdl_entry();
   const i64 l = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= d.nc) return;
@@ -1053,12 +1053,14 @@ __global__ void k_div_q(Dims d, T eta, const T* __restrict__ vt, const T* __rest
   }
   const T qq = rpi[l] + div;
   q[l] = qq;
-  pi[l] = -eta * qq;
+  const T pv = -eta * qq;
+  pi[l] = pv;
+  if (pi64) pi64[l] = (double)pv;
 }
 
-// v += G phi
+// v += G phi (and its FP64 copy v64 unless null)
 template <typename T>
-__global__ void k_add_grad(Dims d, const T* __restrict__ phi, T* __restrict__ v) {
+__global__ void k_add_grad(Dims d, const T* __restrict__ phi, T* __restrict__ v, double* __restrict__ v64) {
   pdl_entry();
   const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.fo[3]) return;
@@ -1067,7 +1069,9 @@ __global__ void k_add_grad(Dims d, const T* __restrict__ phi, T* __restrict__ v)
   int cl[3] = {c[0], c[1], c[2]}, cr[3] = {c[0], c[1], c[2]};
   if (d.per[a]) { cl[a] = c[a] - 1; if (cl[a] < 0) cl[a] += d.n[a]; }
   else { cr[a] = c[a] + 1; }
-  v[t] += (phi[flat3(d.n, cr[0], cr[1], cr[2])] - phi[flat3(d.n, cl[0], cl[1], cl[2])]) * inv_h<T>(d, a);
+  const T nv = v[t] + (phi[flat3(d.n, cr[0], cr[1], cr[2])] - phi[flat3(d.n, cl[0], cl[1], cl[2])]) * inv_h<T>(d, a);
+  v[t] = nv;
+  if (v64) v64[t] = (double)nv;
 }
 
 // ---------------------------------------------------------------- launchers
@@ -1183,13 +1187,13 @@ void p_coarse(const Dims& d, T* u, T* rhs, int sweeps, cudaStream_t s) {
   note_launch();
 }
 template <typename T>
-void div_q(const Dims& d, T eta, const T* vt, const T* rpi, T* q, T* pi, cudaStream_t s) {
-  launch_k(k_div_q<T>, nblk(d.nc, 256), 256, 0, s, d, eta, vt, rpi, q, pi);
+void div_q(const Dims& d, T eta, const T* vt, const T* rpi, T* q, T* pi, double* pi64, cudaStream_t s) {
+  launch_k(k_div_q<T>, nblk(d.nc, 256), 256, 0, s, d, eta, vt, rpi, q, pi, pi64);
   note_launch();
 }
 template <typename T>
-void add_grad(const Dims& d, const T* phi, T* v, cudaStream_t s) {
-  launch_k(k_add_grad<T>, nblk(d.fo[3], 256), 256, 0, s, d, phi, v);
+void add_grad(const Dims& d, const T* phi, T* v, double* v64, cudaStream_t s) {
+  launch_k(k_add_grad<T>, nblk(d.fo[3], 256), 256, 0, s, d, phi, v, v64);
   note_launch();
 }
 
@@ -1207,8 +1211,8 @@ void add_grad(const Dims& d, const T* phi, T* v, cudaStream_t s) {
   template void p_rbgs<T>(const Dims&, int, T*, const T*, cudaStream_t, int);                    \
   template void p_prolong<T>(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);        \
   template void p_coarse<T>(const Dims&, T*, T*, int, cudaStream_t);                             \
-  template void div_q<T>(const Dims&, T, const T*, const T*, T*, T*, cudaStream_t);              \
-  template void add_grad<T>(const Dims&, const T*, T*, cudaStream_t);
+  template void div_q<T>(const Dims&, T, const T*, const T*, T*, T*, double*, cudaStream_t);     \
+  template void add_grad<T>(const Dims&, const T*, T*, double*, cudaStream_t);
 INST(double)
 INST(float)
 #undef INST

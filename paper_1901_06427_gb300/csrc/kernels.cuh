@@ -72,8 +72,10 @@ template <typename T> void vel_coarse(const Dims&, T eta, T* u, const T* rhs, in
 template <typename T> void p_rbgs(const Dims&, int color, T* u, const T* rhs, cudaStream_t, int block = 256);
 template <typename T> void p_prolong(const Dims&, const Dims&, int3, const T*, T*, cudaStream_t);
 template <typename T> void p_coarse(const Dims&, T* u, T* rhs, int sweeps, cudaStream_t);
-template <typename T> void div_q(const Dims&, T eta, const T* vt, const T* rpi, T* q, T* pi, cudaStream_t);
-template <typename T> void add_grad(const Dims&, const T* phi, T* v, cudaStream_t);
+// pi64 / v64: FP64 copies of the outputs (null: none)
+template <typename T> void div_q(const Dims&, T eta, const T* vt, const T* rpi, T* q, T* pi, double* pi64,
+                                 cudaStream_t);
+template <typename T> void add_grad(const Dims&, const T* phi, T* v, double* v64, cudaStream_t);
 
 // Exact solve on a coarse multigrid level by fast diagonalisation (k_fdsolve.cu).
 // The level operator of each grid (a velocity component of -eta LL, or the
@@ -119,8 +121,9 @@ template <typename T> void spread(const Dims&, int nbl, const int* perm, const d
 template <typename T> void interp(const Dims&, const Walls&, int nbl, const double* r, const T* v, double alpha,
                                   double beta, double gamma, T* out, cudaStream_t);
 template <typename T> void interp_res(const Dims&, const BodyView&, const T* v, const T* rl, T* out, cudaStream_t);
+// zlam64 / zU64: FP64 copies of the outputs (null: none)
 template <typename T> void body_precond(const BodyView&, const PrecondView&, const T* sres, const T* rU,
-                                        T* zlam, T* zU, cudaStream_t);
+                                        T* zlam, T* zU, double* zlam64, double* zU64, cudaStream_t);
 void stencil_build(const Dims&, int nbl, const double* r, BlobStencil<double>* s64, BlobStencil<float>* s32,
                    cudaStream_t);
 void interp_tab(const Dims&, const BodyView&, const double* v, double alpha, double beta, double* out, cudaStream_t);
@@ -153,9 +156,14 @@ void dense_body_gj(int nbl, float* Minv, const float* Mw, int* status, cudaStrea
 void dense_body_finish(int nbl, int nb, const int* boff, const double* arm, const float* Minv, float* P, double* N,
                        int* status, cudaStream_t);
 void ns_decide(const double* ss, cudaGraphConditionalHandle h, long long* warm, cudaStream_t);
+// With tab (the configuration's stencil table of type T), the kernel forms
+// its input s = rl + J v itself and stores it in sres_out; sres is unused.
 template <typename T> void dense_body_apply(int nbl, int nb, const int* boff, const int* bob, const double* arm,
                                             const float* Minv, const float* P, const double* N, const T* sres,
-                                            const T* rU, T* zlam, T* zU, cudaStream_t);
+                                            const T* rU, T* zlam, T* zU, double* zlam64, double* zU64,
+                                            cudaStream_t, const Dims* d = nullptr,
+                                            const BlobStencil<T>* tab = nullptr, const T* v = nullptr,
+                                            const T* rl = nullptr, T* sres_out = nullptr);
 
 // k_krylov.cu
 // A grid's partial-sum buffer: nparts x kPartCols doubles, 8 spare doubles,
@@ -212,11 +220,10 @@ void project_mean(double* x, i64 n, double* part, int nparts, cudaStream_t);
 // FGMRES restart cycle as a graph (k_krylov.cu)
 template <typename T> void fg_start(T* V0, const T* w, i64 n, double* gvec, int m, int* ist, const double* dpar,
                                     cudaStream_t, float* V0_32 = nullptr);
-void set_condition(cudaGraphConditionalHandle h, const int* ist, cudaStream_t);
 template <typename T>
 void scale_givens(T* out, const T* in, i64 n, float* out32, double* H, int ldh, double* cs, double* sn, double* g,
                   int j, const double* hcol, const double* hcol2, const double* nrm2, double* res_out, int* ist,
-                  const double* dpar, cudaStream_t s);
+                  const double* dpar, cudaStream_t s, const cudaGraphConditionalHandle* next = nullptr);
 void tri_solve_dev(const double* H, int ldh, const double* g, const int* ist, double* y, cudaStream_t);
 // control of device-driven solves (k_krylov.cu)
 void solve_init(double* dpar, int* ist, double rtol, int maxit, const double* rtol_p, const int* maxit_p,

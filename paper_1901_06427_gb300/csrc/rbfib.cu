@@ -468,8 +468,10 @@ template <> float* sres_of<float>(rbfib_grid* g) { return g->sres32; }
 // Body block: Schur complement [-M K; K^T 0] with M replaced per body by the
 // free-space RPY blob mobility of its shape, right-hand side
 // (r_lam + J v, r_U).
+// z64 (optional): the result is also written in FP64 there by the kernels
+// that produce each block, which saves a conversion launch.
 template <typename T>
-void precond(rbfib_grid* g, const T* r, T* z, bool with_bodies) {
+void precond(rbfib_grid* g, const T* r, T* z, bool with_bodies, double* z64 = nullptr) {
   const Dims& d = g->d;
   T* zv = z;
   T* zp = z + g->nf;
@@ -477,34 +479,40 @@ void precond(rbfib_grid* g, const T* r, T* z, bool with_bodies) {
   vcycle_vel<T>(g, zv, r);
   T* q = *M.prhs[0];
   T* phi = *M.pu[0];
-  div_q<T>(d, (T)g->desc.eta, zv, r + g->nf, q, zp, g->s);
+  div_q<T>(d, (T)g->desc.eta, zv, r + g->nf, q, zp, z64 ? z64 + g->nf : nullptr, g->s);
   vcycle_p<T>(g, phi, q);
-  add_grad<T>(d, phi, zv, g->s);
+  add_grad<T>(d, phi, zv, z64, g->s);
   if (with_bodies && g->nb > 0) {
     const T* rl = r + g->nfl;
     const T* rU = rl + 3 * (i64)g->nbl;
     T* zl = z + g->nfl;
     T* zU = zl + 3 * (i64)g->nbl;
     T* sres = sres_of<T>(g);
-    interp_res<T>(d, view_of(g, g->cur), zv, rl, sres, g->s);
-    if (g->dense_body)
-      dense_body_apply<T>(g->nbl, g->nb, g->boff, g->bob, g->cur.arm, g->dM, g->dP, g->dN, sres, rU, zl, zU, g->s);
-    else
-      body_precond<T>(view_of(g, g->cur), pview(g), sres, rU, zl, zU, g->s);
+    double* zl64 = z64 ? z64 + g->nfl : nullptr;
+    double* zU64 = z64 ? zl64 + 3 * (i64)g->nbl : nullptr;
+    if (g->dense_body) {
+      const BodyView bv = view_of(g, g->cur);
+      const BlobStencil<T>* tab = nullptr;
+      if constexpr (sizeof(T) == 8) tab = (const BlobStencil<T>*)bv.st64; else tab = (const BlobStencil<T>*)bv.st32;
+      dense_body_apply<T>(g->nbl, g->nb, g->boff, g->bob, g->cur.arm, g->dM, g->dP, g->dN, nullptr, rU, zl, zU, zl64,
+                          zU64, g->s, &d, tab, zv, rl, sres);
+    } else {
+      interp_res<T>(d, view_of(g, g->cur), zv, rl, sres, g->s);
+      body_precond<T>(view_of(g, g->cur), pview(g), sres, rU, zl, zU, zl64, zU64, g->s);
+    }
   }
 }
 
 // The preconditioner always runs in FP32: it only has to approximate A^{-1}
 // (FGMRES is flexible), and FP32 halves the bytes of every multigrid sweep and
-// avoids GB300's narrow FP64 pipe.  FP64 vectors are converted on the way in
-// and out.  r32_ready: the Krylov basis kernels already wrote r rounded to
+// avoids GB300's narrow FP64 pipe.  FP64 vectors are converted on the way in;
+// on the way out the kernels that finish each block write it in FP64 too.  r32_ready: the Krylov basis kernels already wrote r rounded to
 // FP32 into f32a (normalising a new basis vector writes both copies, which
 // saves a conversion launch).
 void precond_any(rbfib_grid* g, const double* r, double* z, bool with_bodies, bool r32_ready = false) {
   const i64 n = with_bodies ? g->n_total() : g->nfl;
   if (!r32_ready) convert<double, float>(r, g->f32a, n, g->s);
-  precond<float>(g, g->f32a, g->f32b, with_bodies);
-  convert<float, double>(g->f32b, z, n, g->s);
+  precond<float>(g, g->f32a, g->f32b, with_bodies, z);
 }
 void precond_any(rbfib_grid* g, const float* r, float* z, bool with_bodies, bool = false) {
   precond<float>(g, r, z, with_bodies);
@@ -712,7 +720,7 @@ void cond_node(rbfib_grid* g, cudaGraphConditionalHandle h, cudaGraphConditional
 // second Gram-Schmidt pass sits in a nested IF node whose condition the
 // first pass's multi-axpy sets (ReorthCtl).
 template <typename T>
-void capture_iteration(rbfib_grid* g, int j, bool wb) {
+void capture_iteration(rbfib_grid* g, int j, bool wb, const cudaGraphConditionalHandle* next) {
   KrylovStore<T>& K = kr_of<T>(g);
   const int m = K.m;
   const i64 n = wb ? g->n_total() : g->nfl, ld = K.n, nfl = g->nfl;
@@ -732,15 +740,15 @@ void capture_iteration(rbfib_grid* g, int j, bool wb) {
     multi_axpy<T>(w, V, ld, j + 1, sp.hcol2, -1.0, n, nfl, wf, g->part, g->nparts, sp.nrm2, g->s);
   });
   scale_givens<T>(V + (i64)(j + 1) * ld, w, n, basis32<T>(g), sp.H, m + 1, sp.cs, sp.sn, sp.gv, j, sp.hcol,
-                  sp.hcol2, sp.nrm2, sp.res, g->gst, g->dpar, g->s);
+                  sp.hcol2, sp.nrm2, sp.res, g->gst, g->dpar, g->s, next);
 }
 
 // One restart cycle of FGMRES(m), captured on g->s: the cycle start, then m
-// Arnoldi iterations, iteration j inside an IF node whose condition a small
-// kernel sets from the device continue-flag written by iteration j-1's
-// Givens update (so at most m iterations run, whatever the flags), then the
-// solution update and the true residual w = b - A x with its norm in
-// dpar[2].  per_iter (if not null) receives the launches of one iteration
+// Arnoldi iterations, iteration j inside an IF node whose condition
+// iteration j-1's Givens update sets from its continue decision (the
+// handles default to 0 at every launch, so an iteration runs only if the one
+// before it ran and chose to continue), then the solution update and the
+// true residual w = b - A x with its norm in dpar[2].  per_iter (if not null) receives the launches of one iteration
 // with its gated second pass (two launches).
 template <typename T>
 void capture_cycle(rbfib_grid* g, const T* b, T* x, bool wb, long long* per_iter) {
@@ -750,11 +758,12 @@ void capture_cycle(rbfib_grid* g, const T* b, T* x, bool wb, long long* per_iter
   const double wf = g->dV;
   SmallPtrs sp = small_ptrs(g, m);
   fg_start<T>(K.V, K.w, n, sp.gv, m, g->gst, g->dpar, g->s, basis32<T>(g));
+  std::vector<cudaGraphConditionalHandle> hs(m);
+  for (int j = 0; j < m; ++j) hs[j] = new_handle(g, j == 0 ? 1u : 0u);
   for (int j = 0; j < m; ++j) {
-    const cudaGraphConditionalHandle h = new_handle(g, j == 0 ? 1u : 0u);
-    if (j > 0) set_condition(h, g->gst, g->s);
     const long long a0 = rbfib::g_launches.load();
-    cond_node(g, h, cudaGraphCondTypeIf, 1, [&](int) { capture_iteration<T>(g, j, wb); });
+    cond_node(g, hs[j], cudaGraphCondTypeIf, 1,
+              [&](int) { capture_iteration<T>(g, j, wb, j + 1 < m ? &hs[j + 1] : nullptr); });
     if (j == 0 && per_iter) *per_iter = (long long)rbfib::g_launches.load() - a0;
   }
   tri_solve_dev(sp.H, m + 1, sp.gv, g->gst, sp.y, g->s);
