@@ -771,7 +771,8 @@ namespace rbfib {
 
 template <typename T>
 __global__ void k_fg_start(T* __restrict__ V0, const T* __restrict__ w, i64 n, double* __restrict__ gvec, int m,
-                           int* __restrict__ ist, const double* __restrict__ dpar, float* __restrict__ V0_32) {
+                           int* __restrict__ ist, const double* __restrict__ dpar, float* __restrict__ V0_32,
+                           IterConds conds) {
   pdl_entry();
   __shared__ double bs, fs;   // one thread per block forms beta and 1 / beta
   if (threadIdx.x == 0) {
@@ -791,13 +792,17 @@ __global__ void k_fg_start(T* __restrict__ V0, const T* __restrict__ w, i64 n, d
     ist[0] = 0;
     ist[2] = 1;
   }
+  if (blockIdx.x == 0 && (int)threadIdx.x < conds.n)
+    cudaGraphSetConditional(conds.h[threadIdx.x], threadIdx.x == 0 ? 1u : 0u);
 }
 
 template <typename T>
 void fg_start(T* V0, const T* w, i64 n, double* gvec, int m, int* ist, const double* dpar, cudaStream_t s,
-              float* V0_32) {
+              float* V0_32, const IterConds* conds) {
   const unsigned nb = (unsigned)std::min<i64>(nblk(n, 256), 152 * 8);
-  launch_k(k_fg_start<T>, nb, 256, 0, s, V0, w, n, gvec, m, ist, dpar, V0_32);
+  IterConds c{};
+  if (conds) c = *conds;
+  launch_k(k_fg_start<T>, nb, 256, 0, s, V0, w, n, gvec, m, ist, dpar, V0_32, c);
   note_launch();
 }
 
@@ -915,8 +920,9 @@ void multi_axpy_dev(T* w, const T* V, i64 ldv, const int* ist, const double* coe
 }
 
 template void fg_start<double>(double*, const double*, i64, double*, int, int*, const double*, cudaStream_t,
-                               float*);
-template void fg_start<float>(float*, const float*, i64, double*, int, int*, const double*, cudaStream_t, float*);
+                               float*, const IterConds*);
+template void fg_start<float>(float*, const float*, i64, double*, int, int*, const double*, cudaStream_t, float*,
+                              const IterConds*);
 template void multi_axpy_dev<double>(double*, const double*, i64, const int*, const double*, double, i64, int,
                                      cudaStream_t);
 template void multi_axpy_dev<float>(float*, const float*, i64, const int*, const double*, double, i64, int,

@@ -217,9 +217,18 @@ template <typename T> void axpby(T* y, const T* x, double a, double b, i64 n, cu
 template <typename T> void wall_rhs(const Dims&, const Walls&, double eta, T* bv, cudaStream_t);
 void project_mean(double* x, i64 n, double* part, int nparts, cudaStream_t);
 
-// FGMRES restart cycle as a graph (k_krylov.cu)
+// FGMRES restart cycle as a graph (k_krylov.cu).  The IF conditions of a
+// cycle's iterations: iteration j's Givens update sets the condition of
+// iteration j + 1; the cycle start resets them all (condition 0 to 1, the
+// rest to 0), since a cycle that runs again inside a WHILE body keeps the
+// values of its previous pass.
+constexpr int kMaxRestart = 64;
+struct IterConds {
+  cudaGraphConditionalHandle h[kMaxRestart];
+  int n;
+};
 template <typename T> void fg_start(T* V0, const T* w, i64 n, double* gvec, int m, int* ist, const double* dpar,
-                                    cudaStream_t, float* V0_32 = nullptr);
+                                    cudaStream_t, float* V0_32 = nullptr, const IterConds* conds = nullptr);
 template <typename T>
 void scale_givens(T* out, const T* in, i64 n, float* out32, double* H, int ldh, double* cs, double* sn, double* g,
                   int j, const double* hcol, const double* hcol2, const double* nrm2, double* res_out, int* ist,

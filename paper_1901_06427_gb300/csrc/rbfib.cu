@@ -757,9 +757,11 @@ void capture_cycle(rbfib_grid* g, const T* b, T* x, bool wb, long long* per_iter
   const i64 n = wb ? g->n_total() : g->nfl, ld = K.n, nfl = g->nfl;
   const double wf = g->dV;
   SmallPtrs sp = small_ptrs(g, m);
-  fg_start<T>(K.V, K.w, n, sp.gv, m, g->gst, g->dpar, g->s, basis32<T>(g));
-  std::vector<cudaGraphConditionalHandle> hs(m);
-  for (int j = 0; j < m; ++j) hs[j] = new_handle(g, j == 0 ? 1u : 0u);
+  IterConds conds{};
+  conds.n = m;
+  for (int j = 0; j < m; ++j) conds.h[j] = new_handle(g, j == 0 ? 1u : 0u);
+  const cudaGraphConditionalHandle* hs = conds.h;
+  fg_start<T>(K.V, K.w, n, sp.gv, m, g->gst, g->dpar, g->s, basis32<T>(g), &conds);
   for (int j = 0; j < m; ++j) {
     const long long a0 = rbfib::g_launches.load();
     cond_node(g, hs[j], cudaGraphCondTypeIf, 1,
