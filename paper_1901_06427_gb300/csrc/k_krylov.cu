@@ -237,7 +237,9 @@ __global__ void __launch_bounds__(256) k_gs_dot(const T* __restrict__ w, const T
   const i64 nv = n / W;
   const i64 chunk = 256 * (i64)R;
   const i64 nchunks = (nv + chunk - 1) / chunk;
-  const int c0 = blockIdx.y * kCG;
+  // columns split evenly over the groups (gridDim.y): at most kCG each
+  const int cpg = (k + gridDim.y - 1) / gridDim.y;
+  const int c0 = blockIdx.y * cpg, c1 = min(k, c0 + cpg);
   const VT* w4 = reinterpret_cast<const VT*>(w);
   A acc[kCG];
 #pragma unroll
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(256) k_gs_dot(const T* __restrict__ w, const T
     }
 #pragma unroll
     for (int c = 0; c < kCG; ++c) {
-      if (c0 + c < k) {
+      if (c0 + c < c1) {
         const VT* v4 = reinterpret_cast<const VT*>(V + (i64)(c0 + c) * ldv);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -268,12 +270,12 @@ __global__ void __launch_bounds__(256) k_gs_dot(const T* __restrict__ w, const T
       const A x = (A)w[i];
 #pragma unroll
       for (int c = 0; c < kCG; ++c)
-        if (c0 + c < k) acc[c] += x * (A)V[(i64)(c0 + c) * ldv + i];
+        if (c0 + c < c1) acc[c] += x * (A)V[(i64)(c0 + c) * ldv + i];
     }
   }
   const double s = block_transpose_sum8<A>(acc);
   __shared__ bool last;
-  if (threadIdx.x < kCG && c0 + (int)threadIdx.x < k) {
+  if (threadIdx.x < kCG && c0 + (int)threadIdx.x < c1) {
     part[(i64)(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
     __threadfence();
   }
