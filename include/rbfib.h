@@ -42,7 +42,8 @@ enum {
   RBFIB_ENOCONV = -2,    /* Krylov solve hit max_iter above the tolerance    */
   RBFIB_ENAN = -3,       /* non-finite residual                              */
   RBFIB_EREJECT = -4,    /* SEM step produced an unphysical configuration    */
-  RBFIB_ETIMEOUT = -5,   /* a bounded device-side wait gave up               */
+  RBFIB_ETIMEOUT = -5,   /* reserved: no call of this library returns it (no */
+                         /* kernel waits on a flag or a peer)                */
   RBFIB_ECUDA = -6,      /* a CUDA runtime call failed                       */
   RBFIB_EINTERNAL = -7   /* internal inconsistency (device error word set)   */
 };

@@ -5,7 +5,8 @@ wall-edge weights, the saddle matvec in FP64 and FP32 per block (column and
 pipelined stencils), the preconditioner's fluid block with exact inner solves
 (the fast-diagonalisation bases DCT-II / DST-IV / DCT-IV), the Stokes and
 mobility solves in FP64 and FP32-refined (also through the multigrid
-V-cycles), and one SEM step (Algorithm 1), element by element."""
+V-cycles), one SEM step (Algorithm 1) and the adjoint of the mobility solve,
+element by element."""
 import numpy as np
 import pytest
 
@@ -171,6 +172,25 @@ def test_sem_step_free_slip(B, name):
     assert_close(q.cpu().numpy().reshape(-1, 3) - w.q, ref["q"] - w.q, SEM_STEP, "SEM displacement")
     assert_close(quat.cpu().numpy() - w.quat.ravel(), ref["quat"].ravel() - w.quat.ravel(), SEM_STEP,
                  "SEM orientation increment")
+
+
+def test_adjoint_free_slip(B):
+    """Gradient of sum |U|^2 with respect to blob positions and slip next to
+    free-slip walls (the even mirror in the kernel derivative) against the
+    oracle's adjoint."""
+    from oracle import adjoint
+    w = workloads.small_case(n=(12, 10, 9), n_bodies=2, blobs=12, radius=1.0, seed=9, near_wall=True,
+                             free_slip=(T, F, F, T, T, F))
+    og = oracle.Grid(w.n, free_slip=w.free_slip)
+    ob = saddle.Bodies(w.ref_blobs, w.blob_offsets, w.q, w.quat)
+    x0, U0 = adjoint.forward(og, ob, w.eta, w.slip.ravel(), w.force_torque)
+    dr0, ds0 = adjoint.gradient(og, ob, w.eta, x0, 2.0 * U0)
+    g = B.grid_for(w, rtol=1e-12)
+    U, info, x = g.mobility_solve(dev(w.force_torque), slip=dev(w.slip), return_x=True)
+    assert_close(U.cpu().numpy(), U0, SOLVED, "U")
+    dr, ds, ainfo = g.mobility_solve_adjoint(2.0 * U, x)
+    assert_close(dr.cpu().numpy(), dr0.ravel(), (1e-7, 1e-8), "dL/dr")
+    assert_close(ds.cpu().numpy(), ds0, (1e-7, 1e-8), "dL/dslip")
 
 
 def test_free_slip_descriptor_errors(B):
