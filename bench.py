@@ -65,6 +65,7 @@ def parse():
                     help="run only the two-sphere MSD experiment of Sec. V.A (12- and 42-blob spheres)")
     ap.add_argument("--msd-replicas", type=int, default=64)
     ap.add_argument("--msd-steps", type=int, default=1200)
+    ap.add_argument("--msd-blobs", type=int, nargs="+", default=[12, 42], choices=[12, 42, 162])
     ap.add_argument("--boomerang", action="store_true",
                     help="run only the boomerang equilibrium experiment of App. A")
     ap.add_argument("--boomerang-replicas", type=int, default=64)
@@ -683,7 +684,7 @@ def run_ours(args):
     if args.msd:
         if rank == 0:
             print(json.dumps({"msd": {str(b): run_msd(B, torch, b, args.msd_replicas, args.msd_steps)
-                                      for b in (12, 42)}}), flush=True)
+                                      for b in args.msd_blobs}}), flush=True)
         return
     if args.boomerang:
         if rank == 0:

@@ -8,7 +8,7 @@ Every number here comes from oracle/ only (never from the CUDA path):
   two_sphere_step0.json  one Split-Euler-Maruyama step (Algorithm 1) of the
                          two-sphere 48x48x32 workload, seed = workload seed,
                          step 0, attempt 0;
-  gb_two_sphere_msd_{12,42}.json
+  gb_two_sphere_msd_{12,42,162}.json
                          Gibbs-Boltzmann samples (oracle.mcmc) of the tight
                          cavity of Sec. V.A: the covariance of the sphere
                          centres (the long-time MSD limit of Eq. asymRef is
@@ -107,6 +107,7 @@ def gb_boomerang():
 
 FILES = {"single_sphere_32.json": single_sphere, "two_sphere_step0.json": two_sphere_step,
          "gb_two_sphere_msd_12.json": lambda: gb_two_sphere(12), "gb_two_sphere_msd_42.json": lambda: gb_two_sphere(42),
+         "gb_two_sphere_msd_162.json": lambda: gb_two_sphere(162),
          "gb_boomerang.json": gb_boomerang}
 
 if __name__ == "__main__":

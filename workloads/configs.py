@@ -273,16 +273,16 @@ BLOB_RADIUS_6PT = 1.47
 def two_sphere_msd(blobs=12):
     """The tight cavity of Sec. V.A: two neutrally buoyant spheres of
     hydrodynamic radius R_h = 0.656 um in a 3.478 x 1.739 x 1.739 um no-slip
-    box, discretised with the six-point kernel at h = 0.0543 (4, 2) um for
-    12- and 42-blob spheres: 16 x 8 x 8 or 32 x 16 x 16 cells, R_h = 3.02h or
-    6.04h.  The geometric radius is R_h - a, a = 1.47h the blob radius (our
+    box, discretised with the six-point kernel at h = 0.0543 (4, 2, 1) um for
+    12-, 42- and 162-blob spheres: 16 x 8 x 8, 32 x 16 x 16 or 64 x 32 x 32
+    cells, R_h = 3.02h, 6.04h or 12.08h.  The geometric radius is R_h - a, a = 1.47h the blob radius (our
     reading; the paper takes it from a table of the cited multiblob work).
     Soft pair (d = 2 R_h) and wall (d = R_h) repulsion of Eq. (Usoft) with
     b = 0.1 R_h, Phi0 = 4 kT; kT = eta = 1; dt from the dimensionless step
     dtau = kT dt / (6 pi eta R_h^3) = 0.0044.  The spheres start side by side
     along x at mid-height (equilibrium starts come from Gibbs-Boltzmann
     samples)."""
-    scale = {12: 1, 42: 2}[blobs]
+    scale = {12: 1, 42: 2, 162: 4}[blobs]
     n = (16 * scale, 8 * scale, 8 * scale)
     Rh = 0.656 / (0.0543 * 4 / scale)
     Rg = Rh - BLOB_RADIUS_6PT
