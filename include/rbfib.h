@@ -128,7 +128,9 @@ const char* rbfib_last_error(const rbfib_grid* g);   /* g may be NULL */
  * blob offsets in the body frame; q (device, N_b x 3) tracking points; quat
  * (device, N_b x 4) unit quaternions (w,x,y,z).  Blob positions are
  * r_i = q_p + R(quat_p) ref_i.  Builds the blob-to-cell binning and the
- * body-block preconditioner.  Synchronises the stream. */
+ * body-block preconditioner.  Synchronises the stream.  EINVAL: a body with
+ * no blob, or whose blobs lie on one line (its rotation about that line
+ * would be undetermined: fewer than three non-collinear blobs). */
 int rbfib_set_bodies(rbfib_grid* g, int32_t n_bodies, const int32_t* blob_offsets,
                      const double* ref_blobs, const double* q, const double* quat);
 

@@ -1414,6 +1414,31 @@ int rbfib_set_bodies(rbfib_grid* g, int32_t n_bodies, const int32_t* blob_offset
     for (int p = 0; p < n_bodies; ++p)
       if (off[p + 1] <= off[p]) return fail(g, RBFIB_EINVAL, "set_bodies: every body needs at least one blob");
   }
+  if (n_bodies > 0) {
+    // a rigid body needs three blobs off one line: with collinear blobs the
+    // rotation about their line is undetermined and the system is singular
+    std::vector<double> ref(3 * (size_t)off[n_bodies]);
+    if (cudaMemcpy(ref.data(), ref_blobs, sizeof(double) * ref.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(g, RBFIB_ECUDA, "set_bodies: cannot read ref_blobs");
+    for (int p = 0; p < n_bodies; ++p) {
+      const double* r0 = &ref[3 * (size_t)off[p]];
+      double u[3] = {0, 0, 0}, un = 0.0;
+      for (int i = off[p] + 1; i < off[p + 1]; ++i) {
+        const double* r = &ref[3 * (size_t)i];
+        const double d2 = (r[0] - r0[0]) * (r[0] - r0[0]) + (r[1] - r0[1]) * (r[1] - r0[1]) +
+                          (r[2] - r0[2]) * (r[2] - r0[2]);
+        if (d2 > un) { un = d2; for (int a = 0; a < 3; ++a) u[a] = r[a] - r0[a]; }
+      }
+      double worst = 0.0;
+      for (int i = off[p] + 1; i < off[p + 1] && un > 0.0; ++i) {
+        const double* r = &ref[3 * (size_t)i];
+        const double dv[3] = {r[0] - r0[0], r[1] - r0[1], r[2] - r0[2]};
+        const double cx = dv[1] * u[2] - dv[2] * u[1], cy = dv[2] * u[0] - dv[0] * u[2], cz = dv[0] * u[1] - dv[1] * u[0];
+        worst = std::max(worst, std::sqrt(cx * cx + cy * cy + cz * cz) / un);
+      }
+      if (!(worst > 1e-9)) return fail(g, RBFIB_EINVAL, "set_bodies: a body's blobs lie on one line");
+    }
+  }
   try {
     ck(cudaStreamSynchronize(g->s));
     drop_graphs(g);
