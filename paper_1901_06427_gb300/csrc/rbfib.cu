@@ -1418,7 +1418,8 @@ int rbfib_set_bodies(rbfib_grid* g, int32_t n_bodies, const int32_t* blob_offset
     // a rigid body needs three blobs off one line: with collinear blobs the
     // rotation about their line is undetermined and the system is singular
     std::vector<double> ref(3 * (size_t)off[n_bodies]);
-    if (cudaMemcpy(ref.data(), ref_blobs, sizeof(double) * ref.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (cudaStreamSynchronize(g->s) != cudaSuccess ||
+        cudaMemcpy(ref.data(), ref_blobs, sizeof(double) * ref.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
       return fail(g, RBFIB_ECUDA, "set_bodies: cannot read ref_blobs");
     for (int p = 0; p < n_bodies; ++p) {
       const double* r0 = &ref[3 * (size_t)off[p]];
