@@ -103,8 +103,10 @@ def whole_job_rate(world, steps, max_ms):
 def workload_config(w):
     return {"workload": w.name, "grid": list(w.n), "bodies": w.n_bodies, "blobs_per_body": 42,
             "kernel": "3-point Peskin", "dt": w.dt, "kT": w.kT, "rtol": 1e-8, "precision": "fp64",
-            "krylov": "FGMRES(48), CGS2; preconditioner: projection with multigrid V(2,2) velocity and "
-                      "pressure cycles, exact coarse-level solves, dense RPY body block",
+            "krylov": "FGMRES(48), classical Gram-Schmidt with selective re-orthogonalisation; "
+                      "preconditioner: projection with exact fast-diagonalisation solves of the finest "
+                      "level (multigrid V(2,2) cycles on grids above 48 points per axis), coupled RPY body "
+                      "block",
             "l2": "flushed (512 MiB write) between timed steps", "data": "synthetic, seeded"}
 
 
