@@ -230,7 +230,10 @@ def run_reference(args):
 # ------------------------------------------------------ matvec at HBM size
 def run_matvec_large(B, torch, hbm, n=256, reps=20):
     """Saddle matvec (Stokes stencil + body rows + spreading) on an n^3 box
-    whose vectors exceed L2: achieved algorithmic GB/s per precision."""
+    whose vectors exceed L2: achieved algorithmic GB/s per precision, and the
+    algorithmic operations (10 per momentum row, 6 per divergence row, about
+    400 per blob) against the arithmetic peak of the precision (FP64: 152 SMs
+    x 2 FMA per clock x 2 x maximum SM clock; FP32: 128 lanes per SM)."""
     import workloads
     w = workloads.matvec_box(n)
     g = B.grid_for(w, restart=2, max_iter=4)
@@ -249,8 +252,13 @@ def run_matvec_large(B, torch, hbm, n=256, reps=20):
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / reps / 1000.0
         alg = 2.0 * ntot * s + 24.0 * w.n_blobs + 56.0 * w.n_bodies
+        lay = g.layout()
+        nf, nc = lay[3], lay[4] - lay[3]
+        ops = 10.0 * nf + 6.0 * nc + 400.0 * w.n_blobs
+        peak = alu_peak_gflops("fp64" if s == 8 else "fp32", 152)
         out[label] = {"ms": 1000.0 * t, "achieved_gbs": alg / t / 1e9, "frac_of_measured_hbm": alg / t / 1e9 / hbm,
-                      "alg_bytes": alg}
+                      "alg_bytes": alg, "alg_ops": ops, "achieved_gflops": ops / t / 1e9,
+                      "frac_of_alu_peak": ops / t / 1e9 / peak, "alu_peak_gflops": peak}
         del x, y
     g.close()
     torch.cuda.empty_cache()
@@ -280,6 +288,16 @@ CLASS_INFO = {
 TRAFFIC_RATIO = {"dot": 0.97, "axpy": 0.94, "gram_schmidt": 0.955}
 
 
+def alu_peak_gflops(arith, sms):
+    """Arithmetic peak (GFLOP/s) of sms SMs at the maximum SM clock: FP64 2
+    FMA lanes per SM, FP32 128."""
+    try:
+        mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", 2070.0)
+    except Exception:
+        mhz = 2070.0
+    return sms * (2 if arith == "fp64" else 128) * 2 * mhz * 1e6 / 1e9
+
+
 def roofline_for(top, kms, klaunch, kbytes, kflops):
     """Binding roof of the dominant class: achieved algorithmic bytes/s
     against the measured HBM copy rate, and achieved operations/s against the
@@ -295,7 +313,7 @@ def roofline_for(top, kms, klaunch, kbytes, kflops):
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     name, arith, sms = CLASS_INFO[top]
     lanes = 2 if arith == "fp64" else 128
-    alu_peak = sms * lanes * 2 * sm_mhz * 1e6 / 1e9   # GFLOP/s
+    alu_peak = alu_peak_gflops(arith, sms)
     avg_s = (kms / max(klaunch, 1)) * 1e-3
     bw = (kbytes / klaunch) / avg_s / 1e9 if klaunch else 0.0
     fl = (kflops / klaunch) / avg_s / 1e9 if klaunch else 0.0
