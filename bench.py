@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--msd-replicas", type=int, default=64)
     ap.add_argument("--msd-steps", type=int, default=1200)
     ap.add_argument("--msd-blobs", type=int, nargs="+", default=[12, 42], choices=[12, 42, 162])
+    ap.add_argument("--monolayer-step", action="store_true",
+                    help="run one FP32-refined SEM step of the driven monolayer and exit (a profiling case for "
+                         "the multigrid, per-shape body block and cluster coarse-solve kernels)")
     ap.add_argument("--boomerang", action="store_true",
                     help="run only the boomerang equilibrium experiment of App. A")
     ap.add_argument("--boomerang-replicas", type=int, default=64)
@@ -696,6 +699,17 @@ def run_ours(args):
     if args.monolayer_only:
         if rank == 0:
             print(json.dumps({"monolayer": run_monolayer(B, torch)}), flush=True)
+        return
+    if args.monolayer_step:
+        if rank == 0:
+            w = workloads.driven_monolayer()
+            g = B.grid_for(w, precision=B.FP32_REFINED, rtol=1e-8)
+            q = torch.tensor(w.q.ravel(), device="cuda")
+            quat = torch.tensor(w.quat.ravel(), device="cuda")
+            st, info = g.sem_step(B.sem_params(w.potentials, dt=w.dt, kT=w.kT), w.seed, 0, 0, q, quat)
+            torch.cuda.synchronize()
+            print(json.dumps({"monolayer_step": {"status": st, "info": info, "step_mode": g.step_mode()}}),
+                  flush=True)
         return
     if args.ensemble_only:
         if rank == 0:
