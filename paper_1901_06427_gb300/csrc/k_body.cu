@@ -137,69 +137,93 @@ __global__ void k_ktp(int nbl, int nb, const int* __restrict__ boff, const doubl
 
 // Square FP32 products for the Newton-Schulz update of the inverse
 // (n x n, row-major): MODE 0 forms C = I - A B and adds sum(C_ij^2) to
-// *ss; MODE 1 forms C = D + A B.  32 x 32 output tiles, 256 threads (four
-// outputs each), A and B staged through shared memory in 32-wide k-slices;
-// entries past n are zero-filled.  n <= 1536: these products take
-// microseconds, so they stay on the FP32 pipe.
-constexpr int kNSTile = 32;
+// *ss; MODE 1 forms C = D + A B.  16 x 16 output tiles on 64 threads (a
+// 2 x 2 block of outputs each), so that even n = 252 spreads over 256 CTAs;
+// the A rows and B columns of a tile are staged through shared memory in
+// k-slices of up to kNSK (one slice for n <= kNSK, all of its loads in
+// flight at once), A transposed so that a thread reads its two rows and its
+// two columns of a k step as two 8-byte loads.  Entries past n are
+// zero-filled.  n <= 1536: these products take microseconds, so they stay
+// on the FP32 pipe.
+constexpr int kNSTile = 16, kNSK = 256, kNSPad = kNSTile + 2;
 template <int MODE>
-__global__ void __launch_bounds__(256) k_ns_gemm(int n, const float* __restrict__ A, const float* __restrict__ B,
-                                                 const float* __restrict__ D, float* __restrict__ C,
-                                                 double* __restrict__ ss) {
+__global__ void __launch_bounds__(64) k_ns_gemm(int n, const float* __restrict__ A, const float* __restrict__ B,
+                                                const float* __restrict__ D, float* __restrict__ C,
+                                                double* __restrict__ ss) {
   pdl_entry();
-  __shared__ float As[kNSTile][kNSTile + 1], Bs[kNSTile][kNSTile + 1];
-  __shared__ double red[8];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  __shared__ __align__(16) float As[kNSK][kNSPad];   // As[k][r] = A[r0 + r][k0 + k]
+  __shared__ __align__(16) float Bs[kNSK][kNSTile];  // Bs[k][c] = B[k0 + k][c0 + c]
+  __shared__ double red[2];
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
   const int r0 = blockIdx.y * kNSTile, c0 = blockIdx.x * kNSTile;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int k0 = 0; k0 < n; k0 += kNSTile) {
+  float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  for (int k0 = 0; k0 < n; k0 += kNSK) {
+    const int kc = min(kNSK, n - k0);
+    // Thread tid stages elements tid + 64 q (q < 64) of each slice, in two
+    // batches of 32 loads per matrix held in registers, so that the loads
+    // of a batch are in flight together.  A: consecutive threads along k
+    // (element (r, kk) = (q / 4, 64 (q % 4) + tid), coalesced rows of A);
+    // B: consecutive threads along the tile's columns ((kk, c) =
+    // (4 q + tid / 16, tid % 16)).
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int rr = ty + 8 * q;
-      const int ar = r0 + rr, ac = k0 + tx, br = k0 + rr, bc = c0 + tx;
-      As[rr][tx] = (ar < n && ac < n) ? A[(i64)ar * n + ac] : 0.f;
-      Bs[rr][tx] = (br < n && bc < n) ? B[(i64)br * n + bc] : 0.f;
+    for (int h = 0; h < 2; ++h) {
+      float ra[32], rb[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int qq = 32 * h + q;
+        const int r = qq >> 2, ka = 64 * (qq & 3) + tid;
+        const int kb = 4 * qq + (tid >> 4), c = tid & 15;
+        ra[q] = (ka < kc && r0 + r < n) ? A[(i64)(r0 + r) * n + k0 + ka] : 0.f;
+        rb[q] = (kb < kc && c0 + c < n) ? B[(i64)(k0 + kb) * n + c0 + c] : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int qq = 32 * h + q;
+        As[64 * (qq & 3) + tid][qq >> 2] = ra[q];
+        Bs[4 * qq + (tid >> 4)][tid & 15] = rb[q];
+      }
     }
     __syncthreads();
 #pragma unroll 8
-    for (int kk = 0; kk < kNSTile; ++kk) {
-      const float b = Bs[kk][tx];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fmaf(As[ty + 8 * q][kk], b, acc[q]);
+    for (int kk = 0; kk < kc; ++kk) {
+      const float2 a = *reinterpret_cast<const float2*>(&As[kk][2 * ty]);
+      const float2 b = *reinterpret_cast<const float2*>(&Bs[kk][2 * tx]);
+      acc[0][0] = fmaf(a.x, b.x, acc[0][0]);
+      acc[0][1] = fmaf(a.x, b.y, acc[0][1]);
+      acc[1][0] = fmaf(a.y, b.x, acc[1][0]);
+      acc[1][1] = fmaf(a.y, b.y, acc[1][1]);
     }
     __syncthreads();
   }
   double sq = 0.0;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int row = r0 + ty + 8 * q, col = c0 + tx;
-    if (row >= n || col >= n) continue;
-    const i64 o = (i64)row * n + col;
-    float v;
-    if (MODE == 0) {
-      v = (row == col ? 1.f : 0.f) - acc[q];
-      sq += (double)v * (double)v;
-    } else {
-      v = D[o] + acc[q];
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int row = r0 + 2 * ty + u, col = c0 + 2 * tx + q;
+      if (row >= n || col >= n) continue;
+      const i64 o = (i64)row * n + col;
+      float v;
+      if (MODE == 0) {
+        v = (row == col ? 1.f : 0.f) - acc[u][q];
+        sq += (double)v * (double)v;
+      } else {
+        v = D[o] + acc[u][q];
+      }
+      C[o] = v;
     }
-    C[o] = v;
-  }
   if (MODE == 0) {
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-    if (tx == 0) red[ty] = sq;
+    if ((tid & 31) == 0) red[tid >> 5] = sq;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < 8; ++w) t += red[w];
-      atomicAdd(ss, t);
-    }
+    if (tid == 0) atomicAdd(ss, red[0] + red[1]);
   }
 }
 
 template <int MODE>
 void ns_gemm(int n, const float* A, const float* B, const float* D, float* C, double* ss, cudaStream_t s) {
   const unsigned nt = (unsigned)((n + kNSTile - 1) / kNSTile);
-  launch_k(k_ns_gemm<MODE>, dim3(nt, nt), 256, 0, s, n, A, B, D, C, ss);
+  launch_k(k_ns_gemm<MODE>, dim3(nt, nt), 64, 0, s, n, A, B, D, C, ss);
   note_launch();
 }
 

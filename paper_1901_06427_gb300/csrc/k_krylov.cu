@@ -601,31 +601,91 @@ void scale_by(T* out, const T* in, const double* denom, int invert, i64 n, cudaS
   note_launch();
 }
 
-// Hessenberg column j: H[0..j] = hcol (CGS2 sum), H[j+1] = sqrt(hnext2); apply
+// Hessenberg column j: H[0..j] = hcol (CGS sum), H[j+1] = sqrt(hnext2); apply
 // the previous rotations, form rotation j, update g; res_out = |g[j+1]|.
-// Givens update of Hessenberg column j (64 threads): the column (CGS sums
-// hcol + hcol2, then ||w||), the previous rotations and g are staged in
-// shared memory by all threads; one thread applies the j previous rotations
-// with the carried entry in a register (FP64 latency is long on this GPU, so
-// the chain must not go through memory), forms rotation j and updates g; all
-// threads write the column back.  Returns |g[j+1]|; r_out = the new
-// diagonal entry (every thread).
+// Givens update of Hessenberg column j (64 threads or more): the column (CGS
+// sums hcol + hcol2, then ||w||), the previous rotations and g are staged in
+// shared memory by all threads.  Applying rotations 0..j-1 carries one entry
+// down the column: with x_0 = h_0, rotation i outputs h_i = c_i x_i +
+// s_i h_{i+1} and passes on x_{i+1} = -s_i x_i + c_i h_{i+1}, a first-order
+// linear recurrence.  FP64 latency is long on this GPU, so from j =
+// kGivensScanMin on (below, one thread runs the j dependent steps; measured
+// on GB300: 5.3 us at j = 0 and 0.17 us more per rotation, against a flat
+// 7.2 us for the scan) the first warp evaluates it as a scan of affine maps
+// x -> a x + b (a_i = -s_i, b_i = c_i h_{i+1}; composing f_b after f_a
+// gives (a_b a_a, a_b b_a + b_b)): each lane composes the maps of its
+// segment of E = ceil(j / 32) consecutive rotations, a five-step shuffle
+// scan composes the segments, and each lane then runs its segment from the
+// carry entering it.  |a_i| <= 1, so no partial product grows.  One thread
+// then forms rotation j and updates g; all threads write the column back.
+// Returns |g[j+1]|; r_out = the new diagonal entry (every thread).
 constexpr int kGivensMax = 128;
+constexpr int kGivensSeg = kGivensMax / 32;   // rotations per lane at most
+constexpr int kGivensScanMin = 16;            // j from which the scan is faster (GB300)
 RBFIB_DEVFN double givens_core(double* H, int ldh, double* cs, double* sn, double* g, int j, const double* hcol,
                                const double* hcol2, const double* hnext2, double& r_out) {
   __shared__ double h[kGivensMax + 2], c[kGivensMax], s[kGivensMax];
-  __shared__ double res, rdiag;
+  __shared__ double res, rdiag, carry_out;
   for (int i = threadIdx.x; i <= j; i += blockDim.x) h[i] = hcol[i] + (hcol2 ? hcol2[i] : 0.0);
   for (int i = threadIdx.x; i < j; i += blockDim.x) { c[i] = cs[i]; s[i] = sn[i]; }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double carry = h[0];
-    for (int i = 0; i < j; ++i) {
-      const double hi1 = h[i + 1];
-      h[i] = c[i] * carry + s[i] * hi1;
-      carry = -s[i] * carry + c[i] * hi1;
+  if (j < kGivensScanMin) {
+    // few rotations: one thread runs the recurrence (the scan's fixed cost
+    // of about a microsecond is larger than the chain here)
+    if (threadIdx.x == 0) {
+      double x = h[0];
+      for (int i = 0; i < j; ++i) {
+        const double hi1 = h[i + 1];
+        h[i] = c[i] * x + s[i] * hi1;
+        x = -s[i] * x + c[i] * hi1;
+      }
+      carry_out = x;
     }
-    const double a = carry, b = sqrt(fmax(hnext2[0], 0.0));
+  } else if (threadIdx.x < 32) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x;
+    const int E = (j + 31) >> 5;
+    const int i0 = min(lane * E, j), i1 = min(i0 + E, j);
+    // this lane's rotations and the entries below them, in registers (the
+    // entries are overwritten below)
+    double cr[kGivensSeg], sr[kGivensSeg], hn[kGivensSeg];
+    double A = 1.0, B = 0.0;   // composition of the segment's maps
+#pragma unroll
+    for (int e = 0; e < kGivensSeg; ++e) {
+      const int i = i0 + e;
+      cr[e] = 1.0; sr[e] = 0.0; hn[e] = 0.0;
+      if (i < i1) {
+        cr[e] = c[i]; sr[e] = s[i]; hn[e] = h[i + 1];
+        const double a = -sr[e], b = cr[e] * hn[e];
+        B = fma(a, B, b);
+        A = a * A;
+      }
+    }
+    const double h0 = h[0];
+    __syncwarp();
+    // inclusive scan over the lanes' segments (later segment after earlier)
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const double Ap = __shfl_up_sync(full, A, d), Bp = __shfl_up_sync(full, B, d);
+      if (lane >= d) { B = fma(A, Bp, B); A = A * Ap; }
+    }
+    // the carried entry entering this lane's segment
+    double Ae = __shfl_up_sync(full, A, 1), Be = __shfl_up_sync(full, B, 1);
+    if (lane == 0) { Ae = 1.0; Be = 0.0; }
+    double x = fma(Ae, h0, Be);
+#pragma unroll
+    for (int e = 0; e < kGivensSeg; ++e) {
+      const int i = i0 + e;
+      if (i < i1) {
+        h[i] = fma(cr[e], x, sr[e] * hn[e]);
+        x = fma(-sr[e], x, cr[e] * hn[e]);
+      }
+    }
+    if (j == 0 ? lane == 0 : (i0 < i1 && i1 == j)) carry_out = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double a = carry_out, b = sqrt(fmax(hnext2[0], 0.0));
     const double r = hypot(a, b);
     const double cj = r > 0 ? a / r : 1.0, sj = r > 0 ? b / r : 0.0;
     cs[j] = cj; sn[j] = sj;
