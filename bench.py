@@ -488,20 +488,27 @@ def run_variant(B, torch, w, steps, warmup):
 def run_ensemble(args, B, torch):
     """Batched ensemble: independent cuboids n ~ U{16, 20, ..., 48} with 1-16
     12-blob spheres, one SEM step of every system per batch step; FP32-refined
-    and plain FP64 at the same relative residual 1e-8."""
+    and plain FP64 at the same relative residual 1e-8, each on the worker
+    streams (one step graph per system) and in the one-graph form (every
+    system's step a branch of one graph, one launch per batch step)."""
     import workloads
     out = {}
     ws = workloads.batched_ensemble(args.ensemble)
-    for label, prec in (("fp32_refined", B.FP32_REFINED), ("fp64", B.FP64)):
+    for label, prec, one_graph in (("fp32_refined", B.FP32_REFINED, False), ("fp64", B.FP64, False),
+                                   ("fp32_refined_one_graph", B.FP32_REFINED, True),
+                                   ("fp64_one_graph", B.FP64, True)):
         t0 = time.perf_counter()
-        batch = B.Batch(ws, precision=prec, workers=args.workers)
+        batch = B.Batch(ws, precision=prec, workers=args.workers, one_graph=one_graph)
         setup = time.perf_counter() - t0
         q = [torch.tensor(w.q.ravel(), device="cuda") for w in ws]
         quat = [torch.tensor(w.quat.ravel(), device="cuda") for w in ws]
         params = [B.sem_params(w.potentials, dt=w.dt, kT=w.kT) for w in ws]
         seeds = [w.seed + 31 * i for i, w in enumerate(ws)]
-        batch.sem_step(params, seeds, 0, q, quat)            # warm-up
+        t0 = time.perf_counter()
+        batch.sem_step(params, seeds, 0, q, quat)            # warm-up (captures the graphs)
         torch.cuda.synchronize()
+        first_step = time.perf_counter() - t0
+        g0 = batch.graph_steps()
         t0 = time.perf_counter()
         iters = 0
         for k in range(args.ensemble_steps):
@@ -511,7 +518,10 @@ def run_ensemble(args, B, torch):
         dt = time.perf_counter() - t0
         out[label] = {"value": args.ensemble * args.ensemble_steps / dt, "unit": "systems*steps/s",
                       "ms_per_batch_step": 1000.0 * dt / args.ensemble_steps, "setup_s": setup,
+                      "first_step_s": first_step,
                       "krylov_iterations_per_system_step": iters / (args.ensemble * args.ensemble_steps)}
+        if one_graph:
+            out[label]["graph_launches_timed"] = batch.graph_steps() - g0
         batch.close()
         del q, quat
         torch.cuda.empty_cache()

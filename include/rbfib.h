@@ -237,6 +237,22 @@ int rbfib_batch_sem_step(rbfib_batch* b, const rbfib_sem_params* params, const u
                          const uint32_t* attempts, double* const* q, double* const* quat, rbfib_step_info* infos,
                          int32_t* status);
 
+/* One-graph form of rbfib_batch_sem_step (on = 1; 0, the default, restores
+ * the worker streams above).  Once every system's step can run device-driven
+ * (from its second step on: a coupled body block is first built on the
+ * host), all systems' steps are captured as parallel branches of one CUDA
+ * graph, each branch copying its system's seed / step / attempt from pinned
+ * host memory, running the step and copying its report back; a batch step is
+ * then one launch of that graph on a stream of the batch and one
+ * synchronisation.  The graph is captured again when any system's params or
+ * q / quat pointers change.  Steps that cannot use it (a system not ready,
+ * a failed capture) run on the worker streams as before.  Returns
+ * RBFIB_EINVAL for a NULL batch or on values other than 0 and 1.
+ * rbfib_batch_graph_steps counts the batch steps run as one graph launch
+ * (-1 for a NULL batch). */
+int rbfib_batch_set_one_graph(rbfib_batch* b, int32_t on);
+int64_t rbfib_batch_graph_steps(const rbfib_batch* b);
+
 /* Body block of the preconditioner: dense = 1 when it is the coupled
  * all-blob RPY block (at least two bodies, 3 N_bl <= 1536, 6 N_b <= 384),
  * else 0 (per-shape blocks).  The coupled block's inverse RPY matrix is

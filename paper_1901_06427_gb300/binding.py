@@ -95,6 +95,8 @@ def lib():
             "rbfib_create_batch": ([I32, ctypes.POINTER(GridDesc), I32, ctypes.POINTER(P)], I32),
             "rbfib_destroy_batch": ([P], None),
             "rbfib_batch_grid": ([P, I32], P),
+            "rbfib_batch_set_one_graph": ([P, I32], I32),
+            "rbfib_batch_graph_steps": ([P], I64),
             "rbfib_batch_sem_step": ([P, ctypes.POINTER(SemParams), ctypes.POINTER(U64), U64, ctypes.POINTER(U32),
                                       ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(StepInfo),
                                       ctypes.POINTER(ctypes.c_int32)], I32),
@@ -412,9 +414,11 @@ class Batch:
 
     The workers' streams overlap on the GPU only as far as the CUDA runtime
     gives them separate hardware queues: CUDA_DEVICE_MAX_CONNECTIONS (8 unless
-    set in the environment before the CUDA context is created; at most 32)."""
+    set in the environment before the CUDA context is created; at most 32).
+    one_graph: every system's step as a branch of one graph, launched once per
+    batch step (rbfib_batch_set_one_graph)."""
 
-    def __init__(self, workloads_, precision=None, workers=16, restart=30, max_iter=4000):
+    def __init__(self, workloads_, precision=None, workers=16, restart=30, max_iter=4000, one_graph=False):
         n = len(workloads_)
         descs = (GridDesc * n)()
         for i, w in enumerate(workloads_):
@@ -426,6 +430,10 @@ class Batch:
         if st != OK:
             raise RbfibError(st, "create_batch failed")
         self._h = h
+        if one_graph:
+            st = lib().rbfib_batch_set_one_graph(self._h, 1)
+            if st != OK:
+                raise RbfibError(st, "batch_set_one_graph failed")
         self.systems = []
         for i, w in enumerate(workloads_):
             m = _BatchMember(lib().rbfib_batch_grid(self._h, i), descs[i], w.n)
@@ -447,6 +455,10 @@ class Batch:
         if st != OK:
             raise RbfibError(st, "batch_sem_step failed")
         return list(status), [i.as_dict() for i in infos]
+
+    def graph_steps(self):
+        """Batch steps run as one graph launch (the one-graph form)."""
+        return int(lib().rbfib_batch_graph_steps(self._h))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -7,10 +7,14 @@
 // dealt round-robin to a fixed number of worker streams (so each stream gets
 // an even share of large and small systems), the workers' host threads
 // launch in parallel, and the small kernels of different systems overlap on
-// the GPU.  Then every stream is synchronised once.
+// the GPU.  Then every stream is synchronised once.  In the one-graph form
+// (rbfib_batch_set_one_graph) every system's step is instead captured as a
+// branch of a single graph, and a batch step is that graph's one launch and
+// one synchronisation.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstring>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -27,6 +31,13 @@ void rbfib_grid_bind_stream(rbfib_grid* g, cudaStream_t s);
 bool rbfib_grid_step_launch(rbfib_grid* g, const rbfib_sem_params* p, uint64_t seed, uint64_t step,
                             uint32_t attempt, double* q, double* quat);
 int rbfib_grid_step_finish(rbfib_grid* g, rbfib_step_info* info);
+// The one-graph form (rbfib.cu): whether a grid's step can be captured now,
+// staging a step's counters, and capturing every system's step as parallel
+// branches of one graph.
+bool rbfib_grid_step_ready(rbfib_grid* g, const rbfib_sem_params* p, const double* q, const double* quat);
+void rbfib_grid_stage_step(rbfib_grid* g, uint64_t seed, uint64_t step, uint32_t attempt);
+bool rbfib_batch_graph_build(rbfib_grid* const* gs, int n, const rbfib_sem_params* params, double* const* q,
+                             double* const* quat, cudaStream_t s, cudaGraphExec_t* out);
 
 struct rbfib_batch {
   int n = 0;
@@ -36,7 +47,66 @@ struct rbfib_batch {
   std::vector<rbfib_grid*> grids;
   std::vector<double> cost;   // seconds of each system's last step (0 = not yet run)
   std::string err;
+  // one-graph form: every system's step as a branch of one graph, launched
+  // once per batch step on gstream; rebuilt when a system's parameters or
+  // configuration buffers change
+  int one_graph = 0;
+  cudaStream_t gstream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<rbfib_sem_params> gparams;
+  std::vector<double*> gq, gquat;
+  long long graph_steps = 0;   // batch steps run as one graph launch
 };
+
+namespace {
+
+bool same_params(const rbfib_sem_params& a, const rbfib_sem_params& c) {
+  return std::memcmp(&a, &c, sizeof(rbfib_sem_params)) == 0;
+}
+
+// One batch step as one graph launch; false (nothing launched) when some
+// system's step cannot be captured yet (its first step builds the body
+// block on the host) or the capture failed.
+bool batch_graph_step(rbfib_batch* b, const rbfib_sem_params* params, const uint64_t* seeds, uint64_t step,
+                      const uint32_t* attempts, double* const* q, double* const* quat, rbfib_step_info* infos,
+                      int32_t* status, int& first) {
+  bool valid = b->gexec != nullptr;
+  for (int i = 0; valid && i < b->n; ++i)
+    valid = same_params(b->gparams[i], params[i]) && b->gq[i] == q[i] && b->gquat[i] == quat[i];
+  if (!valid) {
+    for (int i = 0; i < b->n; ++i)
+      if (!rbfib_grid_step_ready(b->grids[i], &params[i], q[i], quat[i])) return false;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    if (!b->gstream && cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking) != cudaSuccess) {
+      b->gstream = nullptr;
+      return false;
+    }
+    for (cudaStream_t s : b->streams)
+      if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+    if (!rbfib_batch_graph_build(b->grids.data(), b->n, params, q, quat, b->gstream, &b->gexec)) return false;
+    b->gparams.assign(params, params + b->n);
+    b->gq.assign(q, q + b->n);
+    b->gquat.assign(quat, quat + b->n);
+  }
+  // work queued on the grids' own streams comes first
+  for (cudaStream_t s : b->streams)
+    if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+  for (int i = 0; i < b->n; ++i) rbfib_grid_stage_step(b->grids[i], seeds[i], step, attempts ? attempts[i] : 0u);
+  if (cudaGraphLaunch(b->gexec, b->gstream) != cudaSuccess || cudaStreamSynchronize(b->gstream) != cudaSuccess) {
+    first = RBFIB_ECUDA;
+    for (int i = 0; i < b->n; ++i) status[i] = RBFIB_ECUDA;
+    return true;
+  }
+  ++b->graph_steps;
+  for (int i = 0; i < b->n; ++i) status[i] = rbfib_grid_step_finish(b->grids[i], infos ? &infos[i] : nullptr);
+  first = RBFIB_OK;
+  for (int i = 0; i < b->n; ++i)
+    if (status[i] != RBFIB_OK && status[i] != RBFIB_EREJECT && first == RBFIB_OK) first = status[i];
+  return true;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -73,6 +143,9 @@ int rbfib_create_batch(int32_t n_sys, const rbfib_grid_desc* descs, int32_t n_wo
 
 void rbfib_destroy_batch(rbfib_batch* b) {
   if (!b) return;
+  if (b->gstream) cudaStreamSynchronize(b->gstream);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->gstream) cudaStreamDestroy(b->gstream);
   for (rbfib_grid* g : b->grids) rbfib_destroy(g);
   for (cudaStream_t s : b->streams) {
     cudaStreamSynchronize(s);
@@ -80,6 +153,14 @@ void rbfib_destroy_batch(rbfib_batch* b) {
   }
   delete b;
 }
+
+int rbfib_batch_set_one_graph(rbfib_batch* b, int32_t on) {
+  if (!b || (on != 0 && on != 1)) return RBFIB_EINVAL;
+  b->one_graph = on;
+  return RBFIB_OK;
+}
+
+int64_t rbfib_batch_graph_steps(const rbfib_batch* b) { return b ? b->graph_steps : -1; }
 
 rbfib_grid* rbfib_batch_grid(rbfib_batch* b, int32_t sys) {
   if (!b || sys < 0 || sys >= b->n) return nullptr;
@@ -90,6 +171,10 @@ int rbfib_batch_sem_step(rbfib_batch* b, const rbfib_sem_params* params, const u
                          const uint32_t* attempts, double* const* q, double* const* quat, rbfib_step_info* infos,
                          int32_t* status) {
   if (!b || !params || !seeds || !q || !quat || !status) return RBFIB_EINVAL;
+  if (b->one_graph) {
+    int first = RBFIB_OK;
+    if (batch_graph_step(b, params, seeds, step, attempts, q, quat, infos, status, first)) return first;
+  }
   // largest systems first, dealt round-robin to the worker streams
   std::vector<double> key(b->n);
   for (int i = 0; i < b->n; ++i) {

@@ -2210,6 +2210,96 @@ bool rbfib_grid_step_launch(rbfib_grid* g, const rbfib_sem_params* p, uint64_t s
   }
 }
 
+// Whether a grid's device-driven step can be captured now for these
+// arguments (the checks of rbfib_grid_step_launch, and a valid body block).
+bool rbfib_grid_step_ready(rbfib_grid* g, const rbfib_sem_params* p, const double* q, const double* quat) {
+  return g && p && !(g->nb > 0 && (!q || !quat)) && p->dt > 0 && p->kT >= 0 && g->step_graphs &&
+         (p->no_rfd == 0 || p->no_rfd == 1) && p->reserved == 0 && step_graph_ok(g);
+}
+
+// Puts a step's random-stream counters in the grid's pinned buffer, from
+// which the batch graph's first node for this grid copies them.
+void rbfib_grid_stage_step(rbfib_grid* g, uint64_t seed, uint64_t step, uint32_t attempt) {
+  unsigned long long* hs = (unsigned long long*)(g->h_pinned + 48);
+  hs[0] = seed; hs[1] = step; hs[2] = attempt;
+  g->last_step_dev = 1;
+}
+
+// Captures the device-driven SEM steps of grids gs[0..n) as n parallel
+// branches of one graph, instantiated into *out: each branch copies its
+// grid's staged counters to the device, runs the step (restart cycles,
+// refinement sweeps and the body block's warm start in the grid's own
+// conditional nodes) and copies the step's report back to the grid's pinned
+// buffer, as step_graph_launch does for one grid.  s is the stream the
+// capture starts on (and the graph is launched on).  Returns false, with
+// nothing captured left behind, when a grid is not ready or the capture or
+// instantiation fails.
+bool rbfib_batch_graph_build(rbfib_grid* const* gs, int n, const rbfib_sem_params* params, double* const* q,
+                             double* const* quat, cudaStream_t s, cudaGraphExec_t* out) {
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (!rbfib_grid_step_ready(gs[i], &params[i], q[i], quat[i])) return false;
+  cudaGraph_t graph = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins(n, nullptr);
+  std::vector<cudaStream_t> saved(n, nullptr);
+  for (int i = 0; i < n; ++i) saved[i] = gs[i]->s;
+  bool ok = true;
+  try {
+    ck(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    for (int i = 0; i < n; ++i) ck(cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming));
+    ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    ck(cudaEventRecord(fork, s));
+    for (int i = 0; i < n; ++i) {
+      rbfib_grid* g = gs[i];
+      const long long l0 = rbfib::g_launches.load();
+      g->dev = true;
+      g->cap_depth = 0;
+      g->cap_bodies = 0;
+      g->s = cap_stream(g, 0);
+      ck(cudaStreamWaitEvent(g->s, fork, 0));
+      ck(cudaMemcpyAsync(g->dstep.p, g->h_pinned + 48, sizeof(unsigned long long) * 3, cudaMemcpyHostToDevice,
+                         g->s));
+      rbfib_step_info loc{};
+      sem_step_body(g, &params[i], 0, 0, 0, q[i], quat[i], loc);
+      ck(cudaMemcpyAsync(g->h_pinned + 24, g->dinfo.p, sizeof(int) * 32, cudaMemcpyDeviceToHost, g->s));
+      ck(cudaMemcpyAsync(g->h_pinned + 52, g->drel.p, sizeof(double) * 4, cudaMemcpyDeviceToHost, g->s));
+      ck(cudaMemcpyAsync(g->h_pinned + 56, g->dwarm.p, sizeof(long long), cudaMemcpyDeviceToHost, g->s));
+      ck(cudaEventRecord(joins[i], g->s));
+      ck(cudaStreamWaitEvent(s, joins[i], 0));
+      const long long captured = (long long)rbfib::g_launches.load() - l0;
+      g->cap_outside = captured - g->cap_bodies;
+      rbfib::g_launches.fetch_sub((unsigned long long)captured);   // captured, not launched
+      g->dev = false;
+      g->cap_depth = 0;
+      g->s = saved[i];
+    }
+    ck(cudaStreamEndCapture(s, &graph));
+    ck(cudaGraphInstantiate(out, graph, 0));
+  } catch (CudaError&) {
+    ok = false;
+    cudaStreamCaptureStatus cst;
+    if (cudaStreamIsCapturing(s, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+      cudaGraph_t t = nullptr;
+      cudaStreamEndCapture(s, &t);
+      if (t) cudaGraphDestroy(t);
+    }
+    cudaGetLastError();
+    if (*out) cudaGraphExecDestroy(*out);
+    *out = nullptr;
+  }
+  for (int i = 0; i < n; ++i) {
+    gs[i]->dev = false;
+    gs[i]->cap_depth = 0;
+    gs[i]->s = saved[i];
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (fork) cudaEventDestroy(fork);
+  for (cudaEvent_t e : joins)
+    if (e) cudaEventDestroy(e);
+  return ok;
+}
+
 int rbfib_grid_step_finish(rbfib_grid* g, rbfib_step_info* info) {
   try {
     ck(cudaGetLastError());

@@ -71,3 +71,50 @@ def test_autotuner_picks_a_candidate(B):
     # the smoothing sweeps take one of the candidate block sizes
     assert t[0] == 0 and t[1] == 0
     assert all(v in (64, 128, 256, 512) for v in t[2:])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "refined"])
+def test_one_graph_batch_matches_worker_streams(B, precision):
+    # the same ensemble advanced by the worker streams and by one graph launch
+    # per batch step (every system a branch of the graph), three steps each
+    ws = _systems()
+    prec = B.FP64 if precision == "fp64" else B.FP32_REFINED
+    for w in ws:
+        w.rtol = 1e-11
+    runs = []
+    for one_graph in (False, True):
+        batch = B.Batch(ws, precision=prec, workers=3, one_graph=one_graph)
+        q = [torch.tensor(w.q.ravel(), device="cuda") for w in ws]
+        quat = [torch.tensor(w.quat.ravel(), device="cuda") for w in ws]
+        params = [B.sem_params(w.potentials, dt=0.05, kT=1.0) for w in ws]
+        seeds = [2000 + i for i in range(len(ws))]
+        hist = []
+        for k in range(3):
+            status, infos = batch.sem_step(params, seeds, k, q, quat)
+            assert all(s == 0 for s in status)
+            for info in infos:
+                for key in ("solve_rfd", "solve_stokes", "solve_main"):
+                    assert info[key]["rel_residual"] <= 1e-11 and info[key]["iterations"] > 0
+            hist.append([(x.cpu().numpy().copy(), y.cpu().numpy().copy()) for x, y in zip(q, quat)])
+        # captured once, then relaunched (the configuration buffers stay the same)
+        runs.append((hist, batch.graph_steps()))
+        batch.close()
+    (h0, n0), (h1, n1) = runs
+    assert n0 == 0 and n1 == 3
+    for k in range(3):
+        for i, w in enumerate(ws):
+            # the changes since the start agree (FP32 atomics in the refined
+            # mode's spreading sum in another order on each path)
+            assert rel(h1[k][i][0] - w.q.ravel(), h0[k][i][0] - w.q.ravel()) < 1e-9
+            assert rel(h1[k][i][1] - w.quat.ravel(), h0[k][i][1] - w.quat.ravel()) < 1e-9
+
+
+def test_one_graph_flag_is_checked(B):
+    w = workloads.small_case(n=(12, 12, 12), n_bodies=1, blobs=12, seed=5)
+    batch = B.Batch([w], workers=1)
+    assert B.lib().rbfib_batch_set_one_graph(batch._h, 2) == B.EINVAL
+    assert B.lib().rbfib_batch_set_one_graph(batch._h, 1) == B.OK
+    assert B.lib().rbfib_batch_set_one_graph(None, 1) == B.EINVAL
+    assert B.lib().rbfib_batch_graph_steps(None) == -1
+    assert batch.graph_steps() == 0
+    batch.close()

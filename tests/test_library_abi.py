@@ -45,7 +45,7 @@ def test_binding_argument_counts_match_header():
     hdr = "".join(open(os.path.join(ROOT, "include", f)).read()
                   for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
     decl = {}
-    for m in re.finditer(r"\b(?:int|void|const char\*|uint64_t|rbfib_grid\*)\s+(rbfib_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", hdr):
+    for m in re.finditer(r"\b(?:int|void|const char\*|uint64_t|int64_t|rbfib_grid\*)\s+(rbfib_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", hdr):
         args = [a for a in m.group(2).split(",") if a.strip() and a.strip() != "void"]
         decl[m.group(1)] = len(args)
     assert set(decl) == set(_declared())
