@@ -718,19 +718,43 @@ void givens_step(double* H, int ldh, double* cs, double* sn, double* g, int j, c
   note_launch();
 }
 
-// y = H[0:k,0:k]^{-1} g (upper triangular, column-major with leading dim ldh)
-__global__ void k_tri(const double* H, int ldh, const double* g, int k, double* y) {
-  pdl_entry();
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  for (int i = k - 1; i >= 0; --i) {
-    double acc = g[i];
-    for (int c = i + 1; c < k; ++c) acc -= H[(i64)c * ldh + i] * y[c];
-    y[i] = acc / H[(i64)i * ldh + i];
+// y = H[0:k,0:k]^{-1} g (upper triangular, column-major with leading dim
+// ldh; k <= kTriMax, the longest restart cycle), by one block of kTriMax
+// threads.  The triangle is staged in shared memory and the diagonal's
+// reciprocals formed in parallel; back substitution then goes column by
+// column: thread i forms y_i = r_i / H_ii from its own running entry r_i,
+// and after one barrier every thread t < i takes H_ti y_i off its r_t.  So
+// the dependent chain per column is one product, one barrier and one FMA
+// (the FP64 latency of this GPU made the one-thread row-by-row form, with
+// its entries read back from memory, take about 54 us at k = 33).
+constexpr int kTriMax = 64;
+RBFIB_DEVFN void tri_core(const double* H, int ldh, const double* g, int k, double* y) {
+  __shared__ double Hs[kTriMax][kTriMax];   // Hs[c][t] = H(t, c), t <= c
+  __shared__ double dinv[kTriMax], ys[kTriMax];
+  const int t = threadIdx.x;
+  for (int c = 0; c < k; ++c)
+    for (int i = t; i <= c; i += blockDim.x) Hs[c][i] = H[(i64)c * ldh + i];
+  double r = 0.0;
+  if (t < k) {
+    r = g[t];
+    dinv[t] = 1.0 / H[(i64)t * ldh + t];
   }
+  __syncthreads();
+  for (int i = k - 1; i >= 0; --i) {
+    if (t == i) ys[i] = r * dinv[i];
+    __syncthreads();
+    if (t < i) r = fma(-Hs[i][t], ys[i], r);
+  }
+  if (t < k) y[t] = ys[t];
+}
+
+__global__ void __launch_bounds__(kTriMax) k_tri(const double* H, int ldh, const double* g, int k, double* y) {
+  pdl_entry();
+  tri_core(H, ldh, g, k, y);
 }
 
 void tri_solve(const double* H, int ldh, const double* g, int k, double* y, cudaStream_t s) {
-  launch_k(k_tri, 1, 32, 0, s, H, ldh, g, k, y);
+  launch_k(k_tri, 1, kTriMax, 0, s, H, ldh, g, k, y);
   note_launch();
 }
 
@@ -931,19 +955,14 @@ template void scale_givens<float>(float*, const float*, i64, float*, double*, in
                                   const double*, const double*, const double*, double*, int*, const double*,
                                   cudaStream_t, const cudaGraphConditionalHandle*);
 
-__global__ void k_tri_dev(const double* H, int ldh, const double* g, const int* ist, double* y) {
+__global__ void __launch_bounds__(kTriMax) k_tri_dev(const double* H, int ldh, const double* g, const int* ist,
+                                                     double* y) {
   pdl_entry();
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int k = ist[0];
-  for (int i = k - 1; i >= 0; --i) {
-    double acc = g[i];
-    for (int c = i + 1; c < k; ++c) acc -= H[(i64)c * ldh + i] * y[c];
-    y[i] = acc / H[(i64)i * ldh + i];
-  }
+  tri_core(H, ldh, g, min(ist[0], kTriMax), y);
 }
 
 void tri_solve_dev(const double* H, int ldh, const double* g, const int* ist, double* y, cudaStream_t s) {
-  launch_k(k_tri_dev, 1, 32, 0, s, H, ldh, g, ist, y);
+  launch_k(k_tri_dev, 1, kTriMax, 0, s, H, ldh, g, ist, y);
   note_launch();
 }
 
