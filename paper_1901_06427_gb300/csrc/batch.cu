@@ -55,6 +55,7 @@ struct rbfib_batch {
   cudaGraphExec_t gexec = nullptr;
   std::vector<rbfib_sem_params> gparams;
   std::vector<double*> gq, gquat;
+  bool gfailed = false;        // the capture failed for the current key: not retried until it changes
   long long graph_steps = 0;   // batch steps run as one graph launch
 };
 
@@ -70,10 +71,11 @@ bool same_params(const rbfib_sem_params& a, const rbfib_sem_params& c) {
 bool batch_graph_step(rbfib_batch* b, const rbfib_sem_params* params, const uint64_t* seeds, uint64_t step,
                       const uint32_t* attempts, double* const* q, double* const* quat, rbfib_step_info* infos,
                       int32_t* status, int& first) {
-  bool valid = b->gexec != nullptr;
-  for (int i = 0; valid && i < b->n; ++i)
-    valid = same_params(b->gparams[i], params[i]) && b->gq[i] == q[i] && b->gquat[i] == quat[i];
-  if (!valid) {
+  bool same_key = (b->gexec != nullptr || b->gfailed) && (int)b->gparams.size() == b->n;
+  for (int i = 0; same_key && i < b->n; ++i)
+    same_key = same_params(b->gparams[i], params[i]) && b->gq[i] == q[i] && b->gquat[i] == quat[i];
+  if (same_key && b->gfailed) return false;
+  if (!same_key) {
     for (int i = 0; i < b->n; ++i)
       if (!rbfib_grid_step_ready(b->grids[i], &params[i], q[i], quat[i])) return false;
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
@@ -84,10 +86,11 @@ bool batch_graph_step(rbfib_batch* b, const rbfib_sem_params* params, const uint
     }
     for (cudaStream_t s : b->streams)
       if (cudaStreamSynchronize(s) != cudaSuccess) return false;
-    if (!rbfib_batch_graph_build(b->grids.data(), b->n, params, q, quat, b->gstream, &b->gexec)) return false;
     b->gparams.assign(params, params + b->n);
     b->gq.assign(q, q + b->n);
     b->gquat.assign(quat, quat + b->n);
+    b->gfailed = !rbfib_batch_graph_build(b->grids.data(), b->n, params, q, quat, b->gstream, &b->gexec);
+    if (b->gfailed) return false;
   }
   // work queued on the grids' own streams comes first
   for (cudaStream_t s : b->streams)

@@ -2278,12 +2278,18 @@ bool rbfib_batch_graph_build(rbfib_grid* const* gs, int n, const rbfib_sem_param
     ck(cudaGraphInstantiate(out, graph, 0));
   } catch (CudaError&) {
     ok = false;
-    cudaStreamCaptureStatus cst;
-    if (cudaStreamIsCapturing(s, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
-      cudaGraph_t t = nullptr;
-      cudaStreamEndCapture(s, &t);
-      if (t) cudaGraphDestroy(t);
-    }
+    // end the capture on the origin stream, then on any grid's capture
+    // stream that a failure left joined to it, so every stream is usable
+    auto end_capture = [](cudaStream_t st) {
+      cudaStreamCaptureStatus cst;
+      if (st && cudaStreamIsCapturing(st, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+        cudaGraph_t t = nullptr;
+        cudaStreamEndCapture(st, &t);
+        if (t) cudaGraphDestroy(t);
+      }
+    };
+    end_capture(s);
+    for (int i = 0; i < n; ++i) end_capture(gs[i]->cap_streams[0]);
     cudaGetLastError();
     if (*out) cudaGraphExecDestroy(*out);
     *out = nullptr;
