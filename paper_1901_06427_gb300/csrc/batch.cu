@@ -71,13 +71,15 @@ bool same_params(const rbfib_sem_params& a, const rbfib_sem_params& c) {
 bool batch_graph_step(rbfib_batch* b, const rbfib_sem_params* params, const uint64_t* seeds, uint64_t step,
                       const uint32_t* attempts, double* const* q, double* const* quat, rbfib_step_info* infos,
                       int32_t* status, int& first) {
+  // every system must be able to run device-driven now (a step that left a
+  // coupled body block invalid sends the next one to the host path)
+  for (int i = 0; i < b->n; ++i)
+    if (!rbfib_grid_step_ready(b->grids[i], &params[i], q[i], quat[i])) return false;
   bool same_key = (b->gexec != nullptr || b->gfailed) && (int)b->gparams.size() == b->n;
   for (int i = 0; same_key && i < b->n; ++i)
     same_key = same_params(b->gparams[i], params[i]) && b->gq[i] == q[i] && b->gquat[i] == quat[i];
   if (same_key && b->gfailed) return false;
   if (!same_key) {
-    for (int i = 0; i < b->n; ++i)
-      if (!rbfib_grid_step_ready(b->grids[i], &params[i], q[i], quat[i])) return false;
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
     if (!b->gstream && cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking) != cudaSuccess) {
