@@ -1,8 +1,8 @@
 """Host logic of the multi-rank bench path on CPU: two gloo ranks agree on the
 slowest rank's time, the whole-job rate counts every rank's steps, replicas
-get distinct seeds, and a non-zero rank of the reference arm exits without
-work.  (One process per GPU with independent replicas; no data-path
-collective.)"""
+get distinct seeds, a non-zero rank of the reference arm exits without
+work, and rank 0 of the reference arm prints one line of the bench contract.
+(One process per GPU with independent replicas; no data-path collective.)"""
 import os
 import socket
 import subprocess
@@ -59,3 +59,26 @@ def test_reference_arm_other_ranks_exit_without_work():
                         "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_reference_arm_prints_one_contract_line():
+    # rank 0 alone: the oracle timed on the host cores, one JSON line with the
+    # arm's own value repeated in cpu_baseline and e2e (no host-device copies)
+    import json
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--cpu-sample-rhs", "2"], env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "SEM steps/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0
+    assert d["ms_per_step"] == pytest.approx(1000.0 / d["value"], rel=1e-9)
+    assert d["config"]["workload"] == "two-sphere-48x48x32"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e2e = d["e2e"]
+    assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
